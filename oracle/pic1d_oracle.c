@@ -1,0 +1,923 @@
+/*
+ * pic1d_oracle.c -- plain FP64 CPU oracle of the per-step particle loop of the
+ * 1D particle-in-cell method for resonant-inverse-Compton (RICS) pair
+ * cascades on one dipole field line (Mahlmann, Philippov, Soudais,
+ * Beloborodov, Sironi: "1D PIC Simulations of Resonant Scattering-Driven Pair
+ * Cascades in Magnetar Magnetospheres").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load this file.  It shares no code,
+ * header, table or constant generator with the CUDA library; it is written to
+ * be read against the paper, not to be fast.  Every quantity is FP64.
+ *
+ * Sections of the paper followed (LaTeX equation labels in brackets):
+ *   geometry            App. B.2 (dipole B_d, theta_0, mu = B^r/B_d)
+ *   resonance           Sec. 2.1 [elandau, resonancerest, resomega]
+ *   scattering rate     Sec. 2.2 [scatteringNdot]
+ *   drag force          Sec. 2.2 [contdrag]
+ *   PIC cycle           Sec. 3 (CFL step, Ampere with external current,
+ *                       conductor walls, Strang-split drag, limiter,
+ *                       implicit midpoint [implicit], damping to p~)
+ *   MC RICS + pairs     Sec. 3, App. A.1-A.3 [exen, excitedgamma, scatlim1,
+ *                       perpemit, paremit] and the E_gamma(theta) formula
+ *
+ * Readings where the paper is silent or ambiguous (each one is a parameter or
+ * a documented choice, the CUDA library follows the same one):
+ *   - E at cell centres, charge at nodes, linear (CIC) shape; the current
+ *     through a face is the signed length of the particle path inside that
+ *     cell (the 1D charge-conserving deposit); gather interpolates E
+ *     linearly between cell centres, constant beyond the outer centres.
+ *   - RICS zones are decided per cell: b at the cell centre > b_thr gives
+ *     discrete scattering (+ pairs), otherwise continuous drag (SPLIT mode).
+ *   - tau_min = eta_min * sqrt(n_psi/n0) / omega_p0 with omega_p0 = 1/d0.
+ *   - Newton: 4 fixed iterations from the explicit-Euler guess.
+ *   - rest-frame photon direction before excitation: sign(mu_s - beta_s);
+ *     de-excitation angle drawn from (3/8)(1 + cos^2).
+ *   - pair members each take half the photon momentum along s, placed at
+ *     the parent's new position; none is made if that position left the line.
+ *   - the pair cap compares the cell's lepton weight at the start of the
+ *     step (integer fixed-point sums) against n_max.
+ *   - surface supply (RATE): neutral e- + ion pairs injected per footpoint
+ *     per step at the rate that carries j_ext, inward half-Maxwellian.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* physical constants (CODATA 2018)                                          */
+/* ------------------------------------------------------------------------ */
+#define ORC_R_E      2.8179403262e-13   /* classical electron radius [cm]   */
+#define ORC_LAMBDABAR 3.8615926796e-11  /* reduced Compton wavelength [cm]  */
+#define ORC_ME_KEV   510.99895          /* m_e c^2 [keV]                    */
+#define ORC_PI       3.14159265358979323846
+
+/* enums shared by value with the Python side */
+enum { ORC_PHOTON_RADIAL = 0, ORC_PHOTON_DISK = 1 };
+enum { ORC_DRAG_OFF = 0, ORC_DRAG_CLOSED = 1, ORC_DRAG_TABLE = 2 };
+enum { ORC_RICS_SPLIT = 0, ORC_RICS_DRAG_PLUS_PAIRS = 1 };
+enum { ORC_INJECT_NONE = 0, ORC_INJECT_RATE = 1 };
+enum { ORC_SP_ELEC = 0, ORC_SP_POSI = 1, ORC_SP_ION = 2, ORC_SP_ATMO = 3 };
+
+#define ORC_TAG_RICS 0x52494353u   /* counter word 3 of the scattering draw */
+#define ORC_TAG_INJ  0x494E4A31u   /* counter word 3 of the injection draw  */
+#define ORC_S_BITS   12            /* weight fixed point: w_int = rint(w*2^12) */
+
+typedef struct {
+  double r_eq; int32_t n_cells; double cfl; double b_star; int32_t b_convention;
+  double kT_keV; int32_t photon_model; int32_t drag_law; double drag_scale;
+  int32_t table_n_gamma; int32_t table_n_s; double table_log10g_max;
+  int32_t quad_n_mu; int32_t quad_n_phi;
+  double eta_min; int32_t rics_mode; int32_t mc_on;
+  double cells_per_skin_depth; double j_psi; double n0_ppc; double mass_ratio;
+  int32_t inject_mode; double inject_T;
+  int32_t pairs_on; double b_pair_threshold; double pair_energy_threshold; double n_max_ppc;
+  uint64_t seed; double r_star_cm;
+} orc_params;
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11 "Parallel random        */
+/* numbers: as easy as 1, 2, 3"): 10 rounds of a multiply-xor bijection on   */
+/* a 128-bit counter under a 64-bit key bumped by Weyl constants.            */
+/* ------------------------------------------------------------------------ */
+void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+  uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+  uint32_t k0 = key_in[0], k1 = key_in[1];
+  for (int r = 0; r < 10; ++r) {
+    uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n1 = lo1;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    uint32_t n3 = lo0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* 24-bit uniform in [0,1): identical in FP32 and FP64 */
+static double orc_u24(uint32_t x) { return (double)(x >> 8) * (1.0 / 16777216.0); }
+
+/* SplitMix64 finaliser (Steele, Lea, Flood 2014) -- used only to derive
+ * stable identifiers for created particles. */
+uint64_t orc_splitmix64(uint64_t z)
+{
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+uint64_t orc_child_id(uint64_t parent, int64_t step, int member)
+{
+  return orc_splitmix64(parent ^ orc_splitmix64((uint64_t)step * 2u + (uint64_t)member))
+         | 0x8000000000000000ull;
+}
+
+uint64_t orc_inject_id(int64_t step, int foot, int64_t slot, int member)
+{
+  uint64_t key = ((uint64_t)step << 24) ^ ((uint64_t)foot << 23) ^ ((uint64_t)slot << 1) ^ (uint64_t)member;
+  return orc_splitmix64(key ^ 0x5A17A5EEDull) | 0x8000000000000000ull;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gauss-Legendre nodes on [-1,1] (Newton on the three-term recurrence).     */
+/* ------------------------------------------------------------------------ */
+void orc_gauss_legendre(int n, double* x, double* w)
+{
+  for (int i = 0; i < n; ++i) {
+    double z = cos(ORC_PI * (i + 0.75) / (n + 0.5));
+    double pp = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      double p1 = 1.0, p2 = 0.0;
+      for (int j = 1; j <= n; ++j) {
+        double p3 = p2; p2 = p1;
+        p1 = ((2.0 * j - 1.0) * z * p2 - (j - 1.0) * p3) / j;
+      }
+      pp = n * (z * p1 - p2) / (z * z - 1.0);
+      double dz = p1 / pp;
+      z -= dz;
+      if (fabs(dz) < 1e-16) break;
+    }
+    {
+      double p1 = 1.0, p2 = 0.0;
+      for (int j = 1; j <= n; ++j) {
+        double p3 = p2; p2 = p1;
+        p1 = ((2.0 * j - 1.0) * z * p2 - (j - 1.0) * p3) / j;
+      }
+      pp = n * (z * p1 - p2) / (z * z - 1.0);
+    }
+    x[i] = -z;                                   /* ascending order */
+    w[i] = 2.0 / ((1.0 - z * z) * pp * pp);
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Dipole field-line geometry (App. B.2).  The line r = r_eq sin^2(theta)     */
+/* runs from the northern footpoint theta_0 = arcsin(sqrt(R_star/r_eq)) to the    */
+/* southern one pi - theta_0.  Arc length (in R_star):                           */
+/*   ds/dtheta = r_eq sin(theta) sqrt(1 + 3 cos^2 theta).                    */
+/* s(theta) is the integral written out with composite Gauss-Legendre.       */
+/* ------------------------------------------------------------------------ */
+static double orc_dsdtheta(double r_eq, double th)
+{
+  double c = cos(th);
+  return r_eq * sin(th) * sqrt(1.0 + 3.0 * c * c);
+}
+
+double orc_theta0(double r_eq) { return asin(sqrt(1.0 / r_eq)); }
+
+double orc_arc_length(double r_eq, double theta)
+{
+  static int init = 0;
+  static double gx[16], gw[16];
+  if (!init) { orc_gauss_legendre(16, gx, gw); init = 1; }
+  double a = orc_theta0(r_eq), b = theta;
+  const int panels = 32;
+  double h = (b - a) / panels, sum = 0.0;
+  for (int k = 0; k < panels; ++k) {
+    double lo = a + k * h;
+    for (int i = 0; i < 16; ++i) {
+      double th = lo + 0.5 * h * (gx[i] + 1.0);
+      sum += 0.5 * h * gw[i] * orc_dsdtheta(r_eq, th);
+    }
+  }
+  return sum;
+}
+
+double orc_line_length(double r_eq) { return orc_arc_length(r_eq, ORC_PI - orc_theta0(r_eq)); }
+
+/* invert s(theta) = s_target (s in R_star) by Newton from a bisection start */
+double orc_theta_of_s(double r_eq, double s_target)
+{
+  double t0 = orc_theta0(r_eq), t1 = ORC_PI - t0;
+  double lo = t0, hi = t1;
+  for (int it = 0; it < 30; ++it) {                 /* coarse bisection */
+    double mid = 0.5 * (lo + hi);
+    if (orc_arc_length(r_eq, mid) < s_target) lo = mid; else hi = mid;
+  }
+  double th = 0.5 * (lo + hi);
+  for (int it = 0; it < 8; ++it) {
+    double f = orc_arc_length(r_eq, th) - s_target;
+    double d = orc_dsdtheta(r_eq, th);
+    if (d <= 0.0) break;
+    double dt = f / d;
+    th -= dt;
+    if (fabs(dt) < 1e-15) break;
+  }
+  if (th < t0) th = t0;
+  if (th > t1) th = t1;
+  return th;
+}
+
+/* x = r/R_star, b = B/B_QED, mu_s = B^r/B (cosine between the outward radial
+ * direction and +s, the direction of increasing theta). */
+void orc_field_at_theta(const orc_params* p, double th, double* x, double* b, double* mu)
+{
+  double c = cos(th), s = sin(th);
+  double xr = p->r_eq * s * s;
+  double root = sqrt(1.0 + 3.0 * c * c);
+  double bb = p->b_star * root / (xr * xr * xr);
+  if (p->b_convention == 1) bb *= 0.5;
+  *x = xr; *b = bb; *mu = 2.0 * c / root;
+}
+
+/* ------------------------------------------------------------------------ */
+/* RICS physics (Sec. 2.2).  Momentum u = gamma*beta_s along +s.              */
+/* Theta = kT/(m_e c^2).  Resonant photon energy in units of m_e c^2:          */
+/*   eps = b / (gamma (1 - beta_s mu_k))                       [resomega]    */
+/* Rate per lepton (per R_star/c, i.e. N^ = Ndot R_star/c)            [scatteringNdot] */
+/*   N^ = r_e R_star/(4 pi lbar^2 gamma) Int dOmega eps^2/(exp(eps/Theta) - 1)   */
+/* Momentum given per scattering along s: gamma b mu~_k, mu~ = (mu_k - beta)/ */
+/* (1 - beta mu_k); the drag F^ = F R_star/(m_e c^2) is the rate-weighted sum.    */
+/* For radially streaming photons (solid angle pi/x^2, mu_k = mu_s) the sum   */
+/* is the closed form                                           [contdrag]   */
+/*   F^ = r_e R_star Theta^3/(4 x^2 lbar^2) gamma (mu_s - beta_s) g(y),          */
+/*   g(y) = y^3/(e^y - 1), y = eps/Theta.                                    */
+/* ------------------------------------------------------------------------ */
+double orc_g(double y) { return y * y * y / expm1(y); }
+
+static double orc_theta_T(const orc_params* p) { return p->kT_keV / ORC_ME_KEV; }
+
+/* 1 - beta_s*m computed without cancellation when beta -> 1 */
+static double orc_one_minus_beta_m(double u, double gam, double m)
+{
+  double beta = fabs(u) / gam;
+  double sm = (u >= 0.0) ? m : -m;              /* cosine to the velocity */
+  double omb = 1.0 / (gam * (gam + fabs(u)));   /* 1 - |beta| */
+  (void)beta;
+  return (1.0 - sm) + sm * omb;
+}
+
+void orc_radial(const orc_params* p, double u, double x, double b, double mu,
+                double* F, double* Nhat)
+{
+  double th = orc_theta_T(p);
+  double gam = sqrt(1.0 + u * u);
+  double beta = u / gam;
+  double D = orc_one_minus_beta_m(u, gam, mu);
+  double eps = b / (gam * D);
+  double y = eps / th;
+  double pref = ORC_R_E * p->r_star_cm / (ORC_LAMBDABAR * ORC_LAMBDABAR);
+  *F = pref * th * th * th / (4.0 * x * x) * gam * (mu - beta) * orc_g(y);
+  *Nhat = pref / (4.0 * x * x * gam) * eps * eps / expm1(y);
+}
+
+/* Stellar disk of uniform blackbody intensity: directions within alpha_max
+ * = arcsin(1/x) of the radial; mu_k = cos(a) mu_s + sin(a) cos(phi) sqrt(1-mu_s^2).
+ * Gauss-Legendre in cos(a) x midpoint rule in phi on [0, pi] (the integrand
+ * is even in phi). */
+void orc_disk(const orc_params* p, double u, double x, double b, double mu,
+              double* F, double* Nhat)
+{
+  int na = p->quad_n_mu, nph = p->quad_n_phi;
+  double gx[256], gw[256];
+  if (na > 256) na = 256;
+  orc_gauss_legendre(na, gx, gw);
+  double th = orc_theta_T(p);
+  double gam = sqrt(1.0 + u * u);
+  double beta = u / gam;
+  double cmax = (x > 1.0) ? sqrt(1.0 - 1.0 / (x * x)) : 0.0;   /* cos(alpha_max) */
+  double smu = sqrt(fmax(0.0, 1.0 - mu * mu));
+  double sumN = 0.0, sumF = 0.0;
+  for (int i = 0; i < na; ++i) {
+    double ca = cmax + (1.0 - cmax) * 0.5 * (gx[i] + 1.0);
+    double wa = (1.0 - cmax) * 0.5 * gw[i];
+    double sa = sqrt(fmax(0.0, 1.0 - ca * ca));
+    for (int j = 0; j < nph; ++j) {
+      double ph = ORC_PI * (j + 0.5) / nph;
+      double wph = 2.0 * ORC_PI / nph;           /* 2 * (pi/nph) */
+      double mk = ca * mu + sa * cos(ph) * smu;
+      double D = orc_one_minus_beta_m(u, gam, mk);
+      double eps = b / (gam * D);
+      double y = eps / th;
+      double occ = eps * eps / expm1(y);         /* eps^2/(e^y - 1) */
+      double dN = wa * wph * occ;
+      sumN += dN;
+      sumF += dN * gam * b * (mk - beta) / D;    /* momentum per scattering */
+    }
+  }
+  double pref = ORC_R_E * p->r_star_cm / (4.0 * ORC_PI * ORC_LAMBDABAR * ORC_LAMBDABAR * gam);
+  *Nhat = pref * sumN;
+  *F = pref * sumF;
+}
+
+void orc_photon_field(const orc_params* p, double u, double x, double b, double mu,
+                      double* F, double* Nhat)
+{
+  if (p->photon_model == ORC_PHOTON_DISK) orc_disk(p, u, x, b, mu, F, Nhat);
+  else orc_radial(p, u, x, b, mu, F, Nhat);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Drag/rate table: axes log10(gamma) in [0, G] (n_g points), s/L in [0,1]    */
+/* (n_s points), sign of u; entries F^ and ln N^ (floored at -700).           */
+/* layout: ((sign * n_s + js) * n_g + ig) * 2 + {0: F^, 1: ln N^}             */
+/* ------------------------------------------------------------------------ */
+void orc_build_table(const orc_params* p, double* table)
+{
+  int ng = p->table_n_gamma, ns = p->table_n_s;
+  double L = orc_line_length(p->r_eq);
+  for (int js = 0; js < ns; ++js) {
+    double sR = L * (double)js / (ns - 1);
+    double th = orc_theta_of_s(p->r_eq, sR);
+    double x, b, mu;
+    orc_field_at_theta(p, th, &x, &b, &mu);
+    for (int sg = 0; sg < 2; ++sg) {
+      for (int ig = 0; ig < ng; ++ig) {
+        double lg = p->table_log10g_max * (double)ig / (ng - 1);
+        double gam = pow(10.0, lg);
+        double au = sqrt(fmax(0.0, gam * gam - 1.0));
+        double u = sg ? -au : au;
+        double F, N;
+        orc_photon_field(p, u, x, b, mu, &F, &N);
+        double lnN = (N > 0.0) ? log(N) : -700.0;
+        if (lnN < -700.0) lnN = -700.0;
+        size_t k = (((size_t)sg * ns + js) * ng + ig) * 2;
+        table[k] = F;
+        table[k + 1] = lnN;
+      }
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Simulation state                                                          */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  int64_t n_alive[4];
+  int64_t pairs_created, pairs_dropped_cap, pairs_rejected_nmax, pairs_lost_wall;
+  int64_t lost_north, lost_south, injected, scatters, psc_clamped, limiter_branch, newton_branch;
+  double field_energy, kinetic_energy, ext_work, vc, charge, ke_lost;
+} orc_diag;
+
+typedef struct {
+  orc_params p;
+  int N;
+  double L_R;       /* line length in R_star                                  */
+  double R_cells;   /* R_star in cells                                        */
+  double dt;        /* time step in cell-crossing times                   */
+  double q_p;       /* macro charge per unit weight                       */
+  double j_ext;     /* external (twist) current density                   */
+  double tau_min;   /* drag-time floor [code time]                        */
+  double *node_x, *node_b, *node_mu;   /* N+1 nodes                       */
+  unsigned char* zone;                 /* N cells: b(centre) > b_thr      */
+  double* table;
+  double *E, *J;
+  int64_t* dens;                       /* lepton weight per cell, w_int   */
+  int64_t n, cap;
+  double *s, *u, *w;
+  int32_t* sp;
+  uint64_t* id;
+  int64_t step;
+  double inj_acc[2];
+  orc_diag d;
+} orc_sim;
+
+static const double ORC_QM[4]   = { -1.0, 1.0, 0.0 /* set per sim */, -1.0 };
+static const double ORC_QS[4]   = { -1.0, 1.0, 1.0, -1.0 };   /* charge sign */
+
+static int orc_is_lepton(int sp) { return sp != ORC_SP_ION; }
+static double orc_mass(const orc_sim* S, int sp) { return sp == ORC_SP_ION ? S->p.mass_ratio : 1.0; }
+static double orc_qm(const orc_sim* S, int sp) { return sp == ORC_SP_ION ? 1.0 / S->p.mass_ratio : ORC_QM[sp]; }
+
+static int64_t orc_wint(double w) { return (int64_t)llrint(w * (double)(1 << ORC_S_BITS)); }
+
+size_t orc_sim_size(void) { return sizeof(orc_sim); }
+
+static void orc_grow(orc_sim* S, int64_t need)
+{
+  if (need <= S->cap) return;
+  int64_t cap = S->cap ? S->cap : 1024;
+  while (cap < need) cap *= 2;
+  S->s = realloc(S->s, cap * sizeof(double));
+  S->u = realloc(S->u, cap * sizeof(double));
+  S->w = realloc(S->w, cap * sizeof(double));
+  S->sp = realloc(S->sp, cap * sizeof(int32_t));
+  S->id = realloc(S->id, cap * sizeof(uint64_t));
+  S->cap = cap;
+}
+
+/* linear interpolation of a node table at s (cells) */
+static double orc_node_interp(const orc_sim* S, const double* tab, double s)
+{
+  if (s <= 0.0) return tab[0];
+  if (s >= S->N) return tab[S->N];
+  int i = (int)floor(s);
+  if (i >= S->N) i = S->N - 1;
+  double f = s - i;
+  return (1.0 - f) * tab[i] + f * tab[i + 1];
+}
+
+orc_sim* orc_create(const orc_params* p, const double* table_or_null)
+{
+  orc_sim* S = (orc_sim*)calloc(1, sizeof(orc_sim));
+  S->p = *p;
+  S->N = p->n_cells;
+  S->L_R = orc_line_length(p->r_eq);
+  S->R_cells = S->N / S->L_R;
+  S->dt = p->cfl;
+  /* omega_p0 = 1/d0 at density n0 (weight n0_ppc per cell): 4 pi q_p n0 =
+   * omega_p0^2 with q/m = 1.  j_ext = j_psi n0 e c (Sec. 3: j_psi/(n0 e c)). */
+  double n0 = p->n0_ppc;
+  S->q_p = 1.0 / (4.0 * ORC_PI * p->cells_per_skin_depth * p->cells_per_skin_depth * n0);
+  S->j_ext = p->j_psi * n0 * S->q_p;
+  /* eta_min = tau_min omega_p0 = eta_min_param (n_psi/n0)^(1/2), n_psi/n0 = j_psi */
+  S->tau_min = (p->eta_min > 0.0 && p->j_psi > 0.0) ? p->eta_min * sqrt(p->j_psi) * p->cells_per_skin_depth : 0.0;
+  int N = S->N;
+  S->node_x = malloc((N + 1) * sizeof(double));
+  S->node_b = malloc((N + 1) * sizeof(double));
+  S->node_mu = malloc((N + 1) * sizeof(double));
+  for (int k = 0; k <= N; ++k) {
+    double th = orc_theta_of_s(p->r_eq, S->L_R * (double)k / N);
+    orc_field_at_theta(p, th, &S->node_x[k], &S->node_b[k], &S->node_mu[k]);
+  }
+  S->zone = malloc(N);
+  for (int c = 0; c < N; ++c) {
+    double th = orc_theta_of_s(p->r_eq, S->L_R * (c + 0.5) / N);
+    double x, b, mu;
+    orc_field_at_theta(p, th, &x, &b, &mu);
+    S->zone[c] = (b > p->b_pair_threshold) ? 1 : 0;
+  }
+  if (p->drag_law == ORC_DRAG_TABLE) {
+    size_t nt = (size_t)2 * p->table_n_s * p->table_n_gamma * 2;
+    S->table = malloc(nt * sizeof(double));
+    if (table_or_null) memcpy(S->table, table_or_null, nt * sizeof(double));
+    else orc_build_table(p, S->table);
+  }
+  S->E = calloc(N, sizeof(double));
+  S->J = calloc(N, sizeof(double));
+  S->dens = calloc(N, sizeof(int64_t));
+  return S;
+}
+
+void orc_free(orc_sim* S)
+{
+  if (!S) return;
+  free(S->node_x); free(S->node_b); free(S->node_mu); free(S->zone); free(S->table);
+  free(S->E); free(S->J); free(S->dens);
+  free(S->s); free(S->u); free(S->w); free(S->sp); free(S->id);
+  free(S);
+}
+
+static void orc_recount_density(orc_sim* S)
+{
+  memset(S->dens, 0, S->N * sizeof(int64_t));
+  for (int64_t k = 0; k < S->n; ++k) {
+    if (!orc_is_lepton(S->sp[k])) continue;
+    int c = (int)floor(S->s[k]);
+    if (c < 0) c = 0;
+    if (c >= S->N) c = S->N - 1;
+    S->dens[c] += orc_wint(S->w[k]);
+  }
+}
+
+void orc_set_particles(orc_sim* S, int64_t n, const double* s, const double* u,
+                       const double* w, const int32_t* sp, const uint64_t* id)
+{
+  orc_grow(S, n);
+  S->n = n;
+  memcpy(S->s, s, n * sizeof(double));
+  memcpy(S->u, u, n * sizeof(double));
+  memcpy(S->w, w, n * sizeof(double));
+  memcpy(S->sp, sp, n * sizeof(int32_t));
+  memcpy(S->id, id, n * sizeof(uint64_t));
+  orc_recount_density(S);
+}
+
+void orc_set_field(orc_sim* S, const double* E) { memcpy(S->E, E, S->N * sizeof(double)); }
+void orc_set_step(orc_sim* S, int64_t step) { S->step = step; }
+int64_t orc_get_n(const orc_sim* S) { return S->n; }
+
+void orc_get_particles(const orc_sim* S, double* s, double* u, double* w, int32_t* sp, uint64_t* id)
+{
+  memcpy(s, S->s, S->n * sizeof(double));
+  memcpy(u, S->u, S->n * sizeof(double));
+  memcpy(w, S->w, S->n * sizeof(double));
+  memcpy(sp, S->sp, S->n * sizeof(int32_t));
+  memcpy(id, S->id, S->n * sizeof(uint64_t));
+}
+
+void orc_get_fields(const orc_sim* S, double* E, double* J)
+{
+  if (E) memcpy(E, S->E, S->N * sizeof(double));
+  if (J) memcpy(J, S->J, S->N * sizeof(double));
+}
+
+void orc_get_nodes(const orc_sim* S, double* x, double* b, double* mu, unsigned char* zone)
+{
+  if (x) memcpy(x, S->node_x, (S->N + 1) * sizeof(double));
+  if (b) memcpy(b, S->node_b, (S->N + 1) * sizeof(double));
+  if (mu) memcpy(mu, S->node_mu, (S->N + 1) * sizeof(double));
+  if (zone) memcpy(zone, S->zone, S->N);
+}
+
+void orc_get_scalars(const orc_sim* S, double* out)
+{
+  out[0] = S->L_R; out[1] = S->R_cells; out[2] = S->dt; out[3] = S->q_p;
+  out[4] = S->j_ext; out[5] = S->tau_min; out[6] = S->inj_acc[0]; out[7] = S->inj_acc[1];
+}
+
+void orc_get_density(const orc_sim* S, int64_t* dens) { memcpy(dens, S->dens, S->N * sizeof(int64_t)); }
+
+/* ------------------------------------------------------------------------ */
+/* Drag and rate at (u, s) in code units: du/dt = drag_scale F^ / R_cells,    */
+/* p_sc rate = drag_scale N^ / R_cells per cell-crossing time.               */
+/* dF is dF/du of the same interpolant (Newton derivative).                  */
+/* ------------------------------------------------------------------------ */
+static void orc_table_eval(const orc_sim* S, double u, double s, double* F, double* dF, double* lnN)
+{
+  const orc_params* p = &S->p;
+  int ng = p->table_n_gamma, ns = p->table_n_s;
+  double gam = sqrt(1.0 + u * u);
+  double dg = p->table_log10g_max / (ng - 1);
+  double t = log10(gam) / dg;
+  int clamped = 0;
+  if (t < 0.0) t = 0.0;
+  if (t > ng - 1) { t = ng - 1; clamped = 1; }
+  int i = (int)floor(t);
+  if (i > ng - 2) i = ng - 2;
+  double a = t - i;
+  double v = s / S->N * (ns - 1);
+  if (v < 0.0) v = 0.0;
+  if (v > ns - 1) v = ns - 1;
+  int j = (int)floor(v);
+  if (j > ns - 2) j = ns - 2;
+  double c = v - j;
+  int sg = (u >= 0.0) ? 0 : 1;
+  const double* T0 = S->table + (((size_t)sg * ns + j) * ng) * 2;
+  const double* T1 = S->table + (((size_t)sg * ns + j + 1) * ng) * 2;
+  double f00 = T0[2 * i], f10 = T0[2 * (i + 1)], f01 = T1[2 * i], f11 = T1[2 * (i + 1)];
+  double n00 = T0[2 * i + 1], n10 = T0[2 * (i + 1) + 1], n01 = T1[2 * i + 1], n11 = T1[2 * (i + 1) + 1];
+  *F = (1 - a) * (1 - c) * f00 + a * (1 - c) * f10 + (1 - a) * c * f01 + a * c * f11;
+  *lnN = (1 - a) * (1 - c) * n00 + a * (1 - c) * n10 + (1 - a) * c * n01 + a * c * n11;
+  if (dF) {
+    double dFdt = (1 - c) * (f10 - f00) + c * (f11 - f01);
+    double dtdu = clamped ? 0.0 : u / (gam * gam * log(10.0) * dg);
+    *dF = dFdt * dtdu;
+  }
+}
+
+/* closed-form (radial) drag derivative: d[gamma(mu-beta)]/du = beta mu - 1,
+ * D = gamma - u mu, dy/du = -y (beta - mu)/D, g'(y) = g (3/y - e^y/(e^y-1)). */
+static void orc_closed_eval(const orc_sim* S, double u, double s, double* F, double* dF, double* lnN)
+{
+  double x = orc_node_interp(S, S->node_x, s);
+  double b = orc_node_interp(S, S->node_b, s);
+  double mu = orc_node_interp(S, S->node_mu, s);
+  double Fh, Nh;
+  orc_radial(&S->p, u, x, b, mu, &Fh, &Nh);
+  *F = Fh;
+  *lnN = (Nh > 0.0) ? log(Nh) : -700.0;
+  if (dF) {
+    double th = orc_theta_T(&S->p);
+    double gam = sqrt(1.0 + u * u), beta = u / gam;
+    double D = gam * orc_one_minus_beta_m(u, gam, mu);
+    double y = b / (th * D);
+    double g = orc_g(y);
+    double K = ORC_R_E * S->p.r_star_cm / (ORC_LAMBDABAR * ORC_LAMBDABAR) * th * th * th / (4.0 * x * x);
+    double gp = g * (3.0 / y - 1.0 / (-expm1(-y)));
+    double dydu = -y * (beta - mu) / D;
+    *dF = K * ((beta * mu - 1.0) * g + gam * (mu - beta) * gp * dydu);
+  }
+}
+
+/* F and dF in code units (du per cell-crossing time), rate in code units */
+void orc_drag_code(const orc_sim* S, double u, double s, double* F, double* dF, double* rate)
+{
+  double Fh = 0.0, dFh = 0.0, lnN = -700.0;
+  if (S->p.drag_law == ORC_DRAG_TABLE) orc_table_eval(S, u, s, &Fh, &dFh, &lnN);
+  else if (S->p.drag_law == ORC_DRAG_CLOSED) orc_closed_eval(S, u, s, &Fh, &dFh, &lnN);
+  double k = S->p.drag_scale / S->R_cells;
+  *F = k * Fh;
+  if (dF) *dF = k * dFh;
+  if (rate) *rate = k * exp(lnN);
+}
+
+/* One drag update over dt/2 at fixed s (Sec. 3): limiter test, then either
+ * the implicit midpoint [implicit] by Newton or exponential damping to
+ * p~ = mu/sqrt(1-mu^2). */
+static double orc_drag_half(orc_sim* S, double u0, double s)
+{
+  double h = 0.5 * S->dt;
+  double F0, dF0;
+  orc_drag_code(S, u0, s, &F0, &dF0, NULL);
+  int newton = 1;
+  /* |dp/p0| ~ |F dt/(2 p0)| < dt/(2 tau_min)  <=>  |F| tau_min < |p0|;
+   * p0 = 0 always takes the damping branch */
+  if (S->tau_min > 0.0) newton = fabs(F0) * S->tau_min < fabs(u0);
+  if (newton) {
+    S->d.newton_branch++;
+    double u1 = u0 + h * F0;
+    for (int it = 0; it < 4; ++it) {
+      double F1, dF1;
+      orc_drag_code(S, u1, s, &F1, &dF1, NULL);
+      double G = u1 - u0 - 0.5 * h * (F0 + F1);
+      double dG = 1.0 - 0.5 * h * dF1;
+      if (dG < 0.5) dG = 0.5;
+      u1 -= G / dG;
+    }
+    return u1;
+  }
+  S->d.limiter_branch++;
+  double mu = orc_node_interp(S, S->node_mu, s);
+  double ut = mu / sqrt(1.0 - mu * mu);
+  return ut + (u0 - ut) * exp(-h / S->tau_min);
+}
+
+/* ------------------------------------------------------------------------ */
+/* RICS event kinematics (App. A).  Lepton u_i along +s, field b, photon      */
+/* arriving in the lepton rest frame along direction d = +-1 (along +s).     */
+/* Excitation [exen, excitedgamma]: the excited lepton (rest energy E_B =     */
+/* sqrt(1+2b)) moves in the old rest frame with gamma* = (E_B + 1/E_B)/2,    */
+/* gamma* beta* = b/E_B, along d.  De-excitation in its own rest frame at     */
+/* angle ct = cos(theta~): E'_g = (E_B - 1/E_B)/(1 + sqrt(ct^2 + (1-ct^2)/   */
+/* E_B^2)) (the E_gamma(theta) formula of App. A.2 without cancellation),     */
+/* lepton E'_e = E_B - E'_g, p'_e = -E'_g ct.  Boost back to the lab.         */
+/* out: [0] u_f, [1] E_gamma, [2] P_gamma (along s), [3] gamma_e, [4] u_e     */
+/* ------------------------------------------------------------------------ */
+void orc_rics_kinematics(double b, double d, double u_i, double ct, double* out)
+{
+  double EB = sqrt(1.0 + 2.0 * b);
+  double gs = 0.5 * (EB + 1.0 / EB);
+  double gbs = b / EB;                  /* gamma* beta* */
+  double gi = sqrt(1.0 + u_i * u_i);
+  double ge = gs * gi + d * gbs * u_i;  /* lab Lorentz factor of the excited lepton */
+  double ue = gs * u_i + d * gbs * gi;
+  double st2 = 1.0 - ct * ct;
+  double Eg = (EB - 1.0 / EB) / (1.0 + sqrt(ct * ct + st2 / (EB * EB)));
+  double Ee = EB - Eg, pe = -Eg * ct;
+  out[0] = ue * Ee + ge * pe;
+  out[1] = Eg * (ge + ue * ct);
+  out[2] = Eg * (ue + ge * ct);
+  out[3] = ge;
+  out[4] = ue;
+}
+
+/* cos(theta~) with density (3/8)(1 + c^2) from one uniform U: CDF
+ * (c^3 + 3c + 4)/8 = U, the depressed cubic solved by Cardano's formula:
+ * a = 4U - 2, t = cbrt(a + sqrt(a^2 + 1)), c = t - 1/t. */
+double orc_cos_dipole(double U)
+{
+  double a = 4.0 * U - 2.0;
+  double t = cbrt(a + sqrt(a * a + 1.0));
+  return t - 1.0 / t;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Charge-conserving deposit: the signed length of [a, b] inside every cell  */
+/* (the flux through that cell's E point), weighted by q w / dt.             */
+/* ------------------------------------------------------------------------ */
+static void orc_deposit_path(orc_sim* S, double a, double b, double qw)
+{
+  double lo = fmin(a, b), hi = fmax(a, b);
+  double sgn = (b >= a) ? 1.0 : -1.0;
+  int c0 = (int)floor(lo), c1 = (int)floor(hi);
+  if (c1 > S->N - 1) c1 = S->N - 1;
+  if (c0 < 0) c0 = 0;
+  for (int c = c0; c <= c1; ++c) {
+    double l = fmin(hi, (double)(c + 1)) - fmax(lo, (double)c);
+    if (l > 0.0) S->J[c] += sgn * qw * l * S->q_p / S->dt;
+  }
+}
+
+/* The same deposit in integers: positions in fixed point with F fractional
+ * bits, weights w_int = rint(w 2^12); J_int[c] = sum q_sign w_int len_c. */
+void orc_deposit_int(int N, int Fbits, int64_t n, const int64_t* p0, const int64_t* p1,
+                     const double* w, const int32_t* sp, int64_t* Jint)
+{
+  int64_t one = (int64_t)1 << Fbits, top = (int64_t)N << Fbits;
+  for (int64_t k = 0; k < n; ++k) {
+    int64_t a = p0[k], b = p1[k];
+    if (b < 0) b = 0;
+    if (b > top) b = top;
+    int64_t lo = a < b ? a : b, hi = a < b ? b : a;
+    int64_t sgn = (b >= a) ? 1 : -1;
+    int64_t qw = (int64_t)ORC_QS[sp[k]] * orc_wint(w[k]);
+    for (int64_t c = lo / one; c <= hi / one && c < N; ++c) {
+      int64_t cl = c * one, ch = cl + one;
+      int64_t l = (hi < ch ? hi : ch) - (lo > cl ? lo : cl);
+      if (l > 0) Jint[c] += sgn * qw * l;
+    }
+  }
+}
+
+/* E at s: linear between cell centres c + 1/2, constant beyond the ends */
+static double orc_gather(const orc_sim* S, double s)
+{
+  double x = s - 0.5;
+  int i = (int)floor(x);
+  if (i < 0) return S->E[0];
+  if (i >= S->N - 1) return S->E[S->N - 1];
+  double f = x - i;
+  return (1.0 - f) * S->E[i] + f * S->E[i + 1];
+}
+
+/* ------------------------------------------------------------------------ */
+/* One PIC cycle (Sec. 3), n -> n+1.  E at integer times, u at half times.    */
+/* ------------------------------------------------------------------------ */
+void orc_step(orc_sim* S)
+{
+  const orc_params* p = &S->p;
+  int N = S->N;
+  double dt = S->dt;
+  int64_t n0 = S->n;
+  /* created particles are collected here and appended at the end */
+  int64_t nc = 0, ccap = 1024;
+  double *cs = malloc(ccap * sizeof(double)), *cu = malloc(ccap * sizeof(double)), *cw = malloc(ccap * sizeof(double));
+  int32_t* csp = malloc(ccap * sizeof(int32_t));
+  uint64_t* cid = malloc(ccap * sizeof(uint64_t));
+  unsigned char* alive = malloc(n0 > 0 ? n0 : 1);
+  uint32_t key[2] = { (uint32_t)p->seed, (uint32_t)(p->seed >> 32) };
+  int64_t nmax_int = (p->n_max_ppc > 0.0) ? (int64_t)floor(p->n_max_ppc * (double)(1 << ORC_S_BITS)) : -1;
+  memset(S->J, 0, N * sizeof(double));
+  double E_old_sum_sq = 0.0;
+  for (int c = 0; c < N; ++c) E_old_sum_sq += S->E[c] * S->E[c];
+
+  for (int64_t k = 0; k < n0; ++k) {
+    int sp = S->sp[k];
+    double s = S->s[k], u = S->u[k], w = S->w[k];
+    int lep = orc_is_lepton(sp);
+    int cell = (int)floor(s);
+    if (cell < 0) cell = 0;
+    if (cell >= N) cell = N - 1;
+    int zone = S->zone[cell];
+    int cont = lep && p->drag_law != ORC_DRAG_OFF && (p->rics_mode == ORC_RICS_DRAG_PLUS_PAIRS || !zone);
+    /* 1. gather */
+    double Ep = orc_gather(S, s);
+    /* 2-4. Strang: drag dt/2, Lorentz kick dt, drag dt/2 */
+    if (cont) u = orc_drag_half(S, u, s);
+    u += orc_qm(S, sp) * Ep * dt;
+    if (cont) u = orc_drag_half(S, u, s);
+    /* 5. Monte-Carlo RICS in the pair zone */
+    int make_pair = 0;
+    double Pg = 0.0;
+    if (lep && p->mc_on && p->drag_law != ORC_DRAG_OFF && zone) {
+      double F, rate;
+      orc_drag_code(S, u, s, &F, NULL, &rate);
+      double psc = rate * dt;
+      if (psc > 1.0) { psc = 1.0; S->d.psc_clamped++; }
+      if (psc > 0.0) {
+        uint32_t ctr[4] = { (uint32_t)S->id[k], (uint32_t)(S->id[k] >> 32), (uint32_t)S->step, ORC_TAG_RICS };
+        uint32_t r[4];
+        orc_philox4x32_10(ctr, key, r);
+        if (orc_u24(r[0]) < psc) {
+          S->d.scatters++;
+          double b = orc_node_interp(S, S->node_b, s);
+          double mu = orc_node_interp(S, S->node_mu, s);
+          double gam = sqrt(1.0 + u * u);
+          double d = (mu > u / gam) ? 1.0 : -1.0;
+          double ct = orc_cos_dipole(orc_u24(r[1]));
+          double kin[5];
+          orc_rics_kinematics(b, d, u, ct, kin);
+          if (p->rics_mode == ORC_RICS_SPLIT) u = kin[0];
+          if (p->pairs_on && kin[1] >= p->pair_energy_threshold) { make_pair = 1; Pg = kin[2]; }
+        }
+      }
+    }
+    /* 6. move */
+    double gam = sqrt(1.0 + u * u);
+    double s1 = s + dt * u / gam;
+    int lost = (s1 < 0.0) || (s1 >= (double)N);
+    /* 7. deposit along the path, clamped at the conducting walls */
+    double s1c = s1 < 0.0 ? 0.0 : (s1 > (double)N ? (double)N : s1);
+    orc_deposit_path(S, s, s1c, ORC_QS[sp] * w);
+    S->s[k] = s1;
+    S->u[k] = u;
+    alive[k] = !lost;
+    if (lost) {
+      if (s1 < 0.0) S->d.lost_north++; else S->d.lost_south++;
+      S->d.ke_lost += S->q_p * w * orc_mass(S, sp) * (gam - 1.0);   /* energy carried out */
+    }
+    if (make_pair) {
+      if (lost) { S->d.pairs_lost_wall++; }
+      else {
+        int pc = (int)floor(s1);
+        if (nmax_int >= 0 && S->dens[pc] >= nmax_int) { S->d.pairs_rejected_nmax++; }
+        else {
+          if (nc + 2 > ccap) {
+            ccap *= 2;
+            cs = realloc(cs, ccap * sizeof(double)); cu = realloc(cu, ccap * sizeof(double));
+            cw = realloc(cw, ccap * sizeof(double)); csp = realloc(csp, ccap * sizeof(int32_t));
+            cid = realloc(cid, ccap * sizeof(uint64_t));
+          }
+          for (int m = 0; m < 2; ++m) {
+            cs[nc] = s1; cu[nc] = 0.5 * Pg; cw[nc] = w;
+            csp[nc] = (m == 0) ? ORC_SP_ELEC : ORC_SP_POSI;
+            cid[nc] = orc_child_id(S->id[k], S->step, m);
+            nc++;
+          }
+          S->d.pairs_created++;
+        }
+      }
+    }
+  }
+
+  /* 8. Ampere with the external current: dE/dt = 4 pi (j_ext - J) */
+  double E_new_sum = 0.0, E_old_sum = 0.0;
+  for (int c = 0; c < N; ++c) {
+    double Eo = S->E[c];
+    S->E[c] = Eo + 4.0 * ORC_PI * dt * (S->j_ext - S->J[c]);
+    E_old_sum += Eo; E_new_sum += S->E[c];
+  }
+  S->d.ext_work += dt * S->j_ext * 0.5 * (E_old_sum + E_new_sum);
+  (void)E_old_sum_sq;
+
+  /* 9. remove losses, append pairs then surface injection */
+  int64_t m = 0;
+  for (int64_t k = 0; k < n0; ++k) {
+    if (!alive[k]) continue;
+    S->s[m] = S->s[k]; S->u[m] = S->u[k]; S->w[m] = S->w[k]; S->sp[m] = S->sp[k]; S->id[m] = S->id[k];
+    m++;
+  }
+  S->n = m;
+  orc_grow(S, S->n + nc);
+  for (int64_t k = 0; k < nc; ++k) {
+    S->s[S->n] = cs[k]; S->u[S->n] = cu[k]; S->w[S->n] = cw[k]; S->sp[S->n] = csp[k]; S->id[S->n] = cid[k];
+    S->n++;
+  }
+  if (p->inject_mode == ORC_INJECT_RATE) {
+    for (int foot = 0; foot < 2; ++foot) {
+      S->inj_acc[foot] += S->j_ext * dt / S->q_p;        /* carriers per step, w = 1 */
+      int64_t cnt = (int64_t)floor(S->inj_acc[foot]);
+      S->inj_acc[foot] -= (double)cnt;
+      orc_grow(S, S->n + 2 * cnt);
+      for (int64_t slot = 0; slot < cnt; ++slot) {
+        uint32_t ctr[4] = { (uint32_t)slot, (uint32_t)foot, (uint32_t)S->step, ORC_TAG_INJ };
+        uint32_t r[4];
+        orc_philox4x32_10(ctr, key, r);
+        double frac = (double)(r[0] >> 16) * (1.0 / 65536.0);
+        double pos = foot == 0 ? frac : (double)N - (1.0 / 65536.0) - frac;
+        double rad = sqrt(-2.0 * log(1.0 - orc_u24(r[1])));
+        double ang = 2.0 * ORC_PI * orc_u24(r[2]);
+        double dir = foot == 0 ? 1.0 : -1.0;
+        double ue = dir * fabs(sqrt(p->inject_T) * rad * cos(ang));
+        double ui = dir * fabs(sqrt(p->inject_T / p->mass_ratio) * rad * sin(ang));
+        for (int mem = 0; mem < 2; ++mem) {
+          S->s[S->n] = pos; S->w[S->n] = 1.0;
+          S->u[S->n] = mem == 0 ? ue : ui;
+          S->sp[S->n] = mem == 0 ? ORC_SP_ATMO : ORC_SP_ION;
+          S->id[S->n] = orc_inject_id(S->step, foot, slot, mem);
+          S->n++;
+        }
+        S->d.injected += 2;
+      }
+    }
+  }
+  S->step++;
+  orc_recount_density(S);
+  free(cs); free(cu); free(cw); free(csp); free(cid); free(alive);
+}
+
+void orc_run(orc_sim* S, int64_t steps) { for (int64_t i = 0; i < steps; ++i) orc_step(S); }
+
+/* charge density at nodes (CIC), rho_k = q_p sum q w W_k(s) */
+void orc_rho(const orc_sim* S, double* rho)
+{
+  memset(rho, 0, (S->N + 1) * sizeof(double));
+  for (int64_t k = 0; k < S->n; ++k) {
+    double s = S->s[k];
+    int i = (int)floor(s);
+    if (i < 0) i = 0;
+    if (i > S->N - 1) i = S->N - 1;
+    double f = s - i;
+    double q = ORC_QS[S->sp[k]] * S->w[k] * S->q_p;
+    rho[i] += q * (1.0 - f);
+    rho[i + 1] += q * f;
+  }
+}
+
+void orc_get_diag(orc_sim* S, orc_diag* out)
+{
+  orc_diag d = S->d;
+  for (int i = 0; i < 4; ++i) d.n_alive[i] = 0;
+  double ke = 0.0, ch = 0.0;
+  for (int64_t k = 0; k < S->n; ++k) {
+    int sp = S->sp[k];
+    d.n_alive[sp]++;
+    double gam = sqrt(1.0 + S->u[k] * S->u[k]);
+    ke += S->w[k] * orc_mass(S, sp) * (gam - 1.0);
+    ch += ORC_QS[sp] * S->w[k];
+  }
+  double fe = 0.0, vc = 0.0;
+  for (int c = 0; c < S->N; ++c) { fe += S->E[c] * S->E[c] / (8.0 * ORC_PI); vc -= S->E[c]; }
+  d.kinetic_energy = S->q_p * ke;
+  d.field_energy = fe;
+  d.vc = vc;
+  d.charge = S->q_p * ch;
+  *out = d;
+}
+
+/* Exposed for unit tests of the push pieces */
+double orc_drag_half_public(orc_sim* S, double u0, double s) { return orc_drag_half(S, u0, s); }
+double orc_gather_public(const orc_sim* S, double s) { return orc_gather(S, s); }
+double orc_node_interp_public(const orc_sim* S, int which, double s)
+{
+  const double* t = which == 0 ? S->node_x : (which == 1 ? S->node_b : S->node_mu);
+  return orc_node_interp(S, t, s);
+}

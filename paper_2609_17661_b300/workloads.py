@@ -1,0 +1,269 @@
+"""Configurations and seeded synthetic inputs for the field-line workloads.
+
+This module holds no arithmetic of the method itself: it only names
+parameter sets and draws initial particle states from numpy's seeded
+generators.  Both the CUDA library (through ``pic1d_set_state``) and the
+FP64 oracle in the tests consume the same arrays, so the two sides start
+from identical states.
+
+Positions are returned as unsigned 32-bit fixed point over the line,
+``pos = s * 2**F`` with ``s`` in cells and ``F = fbits(n_cells)`` fractional
+bits; ``s = pos / 2**F`` is exact in FP64.
+
+Workloads (the paper runs on clusters and publishes no data set; these
+synthetic states stand in for its simulations):
+
+* ``C1``   r_eq = 4, 1024 cells, 32 particles per cell (16 e-, 8 e+, 8 ions),
+           m_i/m_e = 50, drifting so the load carries j_psi, drag table from
+           the stellar-disk quadrature at kT = 0.5 keV, pairs on.
+* ``C2``   r_eq = 20, 65536 cells, 256 per cell, surface injection at both
+           footpoints at the rate that carries j_psi.
+* ``C5``   r_eq = 30, 262144 cells, a pair-loaded line of 1e9 particles.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+# enum values of the C ABI (include/pic1d.h)
+PHOTON_RADIAL, PHOTON_DISK = 0, 1
+DRAG_OFF, DRAG_CLOSED, DRAG_TABLE, DRAG_SURROGATE = 0, 1, 2, 3
+RICS_SPLIT, RICS_DRAG_PLUS_PAIRS = 0, 1
+INJECT_NONE, INJECT_RATE = 0, 1
+SP_ELEC, SP_POSI, SP_ION, SP_ATMO = 0, 1, 2, 3
+
+BASE = dict(
+    # geometry (App. B.2)
+    r_eq=4.0, n_cells=1024, cfl=0.45, b_star=10.0, b_convention=0,
+    # photon field and drag law (Sec. 2.2, Sec. 3)
+    kT_keV=0.5, photon_model=PHOTON_DISK, drag_law=DRAG_TABLE, drag_scale=1.0,
+    table_n_gamma=256, table_n_s=256, table_log10g_max=8.0, quad_n_mu=32, quad_n_phi=32,
+    eta_min=1.0e3, rics_mode=RICS_SPLIT, mc_on=1,
+    # plasma and twist (Sec. 3)
+    cells_per_skin_depth=48.0, j_psi=28.0, n0_ppc=6.0 / 28.0, mass_ratio=50.0,
+    # supply and pairs
+    inject_mode=INJECT_NONE, inject_T=0.01,
+    pairs_on=1, b_pair_threshold=0.09, pair_energy_threshold=2.0, n_max_ppc=0.0,
+    seed=1, r_star_cm=1.0e6,
+    # library only
+    capacity=0, sort_every=20,
+)
+
+
+def config(name: str, **over) -> dict:
+    """Parameter set of a named workload, with overrides."""
+    c = dict(BASE)
+    if name == "C1":
+        pass
+    elif name == "C2":
+        c.update(r_eq=20.0, n_cells=65536, n0_ppc=48.0 / 28.0, inject_mode=INJECT_RATE, sort_every=20)
+    elif name == "C5":
+        c.update(r_eq=30.0, n_cells=262144, n0_ppc=760.0 / 28.0, sort_every=20, n_max_ppc=8000.0)
+    elif name == "tiny":
+        c.update(n_cells=16)
+    else:
+        raise KeyError(name)
+    c.update(over)
+    return c
+
+
+def fbits(n_cells: int) -> int:
+    """Fractional bits of the u32 fixed-point position for a line of n cells."""
+    return 32 - int(math.ceil(math.log2(n_cells)))
+
+
+def empty_state(n: int) -> dict:
+    return dict(pos=np.zeros(n, np.uint32), u=np.zeros(n, np.float32), w=np.ones(n, np.float32),
+                sp=np.zeros(n, np.uint8), id=np.arange(n, dtype=np.uint64))
+
+
+def to_oracle(state: dict, n_cells: int) -> dict:
+    """The same particles as FP64 arrays for the oracle (exact conversion)."""
+    F = fbits(n_cells)
+    return dict(s=state["pos"].astype(np.float64) / float(1 << F), u=state["u"].astype(np.float64),
+                w=state["w"].astype(np.float64), sp=state["sp"].astype(np.int32), id=state["id"].copy())
+
+
+def _positions(cells: np.ndarray, frac: np.ndarray, F: int) -> np.ndarray:
+    """Fixed point of cell + frac, frac in [0, 1)."""
+    q = np.minimum((frac * (1 << F)).astype(np.int64), (1 << F) - 1)
+    return (cells.astype(np.int64) * (1 << F) + q).astype(np.uint32)
+
+
+def load_drifting_plasma(cfg: dict, ppc_e=16, ppc_p=8, ppc_i=8, multiplicity=4.0, u_sigma=0.1,
+                         seed=None) -> dict:
+    """C1-style initial load: per cell ``ppc_e`` electrons at stratified random
+    positions, positrons and ions on the positions of the first ``ppc_p`` and
+    the next ``ppc_i`` electrons (so every node is neutral and E = 0 is
+    consistent), momenta Gaussian with spread ``u_sigma`` in each species' own
+    m c, leptons drifting at beta = +-1/multiplicity (positrons +s, electrons
+    -s) so that the load carries the twist current; ions at rest on average."""
+    assert ppc_p + ppc_i == ppc_e
+    N = cfg["n_cells"]
+    F = fbits(N)
+    rng = np.random.default_rng(cfg["seed"] if seed is None else seed)
+    beta_d = 1.0 / multiplicity
+    u_d = beta_d / math.sqrt(1.0 - beta_d * beta_d)
+    cells = np.repeat(np.arange(N), ppc_e)
+    strat = np.tile(np.arange(ppc_e), N)
+    frac = (strat + rng.random(N * ppc_e)) / ppc_e
+    pos_e = _positions(cells, frac, F)
+    pos_e2 = pos_e.reshape(N, ppc_e)
+    pos_p = pos_e2[:, :ppc_p].reshape(-1)
+    pos_i = pos_e2[:, ppc_p:].reshape(-1)
+    n_e, n_p, n_i = pos_e.size, pos_p.size, pos_i.size
+    u_e = rng.normal(-u_d, u_sigma, n_e)
+    u_p = rng.normal(+u_d, u_sigma, n_p)
+    u_i = rng.normal(0.0, u_sigma, n_i)
+    n = n_e + n_p + n_i
+    st = empty_state(n)
+    st["pos"][:] = np.concatenate([pos_e, pos_p, pos_i])
+    st["u"][:] = np.concatenate([u_e, u_p, u_i]).astype(np.float32)
+    st["sp"][:] = np.concatenate([np.full(n_e, SP_ELEC), np.full(n_p, SP_POSI), np.full(n_i, SP_ION)])
+    return st
+
+
+def load_random(cfg: dict, n: int, u_scale=30.0, seed=None, species=(SP_ELEC, SP_POSI, SP_ION, SP_ATMO),
+                w_choices=(1.0,)) -> dict:
+    """Unstructured particles for unit and parity tests: uniform positions,
+    momenta with log-uniform |u| in [1e-3, u_scale] and random sign."""
+    N = cfg["n_cells"]
+    F = fbits(N)
+    rng = np.random.default_rng(cfg["seed"] if seed is None else seed)
+    st = empty_state(n)
+    st["pos"][:] = _positions(rng.integers(0, N, n), rng.random(n), F)
+    mag = np.exp(rng.uniform(math.log(1e-3), math.log(u_scale), n))
+    st["u"][:] = (mag * rng.choice([-1.0, 1.0], n)).astype(np.float32)
+    st["sp"][:] = rng.choice(np.array(species, np.uint8), n)
+    st["w"][:] = rng.choice(np.array(w_choices, np.float32), n)
+    st["id"][:] = rng.permutation(np.arange(n, dtype=np.uint64) * 7 + 3)
+    return st
+
+
+def load_beam(cfg: dict, n: int, gamma_lo=10.0, gamma_hi=1.0e4, seed=None, cells=None) -> dict:
+    """Energetic leptons (log-uniform gamma, both directions) for the RICS and
+    pair tests; electron/positron pairs share positions (neutral)."""
+    N = cfg["n_cells"]
+    F = fbits(N)
+    rng = np.random.default_rng(cfg["seed"] if seed is None else seed)
+    half = n // 2
+    if cells is None:
+        c = rng.integers(0, N, half)
+    else:
+        c = rng.choice(np.asarray(cells), half)
+    pos = _positions(c, rng.random(half), F)
+    g = np.exp(rng.uniform(math.log(gamma_lo), math.log(gamma_hi), 2 * half))
+    mag = np.sqrt(g * g - 1.0)
+    sgn = rng.choice([-1.0, 1.0], 2 * half)
+    st = empty_state(2 * half)
+    st["pos"][:] = np.concatenate([pos, pos])
+    st["u"][:] = (mag * sgn).astype(np.float32)
+    st["sp"][:] = np.concatenate([np.full(half, SP_ELEC), np.full(half, SP_POSI)])
+    return st
+
+
+def load_cold_oscillation(cfg: dict, ppc=16, amp=1e-3, mode=1) -> dict:
+    """Cold electrons on a neutralising ion background (same positions), with
+    a sinusoidal velocity perturbation of wavenumber 2 pi mode / L."""
+    N = cfg["n_cells"]
+    F = fbits(N)
+    cells = np.repeat(np.arange(N), ppc)
+    frac = (np.tile(np.arange(ppc), N) + 0.5) / ppc
+    pos = _positions(cells, frac, F)
+    s = pos.astype(np.float64) / (1 << F)
+    u_e = amp * np.sin(2.0 * np.pi * mode * s / N)
+    n = pos.size
+    st = empty_state(2 * n)
+    st["pos"][:] = np.concatenate([pos, pos])
+    st["u"][:] = np.concatenate([u_e, np.zeros(n)]).astype(np.float32)
+    st["sp"][:] = np.concatenate([np.full(n, SP_ELEC), np.full(n, SP_ION)])
+    return st
+
+
+def load_two_stream(cfg: dict, ppc=64, u0=0.2, amp=1e-4, mode=1) -> dict:
+    """Two cold electron beams at +-u0 (half the electrons each) on ions,
+    with a small velocity perturbation in one mode."""
+    N = cfg["n_cells"]
+    F = fbits(N)
+    cells = np.repeat(np.arange(N), ppc)
+    frac = (np.tile(np.arange(ppc), N) + 0.5) / ppc
+    pos = _positions(cells, frac, F)
+    s = pos.astype(np.float64) / (1 << F)
+    n = pos.size
+    beam = np.tile(np.arange(ppc) % 2, N)
+    u_e = np.where(beam == 0, u0, -u0) + amp * np.sin(2.0 * np.pi * mode * s / N)
+    st = empty_state(2 * n)
+    st["pos"][:] = np.concatenate([pos, pos])
+    st["u"][:] = np.concatenate([u_e, np.zeros(n)]).astype(np.float32)
+    st["sp"][:] = np.concatenate([np.full(n, SP_ELEC), np.full(n, SP_ION)])
+    return st
+
+
+def pair_loaded_counts(n_cells: int, total: int) -> np.ndarray:
+    """Particles per cell of the synthetic pair-loaded line: denser toward
+    the footpoints, total ``total`` (even in every cell)."""
+    x = (np.arange(n_cells) + 0.5) / n_cells
+    prof = 1.0 + 3.0 * np.abs(2.0 * x - 1.0) ** 6
+    cnt = np.floor(prof / prof.sum() * total / 2.0).astype(np.int64) * 2
+    short = total - int(cnt.sum())
+    if short > 0:
+        cnt[: short // 2] += 2
+    return cnt
+
+
+def fill_pair_loaded(cfg: dict, out: dict, start_cell: int, end_cell: int, counts: np.ndarray,
+                     offset: int, seed=None, ion_frac=0.1) -> int:
+    """Write the particles of cells [start_cell, end_cell) of a pair-loaded
+    line into the preallocated arrays ``out`` at ``offset``; returns the new
+    offset.  Electrons come paired with a positron or an ion at the same
+    position (neutral nodes).  Lepton |u| is log-normal around gamma ~ 30
+    (outside the inner tenth of the line at each end) or around gamma ~ 2
+    (inside it), with random direction; ions are cold."""
+    N = cfg["n_cells"]
+    F = fbits(N)
+    rng = np.random.default_rng((cfg["seed"] if seed is None else seed, start_cell))
+    cnt = counts[start_cell:end_cell]
+    half = cnt // 2
+    m = int(half.sum())
+    cells = np.repeat(np.arange(start_cell, end_cell), half)
+    pos = _positions(cells, rng.random(m), F)
+    x = (cells + 0.5) / N
+    inner = (x < 0.1) | (x > 0.9)
+    lg = np.where(inner, rng.normal(0.3, 0.15, m), rng.normal(1.5, 0.5, m))
+    g = np.maximum(10.0 ** lg, 1.0 + 1e-6)
+    mag = np.sqrt(g * g - 1.0)
+    u_e = mag * rng.choice([-1.0, 1.0], m)
+    partner_ion = rng.random(m) < 2.0 * ion_frac
+    g2 = np.maximum(10.0 ** np.where(inner, rng.normal(0.3, 0.15, m), rng.normal(1.5, 0.5, m)), 1.0 + 1e-6)
+    u_p = np.where(partner_ion, rng.normal(0.0, 0.01, m), np.sqrt(g2 * g2 - 1.0) * rng.choice([-1.0, 1.0], m))
+    sl = slice(offset, offset + 2 * m)
+    inter = np.empty(2 * m, np.uint32)
+    inter[0::2] = pos
+    inter[1::2] = pos
+    out["pos"][sl] = inter
+    uu = np.empty(2 * m, np.float32)
+    uu[0::2] = u_e
+    uu[1::2] = u_p
+    out["u"][sl] = uu
+    ss = np.empty(2 * m, np.uint8)
+    ss[0::2] = SP_ELEC
+    ss[1::2] = np.where(partner_ion, SP_ION, SP_POSI)
+    out["sp"][sl] = ss
+    out["w"][sl] = 1.0
+    out["id"][sl] = np.arange(offset, offset + 2 * m, dtype=np.uint64)
+    return offset + 2 * m
+
+
+def load_pair_loaded(cfg: dict, total: int, seed=None, chunk_cells=8192, out=None) -> dict:
+    """Whole pair-loaded line (cell-sorted), optionally into given arrays."""
+    N = cfg["n_cells"]
+    counts = pair_loaded_counts(N, total)
+    n = int(counts.sum())
+    if out is None:
+        out = empty_state(n)
+    off = 0
+    for c0 in range(0, N, chunk_cells):
+        off = fill_pair_loaded(cfg, out, c0, min(N, c0 + chunk_cells), counts, off, seed=seed)
+    assert off == n
+    return out
