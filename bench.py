@@ -1,0 +1,320 @@
+"""Benchmark of the per-step particle loop (particle-steps/s, HBM roofline).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload C5|C2|C1]
+                    [--particles P] [--impl b300|reference]
+
+One step = one PIC cycle of the whole line (push with drag, Monte-Carlo RICS
+and pairs, move, integer deposit; surface supply; FP64 field update; a cell
+sort every sort_every steps).  The default workload is the pair-loaded
+r_eq = 30 line with 262,144 cells and 1e9 macroparticles (synthetic state;
+the paper publishes no data set).  With torchrun (N > 1) every rank advances
+its own independent line (replicas; weak scaling) and the value is the
+particle-steps of all ranks over the slowest rank's time.
+
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2609_17661_b300 import workloads as W  # noqa: E402
+
+BYTES_PER_SLOT = 21      # push: read pos 4 + u 4 + w 4 + sp 1, write pos 4 + u 4
+BYTES_PER_DRAW = 8       # id read of a lepton that draws a Philox number
+BYTES_PER_CREATED = 21   # pos, u, w, sp, id written per created particle
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.p = None
+
+    def _read(self):
+        for line in self.p.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cfg_for(args):
+    cfg = W.config(args.workload)
+    if args.workload == "C5":
+        cfg["capacity"] = int(args.particles * 1.06) + (1 << 20)
+    return cfg
+
+
+def make_state_pinned(cfg, total):
+    """Host state in pinned memory (the e2e leg copies it every run)."""
+    import torch
+    n = int(W.pair_loaded_counts(cfg["n_cells"], total).sum())
+    buf = {"pos": torch.empty(n, dtype=torch.int32, pin_memory=True),
+           "u": torch.empty(n, dtype=torch.float32, pin_memory=True),
+           "w": torch.empty(n, dtype=torch.float32, pin_memory=True),
+           "sp": torch.empty(n, dtype=torch.uint8, pin_memory=True),
+           "id": torch.empty(n, dtype=torch.int64, pin_memory=True)}
+    view = {"pos": buf["pos"].numpy().view(np.uint32), "u": buf["u"].numpy(), "w": buf["w"].numpy(),
+            "sp": buf["sp"].numpy(), "id": buf["id"].numpy().view(np.uint64)}
+    W.load_pair_loaded(cfg, total, out=view)
+    return buf, view, n
+
+
+def cpu_baseline(cfg, sample_total, budget_s, max_steps):
+    """The FP64 oracle (single thread, as it stands) on a bounded sample of
+    the workload: the same line and physics with `sample_total`
+    macroparticles in the same pair-loaded profile."""
+    import oracle as O
+    st = W.load_pair_loaded(cfg, sample_total, seed=7)
+    o = W.to_oracle(st, cfg["n_cells"])
+    S = O.Sim(cfg)
+    S.set_particles(o["s"], o["u"], o["w"], o["sp"], o["id"])
+    t0 = time.perf_counter()
+    S.step(1)
+    t1 = time.perf_counter()
+    steps = int(max(1, min(max_steps, budget_s / max(t1 - t0, 1e-9))))
+    n_before = 0
+    units = 0
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        units += S.n
+        S.step(1)
+    dt = time.perf_counter() - t0
+    return {"value": units / dt, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{st['pos'].size} macroparticles of the same line and profile, {steps} steps "
+                      f"(the oracle is single-threaded C, FP64)"}, steps, st["pos"].size
+
+
+def run_reference(args):
+    cfg = cfg_for(args)
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sample = args.ref_sample
+    cb, steps, n = cpu_baseline(cfg, sample, budget_s=max(5.0, 0.6 * args.steps), max_steps=args.steps)
+    v = cb["value"]
+    line = {"metric": "particle-steps/s", "value": v, "unit": "particle-steps/s", "n_gpus": args.gpus,
+            "steps": steps, "warmup": 1, "ms_per_step": n / v * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(args), "cells": cfg["n_cells"], "r_eq": cfg["r_eq"],
+                       "particles": n, "sort_every": cfg["sort_every"], "drag": "table"},
+            "impl": "reference", "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_name(args):
+    return {"C5": f"pair-loaded dipole line r_eq=30, 262144 cells, {args.particles:.3g} macroparticles, "
+                  "table drag, pairs on (n_max cap), sort every 20",
+            "C2": "dipole line r_eq=20, 65536 cells, 256/cell, surface injection",
+            "C1": "dipole line r_eq=4, 1024 cells, 32/cell"}[args.workload]
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2609_17661_b300 import Line
+
+    cfg = cfg_for(args)
+    cfg["seed"] = 1 + rank
+    t_gen = time.perf_counter()
+    buf, view, n = make_state_pinned(cfg, int(args.particles))
+    t_gen = time.perf_counter() - t_gen
+    stream = torch.cuda.current_stream()
+    line = Line(cfg, stream=stream.cuda_stream)
+    line.set_state(view)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up
+    line.step(args.warmup)
+    d0 = line.diag()
+    line.timing(True)
+    clk = Clocks(local)
+    clk.start()
+    time.sleep(0.3)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    line.step(args.steps)
+    e1.record(stream)
+    barrier()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    d1 = line.diag()
+    line.timing(False)
+    units = d1["push_slots"]
+    draws = d1["rng_draws"] - d0["rng_draws"]
+    created = (d1["pairs_created"] - d0["pairs_created"]) * 2 + (d1["injected"] - d0["injected"])
+    t = torch.tensor([ms, units], dtype=torch.float64, device="cuda")
+    if world > 1:
+        tm = t.clone()
+        dist.all_reduce(tm[0:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(tm[1:2], op=dist.ReduceOp.SUM)
+        t = tm
+    ms_max, units_all = float(t[0]), float(t[1])
+    value = units_all / (ms_max * 1e-3)
+
+    # roofline of the push kernel: algorithmic bytes per launch / mean launch time
+    launches = d1["push_launches"]
+    push_bytes = BYTES_PER_SLOT * units + BYTES_PER_DRAW * draws + BYTES_PER_CREATED * created
+    peak, peak_kind = _peaks()
+    achieved = push_bytes / (d1["push_ms"] * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "k_push", "launches": launches,
+            "bytes_per_launch": push_bytes / max(launches, 1), "mean_launch_ms": d1["push_ms"] / max(launches, 1),
+            "peak_kind": peak_kind, "push_share_of_step": d1["push_ms"] / ms}
+
+    # end to end through the C ABI from pinned host buffers: upload the state,
+    # K steps, read back the diagnostics and the field every step
+    e2e = None
+    if not args.no_e2e:
+        barrier()
+        Eh = np.zeros(cfg["n_cells"])
+        t0 = time.perf_counter()
+        line.set_state(view)
+        for _ in range(args.steps):
+            line.step(1)
+            dd = line.diag()
+            line.fields()
+        barrier()
+        te = time.perf_counter() - t0
+        units_e = float(dd["step"]) * 0 + args.steps * n
+        tt = torch.tensor([te, units_e], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(tt[0:1], op=dist.ReduceOp.MAX)
+            dist.all_reduce(tt[1:2], op=dist.ReduceOp.SUM)
+        h2d = 21 * n
+        e2e = {"value": float(tt[1]) / float(tt[0]), "unit": "particle-steps/s",
+               "h2d_bytes_per_step": h2d / args.steps,
+               "d2h_bytes_per_step": 8 * cfg["n_cells"] + 8 * cfg["n_cells"] + 256}
+        del Eh
+
+    cb = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cb, _, _ = cpu_baseline(cfg, args.cpu_sample, budget_s=15.0, max_steps=500)
+        cb["cores"] = 1
+
+    if rank == 0:
+        out = {"metric": "particle-steps/s", "value": value, "unit": "particle-steps/s", "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+               "data": "synthetic",
+               "config": {"workload": workload_name(args), "cells": cfg["n_cells"], "r_eq": cfg["r_eq"],
+                          "particles": n, "sort_every": cfg["sort_every"], "drag": "table",
+                          "l2": "inputs (21 B x particles) far larger than the 126 MB L2",
+                          "parallelism": f"replicas x{world}"},
+               "roofline": roof, "clocks": clocks, "e2e": e2e, "cpu_baseline": cb,
+               "gpu_launches": gpu_launches(args.steps, cfg, d0["step"]),
+               "pairs_created": d1["pairs_created"] - d0["pairs_created"], "rng_draws": draws,
+               "setup_s": {"host_state": t_gen}}
+        print(json.dumps(out), flush=True)
+    line.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def gpu_launches(steps, cfg, step0):
+    """Kernels of this library launched in the timed region: per step push,
+    field, finalize (+ inject with surface supply); per sort hist, scan,
+    scatter, done."""
+    per = 3 + (1 if cfg["inject_mode"] else 0)
+    sorts = sum(1 for s in range(step0 + 1, step0 + steps + 1) if s % cfg["sort_every"] == 0)
+    return per * steps + 4 * sorts
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
+    ap.add_argument("--workload", default="C5", choices=["C5", "C2", "C1"])
+    ap.add_argument("--particles", type=float, default=1e9)
+    ap.add_argument("--cpu-sample", type=int, default=200000)
+    ap.add_argument("--ref-sample", type=int, default=200000)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "b300":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,220 @@
+/*
+ * pic1d.h -- C ABI of the B300 (sm_103a) library that advances the per-step
+ * particle loop of the 1D particle-in-cell method for resonant inverse
+ * Compton (RICS) drag and pair cascades on one dipole field line of a
+ * magnetar (Mahlmann, Philippov, Soudais, Beloborodov, Sironi, "1D PIC
+ * Simulations of Resonant Scattering-Driven Pair Cascades in Magnetar
+ * Magnetospheres").
+ *
+ * One step (Sec. 3 of the paper) gathers E_parallel at every particle,
+ * applies the continuous RICS drag in a Strang split around the Lorentz kick
+ * (limiter, implicit midpoint by Newton, or damping toward p~ = mu/sqrt(1 -
+ * mu^2)), draws Monte-Carlo RICS scatterings with recoil and injects e+e-
+ * pairs when the scattered photon exceeds 2 m_e c^2 (App. A), moves the
+ * particle, deposits a charge-conserving current and advances E from
+ * Ampere's law dE/dt = 4 pi (j_ext - j) against the external twist current.
+ *
+ * Code units: c = 1, one cell = 1, dt = cfl.  Momentum u = gamma beta along
+ * +s in units of the species' m c.  s runs from the northern footpoint
+ * (s = 0) to the southern one (s = n_cells).  Positions are stored as
+ * unsigned 32-bit fixed point: pos = s * 2^F with F = 32 - ceil(log2
+ * n_cells).  Weights are FP32, charges are taken in fixed point w_int =
+ * rint(w * 2^12).  The current is accumulated in int64: J_int[c] = sum over
+ * particles of q_sign * w_int * (signed length of the step's path inside
+ * cell c, in units of 2^-F); the physical current density is
+ * J = q_p 2^(-F-12) J_int / dt.  E lives at cell centres (FP64).
+ *
+ * Conventions for every entry point:
+ *   - return 0 on success, a positive warning (state consistent) or a
+ *     negative error; pic1d_last_error() gives a message.  After
+ *     PIC1D_ECUDA the context must be freed.
+ *   - pointers tagged "host" are caller-owned host memory, read or written
+ *     only during the call; "mem" arguments select host (0) or device (1)
+ *     memory for the caller's arrays; device arrays must be on the device
+ *     the context was created on and are used only during the call.
+ *   - work is issued on the stream given in the parameters (NULL: the
+ *     legacy default stream); entry points that return data synchronise
+ *     that stream.
+ *   - a context is not thread-safe; different contexts are independent.
+ */
+#ifndef PIC1D_H
+#define PIC1D_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define PIC1D_OK          0
+#define PIC1D_WCAPACITY   1   /* pairs/injections dropped: capacity full  */
+#define PIC1D_EINVAL     -1   /* invalid argument                         */
+#define PIC1D_ENOMEM     -2   /* device allocation failed                 */
+#define PIC1D_ECUDA      -3   /* CUDA runtime error                       */
+#define PIC1D_ENUMERIC   -4   /* non-finite momentum met in a step        */
+
+/* photon field model (Sec. 2.2, App. B.2) */
+#define PIC1D_PHOTON_RADIAL 0 /* radially streaming photons, solid angle pi/x^2 (Eq. contdrag) */
+#define PIC1D_PHOTON_DISK   1 /* uniform-intensity stellar disk, quadrature over its solid angle */
+
+/* drag law used by the push (Sec. 2.2, Sec. 3) */
+#define PIC1D_DRAG_OFF       0
+#define PIC1D_DRAG_CLOSED    1 /* closed form Eq. contdrag at the particle (radial photons)    */
+#define PIC1D_DRAG_TABLE     2 /* bilinear table in (log10 gamma, s/L) built by quadrature      */
+
+/* RICS response (Sec. 3) */
+#define PIC1D_RICS_SPLIT           0 /* b > b_thr: discrete scattering + pairs; else continuous drag */
+#define PIC1D_RICS_DRAG_PLUS_PAIRS 1 /* continuous drag everywhere; scattering only creates pairs    */
+
+/* surface supply (Sec. 3, App. B.1) */
+#define PIC1D_INJECT_NONE 0
+#define PIC1D_INJECT_RATE 1 /* neutral e- + ion pairs per footpoint per step at the rate carrying j_ext */
+
+/* species codes */
+#define PIC1D_SP_ELECTRON 0
+#define PIC1D_SP_POSITRON 1
+#define PIC1D_SP_ION      2
+#define PIC1D_SP_ATMO     3   /* electron extracted from the atmosphere */
+#define PIC1D_SP_DEAD     255 /* removed slot (left the line), dropped at the next sort */
+
+typedef struct pic1d_params {
+  /* geometry, App. B.2: r = r_eq sin^2(theta), footpoints at
+   * theta_0 = arcsin(sqrt(R_star/r_eq)); b = b_star (R_star/r)^3 sqrt(1+3cos^2)
+   * (b_convention 0) or half of it (1, the paper's polar normalisation) */
+  double r_eq;              /* equatorial radius of the line, in R*     */
+  int32_t n_cells;          /* cells along the line (>= 8)              */
+  double cfl;               /* dt = cfl * dx / c (0 < cfl < 1)          */
+  double b_star;            /* B_* / B_QED                              */
+  int32_t b_convention;
+  /* photon field and drag law, Sec. 2.2 */
+  double kT_keV;            /* blackbody temperature                    */
+  int32_t photon_model;     /* PIC1D_PHOTON_*                           */
+  int32_t drag_law;         /* PIC1D_DRAG_*                             */
+  double drag_scale;        /* multiplies drag and scattering rate (1 = physical) */
+  int32_t table_n_gamma;    /* table points in log10 gamma (>= 2)       */
+  int32_t table_n_s;        /* table points in s/L (>= 2)               */
+  double table_log10g_max;  /* table spans log10 gamma in [0, max]      */
+  int32_t quad_n_mu;        /* Gauss-Legendre nodes in cos(alpha) over the disk (<= 256) */
+  int32_t quad_n_phi;       /* azimuth nodes on [0, pi]                 */
+  double eta_min;           /* limiter: tau_min omega_p0 = eta_min sqrt(j_psi); <= 0 disables it */
+  int32_t rics_mode;        /* PIC1D_RICS_*                             */
+  int32_t mc_on;            /* Monte-Carlo scattering on/off            */
+  /* plasma and twist, Sec. 3 */
+  double cells_per_skin_depth; /* d0: skin depth at density n0, in cells */
+  double j_psi;             /* j_ext / (n0 e c)                         */
+  double n0_ppc;            /* weight per cell that represents n0       */
+  double mass_ratio;        /* m_i / m_e (ion charge +1)                */
+  /* supply and pairs */
+  int32_t inject_mode;      /* PIC1D_INJECT_*                           */
+  double inject_T;          /* temperature of injected particles, m_e c^2 */
+  int32_t pairs_on;
+  double b_pair_threshold;  /* b above which scattering is discrete and may make pairs (0.09) */
+  double pair_energy_threshold; /* photon energy for a pair, m_e c^2 (2.0) */
+  double n_max_ppc;         /* no pair in a cell holding this lepton weight (<= 0: off) */
+  uint64_t seed;            /* Philox key                               */
+  double r_star_cm;         /* stellar radius, cm                       */
+  /* library */
+  int64_t capacity;         /* particle slots (0: grown on demand)      */
+  int32_t sort_every;       /* cell sort cadence in steps (>= 1)        */
+  void* cuda_stream;        /* cudaStream_t for all work, may be NULL   */
+} pic1d_params;
+
+typedef struct pic1d_diag_t {
+  int64_t step;
+  int64_t n_slots;          /* used slots, including removed ones before the next sort */
+  int64_t n_alive[4];       /* per species                              */
+  int64_t pairs_created, pairs_dropped_cap, pairs_rejected_nmax, pairs_lost_wall;
+  int64_t lost_north, lost_south, injected, injected_dropped;
+  int64_t scatters, psc_clamped, limiter_branch, newton_branch, nonfinite;
+  int64_t rng_draws;        /* Philox draws (one 8-byte id read each) */
+  int64_t push_launches;    /* push kernels timed since pic1d_timing(c, 1) */
+  double push_ms;           /* their summed CUDA-event durations, ms     */
+  int64_t push_slots;       /* sum over those launches of the slots read */
+  double field_energy;      /* sum_c E_c^2 / (8 pi) after the last step          */
+  double kinetic_energy;    /* q_p sum w m (gamma - 1) at the last half step     */
+  double ext_work;          /* cumulative sum_n dt j_ext sum_c (E^n + E^{n+1})/2 */
+  double vc;                /* circuit potential V_c = - sum_c E_c dx            */
+  double ke_lost;           /* cumulative kinetic energy carried out at the walls */
+  double q_p, j_ext, dt, tau_min, R_cells, L_Rstar; /* derived constants         */
+  int32_t fbits, status;
+} pic1d_diag_t;
+
+typedef struct pic1d_ctx pic1d_ctx;
+
+/* Create a context: validates the parameters, builds the geometry tables of
+ * App. B.2 (host FP64), builds the drag/rate table by quadrature on the
+ * device (drag_law TABLE), allocates device memory for `capacity` particles
+ * (double-buffered) and leaves an empty line with E = 0 at step 0.
+ * out: receives the context (NULL on failure).  Errors: EINVAL, ENOMEM, ECUDA. */
+int pic1d_init(const pic1d_params* p, pic1d_ctx** out);
+
+/* Replace the particle state and E (Sec. 3 state at time step `step`): n
+ * particles in SoA form, pos fixed point (see above), u, w, species, id;
+ * E has n_cells values (NULL: zero).  mem = 0 host arrays, 1 device arrays.
+ * Grows the capacity if needed.  Errors: EINVAL (n < 0, bad species, pos out
+ * of the line), ENOMEM, ECUDA. */
+int pic1d_set_state(pic1d_ctx* c, int64_t n, const uint32_t* pos, const float* u, const float* w,
+                    const uint8_t* sp, const uint64_t* id, const double* E, int64_t step, int mem);
+
+/* Advance n_steps PIC cycles (Sec. 3) on the context's stream, sorting the
+ * particles by cell every sort_every steps.  Asynchronous: returns after
+ * issuing the work (errors of the step show up in pic1d_diag).
+ * Errors: EINVAL (n_steps < 0), ECUDA. */
+int pic1d_step(pic1d_ctx* c, int n_steps);
+
+/* Synchronise and fill `out` (host).  Returns PIC1D_ENUMERIC if a step met
+ * a non-finite momentum, PIC1D_WCAPACITY if creations were dropped since
+ * init, otherwise 0. */
+int pic1d_diag(pic1d_ctx* c, pic1d_diag_t* out);
+
+/* Copy E (n_cells doubles) and/or the integer current J_int of the last
+ * step (n_cells int64, zero before the first step) out; either may be NULL.  mem as above.  Synchronises. */
+int pic1d_get_fields(pic1d_ctx* c, double* E, int64_t* J, int mem);
+
+/* Number of used particle slots (alive + removed-but-unsorted); synchronises. */
+int64_t pic1d_slots(pic1d_ctx* c);
+
+/* Copy the first `n` slots (n <= pic1d_slots) of the SoA out; removed
+ * slots carry species PIC1D_SP_DEAD.  Any array may be NULL.  mem as above.
+ * Synchronises. */
+int pic1d_get_particles(pic1d_ctx* c, int64_t n, uint32_t* pos, float* u, float* w, uint8_t* sp,
+                        uint64_t* id, int mem);
+
+/* Sort the particles by cell now (histogram, scan, scatter) and drop the
+ * removed slots.  Asynchronous.  Errors: ECUDA. */
+int pic1d_sort(pic1d_ctx* c);
+
+/* Copy the drag/rate table (drag_law TABLE) out as FP32 pairs (F^, ln N^),
+ * layout ((sign * n_s + js) * n_gamma + ig) * 2, sign 0 for u >= 0:
+ * 2 * table_n_s * table_n_gamma * 2 floats, host memory.  F^ = F R_star/(m_e c^2)
+ * (Eq. contdrag normalisation), N^ = Ndot R_star/c (Eq. scatteringNdot). */
+int pic1d_get_table(pic1d_ctx* c, float* out);
+
+/* Charge-conserving integer deposit alone (the deposit of the step, Sec. 3):
+ * for n particles moving from pos0 to pos1 (int64 fixed point, pos1 may lie
+ * outside [0, n_cells 2^F): the path is clamped at the walls) add
+ * q_sign * rint(w 2^12) * (path length inside cell c) to J[c].  All arrays
+ * are device arrays; J (n_cells int64) is accumulated into, not cleared.
+ * Issued on the context's stream; synchronises. */
+int pic1d_deposit(pic1d_ctx* c, int64_t n, const int64_t* pos0, const int64_t* pos1, const float* w,
+                  const uint8_t* sp, int64_t* J);
+
+/* Per-launch timing of the push kernel (the step's dominant kernel): with
+ * on = 1, every push launch is bracketed by CUDA events on the context's
+ * stream and pic1d_diag reports the launches, their summed duration and the
+ * particle slots they read since the call; on = 0 stops it.  No effect on
+ * results.  Errors: ECUDA. */
+int pic1d_timing(pic1d_ctx* c, int on);
+
+/* Message of the last error on this context (never NULL). */
+const char* pic1d_last_error(const pic1d_ctx* c);
+
+/* Release the context and its device memory (NULL is a no-op). */
+void pic1d_free(pic1d_ctx* c);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PIC1D_H */

@@ -178,7 +178,7 @@ double orc_arc_length(double r_eq, double theta)
   static double gx[16], gw[16];
   if (!init) { orc_gauss_legendre(16, gx, gw); init = 1; }
   double a = orc_theta0(r_eq), b = theta;
-  const int panels = 32;
+  const int panels = 8;
   double h = (b - a) / panels, sum = 0.0;
   for (int k = 0; k < panels; ++k) {
     double lo = a + k * h;
@@ -192,23 +192,22 @@ double orc_arc_length(double r_eq, double theta)
 
 double orc_line_length(double r_eq) { return orc_arc_length(r_eq, ORC_PI - orc_theta0(r_eq)); }
 
-/* invert s(theta) = s_target (s in R_star) by Newton from a bisection start */
+/* invert s(theta) = s_target (s in R_star): Newton from the linear guess,
+ * kept inside a shrinking bracket (bisection when Newton leaves it) */
 double orc_theta_of_s(double r_eq, double s_target)
 {
   double t0 = orc_theta0(r_eq), t1 = ORC_PI - t0;
+  double L = orc_line_length(r_eq);
   double lo = t0, hi = t1;
-  for (int it = 0; it < 30; ++it) {                 /* coarse bisection */
-    double mid = 0.5 * (lo + hi);
-    if (orc_arc_length(r_eq, mid) < s_target) lo = mid; else hi = mid;
-  }
-  double th = 0.5 * (lo + hi);
-  for (int it = 0; it < 8; ++it) {
+  double th = t0 + (t1 - t0) * s_target / L;
+  for (int it = 0; it < 100; ++it) {
     double f = orc_arc_length(r_eq, th) - s_target;
+    if (f > 0.0) hi = th; else lo = th;
     double d = orc_dsdtheta(r_eq, th);
-    if (d <= 0.0) break;
-    double dt = f / d;
-    th -= dt;
-    if (fabs(dt) < 1e-15) break;
+    double nt = (d > 0.0) ? th - f / d : 0.5 * (lo + hi);
+    if (!(nt > lo && nt < hi)) nt = 0.5 * (lo + hi);
+    if (fabs(nt - th) < 1e-15) { th = nt; break; }
+    th = nt;
   }
   if (th < t0) th = t0;
   if (th > t1) th = t1;
@@ -843,7 +842,9 @@ void orc_step(orc_sim* S)
   }
   if (p->inject_mode == ORC_INJECT_RATE) {
     for (int foot = 0; foot < 2; ++foot) {
-      S->inj_acc[foot] += S->j_ext * dt / S->q_p;        /* carriers per step, w = 1 */
+      /* carriers of weight 1 per step that carry j_ext = j_psi n0 e c through
+       * the footpoint: j_psi n0 c dt */
+      S->inj_acc[foot] += p->j_psi * p->n0_ppc * dt;
       int64_t cnt = (int64_t)floor(S->inj_acc[foot]);
       S->inj_acc[foot] -= (double)cnt;
       orc_grow(S, S->n + 2 * cnt);

@@ -1,0 +1,168 @@
+"""B300-native per-step particle loop of the 1D RICS pair-cascade PIC method.
+
+Thin Python layer over the C ABI of ``include/pic1d.h`` (``libpic1d.so``,
+hand-written sm_103a kernels).  PyTorch is used only for device memory and
+streams; every step of the method runs in the library's kernels.  There is
+no CPU fallback: constructing a :class:`Line` without the built library or
+without a CUDA device raises.
+
+Typical use::
+
+    import torch
+    from paper_2609_17661_b300 import Line, workloads as W
+    cfg = W.config("C1")
+    line = Line(cfg)                        # pic1d_init
+    line.set_state(W.load_drifting_plasma(cfg))
+    line.step(100)                          # pic1d_step (asynchronous)
+    print(line.diag())                      # pic1d_diag
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import Diag, Params
+
+__all__ = ["Line", "PicError", "make_params", "workloads"]
+
+
+class PicError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"pic1d error {code}: {msg}")
+        self.code = code
+
+
+def make_params(cfg: dict, stream=None) -> Params:
+    p = Params()
+    for name, _ in Params._fields_:
+        if name == "cuda_stream":
+            continue
+        setattr(p, name, cfg[name])
+    p.cuda_stream = stream
+    return p
+
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def _arr(a, dtype):
+    """(pointer, mem flag, keep-alive) for a numpy array or a torch tensor."""
+    if a is None:
+        return None, 0, None
+    if _is_torch(a):
+        assert a.is_contiguous()
+        return C.c_void_p(a.data_ptr()), (1 if a.is_cuda else 0), a
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return C.c_void_p(a.ctypes.data), 0, a
+
+
+class Line:
+    """One field line on the GPU (a ``pic1d_ctx``)."""
+
+    def __init__(self, cfg: dict, stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("paper_2609_17661_b300 needs a CUDA device (no CPU path)")
+        self.L = _lib.load()
+        self.cfg = dict(cfg)
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self._p = make_params(cfg, stream)
+        h = C.c_void_p()
+        rc = self.L.pic1d_init(C.byref(self._p), C.byref(h))
+        if rc != 0:
+            raise PicError(rc, "pic1d_init failed (see stderr)")
+        self.h = h
+        self.N = cfg["n_cells"]
+
+    def _check(self, rc):
+        if rc < 0:
+            raise PicError(rc, self.L.pic1d_last_error(self.h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.pic1d_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------- state
+    def set_state(self, st: dict, E=None, step=0):
+        """pic1d_set_state from numpy (host) or torch CUDA tensors (device)."""
+        n = len(st["pos"])
+        args = [_arr(st["pos"], np.uint32), _arr(st["u"], np.float32), _arr(st["w"], np.float32),
+                _arr(st["sp"], np.uint8), _arr(st["id"], np.uint64)]
+        mems = {m for _, m, _ in args}
+        e = _arr(E, np.float64)
+        if E is not None:
+            mems.add(e[1])
+        if len(mems) > 1:
+            raise ValueError("mixing host and device arrays")
+        mem = mems.pop() if mems else 0
+        self._check(self.L.pic1d_set_state(self.h, n, *[a[0] for a in args], e[0], int(step), mem))
+
+    def step(self, n=1):
+        self._check(self.L.pic1d_step(self.h, int(n)))
+
+    def sort(self):
+        self._check(self.L.pic1d_sort(self.h))
+
+    def timing(self, on=True):
+        """pic1d_timing: bracket every push launch with CUDA events."""
+        self._check(self.L.pic1d_timing(self.h, 1 if on else 0))
+
+    def slots(self):
+        return int(self.L.pic1d_slots(self.h))
+
+    def diag(self) -> dict:
+        d = Diag()
+        rc = self.L.pic1d_diag(self.h, C.byref(d))
+        out = {}
+        for name, _ in Diag._fields_:
+            v = getattr(d, name)
+            out[name] = list(v) if name == "n_alive" else v
+        out["rc"] = rc
+        return out
+
+    def fields(self):
+        E = np.zeros(self.N, np.float64)
+        J = np.zeros(self.N, np.int64)
+        self._check(self.L.pic1d_get_fields(self.h, E.ctypes.data, J.ctypes.data, 0))
+        return E, J
+
+    def particles(self, alive_only=True) -> dict:
+        n = self.slots()
+        out = dict(pos=np.zeros(n, np.uint32), u=np.zeros(n, np.float32), w=np.zeros(n, np.float32),
+                   sp=np.zeros(n, np.uint8), id=np.zeros(n, np.uint64))
+        self._check(self.L.pic1d_get_particles(self.h, n, out["pos"].ctypes.data, out["u"].ctypes.data,
+                                               out["w"].ctypes.data, out["sp"].ctypes.data,
+                                               out["id"].ctypes.data, 0))
+        if alive_only:
+            keep = out["sp"] != 255
+            out = {k: v[keep] for k, v in out.items()}
+        return out
+
+    def table(self):
+        ng, ns = self.cfg["table_n_gamma"], self.cfg["table_n_s"]
+        t = np.zeros(2 * ns * ng * 2, np.float32)
+        self._check(self.L.pic1d_get_table(self.h, t.ctypes.data))
+        return t
+
+    def deposit(self, pos0, pos1, w, sp, J):
+        """pic1d_deposit on torch CUDA tensors (int64 pos0/pos1, float32 w, uint8 sp, int64 J)."""
+        self._check(self.L.pic1d_deposit(self.h, int(pos0.numel()), C.c_void_p(pos0.data_ptr()),
+                                         C.c_void_p(pos1.data_ptr()), C.c_void_p(w.data_ptr()),
+                                         C.c_void_p(sp.data_ptr()), C.c_void_p(J.data_ptr())))
+        return J
+
+
+from . import workloads  # noqa: E402

@@ -1,0 +1,90 @@
+"""ctypes binding of include/pic1d.h: argument marshalling only.
+
+Every step of the method runs in the CUDA kernels of ``libpic1d.so``; this
+module loads that library (and raises if it is missing: there is no CPU
+path) and mirrors its structs.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpic1d.so")
+
+OK, WCAPACITY, EINVAL, ENOMEM, ECUDA, ENUMERIC = 0, 1, -1, -2, -3, -4
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("r_eq", C.c_double), ("n_cells", C.c_int32), ("cfl", C.c_double), ("b_star", C.c_double),
+        ("b_convention", C.c_int32),
+        ("kT_keV", C.c_double), ("photon_model", C.c_int32), ("drag_law", C.c_int32), ("drag_scale", C.c_double),
+        ("table_n_gamma", C.c_int32), ("table_n_s", C.c_int32), ("table_log10g_max", C.c_double),
+        ("quad_n_mu", C.c_int32), ("quad_n_phi", C.c_int32),
+        ("eta_min", C.c_double), ("rics_mode", C.c_int32), ("mc_on", C.c_int32),
+        ("cells_per_skin_depth", C.c_double), ("j_psi", C.c_double), ("n0_ppc", C.c_double),
+        ("mass_ratio", C.c_double),
+        ("inject_mode", C.c_int32), ("inject_T", C.c_double),
+        ("pairs_on", C.c_int32), ("b_pair_threshold", C.c_double), ("pair_energy_threshold", C.c_double),
+        ("n_max_ppc", C.c_double),
+        ("seed", C.c_uint64), ("r_star_cm", C.c_double),
+        ("capacity", C.c_int64), ("sort_every", C.c_int32), ("cuda_stream", C.c_void_p),
+    ]
+
+
+class Diag(C.Structure):
+    _fields_ = [
+        ("step", C.c_int64), ("n_slots", C.c_int64), ("n_alive", C.c_int64 * 4),
+        ("pairs_created", C.c_int64), ("pairs_dropped_cap", C.c_int64), ("pairs_rejected_nmax", C.c_int64),
+        ("pairs_lost_wall", C.c_int64),
+        ("lost_north", C.c_int64), ("lost_south", C.c_int64), ("injected", C.c_int64),
+        ("injected_dropped", C.c_int64),
+        ("scatters", C.c_int64), ("psc_clamped", C.c_int64), ("limiter_branch", C.c_int64),
+        ("newton_branch", C.c_int64), ("nonfinite", C.c_int64),
+        ("rng_draws", C.c_int64), ("push_launches", C.c_int64), ("push_ms", C.c_double), ("push_slots", C.c_int64),
+        ("field_energy", C.c_double), ("kinetic_energy", C.c_double), ("ext_work", C.c_double),
+        ("vc", C.c_double), ("ke_lost", C.c_double),
+        ("q_p", C.c_double), ("j_ext", C.c_double), ("dt", C.c_double), ("tau_min", C.c_double),
+        ("R_cells", C.c_double), ("L_Rstar", C.c_double),
+        ("fbits", C.c_int32), ("status", C.c_int32),
+    ]
+
+
+# exported symbols and their signatures (the declarations of include/pic1d.h)
+SIGNATURES = {
+    "pic1d_init": (C.c_int, [C.POINTER(Params), C.POINTER(C.c_void_p)]),
+    "pic1d_set_state": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_void_p, C.c_void_p, C.c_int64, C.c_int]),
+    "pic1d_step": (C.c_int, [C.c_void_p, C.c_int]),
+    "pic1d_diag": (C.c_int, [C.c_void_p, C.POINTER(Diag)]),
+    "pic1d_get_fields": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "pic1d_slots": (C.c_int64, [C.c_void_p]),
+    "pic1d_get_particles": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_void_p, C.c_int]),
+    "pic1d_sort": (C.c_int, [C.c_void_p]),
+    "pic1d_get_table": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "pic1d_deposit": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                C.c_void_p]),
+    "pic1d_timing": (C.c_int, [C.c_void_p, C.c_int]),
+    "pic1d_last_error": (C.c_char_p, [C.c_void_p]),
+    "pic1d_free": (None, [C.c_void_p]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libpic1d.so; raises OSError if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise OSError(f"{path} is missing: build it with `python -m paper_2609_17661_b300.build` "
+                          "(the library has no CPU fallback)")
+        L = C.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib

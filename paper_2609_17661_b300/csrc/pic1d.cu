@@ -1,0 +1,717 @@
+// pic1d.cu -- host side of the C ABI declared in include/pic1d.h.
+//
+// Builds the dipole field-line tables of App. B.2 in FP64 on the host (arc
+// length in closed form, theta(s) by Newton), the drag/rate table by FP64
+// quadrature on the device, owns all device memory of a context and issues
+// the per-step kernels of kernels.cu on the caller's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pic1d_internal.h"
+
+using namespace pic1d;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kRe = 2.8179403262e-13;       // classical electron radius, cm (CODATA 2018)
+constexpr double kLbar = 3.8615926796e-11;     // reduced Compton wavelength, cm
+constexpr double kMeKeV = 510.99895;           // m_e c^2, keV
+
+// arc length of r = r_eq sin^2(theta) from the northern footpoint, in R*:
+// the antiderivative of sin(t) sqrt(1 + 3 cos^2 t) is -A(cos t) with
+// A(c) = c sqrt(1+3c^2)/2 + asinh(sqrt(3) c)/(2 sqrt(3)).
+double arc_A(double c) { return 0.5 * c * std::sqrt(1.0 + 3.0 * c * c) + std::asinh(std::sqrt(3.0) * c) / (2.0 * std::sqrt(3.0)); }
+
+struct Line {
+  double r_eq, th0, c0, L;
+  explicit Line(double r) : r_eq(r) {
+    th0 = std::asin(std::sqrt(1.0 / r));
+    c0 = std::cos(th0);
+    L = 2.0 * r * arc_A(c0);
+  }
+  double s_of(double th) const { return r_eq * (arc_A(c0) - arc_A(std::cos(th))); }
+  double ds(double th) const {
+    const double c = std::cos(th);
+    return r_eq * std::sin(th) * std::sqrt(1.0 + 3.0 * c * c);
+  }
+  // theta(s), s in R*; Newton from a guess, guarded by a bracket
+  double theta_of(double s, double guess) const {
+    double lo = th0, hi = kPi - th0;
+    double th = std::min(std::max(guess, lo), hi);
+    for (int it = 0; it < 60; ++it) {
+      const double f = s_of(th) - s;
+      if (f > 0) hi = th; else lo = th;
+      const double d = ds(th);
+      double nt = (d > 0) ? th - f / d : 0.5 * (lo + hi);
+      if (!(nt > lo && nt < hi)) nt = 0.5 * (lo + hi);
+      if (std::fabs(nt - th) < 1e-15) { th = nt; break; }
+      th = nt;
+    }
+    return th;
+  }
+};
+
+void field_at(const pic1d_params& p, double th, double& x, double& b, double& mu) {
+  const double c = std::cos(th), sn = std::sin(th);
+  x = p.r_eq * sn * sn;
+  const double root = std::sqrt(1.0 + 3.0 * c * c);
+  b = p.b_star * root / (x * x * x);
+  if (p.b_convention == 1) b *= 0.5;
+  mu = 2.0 * c / root;
+}
+
+// Gauss-Legendre nodes/weights on [-1, 1]: Newton on P_n from Chebyshev guesses
+void legendre_nodes(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < (n + 1) / 2; ++i) {
+    double z = std::cos(kPi * (i + 0.75) / (n + 0.5)), dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      if (n == 1) { p1 = z; p0 = 1.0; }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    x[i] = -z;
+    x[n - 1 - i] = z;
+    w[i] = w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+int fbits_of(int n) {
+  int b = 0;
+  while ((1 << b) < n) ++b;
+  return 32 - b;
+}
+
+}  // namespace
+
+struct pic1d_ctx {
+  pic1d_params p{};
+  cudaStream_t s = nullptr;
+  int N = 0, F = 0;
+  double L_R = 0, R_cells = 0, q_p = 0, j_ext = 0, tau_min = 0, dt = 0;
+  long long cap = 0;
+  int cur = 0;
+  uint32_t* pos[2] = {nullptr, nullptr};
+  float* u[2] = {nullptr, nullptr};
+  float* w[2] = {nullptr, nullptr};
+  uint8_t* sp[2] = {nullptr, nullptr};
+  uint64_t* id[2] = {nullptr, nullptr};
+  double* E64 = nullptr;
+  float* E32 = nullptr;
+  long long* J = nullptr;
+  long long* dens[2] = {nullptr, nullptr};
+  float *nb = nullptr, *nmu = nullptr, *nx = nullptr;
+  uint8_t* zone = nullptr;
+  float2* table = nullptr;
+  Counters* ctr = nullptr;
+  StepState* st = nullptr;
+  double* ke_partial = nullptr;
+  double* field_partial = nullptr;
+  uint32_t* counts = nullptr;
+  long long* offsets = nullptr;
+  unsigned long long* spc = nullptr;
+  int push_grid = 0;
+  long long step = 0;
+  std::string err;
+  // push timing (pic1d_timing)
+  bool timing = false;
+  std::vector<cudaEvent_t> ev;      // pairs (start, stop) per timed launch
+  std::vector<long long> ev_slots;  // slots read by each timed launch (filled at diag)
+  long long* slot_log = nullptr;    // device copy of n_slots at each timed launch
+  long long slot_log_cap = 0;
+  long long timed = 0;
+  double timed_ms = 0.0;
+  long long timed_slots = 0;
+};
+
+namespace {
+
+int fail(pic1d_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int cuda_fail(pic1d_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, e == cudaErrorMemoryAllocation ? PIC1D_ENOMEM : PIC1D_ECUDA,
+              std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, where)                             \
+  do {                                              \
+    cudaError_t e_ = (call);                        \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, where); \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t n) {
+  return cudaMalloc(reinterpret_cast<void**>(p), std::max<size_t>(n, 1) * sizeof(T));
+}
+
+void free_particles(pic1d_ctx* c) {
+  for (int b = 0; b < 2; ++b) {
+    cudaFree(c->pos[b]); cudaFree(c->u[b]); cudaFree(c->w[b]); cudaFree(c->sp[b]); cudaFree(c->id[b]);
+    c->pos[b] = nullptr; c->u[b] = nullptr; c->w[b] = nullptr; c->sp[b] = nullptr; c->id[b] = nullptr;
+  }
+}
+
+int alloc_particles(pic1d_ctx* c, long long cap) {
+  cap = (cap + kTile - 1) / kTile * kTile + kTile;     // whole tiles plus one of slack for the 128-bit loads
+  free_particles(c);
+  for (int b = 0; b < 2; ++b) {
+    CK(dalloc(&c->pos[b], cap), "alloc pos");
+    CK(dalloc(&c->u[b], cap), "alloc u");
+    CK(dalloc(&c->w[b], cap), "alloc w");
+    CK(dalloc(&c->sp[b], cap), "alloc sp");
+    CK(dalloc(&c->id[b], cap), "alloc id");
+    CK(cudaMemsetAsync(c->sp[b], PIC1D_SP_DEAD, cap, c->s), "memset sp");
+  }
+  c->cap = cap - kTile;
+  return PIC1D_OK;
+}
+
+DevParams dev_params(pic1d_ctx* c) {
+  const pic1d_params& p = c->p;
+  DevParams P{};
+  P.N = c->N;
+  P.F = c->F;
+  P.top = (long long)c->N << c->F;
+  P.inv2F = std::ldexp(1.0f, -c->F);
+  P.dt = (float)c->dt;
+  P.half_dt = (float)(0.5 * c->dt);
+  const float qm[4] = {-1.0f, 1.0f, (float)(1.0 / p.mass_ratio), -1.0f};
+  const int qs[4] = {-1, 1, 1, -1};
+  const float ms[4] = {1.0f, 1.0f, (float)p.mass_ratio, 1.0f};
+  for (int k = 0; k < 4; ++k) { P.qm[k] = qm[k]; P.qs[k] = qs[k]; P.mass[k] = ms[k]; }
+  P.drag_law = p.drag_law;
+  P.rics_mode = p.rics_mode;
+  P.mc_on = p.mc_on;
+  P.pairs_on = p.pairs_on;
+  P.limiter_on = c->tau_min > 0.0;
+  P.use_nmax = p.n_max_ppc > 0.0;
+  P.drag_k = (float)(p.drag_scale / c->R_cells);
+  P.tau_min = (float)c->tau_min;
+  P.damp = c->tau_min > 0.0 ? (float)std::exp(-c->dt / (2.0 * c->tau_min)) : 1.0f;
+  P.pair_e_thr = (float)p.pair_energy_threshold;
+  P.nmax_int = P.use_nmax ? (long long)std::floor(p.n_max_ppc * 4096.0) : 0;
+  P.Ng = p.table_n_gamma;
+  P.Ns = p.table_n_s;
+  const double dg = p.table_log10g_max / (p.table_n_gamma - 1);
+  P.t_scale = (float)(std::log10(2.0) / dg);
+  P.dtdu_scale = (float)(1.0 / (std::log(10.0) * dg));
+  P.v_scale = (float)((double)(p.table_n_s - 1) / ((double)P.top));
+  const double th = p.kT_keV / kMeKeV;
+  P.theta_T = (float)th;
+  P.closedK = (float)(kRe * p.r_star_cm / (kLbar * kLbar) * th * th * th / 4.0);
+  P.closedN = (float)(kRe * p.r_star_cm / (kLbar * kLbar) / 4.0);
+  P.key0 = (uint32_t)p.seed;
+  P.key1 = (uint32_t)(p.seed >> 32);
+  P.step = c->step;
+  const int b = c->cur;
+  P.pos = c->pos[b]; P.u = c->u[b]; P.w = c->w[b]; P.sp = c->sp[b]; P.id = c->id[b];
+  P.E32 = c->E32;
+  P.J = c->J;
+  P.table = c->table;
+  P.nb = c->nb; P.nmu = c->nmu; P.nx = c->nx;
+  P.zone = c->zone;
+  P.dens_cur = c->dens[c->step & 1];
+  P.dens_next = c->dens[(c->step + 1) & 1];
+  P.cap = c->cap;
+  P.ctr = c->ctr;
+  P.st = c->st;
+  P.ke_partial = c->ke_partial;
+  return P;
+}
+
+int validate(const pic1d_params* p, std::string& why) {
+  auto bad = [&](const char* m) { why = m; return PIC1D_EINVAL; };
+  if (!p) return bad("params is NULL");
+  if (!(p->r_eq > 1.0)) return bad("r_eq must exceed 1 (the line must leave the star)");
+  if (p->n_cells < 8 || p->n_cells > (1 << 24)) return bad("n_cells must be in [8, 2^24]");
+  if (!(p->cfl > 0.0 && p->cfl < 1.0)) return bad("cfl must be in (0, 1)");
+  if (!(p->b_star > 0.0)) return bad("b_star must be positive");
+  if (p->b_convention != 0 && p->b_convention != 1) return bad("b_convention must be 0 or 1");
+  if (!(p->kT_keV > 0.0)) return bad("kT_keV must be positive");
+  if (p->photon_model != PIC1D_PHOTON_RADIAL && p->photon_model != PIC1D_PHOTON_DISK) return bad("bad photon_model");
+  if (p->drag_law < PIC1D_DRAG_OFF || p->drag_law > PIC1D_DRAG_TABLE) return bad("bad drag_law");
+  if (p->drag_law == PIC1D_DRAG_TABLE && (p->table_n_gamma < 2 || p->table_n_s < 2 || p->table_n_gamma > 65536 ||
+                                          p->table_n_s > 65536 || !(p->table_log10g_max > 0.0)))
+    return bad("bad table shape");
+  if (p->photon_model == PIC1D_PHOTON_DISK && (p->quad_n_mu < 1 || p->quad_n_mu > 256 || p->quad_n_phi < 1))
+    return bad("bad quadrature node counts");
+  if (p->rics_mode != PIC1D_RICS_SPLIT && p->rics_mode != PIC1D_RICS_DRAG_PLUS_PAIRS) return bad("bad rics_mode");
+  if (!(p->cells_per_skin_depth > 0.0) || !(p->n0_ppc > 0.0) || !(p->j_psi >= 0.0)) return bad("bad plasma scales");
+  if (!(p->mass_ratio > 0.0)) return bad("mass_ratio must be positive");
+  if (p->inject_mode != PIC1D_INJECT_NONE && p->inject_mode != PIC1D_INJECT_RATE) return bad("bad inject_mode");
+  if (p->sort_every < 1) return bad("sort_every must be >= 1");
+  if (p->capacity < 0) return bad("capacity must be >= 0");
+  if (!(p->r_star_cm > 0.0)) return bad("r_star_cm must be positive");
+  return PIC1D_OK;
+}
+
+int build_tables(pic1d_ctx* c) {
+  const pic1d_params& p = c->p;
+  const int N = c->N;
+  Line line(p.r_eq);
+  c->L_R = line.L;
+  c->R_cells = N / line.L;
+  std::vector<float> hb(N + 1), hmu(N + 1), hx(N + 1);
+  std::vector<uint8_t> hz(N);
+  double guess = line.th0;
+  for (int k = 0; k <= N; ++k) {
+    const double th = line.theta_of(line.L * (double)k / N, guess);
+    guess = th;
+    double x, b, mu;
+    field_at(p, th, x, b, mu);
+    hb[k] = (float)b; hmu[k] = (float)mu; hx[k] = (float)x;
+  }
+  guess = line.th0;
+  for (int cc = 0; cc < N; ++cc) {
+    const double th = line.theta_of(line.L * (cc + 0.5) / N, guess);
+    guess = th;
+    double x, b, mu;
+    field_at(p, th, x, b, mu);
+    hz[cc] = (b > p.b_pair_threshold) ? 1 : 0;
+  }
+  CK(dalloc(&c->nb, N + 1), "alloc nodes");
+  CK(dalloc(&c->nmu, N + 1), "alloc nodes");
+  CK(dalloc(&c->nx, N + 1), "alloc nodes");
+  CK(dalloc(&c->zone, N), "alloc zone");
+  CK(cudaMemcpyAsync(c->nb, hb.data(), (N + 1) * sizeof(float), cudaMemcpyHostToDevice, c->s), "copy nodes");
+  CK(cudaMemcpyAsync(c->nmu, hmu.data(), (N + 1) * sizeof(float), cudaMemcpyHostToDevice, c->s), "copy nodes");
+  CK(cudaMemcpyAsync(c->nx, hx.data(), (N + 1) * sizeof(float), cudaMemcpyHostToDevice, c->s), "copy nodes");
+  CK(cudaMemcpyAsync(c->zone, hz.data(), N, cudaMemcpyHostToDevice, c->s), "copy zone");
+  CK(cudaStreamSynchronize(c->s), "sync nodes");
+
+  if (p.drag_law == PIC1D_DRAG_TABLE) {
+    const int Ns = p.table_n_s, Ng = p.table_n_gamma;
+    std::vector<double> xs(Ns), bs(Ns), ms(Ns);
+    guess = line.th0;
+    for (int j = 0; j < Ns; ++j) {
+      const double th = line.theta_of(line.L * (double)j / (Ns - 1), guess);
+      guess = th;
+      field_at(p, th, xs[j], bs[j], ms[j]);
+    }
+    std::vector<double> gx, gw;
+    legendre_nodes(std::max(1, p.quad_n_mu), gx, gw);
+    double *dxs, *dbs, *dms, *dgx, *dgw;
+    CK(dalloc(&dxs, Ns), "alloc quad");
+    CK(dalloc(&dbs, Ns), "alloc quad");
+    CK(dalloc(&dms, Ns), "alloc quad");
+    CK(dalloc(&dgx, gx.size()), "alloc quad");
+    CK(dalloc(&dgw, gw.size()), "alloc quad");
+    CK(cudaMemcpyAsync(dxs, xs.data(), Ns * sizeof(double), cudaMemcpyHostToDevice, c->s), "copy quad");
+    CK(cudaMemcpyAsync(dbs, bs.data(), Ns * sizeof(double), cudaMemcpyHostToDevice, c->s), "copy quad");
+    CK(cudaMemcpyAsync(dms, ms.data(), Ns * sizeof(double), cudaMemcpyHostToDevice, c->s), "copy quad");
+    CK(cudaMemcpyAsync(dgx, gx.data(), gx.size() * sizeof(double), cudaMemcpyHostToDevice, c->s), "copy quad");
+    CK(cudaMemcpyAsync(dgw, gw.data(), gw.size() * sizeof(double), cudaMemcpyHostToDevice, c->s), "copy quad");
+    CK(dalloc(&c->table, (size_t)2 * Ns * Ng), "alloc table");
+    const double pref = kRe * p.r_star_cm / (4.0 * kPi * kLbar * kLbar);
+    CK(launch_table(Ng, Ns, p.quad_n_mu, p.quad_n_phi, p.table_log10g_max, p.kT_keV / kMeKeV, pref, dxs, dbs, dms,
+                    dgx, dgw, p.photon_model, c->table, c->s),
+       "table kernel");
+    CK(cudaStreamSynchronize(c->s), "table sync");
+    cudaFree(dxs); cudaFree(dbs); cudaFree(dms); cudaFree(dgx); cudaFree(dgw);
+  }
+  return PIC1D_OK;
+}
+
+int do_sort(pic1d_ctx* c) {
+  DevParams P = dev_params(c);
+  const int o = 1 - c->cur;
+  CK(launch_sort(P, c->counts, c->offsets, c->pos[o], c->u[o], c->w[o], c->sp[o], c->id[o], c->push_grid, c->s),
+     "sort");
+  c->cur = o;
+  return PIC1D_OK;
+}
+
+__global__ void k_validate(const uint32_t* pos, const uint8_t* sp, long long n, long long top,
+                           unsigned long long* bad) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint8_t s = sp[i];
+  if ((s > 3 && s != PIC1D_SP_DEAD) || (long long)pos[i] >= top) atomicAdd(bad, 1ull);
+}
+
+__global__ void k_density(DevParams P, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint8_t s = P.sp[i];
+  if (s == PIC1D_SP_DEAD || s == PIC1D_SP_ION) return;
+  const int cell = min((int)(P.pos[i] >> P.F), P.N - 1);
+  atomicAdd(reinterpret_cast<unsigned long long*>(P.dens_cur + cell),
+            (unsigned long long)__float2ll_rn(P.w[i] * 4096.0f));
+}
+
+// record the start event of one timed push launch and log the slot count it reads
+int timing_begin(pic1d_ctx* c) {
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a), "timing");
+  CK(cudaEventCreate(&b), "timing");
+  c->ev.push_back(a);
+  c->ev.push_back(b);
+  const long long k = (long long)c->ev.size() / 2 - 1;
+  if (k >= c->slot_log_cap) {
+    long long ncap = std::max<long long>(1024, 2 * c->slot_log_cap);
+    long long* nl = nullptr;
+    CK(dalloc(&nl, ncap), "timing");
+    if (c->slot_log) {
+      CK(cudaMemcpyAsync(nl, c->slot_log, c->slot_log_cap * sizeof(long long), cudaMemcpyDeviceToDevice, c->s), "timing");
+      CK(cudaStreamSynchronize(c->s), "timing");
+      cudaFree(c->slot_log);
+    }
+    c->slot_log = nl;
+    c->slot_log_cap = ncap;
+  }
+  CK(cudaMemcpyAsync(c->slot_log + k, &c->st->n_slots, sizeof(long long), cudaMemcpyDeviceToDevice, c->s), "timing");
+  CK(cudaEventRecord(a, c->s), "timing");
+  return PIC1D_OK;
+}
+
+// fold the recorded events into the totals (stream already synchronised)
+int timing_collect(pic1d_ctx* c) {
+  const long long k = (long long)c->ev.size() / 2;
+  if (k == 0) return PIC1D_OK;
+  std::vector<long long> slots(k);
+  CK(cudaMemcpy(slots.data(), c->slot_log, k * sizeof(long long), cudaMemcpyDeviceToHost), "timing");
+  for (long long i = 0; i < k; ++i) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, c->ev[2 * i], c->ev[2 * i + 1]), "timing");
+    c->timed_ms += ms;
+    c->timed_slots += slots[i];
+    c->timed += 1;
+    cudaEventDestroy(c->ev[2 * i]);
+    cudaEventDestroy(c->ev[2 * i + 1]);
+  }
+  c->ev.clear();
+  return PIC1D_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pic1d_init(const pic1d_params* p, pic1d_ctx** out) {
+  if (!out) return PIC1D_EINVAL;
+  *out = nullptr;
+  std::string why;
+  if (validate(p, why) != PIC1D_OK) {
+    std::fprintf(stderr, "pic1d_init: %s\n", why.c_str());
+    return PIC1D_EINVAL;
+  }
+  pic1d_ctx* c = new pic1d_ctx();
+  c->p = *p;
+  c->s = reinterpret_cast<cudaStream_t>(p->cuda_stream);
+  c->N = p->n_cells;
+  c->F = fbits_of(p->n_cells);
+  c->dt = p->cfl;
+  const double n0 = p->n0_ppc;
+  c->q_p = 1.0 / (4.0 * kPi * p->cells_per_skin_depth * p->cells_per_skin_depth * n0);
+  c->j_ext = p->j_psi * n0 * c->q_p;
+  c->tau_min = (p->eta_min > 0.0 && p->j_psi > 0.0) ? p->eta_min * std::sqrt(p->j_psi) * p->cells_per_skin_depth : 0.0;
+  int rc = build_tables(c);
+  const int N = c->N;
+  if (rc == PIC1D_OK) {
+    cudaError_t e = cudaSuccess;
+    auto chain = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
+    chain(dalloc(&c->E64, N));
+    chain(dalloc(&c->E32, N));
+    chain(dalloc(&c->J, N));
+    chain(dalloc(&c->dens[0], N));
+    chain(dalloc(&c->dens[1], N));
+    chain(dalloc(&c->ctr, 1));
+    chain(dalloc(&c->st, 1));
+    chain(dalloc(&c->field_partial, 3 * kMaxFieldBlocks));
+    chain(dalloc(&c->counts, N));
+    chain(dalloc(&c->offsets, N + 1));
+    chain(dalloc(&c->spc, 4));
+    int dev = 0, sms = 0;
+    chain(cudaGetDevice(&dev));
+    chain(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    c->push_grid = std::max(1, sms) * push_blocks_per_sm();
+    chain(dalloc(&c->ke_partial, c->push_grid));
+    if (e == cudaSuccess) {
+      chain(cudaMemsetAsync(c->E64, 0, N * sizeof(double), c->s));
+      chain(cudaMemsetAsync(c->E32, 0, N * sizeof(float), c->s));
+      chain(cudaMemsetAsync(c->J, 0, N * sizeof(long long), c->s));
+      chain(cudaMemsetAsync(c->dens[0], 0, N * sizeof(long long), c->s));
+      chain(cudaMemsetAsync(c->dens[1], 0, N * sizeof(long long), c->s));
+      chain(cudaMemsetAsync(c->ctr, 0, sizeof(Counters), c->s));
+      chain(cudaMemsetAsync(c->st, 0, sizeof(StepState), c->s));
+      chain(cudaMemsetAsync(c->ke_partial, 0, c->push_grid * sizeof(double), c->s));
+    }
+    if (e != cudaSuccess) rc = cuda_fail(c, e, "init");
+  }
+  if (rc == PIC1D_OK) rc = alloc_particles(c, p->capacity > 0 ? p->capacity : 4 * kTile);
+  if (rc == PIC1D_OK) {
+    cudaError_t e = cudaStreamSynchronize(c->s);
+    if (e != cudaSuccess) rc = cuda_fail(c, e, "init sync");
+  }
+  if (rc != PIC1D_OK) {
+    std::fprintf(stderr, "pic1d_init: %s\n", c->err.c_str());
+    pic1d_free(c);
+    return rc;
+  }
+  *out = c;
+  return PIC1D_OK;
+}
+
+int pic1d_set_state(pic1d_ctx* c, int64_t n, const uint32_t* pos, const float* u, const float* w,
+                    const uint8_t* sp, const uint64_t* id, const double* E, int64_t step, int mem) {
+  if (!c) return PIC1D_EINVAL;
+  if (n < 0 || (n > 0 && (!pos || !u || !w || !sp || !id)) || (mem != 0 && mem != 1) || step < 0)
+    return fail(c, PIC1D_EINVAL, "set_state: bad arguments");
+  const long long top = (long long)c->N << c->F;
+  if (mem == 0) {
+    for (int64_t i = 0; i < n; ++i) {
+      if ((sp[i] > 3 && sp[i] != PIC1D_SP_DEAD) || (long long)pos[i] >= top)
+        return fail(c, PIC1D_EINVAL, "set_state: species or position out of range at index " + std::to_string(i));
+    }
+  }
+  const long long want = c->p.capacity > 0 ? std::max<long long>(c->p.capacity, n) : 2 * n + 4 * kTile;
+  if (n > c->cap || (c->p.capacity == 0 && c->cap < want)) {
+    int rc = alloc_particles(c, want);
+    if (rc != PIC1D_OK) return rc;
+  }
+  c->cur = 0;
+  const cudaMemcpyKind k = mem ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (n > 0) {
+    CK(cudaMemcpyAsync(c->pos[0], pos, n * sizeof(uint32_t), k, c->s), "set_state pos");
+    CK(cudaMemcpyAsync(c->u[0], u, n * sizeof(float), k, c->s), "set_state u");
+    CK(cudaMemcpyAsync(c->w[0], w, n * sizeof(float), k, c->s), "set_state w");
+    CK(cudaMemcpyAsync(c->sp[0], sp, n * sizeof(uint8_t), k, c->s), "set_state sp");
+    CK(cudaMemcpyAsync(c->id[0], id, n * sizeof(uint64_t), k, c->s), "set_state id");
+  }
+  CK(cudaMemsetAsync(c->sp[0] + n, PIC1D_SP_DEAD, (size_t)(c->cap + kTile - n), c->s), "set_state tail");
+  if (mem == 1 && n > 0) {
+    unsigned long long* bad = c->spc;
+    CK(cudaMemsetAsync(bad, 0, sizeof(unsigned long long), c->s), "validate");
+    k_validate<<<(unsigned)((n + 255) / 256), 256, 0, c->s>>>(c->pos[0], c->sp[0], n, top, bad);
+    unsigned long long hb = 0;
+    CK(cudaMemcpyAsync(&hb, bad, sizeof(hb), cudaMemcpyDeviceToHost, c->s), "validate");
+    CK(cudaStreamSynchronize(c->s), "validate");
+    if (hb) return fail(c, PIC1D_EINVAL, "set_state: " + std::to_string(hb) + " particles with bad species or position");
+  }
+  if (E) {
+    std::vector<float> e32;
+    CK(cudaMemcpyAsync(c->E64, E, c->N * sizeof(double), k, c->s), "set_state E");
+    std::vector<double> h(c->N);
+    if (mem == 0) std::memcpy(h.data(), E, c->N * sizeof(double));
+    else CK(cudaMemcpyAsync(h.data(), E, c->N * sizeof(double), cudaMemcpyDeviceToHost, c->s), "set_state E");
+    CK(cudaStreamSynchronize(c->s), "set_state E");
+    e32.resize(c->N);
+    for (int i = 0; i < c->N; ++i) e32[i] = (float)h[i];
+    CK(cudaMemcpyAsync(c->E32, e32.data(), c->N * sizeof(float), cudaMemcpyHostToDevice, c->s), "set_state E32");
+    CK(cudaStreamSynchronize(c->s), "set_state E32");
+  } else {
+    CK(cudaMemsetAsync(c->E64, 0, c->N * sizeof(double), c->s), "set_state E");
+    CK(cudaMemsetAsync(c->E32, 0, c->N * sizeof(float), c->s), "set_state E");
+  }
+  CK(cudaMemsetAsync(c->J, 0, c->N * sizeof(long long), c->s), "set_state J");
+  c->step = step;
+  StepState st{};
+  st.n_slots = n;
+  CK(cudaMemcpyAsync(c->st, &st, sizeof(st), cudaMemcpyHostToDevice, c->s), "set_state st");
+  CK(cudaMemsetAsync(c->dens[0], 0, c->N * sizeof(long long), c->s), "set_state dens");
+  CK(cudaMemsetAsync(c->dens[1], 0, c->N * sizeof(long long), c->s), "set_state dens");
+  if (n > 0 && c->p.n_max_ppc > 0.0) {
+    DevParams P = dev_params(c);
+    k_density<<<(unsigned)((n + 255) / 256), 256, 0, c->s>>>(P, n);
+    CK(cudaGetLastError(), "set_state density");
+  }
+  CK(cudaStreamSynchronize(c->s), "set_state sync");
+  return PIC1D_OK;
+}
+
+int pic1d_step(pic1d_ctx* c, int n_steps) {
+  if (!c) return PIC1D_EINVAL;
+  if (n_steps < 0) return fail(c, PIC1D_EINVAL, "step: n_steps < 0");
+  const pic1d_params& p = c->p;
+  const double four_pi = 4.0 * kPi;
+  const double a = four_pi * c->dt * c->j_ext;
+  const double cJ = four_pi * c->q_p * std::ldexp(1.0, -c->F - kWBits);
+  const double dt_jext = c->dt * c->j_ext;
+  const double carriers = p.j_psi * p.n0_ppc * c->dt;     // j_ext dt / q_p carriers of weight 1
+  const float sig_e = (float)std::sqrt(p.inject_T), sig_i = (float)std::sqrt(p.inject_T / p.mass_ratio);
+  for (int k = 0; k < n_steps; ++k) {
+    DevParams P = dev_params(c);
+    CK(cudaMemsetAsync(c->J, 0, c->N * sizeof(long long), c->s), "clear J");
+    if (c->timing) {
+      int rc = timing_begin(c);
+      if (rc != PIC1D_OK) return rc;
+    }
+    CK(launch_push(P, c->push_grid, c->s), "push");
+    if (c->timing) CK(cudaEventRecord(c->ev.back(), c->s), "timing");
+    if (p.inject_mode == PIC1D_INJECT_RATE) CK(launch_inject(P, carriers, sig_e, sig_i, c->s), "inject");
+    CK(launch_field(P, c->E64, c->E32, a, cJ, dt_jext, c->field_partial, c->push_grid, c->s), "field");
+    c->step += 1;
+    if (c->step % p.sort_every == 0) {
+      int rc = do_sort(c);
+      if (rc != PIC1D_OK) return rc;
+    }
+  }
+  return PIC1D_OK;
+}
+
+int pic1d_sort(pic1d_ctx* c) {
+  if (!c) return PIC1D_EINVAL;
+  return do_sort(c);
+}
+
+int64_t pic1d_slots(pic1d_ctx* c) {
+  if (!c) return -1;
+  StepState st{};
+  if (cudaMemcpyAsync(&st, c->st, sizeof(st), cudaMemcpyDeviceToHost, c->s) != cudaSuccess) return -1;
+  if (cudaStreamSynchronize(c->s) != cudaSuccess) return -1;
+  return st.n_slots;
+}
+
+int pic1d_diag(pic1d_ctx* c, pic1d_diag_t* out) {
+  if (!c || !out) return PIC1D_EINVAL;
+  std::memset(out, 0, sizeof(*out));
+  DevParams P = dev_params(c);
+  CK(launch_count_species(P, c->spc, c->s), "diag count");
+  Counters C{};
+  StepState st{};
+  unsigned long long spc[4];
+  CK(cudaMemcpyAsync(&C, c->ctr, sizeof(C), cudaMemcpyDeviceToHost, c->s), "diag");
+  CK(cudaMemcpyAsync(&st, c->st, sizeof(st), cudaMemcpyDeviceToHost, c->s), "diag");
+  CK(cudaMemcpyAsync(spc, c->spc, sizeof(spc), cudaMemcpyDeviceToHost, c->s), "diag");
+  CK(cudaStreamSynchronize(c->s), "diag sync");
+  out->step = c->step;
+  out->n_slots = st.n_slots;
+  for (int k = 0; k < 4; ++k) out->n_alive[k] = (int64_t)spc[k];
+  out->pairs_created = C.pairs_created;
+  out->pairs_dropped_cap = C.pairs_dropped_cap;
+  out->pairs_rejected_nmax = C.pairs_rejected_nmax;
+  out->pairs_lost_wall = C.pairs_lost_wall;
+  out->lost_north = C.lost_north;
+  out->lost_south = C.lost_south;
+  out->injected = C.injected;
+  out->injected_dropped = C.injected_dropped;
+  out->scatters = C.scatters;
+  out->psc_clamped = C.psc_clamped;
+  out->limiter_branch = C.limiter_branch;
+  out->newton_branch = C.newton_branch;
+  out->nonfinite = C.nonfinite;
+  out->rng_draws = C.rng_draws;
+  {
+    int rc = timing_collect(c);
+    if (rc != PIC1D_OK) return rc;
+  }
+  out->push_launches = c->timed;
+  out->push_ms = c->timed_ms;
+  out->push_slots = c->timed_slots;
+  out->field_energy = st.field_energy;
+  out->kinetic_energy = st.kinetic * c->q_p;
+  out->ext_work = st.ext_work;
+  out->vc = st.vc;
+  out->ke_lost = st.ke_lost * c->q_p;
+  out->q_p = c->q_p;
+  out->j_ext = c->j_ext;
+  out->dt = c->dt;
+  out->tau_min = c->tau_min;
+  out->R_cells = c->R_cells;
+  out->L_Rstar = c->L_R;
+  out->fbits = c->F;
+  int status = PIC1D_OK;
+  if (C.nonfinite) status = PIC1D_ENUMERIC;
+  else if (C.pairs_dropped_cap || C.injected_dropped) status = PIC1D_WCAPACITY;
+  out->status = status;
+  if (status == PIC1D_ENUMERIC) c->err = "a step met a non-finite momentum";
+  return status;
+}
+
+int pic1d_get_fields(pic1d_ctx* c, double* E, int64_t* J, int mem) {
+  if (!c || (mem != 0 && mem != 1)) return PIC1D_EINVAL;
+  const cudaMemcpyKind k = mem ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (E) CK(cudaMemcpyAsync(E, c->E64, c->N * sizeof(double), k, c->s), "get E");
+  if (J) CK(cudaMemcpyAsync(J, c->J, c->N * sizeof(long long), k, c->s), "get J");
+  CK(cudaStreamSynchronize(c->s), "get_fields sync");
+  return PIC1D_OK;
+}
+
+int pic1d_get_particles(pic1d_ctx* c, int64_t n, uint32_t* pos, float* u, float* w, uint8_t* sp, uint64_t* id,
+                        int mem) {
+  if (!c || n < 0 || (mem != 0 && mem != 1)) return PIC1D_EINVAL;
+  const int64_t have = pic1d_slots(c);
+  if (have < 0) return fail(c, PIC1D_ECUDA, "get_particles: slot count");
+  if (n > have) return fail(c, PIC1D_EINVAL, "get_particles: n exceeds the used slots");
+  const cudaMemcpyKind k = mem ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  const int b = c->cur;
+  if (n > 0) {
+    if (pos) CK(cudaMemcpyAsync(pos, c->pos[b], n * sizeof(uint32_t), k, c->s), "get pos");
+    if (u) CK(cudaMemcpyAsync(u, c->u[b], n * sizeof(float), k, c->s), "get u");
+    if (w) CK(cudaMemcpyAsync(w, c->w[b], n * sizeof(float), k, c->s), "get w");
+    if (sp) CK(cudaMemcpyAsync(sp, c->sp[b], n * sizeof(uint8_t), k, c->s), "get sp");
+    if (id) CK(cudaMemcpyAsync(id, c->id[b], n * sizeof(uint64_t), k, c->s), "get id");
+  }
+  CK(cudaStreamSynchronize(c->s), "get_particles sync");
+  return PIC1D_OK;
+}
+
+int pic1d_get_table(pic1d_ctx* c, float* out) {
+  if (!c || !out) return PIC1D_EINVAL;
+  if (!c->table) return fail(c, PIC1D_EINVAL, "get_table: drag_law is not TABLE");
+  const size_t n = (size_t)2 * c->p.table_n_s * c->p.table_n_gamma;
+  CK(cudaMemcpyAsync(out, c->table, n * sizeof(float2), cudaMemcpyDeviceToHost, c->s), "get table");
+  CK(cudaStreamSynchronize(c->s), "get table sync");
+  return PIC1D_OK;
+}
+
+int pic1d_deposit(pic1d_ctx* c, int64_t n, const int64_t* pos0, const int64_t* pos1, const float* w,
+                  const uint8_t* sp, int64_t* J) {
+  if (!c || n < 0 || (n > 0 && (!pos0 || !pos1 || !w || !sp || !J))) return PIC1D_EINVAL;
+  DevParams P = dev_params(c);
+  CK(launch_deposit(P, n, reinterpret_cast<const long long*>(pos0), reinterpret_cast<const long long*>(pos1), w, sp,
+                    reinterpret_cast<long long*>(J), c->s),
+     "deposit");
+  CK(cudaStreamSynchronize(c->s), "deposit sync");
+  return PIC1D_OK;
+}
+
+int pic1d_timing(pic1d_ctx* c, int on) {
+  if (!c) return PIC1D_EINVAL;
+  CK(cudaStreamSynchronize(c->s), "timing sync");
+  int rc = timing_collect(c);
+  if (rc != PIC1D_OK) return rc;
+  c->timing = on != 0;
+  c->timed = 0;
+  c->timed_ms = 0.0;
+  c->timed_slots = 0;
+  return PIC1D_OK;
+}
+
+const char* pic1d_last_error(const pic1d_ctx* c) {
+  if (!c) return "no context";
+  return c->err.c_str();
+}
+
+void pic1d_free(pic1d_ctx* c) {
+  if (!c) return;
+  if (c->s) cudaStreamSynchronize(c->s);
+  else cudaDeviceSynchronize();
+  free_particles(c);
+  for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+  void* ptrs[] = {c->E64, c->E32, c->J, c->dens[0], c->dens[1], c->nb, c->nmu, c->nx, c->zone, c->table,
+                  c->ctr, c->st, c->ke_partial, c->field_partial, c->counts, c->offsets, c->spc, c->slot_log};
+  for (void* q : ptrs) cudaFree(q);
+  delete c;
+}
+
+}  // extern "C"

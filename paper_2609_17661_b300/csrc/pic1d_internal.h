@@ -1,0 +1,96 @@
+// pic1d_internal.h -- data shared between the host glue and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pic1d.h"
+
+namespace pic1d {
+
+constexpr int kBlock = 256;          // threads per block of the particle kernels
+constexpr int kPerThread = 4;        // particles per thread (128-bit SoA loads)
+constexpr int kTile = kBlock * kPerThread;
+constexpr int kWindow = 2048;        // cells of the shared-memory deposit window
+constexpr int kWBits = 12;           // weight fixed point: w_int = rint(w * 2^12)
+constexpr uint32_t kTagRics = 0x52494353u;
+constexpr uint32_t kTagInj = 0x494E4A31u;
+constexpr int kMaxFieldBlocks = 1024;
+
+// Device-side counters, accumulated over the life of the context.
+struct Counters {
+  unsigned long long pairs_created, pairs_dropped_cap, pairs_rejected_nmax, pairs_lost_wall;
+  unsigned long long lost_north, lost_south, injected, injected_dropped;
+  unsigned long long scatters, psc_clamped, limiter_branch, newton_branch, nonfinite;
+  unsigned long long rng_draws;
+  unsigned long long pad[2];
+};
+
+// Per-step device scalars.
+struct StepState {
+  long long n_slots;        // slots read by the particle kernels
+  long long append;         // slots appended during the current step
+  long long sorted_total;   // alive count produced by the sort scan
+  double inj_acc[2];        // RATE injection accumulators (north, south)
+  double field_energy, vc, ext_work, kinetic, ke_lost;
+};
+
+// Everything a particle kernel needs, passed by value.
+struct DevParams {
+  int N, F;
+  long long top;            // N << F
+  float inv2F;              // 2^-F
+  float dt, half_dt;
+  float qm[4];              // q/m per species in units of e/m_e
+  int qs[4];                // charge sign per species
+  float mass[4];
+  int drag_law, rics_mode, mc_on, pairs_on, limiter_on, use_nmax;
+  float drag_k;             // drag_scale / R_cells: F^ and N^ per R_star/c -> per cell-crossing time
+  float tau_min, damp;      // limiter floor and exp(-dt/(2 tau_min))
+  float pair_e_thr;
+  long long nmax_int;
+  // table
+  int Ng, Ns;
+  float t_scale;            // log2(gamma) -> table index
+  float dtdu_scale;         // 1/(ln 10 * dlog10g)
+  float v_scale;            // pos -> s/L index
+  // closed form (radial photons)
+  float theta_T;            // kT / m_e c^2
+  float closedK;            // r_e R* theta^3 / (4 lbar^2)  (divide by x^2)
+  float closedN;            // r_e R* / (4 lbar^2)          (divide by x^2 gamma)
+  uint32_t key0, key1;
+  long long step;
+  // arrays
+  uint32_t* pos; float* u; float* w; uint8_t* sp; uint64_t* id;
+  const float* E32;
+  long long* J;
+  const float2* table;
+  const float* nb; const float* nmu; const float* nx;
+  const uint8_t* zone;
+  long long* dens_cur; long long* dens_next;
+  long long cap;
+  Counters* ctr;
+  StepState* st;
+  double* ke_partial;       // one per block of the push
+};
+
+}  // namespace pic1d
+
+// kernel launchers (kernels.cu)
+namespace pic1d {
+cudaError_t launch_push(const DevParams& P, int grid, cudaStream_t s);
+cudaError_t launch_inject(const DevParams& P, double carriers_per_step, float sig_e, float sig_i,
+                          cudaStream_t s);
+cudaError_t launch_field(const DevParams& P, double* E64, float* E32, double four_pi_dt_jext, double cJ,
+                         double dt_jext, double* field_partial, int grid_push, cudaStream_t s);
+cudaError_t launch_sort(const DevParams& P, uint32_t* counts, long long* offsets,
+                        uint32_t* pos2, float* u2, float* w2, uint8_t* sp2, uint64_t* id2, int grid,
+                        cudaStream_t s);
+cudaError_t launch_table(int Ng, int Ns, int n_mu, int n_phi, double log10g_max, double theta_T,
+                         double pref, const double* xs, const double* bs, const double* mus, const double* gx,
+                         const double* gw, int photon_model, float2* out, cudaStream_t s);
+cudaError_t launch_deposit(const DevParams& P, long long n, const long long* p0, const long long* p1,
+                           const float* w, const uint8_t* sp, long long* J, cudaStream_t s);
+cudaError_t launch_count_species(const DevParams& P, unsigned long long* out4, cudaStream_t s);
+int push_blocks_per_sm();
+}  // namespace pic1d

@@ -200,16 +200,14 @@ def load_two_stream(cfg: dict, ppc=64, u0=0.2, amp=1e-4, mode=1) -> dict:
     return st
 
 
-def pair_loaded_counts(n_cells: int, total: int) -> np.ndarray:
-    """Particles per cell of the synthetic pair-loaded line: denser toward
-    the footpoints, total ``total`` (even in every cell)."""
+def pair_loaded_counts(n_cells: int, total: int, seed: int = 11) -> np.ndarray:
+    """Particles per cell of the synthetic pair-loaded line: a seeded
+    multinomial draw of ``total`` particles (in pairs) from a profile denser
+    toward the footpoints."""
     x = (np.arange(n_cells) + 0.5) / n_cells
     prof = 1.0 + 3.0 * np.abs(2.0 * x - 1.0) ** 6
-    cnt = np.floor(prof / prof.sum() * total / 2.0).astype(np.int64) * 2
-    short = total - int(cnt.sum())
-    if short > 0:
-        cnt[: short // 2] += 2
-    return cnt
+    rng = np.random.default_rng(seed)
+    return 2 * rng.multinomial(total // 2, prof / prof.sum()).astype(np.int64)
 
 
 def fill_pair_loaded(cfg: dict, out: dict, start_cell: int, end_cell: int, counts: np.ndarray,

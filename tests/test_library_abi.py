@@ -1,0 +1,70 @@
+"""The C-ABI library loads and exports every entry point include/pic1d.h
+declares (CPU only: no compute call is made here)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "pic1d.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(pic1d_[a-z_0-9]+)\s*\(", txt)))
+
+
+def _lib_path():
+    from paper_2609_17661_b300 import build
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("pic1d_init", "pic1d_step", "pic1d_diag", "pic1d_set_state", "pic1d_free", "pic1d_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    path = _lib_path()
+    lib = ctypes.CDLL(path)
+    for n in _declared():
+        assert hasattr(lib, n), n
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (pic1d_\w+)", out))
+    assert set(_declared()) <= exported
+
+
+def test_binding_mirrors_header_structs():
+    """The ctypes structs list the header's fields in the header's order."""
+    from paper_2609_17661_b300 import _lib
+    txt = open(os.path.join(ROOT, "include", "pic1d.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    for struct, cls in (("pic1d_params", _lib.Params), ("pic1d_diag_t", _lib.Diag)):
+        body = re.search(r"typedef struct " + struct + r"\s*\{(.*?)\}\s*" + struct, txt, flags=re.S).group(1)
+        names = []
+        for decl in body.split(";"):
+            decl = decl.strip()
+            if not decl:
+                continue
+            decl = re.sub(r"^\w+\*?\s+", "", decl)
+            for piece in decl.split(","):
+                names.append(re.sub(r"\[.*\]", "", piece).strip().lstrip("*"))
+        assert names == [f[0] for f in cls._fields_], struct
+
+
+def test_binding_signatures_cover_header():
+    from paper_2609_17661_b300 import _lib
+    assert sorted(_lib.SIGNATURES) == _declared()
+
+
+def test_no_cpu_fallback_without_device():
+    """Constructing a line without a CUDA device fails loudly."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a device is present")
+    from paper_2609_17661_b300 import Line, workloads as W
+    with pytest.raises(RuntimeError):
+        Line(W.config("C1"))
