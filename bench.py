@@ -279,6 +279,8 @@ def run_gpu(args):
                "roofline": roof, "clocks": clocks, "e2e": e2e, "cpu_baseline": cb,
                "gpu_launches": gpu_launches(args.steps, cfg, d0["step"]),
                "pairs_created": d1["pairs_created"] - d0["pairs_created"], "rng_draws": draws,
+               "branches": {k: d1[k] - d0[k] for k in ("limiter_branch", "newton_branch", "scatters", "psc_clamped",
+                                                       "pairs_rejected_nmax", "lost_north", "lost_south")},
                "setup_s": {"host_state": t_gen}}
         print(json.dumps(out), flush=True)
     line.close()

@@ -138,6 +138,7 @@ typedef struct pic1d_diag_t {
   double ke_lost;           /* cumulative kinetic energy carried out at the walls */
   double q_p, j_ext, dt, tau_min, R_cells, L_Rstar; /* derived constants         */
   int32_t fbits, status;
+  int32_t push_variant;     /* push kernel variant in use (pic1d_set_variant) */
 } pic1d_diag_t;
 
 typedef struct pic1d_ctx pic1d_ctx;
@@ -206,6 +207,15 @@ int pic1d_deposit(pic1d_ctx* c, int64_t n, const int64_t* pos0, const int64_t* p
  * particle slots they read since the call; on = 0 stops it.  No effect on
  * results.  Errors: ECUDA. */
 int pic1d_timing(pic1d_ctx* c, int on);
+
+/* Choose the push kernel variant: particles per thread (128/64/32-bit SoA
+ * accesses) x minimum resident blocks per SM.  Results do not depend on the
+ * variant (integer deposit, per-particle arithmetic).  Errors: EINVAL. */
+int pic1d_set_variant(pic1d_ctx* c, int variant);
+
+/* Describe push variant `variant`; returns the number of variants, or EINVAL.
+ * Either output may be NULL.  Needs no context. */
+int pic1d_variant_info(int variant, int* particles_per_thread, int* min_blocks_per_sm);
 
 /* Message of the last error on this context (never NULL). */
 const char* pic1d_last_error(const pic1d_ctx* c);

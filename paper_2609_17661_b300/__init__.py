@@ -120,6 +120,20 @@ class Line:
         """pic1d_timing: bracket every push launch with CUDA events."""
         self._check(self.L.pic1d_timing(self.h, 1 if on else 0))
 
+    def set_variant(self, v):
+        """pic1d_set_variant: choose the push kernel variant."""
+        self._check(self.L.pic1d_set_variant(self.h, int(v)))
+
+    def variants(self):
+        """[(particles per thread, min blocks per SM)] of every push variant."""
+        out = []
+        n = self.L.pic1d_variant_info(0, None, None)
+        for v in range(n):
+            a, b = C.c_int(), C.c_int()
+            self.L.pic1d_variant_info(v, C.byref(a), C.byref(b))
+            out.append((a.value, b.value))
+        return out
+
     def slots(self):
         return int(self.L.pic1d_slots(self.h))
 

@@ -10,7 +10,7 @@ import ctypes as C
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libpic1d.so")
+LIB_PATH = os.environ.get("PIC1D_LIB", os.path.join(HERE, "libpic1d.so"))
 
 OK, WCAPACITY, EINVAL, ENOMEM, ECUDA, ENUMERIC = 0, 1, -1, -2, -3, -4
 
@@ -47,7 +47,7 @@ class Diag(C.Structure):
         ("vc", C.c_double), ("ke_lost", C.c_double),
         ("q_p", C.c_double), ("j_ext", C.c_double), ("dt", C.c_double), ("tau_min", C.c_double),
         ("R_cells", C.c_double), ("L_Rstar", C.c_double),
-        ("fbits", C.c_int32), ("status", C.c_int32),
+        ("fbits", C.c_int32), ("status", C.c_int32), ("push_variant", C.c_int32),
     ]
 
 
@@ -67,6 +67,8 @@ SIGNATURES = {
     "pic1d_deposit": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                 C.c_void_p]),
     "pic1d_timing": (C.c_int, [C.c_void_p, C.c_int]),
+    "pic1d_set_variant": (C.c_int, [C.c_void_p, C.c_int]),
+    "pic1d_variant_info": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "pic1d_last_error": (C.c_char_p, [C.c_void_p]),
     "pic1d_free": (None, [C.c_void_p]),
 }

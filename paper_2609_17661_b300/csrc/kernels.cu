@@ -72,9 +72,13 @@ struct DragVal {
   float F, dF, lnN;  // F^ (per R*), dF^/du, ln N^ (per R_star/c)
 };
 
+// Bilinear table lookup in (log10 gamma, s/L).  The device copy of the table
+// pairs neighbouring s-rows: tpair[(sg*(Ns-1) + j)*Ng + i] = (F[j][i], lnN[j][i],
+// F[j+1][i], lnN[j+1][i]), so one lookup is two adjacent 16-byte loads.
+// log10 gamma = log10(2)/2 * log2(1 + u^2): no square root is needed.
 __device__ __forceinline__ DragVal table_eval(const DevParams& P, float u, float v, bool want_dF) {
-  const float gam = sqrtf(fmaf(u, u, 1.0f));
-  float t = log2f(gam) * P.t_scale;
+  const float q = fmaf(u, u, 1.0f);                    // gamma^2
+  float t = fmaxf(0.5f * __log2f(q) * P.t_scale, 0.0f);
   bool top = false;
   if (t > (float)(P.Ng - 1)) { t = (float)(P.Ng - 1); top = true; }
   const int i = min((int)t, P.Ng - 2);
@@ -82,17 +86,16 @@ __device__ __forceinline__ DragVal table_eval(const DevParams& P, float u, float
   const int j = min((int)v, P.Ns - 2);
   const float c = v - (float)j;
   const int sg = (u >= 0.0f) ? 0 : 1;
-  const float2* r0 = P.table + ((size_t)(sg * P.Ns + j) * P.Ng);
-  const float2* r1 = r0 + P.Ng;
-  const float2 q00 = __ldg(r0 + i), q10 = __ldg(r0 + i + 1), q01 = __ldg(r1 + i), q11 = __ldg(r1 + i + 1);
+  const float4* row = P.tpair + ((size_t)(sg * (P.Ns - 1) + j) * P.Ng);
+  const float4 A = __ldg(row + i), B = __ldg(row + i + 1);
   const float ac = 1.0f - a, cc = 1.0f - c;
   DragVal d;
-  d.F = ac * cc * q00.x + a * cc * q10.x + ac * c * q01.x + a * c * q11.x;
-  d.lnN = ac * cc * q00.y + a * cc * q10.y + ac * c * q01.y + a * c * q11.y;
+  d.F = ac * (cc * A.x + c * A.z) + a * (cc * B.x + c * B.z);
+  d.lnN = ac * (cc * A.y + c * A.w) + a * (cc * B.y + c * B.w);
   d.dF = 0.0f;
   if (want_dF && !top) {
-    const float dFdt = cc * (q10.x - q00.x) + c * (q11.x - q01.x);
-    d.dF = dFdt * (u / (gam * gam)) * P.dtdu_scale;
+    const float dFdt = cc * (B.x - A.x) + c * (B.z - A.z);
+    d.dF = dFdt * __fdividef(u, q) * P.dtdu_scale;
   }
   return d;
 }
@@ -131,15 +134,15 @@ __device__ __forceinline__ DragVal drag_eval(const DevParams& P, float u, const 
 }
 
 // One drag update over dt/2 at fixed s (Sec. 3): limiter test |F| tau_min <
-// |u0|, then the implicit midpoint [Eq. implicit] by 4 Newton iterations or
-// exponential damping toward p~ = mu / sqrt(1 - mu^2).
+// |u0|, then the implicit midpoint [Eq. implicit] by up to 4 Newton
+// iterations, or exponential damping toward p~ = mu / sqrt(1 - mu^2).  An
+// iteration that leaves u1 unchanged is a fixed point: the remaining ones
+// would repeat it bit for bit, so stopping there gives the 4-iteration result.
 __device__ __forceinline__ float drag_half(const DevParams& P, const Site& S, float u0, unsigned& n_lim,
                                            unsigned& n_newt) {
   const float h = P.half_dt;
-  const DragVal d0 = drag_eval(P, u0, S, true);
-  const float F0 = P.drag_k * d0.F;
-  bool newton = true;
-  if (P.limiter_on) newton = fabsf(F0) * P.tau_min < fabsf(u0);
+  const float F0 = P.drag_k * drag_eval(P, u0, S, false).F;
+  const bool newton = !P.limiter_on || (fabsf(F0) * P.tau_min < fabsf(u0));
   if (newton) {
     ++n_newt;
     float u1 = fmaf(h, F0, u0);
@@ -149,13 +152,15 @@ __device__ __forceinline__ float drag_half(const DevParams& P, const Site& S, fl
       const float F1 = P.drag_k * d1.F;
       const float G = u1 - u0 - 0.5f * h * (F0 + F1);
       const float dG = fmaxf(1.0f - 0.5f * h * P.drag_k * d1.dF, 0.5f);
-      u1 -= G / dG;
+      const float un = u1 - __fdividef(G, dG);
+      if (un == u1) break;
+      u1 = un;
     }
     return u1;
   }
   ++n_lim;
-  const float ut = S.mu / sqrtf(1.0f - S.mu * S.mu);
-  return ut + (u0 - ut) * P.damp;
+  const float ut = S.mu * rsqrtf(1.0f - S.mu * S.mu);
+  return fmaf(u0 - ut, P.damp, ut);
 }
 
 // de-excitation angle with density (3/8)(1 + c^2): Cardano root of c^3 + 3c + 4 - 8U = 0
@@ -199,63 +204,33 @@ __device__ __forceinline__ void add_cell(long long* sWin, int win_lo, long long*
     atomicAdd(reinterpret_cast<unsigned long long*>(g + cell), (unsigned long long)v);
 }
 
-__device__ __forceinline__ void acc_cell(long long (&a)[3], int c_ref, long long* sWin, int win_lo, long long* g,
-                                         int N, int cell, long long v) {
-  const int o = cell - c_ref + 1;
-  if (o == 0) a[0] += v;
-  else if (o == 1) a[1] += v;
-  else if (o == 2) a[2] += v;
-  else add_cell(sWin, win_lo, g, N, cell, v);
+// exact int64 sum over the lanes of `grp` (lanes that share a key): three
+// 21-bit slices, each summed by one redux (|v| < 2^62 keeps every slice sum
+// inside 32 bits), recombined in 64 bits.  Order-independent and exact.
+__device__ __forceinline__ long long group_sum64(unsigned grp, long long v) {
+  const unsigned lo = (unsigned)(v & 0x1FFFFF);
+  const unsigned mid = (unsigned)((v >> 21) & 0x1FFFFF);
+  const int hi = (int)(v >> 42);
+  const unsigned slo = __reduce_add_sync(grp, lo);
+  const unsigned smid = __reduce_add_sync(grp, mid);
+  const int shi = (int)__reduce_add_sync(grp, (unsigned)hi);
+  return ((long long)shi << 42) + ((long long)smid << 21) + (long long)slo;
 }
 
-// path [a, b] in fixed point (both inside [0, top]): signed length inside each
-// cell times wq, the 1D charge-conserving current of Sec. 3.
-__device__ __forceinline__ void deposit_path(long long (&acc)[3], int c_ref, long long* sWin, int win_lo,
-                                             long long* g, const DevParams& P, long long a, long long b,
-                                             long long wq) {
-  if (a == b) return;
-  const long long lo = a < b ? a : b, hi = a < b ? b : a;
-  const long long sw = (b > a) ? wq : -wq;
-  const int c0 = (int)(lo >> P.F), c1 = (int)((hi - 1) >> P.F);
-  if (c0 == c1) {
-    acc_cell(acc, c_ref, sWin, win_lo, g, P.N, c0, sw * (hi - lo));
-  } else {
-    const long long k = (long long)c1 << P.F;
-    acc_cell(acc, c_ref, sWin, win_lo, g, P.N, c0, sw * (k - lo));
-    acc_cell(acc, c_ref, sWin, win_lo, g, P.N, c1, sw * (hi - k));
-  }
-}
-
-// warp-level segmented reduction of the per-thread registers keyed by c_ref
-// (valid when c_ref is non-decreasing along the lanes: cell-sorted data),
-// then one atomic per segment and cell.
+// warp-level flush of the per-thread registers (cells c_ref-1, c_ref, c_ref+1):
+// lanes with equal c_ref form a group (any order along the warp), the group's
+// lowest lane adds the three exact sums; then the registers are cleared.
 __device__ __forceinline__ void warp_flush(long long (&a)[3], int c_ref, long long* sWin, int win_lo,
                                            long long* g, int N) {
-  const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  const int prev = __shfl_up_sync(full, c_ref, 1);
-  const bool ok = (lane == 0) || (prev <= c_ref);
-  if (__all_sync(full, ok)) {
+  const unsigned grp = __match_any_sync(0xffffffffu, c_ref);
+  const bool leader = lane == __ffs(grp) - 1;
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const int kd = __shfl_up_sync(full, c_ref, d);
-      const long long v0 = __shfl_up_sync(full, a[0], d);
-      const long long v1 = __shfl_up_sync(full, a[1], d);
-      const long long v2 = __shfl_up_sync(full, a[2], d);
-      if (lane >= d && kd == c_ref) { a[0] += v0; a[1] += v1; a[2] += v2; }
-    }
-    const int next = __shfl_down_sync(full, c_ref, 1);
-    if (lane == 31 || next != c_ref) {
-      add_cell(sWin, win_lo, g, N, c_ref - 1, a[0]);
-      add_cell(sWin, win_lo, g, N, c_ref, a[1]);
-      add_cell(sWin, win_lo, g, N, c_ref + 1, a[2]);
-    }
-  } else {
-    add_cell(sWin, win_lo, g, N, c_ref - 1, a[0]);
-    add_cell(sWin, win_lo, g, N, c_ref, a[1]);
-    add_cell(sWin, win_lo, g, N, c_ref + 1, a[2]);
+  for (int j = 0; j < 3; ++j) {
+    const long long sum = group_sum64(grp, a[j]);
+    if (leader) add_cell(sWin, win_lo, g, N, c_ref - 1 + j, sum);
+    a[j] = 0;
   }
-  a[0] = a[1] = a[2] = 0;
 }
 
 // --------------------------------------------------------------------------
@@ -263,23 +238,240 @@ __device__ __forceinline__ void warp_flush(long long (&a)[3], int c_ref, long lo
 // --------------------------------------------------------------------------
 enum { C_SCAT, C_CLAMP, C_LIM, C_NEWT, C_NONFIN, C_LOSTN, C_LOSTS, C_PAIRS, C_DROP, C_REJ, C_WALL, C_DRAW, C_COUNT };
 
+// Per-thread tallies of one push launch (registers).
+struct Tally {
+  unsigned c[C_COUNT];
+  unsigned n_lim, n_newt;
+  float ke, ke_c, kl, kl_c;   // Kahan-compensated FP32 sums of w m (gamma - 1)
+};
+
+__device__ __forceinline__ void kahan(float& s, float& c, float x) {
+  const float y = x - c, t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+// Result of pushing one particle.
+struct PushOut {
+  uint32_t pos;               // new position (clamped inside the line if lost)
+  float u;
+  bool lost, want_pair, want_dens;
+  float child_u;
+  unsigned long long pid;     // id (loaded only if a Philox number was drawn)
+  int cA, cB;                 // cells receiving current, -1 if none
+  long long vA, vB;
+  int cD, vD;                 // cell and weight of the lepton density for the pair cap
+  int cell;                   // cell at the start of the step
+};
+
+// One PIC cycle of one particle (Sec. 3): gather, Strang-split drag, kick,
+// Monte-Carlo RICS, move, and the charge-conserving deposit contributions.
+// Positions are u32 fixed point; every particle alive at the start of a step
+// has pos < top, and a step is shorter than one cell.
 template <bool NMAX>
-__global__ void __launch_bounds__(kBlock) k_push(DevParams P) {
+__device__ __forceinline__ PushOut push_one(const DevParams& P, uint32_t idx, uint32_t pos0, float u, float w,
+                                            int sp, Tally& T) {
+  const uint32_t fmask = (1u << P.F) - 1u;
+  const uint32_t half = 1u << (P.F - 1);
+  PushOut o;
+  o.lost = false; o.want_pair = false; o.want_dens = false; o.child_u = 0.0f; o.pid = 0;
+  o.cA = -1; o.cB = -1; o.vA = 0; o.vB = 0; o.cD = 0; o.vD = 0;
+  const bool ion = (sp == PIC1D_SP_ION);
+  const bool lep = !ion;
+  const float qm = ion ? P.qm[PIC1D_SP_ION] : (sp == PIC1D_SP_POSITRON ? 1.0f : -1.0f);
+  const int qs = (sp == PIC1D_SP_ELECTRON || sp == PIC1D_SP_ATMO) ? -1 : 1;
+  const float mass = ion ? P.mass[PIC1D_SP_ION] : 1.0f;
+  const int cell = (int)(pos0 >> P.F);
+  o.cell = cell;
+  // 1. gather E linearly between cell centres (constant beyond the end centres)
+  float Ep;
+  {
+    const uint32_t x = pos0 < half ? 0u : pos0 - half;
+    int ig = (int)(x >> P.F);
+    float f = (float)(x & fmask) * P.inv2F;
+    if (ig > P.N - 2) { ig = P.N - 2; f = 1.0f; }
+    const float e0 = __ldg(P.E32 + ig), e1 = __ldg(P.E32 + ig + 1);
+    Ep = fmaf(f, e1 - e0, e0);
+  }
+  const bool zone = __ldg(P.zone + cell) != 0;
+  const bool cont = lep && P.drag_law != PIC1D_DRAG_OFF && (P.rics_mode == PIC1D_RICS_DRAG_PLUS_PAIRS || !zone);
+  const bool mc = lep && P.mc_on && P.drag_law != PIC1D_DRAG_OFF && zone;
+  Site S;
+  if (cont || mc) {
+    const float f = (float)(pos0 & fmask) * P.inv2F;
+    const float b0 = __ldg(P.nb + cell), b1 = __ldg(P.nb + cell + 1);
+    const float m0 = __ldg(P.nmu + cell), m1 = __ldg(P.nmu + cell + 1);
+    S.b = fmaf(f, b1 - b0, b0);
+    S.mu = fmaf(f, m1 - m0, m0);
+    if (P.drag_law == PIC1D_DRAG_CLOSED) {
+      const float x0 = __ldg(P.nx + cell), x1 = __ldg(P.nx + cell + 1);
+      S.x = fmaf(f, x1 - x0, x0);
+    } else {
+      S.x = 1.0f;
+    }
+    S.v = fminf((float)pos0 * P.v_scale, (float)(P.Ns - 1));
+  }
+  // 2-4. Strang split: drag dt/2, Lorentz kick dt, drag dt/2
+  if (cont) u = drag_half(P, S, u, T.n_lim, T.n_newt);
+  u = fmaf(qm * Ep, P.dt, u);
+  if (cont) u = drag_half(P, S, u, T.n_lim, T.n_newt);
+  // 5. Monte-Carlo RICS in the pair zone
+  bool make_pair = false;
+  float Pg = 0.0f;
+  if (mc) {
+    const DragVal dv = drag_eval(P, u, S, false);
+    float psc = P.drag_k * expf(dv.lnN) * P.dt;
+    if (psc > 1.0f) { psc = 1.0f; ++T.c[C_CLAMP]; }
+    if (psc > 0.0f) {
+      ++T.c[C_DRAW];
+      o.pid = P.id[idx];
+      const uint4 r = philox4x32_10(
+          make_uint4((uint32_t)o.pid, (uint32_t)(o.pid >> 32), (uint32_t)P.step, kTagRics), P.key0, P.key1);
+      if (unit24(r.x) < psc) {
+        ++T.c[C_SCAT];
+        const float beta = u * rsqrtf(fmaf(u, u, 1.0f));
+        const float d = (S.mu > beta) ? 1.0f : -1.0f;
+        const float ct = dipole_cos(unit24(r.y));
+        float uf, Eg;
+        rics_event(S.b, d, u, ct, uf, Eg, Pg);
+        if (P.rics_mode == PIC1D_RICS_SPLIT) u = uf;
+        if (P.pairs_on && Eg >= P.pair_e_thr) make_pair = true;
+      }
+    }
+  }
+  // 6. move: ds = dt u / gamma, rounded to the fixed-point quantum
+  const int wint = __float2int_rn(w * 4096.0f);
+  const int sw0 = qs * wint;
+  if (!isfinite(u)) {
+    // removed in place: no current, counted (the step reports PIC1D_ENUMERIC)
+    ++T.c[C_NONFIN];
+    o.u = 0.0f;
+    o.pos = pos0;
+    o.lost = true;
+    return o;
+  }
+  const float q = fmaf(u, u, 1.0f);
+  const float r = rsqrtf(q);                                   // 1 / gamma
+  const int dfix = __float2int_rn(P.dt * (u * r) * (float)(1u << P.F));
+  const float e = w * mass * __fdividef(u * u * r, 1.0f + r);  // w m (gamma - 1)
+  const bool lostN = dfix < 0 && (uint32_t)(-dfix) > pos0;
+  const bool lostS = dfix > 0 && (uint32_t)dfix > P.top1 - pos0;
+  o.lost = lostN || lostS;
+  kahan(T.ke, T.ke_c, o.lost ? 0.0f : e);
+  kahan(T.kl, T.kl_c, o.lost ? e : 0.0f);
+  // 7. charge-conserving deposit: signed length of the path inside each cell
+  uint32_t p1;
+  if (!o.lost) {
+    p1 = pos0 + (uint32_t)dfix;
+    if (dfix != 0) {
+      const uint32_t lo = dfix > 0 ? pos0 : p1, hi = dfix > 0 ? p1 : pos0;
+      const int sw = dfix > 0 ? sw0 : -sw0;
+      const int c0 = (int)(lo >> P.F), c1 = (int)((hi - 1u) >> P.F);
+      const uint32_t kk = (uint32_t)c1 << P.F;
+      o.cA = c0;
+      if (c0 == c1) {
+        o.vA = (long long)sw * (int)(hi - lo);
+      } else {
+        o.vA = (long long)sw * (int)(kk - lo);
+        o.cB = c1;
+        o.vB = (long long)sw * (int)(hi - kk);
+      }
+    }
+    o.pos = p1;
+    if (NMAX && lep) {
+      o.cD = (int)(p1 >> P.F);
+      o.vD = wint;
+      o.want_dens = __ldg(P.dens_flag + o.cD) != 0;
+    }
+  } else {
+    // leaves through a wall: the path is clamped at the conductor (64-bit: the
+    // southern wall sits at top, which may be 2^32)
+    ++T.c[lostN ? C_LOSTN : C_LOSTS];
+    const long long a = (long long)pos0, b = lostN ? 0ll : P.top;
+    const long long lo = a < b ? a : b, hi = a < b ? b : a;
+    const int sw = b > a ? sw0 : -sw0;
+    if (hi > lo) {
+      const int c0 = (int)(lo >> P.F), c1 = (int)((hi - 1) >> P.F);
+      const long long kk = (long long)c1 << P.F;
+      o.cA = c0;
+      if (c0 == c1) {
+        o.vA = (long long)sw * (int)(hi - lo);
+      } else {
+        o.vA = (long long)sw * (int)(kk - lo);
+        o.cB = c1;
+        o.vB = (long long)sw * (int)(hi - kk);
+      }
+    }
+    o.pos = lostN ? 0u : (uint32_t)(P.top - 1);
+    if (make_pair) ++T.c[C_WALL];     // the parent left the line: no pair
+    make_pair = false;
+  }
+  o.u = u;
+  if (make_pair) {
+    if (NMAX && P.dens_cur[(int)(o.pos >> P.F)] >= P.nmax_int) {
+      ++T.c[C_REJ];
+    } else {
+      o.want_pair = true;
+      o.child_u = 0.5f * Pg;
+    }
+  }
+  return o;
+}
+
+// warp-aggregated add of (cell, v) contributions from the lanes in `mask`
+__device__ __forceinline__ void warp_add_cells(unsigned mask, bool mine, int cell, long long v, long long* sWin,
+                                               int win_lo, long long* g, int N) {
+  if (mine) {
+    const unsigned grp = __match_any_sync(mask, cell);
+    const long long sum = group_sum64(grp, v);
+    if ((threadIdx.x & 31) == __ffs(grp) - 1) add_cell(sWin, win_lo, g, N, cell, sum);
+  }
+}
+
+template <int PPT> struct Vec;
+template <> struct Vec<1> { using U = uint32_t; using F = float; using B = uint8_t; };
+template <> struct Vec<2> { using U = uint2; using F = float2; using B = uchar2; };
+
+__device__ __forceinline__ void unpack_u(uint32_t v, uint32_t (&a)[1]) { a[0] = v; }
+__device__ __forceinline__ void unpack_u(uint2 v, uint32_t (&a)[2]) { a[0] = v.x; a[1] = v.y; }
+__device__ __forceinline__ void unpack_f(float v, float (&a)[1]) { a[0] = v; }
+__device__ __forceinline__ void unpack_f(float2 v, float (&a)[2]) { a[0] = v.x; a[1] = v.y; }
+__device__ __forceinline__ void unpack_b(uint8_t v, uint8_t (&a)[1]) { a[0] = v; }
+__device__ __forceinline__ void unpack_b(uchar2 v, uint8_t (&a)[2]) { a[0] = v.x; a[1] = v.y; }
+__device__ __forceinline__ uint32_t pack_u(const uint32_t (&a)[1]) { return a[0]; }
+__device__ __forceinline__ uint2 pack_u(const uint32_t (&a)[2]) { return make_uint2(a[0], a[1]); }
+__device__ __forceinline__ float pack_f(const float (&a)[1]) { return a[0]; }
+__device__ __forceinline__ float2 pack_f(const float (&a)[2]) { return make_float2(a[0], a[1]); }
+
+// The push kernel.  A thread owns PPT consecutive particles per tile (one
+// PPT-wide access per SoA array), a block owns a contiguous range of tiles of
+// kBlock * PPT particles, so that the cell-sorted particles of a block fall
+// into a narrow window of cells.  The current registers of a thread (cells
+// c_ref-1 .. c_ref+1) persist across its particles and are flushed warp-wide
+// (exact group sums) only when some lane needs a cell outside its anchor
+// range; block sums go through a shared-memory cell window flushed to global
+// memory once per block.  Slot indices are 32-bit (capacity < 2^31).
+template <int PPT, int MINB, bool NMAX>
+__global__ void __launch_bounds__(kBlock, MINB) k_push(DevParams P) {
+  using VU = typename Vec<PPT>::U;
+  using VF = typename Vec<PPT>::F;
+  using VB = typename Vec<PPT>::B;
+  constexpr int TILE = kBlock * PPT;
   __shared__ long long sJ[kWindow];
   __shared__ long long sD[NMAX ? kWindow : 1];
   __shared__ unsigned sCtr[C_COUNT];
   __shared__ double sRed[2][kBlock / 32];
 
-  const long long n = P.st->n_slots;
+  const uint32_t n = (uint32_t)P.st->n_slots;
   const int lane = threadIdx.x & 31;
-  const long long ntiles = (n + kTile - 1) / kTile;
-  const long long tpb = (ntiles + gridDim.x - 1) / gridDim.x;
-  const long long t0 = (long long)blockIdx.x * tpb;
-  const long long t1 = min(ntiles, t0 + tpb);
+  const uint32_t ntiles = (n + TILE - 1) / TILE;
+  const uint32_t tpb = (ntiles + gridDim.x - 1) / gridDim.x;
+  const uint32_t t0 = blockIdx.x * tpb;
+  const uint32_t t1 = min(ntiles, t0 + tpb);
 
   int win_lo = 0;
   if (t0 < t1) {
-    const int c = (int)(P.pos[t0 * kTile] >> P.F);
+    const int c = (int)(P.pos[(size_t)t0 * TILE] >> P.F);
     win_lo = max(0, min(c, P.N - 1) - kWindow / 8);
   }
   for (int i = threadIdx.x; i < kWindow; i += kBlock) {
@@ -289,208 +481,126 @@ __global__ void __launch_bounds__(kBlock) k_push(DevParams P) {
   if (threadIdx.x < C_COUNT) sCtr[threadIdx.x] = 0;
   __syncthreads();
 
-  unsigned cnt[C_COUNT];
+  Tally T;
 #pragma unroll
-  for (int k = 0; k < C_COUNT; ++k) cnt[k] = 0;
-  unsigned n_lim = 0, n_newt = 0;     // scalars: references into cnt[] would force it to local memory
-  // Kahan-compensated FP32 sums (FP64 adds per particle would cost a
-  // noticeable share of the step on this part's FP64 rate)
-  float ke = 0.0f, ke_c = 0.0f, kl = 0.0f, kl_c = 0.0f;
-  const float two_F = (float)(1u << P.F);
-  const unsigned long long fmask = (1ull << P.F) - 1ull;
+  for (int k = 0; k < C_COUNT; ++k) T.c[k] = 0;
+  T.n_lim = T.n_newt = 0;
+  T.ke = T.ke_c = T.kl = T.kl_c = 0.0f;
+  long long aJ[3] = {0, 0, 0};
+  int c_ref = -4;
 
-  for (long long t = t0; t < t1; ++t) {
-    const long long base = t * kTile + (long long)threadIdx.x * kPerThread;
-    uint4 p4 = *reinterpret_cast<const uint4*>(P.pos + base);
-    float4 u4 = *reinterpret_cast<const float4*>(P.u + base);
-    const float4 w4 = *reinterpret_cast<const float4*>(P.w + base);
-    const uchar4 s4 = *reinterpret_cast<const uchar4*>(P.sp + base);
-    uint32_t pp[4] = {p4.x, p4.y, p4.z, p4.w};
-    float uu[4] = {u4.x, u4.y, u4.z, u4.w};
-    const float ww[4] = {w4.x, w4.y, w4.z, w4.w};
-    uint8_t ss[4] = {s4.x, s4.y, s4.z, s4.w};
-    const int c_ref = min((int)(pp[0] >> P.F), P.N - 1);
-    long long aJ[3] = {0, 0, 0};
-    long long aD[3] = {0, 0, 0};
+  // software pipeline: the next tile's loads are in flight while this one is computed
+  VU npos{};
+  VF nu{}, nw{};
+  VB nsp{};
+  if (t0 < t1) {
+    const uint32_t b0 = t0 * TILE + threadIdx.x * PPT;
+    npos = __ldcs(reinterpret_cast<const VU*>(P.pos + b0));
+    nu = __ldcs(reinterpret_cast<const VF*>(P.u + b0));
+    nw = __ldcs(reinterpret_cast<const VF*>(P.w + b0));
+    nsp = *reinterpret_cast<const VB*>(P.sp + b0);
+  }
+
+  for (uint32_t t = t0; t < t1; ++t) {
+    const uint32_t base = t * TILE + threadIdx.x * PPT;
+    uint32_t pp[PPT];
+    float uu[PPT], ww[PPT];
+    uint8_t ss[PPT];
+    unpack_u(npos, pp);
+    unpack_f(nu, uu);
+    unpack_f(nw, ww);
+    unpack_b(nsp, ss);
+    if (t + 1 < t1) {
+      const uint32_t b1 = base + TILE;
+      npos = __ldcs(reinterpret_cast<const VU*>(P.pos + b1));
+      nu = __ldcs(reinterpret_cast<const VF*>(P.u + b1));
+      nw = __ldcs(reinterpret_cast<const VF*>(P.w + b1));
+      nsp = *reinterpret_cast<const VB*>(P.sp + b1);
+    }
     bool dirty = false;
-
 #pragma unroll
-    for (int k = 0; k < kPerThread; ++k) {
-      const long long idx = base + k;
+    for (int k = 0; k < PPT; ++k) {
+      const uint32_t idx = base + k;
       const bool valid = (idx < n) && (ss[k] != PIC1D_SP_DEAD);
-      bool want_pair = false;
-      float child_u = 0.0f;
-      long long p1 = 0;
-      unsigned long long pid = 0;
+      PushOut o;
+      o.cA = o.cB = -1;
+      o.want_pair = false;
+      o.want_dens = false;
       if (valid) {
-        const int sp = ss[k] & 3;
-        const uint32_t pos0 = pp[k];
-        float u = uu[k];
-        const float w = ww[k];
-        const bool lep = (sp != PIC1D_SP_ION);
-        const int cell = min((int)(pos0 >> P.F), P.N - 1);
-        // 1. gather E linearly between cell centres
-        float Ep;
-        {
-          const long long xg = (long long)pos0 - (1ll << (P.F - 1));
-          const int ig = (int)(xg >> P.F);
-          if (ig < 0) Ep = __ldg(P.E32);
-          else if (ig >= P.N - 1) Ep = __ldg(P.E32 + P.N - 1);
-          else {
-            const float f = (float)((unsigned long long)xg & fmask) * P.inv2F;
-            const float e0 = __ldg(P.E32 + ig), e1 = __ldg(P.E32 + ig + 1);
-            Ep = fmaf(f, e1 - e0, e0);
-          }
-        }
-        const bool zone = __ldg(P.zone + cell) != 0;
-        const bool cont = lep && P.drag_law != PIC1D_DRAG_OFF && (P.rics_mode == PIC1D_RICS_DRAG_PLUS_PAIRS || !zone);
-        const bool mc = lep && P.mc_on && P.drag_law != PIC1D_DRAG_OFF && zone;
-        Site S;
-        if (cont || mc) {
-          const float f = (float)(pos0 & (uint32_t)fmask) * P.inv2F;
-          const int cn = cell;
-          const float b0 = __ldg(P.nb + cn), b1 = __ldg(P.nb + cn + 1);
-          const float m0 = __ldg(P.nmu + cn), m1 = __ldg(P.nmu + cn + 1);
-          S.b = fmaf(f, b1 - b0, b0);
-          S.mu = fmaf(f, m1 - m0, m0);
-          if (P.drag_law == PIC1D_DRAG_CLOSED) {
-            const float x0 = __ldg(P.nx + cn), x1 = __ldg(P.nx + cn + 1);
-            S.x = fmaf(f, x1 - x0, x0);
-          } else {
-            S.x = 1.0f;
-          }
-          S.v = fminf((float)pos0 * P.v_scale, (float)(P.Ns - 1));
-        }
-        // 2-4. Strang split: drag dt/2, Lorentz kick dt, drag dt/2
-        if (cont) u = drag_half(P, S, u, n_lim, n_newt);
-        u = fmaf(P.qm[sp] * Ep, P.dt, u);
-        if (cont) u = drag_half(P, S, u, n_lim, n_newt);
-        // 5. Monte-Carlo RICS in the pair zone
-        bool make_pair = false;
-        float Pg = 0.0f;
-        if (mc) {
-          const DragVal dv = drag_eval(P, u, S, false);
-          float psc = P.drag_k * expf(dv.lnN) * P.dt;
-          if (psc > 1.0f) { psc = 1.0f; ++cnt[C_CLAMP]; }
-          if (psc > 0.0f) {
-            ++cnt[C_DRAW];
-            pid = P.id[idx];
-            const uint4 r = philox4x32_10(
-                make_uint4((uint32_t)pid, (uint32_t)(pid >> 32), (uint32_t)P.step, kTagRics), P.key0, P.key1);
-            if (unit24(r.x) < psc) {
-              ++cnt[C_SCAT];
-              const float gam = sqrtf(fmaf(u, u, 1.0f));
-              const float d = (S.mu > u / gam) ? 1.0f : -1.0f;
-              const float ct = dipole_cos(unit24(r.y));
-              float uf, Eg;
-              rics_event(S.b, d, u, ct, uf, Eg, Pg);
-              if (P.rics_mode == PIC1D_RICS_SPLIT) u = uf;
-              if (P.pairs_on && Eg >= P.pair_e_thr) make_pair = true;
-            }
-          }
-        }
-        // 6. move
-        bool lost;
-        if (!isfinite(u)) {
-          ++cnt[C_NONFIN];
-          u = 0.0f;
-          p1 = (long long)pos0;
-          lost = true;
-          make_pair = false;
-        } else {
-          const float gam = sqrtf(fmaf(u, u, 1.0f));
-          const float ds = P.dt * (u / gam);
-          p1 = (long long)pos0 + __float2ll_rn(ds * two_F);
-          lost = (p1 < 0) || (p1 >= P.top);
-          const float gm1 = (u * u) / (gam + 1.0f);
-          const float e = w * P.mass[sp] * gm1;
-          if (lost) {
-            const float y = e - kl_c, t = kl + y;
-            kl_c = (t - kl) - y;
-            kl = t;
-            if (p1 < 0) ++cnt[C_LOSTN]; else ++cnt[C_LOSTS];
-          } else {
-            const float y = e - ke_c, t = ke + y;
-            ke_c = (t - ke) - y;
-            ke = t;
-          }
-        }
-        // 7. charge-conserving deposit along the path, clamped at the walls
-        const long long pc = p1 < 0 ? 0 : (p1 > P.top ? P.top : p1);
-        const long long wint = __float2ll_rn(w * 4096.0f);
-        deposit_path(aJ, c_ref, sJ, win_lo, P.J, P, (long long)pos0, pc, (long long)P.qs[sp] * wint);
-        if (NMAX && lep && !lost) acc_cell(aD, c_ref, sD, win_lo, P.dens_next, P.N, (int)(p1 >> P.F), wint);
-        pp[k] = lost ? (uint32_t)min(pc, P.top - 1) : (uint32_t)p1;
-        uu[k] = u;
-        if (lost) { ss[k] = PIC1D_SP_DEAD; dirty = true; }
-        if (make_pair) {
-          if (lost) {
-            ++cnt[C_WALL];
-          } else if (NMAX && P.dens_cur[(int)(p1 >> P.F)] >= P.nmax_int) {
-            ++cnt[C_REJ];
-          } else {
-            want_pair = true;
-            child_u = 0.5f * Pg;
-          }
-        }
+        o = push_one<NMAX>(P, idx, pp[k], uu[k], ww[k], ss[k] & 3, T);
+        pp[k] = o.pos;
+        uu[k] = o.u;
+        if (o.lost) { ss[k] = PIC1D_SP_DEAD; dirty = true; }
       }
-      // pair append, warp-aggregated (uniform control flow)
-      const unsigned m = __ballot_sync(0xffffffffu, want_pair);
+      // current into the thread's registers; flush warp-wide first if some
+      // lane needs cells outside its anchor range
+      const bool out = valid && ((o.cA >= 0 && abs(o.cA - c_ref) > 1) || (o.cB >= 0 && abs(o.cB - c_ref) > 1));
+      if (__any_sync(0xffffffffu, out)) {
+        warp_flush(aJ, c_ref, sJ, win_lo, P.J, P.N);
+        if (valid) c_ref = o.cell;
+      }
+      if (o.cA >= 0) { const int d = o.cA - c_ref; if (d < 0) aJ[0] += o.vA; else if (d == 0) aJ[1] += o.vA; else aJ[2] += o.vA; }
+      if (o.cB >= 0) { const int d = o.cB - c_ref; if (d < 0) aJ[0] += o.vB; else if (d == 0) aJ[1] += o.vB; else aJ[2] += o.vB; }
+      // lepton density for the pair cap: only cells where a pair can be tested
+      if (NMAX) {
+        const unsigned md = __ballot_sync(0xffffffffu, o.want_dens);
+        if (md) warp_add_cells(md, o.want_dens, o.cD, (long long)o.vD, sD, win_lo, P.dens_next, P.N);
+      }
+      // pair append, warp-aggregated
+      const unsigned m = __ballot_sync(0xffffffffu, o.want_pair);
       if (m) {
         const int leader = __ffs(m) - 1;
         long long slot0 = 0;
         if (lane == leader) slot0 = atomicAdd(reinterpret_cast<unsigned long long*>(&P.st->append),
                                               (unsigned long long)(2 * __popc(m)));
         slot0 = __shfl_sync(0xffffffffu, slot0, leader);
-        if (want_pair) {
-          const long long dst = n + slot0 + 2ll * __popc(m & lanemask_lt());
+        if (o.want_pair) {
+          const long long dst = (long long)n + slot0 + 2ll * __popc(m & lanemask_lt());
           if (dst + 2 > P.cap) {
-            ++cnt[C_DROP];
+            ++T.c[C_DROP];
           } else {
-            ++cnt[C_PAIRS];
-            const uint32_t cpos = (uint32_t)p1;
+            ++T.c[C_PAIRS];
 #pragma unroll
             for (int mm = 0; mm < 2; ++mm) {
-              P.pos[dst + mm] = cpos;
-              P.u[dst + mm] = child_u;
+              P.pos[dst + mm] = o.pos;
+              P.u[dst + mm] = o.child_u;
               P.w[dst + mm] = ww[k];
               P.sp[dst + mm] = (mm == 0) ? PIC1D_SP_ELECTRON : PIC1D_SP_POSITRON;
-              P.id[dst + mm] = pair_child_id(pid, P.step, mm);
+              P.id[dst + mm] = pair_child_id(o.pid, P.step, mm);
             }
-            if (NMAX)
-              atomicAdd(reinterpret_cast<unsigned long long*>(P.dens_next + (int)(p1 >> P.F)),
-                        (unsigned long long)(2ll * __float2ll_rn(ww[k] * 4096.0f)));
+            if (NMAX && __ldg(P.dens_flag + (o.pos >> P.F)))
+              atomicAdd(reinterpret_cast<unsigned long long*>(P.dens_next + (int)(o.pos >> P.F)),
+                        (unsigned long long)(2ll * __float2int_rn(ww[k] * 4096.0f)));
           }
         }
       }
     }
-    // write back
-    if (base + kPerThread <= n) {
-      *reinterpret_cast<uint4*>(P.pos + base) = make_uint4(pp[0], pp[1], pp[2], pp[3]);
-      *reinterpret_cast<float4*>(P.u + base) = make_float4(uu[0], uu[1], uu[2], uu[3]);
+    // write back (streaming stores: the data is not re-read in this kernel)
+    if (base + PPT <= n) {
+      __stcs(reinterpret_cast<VU*>(P.pos + base), pack_u(pp));
+      __stcs(reinterpret_cast<VF*>(P.u + base), pack_f(uu));
     } else {
 #pragma unroll
-      for (int k = 0; k < kPerThread; ++k)
+      for (int k = 0; k < PPT; ++k)
         if (base + k < n) { P.pos[base + k] = pp[k]; P.u[base + k] = uu[k]; }
     }
     if (dirty) {
 #pragma unroll
-      for (int k = 0; k < kPerThread; ++k)
+      for (int k = 0; k < PPT; ++k)
         if (base + k < n && ss[k] == PIC1D_SP_DEAD) P.sp[base + k] = PIC1D_SP_DEAD;
     }
-    warp_flush(aJ, c_ref, sJ, win_lo, P.J, P.N);
-    if (NMAX) warp_flush(aD, c_ref, sD, win_lo, P.dens_next, P.N);
   }
+  warp_flush(aJ, c_ref, sJ, win_lo, P.J, P.N);
 
   // counters and energy totals of the block
-  cnt[C_LIM] = n_lim;
-  cnt[C_NEWT] = n_newt;
+  T.c[C_LIM] = T.n_lim;
+  T.c[C_NEWT] = T.n_newt;
 #pragma unroll
   for (int k = 0; k < C_COUNT; ++k) {
-    const unsigned v = __reduce_add_sync(0xffffffffu, cnt[k]);
+    const unsigned v = __reduce_add_sync(0xffffffffu, T.c[k]);
     if (lane == 0 && v) atomicAdd(&sCtr[k], v);
   }
-  double ked = (double)ke - (double)ke_c, kld = (double)kl - (double)kl_c;
+  double ked = (double)T.ke - (double)T.ke_c, kld = (double)T.kl - (double)T.kl_c;
   for (int d = 16; d > 0; d >>= 1) {
     ked += __shfl_down_sync(0xffffffffu, ked, d);
     kld += __shfl_down_sync(0xffffffffu, kld, d);
@@ -499,10 +609,10 @@ __global__ void __launch_bounds__(kBlock) k_push(DevParams P) {
   __syncthreads();
   // flush the window
   for (int i = threadIdx.x; i < kWindow; i += kBlock) {
-    const int cell = win_lo + i;
-    if (cell < P.N) {
-      if (sJ[i]) atomicAdd(reinterpret_cast<unsigned long long*>(P.J + cell), (unsigned long long)sJ[i]);
-      if (NMAX && sD[i]) atomicAdd(reinterpret_cast<unsigned long long*>(P.dens_next + cell), (unsigned long long)sD[i]);
+    const int c = win_lo + i;
+    if (c < P.N) {
+      if (sJ[i]) atomicAdd(reinterpret_cast<unsigned long long*>(P.J + c), (unsigned long long)sJ[i]);
+      if (NMAX && sD[i]) atomicAdd(reinterpret_cast<unsigned long long*>(P.dens_next + c), (unsigned long long)sD[i]);
     }
   }
   if (threadIdx.x == 0) {
@@ -630,8 +740,19 @@ __global__ void k_finalize(DevParams P, const double* fpart, int nfb, int npb, d
 }
 
 // --------------------------------------------------------------------------
-// cell sort: histogram, exclusive scan, scatter (removed slots dropped)
+// cell sort: histogram, exclusive scan, scatter (removed slots dropped).
+// Key = 2 * cell + (ion ? 1 : 0): cells in order, leptons before ions in a
+// cell, so that a warp of the push mostly follows one species' code path.
 // --------------------------------------------------------------------------
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanChunk = kScanThreads * kScanItems;
+
+__device__ __forceinline__ int sort_key(const DevParams& P, uint32_t pos, uint8_t sp) {
+  const int cell = min((int)(pos >> P.F), P.N - 1);
+  return 2 * cell + (sp == PIC1D_SP_ION ? 1 : 0);
+}
+
 __global__ void __launch_bounds__(256) k_hist(DevParams P, uint32_t* counts) {
   const long long n = P.st->n_slots;
   const unsigned full = 0xffffffffu;
@@ -639,37 +760,91 @@ __global__ void __launch_bounds__(256) k_hist(DevParams P, uint32_t* counts) {
   for (long long i0 = (long long)blockIdx.x * blockDim.x; i0 < n; i0 += (long long)gridDim.x * blockDim.x) {
     const long long i = i0 + threadIdx.x;
     bool valid = i < n;
-    int cell = 0;
+    int key = 0;
     if (valid) {
-      valid = P.sp[i] != PIC1D_SP_DEAD;
-      cell = min((int)(P.pos[i] >> P.F), P.N - 1);
+      const uint8_t sp = P.sp[i];
+      valid = sp != PIC1D_SP_DEAD;
+      key = sort_key(P, P.pos[i], sp);
     }
     const unsigned vm = __ballot_sync(full, valid);
     if (valid) {
-      const unsigned grp = __match_any_sync(vm, cell);
-      if (lane == __ffs(grp) - 1) atomicAdd(counts + cell, (unsigned)__popc(grp));
+      const unsigned grp = __match_any_sync(vm, key);
+      if (lane == __ffs(grp) - 1) atomicAdd(counts + key, (unsigned)__popc(grp));
     }
   }
 }
 
-__global__ void __launch_bounds__(1024) k_scan(DevParams P, const uint32_t* counts, long long* offsets) {
-  __shared__ long long part[1024];
-  const int N = P.N;
-  const int per = (N + 1023) / 1024;
-  const int lo = threadIdx.x * per, hi = min(N, lo + per);
-  long long s = 0;
-  for (int c = lo; c < hi; ++c) s += counts[c];
-  part[threadIdx.x] = s;
-  __syncthreads();
-  for (int d = 1; d < 1024; d <<= 1) {
-    long long v = (threadIdx.x >= (unsigned)d) ? part[threadIdx.x - d] : 0;
-    __syncthreads();
-    part[threadIdx.x] += v;
-    __syncthreads();
+// exclusive scan of the block's values (one per thread) in a 1024-thread block
+__device__ __forceinline__ long long block_exclusive_scan(long long v, long long* warp_tot, long long& total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  long long x = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const long long y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
   }
-  long long run = part[threadIdx.x] - s;
-  for (int c = lo; c < hi; ++c) { offsets[c] = run; run += counts[c]; }
-  if (threadIdx.x == 1023) { offsets[N] = part[1023]; P.st->sorted_total = part[1023]; }
+  if (lane == 31) warp_tot[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    long long t = warp_tot[lane];
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const long long y = __shfl_up_sync(0xffffffffu, t, d);
+      if (lane >= d) t += y;
+    }
+    warp_tot[lane] = t;            // inclusive scan of the warp totals
+  }
+  __syncthreads();
+  total = warp_tot[31];
+  const long long before = wid ? warp_tot[wid - 1] : 0;
+  __syncthreads();
+  return before + x - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* counts, int B, long long* bsum) {
+  __shared__ long long wt[32];
+  const long long base = (long long)blockIdx.x * kScanChunk + (long long)threadIdx.x * kScanItems;
+  long long s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k)
+    if (base + k < B) s += counts[base + k];
+  long long total;
+  block_exclusive_scan(s, wt, total);
+  if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_top(long long* bsum, int nb, DevParams P) {
+  __shared__ long long wt[32];
+  long long carry = 0;
+  for (int b0 = 0; b0 < nb; b0 += kScanThreads) {
+    const int i = b0 + threadIdx.x;
+    const long long v = i < nb ? bsum[i] : 0;
+    long long total;
+    const long long ex = block_exclusive_scan(v, wt, total);
+    if (i < nb) bsum[i] = carry + ex;
+    carry += total;
+  }
+  if (threadIdx.x == 0) P.st->sorted_total = carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t* counts, int B, const long long* bsum,
+                                                              long long* offsets) {
+  __shared__ long long wt[32];
+  const long long base = (long long)blockIdx.x * kScanChunk + (long long)threadIdx.x * kScanItems;
+  uint32_t c[kScanItems];
+  long long s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    c[k] = (base + k < B) ? counts[base + k] : 0u;
+    s += c[k];
+  }
+  long long total;
+  long long run = bsum[blockIdx.x] + block_exclusive_scan(s, wt, total);
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    if (base + k < B) offsets[base + k] = run;
+    run += c[k];
+  }
 }
 
 __global__ void __launch_bounds__(256) k_scatter(DevParams P, long long* cursor, uint32_t* pos2, float* u2,
@@ -682,20 +857,20 @@ __global__ void __launch_bounds__(256) k_scatter(DevParams P, long long* cursor,
     bool valid = i < n;
     uint32_t pos = 0;
     uint8_t sp = 0;
-    int cell = 0;
+    int key = 0;
     if (valid) {
       sp = P.sp[i];
       pos = P.pos[i];
       valid = sp != PIC1D_SP_DEAD;
-      cell = min((int)(pos >> P.F), P.N - 1);
+      key = sort_key(P, pos, sp);
     }
     const unsigned vm = __ballot_sync(full, valid);
     if (valid) {
-      const unsigned grp = __match_any_sync(vm, cell);
+      const unsigned grp = __match_any_sync(vm, key);
       const int leader = __ffs(grp) - 1;
       long long b = 0;
       if (lane == leader)
-        b = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(cursor + cell), (unsigned long long)__popc(grp));
+        b = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(cursor + key), (unsigned long long)__popc(grp));
       b = __shfl_sync(grp, b, leader);
       const long long dst = b + __popc(grp & lanemask_lt());
       pos2[dst] = pos;
@@ -710,6 +885,18 @@ __global__ void __launch_bounds__(256) k_scatter(DevParams P, long long* cursor,
 __global__ void k_sort_done(DevParams P) {
   P.st->n_slots = P.st->sorted_total;
   P.st->append = 0;
+}
+
+// device copy of the table with neighbouring s-rows paired (see table_eval)
+__global__ void k_pair_table(const float2* t, int Ng, int Ns, float4* out) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= 2 * (Ns - 1) * Ng) return;
+  const int i = idx % Ng;
+  const int j = (idx / Ng) % (Ns - 1);
+  const int sg = idx / (Ng * (Ns - 1));
+  const float2 a = t[((size_t)sg * Ns + j) * Ng + i];
+  const float2 b = t[((size_t)sg * Ns + j + 1) * Ng + i];
+  out[idx] = make_float4(a.x, a.y, b.x, b.y);
 }
 
 // --------------------------------------------------------------------------
@@ -811,16 +998,32 @@ __global__ void k_count_species(DevParams P, unsigned long long* out4) {
 // --------------------------------------------------------------------------
 // launchers
 // --------------------------------------------------------------------------
-int push_blocks_per_sm() {
+// push variants: particles per thread x minimum resident blocks per SM
+struct PushVariant {
+  int ppt, minb;
+  const void* k_plain;
+  const void* k_nmax;
+};
+#define PV(PPT_, MINB_) {PPT_, MINB_, (const void*)k_push<PPT_, MINB_, false>, (const void*)k_push<PPT_, MINB_, true>}
+static const PushVariant kPushVariants[] = {PV(1, 4), PV(1, 3), PV(2, 3), PV(2, 4)};
+#undef PV
+constexpr int kNumPushVariants = sizeof(kPushVariants) / sizeof(kPushVariants[0]);
+
+int push_variant_count() { return kNumPushVariants; }
+int push_variant_ppt(int v) { return kPushVariants[v].ppt; }
+int push_variant_minb(int v) { return kPushVariants[v].minb; }
+
+int push_blocks_per_sm(int v, bool nmax) {
   int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_push<false>, kBlock, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, nmax ? kPushVariants[v].k_nmax : kPushVariants[v].k_plain,
+                                                kBlock, 0);
   return nb > 0 ? nb : 1;
 }
 
-cudaError_t launch_push(const DevParams& P, int grid, cudaStream_t s) {
-  if (P.use_nmax) k_push<true><<<grid, kBlock, 0, s>>>(P);
-  else k_push<false><<<grid, kBlock, 0, s>>>(P);
-  return cudaGetLastError();
+cudaError_t launch_push(const DevParams& P, int variant, int grid, cudaStream_t s) {
+  const PushVariant& V = kPushVariants[variant];
+  void* args[] = {const_cast<DevParams*>(&P)};
+  return cudaLaunchKernel(P.use_nmax ? V.k_nmax : V.k_plain, dim3(grid), dim3(kBlock), args, 0, s);
 }
 
 cudaError_t launch_inject(const DevParams& P, double carriers, float sig_e, float sig_i, cudaStream_t s) {
@@ -837,13 +1040,25 @@ cudaError_t launch_field(const DevParams& P, double* E64, float* E32, double a, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_sort(const DevParams& P, uint32_t* counts, long long* offsets, uint32_t* pos2, float* u2,
-                        float* w2, uint8_t* sp2, uint64_t* id2, int grid, cudaStream_t s) {
-  cudaMemsetAsync(counts, 0, sizeof(uint32_t) * (size_t)P.N, s);
+int sort_bins(int N) { return 2 * N; }
+int scan_blocks(int N) { return (sort_bins(N) + kScanChunk - 1) / kScanChunk; }
+
+cudaError_t launch_sort(const DevParams& P, uint32_t* counts, long long* offsets, long long* bsum, uint32_t* pos2,
+                        float* u2, float* w2, uint8_t* sp2, uint64_t* id2, int grid, cudaStream_t s) {
+  const int B = sort_bins(P.N), nb = scan_blocks(P.N);
+  cudaMemsetAsync(counts, 0, sizeof(uint32_t) * (size_t)B, s);
   k_hist<<<grid, 256, 0, s>>>(P, counts);
-  k_scan<<<1, 1024, 0, s>>>(P, counts, offsets);
+  k_scan_reduce<<<nb, kScanThreads, 0, s>>>(counts, B, bsum);
+  k_scan_top<<<1, kScanThreads, 0, s>>>(bsum, nb, P);
+  k_scan_apply<<<nb, kScanThreads, 0, s>>>(counts, B, bsum, offsets);
   k_scatter<<<grid, 256, 0, s>>>(P, offsets, pos2, u2, w2, sp2, id2);
   k_sort_done<<<1, 1, 0, s>>>(P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pair_table(const float2* t, int Ng, int Ns, float4* out, cudaStream_t s) {
+  const int total = 2 * (Ns - 1) * Ng;
+  k_pair_table<<<(total + 255) / 256, 256, 0, s>>>(t, Ng, Ns, out);
   return cudaGetLastError();
 }
 

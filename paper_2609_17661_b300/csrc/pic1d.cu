@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -92,6 +93,20 @@ void legendre_nodes(int n, std::vector<double>& x, std::vector<double>& w) {
   }
 }
 
+// default push variant: PIC1D_PUSH_VARIANT (index) if set, else one particle
+// per thread at 4 resident blocks per SM (the fastest measured on the
+// 1e9-particle line)
+int default_push_variant() {
+  const char* e = std::getenv("PIC1D_PUSH_VARIANT");
+  if (e) {
+    const int v = std::atoi(e);
+    if (v >= 0 && v < push_variant_count()) return v;
+  }
+  for (int v = 0; v < push_variant_count(); ++v)
+    if (push_variant_ppt(v) == 1 && push_variant_minb(v) == 4) return v;
+  return 0;
+}
+
 int fbits_of(int n) {
   int b = 0;
   while ((1 << b) < n) ++b;
@@ -105,7 +120,8 @@ struct pic1d_ctx {
   cudaStream_t s = nullptr;
   int N = 0, F = 0;
   double L_R = 0, R_cells = 0, q_p = 0, j_ext = 0, tau_min = 0, dt = 0;
-  long long cap = 0;
+  long long cap = 0;     // logical capacity (slots)
+  long long alloc = 0;   // allocated slots per buffer
   int cur = 0;
   uint32_t* pos[2] = {nullptr, nullptr};
   float* u[2] = {nullptr, nullptr};
@@ -118,15 +134,20 @@ struct pic1d_ctx {
   long long* dens[2] = {nullptr, nullptr};
   float *nb = nullptr, *nmu = nullptr, *nx = nullptr;
   uint8_t* zone = nullptr;
+  uint8_t* dens_flag = nullptr;
   float2* table = nullptr;
+  float4* tpair = nullptr;
   Counters* ctr = nullptr;
   StepState* st = nullptr;
   double* ke_partial = nullptr;
   double* field_partial = nullptr;
   uint32_t* counts = nullptr;
   long long* offsets = nullptr;
+  long long* bsum = nullptr;
   unsigned long long* spc = nullptr;
-  int push_grid = 0;
+  int push_grid = 0;      // grid of the current push variant
+  int push_variant = 0;   // index into the push variants (particles per thread x occupancy)
+  int sms = 0;
   long long step = 0;
   std::string err;
   // push timing (pic1d_timing)
@@ -170,8 +191,10 @@ void free_particles(pic1d_ctx* c) {
   }
 }
 
-int alloc_particles(pic1d_ctx* c, long long cap) {
-  cap = (cap + kTile - 1) / kTile * kTile + kTile;     // whole tiles plus one of slack for the 128-bit loads
+int alloc_particles(pic1d_ctx* c, long long want) {
+  // whole tiles plus one tile of slack for the 128-bit loads past the end;
+  // the logical capacity is exactly what was asked for
+  const long long cap = (want + kTile - 1) / kTile * kTile + kTile;
   free_particles(c);
   for (int b = 0; b < 2; ++b) {
     CK(dalloc(&c->pos[b], cap), "alloc pos");
@@ -181,7 +204,8 @@ int alloc_particles(pic1d_ctx* c, long long cap) {
     CK(dalloc(&c->id[b], cap), "alloc id");
     CK(cudaMemsetAsync(c->sp[b], PIC1D_SP_DEAD, cap, c->s), "memset sp");
   }
-  c->cap = cap - kTile;
+  c->cap = want;
+  c->alloc = cap;
   return PIC1D_OK;
 }
 
@@ -191,6 +215,7 @@ DevParams dev_params(pic1d_ctx* c) {
   P.N = c->N;
   P.F = c->F;
   P.top = (long long)c->N << c->F;
+  P.top1 = (uint32_t)(P.top - 1);
   P.inv2F = std::ldexp(1.0f, -c->F);
   P.dt = (float)c->dt;
   P.half_dt = (float)(0.5 * c->dt);
@@ -226,9 +251,10 @@ DevParams dev_params(pic1d_ctx* c) {
   P.pos = c->pos[b]; P.u = c->u[b]; P.w = c->w[b]; P.sp = c->sp[b]; P.id = c->id[b];
   P.E32 = c->E32;
   P.J = c->J;
-  P.table = c->table;
+  P.tpair = c->tpair;
   P.nb = c->nb; P.nmu = c->nmu; P.nx = c->nx;
   P.zone = c->zone;
+  P.dens_flag = c->dens_flag;
   P.dens_cur = c->dens[c->step & 1];
   P.dens_next = c->dens[(c->step + 1) & 1];
   P.cap = c->cap;
@@ -292,6 +318,11 @@ int build_tables(pic1d_ctx* c) {
   CK(dalloc(&c->nmu, N + 1), "alloc nodes");
   CK(dalloc(&c->nx, N + 1), "alloc nodes");
   CK(dalloc(&c->zone, N), "alloc zone");
+  std::vector<uint8_t> hf(N);
+  for (int cc = 0; cc < N; ++cc)
+    hf[cc] = hz[cc] | (cc > 0 ? hz[cc - 1] : 0) | (cc + 1 < N ? hz[cc + 1] : 0);
+  CK(dalloc(&c->dens_flag, N), "alloc zone");
+  CK(cudaMemcpyAsync(c->dens_flag, hf.data(), N, cudaMemcpyHostToDevice, c->s), "copy zone");
   CK(cudaMemcpyAsync(c->nb, hb.data(), (N + 1) * sizeof(float), cudaMemcpyHostToDevice, c->s), "copy nodes");
   CK(cudaMemcpyAsync(c->nmu, hmu.data(), (N + 1) * sizeof(float), cudaMemcpyHostToDevice, c->s), "copy nodes");
   CK(cudaMemcpyAsync(c->nx, hx.data(), (N + 1) * sizeof(float), cudaMemcpyHostToDevice, c->s), "copy nodes");
@@ -325,6 +356,8 @@ int build_tables(pic1d_ctx* c) {
     CK(launch_table(Ng, Ns, p.quad_n_mu, p.quad_n_phi, p.table_log10g_max, p.kT_keV / kMeKeV, pref, dxs, dbs, dms,
                     dgx, dgw, p.photon_model, c->table, c->s),
        "table kernel");
+    CK(dalloc(&c->tpair, (size_t)2 * (Ns - 1) * Ng), "alloc table");
+    CK(launch_pair_table(c->table, Ng, Ns, c->tpair, c->s), "pair table");
     CK(cudaStreamSynchronize(c->s), "table sync");
     cudaFree(dxs); cudaFree(dbs); cudaFree(dms); cudaFree(dgx); cudaFree(dgw);
   }
@@ -334,7 +367,8 @@ int build_tables(pic1d_ctx* c) {
 int do_sort(pic1d_ctx* c) {
   DevParams P = dev_params(c);
   const int o = 1 - c->cur;
-  CK(launch_sort(P, c->counts, c->offsets, c->pos[o], c->u[o], c->w[o], c->sp[o], c->id[o], c->push_grid, c->s),
+  CK(launch_sort(P, c->counts, c->offsets, c->bsum, c->pos[o], c->u[o], c->w[o], c->sp[o], c->id[o], c->push_grid,
+                 c->s),
      "sort");
   c->cur = o;
   return PIC1D_OK;
@@ -437,14 +471,17 @@ int pic1d_init(const pic1d_params* p, pic1d_ctx** out) {
     chain(dalloc(&c->ctr, 1));
     chain(dalloc(&c->st, 1));
     chain(dalloc(&c->field_partial, 3 * kMaxFieldBlocks));
-    chain(dalloc(&c->counts, N));
-    chain(dalloc(&c->offsets, N + 1));
+    chain(dalloc(&c->counts, sort_bins(N)));
+    chain(dalloc(&c->offsets, sort_bins(N) + 1));
+    chain(dalloc(&c->bsum, scan_blocks(N)));
     chain(dalloc(&c->spc, 4));
     int dev = 0, sms = 0;
     chain(cudaGetDevice(&dev));
     chain(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    c->push_grid = std::max(1, sms) * push_blocks_per_sm();
-    chain(dalloc(&c->ke_partial, c->push_grid));
+    c->sms = std::max(1, sms);
+    chain(dalloc(&c->ke_partial, c->sms * 8));     // at most 8 blocks of 256 threads per SM
+    c->push_variant = default_push_variant();
+    c->push_grid = c->sms * push_blocks_per_sm(c->push_variant, p->n_max_ppc > 0.0);
     if (e == cudaSuccess) {
       chain(cudaMemsetAsync(c->E64, 0, N * sizeof(double), c->s));
       chain(cudaMemsetAsync(c->E32, 0, N * sizeof(float), c->s));
@@ -453,7 +490,7 @@ int pic1d_init(const pic1d_params* p, pic1d_ctx** out) {
       chain(cudaMemsetAsync(c->dens[1], 0, N * sizeof(long long), c->s));
       chain(cudaMemsetAsync(c->ctr, 0, sizeof(Counters), c->s));
       chain(cudaMemsetAsync(c->st, 0, sizeof(StepState), c->s));
-      chain(cudaMemsetAsync(c->ke_partial, 0, c->push_grid * sizeof(double), c->s));
+      chain(cudaMemsetAsync(c->ke_partial, 0, c->sms * 8 * sizeof(double), c->s));
     }
     if (e != cudaSuccess) rc = cuda_fail(c, e, "init");
   }
@@ -497,7 +534,7 @@ int pic1d_set_state(pic1d_ctx* c, int64_t n, const uint32_t* pos, const float* u
     CK(cudaMemcpyAsync(c->sp[0], sp, n * sizeof(uint8_t), k, c->s), "set_state sp");
     CK(cudaMemcpyAsync(c->id[0], id, n * sizeof(uint64_t), k, c->s), "set_state id");
   }
-  CK(cudaMemsetAsync(c->sp[0] + n, PIC1D_SP_DEAD, (size_t)(c->cap + kTile - n), c->s), "set_state tail");
+  CK(cudaMemsetAsync(c->sp[0] + n, PIC1D_SP_DEAD, (size_t)(c->alloc - n), c->s), "set_state tail");
   if (mem == 1 && n > 0) {
     unsigned long long* bad = c->spc;
     CK(cudaMemsetAsync(bad, 0, sizeof(unsigned long long), c->s), "validate");
@@ -555,7 +592,7 @@ int pic1d_step(pic1d_ctx* c, int n_steps) {
       int rc = timing_begin(c);
       if (rc != PIC1D_OK) return rc;
     }
-    CK(launch_push(P, c->push_grid, c->s), "push");
+    CK(launch_push(P, c->push_variant, c->push_grid, c->s), "push");
     if (c->timing) CK(cudaEventRecord(c->ev.back(), c->s), "timing");
     if (p.inject_mode == PIC1D_INJECT_RATE) CK(launch_inject(P, carriers, sig_e, sig_i, c->s), "inject");
     CK(launch_field(P, c->E64, c->E32, a, cJ, dt_jext, c->field_partial, c->push_grid, c->s), "field");
@@ -629,6 +666,7 @@ int pic1d_diag(pic1d_ctx* c, pic1d_diag_t* out) {
   out->R_cells = c->R_cells;
   out->L_Rstar = c->L_R;
   out->fbits = c->F;
+  out->push_variant = c->push_variant;
   int status = PIC1D_OK;
   if (C.nonfinite) status = PIC1D_ENUMERIC;
   else if (C.pairs_dropped_cap || C.injected_dropped) status = PIC1D_WCAPACITY;
@@ -685,6 +723,21 @@ int pic1d_deposit(pic1d_ctx* c, int64_t n, const int64_t* pos0, const int64_t* p
   return PIC1D_OK;
 }
 
+int pic1d_set_variant(pic1d_ctx* c, int variant) {
+  if (!c) return PIC1D_EINVAL;
+  if (variant < 0 || variant >= push_variant_count()) return fail(c, PIC1D_EINVAL, "set_variant: no such variant");
+  c->push_variant = variant;
+  c->push_grid = c->sms * push_blocks_per_sm(variant, c->p.n_max_ppc > 0.0);
+  return PIC1D_OK;
+}
+
+int pic1d_variant_info(int variant, int* particles_per_thread, int* min_blocks_per_sm) {
+  if (variant < 0 || variant >= push_variant_count()) return PIC1D_EINVAL;
+  if (particles_per_thread) *particles_per_thread = push_variant_ppt(variant);
+  if (min_blocks_per_sm) *min_blocks_per_sm = push_variant_minb(variant);
+  return push_variant_count();
+}
+
 int pic1d_timing(pic1d_ctx* c, int on) {
   if (!c) return PIC1D_EINVAL;
   CK(cudaStreamSynchronize(c->s), "timing sync");
@@ -708,8 +761,9 @@ void pic1d_free(pic1d_ctx* c) {
   else cudaDeviceSynchronize();
   free_particles(c);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
-  void* ptrs[] = {c->E64, c->E32, c->J, c->dens[0], c->dens[1], c->nb, c->nmu, c->nx, c->zone, c->table,
-                  c->ctr, c->st, c->ke_partial, c->field_partial, c->counts, c->offsets, c->spc, c->slot_log};
+  void* ptrs[] = {c->E64, c->E32, c->J, c->dens[0], c->dens[1], c->nb, c->nmu, c->nx, c->zone, c->dens_flag, c->table,
+                  c->ctr, c->st, c->ke_partial, c->field_partial, c->counts, c->offsets, c->spc, c->slot_log,
+                  c->tpair, c->bsum};
   for (void* q : ptrs) cudaFree(q);
   delete c;
 }

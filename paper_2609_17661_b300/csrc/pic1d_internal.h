@@ -39,6 +39,7 @@ struct StepState {
 struct DevParams {
   int N, F;
   long long top;            // N << F
+  uint32_t top1;            // top - 1
   float inv2F;              // 2^-F
   float dt, half_dt;
   float qm[4];              // q/m per species in units of e/m_e
@@ -64,9 +65,10 @@ struct DevParams {
   uint32_t* pos; float* u; float* w; uint8_t* sp; uint64_t* id;
   const float* E32;
   long long* J;
-  const float2* table;
+  const float4* tpair;      // table with neighbouring s-rows paired
   const float* nb; const float* nmu; const float* nx;
   const uint8_t* zone;
+  const uint8_t* dens_flag; // cells where the pair cap can be tested: zone cells and their neighbours
   long long* dens_cur; long long* dens_next;
   long long cap;
   Counters* ctr;
@@ -78,19 +80,25 @@ struct DevParams {
 
 // kernel launchers (kernels.cu)
 namespace pic1d {
-cudaError_t launch_push(const DevParams& P, int grid, cudaStream_t s);
+cudaError_t launch_push(const DevParams& P, int variant, int grid, cudaStream_t s);
+int push_variant_count();
+int push_variant_ppt(int v);
+int push_variant_minb(int v);
 cudaError_t launch_inject(const DevParams& P, double carriers_per_step, float sig_e, float sig_i,
                           cudaStream_t s);
 cudaError_t launch_field(const DevParams& P, double* E64, float* E32, double four_pi_dt_jext, double cJ,
                          double dt_jext, double* field_partial, int grid_push, cudaStream_t s);
-cudaError_t launch_sort(const DevParams& P, uint32_t* counts, long long* offsets,
+cudaError_t launch_sort(const DevParams& P, uint32_t* counts, long long* offsets, long long* bsum,
                         uint32_t* pos2, float* u2, float* w2, uint8_t* sp2, uint64_t* id2, int grid,
                         cudaStream_t s);
+cudaError_t launch_pair_table(const float2* t, int Ng, int Ns, float4* out, cudaStream_t s);
+int sort_bins(int N);
+int scan_blocks(int N);
 cudaError_t launch_table(int Ng, int Ns, int n_mu, int n_phi, double log10g_max, double theta_T,
                          double pref, const double* xs, const double* bs, const double* mus, const double* gx,
                          const double* gw, int photon_model, float2* out, cudaStream_t s);
 cudaError_t launch_deposit(const DevParams& P, long long n, const long long* p0, const long long* p1,
                            const float* w, const uint8_t* sp, long long* J, cudaStream_t s);
 cudaError_t launch_count_species(const DevParams& P, unsigned long long* out4, cudaStream_t s);
-int push_blocks_per_sm();
+int push_blocks_per_sm(int variant, bool nmax);
 }  // namespace pic1d
