@@ -217,6 +217,35 @@ int pic1d_set_variant(pic1d_ctx* c, int variant);
  * Either output may be NULL.  Needs no context. */
 int pic1d_variant_info(int variant, int* particles_per_thread, int* min_blocks_per_sm);
 
+/* Cell sort without any allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc -- code that
+ * runs inside a device memory pool it does not own, or on a device whose
+ * memory an application has reserved in full -- and so cannot create a
+ * context, whose sort scratch comes from cudaMalloc.  It sorts n particles of
+ * a line of n_cells cells (SoA device arrays in the layout above) by the key
+ * 2*cell + (ion ? 1 : 0), drops removed slots (species PIC1D_SP_DEAD), writes
+ * the sorted particles to the *_out device arrays (capacity n each) and the
+ * number kept to *n_out (a device int64).  The order inside one key is not
+ * specified.  Input and output arrays must not overlap.
+ *
+ * Its scratch (histogram, offsets, block sums, counters; about 1.6 MB) is one
+ * fixed-size device array inside this library: every GPU that loads the
+ * library holds it until the process exits, so n_cells is limited to
+ * PIC1D_SORT_STATIC_MAX_CELLS and larger lines are rejected with
+ * PIC1D_EINVAL and a message on stderr.  The first call on a device looks up
+ * the array's device address (once per device); make that first call before
+ * any stream capture.  Every call uses the same array: calls that overlap on
+ * the GPU (on different streams, or from different host threads) race and
+ * corrupt each other's results; serialise them.  The histogram is cleared
+ * by each call.  Work is issued on cuda_stream (NULL: legacy default
+ * stream) and the call returns without synchronising.
+ * Errors: EINVAL (n_cells outside [8, PIC1D_SORT_STATIC_MAX_CELLS], n < 0 or
+ * n >= 2^31, a NULL array), ECUDA. */
+#define PIC1D_SORT_STATIC_MAX_CELLS 65536
+int pic1d_sort_static(int32_t n_cells, int64_t n, const uint32_t* pos, const float* u, const float* w,
+                      const uint8_t* sp, const uint64_t* id, uint32_t* pos_out, float* u_out, float* w_out,
+                      uint8_t* sp_out, uint64_t* id_out, int64_t* n_out, void* cuda_stream);
+
 /* Message of the last error on this context (never NULL). */
 const char* pic1d_last_error(const pic1d_ctx* c);
 

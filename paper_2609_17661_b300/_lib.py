@@ -69,6 +69,7 @@ SIGNATURES = {
     "pic1d_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "pic1d_set_variant": (C.c_int, [C.c_void_p, C.c_int]),
     "pic1d_variant_info": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "pic1d_sort_static": (C.c_int, [C.c_int32, C.c_int64] + [C.c_void_p] * 11 + [C.c_void_p]),
     "pic1d_last_error": (C.c_char_p, [C.c_void_p]),
     "pic1d_free": (None, [C.c_void_p]),
 }

@@ -10,7 +10,7 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-SRC = [os.path.join(HERE, "csrc", f) for f in ("kernels.cu", "pic1d.cu")]
+SRC = [os.path.join(HERE, "csrc", f) for f in ("kernels.cu", "pic1d.cu", "sort_static.cu")]
 DEPS = SRC + [os.path.join(HERE, "csrc", "pic1d_internal.h"), os.path.join(ROOT, "include", "pic1d.h")]
 LIB = os.path.join(HERE, "libpic1d.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
