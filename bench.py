@@ -190,6 +190,7 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
     line = Line(cfg, stream=stream.cuda_stream)
     line.set_state(view)
+    line.sort()
 
     def barrier():
         torch.cuda.synchronize()
@@ -245,6 +246,7 @@ def run_gpu(args):
         Eh = np.zeros(cfg["n_cells"])
         t0 = time.perf_counter()
         line.set_state(view)
+        line.sort()
         for _ in range(args.steps):
             line.step(1)
             dd = line.diag()

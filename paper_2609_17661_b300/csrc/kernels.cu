@@ -64,9 +64,16 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 // drag and scattering rate at one particle
 // --------------------------------------------------------------------------
 struct Site {        // what the push needs about the particle's place on the line
-  float v;           // table coordinate in s/L
+  int j;             // table row in s/L below the particle
+  float c;           // fractional position between rows j and j+1
   float x, b, mu;    // r/R*, B/B_QED, cos(radial, +s) interpolated at s
 };
+
+__device__ __forceinline__ void site_rows(const DevParams& P, uint32_t pos0, Site& S) {
+  const float v = fminf((float)pos0 * P.v_scale, (float)(P.Ns - 1));
+  S.j = min((int)v, P.Ns - 2);
+  S.c = v - (float)S.j;
+}
 
 struct DragVal {
   float F, dF, lnN;  // F^ (per R*), dF^/du, ln N^ (per R_star/c)
@@ -76,15 +83,13 @@ struct DragVal {
 // pairs neighbouring s-rows: tpair[(sg*(Ns-1) + j)*Ng + i] = (F[j][i], lnN[j][i],
 // F[j+1][i], lnN[j+1][i]), so one lookup is two adjacent 16-byte loads.
 // log10 gamma = log10(2)/2 * log2(1 + u^2): no square root is needed.
-__device__ __forceinline__ DragVal table_eval(const DevParams& P, float u, float v, bool want_dF) {
+__device__ __forceinline__ DragVal table_eval(const DevParams& P, float u, int j, float c, bool want_dF) {
   const float q = fmaf(u, u, 1.0f);                    // gamma^2
   float t = fmaxf(0.5f * __log2f(q) * P.t_scale, 0.0f);
   bool top = false;
   if (t > (float)(P.Ng - 1)) { t = (float)(P.Ng - 1); top = true; }
   const int i = min((int)t, P.Ng - 2);
   const float a = t - (float)i;
-  const int j = min((int)v, P.Ns - 2);
-  const float c = v - (float)j;
   const int sg = (u >= 0.0f) ? 0 : 1;
   const float4* row = P.tpair + ((size_t)(sg * (P.Ns - 1) + j) * P.Ng);
   const float4 A = __ldg(row + i), B = __ldg(row + i + 1);
@@ -129,7 +134,7 @@ __device__ __forceinline__ DragVal closed_eval(const DevParams& P, float u, cons
 }
 
 __device__ __forceinline__ DragVal drag_eval(const DevParams& P, float u, const Site& S, bool want_dF) {
-  if (P.drag_law == PIC1D_DRAG_TABLE) return table_eval(P, u, S.v, want_dF);
+  if (P.drag_law == PIC1D_DRAG_TABLE) return table_eval(P, u, S.j, S.c, want_dF);
   return closed_eval(P, u, S, want_dF);
 }
 
@@ -251,6 +256,22 @@ __device__ __forceinline__ void kahan(float& s, float& c, float x) {
   s = t;
 }
 
+// The 1D charge-conserving current of one step (Sec. 3): the signed path length
+// inside each cell.  A step is shorter than a cell, so from the start cell
+// only the cell itself and one neighbour receive current.  d is the
+// displacement in fixed point (clamped at a wall), frac the start position
+// inside its cell; sw = q_sign * w_int.
+__device__ __forceinline__ void path_split(int d, uint32_t frac, int F, int sw, long long& xm, long long& x0,
+                                           long long& xp) {
+  const int up = (int)((1u << F) - frac), dn = (int)frac;
+  int l0, lm = 0, lp = 0;
+  if (d >= 0) { l0 = min(d, up); lp = d - l0; }
+  else { l0 = max(d, -dn); lm = d - l0; }
+  x0 = (long long)sw * l0;
+  xm = (long long)sw * lm;
+  xp = (long long)sw * lp;
+}
+
 // Result of pushing one particle.
 struct PushOut {
   uint32_t pos;               // new position (clamped inside the line if lost)
@@ -258,8 +279,7 @@ struct PushOut {
   bool lost, want_pair, want_dens;
   float child_u;
   unsigned long long pid;     // id (loaded only if a Philox number was drawn)
-  int cA, cB;                 // cells receiving current, -1 if none
-  long long vA, vB;
+  long long xm, x0, xp;       // signed current into cells cell-1, cell, cell+1
   int cD, vD;                 // cell and weight of the lepton density for the pair cap
   int cell;                   // cell at the start of the step
 };
@@ -275,7 +295,7 @@ __device__ __forceinline__ PushOut push_one(const DevParams& P, uint32_t idx, ui
   const uint32_t half = 1u << (P.F - 1);
   PushOut o;
   o.lost = false; o.want_pair = false; o.want_dens = false; o.child_u = 0.0f; o.pid = 0;
-  o.cA = -1; o.cB = -1; o.vA = 0; o.vB = 0; o.cD = 0; o.vD = 0;
+  o.xm = 0; o.x0 = 0; o.xp = 0; o.cD = 0; o.vD = 0;
   const bool ion = (sp == PIC1D_SP_ION);
   const bool lep = !ion;
   const float qm = ion ? P.qm[PIC1D_SP_ION] : (sp == PIC1D_SP_POSITRON ? 1.0f : -1.0f);
@@ -309,7 +329,7 @@ __device__ __forceinline__ PushOut push_one(const DevParams& P, uint32_t idx, ui
     } else {
       S.x = 1.0f;
     }
-    S.v = fminf((float)pos0 * P.v_scale, (float)(P.Ns - 1));
+    site_rows(P, pos0, S);
   }
   // 2-4. Strang split: drag dt/2, Lorentz kick dt, drag dt/2
   if (cont) u = drag_half(P, S, u, T.n_lim, T.n_newt);
@@ -363,20 +383,7 @@ __device__ __forceinline__ PushOut push_one(const DevParams& P, uint32_t idx, ui
   uint32_t p1;
   if (!o.lost) {
     p1 = pos0 + (uint32_t)dfix;
-    if (dfix != 0) {
-      const uint32_t lo = dfix > 0 ? pos0 : p1, hi = dfix > 0 ? p1 : pos0;
-      const int sw = dfix > 0 ? sw0 : -sw0;
-      const int c0 = (int)(lo >> P.F), c1 = (int)((hi - 1u) >> P.F);
-      const uint32_t kk = (uint32_t)c1 << P.F;
-      o.cA = c0;
-      if (c0 == c1) {
-        o.vA = (long long)sw * (int)(hi - lo);
-      } else {
-        o.vA = (long long)sw * (int)(kk - lo);
-        o.cB = c1;
-        o.vB = (long long)sw * (int)(hi - kk);
-      }
-    }
+    path_split(dfix, pos0 & fmask, P.F, sw0, o.xm, o.x0, o.xp);
     o.pos = p1;
     if (NMAX && lep) {
       o.cD = (int)(p1 >> P.F);
@@ -387,21 +394,9 @@ __device__ __forceinline__ PushOut push_one(const DevParams& P, uint32_t idx, ui
     // leaves through a wall: the path is clamped at the conductor (64-bit: the
     // southern wall sits at top, which may be 2^32)
     ++T.c[lostN ? C_LOSTN : C_LOSTS];
-    const long long a = (long long)pos0, b = lostN ? 0ll : P.top;
-    const long long lo = a < b ? a : b, hi = a < b ? b : a;
-    const int sw = b > a ? sw0 : -sw0;
-    if (hi > lo) {
-      const int c0 = (int)(lo >> P.F), c1 = (int)((hi - 1) >> P.F);
-      const long long kk = (long long)c1 << P.F;
-      o.cA = c0;
-      if (c0 == c1) {
-        o.vA = (long long)sw * (int)(hi - lo);
-      } else {
-        o.vA = (long long)sw * (int)(kk - lo);
-        o.cB = c1;
-        o.vB = (long long)sw * (int)(hi - kk);
-      }
-    }
+    // the path ends at the wall: to node 0 from cell 0, or to node N from cell N-1
+    const int d = lostN ? -(int)pos0 : (int)(P.top - (long long)pos0);
+    path_split(d, pos0 & fmask, P.F, sw0, o.xm, o.x0, o.xp);
     o.pos = lostN ? 0u : (uint32_t)(P.top - 1);
     if (make_pair) ++T.c[C_WALL];     // the parent left the line: no pair
     make_pair = false;
@@ -416,6 +411,72 @@ __device__ __forceinline__ PushOut push_one(const DevParams& P, uint32_t idx, ui
     }
   }
   return o;
+}
+
+// The same PIC cycle for a particle in a "fast" cell (no pair zone within two
+// cells, not next to a wall): gather, continuous drag for leptons, kick,
+// move, deposit.  A particle there cannot leave the line in one step.  It
+// must give bit-for-bit what push_one gives for the same particle.
+__device__ __forceinline__ void push_fast(const DevParams& P, uint32_t pos0, float u, float w, int sp, Tally& T,
+                                          PushOut& o) {
+  const uint32_t fmask = (1u << P.F) - 1u;
+  const uint32_t half = 1u << (P.F - 1);
+  const bool ion = (sp == PIC1D_SP_ION);
+  const float qm = ion ? P.qm[PIC1D_SP_ION] : (sp == PIC1D_SP_POSITRON ? 1.0f : -1.0f);
+  const int qs = (sp == PIC1D_SP_ELECTRON || sp == PIC1D_SP_ATMO) ? -1 : 1;
+  const float mass = ion ? P.mass[PIC1D_SP_ION] : 1.0f;
+  const int cell = (int)(pos0 >> P.F);
+  o.cell = cell;
+  o.lost = false;
+  o.want_pair = false;
+  o.want_dens = false;
+  o.xm = o.x0 = o.xp = 0;
+  float Ep;
+  {
+    const uint32_t x = pos0 - half;          // pos0 >= 2^F here: cell >= 1
+    int ig = (int)(x >> P.F);
+    float f = (float)(x & fmask) * P.inv2F;
+    if (ig > P.N - 2) { ig = P.N - 2; f = 1.0f; }
+    const float e0 = __ldg(P.E32 + ig), e1 = __ldg(P.E32 + ig + 1);
+    Ep = fmaf(f, e1 - e0, e0);
+  }
+  if (!ion && P.drag_law != PIC1D_DRAG_OFF) {
+    Site S;
+    const float f = (float)(pos0 & fmask) * P.inv2F;
+    const float m0 = __ldg(P.nmu + cell), m1 = __ldg(P.nmu + cell + 1);
+    S.mu = fmaf(f, m1 - m0, m0);
+    if (P.drag_law == PIC1D_DRAG_CLOSED) {
+      const float b0 = __ldg(P.nb + cell), b1 = __ldg(P.nb + cell + 1);
+      const float x0 = __ldg(P.nx + cell), x1 = __ldg(P.nx + cell + 1);
+      S.b = fmaf(f, b1 - b0, b0);
+      S.x = fmaf(f, x1 - x0, x0);
+    } else {
+      S.b = 0.0f;
+      S.x = 1.0f;
+    }
+    site_rows(P, pos0, S);
+    u = drag_half(P, S, u, T.n_lim, T.n_newt);
+    u = fmaf(qm * Ep, P.dt, u);
+    u = drag_half(P, S, u, T.n_lim, T.n_newt);
+  } else {
+    u = fmaf(qm * Ep, P.dt, u);
+  }
+  if (!isfinite(u)) {
+    ++T.c[C_NONFIN];
+    o.u = 0.0f;
+    o.pos = pos0;
+    o.lost = true;
+    return;
+  }
+  const float q = fmaf(u, u, 1.0f);
+  const float r = rsqrtf(q);
+  const int dfix = __float2int_rn(P.dt * (u * r) * (float)(1u << P.F));
+  kahan(T.ke, T.ke_c, w * mass * __fdividef(u * u * r, 1.0f + r));
+  kahan(T.kl, T.kl_c, 0.0f);
+  const uint32_t p1 = pos0 + (uint32_t)dfix;
+  path_split(dfix, pos0 & fmask, P.F, qs * __float2int_rn(w * 4096.0f), o.xm, o.x0, o.xp);
+  o.pos = p1;
+  o.u = u;
 }
 
 // warp-aggregated add of (cell, v) contributions from the lanes in `mask`
@@ -443,42 +504,95 @@ __device__ __forceinline__ uint2 pack_u(const uint32_t (&a)[2]) { return make_ui
 __device__ __forceinline__ float pack_f(const float (&a)[1]) { return a[0]; }
 __device__ __forceinline__ float2 pack_f(const float (&a)[2]) { return make_float2(a[0], a[1]); }
 
+// a lane's current registers (cells c_ref-1, c_ref, c_ref+1) to global memory
+// (native 64-bit atomics; exact and order-independent), then cleared
+__device__ __forceinline__ void flush_lane(long long (&a)[3], int c_ref, long long* J, int N) {
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const int c = c_ref - 1 + j;
+    if (a[j] != 0 && c >= 0 && c < N) atomicAdd(reinterpret_cast<unsigned long long*>(J + c), (unsigned long long)a[j]);
+    a[j] = 0;
+  }
+}
+
+// shared-memory window add; the thread records the window range it touched
+// in two registers (lo, hi), reduced once per chunk
+__device__ __forceinline__ void win_add(long long* sWin, int win_lo, int& lo, int& hi, long long* g, int N, int cell,
+                                        long long v) {
+  if (v == 0 || cell < 0 || cell >= N) return;
+  const int o = cell - win_lo;
+  if (o >= 0 && o < kWindow) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(sWin + o), (unsigned long long)v);
+    lo = min(lo, o);
+    hi = max(hi, o);
+  } else {
+    atomicAdd(reinterpret_cast<unsigned long long*>(g + cell), (unsigned long long)v);
+  }
+}
+
+__device__ __forceinline__ void warp_flush_w(long long (&a)[3], int c_ref, long long* sWin, int win_lo, int& lo,
+                                             int& hi, long long* g, int N) {
+  const int lane = threadIdx.x & 31;
+  const unsigned grp = __match_any_sync(0xffffffffu, c_ref);
+  const bool leader = lane == __ffs(grp) - 1;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const long long sum = group_sum64(grp, a[j]);
+    if (leader) win_add(sWin, win_lo, lo, hi, g, N, c_ref - 1 + j, sum);
+    a[j] = 0;
+  }
+}
+
+// flush the touched part [s_rng[0], s_rng[1]] of a shared window to global
+// memory and clear it
+__device__ __forceinline__ void window_drain(long long* sWin, int win_lo, const int* s_rng, long long* g, int N) {
+  const int lo = s_rng[0], hi = s_rng[1];
+  for (int i = lo + (int)threadIdx.x; i <= hi; i += kBlock) {
+    const long long v = sWin[i];
+    if (v) {
+      const int c = win_lo + i;
+      if (c < N) atomicAdd(reinterpret_cast<unsigned long long*>(g + c), (unsigned long long)v);
+      sWin[i] = 0;
+    }
+  }
+}
+
 // The push kernel.  A thread owns PPT consecutive particles per tile (one
-// PPT-wide access per SoA array), a block owns a contiguous range of tiles of
-// kBlock * PPT particles, so that the cell-sorted particles of a block fall
-// into a narrow window of cells.  The current registers of a thread (cells
-// c_ref-1 .. c_ref+1) persist across its particles and are flushed warp-wide
-// (exact group sums) only when some lane needs a cell outside its anchor
-// range; block sums go through a shared-memory cell window flushed to global
-// memory once per block.  Slot indices are 32-bit (capacity < 2^31).
+// PPT-wide access per SoA array); blocks take chunks of kChunkTiles tiles
+// (kBlock * PPT particles each) from a global counter, so that expensive
+// regions of the line (pair zones, dense footpoints) are shared by all SMs.
+// The current registers of a thread (cells c_ref-1 .. c_ref+1) persist across
+// its particles and are flushed warp-wide (exact group sums) only when some
+// lane needs a cell outside its anchor range; block sums go through a
+// shared-memory cell window anchored at each chunk's first particle, whose
+// touched range is drained to global memory at the end of the chunk.  The
+// lepton density of the pair cap is summed per warp in a warp-uniform pending
+// register while the warp's contributions stay in one cell.  Slot indices are
+// 32-bit (capacity < 2^31).
 template <int PPT, int MINB, bool NMAX>
 __global__ void __launch_bounds__(kBlock, MINB) k_push(DevParams P) {
   using VU = typename Vec<PPT>::U;
   using VF = typename Vec<PPT>::F;
   using VB = typename Vec<PPT>::B;
   constexpr int TILE = kBlock * PPT;
-  __shared__ long long sJ[kWindow];
   __shared__ long long sD[NMAX ? kWindow : 1];
+  __shared__ int s_rngD[2];
+  __shared__ unsigned s_chunk;
+  __shared__ int s_anchor;
   __shared__ unsigned sCtr[C_COUNT];
   __shared__ double sRed[2][kBlock / 32];
 
   const uint32_t n = (uint32_t)P.st->n_slots;
   const int lane = threadIdx.x & 31;
-  const uint32_t ntiles = (n + TILE - 1) / TILE;
-  const uint32_t tpb = (ntiles + gridDim.x - 1) / gridDim.x;
-  const uint32_t t0 = blockIdx.x * tpb;
-  const uint32_t t1 = min(ntiles, t0 + tpb);
 
-  int win_lo = 0;
-  if (t0 < t1) {
-    const int c = (int)(P.pos[(size_t)t0 * TILE] >> P.F);
-    win_lo = max(0, min(c, P.N - 1) - kWindow / 8);
-  }
-  for (int i = threadIdx.x; i < kWindow; i += kBlock) {
-    sJ[i] = 0;
-    if (NMAX) sD[i] = 0;
-  }
+  if (NMAX)
+    for (int i = threadIdx.x; i < kWindow; i += kBlock) sD[i] = 0;
   if (threadIdx.x < C_COUNT) sCtr[threadIdx.x] = 0;
+  if (threadIdx.x == 0) {
+    s_rngD[0] = kWindow;
+    s_rngD[1] = -1;
+    s_chunk = (unsigned)atomicAdd(&P.st->work, 1ull);
+  }
   __syncthreads();
 
   Tally T;
@@ -488,109 +602,179 @@ __global__ void __launch_bounds__(kBlock, MINB) k_push(DevParams P) {
   T.ke = T.ke_c = T.kl = T.kl_c = 0.0f;
   long long aJ[3] = {0, 0, 0};
   int c_ref = -4;
+  int dlo = kWindow, dhi = -1;   // density window range this thread touched
+  // warp-uniform pending lepton density (pair cap)
+  int dcell = -1;
+  long long dsum = 0;
 
-  // software pipeline: the next tile's loads are in flight while this one is computed
-  VU npos{};
-  VF nu{}, nw{};
-  VB nsp{};
-  if (t0 < t1) {
-    const uint32_t b0 = t0 * TILE + threadIdx.x * PPT;
-    npos = __ldcs(reinterpret_cast<const VU*>(P.pos + b0));
-    nu = __ldcs(reinterpret_cast<const VF*>(P.u + b0));
-    nw = __ldcs(reinterpret_cast<const VF*>(P.w + b0));
-    nsp = *reinterpret_cast<const VB*>(P.sp + b0);
-  }
-
-  for (uint32_t t = t0; t < t1; ++t) {
-    const uint32_t base = t * TILE + threadIdx.x * PPT;
-    uint32_t pp[PPT];
-    float uu[PPT], ww[PPT];
-    uint8_t ss[PPT];
-    unpack_u(npos, pp);
-    unpack_f(nu, uu);
-    unpack_f(nw, ww);
-    unpack_b(nsp, ss);
-    if (t + 1 < t1) {
-      const uint32_t b1 = base + TILE;
-      npos = __ldcs(reinterpret_cast<const VU*>(P.pos + b1));
-      nu = __ldcs(reinterpret_cast<const VF*>(P.u + b1));
-      nw = __ldcs(reinterpret_cast<const VF*>(P.w + b1));
-      nsp = *reinterpret_cast<const VB*>(P.sp + b1);
+  // a chunk is split among the warps: warp w walks its own contiguous eighth
+  // of the chunk, 32 * PPT particles per step of its loop, so a lane's
+  // consecutive particles are neighbours in the cell order
+  constexpr uint32_t CHUNK = (uint32_t)kChunkTiles * TILE;
+  constexpr uint32_t WSPAN = CHUNK / (kBlock / 32);
+  constexpr uint32_t WSTEP = 32u * PPT;
+  const uint32_t nchunks_w = (n + CHUNK - 1) / CHUNK;
+  unsigned chunk = s_chunk;
+  while (chunk < nchunks_w) {
+    if (threadIdx.x == 0) {
+      const int c = (int)(P.pos[(size_t)chunk * CHUNK] >> P.F);
+      s_anchor = max(0, min(c, P.N - 1) - kWindow / 8);
     }
-    bool dirty = false;
+    __syncthreads();
+    const int win_lo = s_anchor;
+    const uint32_t wbase = chunk * CHUNK + (threadIdx.x >> 5) * WSPAN + (uint32_t)lane * PPT;
+    const uint32_t t1 = WSPAN / WSTEP;
+
+    VU npos{};
+    VF nu{}, nw{};
+    VB nsp{};
+    // loads are guarded: a chunk may run past the last slot by up to a chunk,
+    // beyond the arrays' slack (the arrays have >= PPT slots past n)
+    if (wbase < n) {
+      npos = __ldcs(reinterpret_cast<const VU*>(P.pos + wbase));
+      nu = __ldcs(reinterpret_cast<const VF*>(P.u + wbase));
+      nw = __ldcs(reinterpret_cast<const VF*>(P.w + wbase));
+      nsp = *reinterpret_cast<const VB*>(P.sp + wbase);
+    }
+    for (uint32_t t = 0; t < t1; ++t) {
+      const uint32_t base = wbase + t * WSTEP;
+      uint32_t pp[PPT];
+      float uu[PPT], ww[PPT];
+      uint8_t ss[PPT];
+      unpack_u(npos, pp);
+      unpack_f(nu, uu);
+      unpack_f(nw, ww);
+      unpack_b(nsp, ss);
+      if (t + 1 < t1 && base + WSTEP < n) {
+        const uint32_t b1 = base + WSTEP;
+        npos = __ldcs(reinterpret_cast<const VU*>(P.pos + b1));
+        nu = __ldcs(reinterpret_cast<const VF*>(P.u + b1));
+        nw = __ldcs(reinterpret_cast<const VF*>(P.w + b1));
+        nsp = *reinterpret_cast<const VB*>(P.sp + b1);
+      }
+      bool dirty = false;
 #pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-      const uint32_t idx = base + k;
-      const bool valid = (idx < n) && (ss[k] != PIC1D_SP_DEAD);
-      PushOut o;
-      o.cA = o.cB = -1;
-      o.want_pair = false;
-      o.want_dens = false;
-      if (valid) {
-        o = push_one<NMAX>(P, idx, pp[k], uu[k], ww[k], ss[k] & 3, T);
-        pp[k] = o.pos;
-        uu[k] = o.u;
-        if (o.lost) { ss[k] = PIC1D_SP_DEAD; dirty = true; }
-      }
-      // current into the thread's registers; flush warp-wide first if some
-      // lane needs cells outside its anchor range
-      const bool out = valid && ((o.cA >= 0 && abs(o.cA - c_ref) > 1) || (o.cB >= 0 && abs(o.cB - c_ref) > 1));
-      if (__any_sync(0xffffffffu, out)) {
-        warp_flush(aJ, c_ref, sJ, win_lo, P.J, P.N);
-        if (valid) c_ref = o.cell;
-      }
-      if (o.cA >= 0) { const int d = o.cA - c_ref; if (d < 0) aJ[0] += o.vA; else if (d == 0) aJ[1] += o.vA; else aJ[2] += o.vA; }
-      if (o.cB >= 0) { const int d = o.cB - c_ref; if (d < 0) aJ[0] += o.vB; else if (d == 0) aJ[1] += o.vB; else aJ[2] += o.vB; }
-      // lepton density for the pair cap: only cells where a pair can be tested
-      if (NMAX) {
-        const unsigned md = __ballot_sync(0xffffffffu, o.want_dens);
-        if (md) warp_add_cells(md, o.want_dens, o.cD, (long long)o.vD, sD, win_lo, P.dens_next, P.N);
-      }
-      // pair append, warp-aggregated
-      const unsigned m = __ballot_sync(0xffffffffu, o.want_pair);
-      if (m) {
-        const int leader = __ffs(m) - 1;
-        long long slot0 = 0;
-        if (lane == leader) slot0 = atomicAdd(reinterpret_cast<unsigned long long*>(&P.st->append),
-                                              (unsigned long long)(2 * __popc(m)));
-        slot0 = __shfl_sync(0xffffffffu, slot0, leader);
-        if (o.want_pair) {
-          const long long dst = (long long)n + slot0 + 2ll * __popc(m & lanemask_lt());
-          if (dst + 2 > P.cap) {
-            ++T.c[C_DROP];
-          } else {
-            ++T.c[C_PAIRS];
-#pragma unroll
-            for (int mm = 0; mm < 2; ++mm) {
-              P.pos[dst + mm] = o.pos;
-              P.u[dst + mm] = o.child_u;
-              P.w[dst + mm] = ww[k];
-              P.sp[dst + mm] = (mm == 0) ? PIC1D_SP_ELECTRON : PIC1D_SP_POSITRON;
-              P.id[dst + mm] = pair_child_id(o.pid, P.step, mm);
+      for (int k = 0; k < PPT; ++k) {
+        const uint32_t idx = base + k;
+        const bool valid = (idx < n) && (ss[k] != PIC1D_SP_DEAD);
+        PushOut o;
+        // warp-uniform fast path: every lane's particle sits in a cell at least
+        // two cells away from any pair zone and from the walls
+        const bool fast = !valid || __ldg(P.fast_cell + (pp[k] >> P.F)) != 0;
+        if (__all_sync(0xffffffffu, fast)) {
+          if (valid) push_fast(P, pp[k], uu[k], ww[k], ss[k] & 3, T, o);
+        } else {
+          o.want_pair = false;
+          o.want_dens = false;
+          if (valid) o = push_one<NMAX>(P, idx, pp[k], uu[k], ww[k], ss[k] & 3, T);
+          // lepton density for the pair cap: only cells where a pair can be tested
+          if (NMAX) {
+            const unsigned md = __ballot_sync(0xffffffffu, o.want_dens);
+            if (md) {
+              const int c0 = __shfl_sync(0xffffffffu, o.cD, __ffs(md) - 1);
+              if (__all_sync(0xffffffffu, !o.want_dens || o.cD == c0)) {
+                long long sd = 0;
+                if (o.want_dens) sd = group_sum64(md, (long long)o.vD);
+                sd = __shfl_sync(0xffffffffu, sd, __ffs(md) - 1);
+                if (c0 != dcell) {
+                  if (lane == 0 && dcell >= 0) win_add(sD, win_lo, dlo, dhi, P.dens_next, P.N, dcell, dsum);
+                  dcell = c0;
+                  dsum = 0;
+                }
+                dsum += sd;
+              } else if (o.want_dens) {
+                const unsigned grp = __match_any_sync(md, o.cD);
+                const long long sum = group_sum64(grp, (long long)o.vD);
+                if (lane == __ffs(grp) - 1) win_add(sD, win_lo, dlo, dhi, P.dens_next, P.N, o.cD, sum);
+              }
             }
-            if (NMAX && __ldg(P.dens_flag + (o.pos >> P.F)))
-              atomicAdd(reinterpret_cast<unsigned long long*>(P.dens_next + (int)(o.pos >> P.F)),
-                        (unsigned long long)(2ll * __float2int_rn(ww[k] * 4096.0f)));
+          }
+          // pair append, warp-aggregated
+          const unsigned m = __ballot_sync(0xffffffffu, o.want_pair);
+          if (m) {
+            const int leader = __ffs(m) - 1;
+            long long slot0 = 0;
+            if (lane == leader) slot0 = atomicAdd(reinterpret_cast<unsigned long long*>(&P.st->append),
+                                                  (unsigned long long)(2 * __popc(m)));
+            slot0 = __shfl_sync(0xffffffffu, slot0, leader);
+            if (o.want_pair) {
+              const long long dst = (long long)n + slot0 + 2ll * __popc(m & lanemask_lt());
+              if (dst + 2 > P.cap) {
+                ++T.c[C_DROP];
+              } else {
+                ++T.c[C_PAIRS];
+#pragma unroll
+                for (int mm = 0; mm < 2; ++mm) {
+                  P.pos[dst + mm] = o.pos;
+                  P.u[dst + mm] = o.child_u;
+                  P.w[dst + mm] = ww[k];
+                  P.sp[dst + mm] = (mm == 0) ? PIC1D_SP_ELECTRON : PIC1D_SP_POSITRON;
+                  P.id[dst + mm] = pair_child_id(o.pid, P.step, mm);
+                }
+                if (NMAX && __ldg(P.dens_flag + (o.pos >> P.F)))
+                  atomicAdd(reinterpret_cast<unsigned long long*>(P.dens_next + (int)(o.pos >> P.F)),
+                            (unsigned long long)(2ll * __float2int_rn(ww[k] * 4096.0f)));
+              }
+            }
           }
         }
+        if (valid) {
+          pp[k] = o.pos;
+          uu[k] = o.u;
+          if (o.lost) { ss[k] = PIC1D_SP_DEAD; dirty = true; }
+          // current into the lane's registers for cells c_ref-1 .. c_ref+1; when
+          // the lane's start cell changes, the registers go to global memory
+          if (o.cell != c_ref) {
+            flush_lane(aJ, c_ref, P.J, P.N);
+            c_ref = o.cell;
+          }
+          aJ[0] += o.xm;
+          aJ[1] += o.x0;
+          aJ[2] += o.xp;
+        }
+      }
+      // write back (streaming stores: the data is not re-read in this kernel)
+      if (base + PPT <= n) {
+        __stcs(reinterpret_cast<VU*>(P.pos + base), pack_u(pp));
+        __stcs(reinterpret_cast<VF*>(P.u + base), pack_f(uu));
+      } else {
+#pragma unroll
+        for (int k = 0; k < PPT; ++k)
+          if (base + k < n) { P.pos[base + k] = pp[k]; P.u[base + k] = uu[k]; }
+      }
+      if (dirty) {
+#pragma unroll
+        for (int k = 0; k < PPT; ++k)
+          if (base + k < n && ss[k] == PIC1D_SP_DEAD) P.sp[base + k] = PIC1D_SP_DEAD;
       }
     }
-    // write back (streaming stores: the data is not re-read in this kernel)
-    if (base + PPT <= n) {
-      __stcs(reinterpret_cast<VU*>(P.pos + base), pack_u(pp));
-      __stcs(reinterpret_cast<VF*>(P.u + base), pack_f(uu));
-    } else {
-#pragma unroll
-      for (int k = 0; k < PPT; ++k)
-        if (base + k < n) { P.pos[base + k] = pp[k]; P.u[base + k] = uu[k]; }
+    // end of the chunk: everything pending goes to the window, the window's
+    // touched range to global memory, and the next chunk is taken
+    flush_lane(aJ, c_ref, P.J, P.N);
+    c_ref = -4;
+    if (NMAX) {
+      if (lane == 0 && dcell >= 0) win_add(sD, win_lo, dlo, dhi, P.dens_next, P.N, dcell, dsum);
+      dcell = -1;
+      dsum = 0;
     }
-    if (dirty) {
-#pragma unroll
-      for (int k = 0; k < PPT; ++k)
-        if (base + k < n && ss[k] == PIC1D_SP_DEAD) P.sp[base + k] = PIC1D_SP_DEAD;
+    if (NMAX) {
+      // the density window range touched by the block in this chunk
+      const int c = __reduce_min_sync(0xffffffffu, dlo), d = __reduce_max_sync(0xffffffffu, dhi);
+      if (lane == 0 && d >= 0) { atomicMin(&s_rngD[0], c); atomicMax(&s_rngD[1], d); }
+      dlo = kWindow;
+      dhi = -1;
     }
+    __syncthreads();
+    if (NMAX) window_drain(sD, win_lo, s_rngD, P.dens_next, P.N);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_rngD[0] = kWindow;
+      s_rngD[1] = -1;
+      s_chunk = (unsigned)atomicAdd(&P.st->work, 1ull);
+    }
+    __syncthreads();
+    chunk = s_chunk;
   }
-  warp_flush(aJ, c_ref, sJ, win_lo, P.J, P.N);
 
   // counters and energy totals of the block
   T.c[C_LIM] = T.n_lim;
@@ -607,14 +791,6 @@ __global__ void __launch_bounds__(kBlock, MINB) k_push(DevParams P) {
   }
   if (lane == 0) { sRed[0][threadIdx.x >> 5] = ked; sRed[1][threadIdx.x >> 5] = kld; }
   __syncthreads();
-  // flush the window
-  for (int i = threadIdx.x; i < kWindow; i += kBlock) {
-    const int c = win_lo + i;
-    if (c < P.N) {
-      if (sJ[i]) atomicAdd(reinterpret_cast<unsigned long long*>(P.J + c), (unsigned long long)sJ[i]);
-      if (NMAX && sD[i]) atomicAdd(reinterpret_cast<unsigned long long*>(P.dens_next + c), (unsigned long long)sD[i]);
-    }
-  }
   if (threadIdx.x == 0) {
     double a = 0.0, b = 0.0;
     for (int i = 0; i < kBlock / 32; ++i) { a += sRed[0][i]; b += sRed[1][i]; }
@@ -741,16 +917,21 @@ __global__ void k_finalize(DevParams P, const double* fpart, int nfb, int npb, d
 
 // --------------------------------------------------------------------------
 // cell sort: histogram, exclusive scan, scatter (removed slots dropped).
-// Key = 2 * cell + (ion ? 1 : 0): cells in order, leptons before ions in a
-// cell, so that a warp of the push mostly follows one species' code path.
+// Key = group * N + cell with group = 2 * (ion) + (u < 0): four runs (leptons
+// moving +s, leptons moving -s, ions moving +s, ions moving -s), each in cell
+// order.  The particles of one run move nearly together until the next sort,
+// so neighbouring slots stay within a cell or two of each other (the push's
+// current registers and shared window stay valid) and a warp mostly follows
+// one species' code path.
 // --------------------------------------------------------------------------
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
 constexpr int kScanChunk = kScanThreads * kScanItems;
 
-__device__ __forceinline__ int sort_key(const DevParams& P, uint32_t pos, uint8_t sp) {
+__device__ __forceinline__ int sort_key(const DevParams& P, uint32_t pos, uint8_t sp, float u) {
   const int cell = min((int)(pos >> P.F), P.N - 1);
-  return 2 * cell + (sp == PIC1D_SP_ION ? 1 : 0);
+  const int group = (sp == PIC1D_SP_ION ? 2 : 0) + (u < 0.0f ? 1 : 0);
+  return group * P.N + cell;
 }
 
 __global__ void __launch_bounds__(256) k_hist(DevParams P, uint32_t* counts) {
@@ -764,7 +945,7 @@ __global__ void __launch_bounds__(256) k_hist(DevParams P, uint32_t* counts) {
     if (valid) {
       const uint8_t sp = P.sp[i];
       valid = sp != PIC1D_SP_DEAD;
-      key = sort_key(P, P.pos[i], sp);
+      key = sort_key(P, P.pos[i], sp, P.u[i]);
     }
     const unsigned vm = __ballot_sync(full, valid);
     if (valid) {
@@ -857,12 +1038,14 @@ __global__ void __launch_bounds__(256) k_scatter(DevParams P, long long* cursor,
     bool valid = i < n;
     uint32_t pos = 0;
     uint8_t sp = 0;
+    float uu = 0.0f;
     int key = 0;
     if (valid) {
       sp = P.sp[i];
       pos = P.pos[i];
+      uu = P.u[i];
       valid = sp != PIC1D_SP_DEAD;
-      key = sort_key(P, pos, sp);
+      key = sort_key(P, pos, sp, uu);
     }
     const unsigned vm = __ballot_sync(full, valid);
     if (valid) {
@@ -874,7 +1057,7 @@ __global__ void __launch_bounds__(256) k_scatter(DevParams P, long long* cursor,
       b = __shfl_sync(grp, b, leader);
       const long long dst = b + __popc(grp & lanemask_lt());
       pos2[dst] = pos;
-      u2[dst] = P.u[i];
+      u2[dst] = uu;
       w2[dst] = P.w[i];
       sp2[dst] = sp;
       id2[dst] = P.id[i];
@@ -1040,7 +1223,7 @@ cudaError_t launch_field(const DevParams& P, double* E64, float* E32, double a, 
   return cudaGetLastError();
 }
 
-int sort_bins(int N) { return 2 * N; }
+int sort_bins(int N) { return 4 * N; }
 int scan_blocks(int N) { return (sort_bins(N) + kScanChunk - 1) / kScanChunk; }
 
 cudaError_t launch_sort(const DevParams& P, uint32_t* counts, long long* offsets, long long* bsum, uint32_t* pos2,

@@ -135,6 +135,7 @@ struct pic1d_ctx {
   float *nb = nullptr, *nmu = nullptr, *nx = nullptr;
   uint8_t* zone = nullptr;
   uint8_t* dens_flag = nullptr;
+  uint8_t* fast_cell = nullptr;
   float2* table = nullptr;
   float4* tpair = nullptr;
   Counters* ctr = nullptr;
@@ -255,6 +256,7 @@ DevParams dev_params(pic1d_ctx* c) {
   P.nb = c->nb; P.nmu = c->nmu; P.nx = c->nx;
   P.zone = c->zone;
   P.dens_flag = c->dens_flag;
+  P.fast_cell = c->fast_cell;
   P.dens_cur = c->dens[c->step & 1];
   P.dens_next = c->dens[(c->step + 1) & 1];
   P.cap = c->cap;
@@ -323,6 +325,19 @@ int build_tables(pic1d_ctx* c) {
     hf[cc] = hz[cc] | (cc > 0 ? hz[cc - 1] : 0) | (cc + 1 < N ? hz[cc + 1] : 0);
   CK(dalloc(&c->dens_flag, N), "alloc zone");
   CK(cudaMemcpyAsync(c->dens_flag, hf.data(), N, cudaMemcpyHostToDevice, c->s), "copy zone");
+  // fast cells: no zone cell within two cells, not an end cell
+  std::vector<uint8_t> hq(N);
+  for (int cc = 0; cc < N; ++cc) {
+    bool ok = cc >= 1 && cc <= N - 2;
+    for (int d = -2; d <= 2 && ok; ++d) {
+      const int k = cc + d;
+      if (k >= 0 && k < N && hz[k]) ok = false;
+    }
+    hq[cc] = ok ? 1 : 0;
+  }
+  CK(dalloc(&c->fast_cell, N), "alloc zone");
+  CK(cudaMemcpyAsync(c->fast_cell, hq.data(), N, cudaMemcpyHostToDevice, c->s), "copy zone");
+  CK(cudaStreamSynchronize(c->s), "copy zone");
   CK(cudaMemcpyAsync(c->nb, hb.data(), (N + 1) * sizeof(float), cudaMemcpyHostToDevice, c->s), "copy nodes");
   CK(cudaMemcpyAsync(c->nmu, hmu.data(), (N + 1) * sizeof(float), cudaMemcpyHostToDevice, c->s), "copy nodes");
   CK(cudaMemcpyAsync(c->nx, hx.data(), (N + 1) * sizeof(float), cudaMemcpyHostToDevice, c->s), "copy nodes");
@@ -588,6 +603,7 @@ int pic1d_step(pic1d_ctx* c, int n_steps) {
   for (int k = 0; k < n_steps; ++k) {
     DevParams P = dev_params(c);
     CK(cudaMemsetAsync(c->J, 0, c->N * sizeof(long long), c->s), "clear J");
+    CK(cudaMemsetAsync(&c->st->work, 0, sizeof(unsigned long long), c->s), "clear schedule");
     if (c->timing) {
       int rc = timing_begin(c);
       if (rc != PIC1D_OK) return rc;
@@ -761,7 +777,7 @@ void pic1d_free(pic1d_ctx* c) {
   else cudaDeviceSynchronize();
   free_particles(c);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
-  void* ptrs[] = {c->E64, c->E32, c->J, c->dens[0], c->dens[1], c->nb, c->nmu, c->nx, c->zone, c->dens_flag, c->table,
+  void* ptrs[] = {c->E64, c->E32, c->J, c->dens[0], c->dens[1], c->nb, c->nmu, c->nx, c->zone, c->dens_flag, c->fast_cell, c->table,
                   c->ctr, c->st, c->ke_partial, c->field_partial, c->counts, c->offsets, c->spc, c->slot_log,
                   c->tpair, c->bsum};
   for (void* q : ptrs) cudaFree(q);

@@ -12,6 +12,7 @@ constexpr int kBlock = 256;          // threads per block of the particle kernel
 constexpr int kPerThread = 4;        // particles per thread (128-bit SoA loads)
 constexpr int kTile = kBlock * kPerThread;
 constexpr int kWindow = 2048;        // cells of the shared-memory deposit window
+constexpr int kChunkTiles = 32;      // tiles per dynamically scheduled chunk of the push
 constexpr int kWBits = 12;           // weight fixed point: w_int = rint(w * 2^12)
 constexpr uint32_t kTagRics = 0x52494353u;
 constexpr uint32_t kTagInj = 0x494E4A31u;
@@ -33,6 +34,7 @@ struct StepState {
   long long sorted_total;   // alive count produced by the sort scan
   double inj_acc[2];        // RATE injection accumulators (north, south)
   double field_energy, vc, ext_work, kinetic, ke_lost;
+  unsigned long long work;  // next chunk of the push's dynamic schedule (cleared before each push)
 };
 
 // Everything a particle kernel needs, passed by value.
@@ -69,6 +71,7 @@ struct DevParams {
   const float* nb; const float* nmu; const float* nx;
   const uint8_t* zone;
   const uint8_t* dens_flag; // cells where the pair cap can be tested: zone cells and their neighbours
+  const uint8_t* fast_cell; // no zone cell within two cells and not at a wall: the push's fast path
   long long* dens_cur; long long* dens_next;
   long long cap;
   Counters* ctr;

@@ -16,8 +16,8 @@ from paper_2609_17661_b300 import workloads as W
 torch = pytest.importorskip("torch")
 
 
-def _key(pos, sp, F):
-    return 2 * (pos.astype(np.int64) >> F) + (sp == W.SP_ION)
+def _key(pos, sp, u, F, N):
+    return (2 * (sp == W.SP_ION) + (u < 0)) * N + (pos.astype(np.int64) >> F)
 
 
 @pytest.mark.gpu
@@ -50,7 +50,7 @@ def test_static_sort_matches_context_sort_on_two_calls():
         assert m == ref["pos"].size == int((st["sp"] != 255).sum()), call
         got = {k: v[:m].cpu().numpy() for k, v in out.items()}
         # same key sequence (the sort's order is unique up to order inside a key)
-        kg, kr = _key(got["pos"], got["sp"], F), _key(ref["pos"], ref["sp"], F)
+        kg, kr = _key(got["pos"], got["sp"], got["u"], F, N), _key(ref["pos"], ref["sp"], ref["u"], F, N)
         np.testing.assert_array_equal(kg, kr)
         assert np.all(np.diff(kg) >= 0)
         # same particles under each key
