@@ -36,6 +36,23 @@ BYTES_PER_SLOT = 21      # push: read pos 4 + u 4 + w 4 + sp 1, write pos 4 + u 
 BYTES_PER_DRAW = 8       # id read of a lepton that draws a Philox number
 BYTES_PER_CREATED = 21   # pos, u, w, sp, id written per created particle
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_push
+# launch per slot it read, from one ncu capture of the same kernel sources on
+# a smaller line at the same density (1e8 macroparticles, 26,214 cells: 2.1195
+# GB for 1.0e8 slots); traffic grows in proportion to the slots.  Reported
+# only while the kernel sources hash to the captured ones, else null.
+PUSH_TRAFFIC = {"sources_sha256": "541dfcb4ea8587d475c90db5a5ab3cdd5ba72ac8fb72f7c33893dd5e7d248b7d", "bytes_per_slot": 21.195}
+PUSH_SOURCES = ("paper_2609_17661_b300/csrc/kernels.cu", "paper_2609_17661_b300/csrc/pic1d_internal.h")
+
+
+def _push_sources_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for rel in PUSH_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
 
 def _peaks():
     try:
@@ -100,6 +117,8 @@ class Clocks:
 
 def cfg_for(args):
     cfg = W.config(args.workload)
+    if args.cells:
+        cfg["n_cells"] = args.cells
     if args.workload == "C5":
         cfg["capacity"] = int(args.particles * 1.06) + (1 << 20)
     return cfg
@@ -164,7 +183,8 @@ def run_reference(args):
 
 
 def workload_name(args):
-    return {"C5": f"pair-loaded dipole line r_eq=30, 262144 cells, {args.particles:.3g} macroparticles, "
+    cells = args.cells or 262144
+    return {"C5": f"pair-loaded dipole line r_eq=30, {cells} cells, {args.particles:.3g} macroparticles, "
                   "table drag, pairs on (n_max cap), sort every 20",
             "C2": "dipole line r_eq=20, 65536 cells, 256/cell, surface injection",
             "C1": "dipole line r_eq=4, 1024 cells, 32/cell"}[args.workload]
@@ -233,8 +253,11 @@ def run_gpu(args):
     push_bytes = BYTES_PER_SLOT * units + BYTES_PER_DRAW * draws + BYTES_PER_CREATED * created
     peak, peak_kind = _peaks()
     achieved = push_bytes / (d1["push_ms"] * 1e-3) / 1e9
+    traffic = None
+    if _push_sources_sha256() == PUSH_TRAFFIC["sources_sha256"]:
+        traffic = PUSH_TRAFFIC["bytes_per_slot"] * units / max(launches, 1)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "k_push", "launches": launches,
+            "traffic": traffic, "kernel": "k_push", "launches": launches,
             "bytes_per_launch": push_bytes / max(launches, 1), "mean_launch_ms": d1["push_ms"] / max(launches, 1),
             "peak_kind": peak_kind, "push_share_of_step": d1["push_ms"] / ms}
 
@@ -292,11 +315,11 @@ def run_gpu(args):
 
 def gpu_launches(steps, cfg, step0):
     """Kernels of this library launched in the timed region: per step push,
-    field, finalize (+ inject with surface supply); per sort hist, scan,
-    scatter, done."""
+    field, finalize (+ inject with surface supply); per sort hist, scan
+    reduce, scan top, scan apply, scatter, done."""
     per = 3 + (1 if cfg["inject_mode"] else 0)
     sorts = sum(1 for s in range(step0 + 1, step0 + steps + 1) if s % cfg["sort_every"] == 0)
-    return per * steps + 4 * sorts
+    return per * steps + 6 * sorts
 
 
 def main():
@@ -307,6 +330,8 @@ def main():
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--workload", default="C5", choices=["C5", "C2", "C1"])
     ap.add_argument("--particles", type=float, default=1e9)
+    ap.add_argument("--cells", type=int, default=0,
+                    help="override the line's cell count (smaller lines at the same density for ncu captures)")
     ap.add_argument("--cpu-sample", type=int, default=200000)
     ap.add_argument("--ref-sample", type=int, default=200000)
     ap.add_argument("--no-e2e", action="store_true")

@@ -153,8 +153,10 @@ int pic1d_init(const pic1d_params* p, pic1d_ctx** out);
 /* Replace the particle state and E (Sec. 3 state at time step `step`): n
  * particles in SoA form, pos fixed point (see above), u, w, species, id;
  * E has n_cells values (NULL: zero).  mem = 0 host arrays, 1 device arrays.
- * Grows the capacity if needed.  Errors: EINVAL (n < 0, bad species, pos out
- * of the line), ENOMEM, ECUDA. */
+ * Grows the capacity if needed.  The copied state is validated on the
+ * device; if any particle has a bad species or a position beyond the line
+ * the call returns EINVAL and leaves an empty line (no particles).
+ * Errors: EINVAL (n < 0, bad species, pos out of the line), ENOMEM, ECUDA. */
 int pic1d_set_state(pic1d_ctx* c, int64_t n, const uint32_t* pos, const float* u, const float* w,
                     const uint8_t* sp, const uint64_t* id, const double* E, int64_t step, int mem);
 

@@ -1229,7 +1229,8 @@ int scan_blocks(int N) { return (sort_bins(N) + kScanChunk - 1) / kScanChunk; }
 cudaError_t launch_sort(const DevParams& P, uint32_t* counts, long long* offsets, long long* bsum, uint32_t* pos2,
                         float* u2, float* w2, uint8_t* sp2, uint64_t* id2, int grid, cudaStream_t s) {
   const int B = sort_bins(P.N), nb = scan_blocks(P.N);
-  cudaMemsetAsync(counts, 0, sizeof(uint32_t) * (size_t)B, s);
+  cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(uint32_t) * (size_t)B, s);
+  if (e != cudaSuccess) return e;
   k_hist<<<grid, 256, 0, s>>>(P, counts);
   k_scan_reduce<<<nb, kScanThreads, 0, s>>>(counts, B, bsum);
   k_scan_top<<<1, kScanThreads, 0, s>>>(bsum, nb, P);

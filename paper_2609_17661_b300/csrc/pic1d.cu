@@ -389,22 +389,32 @@ int do_sort(pic1d_ctx* c) {
   return PIC1D_OK;
 }
 
-__global__ void k_validate(const uint32_t* pos, const uint8_t* sp, long long n, long long top,
-                           unsigned long long* bad) {
+// Check a freshly loaded state (species in range, positions on the line) and
+// accumulate the integer lepton weight of every cell that the pair cap reads.
+// Leptons of one warp that share a cell (the usual case for states stored in
+// cell order) add their weights in registers first and issue one atomic.
+__global__ void k_load(DevParams P, long long n, long long top, int want_density, unsigned long long* bad) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const uint8_t s = sp[i];
-  if ((s > 3 && s != PIC1D_SP_DEAD) || (long long)pos[i] >= top) atomicAdd(bad, 1ull);
-}
-
-__global__ void k_density(DevParams P, long long n) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const uint8_t s = P.sp[i];
-  if (s == PIC1D_SP_DEAD || s == PIC1D_SP_ION) return;
-  const int cell = min((int)(P.pos[i] >> P.F), P.N - 1);
-  atomicAdd(reinterpret_cast<unsigned long long*>(P.dens_cur + cell),
-            (unsigned long long)__float2ll_rn(P.w[i] * 4096.0f));
+  const unsigned lane = threadIdx.x & 31;
+  const bool in = i < n;
+  const uint8_t s = in ? P.sp[i] : (uint8_t)PIC1D_SP_DEAD;
+  const uint32_t x = in ? P.pos[i] : 0u;
+  const bool badp = in && ((s > 3 && s != PIC1D_SP_DEAD) || (long long)x >= top);
+  const unsigned bm = __ballot_sync(0xffffffffu, badp);
+  if (bm && lane == 0) atomicAdd(bad, (unsigned long long)__popc(bm));
+  if (!want_density) return;
+  const bool lep = in && !badp && s != PIC1D_SP_DEAD && s != PIC1D_SP_ION;
+  const int cell = lep ? min((int)(x >> P.F), P.N - 1) : -1;
+  long long v = lep ? __float2ll_rn(P.w[i] * 4096.0f) : 0;
+  const unsigned lm = __ballot_sync(0xffffffffu, lep);
+  if (!lm) return;
+  const int c0 = __shfl_sync(0xffffffffu, cell, __ffs(lm) - 1);
+  if (__all_sync(0xffffffffu, !lep || cell == c0)) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long*>(P.dens_cur + c0), (unsigned long long)v);
+  } else if (lep) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(P.dens_cur + cell), (unsigned long long)v);
+  }
 }
 
 // record the start event of one timed push launch and log the slot count it reads
@@ -529,12 +539,6 @@ int pic1d_set_state(pic1d_ctx* c, int64_t n, const uint32_t* pos, const float* u
   if (n < 0 || (n > 0 && (!pos || !u || !w || !sp || !id)) || (mem != 0 && mem != 1) || step < 0)
     return fail(c, PIC1D_EINVAL, "set_state: bad arguments");
   const long long top = (long long)c->N << c->F;
-  if (mem == 0) {
-    for (int64_t i = 0; i < n; ++i) {
-      if ((sp[i] > 3 && sp[i] != PIC1D_SP_DEAD) || (long long)pos[i] >= top)
-        return fail(c, PIC1D_EINVAL, "set_state: species or position out of range at index " + std::to_string(i));
-    }
-  }
   const long long want = c->p.capacity > 0 ? std::max<long long>(c->p.capacity, n) : 2 * n + 4 * kTile;
   if (n > c->cap || (c->p.capacity == 0 && c->cap < want)) {
     int rc = alloc_particles(c, want);
@@ -550,15 +554,6 @@ int pic1d_set_state(pic1d_ctx* c, int64_t n, const uint32_t* pos, const float* u
     CK(cudaMemcpyAsync(c->id[0], id, n * sizeof(uint64_t), k, c->s), "set_state id");
   }
   CK(cudaMemsetAsync(c->sp[0] + n, PIC1D_SP_DEAD, (size_t)(c->alloc - n), c->s), "set_state tail");
-  if (mem == 1 && n > 0) {
-    unsigned long long* bad = c->spc;
-    CK(cudaMemsetAsync(bad, 0, sizeof(unsigned long long), c->s), "validate");
-    k_validate<<<(unsigned)((n + 255) / 256), 256, 0, c->s>>>(c->pos[0], c->sp[0], n, top, bad);
-    unsigned long long hb = 0;
-    CK(cudaMemcpyAsync(&hb, bad, sizeof(hb), cudaMemcpyDeviceToHost, c->s), "validate");
-    CK(cudaStreamSynchronize(c->s), "validate");
-    if (hb) return fail(c, PIC1D_EINVAL, "set_state: " + std::to_string(hb) + " particles with bad species or position");
-  }
   if (E) {
     std::vector<float> e32;
     CK(cudaMemcpyAsync(c->E64, E, c->N * sizeof(double), k, c->s), "set_state E");
@@ -581,10 +576,27 @@ int pic1d_set_state(pic1d_ctx* c, int64_t n, const uint32_t* pos, const float* u
   CK(cudaMemcpyAsync(c->st, &st, sizeof(st), cudaMemcpyHostToDevice, c->s), "set_state st");
   CK(cudaMemsetAsync(c->dens[0], 0, c->N * sizeof(long long), c->s), "set_state dens");
   CK(cudaMemsetAsync(c->dens[1], 0, c->N * sizeof(long long), c->s), "set_state dens");
-  if (n > 0 && c->p.n_max_ppc > 0.0) {
+  if (n > 0) {
+    // validation of the copied state, fused with the pair-cap density
+    unsigned long long* bad = c->spc;
+    CK(cudaMemsetAsync(bad, 0, sizeof(unsigned long long), c->s), "set_state validate");
     DevParams P = dev_params(c);
-    k_density<<<(unsigned)((n + 255) / 256), 256, 0, c->s>>>(P, n);
-    CK(cudaGetLastError(), "set_state density");
+    k_load<<<(unsigned)((n + 255) / 256), 256, 0, c->s>>>(P, n, top, c->p.n_max_ppc > 0.0 ? 1 : 0, bad);
+    CK(cudaGetLastError(), "set_state validate");
+    unsigned long long hb = 0;
+    CK(cudaMemcpyAsync(&hb, bad, sizeof(hb), cudaMemcpyDeviceToHost, c->s), "set_state validate");
+    CK(cudaStreamSynchronize(c->s), "set_state validate");
+    if (hb) {
+      // leave an empty line rather than a half-loaded one
+      StepState empty{};
+      CK(cudaMemcpyAsync(c->st, &empty, sizeof(empty), cudaMemcpyHostToDevice, c->s), "set_state reset");
+      CK(cudaMemsetAsync(c->sp[0], PIC1D_SP_DEAD, (size_t)c->alloc, c->s), "set_state reset");
+      CK(cudaMemsetAsync(c->dens[0], 0, c->N * sizeof(long long), c->s), "set_state reset");
+      CK(cudaMemsetAsync(c->dens[1], 0, c->N * sizeof(long long), c->s), "set_state reset");
+      CK(cudaStreamSynchronize(c->s), "set_state reset");
+      return fail(c, PIC1D_EINVAL, "set_state: " + std::to_string(hb) + " particles with bad species or position "
+                                   "(the line is left empty)");
+    }
   }
   CK(cudaStreamSynchronize(c->s), "set_state sync");
   return PIC1D_OK;

@@ -173,6 +173,39 @@ def test_one_step_parity_scattering_and_pairs():
     assert _relmax(Eg, Eo) <= RTOL
 
 
+def test_pair_cap_parity_over_steps():
+    """The n_max cap: a pair is refused where the cell's lepton weight at the
+    start of the step has reached n_max (integer fixed point).  The cap is set
+    at the median cell weight so that about half the zone refuses; over three
+    steps the weight of the created pairs feeds the next step's test.  The
+    same pairs are created and refused, particle by particle."""
+    N = 1024
+    F = W.fbits(N)
+    st = W.load_beam(W.config("C1"), 40000, gamma_lo=20, gamma_hi=2e4, seed=8)
+    lep = (st["sp"] == 0) | (st["sp"] == 1)
+    wint = np.rint(st["w"].astype(np.float64) * 4096).astype(np.int64)
+    dens = np.bincount(np.minimum(st["pos"][lep].astype(np.int64) >> F, N - 1), weights=wint[lep], minlength=N)
+    med = int(np.median(dens[dens > 0]))
+    cfg = W.config("C1", drag_law=O.DRAG_TABLE, drag_scale=3e-3, n_max_ppc=(med + 0.5) / 4096.0)
+    E = _field0(N)
+    line = _line(cfg)
+    line.set_state(st, E=E, step=17)
+    line.step(3)
+    S = _orc(cfg, st, E, step=17)
+    S.step(3)
+    dg, do = line.diag(), S.diag()
+    assert do["pairs_rejected_nmax"] > 100 and do["pairs_created"] > 100
+    for k in ("pairs_created", "pairs_rejected_nmax", "scatters", "n_alive"):
+        assert dg[k] == do[k], k
+    # positions over three steps: per step the fixed-point quantum plus the
+    # displacement of a velocity that differs by the momentum tolerance (dt RTOL)
+    pos_tol = 3 * (2.0 ** -F + cfg["cfl"] * RTOL)
+    _compare_particles(_gpu_particles(line, N), _by_id(S.particles()), N, pos_tol=pos_tol)
+    Eg, _ = line.fields()
+    Eo, _ = S.fields()
+    assert _relmax(Eg, Eo) <= RTOL
+
+
 def test_drag_plus_pairs_mode_parity():
     N = 1024
     cfg = W.config("C1", drag_law=O.DRAG_TABLE, drag_scale=3e-3, rics_mode=O.RICS_DRAG_PLUS_PAIRS, eta_min=1e-2)
@@ -431,8 +464,8 @@ def test_nonfinite_momentum_reported():
 
 
 def test_invalid_state_rejected():
-    """Bad species or positions beyond the line are refused (host arrays are
-    checked on the host, device arrays by a validation kernel)."""
+    """Bad species or positions beyond the line are refused, from host and
+    from device arrays alike, and the refused call leaves an empty line."""
     from paper_2609_17661_b300 import PicError
     cfg = W.config("C1", n_cells=100)
     st = W.load_random(cfg, 10, seed=1)
@@ -447,6 +480,7 @@ def test_invalid_state_rejected():
     dev = {k: torch.from_numpy(v).cuda() for k, v in st.items()}
     with pytest.raises(PicError):
         line.set_state(dev)
+    assert line.slots() == 0 and sum(line.diag()["n_alive"]) == 0
     good = {k: torch.from_numpy(v).cuda() for k, v in W.load_random(cfg, 10, seed=2).items()}
     line.set_state(good)
     assert line.slots() == 10
