@@ -124,6 +124,12 @@ def lib():
             "orc_drag_half_public": (C.c_double, [C.c_void_p, C.c_double, C.c_double]),
             "orc_gather_public": (C.c_double, [C.c_void_p, C.c_double]),
             "orc_node_interp_public": (C.c_double, [C.c_void_p, C.c_int, C.c_double]),
+            "orc_sur_edge_mu": (C.c_double, [C.c_double, C.c_double, C.c_double]),
+            "orc_sur_baseline": (C.c_double, [C.POINTER(OrcParams), C.c_double, C.c_double, C.c_double, C.c_double]),
+            "orc_sur_point": (None, [C.POINTER(OrcParams), C.c_double, C.c_double, C.c_double, C.c_int, _D]),
+            "orc_sur_sample": (None, [C.POINTER(OrcParams), C.c_uint64, C.c_uint64, C.c_double, C.c_double, _D]),
+            "orc_sur_samples": (None, [C.POINTER(OrcParams), C.c_uint64, C.c_uint64, C.c_int64, C.c_double,
+                                       C.c_double, _D]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -348,3 +354,22 @@ class Sim:
         d = OrcDiag()
         lib().orc_get_diag(self.h, C.byref(d))
         return diag_dict(d)
+
+
+SUR_FIELDS = ("f0", "f1", "f2", "f3", "t1", "t2", "mask", "lnN", "lnN_base", "F", "F_abs", "b", "x", "mu", "u")
+
+
+def sur_point(cfg, r_eq, s_frac, log10g, neg):
+    """One surrogate training sample at a given point (dict of SUR_FIELDS)."""
+    p = make_params(cfg)
+    out = np.zeros(15)
+    lib().orc_sur_point(C.byref(p), r_eq, s_frac, log10g, int(neg), _ptr(out, _D))
+    return dict(zip(SUR_FIELDS, out))
+
+
+def sur_samples(cfg, seed, start, n, r_lo, r_hi):
+    """n Philox-drawn samples from index `start`: array n x 15 (SUR_FIELDS)."""
+    p = make_params(cfg)
+    out = np.zeros((n, 15))
+    lib().orc_sur_samples(C.byref(p), seed, start, n, r_lo, r_hi, _ptr(out, _D))
+    return out

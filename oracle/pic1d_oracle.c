@@ -271,8 +271,11 @@ void orc_radial(const orc_params* p, double u, double x, double b, double mu,
  * = arcsin(1/x) of the radial; mu_k = cos(a) mu_s + sin(a) cos(phi) sqrt(1-mu_s^2).
  * Gauss-Legendre in cos(a) x midpoint rule in phi on [0, pi] (the integrand
  * is even in phi). */
-void orc_disk(const orc_params* p, double u, double x, double b, double mu,
-              double* F, double* Nhat)
+/* The three rate-weighted sums over the disk: sum dN, sum dN * (momentum per
+ * scattering), sum dN * |momentum per scattering| (the last one is the scale
+ * of the surrogate's error metric), in units of the prefactor below. */
+static void orc_disk_sums(const orc_params* p, double u, double x, double b, double mu,
+                          double* sN, double* sF, double* sFa)
 {
   int na = p->quad_n_mu, nph = p->quad_n_phi;
   double gx[256], gw[256];
@@ -283,7 +286,7 @@ void orc_disk(const orc_params* p, double u, double x, double b, double mu,
   double beta = u / gam;
   double cmax = (x > 1.0) ? sqrt(1.0 - 1.0 / (x * x)) : 0.0;   /* cos(alpha_max) */
   double smu = sqrt(fmax(0.0, 1.0 - mu * mu));
-  double sumN = 0.0, sumF = 0.0;
+  double sumN = 0.0, sumF = 0.0, sumFa = 0.0;
   for (int i = 0; i < na; ++i) {
     double ca = cmax + (1.0 - cmax) * 0.5 * (gx[i] + 1.0);
     double wa = (1.0 - cmax) * 0.5 * gw[i];
@@ -297,10 +300,21 @@ void orc_disk(const orc_params* p, double u, double x, double b, double mu,
       double y = eps / th;
       double occ = eps * eps / expm1(y);         /* eps^2/(e^y - 1) */
       double dN = wa * wph * occ;
+      double dNP = dN * gam * b * (mk - beta) / D;   /* dN x momentum per scattering */
       sumN += dN;
-      sumF += dN * gam * b * (mk - beta) / D;    /* momentum per scattering */
+      sumF += dNP;
+      sumFa += fabs(dNP);
     }
   }
+  *sN = sumN; *sF = sumF; *sFa = sumFa;
+}
+
+void orc_disk(const orc_params* p, double u, double x, double b, double mu,
+              double* F, double* Nhat)
+{
+  double sumN, sumF, sumFa;
+  orc_disk_sums(p, u, x, b, mu, &sumN, &sumF, &sumFa);
+  double gam = sqrt(1.0 + u * u);
   double pref = ORC_R_E * p->r_star_cm / (4.0 * ORC_PI * ORC_LAMBDABAR * ORC_LAMBDABAR * gam);
   *Nhat = pref * sumN;
   *F = pref * sumF;
@@ -343,6 +357,113 @@ void orc_build_table(const orc_params* p, double* table)
       }
     }
   }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Learned surrogate of the photon-field quadrature: one training sample.    */
+/*                                                                           */
+/* Per photon direction the momentum given per scattering is gamma b mu~,    */
+/* mu~ = (mu_k - beta)/(1 - beta mu_k) (Sec. 2.2), so the drag is            */
+/*   F^ = gamma b N^ <mu~>,                                                  */
+/* <mu~> the rate-weighted mean of mu~ over the photon directions, which     */
+/* lies in [-1, 1].  The network learns                                      */
+/*   t1 = <mu~>                                                              */
+/*   t2 = max(ln N^, LF) - max(B, LF)                                        */
+/* with the baseline B = ln(0.9 N^_rad(mu_s) + 0.1 N^_rad(mu_e)): N^_rad is  */
+/* the closed form for photons streaming along one direction [contdrag] and  */
+/* mu_e the edge of the stellar disk most favourable to the resonance (the   */
+/* largest 1 - beta mu_k), whose Wien factor dominates the rate near the     */
+/* star.  LF = -20 is the floor below which a rate is negligible (less than  */
+/* one scattering per 1e12 particle-steps; the drag then moves u by less     */
+/* than FP32 rounding).  t1 is masked (weight 0) where ln N^ <= LF.          */
+/* Inputs, each in [-1, 1] over the training box:                            */
+/*   f0 = 2 log10(gamma)/G - 1, f1 = 2 s/L - 1,                              */
+/*   f2 = (log10 b - B_MID)/B_HALF, f3 = sign(u).                            */
+/* ------------------------------------------------------------------------ */
+#define ORC_TAG_SUR    0x53555247u   /* counter word 3 of a sample draw */
+#define ORC_SUR_LF     (-20.0)
+#define ORC_SUR_B_MID  (-1.25)
+#define ORC_SUR_B_HALF 2.75
+
+/* cosine of the disk edge direction with the largest 1 - beta mu_k */
+double orc_sur_edge_mu(double u, double x, double mu)
+{
+  double ths = acos(fmax(-1.0, fmin(1.0, mu)));
+  double am = asin(fmin(1.0, 1.0 / x));
+  return (u >= 0.0) ? cos(fmin(ORC_PI, ths + am)) : cos(fmax(0.0, ths - am));
+}
+
+/* the rate baseline B of the surrogate (see above) */
+double orc_sur_baseline(const orc_params* q, double u, double x, double b, double mu)
+{
+  double Fr, Nr, Fe, Ne;
+  orc_radial(q, u, x, b, mu, &Fr, &Nr);
+  orc_radial(q, u, x, b, orc_sur_edge_mu(u, x, mu), &Fe, &Ne);
+  double N = 0.9 * Nr + 0.1 * Ne;
+  return (N > 0.0) ? log(N) : -745.0;
+}
+
+/* out[15]: f0 f1 f2 f3 | t1 t2 mask | lnN B F^ F^_abs | b x mu u */
+void orc_sur_point(const orc_params* p, double r_eq, double s_frac, double log10g, int neg, double* out)
+{
+  orc_params q = *p;
+  q.r_eq = r_eq;
+  double L = orc_line_length(r_eq);
+  double th = orc_theta_of_s(r_eq, s_frac * L);
+  double x, b, mu;
+  orc_field_at_theta(&q, th, &x, &b, &mu);
+  double gam = pow(10.0, log10g);
+  double au = sqrt(fmax(0.0, gam * gam - 1.0));
+  double u = neg ? -au : au;
+  gam = sqrt(1.0 + u * u);
+  double beta = u / gam;
+  double F, N, Fa, mubar;
+  if (p->photon_model == ORC_PHOTON_DISK) {
+    double sN, sF, sFa;
+    orc_disk_sums(&q, u, x, b, mu, &sN, &sF, &sFa);
+    double pref = ORC_R_E * p->r_star_cm / (4.0 * ORC_PI * ORC_LAMBDABAR * ORC_LAMBDABAR * gam);
+    N = pref * sN; F = pref * sF; Fa = pref * sFa;
+    mubar = (sN > 0.0) ? sF / (gam * b * sN) : (mu - beta) / orc_one_minus_beta_m(u, gam, mu);
+  } else {
+    orc_radial(&q, u, x, b, mu, &F, &N);
+    Fa = fabs(F);
+    mubar = (mu - beta) / orc_one_minus_beta_m(u, gam, mu);
+  }
+  double lnN = (N > 0.0) ? log(N) : -745.0;
+  double lnNr = orc_sur_baseline(&q, u, x, b, mu);
+  out[0] = 2.0 * log10g / p->table_log10g_max - 1.0;
+  out[1] = 2.0 * s_frac - 1.0;
+  out[2] = (log10(b) - ORC_SUR_B_MID) / ORC_SUR_B_HALF;
+  out[3] = neg ? -1.0 : 1.0;
+  out[4] = mubar;
+  out[5] = fmax(lnN, ORC_SUR_LF) - fmax(lnNr, ORC_SUR_LF);
+  out[6] = (lnN > ORC_SUR_LF) ? 1.0 : 0.0;
+  out[7] = lnN; out[8] = lnNr; out[9] = F; out[10] = Fa;
+  out[11] = b; out[12] = x; out[13] = mu; out[14] = u;
+}
+
+/* Sample `index` of a training set: one Philox4x32-10 draw with counter
+ * (index_lo, index_hi, 0, TAG_SUR) and key = seed gives log10 gamma uniform in
+ * [0, G] (log-uniform gamma), s/L uniform in [0, 1), the sign of u from the
+ * top bit of the third word, and r_eq log-uniform in [r_lo, r_hi]. */
+void orc_sur_sample(const orc_params* p, uint64_t seed, uint64_t index, double r_lo, double r_hi, double* out)
+{
+  uint32_t ctr[4] = {(uint32_t)index, (uint32_t)(index >> 32), 0u, ORC_TAG_SUR};
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint32_t r[4];
+  orc_philox4x32_10(ctr, key, r);
+  double log10g = p->table_log10g_max * orc_u24(r[0]);
+  double s_frac = orc_u24(r[1]);
+  int neg = (int)(r[2] >> 31);
+  double r_eq = (r_hi > r_lo) ? r_lo * pow(r_hi / r_lo, orc_u24(r[3])) : r_lo;
+  orc_sur_point(p, r_eq, s_frac, log10g, neg, out);
+}
+
+/* n consecutive samples from index `start` (out: n x 15, row-major) */
+void orc_sur_samples(const orc_params* p, uint64_t seed, uint64_t start, int64_t n, double r_lo, double r_hi,
+                     double* out)
+{
+  for (int64_t i = 0; i < n; ++i) orc_sur_sample(p, seed, start + (uint64_t)i, r_lo, r_hi, out + 15 * i);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -265,3 +265,30 @@ def load_pair_loaded(cfg: dict, total: int, seed=None, chunk_cells=8192, out=Non
         off = fill_pair_loaded(cfg, out, c0, min(N, c0 + chunk_cells), counts, off, seed=seed)
     assert off == n
     return out
+
+
+# ---------------------------------------------------------------- surrogate
+# MLP 4 -> 64 -> 64 -> 64 -> 2, parameters flat in the C ABI's layout
+# (W[out][in] then b, layer by layer): 8770 values.
+SUR_LAYERS = ((64, 4), (64, 64), (64, 64), (2, 64))
+SUR_N_PARAMS = sum(o * i + o for o, i in SUR_LAYERS)
+
+# Training of the learned surrogate on the r_eq = 20 line: 1e7 quadrature
+# samples (log-uniform gamma in [1, 1e8], uniform s), 20 epochs of Adam at
+# lr 1e-3 with batches of 8192.
+SUR_TRAIN = dict(n_samples=10_000_000, epochs=20, batch=8192, lr=1e-3, r_lo=20.0, r_hi=20.0, seed=3,
+                 n_val=100_000, val_seed=1003)
+# one network for every line of the r_eq in [2, 30] ensemble
+SUR_TRAIN_ENSEMBLE = dict(SUR_TRAIN, r_lo=2.0, r_hi=30.0)
+
+
+def sur_init_params(seed: int = 0) -> np.ndarray:
+    """Seeded initial parameters (FP32): every weight and bias uniform in
+    +-1/sqrt(fan_in) of its layer."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for o, i in SUR_LAYERS:
+        bound = 1.0 / math.sqrt(i)
+        out.append(rng.uniform(-bound, bound, o * i))
+        out.append(rng.uniform(-bound, bound, o))
+    return np.concatenate(out).astype(np.float32)
