@@ -53,6 +53,7 @@ extern "C" {
 #define PIC1D_ENOMEM     -2   /* device allocation failed                 */
 #define PIC1D_ECUDA      -3   /* CUDA runtime error                       */
 #define PIC1D_ENUMERIC   -4   /* non-finite momentum met in a step        */
+#define PIC1D_ETIMEOUT   -5   /* a bounded wait inside a kernel gave up   */
 
 /* photon field model (Sec. 2.2, App. B.2) */
 #define PIC1D_PHOTON_RADIAL 0 /* radially streaming photons, solid angle pi/x^2 (Eq. contdrag) */
@@ -250,6 +251,97 @@ int pic1d_variant_info(int variant, int* particles_per_thread, int* min_blocks_p
 int pic1d_sort_static(int32_t n_cells, int64_t n, const uint32_t* pos, const float* u, const float* w,
                       const uint8_t* sp, const uint64_t* id, uint32_t* pos_out, float* u_out, float* w_out,
                       uint8_t* sp_out, uint64_t* id_out, int64_t* n_out, void* cuda_stream);
+
+/* ------------------------------------------------------------------------
+ * Learned surrogate of the photon-field quadrature (Sec. 2.2, Eq.
+ * scatteringNdot and the momentum given per scattering).
+ *
+ * An MLP 4 -> 64 -> 64 -> 64 -> 2 with SiLU activations, BF16 weights and
+ * activations and FP32 accumulation.  Per photon direction a scattering gives
+ * the lepton the momentum gamma b mu~ along s (mu~ the cosine of the
+ * direction in the lepton frame), so F^ = gamma b N^ <mu~>, <mu~> the
+ * rate-weighted mean of mu~ (in [-1, 1]).  The network maps
+ *   f0 = 2 log10(gamma)/G - 1, f1 = 2 s/L - 1, f2 = (log10 b + 1.25)/2.75,
+ *   f3 = sign(u)
+ * to y0 ~ <mu~> and y1 ~ max(ln N^, -30) - max(B, -30), where B = ln(0.9
+ * N^_rad(mu_s) + 0.1 N^_rad(mu_e)) is the closed form for photons along one
+ * direction [contdrag] taken along the radial and along the disk edge most
+ * favourable to the resonance; -30 clamps the targets, and the network is
+ * judged where ln N^ > -20 (below it a rate is negligible).  G is the
+ * context's table_log10g_max; the quadrature uses the context's photon
+ * model, kT, quad_n_mu x quad_n_phi nodes, b_star and b_convention.
+ *
+ * Parameters: PIC1D_SUR_N_PARAMS FP32 values, layer by layer W[out][in]
+ * then b (W1 64x4, b1, W2 64x64, b2, W3 64x64, b3, W4 2x64, b4).  The
+ * context keeps FP32 master values; the tensor-core layers use the BF16
+ * roundings of W2 and W3 (and BF16 activations), the rest stays FP32.
+ *
+ * Sample records (PIC1D_SUR_RECORD floats each, device memory):
+ *   0-3 f0..f3 | 4 t1 = <mu~> | 5 t2 (the y1 target) | 6 mask (1 where
+ *   ln N^ > -30) | 7 B | 8 ln N^ | 9 F^ | 10 F^_abs (the quadrature of
+ *   |momentum| x rate, the scale of the drag error) | 11 gamma | 12 b |
+ *   13 u | 14 x = r/R* | 15 mu_s
+ * Loss of a batch: mean of mask (y0 - t1)^2 + (y1 - t2)^2.
+ * ------------------------------------------------------------------------ */
+#define PIC1D_SUR_N_PARAMS 8770
+#define PIC1D_SUR_RECORD 16
+
+typedef struct {
+  int64_t n_samples;   /* training samples (1e7)                           */
+  int32_t epochs;      /* 20                                               */
+  int32_t batch;       /* 8192 (a multiple of 128)                         */
+  double lr;           /* Adam learning rate (1e-3; beta 0.9, 0.999, eps 1e-8) */
+  double lr_final;     /* > 0: cosine decay from lr to lr_final over the run; <= 0: constant */
+  double r_lo, r_hi;   /* r_eq of the sampled lines, log-uniform (equal: one line) */
+  uint64_t seed;       /* Philox key of the training samples and the shuffles */
+  int64_t n_val;       /* held-out validation samples                      */
+  uint64_t val_seed;   /* their Philox key                                 */
+} pic1d_train_cfg;
+
+typedef struct {
+  int64_t steps, n_samples, n_val, val_count;   /* val_count: records with ln N^ > -20 */
+  double samples_ms, train_ms, val_ms;          /* device time of each phase */
+  double loss_first, loss_last;                 /* mean batch loss, first and last step */
+  double drag_err_max, drag_err_p99, drag_err_median;  /* |F_nn - F_q| / (|F_q| + F_abs) */
+  double lnN_err_max, lnN_err_p99, lnN_err_median;     /* |ln N_nn - ln N_q| */
+} pic1d_train_report;
+
+/* Set (host, PIC1D_SUR_N_PARAMS values) or read back the master parameters.
+ * Setting resets the Adam moments and step count.  Errors: EINVAL, ECUDA. */
+int pic1d_sur_set_params(pic1d_ctx* c, const float* theta);
+int pic1d_sur_get_params(pic1d_ctx* c, float* theta);
+
+/* n sample records from index `start` of the set keyed by `seed` (one
+ * Philox4x32-10 draw per record, counter (index, 0, 0x53555247), key = seed:
+ * log10 gamma = G U0, s/L = U1, sign from the top bit of word 2, r_eq =
+ * r_lo (r_hi/r_lo)^U3, U = (word >> 8) 2^-24), by FP64 quadrature on the
+ * device.  out: device, n x PIC1D_SUR_RECORD floats.  Errors: EINVAL, ECUDA. */
+int pic1d_sur_samples(pic1d_ctx* c, uint64_t seed, uint64_t start, int64_t n, double r_lo, double r_hi,
+                      float* out_dev);
+
+/* Gradient of the mean loss over n records (device, 1 <= n <= 65536) at the
+ * current parameters: grad_host receives PIC1D_SUR_N_PARAMS values, loss_host
+ * the mean loss.  Errors: EINVAL, ECUDA, ETIMEOUT. */
+int pic1d_sur_grad(pic1d_ctx* c, const float* samples_dev, int64_t n, float* grad_host, double* loss_host);
+
+/* `steps` Adam steps on consecutive batches of `batch` records (device),
+ * batch k taking records k*batch .. k*batch+batch-1 modulo n (no shuffle).
+ * Errors: EINVAL, ECUDA, ETIMEOUT. */
+int pic1d_sur_train_steps(pic1d_ctx* c, const float* samples_dev, int64_t n, int32_t batch, int32_t steps,
+                          double lr);
+
+/* Network outputs for n rows of `stride` floats (device; inputs f0..f3 in
+ * the first four columns): out (device, n x 4) = y0, y1, dy0/df0, dy1/df0.
+ * Errors: EINVAL, ECUDA, ETIMEOUT. */
+int pic1d_sur_infer(pic1d_ctx* c, const float* feat_dev, int32_t stride, int64_t n, float* out_dev);
+
+/* Train the context's network from its current parameters: n_samples records
+ * by quadrature (seed), epochs x (n_samples / batch) Adam steps over
+ * batches drawn without replacement (a fresh affine permutation of the
+ * records per epoch), then the drag and rate errors on n_val held-out
+ * records (val_seed).  rep (host) receives the timings and errors.
+ * Errors: EINVAL, ENOMEM, ECUDA, ETIMEOUT. */
+int pic1d_train_surrogate(pic1d_ctx* c, const pic1d_train_cfg* cfg, pic1d_train_report* rep);
 
 /* Message of the last error on this context (never NULL). */
 const char* pic1d_last_error(const pic1d_ctx* c);

@@ -368,20 +368,23 @@ void orc_build_table(const orc_params* p, double* table)
 /* <mu~> the rate-weighted mean of mu~ over the photon directions, which     */
 /* lies in [-1, 1].  The network learns                                      */
 /*   t1 = <mu~>                                                              */
-/*   t2 = max(ln N^, LF) - max(B, LF)                                        */
+/*   t2 = max(ln N^, LT) - max(B, LT)                                        */
 /* with the baseline B = ln(0.9 N^_rad(mu_s) + 0.1 N^_rad(mu_e)): N^_rad is  */
 /* the closed form for photons streaming along one direction [contdrag] and  */
 /* mu_e the edge of the stellar disk most favourable to the resonance (the   */
 /* largest 1 - beta mu_k), whose Wien factor dominates the rate near the     */
-/* star.  LF = -20 is the floor below which a rate is negligible (less than  */
-/* one scattering per 1e12 particle-steps; the drag then moves u by less     */
-/* than FP32 rounding).  t1 is masked (weight 0) where ln N^ <= LF.          */
+/* star.  Two floors: rates below LE = -20 are negligible (less than one     */
+/* scattering per 1e12 particle-steps; the drag then moves u by less than    */
+/* FP32 rounding), and the surrogate is judged only above LE; the targets   */
+/* are clamped at LT = -30, ten e-folds lower, so that the kink of the clamp */
+/* lies outside the judged region.  t1 is masked (weight 0) where ln N^ <=   */
+/* LT.                                                                       */
 /* Inputs, each in [-1, 1] over the training box:                            */
 /*   f0 = 2 log10(gamma)/G - 1, f1 = 2 s/L - 1,                              */
 /*   f2 = (log10 b - B_MID)/B_HALF, f3 = sign(u).                            */
 /* ------------------------------------------------------------------------ */
 #define ORC_TAG_SUR    0x53555247u   /* counter word 3 of a sample draw */
-#define ORC_SUR_LF     (-20.0)
+#define ORC_SUR_LT     (-30.0)   /* clamp of the targets */
 #define ORC_SUR_B_MID  (-1.25)
 #define ORC_SUR_B_HALF 2.75
 
@@ -436,8 +439,8 @@ void orc_sur_point(const orc_params* p, double r_eq, double s_frac, double log10
   out[2] = (log10(b) - ORC_SUR_B_MID) / ORC_SUR_B_HALF;
   out[3] = neg ? -1.0 : 1.0;
   out[4] = mubar;
-  out[5] = fmax(lnN, ORC_SUR_LF) - fmax(lnNr, ORC_SUR_LF);
-  out[6] = (lnN > ORC_SUR_LF) ? 1.0 : 0.0;
+  out[5] = fmax(lnN, ORC_SUR_LT) - fmax(lnNr, ORC_SUR_LT);
+  out[6] = (lnN > ORC_SUR_LT) ? 1.0 : 0.0;
   out[7] = lnN; out[8] = lnNr; out[9] = F; out[10] = Fa;
   out[11] = b; out[12] = x; out[13] = mu; out[14] = u;
 }

@@ -10,11 +10,15 @@ training samples in ``pic1d_oracle.c`` (``orc_sur_point``):
     inputs  f0 = 2 log10(gamma)/G - 1, f1 = 2 s/L - 1,
             f2 = (log10 b - B_MID)/B_HALF, f3 = sign(u)
     outputs y0 ~ <mu~>  (rate-weighted mean aberrated cosine, in [-1, 1])
-            y1 ~ max(ln N^, LF) - max(B, LF)  (rate relative to a closed-form
+            y1 ~ max(ln N^, LT) - max(B, LT)  (rate relative to a closed-form
                                               baseline B)
 
-from which the drag and rate follow as ``ln N^ = max(B, LF) + y1`` and
-``F^ = gamma b N^ y0``.
+from which the drag and rate follow as ``ln N^ = max(B, LT) + y1`` and
+``F^ = gamma b N^ y0``.  LT = -30 clamps the targets; the surrogate is
+judged where ln N^ > LE = -20 (below it a rate is negligible).
+
+The tensor-core layers (W2, W3 and the activations h1, h2 that feed them)
+are BF16 on the GPU; layers 1 and 4 and the biases are FP32.
 
 Parameters are one flat vector in the layout of the C ABI (PyTorch's
 Linear convention, W[out][in]): W1[64][4] b1[64] W2[64][64] b2[64] W3[64][64]
@@ -35,7 +39,8 @@ import math
 import numpy as np
 
 SIZES = ((64, 4), (64, 64), (64, 64), (2, 64))   # (out, in) per layer
-LF = -20.0          # rate floor (ln N^) of the targets
+LT = -30.0          # clamp of the rate targets (ln N^)
+LE = -20.0          # floor of the judged region (ln N^)
 B_MID, B_HALF = -1.25, 2.75
 BASE_MIX = (0.9, 0.1)  # weights of N^_rad(mu_s) and N^_rad(mu_edge) in the baseline
 
@@ -153,7 +158,7 @@ def features(log10g, s_frac, b, u, log10g_max=8.0):
 
 def reconstruct(Y, base, gamma, b):
     """(F^, ln N^) from the outputs and the baseline B at each point."""
-    lnN = np.maximum(base, LF) + Y[:, 1]
+    lnN = np.maximum(base, LT) + Y[:, 1]
     F = gamma * b * np.exp(lnN) * Y[:, 0]
     return F, lnN
 
@@ -168,6 +173,15 @@ def bf16(x):
     f = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
     r = ((f + 0x7FFF + ((f >> 16) & 1)) >> 16) << 16
     return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def bf16_tensor_layers(theta):
+    """The parameters as the GPU uses them: W2 and W3 rounded to BF16."""
+    th = np.array(theta, dtype=np.float64)
+    for layer in (1, 2):
+        kw, kb = OFFSETS[layer]
+        th[kw:kb] = bf16(th[kw:kb])
+    return th
 
 
 def init_uniform_bound(layer):

@@ -179,4 +179,57 @@ class Line:
         return J
 
 
+    # ------------------------------------------------------------ surrogate
+    def sur_set_params(self, theta):
+        """pic1d_sur_set_params from a host array of 8770 FP32 values."""
+        a = np.ascontiguousarray(theta, dtype=np.float32)
+        assert a.size == _lib.SUR_N_PARAMS
+        self._check(self.L.pic1d_sur_set_params(self.h, C.c_void_p(a.ctypes.data)))
+
+    def sur_get_params(self):
+        a = np.zeros(_lib.SUR_N_PARAMS, np.float32)
+        self._check(self.L.pic1d_sur_get_params(self.h, C.c_void_p(a.ctypes.data)))
+        return a
+
+    def sur_samples(self, seed, start, n, r_lo, r_hi):
+        """pic1d_sur_samples into a new CUDA tensor of n x 16 records."""
+        import torch
+        out = torch.empty((max(int(n), 1), _lib.SUR_RECORD), dtype=torch.float32, device="cuda")
+        self._check(self.L.pic1d_sur_samples(self.h, int(seed), int(start), int(n), float(r_lo), float(r_hi),
+                                             C.c_void_p(out.data_ptr())))
+        return out[:int(n)]
+
+    def sur_grad(self, records):
+        """pic1d_sur_grad over a CUDA tensor of records: (gradient, mean loss)."""
+        assert records.is_cuda and records.is_contiguous()
+        g = np.zeros(_lib.SUR_N_PARAMS, np.float32)
+        loss = C.c_double()
+        self._check(self.L.pic1d_sur_grad(self.h, C.c_void_p(records.data_ptr()), int(records.shape[0]),
+                                          C.c_void_p(g.ctypes.data), C.byref(loss)))
+        return g, loss.value
+
+    def sur_train_steps(self, records, batch, steps, lr):
+        assert records.is_cuda and records.is_contiguous()
+        self._check(self.L.pic1d_sur_train_steps(self.h, C.c_void_p(records.data_ptr()), int(records.shape[0]),
+                                                 int(batch), int(steps), float(lr)))
+
+    def sur_infer(self, rows):
+        """pic1d_sur_infer on a CUDA tensor (inputs in the first 4 columns): n x 4 tensor."""
+        import torch
+        assert rows.is_cuda and rows.is_contiguous() and rows.dim() == 2
+        out = torch.empty((max(rows.shape[0], 1), 4), dtype=torch.float32, device="cuda")
+        self._check(self.L.pic1d_sur_infer(self.h, C.c_void_p(rows.data_ptr()), int(rows.shape[1]),
+                                           int(rows.shape[0]), C.c_void_p(out.data_ptr())))
+        return out[:rows.shape[0]]
+
+    def train_surrogate(self, n_samples, epochs, batch, lr, r_lo, r_hi, seed, n_val, val_seed,
+                        lr_final=0.0) -> dict:
+        """pic1d_train_surrogate: returns the report as a dict."""
+        cfg = _lib.TrainCfg(int(n_samples), int(epochs), int(batch), float(lr), float(lr_final), float(r_lo),
+                            float(r_hi), int(seed), int(n_val), int(val_seed))
+        rep = _lib.TrainReport()
+        self._check(self.L.pic1d_train_surrogate(self.h, C.byref(cfg), C.byref(rep)))
+        return {name: getattr(rep, name) for name, _ in _lib.TrainReport._fields_}
+
+
 from . import workloads  # noqa: E402

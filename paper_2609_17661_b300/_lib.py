@@ -52,6 +52,23 @@ class Diag(C.Structure):
 
 
 # exported symbols and their signatures (the declarations of include/pic1d.h)
+class TrainCfg(C.Structure):
+    _fields_ = [("n_samples", C.c_int64), ("epochs", C.c_int32), ("batch", C.c_int32), ("lr", C.c_double),
+                ("lr_final", C.c_double), ("r_lo", C.c_double), ("r_hi", C.c_double), ("seed", C.c_uint64), ("n_val", C.c_int64),
+                ("val_seed", C.c_uint64)]
+
+
+class TrainReport(C.Structure):
+    _fields_ = [("steps", C.c_int64), ("n_samples", C.c_int64), ("n_val", C.c_int64), ("val_count", C.c_int64),
+                ("samples_ms", C.c_double), ("train_ms", C.c_double), ("val_ms", C.c_double),
+                ("loss_first", C.c_double), ("loss_last", C.c_double),
+                ("drag_err_max", C.c_double), ("drag_err_p99", C.c_double), ("drag_err_median", C.c_double),
+                ("lnN_err_max", C.c_double), ("lnN_err_p99", C.c_double), ("lnN_err_median", C.c_double)]
+
+
+SUR_N_PARAMS = 8770
+SUR_RECORD = 16
+
 SIGNATURES = {
     "pic1d_init": (C.c_int, [C.POINTER(Params), C.POINTER(C.c_void_p)]),
     "pic1d_set_state": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -70,6 +87,14 @@ SIGNATURES = {
     "pic1d_set_variant": (C.c_int, [C.c_void_p, C.c_int]),
     "pic1d_variant_info": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "pic1d_sort_static": (C.c_int, [C.c_int32, C.c_int64] + [C.c_void_p] * 11 + [C.c_void_p]),
+    "pic1d_sur_set_params": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "pic1d_sur_get_params": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "pic1d_sur_samples": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_int64, C.c_double, C.c_double,
+                                    C.c_void_p]),
+    "pic1d_sur_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.POINTER(C.c_double)]),
+    "pic1d_sur_train_steps": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_double]),
+    "pic1d_sur_infer": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int64, C.c_void_p]),
+    "pic1d_train_surrogate": (C.c_int, [C.c_void_p, C.POINTER(TrainCfg), C.POINTER(TrainReport)]),
     "pic1d_last_error": (C.c_char_p, [C.c_void_p]),
     "pic1d_free": (None, [C.c_void_p]),
 }

@@ -11,6 +11,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <numeric>
+#include <random>
 #include <string>
 #include <vector>
 
@@ -160,6 +162,14 @@ struct pic1d_ctx {
   long long timed = 0;
   double timed_ms = 0.0;
   long long timed_slots = 0;
+  // learned surrogate (allocated on first use)
+  bool sur_on = false;
+  SurBufs sur{};
+  int sur_t = 0;                 // Adam steps taken since the parameters were set
+  double* sur_gx = nullptr;      // Gauss-Legendre nodes of the sample quadrature
+  double* sur_gw = nullptr;
+  float* sur_grad = nullptr;
+  float* sur_loss = nullptr;     // loss sum of a gradient call
 };
 
 namespace {
@@ -778,6 +788,240 @@ int pic1d_timing(pic1d_ctx* c, int on) {
   return PIC1D_OK;
 }
 
+// ------------------------------------------------------------- surrogate
+namespace {
+
+constexpr int kSurMaxTiles = 512;   // rows per gradient launch: 512 x 128
+
+int sur_ensure(pic1d_ctx* c) {
+  if (c->sur_on) return PIC1D_OK;
+  SurBufs& B = c->sur;
+  B.max_tiles = kSurMaxTiles;
+  CK(dalloc(&B.master, W_N_PARAMS), "surrogate alloc");
+  CK(dalloc(&B.m, W_N_PARAMS), "surrogate alloc");
+  CK(dalloc(&B.v, W_N_PARAMS), "surrogate alloc");
+  CK(dalloc(&B.img, 32768), "surrogate alloc");
+  CK(dalloc(&B.small, 580), "surrogate alloc");
+  CK(dalloc(&B.part, (size_t)kSurMaxTiles * W_N_PARAMS), "surrogate alloc");
+  CK(dalloc(&B.loss_part, kSurMaxTiles), "surrogate alloc");
+  CK(dalloc(&B.err, 1), "surrogate alloc");
+  CK(dalloc(&c->sur_grad, W_N_PARAMS), "surrogate alloc");
+  CK(dalloc(&c->sur_loss, 1), "surrogate alloc");
+  CK(cudaMemsetAsync(B.master, 0, W_N_PARAMS * sizeof(float), c->s), "surrogate init");
+  CK(cudaMemsetAsync(B.m, 0, W_N_PARAMS * sizeof(float), c->s), "surrogate init");
+  CK(cudaMemsetAsync(B.v, 0, W_N_PARAMS * sizeof(float), c->s), "surrogate init");
+  CK(cudaMemsetAsync(B.img, 0, 32768, c->s), "surrogate init");
+  CK(cudaMemsetAsync(B.small, 0, 580 * sizeof(float), c->s), "surrogate init");
+  CK(cudaMemsetAsync(B.err, 0, sizeof(unsigned), c->s), "surrogate init");
+  std::vector<double> gx, gw;
+  legendre_nodes(std::max(1, c->p.quad_n_mu), gx, gw);
+  CK(dalloc(&c->sur_gx, gx.size()), "surrogate alloc");
+  CK(dalloc(&c->sur_gw, gw.size()), "surrogate alloc");
+  CK(cudaMemcpyAsync(c->sur_gx, gx.data(), gx.size() * sizeof(double), cudaMemcpyHostToDevice, c->s), "surrogate");
+  CK(cudaMemcpyAsync(c->sur_gw, gw.data(), gw.size() * sizeof(double), cudaMemcpyHostToDevice, c->s), "surrogate");
+  CK(cudaStreamSynchronize(c->s), "surrogate init");
+  c->sur_on = true;
+  return PIC1D_OK;
+}
+
+SurPhys sur_phys(const pic1d_ctx* c) {
+  SurPhys Q;
+  Q.theta_T = c->p.kT_keV / kMeKeV;
+  Q.pref = kRe * c->p.r_star_cm / (4.0 * kPi * kLbar * kLbar);
+  Q.log10g_max = c->p.table_log10g_max;
+  Q.b_star = c->p.b_star;
+  Q.b_convention = c->p.b_convention;
+  Q.photon_model = c->p.photon_model;
+  Q.n_mu = std::max(1, c->p.quad_n_mu);
+  Q.n_phi = std::max(1, c->p.quad_n_phi);
+  Q.gx = c->sur_gx;
+  Q.gw = c->sur_gw;
+  return Q;
+}
+
+// the error flag of the surrogate's kernels (bounded waits that gave up)
+int sur_check(pic1d_ctx* c) {
+  unsigned h = 0;
+  CK(cudaMemcpyAsync(&h, c->sur.err, sizeof(h), cudaMemcpyDeviceToHost, c->s), "surrogate status");
+  CK(cudaStreamSynchronize(c->s), "surrogate status");
+  if (h) return fail(c, PIC1D_ETIMEOUT, "surrogate: a wait for the tensor cores gave up");
+  return PIC1D_OK;
+}
+
+}  // namespace
+
+int pic1d_sur_set_params(pic1d_ctx* c, const float* theta) {
+  if (!c || !theta) return fail(c, PIC1D_EINVAL, "sur_set_params: NULL argument");
+  int rc = sur_ensure(c);
+  if (rc != PIC1D_OK) return rc;
+  CK(cudaMemcpyAsync(c->sur.master, theta, W_N_PARAMS * sizeof(float), cudaMemcpyHostToDevice, c->s), "sur_set_params");
+  CK(cudaMemsetAsync(c->sur.m, 0, W_N_PARAMS * sizeof(float), c->s), "sur_set_params");
+  CK(cudaMemsetAsync(c->sur.v, 0, W_N_PARAMS * sizeof(float), c->s), "sur_set_params");
+  CK(sur_launch_update(c->sur, 0, 2, 0.0f, 1, nullptr, nullptr, c->s), "sur_set_params");
+  CK(cudaStreamSynchronize(c->s), "sur_set_params");
+  c->sur_t = 0;
+  return PIC1D_OK;
+}
+
+int pic1d_sur_get_params(pic1d_ctx* c, float* theta) {
+  if (!c || !theta) return fail(c, PIC1D_EINVAL, "sur_get_params: NULL argument");
+  int rc = sur_ensure(c);
+  if (rc != PIC1D_OK) return rc;
+  CK(cudaMemcpyAsync(theta, c->sur.master, W_N_PARAMS * sizeof(float), cudaMemcpyDeviceToHost, c->s), "sur_get_params");
+  CK(cudaStreamSynchronize(c->s), "sur_get_params");
+  return PIC1D_OK;
+}
+
+int pic1d_sur_samples(pic1d_ctx* c, uint64_t seed, uint64_t start, int64_t n, double r_lo, double r_hi,
+                      float* out_dev) {
+  if (!c) return PIC1D_EINVAL;
+  if (n < 0 || (n > 0 && !out_dev) || !(r_lo >= 1.0) || !(r_hi >= r_lo))
+    return fail(c, PIC1D_EINVAL, "sur_samples: bad arguments (need n >= 0, 1 <= r_lo <= r_hi)");
+  int rc = sur_ensure(c);
+  if (rc != PIC1D_OK) return rc;
+  CK(sur_launch_samples(sur_phys(c), seed, start, n, r_lo, r_hi, out_dev, c->s), "sur_samples");
+  CK(cudaStreamSynchronize(c->s), "sur_samples");
+  return PIC1D_OK;
+}
+
+int pic1d_sur_grad(pic1d_ctx* c, const float* samples_dev, int64_t n, float* grad_host, double* loss_host) {
+  if (!c) return PIC1D_EINVAL;
+  if (!samples_dev || !grad_host || n < 1 || n > (int64_t)kSurMaxTiles * 128)
+    return fail(c, PIC1D_EINVAL, "sur_grad: bad arguments (1 <= n <= 65536)");
+  int rc = sur_ensure(c);
+  if (rc != PIC1D_OK) return rc;
+  const int tiles = (int)((n + 127) / 128);
+  float* loss_d = c->sur_loss;
+  CK(sur_launch_train(c->sur, samples_dev, n, 1, 0, 0, (int)n, c->s), "sur_grad");
+  CK(sur_launch_update(c->sur, tiles, 0, 0.0f, 1, c->sur_grad, loss_d, c->s), "sur_grad");
+  float hl = 0.0f;
+  CK(cudaMemcpyAsync(grad_host, c->sur_grad, W_N_PARAMS * sizeof(float), cudaMemcpyDeviceToHost, c->s), "sur_grad");
+  CK(cudaMemcpyAsync(&hl, loss_d, sizeof(float), cudaMemcpyDeviceToHost, c->s), "sur_grad");
+  CK(cudaStreamSynchronize(c->s), "sur_grad");
+  if (loss_host) *loss_host = (double)hl / (double)n;
+  return sur_check(c);
+}
+
+int pic1d_sur_train_steps(pic1d_ctx* c, const float* samples_dev, int64_t n, int32_t batch, int32_t steps,
+                          double lr) {
+  if (!c) return PIC1D_EINVAL;
+  if (!samples_dev || n < 1 || batch < 1 || batch > kSurMaxTiles * 128 || steps < 0 || !(lr > 0.0))
+    return fail(c, PIC1D_EINVAL, "sur_train_steps: bad arguments");
+  int rc = sur_ensure(c);
+  if (rc != PIC1D_OK) return rc;
+  const int tiles = (batch + 127) / 128;
+  for (int k = 0; k < steps; ++k) {
+    CK(sur_launch_train(c->sur, samples_dev, n, 1, 0, (long long)k * batch, batch, c->s), "sur_train_steps");
+    CK(sur_launch_update(c->sur, tiles, 1, (float)lr, ++c->sur_t, nullptr, nullptr, c->s), "sur_train_steps");
+  }
+  CK(cudaStreamSynchronize(c->s), "sur_train_steps");
+  return sur_check(c);
+}
+
+int pic1d_sur_infer(pic1d_ctx* c, const float* feat_dev, int32_t stride, int64_t n, float* out_dev) {
+  if (!c) return PIC1D_EINVAL;
+  if (n < 0 || stride < 4 || (n > 0 && (!feat_dev || !out_dev)))
+    return fail(c, PIC1D_EINVAL, "sur_infer: bad arguments");
+  int rc = sur_ensure(c);
+  if (rc != PIC1D_OK) return rc;
+  CK(sur_launch_infer(c->sur, feat_dev, stride, n, out_dev, c->sms, c->s), "sur_infer");
+  CK(cudaStreamSynchronize(c->s), "sur_infer");
+  return sur_check(c);
+}
+
+int pic1d_train_surrogate(pic1d_ctx* c, const pic1d_train_cfg* cfg, pic1d_train_report* rep) {
+  if (!c) return PIC1D_EINVAL;
+  if (!cfg || !rep || cfg->n_samples < cfg->batch || cfg->batch < 128 || cfg->batch % 128 != 0 ||
+      cfg->batch > kSurMaxTiles * 128 || cfg->epochs < 0 || !(cfg->lr > 0.0) || !(cfg->r_lo >= 1.0) ||
+      !(cfg->r_hi >= cfg->r_lo) || cfg->n_val < 0)
+    return fail(c, PIC1D_EINVAL, "train_surrogate: bad configuration");
+  int rc = sur_ensure(c);
+  if (rc != PIC1D_OK) return rc;
+  *rep = pic1d_train_report{};
+  const long long n = cfg->n_samples, nv = cfg->n_val;
+  const int tiles = cfg->batch / 128;
+  const long long per_epoch = n / cfg->batch;
+  const long long steps = per_epoch * cfg->epochs;
+  float *rec = nullptr, *vrec = nullptr, *vy = nullptr, *verr = nullptr, *losses = nullptr;
+  cudaEvent_t e0, e1, e2, e3;
+  CK(cudaEventCreate(&e0), "train");
+  CK(cudaEventCreate(&e1), "train");
+  CK(cudaEventCreate(&e2), "train");
+  CK(cudaEventCreate(&e3), "train");
+  auto cleanup = [&]() {
+    cudaFree(rec); cudaFree(vrec); cudaFree(vy); cudaFree(verr); cudaFree(losses);
+    cudaEventDestroy(e0); cudaEventDestroy(e1); cudaEventDestroy(e2); cudaEventDestroy(e3);
+  };
+  cudaError_t e = dalloc(&rec, (size_t)n * kSurRecord);
+  if (e == cudaSuccess && nv > 0) e = dalloc(&vrec, (size_t)nv * kSurRecord);
+  if (e == cudaSuccess && nv > 0) e = dalloc(&vy, (size_t)nv * 4);
+  if (e == cudaSuccess && nv > 0) e = dalloc(&verr, (size_t)nv * 2);
+  if (e == cudaSuccess && steps > 0) e = dalloc(&losses, (size_t)steps);
+  if (e != cudaSuccess) { cleanup(); return cuda_fail(c, e, "train_surrogate alloc"); }
+  const SurPhys Q = sur_phys(c);
+  e = cudaEventRecord(e0, c->s);
+  if (e == cudaSuccess) e = sur_launch_samples(Q, cfg->seed, 0, n, cfg->r_lo, cfg->r_hi, rec, c->s);
+  if (e == cudaSuccess && nv > 0) e = sur_launch_samples(Q, cfg->val_seed, 0, nv, cfg->r_lo, cfg->r_hi, vrec, c->s);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, c->s);
+  // epochs: batches drawn through an affine permutation i -> (a i + c) mod n
+  // with a coprime to n, fresh per epoch
+  std::mt19937_64 rng(cfg->seed ^ 0x5EEDull);
+  for (int ep = 0; ep < cfg->epochs && e == cudaSuccess; ++ep) {
+    unsigned long long a = (rng() % (unsigned long long)n) | 1ull, cc = rng() % (unsigned long long)n;
+    while (std::gcd(a, (unsigned long long)n) != 1ull) a += 2;
+    a %= (unsigned long long)n;
+    if (a == 0) a = 1;
+    for (long long k = 0; k < per_epoch && e == cudaSuccess; ++k) {
+      const long long step = (long long)ep * per_epoch + k;
+      double lr = cfg->lr;
+      if (cfg->lr_final > 0.0 && steps > 1)
+        lr = cfg->lr_final + 0.5 * (cfg->lr - cfg->lr_final) * (1.0 + std::cos(kPi * (double)step / (double)(steps - 1)));
+      e = sur_launch_train(c->sur, rec, n, a, cc, k * cfg->batch, cfg->batch, c->s);
+      if (e == cudaSuccess)
+        e = sur_launch_update(c->sur, tiles, 1, (float)lr, ++c->sur_t, nullptr, losses + step, c->s);
+    }
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(e2, c->s);
+  if (e == cudaSuccess && nv > 0) e = sur_launch_infer(c->sur, vrec, kSurRecord, nv, vy, c->sms, c->s);
+  if (e == cudaSuccess && nv > 0) e = sur_launch_val(vrec, vy, nv, verr, c->s);
+  if (e == cudaSuccess) e = cudaEventRecord(e3, c->s);
+  std::vector<float> herr((size_t)nv * 2), hl(2, 0.0f);
+  if (e == cudaSuccess && nv > 0)
+    e = cudaMemcpyAsync(herr.data(), verr, (size_t)nv * 2 * sizeof(float), cudaMemcpyDeviceToHost, c->s);
+  if (e == cudaSuccess && steps > 0) e = cudaMemcpyAsync(&hl[0], losses, sizeof(float), cudaMemcpyDeviceToHost, c->s);
+  if (e == cudaSuccess && steps > 0)
+    e = cudaMemcpyAsync(&hl[1], losses + steps - 1, sizeof(float), cudaMemcpyDeviceToHost, c->s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->s);
+  if (e != cudaSuccess) { cleanup(); return cuda_fail(c, e, "train_surrogate"); }
+  float ms = 0.0f;
+  cudaEventElapsedTime(&ms, e0, e1); rep->samples_ms = ms;
+  cudaEventElapsedTime(&ms, e1, e2); rep->train_ms = ms;
+  cudaEventElapsedTime(&ms, e2, e3); rep->val_ms = ms;
+  cleanup();
+  rep->steps = steps;
+  rep->n_samples = n;
+  rep->n_val = nv;
+  rep->loss_first = hl[0] / cfg->batch;
+  rep->loss_last = hl[1] / cfg->batch;
+  std::vector<float> de, le;
+  for (long long i = 0; i < nv; ++i)
+    if (herr[2 * i] >= 0.0f) { de.push_back(herr[2 * i]); le.push_back(herr[2 * i + 1]); }
+  rep->val_count = (int64_t)de.size();
+  auto pct = [](std::vector<float>& v, double q) -> double {
+    if (v.empty()) return 0.0;
+    const size_t k = std::min(v.size() - 1, (size_t)(q * (double)(v.size() - 1)));
+    std::nth_element(v.begin(), v.begin() + k, v.end());
+    return v[k];
+  };
+  rep->drag_err_median = pct(de, 0.5);
+  rep->drag_err_p99 = pct(de, 0.99);
+  rep->drag_err_max = de.empty() ? 0.0 : *std::max_element(de.begin(), de.end());
+  rep->lnN_err_median = pct(le, 0.5);
+  rep->lnN_err_p99 = pct(le, 0.99);
+  rep->lnN_err_max = le.empty() ? 0.0 : *std::max_element(le.begin(), le.end());
+  return sur_check(c);
+}
+
 const char* pic1d_last_error(const pic1d_ctx* c) {
   if (!c) return "no context";
   return c->err.c_str();
@@ -791,7 +1035,8 @@ void pic1d_free(pic1d_ctx* c) {
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   void* ptrs[] = {c->E64, c->E32, c->J, c->dens[0], c->dens[1], c->nb, c->nmu, c->nx, c->zone, c->dens_flag, c->fast_cell, c->table,
                   c->ctr, c->st, c->ke_partial, c->field_partial, c->counts, c->offsets, c->spc, c->slot_log,
-                  c->tpair, c->bsum};
+                  c->tpair, c->bsum, c->sur.master, c->sur.m, c->sur.v, c->sur.img, c->sur.small,
+                  c->sur.part, c->sur.loss_part, c->sur.err, c->sur_gx, c->sur_gw, c->sur_grad, c->sur_loss};
   for (void* q : ptrs) cudaFree(q);
   delete c;
 }

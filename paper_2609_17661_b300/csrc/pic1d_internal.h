@@ -105,3 +105,43 @@ cudaError_t launch_deposit(const DevParams& P, long long n, const long long* p0,
 cudaError_t launch_count_species(const DevParams& P, unsigned long long* out4, cudaStream_t s);
 int push_blocks_per_sm(int variant, bool nmax);
 }  // namespace pic1d
+
+// learned surrogate of the photon-field quadrature (surrogate.cu)
+namespace pic1d {
+// flat parameter layout: W[out][in] then b, layer by layer (4-64-64-64-2)
+constexpr int W_OW1 = 0, W_OB1 = 256, W_OW2 = 320, W_OB2 = 4416, W_OW3 = 4480, W_OB3 = 8576, W_OW4 = 8640,
+              W_OB4 = 8768, W_N_PARAMS = 8770;
+constexpr int kSurRecord = 16;   // floats per sample record
+
+struct SurPhys {              // what the quadrature needs about the star and the photon field
+  double theta_T;             // kT / (m_e c^2)
+  double pref;                // r_e R* / (4 pi lbar^2)
+  double log10g_max;          // gamma range of the samples: [1, 10^log10g_max]
+  double b_star;
+  int b_convention, photon_model, n_mu, n_phi;
+  const double* gx;           // Gauss-Legendre nodes and weights on [-1, 1] (device)
+  const double* gw;
+};
+
+struct SurBufs {              // device buffers of one network
+  float* master;              // FP32 master parameters
+  float* m;                   // Adam moments
+  float* v;
+  uint8_t* img;               // BF16 tensor-core operand images (32 KB)
+  float* small;               // FP32 copies of layers 1 and 4 and the biases
+  float* part;                // gradient partials [tiles][W_N_PARAMS]
+  float* loss_part;           // [tiles]
+  unsigned* err;              // set when a wait inside a kernel gave up
+  int max_tiles;
+};
+
+cudaError_t sur_launch_samples(const SurPhys& Q, unsigned long long seed, unsigned long long start, long long n,
+                               double r_lo, double r_hi, float* out, cudaStream_t s);
+cudaError_t sur_launch_train(const SurBufs& B, const float* samples, long long n, unsigned long long perm_a,
+                             unsigned long long perm_c, long long row0, int rows, cudaStream_t s);
+cudaError_t sur_launch_update(const SurBufs& B, int tiles, int mode, float lr, int adam_t, float* grad_out,
+                              float* loss_out, cudaStream_t s);
+cudaError_t sur_launch_infer(const SurBufs& B, const float* feat, int stride, long long n, float* out, int grid,
+                             cudaStream_t s);
+cudaError_t sur_launch_val(const float* rec, const float* y, long long n, float* err2, cudaStream_t s);
+}  // namespace pic1d

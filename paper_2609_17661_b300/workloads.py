@@ -278,6 +278,8 @@ SUR_N_PARAMS = sum(o * i + o for o, i in SUR_LAYERS)
 # lr 1e-3 with batches of 8192.
 SUR_TRAIN = dict(n_samples=10_000_000, epochs=20, batch=8192, lr=1e-3, r_lo=20.0, r_hi=20.0, seed=3,
                  n_val=100_000, val_seed=1003)
+# the same run with a cosine decay of the learning rate from 3e-3 to 1e-5
+SUR_TRAIN_COSINE = dict(SUR_TRAIN, lr=3e-3, lr_final=1e-5)
 # one network for every line of the r_eq in [2, 30] ensemble
 SUR_TRAIN_ENSEMBLE = dict(SUR_TRAIN, r_lo=2.0, r_hi=30.0)
 
@@ -292,3 +294,18 @@ def sur_init_params(seed: int = 0) -> np.ndarray:
         out.append(rng.uniform(-bound, bound, o * i))
         out.append(rng.uniform(-bound, bound, o))
     return np.concatenate(out).astype(np.float32)
+
+
+def sur_random_records(n: int, seed: int = 0) -> np.ndarray:
+    """n synthetic sample records (n x 16, FP32) with random inputs in the
+    network's box and random targets -- for gradient and optimiser checks,
+    which need no physical targets.  Columns 0-3 inputs (f3 = +-1), 4 t1 in
+    [-1, 1], 5 t2 ~ N(0, 1), 6 mask (80 % ones), the rest zero."""
+    rng = np.random.default_rng(seed)
+    r = np.zeros((n, 16), np.float32)
+    r[:, 0:3] = rng.uniform(-1, 1, (n, 3))
+    r[:, 3] = rng.choice([-1.0, 1.0], n)
+    r[:, 4] = rng.uniform(-1, 1, n)
+    r[:, 5] = rng.normal(0, 1, n)
+    r[:, 6] = (rng.random(n) < 0.8).astype(np.float32)
+    return r

@@ -1,0 +1,139 @@
+"""The learned surrogate on the GPU (through the C ABI) against its FP64
+oracle: quadrature samples, the tensor-core forward pass and its derivative,
+gradients (GPU BF16 vs CPU FP64 within 1e-2), Adam steps, and training.
+
+BF16 tolerance: the GPU rounds the hidden activations that feed the tensor
+cores to BF16 (relative 2^-9) and accumulates in FP32; with BF16-exact
+weights the outputs and gradients then differ from FP64 by a few 1e-3 of
+their scale, checked at 1e-2."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import surrogate as S
+from paper_2609_17661_b300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _line(**over):
+    from paper_2609_17661_b300 import Line
+    return Line(W.config("C2", n_cells=1024, **over))
+
+
+def _bf16_params(seed, scale=1.0):
+    """Parameters whose W2 and W3 are BF16-exact (the GPU's tensor-core operands)."""
+    return S.bf16_tensor_layers((W.sur_init_params(seed).astype(np.float64) * scale).astype(np.float32))
+
+
+FIELDS = ("f0", "f1", "f2", "f3", "t1", "t2", "mask", "base", "lnN", "F", "F_abs", "gamma", "b", "u", "x", "mu")
+
+
+@pytest.mark.parametrize("model,r_lo,r_hi", [(O.PHOTON_DISK, 2.0, 30.0), (O.PHOTON_DISK, 20.0, 20.0),
+                                             (O.PHOTON_RADIAL, 4.0, 4.0)])
+def test_samples_match_oracle(model, r_lo, r_hi):
+    """Records from the device quadrature equal the oracle's FP64 records
+    (the same Philox draws), to FP32 storage."""
+    line = _line(photon_model=model)
+    n = 3000
+    g = line.sur_samples(9, 100, n, r_lo, r_hi).cpu().numpy().astype(np.float64)
+    o = O.sur_samples(W.config("C2", photon_model=model), 9, 100, n, r_lo, r_hi)
+    D = dict(zip(O.SUR_FIELDS, o.T))
+    G = dict(zip(FIELDS, g.T))
+    for k in ("f0", "f1", "f2", "f3", "x", "mu", "u"):
+        np.testing.assert_allclose(G[k], D[k], rtol=2e-6, atol=2e-6, err_msg=k)
+    np.testing.assert_allclose(G["b"], D["b"], rtol=1e-5)
+    m = D["mask"] > 0
+    # the mask flips only where ln N sits at the floor itself
+    flip = G["mask"] != D["mask"]
+    assert np.all(np.abs(D["lnN"][flip] - S.LT) < 1e-4)
+    keep = m & ~flip
+    np.testing.assert_allclose(G["t1"][keep], D["t1"][keep], rtol=1e-5, atol=1e-6)
+    np.testing.assert_allclose(G["t2"], D["t2"], rtol=1e-5, atol=2e-5)
+    np.testing.assert_allclose(G["lnN"][keep], D["lnN"][keep], rtol=1e-6, atol=2e-5)
+    np.testing.assert_allclose(G["base"], np.maximum(D["lnN_base"], -745.0), rtol=1e-6, atol=2e-5)
+    big = keep & (np.abs(D["F"]) > 1e-30)
+    np.testing.assert_allclose(G["F"][big], D["F"][big], rtol=1e-5, atol=1e-6 * np.max(np.abs(D["F"][big])))
+    np.testing.assert_allclose(G["F_abs"][big], D["F_abs"][big], rtol=1e-5)
+
+
+def test_infer_matches_oracle_forward_and_derivative():
+    """Tensor-core forward pass (and its derivative in f0) against the FP64
+    network with the same BF16 weights: a wrong operand layout, descriptor or
+    transposition would miss by O(1)."""
+    line = _line()
+    th = _bf16_params(4, scale=2.0)
+    line.sur_set_params(th.astype(np.float32))
+    rec = W.sur_random_records(1000, seed=3)      # 7 full tiles + a ragged one
+    Y = line.sur_infer(torch.from_numpy(rec).cuda()).cpu().numpy().astype(np.float64)
+    X = rec[:, :4].astype(np.float64)
+    Yo, Yd = S.jvp_log10g(th, X)
+    scale = np.max(np.abs(Yo), axis=0)
+    assert np.max(np.abs(Y[:, :2] - Yo) / scale) <= 1e-2
+    dscale = np.max(np.abs(Yd), axis=0)
+    assert np.max(np.abs(Y[:, 2:] - Yd) / dscale) <= 2e-2
+    # and far below an O(1) miss: the typical error is at BF16 level
+    assert np.median(np.abs(Y[:, :2] - Yo) / scale) <= 3e-3
+
+
+def test_gradient_matches_oracle():
+    """Gradient of the mean loss, GPU (BF16 activations, FP32 sums) against
+    CPU FP64 backprop on the same records: within 1e-2 relative per layer."""
+    line = _line()
+    th = _bf16_params(5, scale=1.5)
+    line.sur_set_params(th.astype(np.float32))
+    rec = W.sur_random_records(1000, seed=6)
+    g, loss = line.sur_grad(torch.from_numpy(rec).cuda())
+    X = rec[:, :4].astype(np.float64)
+    lo, go = S.loss_grad(th, X, rec[:, 4].astype(np.float64), rec[:, 5].astype(np.float64),
+                         rec[:, 6].astype(np.float64))
+    assert loss == pytest.approx(lo, rel=1e-2)
+    for (kw, kb), (o, i) in zip(S.OFFSETS, S.SIZES):
+        for a, b in ((kw, kw + o * i), (kb, kb + o)):
+            err = np.linalg.norm(g[a:b] - go[a:b]) / np.linalg.norm(go[a:b])
+            assert err <= 1e-2, (a, b, err)
+
+
+def test_adam_steps_follow_the_oracle():
+    """Three Adam steps on consecutive batches: the parameter updates point the
+    same way as the FP64 oracle's and have the same size."""
+    line = _line()
+    th0 = _bf16_params(7)
+    line.sur_set_params(th0.astype(np.float32))
+    rec = W.sur_random_records(768, seed=8)
+    line.sur_train_steps(torch.from_numpy(rec).cuda(), 256, 3, 1e-3)
+    th_g = line.sur_get_params().astype(np.float64)
+    A = S.Adam(S.N_PARAMS, lr=1e-3)
+    th = th0.copy()
+    for k in range(3):
+        r = rec[256 * k:256 * (k + 1)].astype(np.float64)
+        # the GPU computes with the BF16 rounding of its FP32 W2 and W3
+        _, g = S.loss_grad(S.bf16_tensor_layers(th), r[:, :4], r[:, 4], r[:, 5], r[:, 6])
+        th = A.step(th, g)
+    dg, do = th_g - th0, th - th0
+    big = np.abs(do) > 1e-3     # parameters that moved by about lr each step
+    assert big.mean() > 0.5
+    assert np.mean(np.sign(dg[big]) == np.sign(do[big])) > 0.99
+    # Adam divides by the gradient's running size, so a parameter whose
+    # gradient is near zero in one step can move differently when its BF16
+    # and FP64 gradients differ in that step; all but a few agree within 5 %
+    close = np.isclose(dg[big], do[big], rtol=0.05, atol=5e-5)
+    assert close.mean() > 0.99, close.mean()
+
+
+def test_training_run_learns_the_quadrature():
+    """A short training run on the r_eq = 20 line (2e5 samples, 5 epochs):
+    the loss falls by a factor 20 and the held-out drag and rate errors
+    against quadrature are reported."""
+    line = _line()
+    line.sur_set_params(W.sur_init_params(0))
+    rep = line.train_surrogate(n_samples=200_000, epochs=5, batch=8192, lr=3e-3, r_lo=20.0, r_hi=20.0, seed=3,
+                               n_val=20_000, val_seed=1003)
+    assert rep["steps"] == 5 * (200_000 // 8192)
+    assert rep["loss_last"] < rep["loss_first"] / 5
+    assert rep["val_count"] > 15_000
+    print(rep)
+    assert rep["drag_err_median"] < 0.05 and rep["lnN_err_median"] < 0.1
