@@ -63,6 +63,8 @@ extern "C" {
 #define PIC1D_DRAG_OFF       0
 #define PIC1D_DRAG_CLOSED    1 /* closed form Eq. contdrag at the particle (radial photons)    */
 #define PIC1D_DRAG_TABLE     2 /* bilinear table in (log10 gamma, s/L) built by quadrature      */
+#define PIC1D_DRAG_SURROGATE 3 /* the learned network (pic1d_sur_*; set its parameters or train
+                                  it before stepping), the closed form outside its box        */
 
 /* RICS response (Sec. 3) */
 #define PIC1D_RICS_SPLIT           0 /* b > b_thr: discrete scattering + pairs; else continuous drag */

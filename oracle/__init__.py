@@ -30,7 +30,7 @@ _SRC = os.path.join(_HERE, "pic1d_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 PHOTON_RADIAL, PHOTON_DISK = 0, 1
-DRAG_OFF, DRAG_CLOSED, DRAG_TABLE = 0, 1, 2
+DRAG_OFF, DRAG_CLOSED, DRAG_TABLE, DRAG_SURROGATE = 0, 1, 2, 3
 RICS_SPLIT, RICS_DRAG_PLUS_PAIRS = 0, 1
 INJECT_NONE, INJECT_RATE = 0, 1
 S_BITS = 12
@@ -125,6 +125,8 @@ def lib():
             "orc_gather_public": (C.c_double, [C.c_void_p, C.c_double]),
             "orc_node_interp_public": (C.c_double, [C.c_void_p, C.c_int, C.c_double]),
             "orc_sur_edge_mu": (C.c_double, [C.c_double, C.c_double, C.c_double]),
+            "orc_set_surrogate": (None, [C.c_void_p, _D]),
+            "orc_sur_forward": (None, [_D, _D, _D, _D]),
             "orc_sur_baseline": (C.c_double, [C.POINTER(OrcParams), C.c_double, C.c_double, C.c_double, C.c_double]),
             "orc_sur_point": (None, [C.POINTER(OrcParams), C.c_double, C.c_double, C.c_double, C.c_int, _D]),
             "orc_sur_sample": (None, [C.POINTER(OrcParams), C.c_uint64, C.c_uint64, C.c_double, C.c_double, _D]),
@@ -291,6 +293,11 @@ class Sim:
         assert E.shape == (self.N,)
         lib().orc_set_field(self.h, _ptr(E, _D))
 
+    def set_surrogate(self, theta):
+        """Parameters (8770) of the network that drag law SURROGATE evaluates."""
+        self._sur = np.ascontiguousarray(theta, dtype=np.float64)
+        lib().orc_set_surrogate(self.h, _ptr(self._sur, _D))
+
     def set_step(self, step):
         lib().orc_set_step(self.h, int(step))
 
@@ -373,3 +380,12 @@ def sur_samples(cfg, seed, start, n, r_lo, r_hi):
     out = np.zeros((n, 15))
     lib().orc_sur_samples(C.byref(p), seed, start, n, r_lo, r_hi, _ptr(out, _D))
     return out
+
+
+def sur_forward(theta, x):
+    """The C oracle's FP64 network at one input: (y[2], dy/df0[2])."""
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    xx = np.ascontiguousarray(x, dtype=np.float64)
+    y, dy = np.zeros(2), np.zeros(2)
+    lib().orc_sur_forward(_ptr(th, _D), _ptr(xx, _D), _ptr(y, _D), _ptr(dy, _D))
+    return y, dy

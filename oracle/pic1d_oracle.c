@@ -55,7 +55,7 @@
 
 /* enums shared by value with the Python side */
 enum { ORC_PHOTON_RADIAL = 0, ORC_PHOTON_DISK = 1 };
-enum { ORC_DRAG_OFF = 0, ORC_DRAG_CLOSED = 1, ORC_DRAG_TABLE = 2 };
+enum { ORC_DRAG_OFF = 0, ORC_DRAG_CLOSED = 1, ORC_DRAG_TABLE = 2, ORC_DRAG_SURROGATE = 3 };
 enum { ORC_RICS_SPLIT = 0, ORC_RICS_DRAG_PLUS_PAIRS = 1 };
 enum { ORC_INJECT_NONE = 0, ORC_INJECT_RATE = 1 };
 enum { ORC_SP_ELEC = 0, ORC_SP_POSI = 1, ORC_SP_ION = 2, ORC_SP_ATMO = 3 };
@@ -491,6 +491,7 @@ typedef struct {
   double *node_x, *node_b, *node_mu;   /* N+1 nodes                       */
   unsigned char* zone;                 /* N cells: b(centre) > b_thr      */
   double* table;
+  double* sur;                         /* surrogate parameters (8770) or NULL */
   double *E, *J;
   int64_t* dens;                       /* lepton weight per cell, w_int   */
   int64_t n, cap;
@@ -583,7 +584,7 @@ void orc_free(orc_sim* S)
 {
   if (!S) return;
   free(S->node_x); free(S->node_b); free(S->node_mu); free(S->zone); free(S->table);
-  free(S->E); free(S->J); free(S->dens);
+  free(S->E); free(S->J); free(S->dens); free(S->sur);
   free(S->s); free(S->u); free(S->w); free(S->sp); free(S->id);
   free(S);
 }
@@ -710,12 +711,114 @@ static void orc_closed_eval(const orc_sim* S, double u, double s, double* F, dou
   }
 }
 
+/* ------------------------------------------------------------------------ */
+/* The learned surrogate as a drag law (FP64 network; see orc_sur_point for  */
+/* its inputs and targets).  Parameters: W1[64][4] b1 W2[64][64] b2          */
+/* W3[64][64] b3 W4[2][64] b4, 8770 values.                                  */
+/* ------------------------------------------------------------------------ */
+#define ORC_SUR_NP 8770
+
+void orc_set_surrogate(orc_sim* S, const double* theta)
+{
+  if (!S->sur) S->sur = malloc(ORC_SUR_NP * sizeof(double));
+  memcpy(S->sur, theta, ORC_SUR_NP * sizeof(double));
+}
+
+static double orc_silu(double z) { return z / (1.0 + exp(-z)); }
+static double orc_dsilu(double z) { double q = 1.0 / (1.0 + exp(-z)); return q * (1.0 + z * (1.0 - q)); }
+
+/* outputs y and their derivatives dy in the first input (forward mode) */
+void orc_sur_forward(const double* th, const double* x, double* y, double* dy)
+{
+  static const int in_n[4] = {4, 64, 64, 64}, out_n[4] = {64, 64, 64, 2};
+  double h[64], hd[64], z[64], zd[64];
+  for (int i = 0; i < 4; ++i) { h[i] = x[i]; hd[i] = (i == 0) ? 1.0 : 0.0; }
+  const double* p = th;
+  for (int l = 0; l < 4; ++l) {
+    const double* W = p;
+    const double* bb = p + out_n[l] * in_n[l];
+    for (int j = 0; j < out_n[l]; ++j) {
+      double a = bb[j], ad = 0.0;
+      for (int i = 0; i < in_n[l]; ++i) { a += W[j * in_n[l] + i] * h[i]; ad += W[j * in_n[l] + i] * hd[i]; }
+      z[j] = a; zd[j] = ad;
+    }
+    for (int j = 0; j < out_n[l]; ++j) {
+      if (l < 3) { h[j] = orc_silu(z[j]); hd[j] = orc_dsilu(z[j]) * zd[j]; }
+      else { h[j] = z[j]; hd[j] = zd[j]; }
+    }
+    p = bb + out_n[l];
+  }
+  y[0] = h[0]; y[1] = h[1]; dy[0] = hd[0]; dy[1] = hd[1];
+}
+
+/* ln N^_rad (the single-direction closed form, solid angle pi/x^2) and its
+ * derivative in u, in log form (no underflow):
+ *   ln N = ln(P/x^2) + 2 ln eps - ln gamma - ln(e^y - 1), eps = b/(gamma D),
+ *   D = 1 - beta mu, y = eps/Theta. */
+static void orc_ln_nrad(const orc_params* p, double u, double x, double b, double mu, double* lnN, double* dlnN)
+{
+  double th = orc_theta_T(p);
+  double gam = sqrt(1.0 + u * u);
+  double D = orc_one_minus_beta_m(u, gam, mu);
+  double eps = b / (gam * D), y = eps / th;
+  double P = ORC_R_E * p->r_star_cm / (4.0 * ORC_LAMBDABAR * ORC_LAMBDABAR);
+  double lnem1 = (y > 20.0) ? y + log1p(-exp(-y)) : log(expm1(y));
+  *lnN = log(P / (x * x)) + 2.0 * log(eps) - log(gam) - lnem1;
+  double dlng = u / (gam * gam);
+  double dlnD = (-mu / (gam * gam * gam)) / D;
+  double dlne = -dlng - dlnD;
+  *dlnN = (2.0 - y / (-expm1(-y))) * dlne - dlng;
+}
+
+/* surrogate F^ (per R_star), dF^/du and ln N^ at (u, s); outside the training
+ * box (gamma above 10^G or b outside the range of f2) the closed form */
+static void orc_closed_eval(const orc_sim* S, double u, double s, double* F, double* dF, double* lnN);
+static void orc_sur_eval(const orc_sim* S, double u, double s, double* F, double* dF, double* lnN)
+{
+  const orc_params* p = &S->p;
+  double x = orc_node_interp(S, S->node_x, s);
+  double b = orc_node_interp(S, S->node_b, s);
+  double mu = orc_node_interp(S, S->node_mu, s);
+  double gam = sqrt(1.0 + u * u);
+  double G = p->table_log10g_max;
+  double f[4];
+  f[0] = 2.0 * log10(gam) / G - 1.0;
+  f[1] = 2.0 * s / S->N - 1.0;
+  f[2] = (log10(b) - ORC_SUR_B_MID) / ORC_SUR_B_HALF;
+  f[3] = (u < 0.0) ? -1.0 : 1.0;
+  if (f[0] > 1.0 || f[2] < -1.0 || f[2] > 1.0 || !S->sur) {
+    orc_closed_eval(S, u, s, F, dF, lnN);
+    return;
+  }
+  double y[2], dy[2];
+  orc_sur_forward(S->sur, f, y, dy);
+  double l1, d1, l2, d2;
+  orc_ln_nrad(p, u, x, b, mu, &l1, &d1);
+  orc_ln_nrad(p, u, x, b, orc_sur_edge_mu(u, x, mu), &l2, &d2);
+  double a1 = log(0.9) + l1, a2 = log(0.1) + l2;
+  double mx = fmax(a1, a2);
+  double e1 = exp(a1 - mx), e2 = exp(a2 - mx);
+  double B = mx + log(e1 + e2);
+  double dB = (e1 * d1 + e2 * d2) / (e1 + e2);
+  double Bc = fmax(B, ORC_SUR_LT), dBc = (B > ORC_SUR_LT) ? dB : 0.0;
+  double ln_n = Bc + y[1];
+  double N = exp(ln_n);
+  *lnN = ln_n;
+  *F = gam * b * N * y[0];
+  if (dF) {
+    double df0 = 2.0 / G * u / (gam * gam * log(10.0));
+    double dln = dBc + dy[1] * df0;
+    *dF = b * N * ((u / gam) * y[0] + gam * y[0] * dln + gam * dy[0] * df0);
+  }
+}
+
 /* F and dF in code units (du per cell-crossing time), rate in code units */
 void orc_drag_code(const orc_sim* S, double u, double s, double* F, double* dF, double* rate)
 {
   double Fh = 0.0, dFh = 0.0, lnN = -700.0;
   if (S->p.drag_law == ORC_DRAG_TABLE) orc_table_eval(S, u, s, &Fh, &dFh, &lnN);
   else if (S->p.drag_law == ORC_DRAG_CLOSED) orc_closed_eval(S, u, s, &Fh, &dFh, &lnN);
+  else if (S->p.drag_law == ORC_DRAG_SURROGATE) orc_sur_eval(S, u, s, &Fh, &dFh, &lnN);
   double k = S->p.drag_scale / S->R_cells;
   *F = k * Fh;
   if (dF) *dF = k * dFh;

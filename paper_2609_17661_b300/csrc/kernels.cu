@@ -18,6 +18,7 @@
 #include <math.h>
 
 #include "pic1d_internal.h"
+#include "sur_mlp.h"
 
 namespace pic1d {
 
@@ -807,6 +808,330 @@ __global__ void __launch_bounds__(kBlock, MINB) k_push(DevParams P) {
 }
 
 // --------------------------------------------------------------------------
+// the push with drag law SURROGATE: the drag and the scattering rate come
+// from the learned network, evaluated for the CTA's 128 particles at once on
+// the tensor cores (sur_mlp.h).  One particle per thread; tiles of 128 slots
+// from the dynamic schedule.  The per-particle physics is push_one's; the
+// Newton iterations of the implicit midpoint run in lockstep over the CTA
+// (a lane that has converged contributes a dummy row).
+// --------------------------------------------------------------------------
+
+// ln N^ along one photon direction mu (the closed form [contdrag] with solid
+// angle pi/x^2) in log form, and its derivative in u:
+//   ln N = ln(P/x^2) + 2 ln eps - ln gamma - ln(e^y - 1)
+__device__ __forceinline__ float sur_lnrad(const DevParams& P, float u, float gam, float x, float b, float mu,
+                                           float& dln) {
+  const float au = fabsf(u);
+  const float sm = (u >= 0.0f) ? mu : -mu;
+  const float D = (1.0f - sm) + sm / (gam * (gam + au));     // 1 - beta mu
+  const float eps = b / (gam * D), y = eps / P.theta_T;
+  const float lnem1 = (y > 20.0f) ? y + log1pf(-__expf(-y)) : logf(expm1f(y));
+  const float dlng = u / (gam * gam);
+  const float dlnD = (-mu / (gam * gam * gam)) / D;
+  const float dlne = -dlng - dlnD;
+  dln = (2.0f - y / (-expm1f(-y))) * dlne - dlng;
+  return P.sur_lnP - 2.0f * logf(x) + 2.0f * logf(eps) - logf(gam) - lnem1;
+}
+
+// F^ (per R_star), dF^/du and ln N^ of the surrogate at u for this thread's
+// particle.  Collective: every thread of the CTA calls it; `want` only says
+// whether the caller uses the result.  Outside the training box (gamma above
+// 10^G, b outside the range of f2) the closed form stands in.
+__device__ DragVal sur_eval(const DevParams& P, sur::MlpCta& M, float u, const Site& S, float sL, bool want) {
+  const float q = fmaf(u, u, 1.0f);
+  const float gam = sqrtf(q);
+  float x[4];
+  x[0] = 2.0f * (0.5f * __log2f(q) * 0.30102999566f) / P.sur_G - 1.0f;
+  x[1] = 2.0f * sL - 1.0f;
+  x[2] = (log10f(S.b) - (float)sur::B_MID) / (float)sur::B_HALF;
+  x[3] = (u < 0.0f) ? -1.0f : 1.0f;
+  const bool inbox = x[0] <= 1.0f && x[2] >= -1.0f && x[2] <= 1.0f;
+  if (!want || !inbox) { x[0] = 0.0f; x[1] = 0.0f; x[2] = 0.0f; }
+  float y0, y1, g0, g1;
+  sur::mlp_tile(M, x, y0, y1, g0, g1);
+  DragVal d;
+  d.F = d.dF = 0.0f;
+  d.lnN = -700.0f;
+  if (!want) return d;
+  if (!inbox) return closed_eval(P, u, S, true);
+  float d1, d2;
+  const float l1 = sur_lnrad(P, u, gam, S.x, S.b, S.mu, d1);
+  const float ths = acosf(fmaxf(-1.0f, fminf(1.0f, S.mu))), am = asinf(fminf(1.0f, 1.0f / S.x));
+  const float me = (u >= 0.0f) ? cosf(fminf(3.14159265f, ths + am)) : cosf(fmaxf(0.0f, ths - am));
+  const float l2 = sur_lnrad(P, u, gam, S.x, S.b, me, d2);
+  const float a1 = -0.105360516f + l1, a2 = -2.302585093f + l2;   // ln 0.9, ln 0.1
+  const float mx = fmaxf(a1, a2);
+  const float e1 = __expf(a1 - mx), e2 = __expf(a2 - mx);
+  const float B = mx + logf(e1 + e2);
+  const float dB = (e1 * d1 + e2 * d2) / (e1 + e2);
+  const float Bc = fmaxf(B, sur::LT), dBc = (B > sur::LT) ? dB : 0.0f;
+  d.lnN = Bc + y1;
+  const float N = __expf(d.lnN);
+  d.F = gam * S.b * N * y0;
+  const float df0 = 2.0f / P.sur_G * u / (q * 2.302585093f);
+  const float dln = dBc + g1 * df0;
+  d.dF = S.b * N * ((u / gam) * y0 + gam * y0 * dln + gam * g0 * df0);
+  return d;
+}
+
+// One drag update over dt/2 (as drag_half) with the surrogate; collective.
+__device__ float sur_drag_half(const DevParams& P, sur::MlpCta& M, const Site& S, float sL, float u0, bool act,
+                               unsigned& n_lim, unsigned& n_newt) {
+  const float h = P.half_dt;
+  const float F0 = P.drag_k * sur_eval(P, M, u0, S, sL, act).F;
+  const bool newton = act && (!P.limiter_on || (fabsf(F0) * P.tau_min < fabsf(u0)));
+  float u1 = u0;
+  if (act) {
+    if (newton) {
+      ++n_newt;
+      u1 = fmaf(h, F0, u0);
+    } else {
+      ++n_lim;
+      const float ut = S.mu * rsqrtf(1.0f - S.mu * S.mu);
+      u1 = fmaf(u0 - ut, P.damp, ut);
+    }
+  }
+  bool going = newton;
+  int it = 0;
+  while (__syncthreads_or(going)) {
+    const DragVal d1 = sur_eval(P, M, u1, S, sL, going);
+    if (going) {
+      const float F1 = P.drag_k * d1.F;
+      const float G = u1 - u0 - 0.5f * h * (F0 + F1);
+      const float dG = fmaxf(1.0f - 0.5f * h * P.drag_k * d1.dF, 0.5f);
+      const float un = u1 - __fdividef(G, dG);
+      if (un == u1) {
+        going = false;
+      } else {
+        u1 = un;
+        if (++it == 4) going = false;
+      }
+    }
+  }
+  return u1;
+}
+
+// warp-aggregated exact add of v into g[cell] from the lanes with `mine`
+__device__ __forceinline__ void warp_atomic_cell(bool mine, int cell, long long v, long long* g, int N) {
+  const unsigned m = __ballot_sync(0xffffffffu, mine);
+  if (!mine) return;
+  const unsigned grp = __match_any_sync(m, cell);
+  const long long sum = group_sum64(grp, v);
+  if ((int)(threadIdx.x & 31) == __ffs(grp) - 1 && sum != 0 && cell >= 0 && cell < N)
+    atomicAdd(reinterpret_cast<unsigned long long*>(g + cell), (unsigned long long)sum);
+}
+
+template <bool NMAX>
+__global__ void __launch_bounds__(sur::NT, 1) k_push_sur(DevParams P) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t bar_ld, bar_mma;
+  __shared__ uint32_t s_taddr;
+  __shared__ unsigned s_tile;
+  __shared__ unsigned sCtr[C_COUNT];
+  __shared__ double sRed[2][sur::NT / 32];
+  sur::MlpCta M;
+  sur::mlp_begin(M, smem_raw, &bar_ld, &bar_mma, &s_taddr, P.sur_img, P.sur_small);
+  const int t = threadIdx.x, lane = t & 31;
+  if (t < C_COUNT) sCtr[t] = 0;
+  if (t == 0) s_tile = (unsigned)atomicAdd(&P.st->work, 1ull);
+  __syncthreads();
+  const uint32_t n = (uint32_t)P.st->n_slots;
+  const uint32_t ntiles = (n + sur::TM - 1) / sur::TM;
+  const uint32_t fmask = (1u << P.F) - 1u;
+  const uint32_t half = 1u << (P.F - 1);
+  Tally T;
+#pragma unroll
+  for (int k = 0; k < C_COUNT; ++k) T.c[k] = 0;
+  T.n_lim = T.n_newt = 0;
+  T.ke = T.ke_c = T.kl = T.kl_c = 0.0f;
+  unsigned tile = s_tile;
+  while (tile < ntiles) {
+    const uint32_t idx = tile * sur::TM + t;
+    uint32_t pos0 = 0;
+    float u = 0.0f, w = 0.0f;
+    uint8_t spb = PIC1D_SP_DEAD;
+    if (idx < n) {
+      pos0 = P.pos[idx];
+      u = P.u[idx];
+      w = P.w[idx];
+      spb = P.sp[idx];
+    }
+    const bool valid = idx < n && spb != PIC1D_SP_DEAD;
+    const int sp = spb & 3;
+    const bool ion = (sp == PIC1D_SP_ION), lep = !ion;
+    const float qm = ion ? P.qm[PIC1D_SP_ION] : (sp == PIC1D_SP_POSITRON ? 1.0f : -1.0f);
+    const int qs = (sp == PIC1D_SP_ELECTRON || sp == PIC1D_SP_ATMO) ? -1 : 1;
+    const float mass = ion ? P.mass[PIC1D_SP_ION] : 1.0f;
+    const int cell = valid ? (int)(pos0 >> P.F) : 0;
+    float Ep = 0.0f;
+    Site S;
+    S.x = 1.0f; S.b = 1.0f; S.mu = 0.0f; S.j = 0; S.c = 0.0f;
+    bool zone = false;
+    if (valid) {
+      const uint32_t xg = pos0 < half ? 0u : pos0 - half;
+      int ig = (int)(xg >> P.F);
+      float fg = (float)(xg & fmask) * P.inv2F;
+      if (ig > P.N - 2) { ig = P.N - 2; fg = 1.0f; }
+      const float e0 = __ldg(P.E32 + ig), e1 = __ldg(P.E32 + ig + 1);
+      Ep = fmaf(fg, e1 - e0, e0);
+      zone = __ldg(P.zone + cell) != 0;
+      const float f = (float)(pos0 & fmask) * P.inv2F;
+      S.b = fmaf(f, __ldg(P.nb + cell + 1) - __ldg(P.nb + cell), __ldg(P.nb + cell));
+      S.mu = fmaf(f, __ldg(P.nmu + cell + 1) - __ldg(P.nmu + cell), __ldg(P.nmu + cell));
+      S.x = fmaf(f, __ldg(P.nx + cell + 1) - __ldg(P.nx + cell), __ldg(P.nx + cell));
+    }
+    const bool cont = valid && lep && (P.rics_mode == PIC1D_RICS_DRAG_PLUS_PAIRS || !zone);
+    const bool mc = valid && lep && P.mc_on && zone;
+    const float sL = (float)((double)pos0 / (double)P.top);
+    // 2-4. Strang split with the surrogate drag
+    u = sur_drag_half(P, M, S, sL, u, cont, T.n_lim, T.n_newt);
+    if (valid) u = fmaf(qm * Ep, P.dt, u);
+    u = sur_drag_half(P, M, S, sL, u, cont, T.n_lim, T.n_newt);
+    // 5. Monte-Carlo RICS in the pair zone
+    bool make_pair = false;
+    float Pg = 0.0f;
+    unsigned long long pid = 0;
+    if (__syncthreads_or(mc)) {
+      const DragVal dv = sur_eval(P, M, u, S, sL, mc);
+      if (mc) {
+        float psc = P.drag_k * expf(dv.lnN) * P.dt;
+        if (psc > 1.0f) { psc = 1.0f; ++T.c[C_CLAMP]; }
+        if (psc > 0.0f) {
+          ++T.c[C_DRAW];
+          pid = P.id[idx];
+          const uint4 r = philox4x32_10(
+              make_uint4((uint32_t)pid, (uint32_t)(pid >> 32), (uint32_t)P.step, kTagRics), P.key0, P.key1);
+          if (unit24(r.x) < psc) {
+            ++T.c[C_SCAT];
+            const float beta = u * rsqrtf(fmaf(u, u, 1.0f));
+            const float d = (S.mu > beta) ? 1.0f : -1.0f;
+            const float ct = dipole_cos(unit24(r.y));
+            float uf, Eg;
+            rics_event(S.b, d, u, ct, uf, Eg, Pg);
+            if (P.rics_mode == PIC1D_RICS_SPLIT) u = uf;
+            if (P.pairs_on && Eg >= P.pair_e_thr) make_pair = true;
+          }
+        }
+      }
+    }
+    // 6. move, 7. deposit
+    long long xm = 0, x0 = 0, xp = 0;
+    uint32_t p1 = pos0;
+    bool lost = false;
+    const int wint = __float2int_rn(w * 4096.0f);
+    if (valid) {
+      if (!isfinite(u)) {
+        ++T.c[C_NONFIN];
+        u = 0.0f;
+        lost = true;
+        make_pair = false;
+      } else {
+        const float q = fmaf(u, u, 1.0f);
+        const float r = rsqrtf(q);
+        const int dfix = __float2int_rn(P.dt * (u * r) * (float)(1u << P.F));
+        const float e = w * mass * __fdividef(u * u * r, 1.0f + r);
+        const bool lostN = dfix < 0 && (uint32_t)(-dfix) > pos0;
+        const bool lostS = dfix > 0 && (uint32_t)dfix > P.top1 - pos0;
+        lost = lostN || lostS;
+        kahan(T.ke, T.ke_c, lost ? 0.0f : e);
+        kahan(T.kl, T.kl_c, lost ? e : 0.0f);
+        if (!lost) {
+          p1 = pos0 + (uint32_t)dfix;
+          path_split(dfix, pos0 & fmask, P.F, qs * wint, xm, x0, xp);
+        } else {
+          ++T.c[lostN ? C_LOSTN : C_LOSTS];
+          const int dd = lostN ? -(int)pos0 : (int)(P.top - (long long)pos0);
+          path_split(dd, pos0 & fmask, P.F, qs * wint, xm, x0, xp);
+          p1 = lostN ? 0u : (uint32_t)(P.top - 1);
+          if (make_pair) ++T.c[C_WALL];
+          make_pair = false;
+        }
+      }
+    }
+    if (make_pair) {
+      if (NMAX && P.dens_cur[(int)(p1 >> P.F)] >= P.nmax_int) {
+        ++T.c[C_REJ];
+        make_pair = false;
+      }
+    }
+    warp_atomic_cell(xm != 0, cell - 1, xm, P.J, P.N);
+    warp_atomic_cell(x0 != 0, cell, x0, P.J, P.N);
+    warp_atomic_cell(xp != 0, cell + 1, xp, P.J, P.N);
+    if (NMAX) {
+      const int cD = (int)(p1 >> P.F);
+      const bool wd = valid && lep && !lost && __ldg(P.dens_flag + cD) != 0;
+      warp_atomic_cell(wd, cD, (long long)wint, P.dens_next, P.N);
+    }
+    // pair append, warp-aggregated
+    const unsigned mp = __ballot_sync(0xffffffffu, make_pair);
+    if (mp) {
+      const int leader = __ffs(mp) - 1;
+      long long slot0 = 0;
+      if (lane == leader)
+        slot0 = atomicAdd(reinterpret_cast<unsigned long long*>(&P.st->append), (unsigned long long)(2 * __popc(mp)));
+      slot0 = __shfl_sync(0xffffffffu, slot0, leader);
+      if (make_pair) {
+        const long long dst = (long long)n + slot0 + 2ll * __popc(mp & lanemask_lt());
+        if (dst + 2 > P.cap) {
+          ++T.c[C_DROP];
+        } else {
+          ++T.c[C_PAIRS];
+          for (int mm = 0; mm < 2; ++mm) {
+            P.pos[dst + mm] = p1;
+            P.u[dst + mm] = 0.5f * Pg;
+            P.w[dst + mm] = w;
+            P.sp[dst + mm] = (mm == 0) ? PIC1D_SP_ELECTRON : PIC1D_SP_POSITRON;
+            P.id[dst + mm] = pair_child_id(pid, P.step, mm);
+          }
+          if (NMAX && __ldg(P.dens_flag + (p1 >> P.F)))
+            atomicAdd(reinterpret_cast<unsigned long long*>(P.dens_next + (int)(p1 >> P.F)),
+                      (unsigned long long)(2ll * wint));
+        }
+      }
+    }
+    if (valid) {
+      P.pos[idx] = p1;
+      P.u[idx] = u;
+      if (lost) P.sp[idx] = PIC1D_SP_DEAD;
+    }
+    __syncthreads();
+    if (t == 0) s_tile = (unsigned)atomicAdd(&P.st->work, 1ull);
+    __syncthreads();
+    tile = s_tile;
+  }
+  // counters and energy totals of the block
+  T.c[C_LIM] = T.n_lim;
+  T.c[C_NEWT] = T.n_newt;
+#pragma unroll
+  for (int k = 0; k < C_COUNT; ++k) {
+    const unsigned v = __reduce_add_sync(0xffffffffu, T.c[k]);
+    if (lane == 0 && v) atomicAdd(&sCtr[k], v);
+  }
+  double ked = (double)T.ke - (double)T.ke_c, kld = (double)T.kl - (double)T.kl_c;
+  for (int d = 16; d > 0; d >>= 1) {
+    ked += __shfl_down_sync(0xffffffffu, ked, d);
+    kld += __shfl_down_sync(0xffffffffu, kld, d);
+  }
+  if (lane == 0) { sRed[0][t >> 5] = ked; sRed[1][t >> 5] = kld; }
+  __syncthreads();
+  if (t == 0) {
+    double a = 0.0, b = 0.0;
+    for (int i = 0; i < sur::NT / 32; ++i) { a += sRed[0][i]; b += sRed[1][i]; }
+    P.ke_partial[blockIdx.x] = a;
+    if (b != 0.0) atomicAdd(&P.st->ke_lost, b);
+    Counters* C = P.ctr;
+    unsigned long long* dst[C_COUNT] = {&C->scatters, &C->psc_clamped, &C->limiter_branch, &C->newton_branch,
+                                        &C->nonfinite, &C->lost_north, &C->lost_south, &C->pairs_created,
+                                        &C->pairs_dropped_cap, &C->pairs_rejected_nmax, &C->pairs_lost_wall,
+                                        &C->rng_draws};
+    for (int k = 0; k < C_COUNT; ++k)
+      if (sCtr[k]) atomicAdd(dst[k], (unsigned long long)sCtr[k]);
+    if (!M.ok) atomicOr(P.sur_err, 1u);
+  }
+  sur::mlp_end(M);
+}
+
+// --------------------------------------------------------------------------
 // surface supply: neutral e- (atmospheric) + ion pairs at both footpoints
 // --------------------------------------------------------------------------
 __global__ void k_inject(DevParams P, double carriers, float sig_e, float sig_i) {
@@ -1207,6 +1532,20 @@ cudaError_t launch_push(const DevParams& P, int variant, int grid, cudaStream_t 
   const PushVariant& V = kPushVariants[variant];
   void* args[] = {const_cast<DevParams*>(&P)};
   return cudaLaunchKernel(P.use_nmax ? V.k_nmax : V.k_plain, dim3(grid), dim3(kBlock), args, 0, s);
+}
+
+cudaError_t launch_push_sur(const DevParams& P, int grid, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_push_sur<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sur::MF_SMEM);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_push_sur<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sur::MF_SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  if (P.use_nmax) k_push_sur<true><<<grid, sur::NT, sur::MF_SMEM, s>>>(P);
+  else k_push_sur<false><<<grid, sur::NT, sur::MF_SMEM, s>>>(P);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_inject(const DevParams& P, double carriers, float sig_e, float sig_i, cudaStream_t s) {

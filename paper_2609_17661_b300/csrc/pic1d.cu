@@ -117,6 +117,10 @@ int fbits_of(int n) {
 
 }  // namespace
 
+namespace {
+constexpr int kSurPushPerSm = 4;     // CTAs per SM of the surrogate push (52 KB shared, 128 TMEM columns each)
+}
+
 struct pic1d_ctx {
   pic1d_params p{};
   cudaStream_t s = nullptr;
@@ -273,6 +277,11 @@ DevParams dev_params(pic1d_ctx* c) {
   P.ctr = c->ctr;
   P.st = c->st;
   P.ke_partial = c->ke_partial;
+  P.sur_img = c->sur.img;
+  P.sur_small = c->sur.small;
+  P.sur_G = (float)p.table_log10g_max;
+  P.sur_lnP = (float)std::log(kRe * p.r_star_cm / (4.0 * kLbar * kLbar));
+  P.sur_err = c->sur.err;
   return P;
 }
 
@@ -286,7 +295,7 @@ int validate(const pic1d_params* p, std::string& why) {
   if (p->b_convention != 0 && p->b_convention != 1) return bad("b_convention must be 0 or 1");
   if (!(p->kT_keV > 0.0)) return bad("kT_keV must be positive");
   if (p->photon_model != PIC1D_PHOTON_RADIAL && p->photon_model != PIC1D_PHOTON_DISK) return bad("bad photon_model");
-  if (p->drag_law < PIC1D_DRAG_OFF || p->drag_law > PIC1D_DRAG_TABLE) return bad("bad drag_law");
+  if (p->drag_law < PIC1D_DRAG_OFF || p->drag_law > PIC1D_DRAG_SURROGATE) return bad("bad drag_law");
   if (p->drag_law == PIC1D_DRAG_TABLE && (p->table_n_gamma < 2 || p->table_n_s < 2 || p->table_n_gamma > 65536 ||
                                           p->table_n_s > 65536 || !(p->table_log10g_max > 0.0)))
     return bad("bad table shape");
@@ -622,6 +631,8 @@ int pic1d_step(pic1d_ctx* c, int n_steps) {
   const double dt_jext = c->dt * c->j_ext;
   const double carriers = p.j_psi * p.n0_ppc * c->dt;     // j_ext dt / q_p carriers of weight 1
   const float sig_e = (float)std::sqrt(p.inject_T), sig_i = (float)std::sqrt(p.inject_T / p.mass_ratio);
+  const bool sur_law = p.drag_law == PIC1D_DRAG_SURROGATE;
+  if (sur_law && !c->sur_on) return fail(c, PIC1D_EINVAL, "step: drag law SURROGATE without a network (set or train it)");
   for (int k = 0; k < n_steps; ++k) {
     DevParams P = dev_params(c);
     CK(cudaMemsetAsync(c->J, 0, c->N * sizeof(long long), c->s), "clear J");
@@ -630,10 +641,16 @@ int pic1d_step(pic1d_ctx* c, int n_steps) {
       int rc = timing_begin(c);
       if (rc != PIC1D_OK) return rc;
     }
-    CK(launch_push(P, c->push_variant, c->push_grid, c->s), "push");
+    int grid = c->push_grid;
+    if (sur_law) {
+      grid = c->sms * kSurPushPerSm;
+      CK(launch_push_sur(P, grid, c->s), "push");
+    } else {
+      CK(launch_push(P, c->push_variant, c->push_grid, c->s), "push");
+    }
     if (c->timing) CK(cudaEventRecord(c->ev.back(), c->s), "timing");
     if (p.inject_mode == PIC1D_INJECT_RATE) CK(launch_inject(P, carriers, sig_e, sig_i, c->s), "inject");
-    CK(launch_field(P, c->E64, c->E32, a, cJ, dt_jext, c->field_partial, c->push_grid, c->s), "field");
+    CK(launch_field(P, c->E64, c->E32, a, cJ, dt_jext, c->field_partial, grid, c->s), "field");
     c->step += 1;
     if (c->step % p.sort_every == 0) {
       int rc = do_sort(c);

@@ -77,6 +77,12 @@ struct DevParams {
   Counters* ctr;
   StepState* st;
   double* ke_partial;       // one per block of the push
+  // learned surrogate (drag law SURROGATE)
+  const uint8_t* sur_img;   // BF16 operand images of layers 2 and 3
+  const float* sur_small;   // FP32 layers 1 and 4 and the biases
+  float sur_G;              // table_log10g_max: f0 = 2 log10(gamma)/G - 1
+  float sur_lnP;            // ln(r_e R* / (4 lbar^2))
+  unsigned* sur_err;
 };
 
 }  // namespace pic1d
@@ -84,6 +90,7 @@ struct DevParams {
 // kernel launchers (kernels.cu)
 namespace pic1d {
 cudaError_t launch_push(const DevParams& P, int variant, int grid, cudaStream_t s);
+cudaError_t launch_push_sur(const DevParams& P, int grid, cudaStream_t s);   // drag law SURROGATE
 int push_variant_count();
 int push_variant_ppt(int v);
 int push_variant_minb(int v);

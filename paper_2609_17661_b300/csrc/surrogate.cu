@@ -39,61 +39,11 @@
 #include <cmath>
 
 #include "pic1d_internal.h"
+#include "sur_mlp.h"
 #include "tc05.h"
 
 namespace pic1d {
 namespace sur {
-
-// --------------------------------------------------------------- constants
-constexpr int TM = 128;      // rows (samples) per tile = TMEM lanes = threads
-constexpr int NT = 128;      // threads per CTA (one row each)
-constexpr float LT = -30.0f;   // clamp of the rate targets
-constexpr float LE = -20.0f;   // floor of the judged region
-constexpr double B_MID = -1.25, B_HALF = 2.75;
-constexpr uint32_t kTagSur = 0x53555247u;
-
-// image of the tensor-core operands (BF16, swizzled K-major, 8 KB each)
-constexpr int IMG_W2 = 0, IMG_W3 = 8192, IMG_W2T = 16384, IMG_W3T = 24576, IMG_BYTES = 32768;
-// FP32 copies of layers 1 and 4 and the biases
-constexpr int S_W1 = 0, S_B1 = 256, S_B2 = 320, S_B3 = 384, S_W4 = 448, S_B4 = 576, S_N = 580;
-
-constexpr uint32_t IDESC_128x64 = tc::idesc_bf16(128, 64);
-
-__device__ __forceinline__ float silu(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
-__device__ __forceinline__ float dsilu(float z) {
-  const float s = __frcp_rn(1.0f + __expf(-z));
-  return s * (1.0f + z * (1.0f - s));
-}
-
-// store 8 FP32 values as BF16 into chunk c of row r of a swizzled tile
-__device__ __forceinline__ void store_chunk(uint8_t* tile, int r, int c, const float* v) {
-  __align__(16) __nv_bfloat162 p[4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) p[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
-  *reinterpret_cast<uint4*>(tile + r * 128 + (((c ^ r) & 7) << 4)) = *reinterpret_cast<uint4*>(p);
-}
-
-// element (row j, k = batch index t) of a transposed tile with K = 128 (two
-// 64-wide swizzle atoms of `rows` rows each)
-__device__ __forceinline__ void store_t(uint8_t* tile, int rows, int j, int t, float v) {
-  uint8_t* atom = tile + (t >> 6) * rows * 128;
-  *reinterpret_cast<__nv_bfloat16*>(atom + tc::sw128(j, t & 63)) = __float2bfloat16_rn(v);
-}
-
-// warp sum then one shared atomic per warp
-__device__ __forceinline__ void red_add(float v, float* acc) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) atomicAdd(acc, v);
-}
-
-// one MMA chain of K = 64 (4 slices): D = A(128 x 64) * B(64 x 64)^T
-__device__ __forceinline__ void mma_k64(uint32_t d, const uint8_t* A, const uint8_t* B) {
-  const uint32_t a = tc::smem_addr(A), b = tc::smem_addr(B);
-#pragma unroll
-  for (int kk = 0; kk < 4; ++kk)
-    tc::mma_bf16(d, tc::desc_sw128(a + 32 * kk), tc::desc_sw128(b + 32 * kk), IDESC_128x64, kk > 0);
-}
 
 // K = 128 (two atoms): D = A(128 x 128) * B(64 x 128)^T, A atoms 16 KB apart, B atoms 8 KB apart
 __device__ __forceinline__ void mma_k128(uint32_t d, const uint8_t* A, const uint8_t* B) {
@@ -577,126 +527,30 @@ struct InferArgs {
   unsigned* err;
 };
 
-constexpr int IF_W = 0;          // W2, W3 images (16 KB)
-constexpr int IF_A = 16384;      // h tile (16 KB)
-constexpr int IF_AD = 32768;     // dh/df0 tile (16 KB)
-constexpr int IF_SMALL = 49152;
-constexpr int INFER_SMEM = IF_SMALL + 4 * S_N + 1024;
-
-// Forward pass of 128-row tiles with the tangent in f0 carried alongside
-// (forward mode): the value and tangent tiles go through the same weights,
-// D[cols 0..63] = h W^T and D[cols 64..127] = h' W^T.
+// Forward pass of 128-row tiles with the tangent in f0 (sur_mlp.h), tiles
+// taken grid-stride.
 __global__ void __launch_bounds__(NT, 1) k_sur_infer(InferArgs A) {
   extern __shared__ uint8_t smem_raw[];
-  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ __align__(8) uint64_t bar_ld, bar_mma;
   __shared__ uint32_t s_taddr;
-  const int t = threadIdx.x, warp = t >> 5;
-  float* sSmall = reinterpret_cast<float*>(sm + IF_SMALL);
-  uint8_t* sA = sm + IF_A;
-  uint8_t* sAd = sm + IF_AD;
-  if (t == 0) {
-    tc::mbar_init(&bar_ld, 1);
-    tc::mbar_init(&bar_mma, 1);
-    tc::mbar_fence_init();
-  }
-  __syncthreads();
-  if (t == 0) {
-    tc::mbar_expect_tx(&bar_ld, 16384);
-    tc::bulk_g2s(sm + IF_W, A.img + IMG_W2, 8192, &bar_ld);
-    tc::bulk_g2s(sm + IF_W + 8192, A.img + IMG_W3, 8192, &bar_ld);
-  }
-  if (warp == 0) tc::tmem_alloc(&s_taddr, 128);
-  for (int k = t; k < S_N; k += NT) sSmall[k] = A.small[k];
-  tc::fence_before();
-  __syncthreads();
-  tc::fence_after();
-  const uint32_t tmem = s_taddr;
-  const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
-  uint32_t ph = 0;
-  bool ok = tc::mbar_wait(&bar_ld, 0);
+  MlpCta M;
+  mlp_begin(M, smem_raw, &bar_ld, &bar_mma, &s_taddr, A.img, A.small);
+  const int t = threadIdx.x;
   const long long ntiles = (A.n + TM - 1) / TM;
-  for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const long long row = tile * TM + t;
     const bool valid = row < A.n;
-    float x[4] = {0.f, 0.f, 0.f, 0.f};
+    float x[4] = {0.f, 0.f, 0.f, 1.f};
     if (valid) {
       const float* f = A.feat + (size_t)row * A.stride;
       x[0] = f[0]; x[1] = f[1]; x[2] = f[2]; x[3] = f[3];
     }
-    for (int c = 0; c < 8; ++c) {
-      float hv[8], hd[8];
-#pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int j = 8 * c + e;
-        float z = sSmall[S_B1 + j];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) z = fmaf(sSmall[S_W1 + 4 * j + i], x[i], z);
-        hv[e] = silu(z);
-        hd[e] = dsilu(z) * sSmall[S_W1 + 4 * j];
-      }
-      store_chunk(sA, t, c, hv);
-      store_chunk(sAd, t, c, hd);
-    }
-    float h3[64], hd3[64];
-    for (int layer = 0; layer < 2; ++layer) {
-      tc::fence_async_smem();
-      tc::fence_before();
-      __syncthreads();
-      if (t == 0) {
-        tc::fence_after();
-        mma_k64(tmem, sA, sm + IF_W + 8192 * layer);
-        mma_k64(tmem + 64, sAd, sm + IF_W + 8192 * layer);
-        tc::mma_commit(&bar_mma);
-      }
-      ok = ok && tc::mbar_wait(&bar_mma, ph);
-      ph ^= 1;
-      tc::fence_after();
-      const float* bias = sSmall + (layer == 0 ? S_B2 : S_B3);
-      for (int c = 0; c < 4; ++c) {
-        float v[16], vd[16];
-        tc::tmem_ld16(tl + 16 * c, v);
-        tc::tmem_ld16(tl + 64 + 16 * c, vd);
-        float hv[16], hd[16];
-#pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          const float z = v[e] + bias[16 * c + e];
-          hv[e] = silu(z);
-          hd[e] = dsilu(z) * vd[e];
-        }
-        if (layer == 0) {
-          store_chunk(sA, t, 2 * c, hv);
-          store_chunk(sA, t, 2 * c + 1, hv + 8);
-          store_chunk(sAd, t, 2 * c, hd);
-          store_chunk(sAd, t, 2 * c + 1, hd + 8);
-        } else {
-#pragma unroll
-          for (int e = 0; e < 16; ++e) {
-            h3[16 * c + e] = hv[e];
-            hd3[16 * c + e] = hd[e];
-          }
-        }
-      }
-    }
-    float y0 = sSmall[S_B4], y1 = sSmall[S_B4 + 1], g0 = 0.f, g1 = 0.f;
-#pragma unroll
-    for (int j = 0; j < 64; ++j) {
-      y0 = fmaf(sSmall[S_W4 + j], h3[j], y0);
-      y1 = fmaf(sSmall[S_W4 + 64 + j], h3[j], y1);
-      g0 = fmaf(sSmall[S_W4 + j], hd3[j], g0);
-      g1 = fmaf(sSmall[S_W4 + 64 + j], hd3[j], g1);
-    }
+    float y0, y1, g0, g1;
+    mlp_tile(M, x, y0, y1, g0, g1);
     if (valid) *reinterpret_cast<float4*>(A.out + 4 * row) = make_float4(y0, y1, g0, g1);
-    // the tiles' next writes to sA/sAd and TMEM come after this barrier
-    tc::fence_before();
-    __syncthreads();
-    tc::fence_after();
   }
-  if (!ok && t == 0) atomicOr(A.err, 1u);
-  tc::fence_before();
-  __syncthreads();
-  tc::fence_after();
-  if (warp == 0) tc::tmem_free(tmem, 128);
+  if (!M.ok && t == 0) atomicOr(A.err, 1u);
+  mlp_end(M);
 }
 
 // ------------------------------------------------------------- validation
@@ -735,7 +589,7 @@ static cudaError_t set_smem() {
   cudaError_t e = cudaFuncSetAttribute(sur::k_sur_train, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        sur::TRAIN_SMEM);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(sur::k_sur_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, sur::INFER_SMEM);
+    e = cudaFuncSetAttribute(sur::k_sur_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, sur::MF_SMEM);
   if (e == cudaSuccess) g_smem_set = true;
   return e;
 }
@@ -801,7 +655,7 @@ cudaError_t sur_launch_infer(const SurBufs& B, const float* feat, int stride, lo
   A.err = B.err;
   const long long tiles = (n + sur::TM - 1) / sur::TM;
   const int g = (int)std::min<long long>(tiles, grid);
-  sur::k_sur_infer<<<g, sur::NT, sur::INFER_SMEM, s>>>(A);
+  sur::k_sur_infer<<<g, sur::NT, sur::MF_SMEM, s>>>(A);
   return cudaGetLastError();
 }
 

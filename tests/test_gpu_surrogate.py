@@ -137,3 +137,74 @@ def test_training_run_learns_the_quadrature():
     assert rep["val_count"] > 15_000
     print(rep)
     assert rep["drag_err_median"] < 0.05 and rep["lnN_err_median"] < 0.1
+
+
+# ------------------------------------------------- the surrogate in the push
+def _sur_cfg(**over):
+    base = dict(drag_law=O.DRAG_SURROGATE, b_pair_threshold=1e30, mc_on=0, pairs_on=0, eta_min=0.0,
+                drag_scale=3e-3)
+    base.update(over)
+    return W.config("C1", n_cells=1024, **base)
+
+
+def _by_id(p):
+    o = np.argsort(p["id"])
+    return {k: v[o] for k, v in p.items()}
+
+
+def test_push_with_surrogate_drag_matches_oracle():
+    """One step with drag law SURROGATE (the network in the push, Newton on
+    its exact derivative), no limiter: momenta agree with the FP64 oracle to
+    1e-5 of the line's scale plus 3 % of the drag's own change of u (the
+    network's BF16 activations), and the integer current matches where the
+    motion does."""
+    from paper_2609_17661_b300 import Line
+    cfg = _sur_cfg()
+    th = _bf16_params(21, scale=1.0)
+    st = W.load_random(cfg, 50_000, u_scale=3000.0, seed=22)
+    line = Line(cfg)
+    line.sur_set_params(th.astype(np.float32))
+    line.set_state(st)
+    line.step(1)
+    g = _by_id(line.particles())
+    S_ = O.Sim(cfg)
+    S_.set_surrogate(th)
+    o_ = W.to_oracle(st, cfg["n_cells"])
+    S_.set_particles(o_["s"], o_["u"], o_["w"], o_["sp"], o_["id"])
+    S_.step(1)
+    o = _by_id(S_.particles())
+    S0 = O.Sim(dict(cfg, drag_law=O.DRAG_OFF))
+    S0.set_particles(o_["s"], o_["u"], o_["w"], o_["sp"], o_["id"])
+    S0.step(1)
+    o0 = _by_id(S0.particles())
+    assert g["id"].tolist() == o["id"].tolist()
+    du_drag = np.abs(o["u"] - o0["u"])
+    assert np.mean(du_drag > 1e-3) > 0.1          # the drag acts (elsewhere the rate is in the Wien tail)
+    tol = 1e-5 * np.max(np.abs(o["u"])) + 0.03 * du_drag
+    err = np.abs(g["u"].astype(np.float64) - o["u"])
+    assert np.all(err <= tol), (np.max(err / tol), int(np.sum(err > tol)))
+    dg, do = line.diag(), S_.diag()
+    assert dg["newton_branch"] == do["newton_branch"] > 10_000
+
+
+def test_push_with_surrogate_limiter_and_scattering_statistics():
+    """Limiter on, scattering and pairs on: branch counts and yields of the
+    GPU's surrogate law agree with the oracle's within what a 1 % drag or rate
+    difference can move (decisions near a threshold may flip)."""
+    from paper_2609_17661_b300 import Line
+    cfg = W.config("C1", n_cells=1024, drag_law=O.DRAG_SURROGATE, drag_scale=3e-3, eta_min=1.0)
+    th = _bf16_params(23, scale=1.0)
+    st = W.load_beam(cfg, 40_000, gamma_lo=20, gamma_hi=2e4, seed=8)
+    line = Line(cfg)
+    line.sur_set_params(th.astype(np.float32))
+    line.set_state(st)
+    line.step(2)
+    S_ = O.Sim(cfg)
+    S_.set_surrogate(th)
+    o_ = W.to_oracle(st, cfg["n_cells"])
+    S_.set_particles(o_["s"], o_["u"], o_["w"], o_["sp"], o_["id"])
+    S_.step(2)
+    dg, do = line.diag(), S_.diag()
+    assert do["scatters"] > 1000
+    for k in ("scatters", "limiter_branch", "newton_branch", "pairs_created"):
+        assert abs(dg[k] - do[k]) <= 0.02 * do[k] + 20, (k, dg[k], do[k])

@@ -207,3 +207,75 @@ def test_reconstruction_inverts_the_targets():
     F, lnN = S.reconstruct(np.stack([D["t1"], D["t2"]], 1), D["lnN_base"], gam, D["b"])
     np.testing.assert_allclose(lnN[m], D["lnN"][m], atol=1e-12)
     assert np.max(S.drag_error(F[m], D["F"][m], D["F_abs"][m])) < 1e-10
+
+
+# ------------------------------------------------- the surrogate drag law
+def test_c_network_matches_numpy_network():
+    """Two separate FP64 implementations of the same network (the C oracle's,
+    used by the drag law, and the numpy one, pinned to autograd) agree."""
+    th = _theta(11, scale=1.7)
+    X, *_ = _batch(20, seed=12)
+    Y, Yd = S.jvp_log10g(th, X)
+    for k in range(20):
+        y, dy = O.sur_forward(th, X[k])
+        np.testing.assert_allclose(y, Y[k], rtol=1e-12, atol=1e-13)
+        np.testing.assert_allclose(dy, Yd[k], rtol=1e-12, atol=1e-13)
+
+
+def _sur_sim(theta, **over):
+    cfg = W.config("C2", n_cells=2048, drag_law=O.DRAG_SURROGATE, **over)
+    S_ = O.Sim(cfg)
+    S_.set_surrogate(theta)
+    return S_, cfg
+
+
+def test_surrogate_drag_is_the_reconstruction_of_the_samples():
+    """The drag law evaluates F^ = gamma b N^ y0 and ln N^ = max(B, LT) + y1
+    from the network at the particle's place: equal to the reconstruction
+    from the sample definitions (orc_sur_point: features and baseline B) fed
+    through the numpy network."""
+    th = _theta(13, scale=0.8)
+    Sim, cfg = _sur_sim(th)
+    N = cfg["n_cells"]
+    k = cfg["drag_scale"] / Sim.scalars()["R_cells"]     # code units per F^ (and per N^)
+    for s_cells, u in [(300.5, 40.0), (1024.0, -3.0), (1800.25, 2500.0), (77.0, 0.3)]:
+        x = Sim.node_interp(0, s_cells)
+        b = Sim.node_interp(1, s_cells)
+        mu = Sim.node_interp(2, s_cells)
+        F, dF, rate = Sim.drag(u, s_cells)
+        lg = math.log10(math.sqrt(1 + u * u))
+        f = S.features(np.array([lg]), np.array([s_cells / N]), np.array([b]), np.array([u]),
+                       cfg["table_log10g_max"])
+        Y, _ = S.forward(th, f)
+        base = O.lib().orc_sur_baseline(C_params(cfg), u, x, b, mu)
+        gam = math.sqrt(1 + u * u)
+        Fr, lnNr = S.reconstruct(Y, np.array([base]), gam, b)
+        assert F / k == pytest.approx(Fr[0], rel=1e-9)
+        assert math.log(rate / k) == pytest.approx(lnNr[0], abs=1e-9)
+
+
+def C_params(cfg):
+    import ctypes
+    return ctypes.byref(O.make_params(cfg))
+
+
+def test_surrogate_drag_derivative_matches_differences():
+    """dF/du of the surrogate law (used by Newton in the implicit midpoint)
+    equals the central difference of F, across the box and both signs."""
+    th = _theta(14, scale=1.2)
+    Sim, _ = _sur_sim(th)
+    for s_cells, u in [(300.5, 40.0), (1024.0, -3.0), (1800.25, 2500.0), (77.0, 0.3), (1500.0, -700.0)]:
+        F, dF, _ = Sim.drag(u, s_cells)
+        h = 1e-6 * max(1.0, abs(u))
+        Fp, _, _ = Sim.drag(u + h, s_cells)
+        Fm, _, _ = Sim.drag(u - h, s_cells)
+        fd = (Fp - Fm) / (2 * h)
+        assert dF == pytest.approx(fd, rel=2e-5, abs=1e-12 * max(abs(F), 1e-300) + 1e-300)
+
+
+def test_surrogate_law_outside_the_box_is_the_closed_form():
+    th = _theta(15)
+    Sim, cfg = _sur_sim(th)
+    Sc = O.Sim(dict(cfg, drag_law=O.DRAG_CLOSED))
+    u = 3.0e8     # gamma above 10^8
+    assert Sim.drag(u, 500.0) == pytest.approx(Sc.drag(u, 500.0), rel=1e-14)
