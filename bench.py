@@ -287,6 +287,11 @@ def run_gpu(args):
                "d2h_bytes_per_step": 8 * cfg["n_cells"] + 8 * cfg["n_cells"] + 256}
         del Eh
 
+    line.close()
+    sur = None
+    if not args.no_surrogate:
+        sur = surrogate_leg(cfg, view, stream, args.sur_steps, value / max(world, 1), barrier)
+
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cb, _, _ = cpu_baseline(cfg, args.cpu_sample, budget_s=15.0, max_steps=500)
@@ -301,16 +306,68 @@ def run_gpu(args):
                           "particles": n, "sort_every": cfg["sort_every"], "drag": "table",
                           "l2": "inputs (21 B x particles) far larger than the 126 MB L2",
                           "parallelism": f"replicas x{world}"},
-               "roofline": roof, "clocks": clocks, "e2e": e2e, "cpu_baseline": cb,
+               "roofline": roof, "clocks": clocks, "e2e": e2e, "cpu_baseline": cb, "surrogate": sur,
                "gpu_launches": gpu_launches(args.steps, cfg, d0["step"]),
                "pairs_created": d1["pairs_created"] - d0["pairs_created"], "rng_draws": draws,
                "branches": {k: d1[k] - d0[k] for k in ("limiter_branch", "newton_branch", "scatters", "psc_clamped",
                                                        "pairs_rejected_nmax", "lost_north", "lost_south")},
                "setup_s": {"host_state": t_gen}}
         print(json.dumps(out), flush=True)
-    line.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+SUR_TENSOR_FLOP_PER_ROW = 2 * 2 * 2 * 64 * 64   # layers 2 and 3, value and tangent, 2 flop per multiply-add
+
+
+def surrogate_leg(cfg, view, stream, steps, value_plain, barrier):
+    """The same line and state with drag law SURROGATE: the network is trained
+    first (1e7 quadrature samples over r_eq in [2, 30], 20 epochs), then
+    `steps` steps are timed like the plain path."""
+    import torch
+    from paper_2609_17661_b300 import Line
+    cs = dict(cfg, drag_law=3)
+    line = Line(cs, stream=stream.cuda_stream)
+    line.sur_set_params(W.sur_init_params(0))
+    rep = line.train_surrogate(**W.SUR_TRAIN_ENSEMBLE_COSINE)
+    line.set_state(view)
+    line.sort()
+    line.step(1)
+    d0 = line.diag()
+    line.timing(True)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    line.step(steps)
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    d1 = line.diag()
+    line.close()
+    units = d1["push_slots"]
+    rows = d1["sur_rows"] - d0["sur_rows"]
+    push_s = d1["push_ms"] * 1e-3
+    peak = _bf16_peak()
+    tflops = rows * SUR_TENSOR_FLOP_PER_ROW / push_s / 1e12
+    v = units / (ms * 1e-3)
+    return {"value": v, "unit": "particle-steps/s", "steps": steps, "ms_per_step": ms / steps,
+            "vs_plain": v / value_plain, "drag": "surrogate (one network for r_eq in [2, 30], trained in the run)",
+            "network_rows_per_particle_step": rows / max(units, 1),
+            "tensor": {"bound": "tensor", "achieved": tflops, "peak": peak[0], "unit": "TFLOP/s",
+                       "frac": tflops / peak[0], "peak_kind": peak[1],
+                       "flop_per_row": SUR_TENSOR_FLOP_PER_ROW},
+            "training": {k: rep[k] for k in ("steps", "samples_ms", "train_ms", "loss_last", "val_count",
+                                             "drag_err_median", "drag_err_p99", "drag_err_max",
+                                             "lnN_err_median", "lnN_err_p99", "lnN_err_max")}}
+
+
+def _bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops_sustained"]), "measured sustained"
+    except Exception:
+        return 1400.0, "fallback sustained"
 
 
 def gpu_launches(steps, cfg, step0):
@@ -336,6 +393,8 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=200000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--sur-steps", type=int, default=3)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "b300":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

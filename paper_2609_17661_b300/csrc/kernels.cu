@@ -1126,6 +1126,7 @@ __global__ void __launch_bounds__(sur::NT, 1) k_push_sur(DevParams P) {
                                         &C->rng_draws};
     for (int k = 0; k < C_COUNT; ++k)
       if (sCtr[k]) atomicAdd(dst[k], (unsigned long long)sCtr[k]);
+    if (M.passes) atomicAdd(&C->sur_rows, (unsigned long long)M.passes * sur::TM);
     if (!M.ok) atomicOr(P.sur_err, 1u);
   }
   sur::mlp_end(M);

@@ -702,6 +702,7 @@ int pic1d_diag(pic1d_ctx* c, pic1d_diag_t* out) {
   out->newton_branch = C.newton_branch;
   out->nonfinite = C.nonfinite;
   out->rng_draws = C.rng_draws;
+  out->sur_rows = C.sur_rows;
   {
     int rc = timing_collect(c);
     if (rc != PIC1D_OK) return rc;

@@ -24,7 +24,8 @@ struct Counters {
   unsigned long long lost_north, lost_south, injected, injected_dropped;
   unsigned long long scatters, psc_clamped, limiter_branch, newton_branch, nonfinite;
   unsigned long long rng_draws;
-  unsigned long long pad[2];
+  unsigned long long sur_rows;   // rows evaluated by the surrogate network inside the push
+  unsigned long long pad[1];
 };
 
 // Per-step device scalars.

@@ -79,6 +79,7 @@ __device__ __forceinline__ void mma_k64(uint32_t d, const uint8_t* A, const uint
 // (128 columns), the small layers.  All NT threads call it.
 struct MlpCta {
   uint8_t* sm;
+  unsigned passes;   // forward passes made by this CTA
   uint64_t* bar_ld;
   uint64_t* bar_mma;
   uint32_t tmem;
@@ -111,6 +112,7 @@ __device__ __forceinline__ void mlp_begin(MlpCta& M, uint8_t* smem_raw, uint64_t
   tc::fence_after();
   M.tmem = *s_taddr;
   M.ph = 0;
+  M.passes = 0;
   M.ok = tc::mbar_wait(bar_ld, 0);
 }
 
@@ -192,6 +194,7 @@ __device__ __forceinline__ void mlp_tile(MlpCta& M, const float (&x)[4], float& 
   y1 = a1;
   g0 = d0;
   g1 = d1;
+  ++M.passes;
   // the next pass's writes to the tiles and to TMEM come after this barrier
   tc::fence_before();
   __syncthreads();

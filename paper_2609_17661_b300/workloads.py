@@ -282,6 +282,7 @@ SUR_TRAIN = dict(n_samples=10_000_000, epochs=20, batch=8192, lr=1e-3, r_lo=20.0
 SUR_TRAIN_COSINE = dict(SUR_TRAIN, lr=3e-3, lr_final=1e-5)
 # one network for every line of the r_eq in [2, 30] ensemble
 SUR_TRAIN_ENSEMBLE = dict(SUR_TRAIN, r_lo=2.0, r_hi=30.0)
+SUR_TRAIN_ENSEMBLE_COSINE = dict(SUR_TRAIN_ENSEMBLE, lr=3e-3, lr_final=1e-5)
 
 
 def sur_init_params(seed: int = 0) -> np.ndarray:

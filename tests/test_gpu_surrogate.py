@@ -208,3 +208,52 @@ def test_push_with_surrogate_limiter_and_scattering_statistics():
     assert do["scatters"] > 1000
     for k in ("scatters", "limiter_branch", "newton_branch", "pairs_created"):
         assert abs(dg[k] - do[k]) <= 0.02 * do[k] + 20, (k, dg[k], do[k])
+
+
+def test_gain_over_quadrature_and_tables():
+    """What the trained network gains (G8 of the method's design):
+    (i) against the method without it -- the quadrature evaluated per point --
+        it is much faster per evaluation (both on this GPU);
+    (ii) against tables for an ensemble of lines it is one 35 KB network for
+        every line of r_eq in [2, 30] where a table is 1 MiB per line; its
+        accuracy off the table nodes is measured against quadrature beside the
+        bilinear table's (both reported; the table is faster per lookup)."""
+    from paper_2609_17661_b300 import Line
+    cfg = W.config("C2", n_cells=1024)
+    line = Line(cfg)
+    line.sur_set_params(W.sur_init_params(0))
+    rep = line.train_surrogate(**dict(W.SUR_TRAIN_ENSEMBLE, n_samples=4_000_000, epochs=10, lr=3e-3,
+                                      lr_final=1e-5, n_val=50_000))
+    # (i) speed per point: quadrature (32 x 32 directions, FP64) vs network
+    n = 1_000_000
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record()
+    rec = line.sur_samples(77, 0, n, 2.0, 30.0)
+    e1.record()
+    y = line.sur_infer(rec)
+    e2.record()
+    torch.cuda.synchronize()
+    t_quad, t_net = e0.elapsed_time(e1), e1.elapsed_time(e2)
+    assert t_quad / t_net > 20, (t_quad, t_net)
+    # (ii) accuracy off the nodes of a 256 x 256 table on one line (r_eq = 20):
+    # the network (GPU) and the bilinear table (FP64 oracle), both against
+    # quadrature at the same random points
+    m = 4000
+    pts = O.sur_samples(cfg, 78, 0, m, 20.0, 20.0)
+    D = dict(zip(O.SUR_FIELDS, pts.T))
+    keep = (D["lnN"] > S.LE) & (D["F_abs"] > 0)
+    X = torch.from_numpy(np.ascontiguousarray(pts[:, :4], dtype=np.float32)).cuda()
+    Y = line.sur_infer(X).cpu().numpy().astype(np.float64)
+    gam = np.sqrt(1 + D["u"] ** 2)
+    Fn, lnNn = S.reconstruct(Y, D["lnN_base"], gam, D["b"])
+    err_net = S.drag_error(Fn, D["F"], D["F_abs"])[keep]
+    T = O.Sim(dict(cfg, r_eq=20.0, n_cells=4096, drag_law=O.DRAG_TABLE))
+    k = cfg["drag_scale"] / T.scalars()["R_cells"]
+    s_cells = (D["f1"] + 1) / 2 * 4096
+    Ft = np.array([T.drag(u, s)[0] / k for u, s in zip(D["u"], s_cells)])
+    err_tab = S.drag_error(Ft, D["F"], D["F_abs"])[keep]
+    print("gain: quadrature %.1f ms, network %.2f ms per 1e6 points (x%.0f); network 35 KB for all lines vs "
+          "1 MiB table per line; drag error median/p99 network %.2e/%.2e, table %.2e/%.2e; training %s"
+          % (t_quad, t_net, t_quad / t_net, np.median(err_net), np.percentile(err_net, 99),
+             np.median(err_tab), np.percentile(err_tab, 99), {k2: rep[k2] for k2 in ("train_ms", "steps")}))
+    assert np.median(err_net) < 2e-2
