@@ -347,6 +347,60 @@ int pic1d_sur_infer(pic1d_ctx* c, const float* feat_dev, int32_t stride, int64_t
  * Errors: EINVAL, ENOMEM, ECUDA, ETIMEOUT. */
 int pic1d_train_surrogate(pic1d_ctx* c, const pic1d_train_cfg* cfg, pic1d_train_report* rep);
 
+/* ------------------------------------------------------------------------
+ * Ensemble: many independent field lines advanced together (the paper runs
+ * one line per simulation; batching lines of uneven lengths and particle
+ * counts is this library's addition).  Each line is a full context of its
+ * own (its geometry, particles, fields, counters; pic1d_ens_line gives it
+ * for set_state, diag, get_fields, get_particles).  Every phase of a step is
+ * one launch for all lines: a persistent push kernel takes (line, tiles)
+ * items from one queue, one field kernel and one finalize kernel cover all
+ * lines, and each line is sorted every sort_every of its own steps.  A
+ * super-step of 80 steps is captured once as a CUDA graph and replayed
+ * (sort cadences are 10, 20 or 40 steps, so every line's buffer flips an
+ * even number of times per super-step).  Per line the results are those of
+ * the line advanced alone.
+ *
+ * The ensemble runs drag law PIC1D_DRAG_SURROGATE with one network for all
+ * lines: the network of line 0's context (pic1d_sur_set_params or
+ * pic1d_train_surrogate on pic1d_ens_line(e, 0)).  No surface supply.  The
+ * ensemble works on a stream of its own (cuda_stream of the parameters is
+ * not used); pic1d_ens_step is asynchronous, the per-line calls synchronise.
+ * ------------------------------------------------------------------------ */
+typedef struct pic1d_ens pic1d_ens;
+
+/* Create n_lines lines from params[0..n_lines-1] (drag_law SURROGATE,
+ * inject_mode NONE, capacity per line).  Errors: EINVAL, ENOMEM, ECUDA. */
+int pic1d_ens_init(const pic1d_params* params, int32_t n_lines, pic1d_ens** out);
+
+/* The context of one line (owned by the ensemble; NULL if out of range). */
+pic1d_ctx* pic1d_ens_line(pic1d_ens* e, int32_t line);
+
+/* Per-line schedule: push items of chunk_tiles x 128 slots and a sort every
+ * sort_every steps (10, 20 or 40).  Either array may be NULL (unchanged).
+ * Errors: EINVAL. */
+int pic1d_ens_set_schedule(pic1d_ens* e, const int32_t* chunk_tiles, const int32_t* sort_every);
+int pic1d_ens_get_schedule(pic1d_ens* e, int32_t* chunk_tiles, int32_t* sort_every);
+
+/* Advance every line by n_steps: whole super-steps of 80 replay the captured
+ * graph (captured again when the schedule or a line's buffer or step phase
+ * changed), the rest is launched directly.  Errors: EINVAL (no network),
+ * ECUDA. */
+int pic1d_ens_step(pic1d_ens* e, int n_steps);
+
+/* Autotuner: for every pair (chunk_tiles in {1, 4, 16}, sort_every in {10,
+ * 20, 40}) run max(trial_steps, sort_every) real steps of all lines, with
+ * each line's push time measured in SM clocks inside the push and each sort
+ * timed with events; per line keep the pair of least push time per step
+ * plus sort time per sort / sort_every.  The trial steps advance the lines.
+ * Outputs (host, n_lines each, may be NULL): the chosen chunk_tiles and
+ * sort_every and the estimated ms per step.  Errors: EINVAL, ECUDA. */
+int pic1d_ens_tune(pic1d_ens* e, int32_t trial_steps, int32_t* chunk_out, int32_t* cadence_out,
+                   double* cost_ms);
+
+const char* pic1d_ens_last_error(const pic1d_ens* e);
+void pic1d_ens_free(pic1d_ens* e);
+
 /* Message of the last error on this context (never NULL). */
 const char* pic1d_last_error(const pic1d_ctx* c);
 

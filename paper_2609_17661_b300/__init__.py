@@ -25,7 +25,7 @@ import numpy as np
 from . import _lib
 from ._lib import Diag, Params
 
-__all__ = ["Line", "PicError", "make_params", "workloads"]
+__all__ = ["Ensemble", "Line", "PicError", "make_params", "workloads"]
 
 
 class PicError(RuntimeError):
@@ -62,13 +62,18 @@ def _arr(a, dtype):
 class Line:
     """One field line on the GPU (a ``pic1d_ctx``)."""
 
-    def __init__(self, cfg: dict, stream=None):
+    def __init__(self, cfg: dict, stream=None, _handle=None):
         import torch
 
         if not torch.cuda.is_available():
             raise RuntimeError("paper_2609_17661_b300 needs a CUDA device (no CPU path)")
         self.L = _lib.load()
         self.cfg = dict(cfg)
+        self.N = cfg["n_cells"]
+        self._owned = _handle is None
+        if _handle is not None:      # a line owned by an Ensemble
+            self.h = C.c_void_p(_handle)
+            return
         if stream is None:
             stream = torch.cuda.current_stream().cuda_stream
         self._p = make_params(cfg, stream)
@@ -77,7 +82,6 @@ class Line:
         if rc != 0:
             raise PicError(rc, "pic1d_init failed (see stderr)")
         self.h = h
-        self.N = cfg["n_cells"]
 
     def _check(self, rc):
         if rc < 0:
@@ -86,7 +90,8 @@ class Line:
 
     def close(self):
         if getattr(self, "h", None):
-            self.L.pic1d_free(self.h)
+            if getattr(self, "_owned", True):
+                self.L.pic1d_free(self.h)
             self.h = None
 
     def __del__(self):
@@ -230,6 +235,68 @@ class Line:
         rep = _lib.TrainReport()
         self._check(self.L.pic1d_train_surrogate(self.h, C.byref(cfg), C.byref(rep)))
         return {name: getattr(rep, name) for name, _ in _lib.TrainReport._fields_}
+
+
+class Ensemble:
+    """Many independent lines advanced together (a ``pic1d_ens``): one launch
+    per phase of a step for all lines, super-steps replayed as a CUDA graph,
+    per-line schedule from the autotuner."""
+
+    def __init__(self, cfgs):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("paper_2609_17661_b300 needs a CUDA device (no CPU path)")
+        self.L = _lib.load()
+        self.cfgs = [dict(c) for c in cfgs]
+        arr = (Params * len(cfgs))(*[make_params(c, None) for c in cfgs])
+        h = C.c_void_p()
+        rc = self.L.pic1d_ens_init(arr, len(cfgs), C.byref(h))
+        if rc != 0:
+            raise PicError(rc, "pic1d_ens_init failed (see stderr)")
+        self.h = h
+        self.lines = [Line(c, _handle=self.L.pic1d_ens_line(self.h, k)) for k, c in enumerate(self.cfgs)]
+
+    def _check(self, rc):
+        if rc < 0:
+            raise PicError(rc, self.L.pic1d_ens_last_error(self.h).decode())
+        return rc
+
+    def step(self, n=1):
+        self._check(self.L.pic1d_ens_step(self.h, int(n)))
+
+    def schedule(self):
+        n = len(self.cfgs)
+        a, b = np.zeros(n, np.int32), np.zeros(n, np.int32)
+        self._check(self.L.pic1d_ens_get_schedule(self.h, C.c_void_p(a.ctypes.data), C.c_void_p(b.ctypes.data)))
+        return a, b
+
+    def set_schedule(self, chunk_tiles=None, sort_every=None):
+        a = None if chunk_tiles is None else np.ascontiguousarray(chunk_tiles, np.int32)
+        b = None if sort_every is None else np.ascontiguousarray(sort_every, np.int32)
+        self._check(self.L.pic1d_ens_set_schedule(self.h, None if a is None else C.c_void_p(a.ctypes.data),
+                                                  None if b is None else C.c_void_p(b.ctypes.data)))
+
+    def tune(self, trial_steps=10):
+        """pic1d_ens_tune: (chunk_tiles, sort_every, estimated ms per step) per line."""
+        n = len(self.cfgs)
+        a, b, c = np.zeros(n, np.int32), np.zeros(n, np.int32), np.zeros(n)
+        self._check(self.L.pic1d_ens_tune(self.h, int(trial_steps), C.c_void_p(a.ctypes.data),
+                                          C.c_void_p(b.ctypes.data), C.c_void_p(c.ctypes.data)))
+        return a, b, c
+
+    def close(self):
+        if getattr(self, "h", None):
+            for ln in self.lines:
+                ln.h = None
+            self.L.pic1d_ens_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 from . import workloads  # noqa: E402

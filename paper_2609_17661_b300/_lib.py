@@ -95,6 +95,14 @@ SIGNATURES = {
     "pic1d_sur_train_steps": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_double]),
     "pic1d_sur_infer": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int64, C.c_void_p]),
     "pic1d_train_surrogate": (C.c_int, [C.c_void_p, C.POINTER(TrainCfg), C.POINTER(TrainReport)]),
+    "pic1d_ens_init": (C.c_int, [C.POINTER(Params), C.c_int32, C.POINTER(C.c_void_p)]),
+    "pic1d_ens_line": (C.c_void_p, [C.c_void_p, C.c_int32]),
+    "pic1d_ens_set_schedule": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "pic1d_ens_get_schedule": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "pic1d_ens_step": (C.c_int, [C.c_void_p, C.c_int]),
+    "pic1d_ens_tune": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "pic1d_ens_last_error": (C.c_char_p, [C.c_void_p]),
+    "pic1d_ens_free": (None, [C.c_void_p]),
     "pic1d_last_error": (C.c_char_p, [C.c_void_p]),
     "pic1d_free": (None, [C.c_void_p]),
 }

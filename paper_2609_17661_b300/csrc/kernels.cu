@@ -921,185 +921,169 @@ __device__ __forceinline__ void warp_atomic_cell(bool mine, int cell, long long 
     atomicAdd(reinterpret_cast<unsigned long long*>(g + cell), (unsigned long long)sum);
 }
 
+// One tile of 128 slots of the surrogate push (collective over the CTA):
+// slots tile*128 .. tile*128+127 of P's line, n slots in use.
 template <bool NMAX>
-__global__ void __launch_bounds__(sur::NT, 1) k_push_sur(DevParams P) {
-  extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t bar_ld, bar_mma;
-  __shared__ uint32_t s_taddr;
-  __shared__ unsigned s_tile;
-  __shared__ unsigned sCtr[C_COUNT];
-  __shared__ double sRed[2][sur::NT / 32];
-  sur::MlpCta M;
-  sur::mlp_begin(M, smem_raw, &bar_ld, &bar_mma, &s_taddr, P.sur_img, P.sur_small);
+__device__ void sur_tile(const DevParams& P, sur::MlpCta& M, uint32_t tile, uint32_t n, Tally& T) {
   const int t = threadIdx.x, lane = t & 31;
-  if (t < C_COUNT) sCtr[t] = 0;
-  if (t == 0) s_tile = (unsigned)atomicAdd(&P.st->work, 1ull);
-  __syncthreads();
-  const uint32_t n = (uint32_t)P.st->n_slots;
-  const uint32_t ntiles = (n + sur::TM - 1) / sur::TM;
   const uint32_t fmask = (1u << P.F) - 1u;
   const uint32_t half = 1u << (P.F - 1);
-  Tally T;
-#pragma unroll
-  for (int k = 0; k < C_COUNT; ++k) T.c[k] = 0;
-  T.n_lim = T.n_newt = 0;
-  T.ke = T.ke_c = T.kl = T.kl_c = 0.0f;
-  unsigned tile = s_tile;
-  while (tile < ntiles) {
-    const uint32_t idx = tile * sur::TM + t;
-    uint32_t pos0 = 0;
-    float u = 0.0f, w = 0.0f;
-    uint8_t spb = PIC1D_SP_DEAD;
-    if (idx < n) {
-      pos0 = P.pos[idx];
-      u = P.u[idx];
-      w = P.w[idx];
-      spb = P.sp[idx];
-    }
-    const bool valid = idx < n && spb != PIC1D_SP_DEAD;
-    const int sp = spb & 3;
-    const bool ion = (sp == PIC1D_SP_ION), lep = !ion;
-    const float qm = ion ? P.qm[PIC1D_SP_ION] : (sp == PIC1D_SP_POSITRON ? 1.0f : -1.0f);
-    const int qs = (sp == PIC1D_SP_ELECTRON || sp == PIC1D_SP_ATMO) ? -1 : 1;
-    const float mass = ion ? P.mass[PIC1D_SP_ION] : 1.0f;
-    const int cell = valid ? (int)(pos0 >> P.F) : 0;
-    float Ep = 0.0f;
-    Site S;
-    S.x = 1.0f; S.b = 1.0f; S.mu = 0.0f; S.j = 0; S.c = 0.0f;
-    bool zone = false;
-    if (valid) {
-      const uint32_t xg = pos0 < half ? 0u : pos0 - half;
-      int ig = (int)(xg >> P.F);
-      float fg = (float)(xg & fmask) * P.inv2F;
-      if (ig > P.N - 2) { ig = P.N - 2; fg = 1.0f; }
-      const float e0 = __ldg(P.E32 + ig), e1 = __ldg(P.E32 + ig + 1);
-      Ep = fmaf(fg, e1 - e0, e0);
-      zone = __ldg(P.zone + cell) != 0;
-      const float f = (float)(pos0 & fmask) * P.inv2F;
-      S.b = fmaf(f, __ldg(P.nb + cell + 1) - __ldg(P.nb + cell), __ldg(P.nb + cell));
-      S.mu = fmaf(f, __ldg(P.nmu + cell + 1) - __ldg(P.nmu + cell), __ldg(P.nmu + cell));
-      S.x = fmaf(f, __ldg(P.nx + cell + 1) - __ldg(P.nx + cell), __ldg(P.nx + cell));
-    }
-    const bool cont = valid && lep && (P.rics_mode == PIC1D_RICS_DRAG_PLUS_PAIRS || !zone);
-    const bool mc = valid && lep && P.mc_on && zone;
-    const float sL = (float)((double)pos0 / (double)P.top);
-    // 2-4. Strang split with the surrogate drag
-    u = sur_drag_half(P, M, S, sL, u, cont, T.n_lim, T.n_newt);
-    if (valid) u = fmaf(qm * Ep, P.dt, u);
-    u = sur_drag_half(P, M, S, sL, u, cont, T.n_lim, T.n_newt);
-    // 5. Monte-Carlo RICS in the pair zone
-    bool make_pair = false;
-    float Pg = 0.0f;
-    unsigned long long pid = 0;
-    if (__syncthreads_or(mc)) {
-      const DragVal dv = sur_eval(P, M, u, S, sL, mc);
-      if (mc) {
-        float psc = P.drag_k * expf(dv.lnN) * P.dt;
-        if (psc > 1.0f) { psc = 1.0f; ++T.c[C_CLAMP]; }
-        if (psc > 0.0f) {
-          ++T.c[C_DRAW];
-          pid = P.id[idx];
-          const uint4 r = philox4x32_10(
-              make_uint4((uint32_t)pid, (uint32_t)(pid >> 32), (uint32_t)P.step, kTagRics), P.key0, P.key1);
-          if (unit24(r.x) < psc) {
-            ++T.c[C_SCAT];
-            const float beta = u * rsqrtf(fmaf(u, u, 1.0f));
-            const float d = (S.mu > beta) ? 1.0f : -1.0f;
-            const float ct = dipole_cos(unit24(r.y));
-            float uf, Eg;
-            rics_event(S.b, d, u, ct, uf, Eg, Pg);
-            if (P.rics_mode == PIC1D_RICS_SPLIT) u = uf;
-            if (P.pairs_on && Eg >= P.pair_e_thr) make_pair = true;
-          }
-        }
-      }
-    }
-    // 6. move, 7. deposit
-    long long xm = 0, x0 = 0, xp = 0;
-    uint32_t p1 = pos0;
-    bool lost = false;
-    const int wint = __float2int_rn(w * 4096.0f);
-    if (valid) {
-      if (!isfinite(u)) {
-        ++T.c[C_NONFIN];
-        u = 0.0f;
-        lost = true;
-        make_pair = false;
-      } else {
-        const float q = fmaf(u, u, 1.0f);
-        const float r = rsqrtf(q);
-        const int dfix = __float2int_rn(P.dt * (u * r) * (float)(1u << P.F));
-        const float e = w * mass * __fdividef(u * u * r, 1.0f + r);
-        const bool lostN = dfix < 0 && (uint32_t)(-dfix) > pos0;
-        const bool lostS = dfix > 0 && (uint32_t)dfix > P.top1 - pos0;
-        lost = lostN || lostS;
-        kahan(T.ke, T.ke_c, lost ? 0.0f : e);
-        kahan(T.kl, T.kl_c, lost ? e : 0.0f);
-        if (!lost) {
-          p1 = pos0 + (uint32_t)dfix;
-          path_split(dfix, pos0 & fmask, P.F, qs * wint, xm, x0, xp);
-        } else {
-          ++T.c[lostN ? C_LOSTN : C_LOSTS];
-          const int dd = lostN ? -(int)pos0 : (int)(P.top - (long long)pos0);
-          path_split(dd, pos0 & fmask, P.F, qs * wint, xm, x0, xp);
-          p1 = lostN ? 0u : (uint32_t)(P.top - 1);
-          if (make_pair) ++T.c[C_WALL];
-          make_pair = false;
-        }
-      }
-    }
-    if (make_pair) {
-      if (NMAX && P.dens_cur[(int)(p1 >> P.F)] >= P.nmax_int) {
-        ++T.c[C_REJ];
-        make_pair = false;
-      }
-    }
-    warp_atomic_cell(xm != 0, cell - 1, xm, P.J, P.N);
-    warp_atomic_cell(x0 != 0, cell, x0, P.J, P.N);
-    warp_atomic_cell(xp != 0, cell + 1, xp, P.J, P.N);
-    if (NMAX) {
-      const int cD = (int)(p1 >> P.F);
-      const bool wd = valid && lep && !lost && __ldg(P.dens_flag + cD) != 0;
-      warp_atomic_cell(wd, cD, (long long)wint, P.dens_next, P.N);
-    }
-    // pair append, warp-aggregated
-    const unsigned mp = __ballot_sync(0xffffffffu, make_pair);
-    if (mp) {
-      const int leader = __ffs(mp) - 1;
-      long long slot0 = 0;
-      if (lane == leader)
-        slot0 = atomicAdd(reinterpret_cast<unsigned long long*>(&P.st->append), (unsigned long long)(2 * __popc(mp)));
-      slot0 = __shfl_sync(0xffffffffu, slot0, leader);
-      if (make_pair) {
-        const long long dst = (long long)n + slot0 + 2ll * __popc(mp & lanemask_lt());
-        if (dst + 2 > P.cap) {
-          ++T.c[C_DROP];
-        } else {
-          ++T.c[C_PAIRS];
-          for (int mm = 0; mm < 2; ++mm) {
-            P.pos[dst + mm] = p1;
-            P.u[dst + mm] = 0.5f * Pg;
-            P.w[dst + mm] = w;
-            P.sp[dst + mm] = (mm == 0) ? PIC1D_SP_ELECTRON : PIC1D_SP_POSITRON;
-            P.id[dst + mm] = pair_child_id(pid, P.step, mm);
-          }
-          if (NMAX && __ldg(P.dens_flag + (p1 >> P.F)))
-            atomicAdd(reinterpret_cast<unsigned long long*>(P.dens_next + (int)(p1 >> P.F)),
-                      (unsigned long long)(2ll * wint));
-        }
-      }
-    }
-    if (valid) {
-      P.pos[idx] = p1;
-      P.u[idx] = u;
-      if (lost) P.sp[idx] = PIC1D_SP_DEAD;
-    }
-    __syncthreads();
-    if (t == 0) s_tile = (unsigned)atomicAdd(&P.st->work, 1ull);
-    __syncthreads();
-    tile = s_tile;
+  const uint32_t idx = tile * sur::TM + t;
+  uint32_t pos0 = 0;
+  float u = 0.0f, w = 0.0f;
+  uint8_t spb = PIC1D_SP_DEAD;
+  if (idx < n) {
+    pos0 = P.pos[idx];
+    u = P.u[idx];
+    w = P.w[idx];
+    spb = P.sp[idx];
   }
-  // counters and energy totals of the block
+  const bool valid = idx < n && spb != PIC1D_SP_DEAD;
+  const int sp = spb & 3;
+  const bool ion = (sp == PIC1D_SP_ION), lep = !ion;
+  const float qm = ion ? P.qm[PIC1D_SP_ION] : (sp == PIC1D_SP_POSITRON ? 1.0f : -1.0f);
+  const int qs = (sp == PIC1D_SP_ELECTRON || sp == PIC1D_SP_ATMO) ? -1 : 1;
+  const float mass = ion ? P.mass[PIC1D_SP_ION] : 1.0f;
+  const int cell = valid ? (int)(pos0 >> P.F) : 0;
+  float Ep = 0.0f;
+  Site S;
+  S.x = 1.0f; S.b = 1.0f; S.mu = 0.0f; S.j = 0; S.c = 0.0f;
+  bool zone = false;
+  if (valid) {
+    const uint32_t xg = pos0 < half ? 0u : pos0 - half;
+    int ig = (int)(xg >> P.F);
+    float fg = (float)(xg & fmask) * P.inv2F;
+    if (ig > P.N - 2) { ig = P.N - 2; fg = 1.0f; }
+    const float e0 = __ldg(P.E32 + ig), e1 = __ldg(P.E32 + ig + 1);
+    Ep = fmaf(fg, e1 - e0, e0);
+    zone = __ldg(P.zone + cell) != 0;
+    const float f = (float)(pos0 & fmask) * P.inv2F;
+    S.b = fmaf(f, __ldg(P.nb + cell + 1) - __ldg(P.nb + cell), __ldg(P.nb + cell));
+    S.mu = fmaf(f, __ldg(P.nmu + cell + 1) - __ldg(P.nmu + cell), __ldg(P.nmu + cell));
+    S.x = fmaf(f, __ldg(P.nx + cell + 1) - __ldg(P.nx + cell), __ldg(P.nx + cell));
+  }
+  const bool cont = valid && lep && (P.rics_mode == PIC1D_RICS_DRAG_PLUS_PAIRS || !zone);
+  const bool mc = valid && lep && P.mc_on && zone;
+  const float sL = (float)((double)pos0 / (double)P.top);
+  // 2-4. Strang split with the surrogate drag
+  u = sur_drag_half(P, M, S, sL, u, cont, T.n_lim, T.n_newt);
+  if (valid) u = fmaf(qm * Ep, P.dt, u);
+  u = sur_drag_half(P, M, S, sL, u, cont, T.n_lim, T.n_newt);
+  // 5. Monte-Carlo RICS in the pair zone
+  bool make_pair = false;
+  float Pg = 0.0f;
+  unsigned long long pid = 0;
+  if (__syncthreads_or(mc)) {
+    const DragVal dv = sur_eval(P, M, u, S, sL, mc);
+    if (mc) {
+      float psc = P.drag_k * expf(dv.lnN) * P.dt;
+      if (psc > 1.0f) { psc = 1.0f; ++T.c[C_CLAMP]; }
+      if (psc > 0.0f) {
+        ++T.c[C_DRAW];
+        pid = P.id[idx];
+        const uint4 r = philox4x32_10(
+            make_uint4((uint32_t)pid, (uint32_t)(pid >> 32), (uint32_t)P.step, kTagRics), P.key0, P.key1);
+        if (unit24(r.x) < psc) {
+          ++T.c[C_SCAT];
+          const float beta = u * rsqrtf(fmaf(u, u, 1.0f));
+          const float d = (S.mu > beta) ? 1.0f : -1.0f;
+          const float ct = dipole_cos(unit24(r.y));
+          float uf, Eg;
+          rics_event(S.b, d, u, ct, uf, Eg, Pg);
+          if (P.rics_mode == PIC1D_RICS_SPLIT) u = uf;
+          if (P.pairs_on && Eg >= P.pair_e_thr) make_pair = true;
+        }
+      }
+    }
+  }
+  // 6. move, 7. deposit
+  long long xm = 0, x0 = 0, xp = 0;
+  uint32_t p1 = pos0;
+  bool lost = false;
+  const int wint = __float2int_rn(w * 4096.0f);
+  if (valid) {
+    if (!isfinite(u)) {
+      ++T.c[C_NONFIN];
+      u = 0.0f;
+      lost = true;
+      make_pair = false;
+    } else {
+      const float q = fmaf(u, u, 1.0f);
+      const float r = rsqrtf(q);
+      const int dfix = __float2int_rn(P.dt * (u * r) * (float)(1u << P.F));
+      const float e = w * mass * __fdividef(u * u * r, 1.0f + r);
+      const bool lostN = dfix < 0 && (uint32_t)(-dfix) > pos0;
+      const bool lostS = dfix > 0 && (uint32_t)dfix > P.top1 - pos0;
+      lost = lostN || lostS;
+      kahan(T.ke, T.ke_c, lost ? 0.0f : e);
+      kahan(T.kl, T.kl_c, lost ? e : 0.0f);
+      if (!lost) {
+        p1 = pos0 + (uint32_t)dfix;
+        path_split(dfix, pos0 & fmask, P.F, qs * wint, xm, x0, xp);
+      } else {
+        ++T.c[lostN ? C_LOSTN : C_LOSTS];
+        const int dd = lostN ? -(int)pos0 : (int)(P.top - (long long)pos0);
+        path_split(dd, pos0 & fmask, P.F, qs * wint, xm, x0, xp);
+        p1 = lostN ? 0u : (uint32_t)(P.top - 1);
+        if (make_pair) ++T.c[C_WALL];
+        make_pair = false;
+      }
+    }
+  }
+  if (make_pair) {
+    if (NMAX && P.dens_cur[(int)(p1 >> P.F)] >= P.nmax_int) {
+      ++T.c[C_REJ];
+      make_pair = false;
+    }
+  }
+  warp_atomic_cell(xm != 0, cell - 1, xm, P.J, P.N);
+  warp_atomic_cell(x0 != 0, cell, x0, P.J, P.N);
+  warp_atomic_cell(xp != 0, cell + 1, xp, P.J, P.N);
+  if (NMAX) {
+    const int cD = (int)(p1 >> P.F);
+    const bool wd = valid && lep && !lost && __ldg(P.dens_flag + cD) != 0;
+    warp_atomic_cell(wd, cD, (long long)wint, P.dens_next, P.N);
+  }
+  // pair append, warp-aggregated
+  const unsigned mp = __ballot_sync(0xffffffffu, make_pair);
+  if (mp) {
+    const int leader = __ffs(mp) - 1;
+    long long slot0 = 0;
+    if (lane == leader)
+      slot0 = atomicAdd(reinterpret_cast<unsigned long long*>(&P.st->append), (unsigned long long)(2 * __popc(mp)));
+    slot0 = __shfl_sync(0xffffffffu, slot0, leader);
+    if (make_pair) {
+      const long long dst = (long long)n + slot0 + 2ll * __popc(mp & lanemask_lt());
+      if (dst + 2 > P.cap) {
+        ++T.c[C_DROP];
+      } else {
+        ++T.c[C_PAIRS];
+        for (int mm = 0; mm < 2; ++mm) {
+          P.pos[dst + mm] = p1;
+          P.u[dst + mm] = 0.5f * Pg;
+          P.w[dst + mm] = w;
+          P.sp[dst + mm] = (mm == 0) ? PIC1D_SP_ELECTRON : PIC1D_SP_POSITRON;
+          P.id[dst + mm] = pair_child_id(pid, P.step, mm);
+        }
+        if (NMAX && __ldg(P.dens_flag + (p1 >> P.F)))
+          atomicAdd(reinterpret_cast<unsigned long long*>(P.dens_next + (int)(p1 >> P.F)),
+                    (unsigned long long)(2ll * wint));
+      }
+    }
+  }
+  if (valid) {
+    P.pos[idx] = p1;
+    P.u[idx] = u;
+    if (lost) P.sp[idx] = PIC1D_SP_DEAD;
+  }
+}
+
+// Counters and energy totals of a CTA's tallies into its line (block-wide)
+__device__ void sur_flush_tally(const DevParams& P, Tally& T, unsigned* sCtr, double (*sRed)[sur::NT / 32],
+                                double* ke_dst, bool ke_atomic) {
+  const int t = threadIdx.x, lane = t & 31;
+  if (t < C_COUNT) sCtr[t] = 0;
+  __syncthreads();
   T.c[C_LIM] = T.n_lim;
   T.c[C_NEWT] = T.n_newt;
 #pragma unroll
@@ -1117,7 +1101,8 @@ __global__ void __launch_bounds__(sur::NT, 1) k_push_sur(DevParams P) {
   if (t == 0) {
     double a = 0.0, b = 0.0;
     for (int i = 0; i < sur::NT / 32; ++i) { a += sRed[0][i]; b += sRed[1][i]; }
-    P.ke_partial[blockIdx.x] = a;
+    if (ke_atomic) atomicAdd(ke_dst, a);
+    else *ke_dst = a;
     if (b != 0.0) atomicAdd(&P.st->ke_lost, b);
     Counters* C = P.ctr;
     unsigned long long* dst[C_COUNT] = {&C->scatters, &C->psc_clamped, &C->limiter_branch, &C->newton_branch,
@@ -1126,10 +1111,188 @@ __global__ void __launch_bounds__(sur::NT, 1) k_push_sur(DevParams P) {
                                         &C->rng_draws};
     for (int k = 0; k < C_COUNT; ++k)
       if (sCtr[k]) atomicAdd(dst[k], (unsigned long long)sCtr[k]);
-    if (M.passes) atomicAdd(&C->sur_rows, (unsigned long long)M.passes * sur::TM);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < C_COUNT; ++k) T.c[k] = 0;
+  T.n_lim = T.n_newt = 0;
+  T.ke = T.ke_c = T.kl = T.kl_c = 0.0f;
+}
+
+template <bool NMAX>
+__global__ void __launch_bounds__(sur::NT, 1) k_push_sur(DevParams P) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t bar_ld, bar_mma;
+  __shared__ uint32_t s_taddr;
+  __shared__ unsigned s_tile;
+  __shared__ unsigned sCtr[C_COUNT];
+  __shared__ double sRed[2][sur::NT / 32];
+  sur::MlpCta M;
+  sur::mlp_begin(M, smem_raw, &bar_ld, &bar_mma, &s_taddr, P.sur_img, P.sur_small);
+  const int t = threadIdx.x;
+  if (t == 0) s_tile = (unsigned)atomicAdd(&P.st->work, 1ull);
+  __syncthreads();
+  const uint32_t n = (uint32_t)P.st->n_slots;
+  const uint32_t ntiles = (n + sur::TM - 1) / sur::TM;
+  Tally T;
+#pragma unroll
+  for (int k = 0; k < C_COUNT; ++k) T.c[k] = 0;
+  T.n_lim = T.n_newt = 0;
+  T.ke = T.ke_c = T.kl = T.kl_c = 0.0f;
+  unsigned tile = s_tile;
+  while (tile < ntiles) {
+    sur_tile<NMAX>(P, M, tile, n, T);
+    __syncthreads();
+    if (t == 0) s_tile = (unsigned)atomicAdd(&P.st->work, 1ull);
+    __syncthreads();
+    tile = s_tile;
+  }
+  sur_flush_tally(P, T, sCtr, sRed, P.ke_partial + blockIdx.x, false);
+  if (t == 0) {
+    if (M.passes) atomicAdd(&P.ctr->sur_rows, (unsigned long long)M.passes * sur::TM);
     if (!M.ok) atomicOr(P.sur_err, 1u);
   }
   sur::mlp_end(M);
+}
+
+// --------------------------------------------------------------------------
+// ensemble: every phase of a step is one launch for all lines
+// --------------------------------------------------------------------------
+
+// a line's record into the block's shared DevParams, with the line's step
+// and the pair-cap density buffers of that step
+__device__ void ens_load(const EnsLine* L, int line, DevParams& sP) {
+  const int* src = reinterpret_cast<const int*>(&L[line].P);
+  int* dst = reinterpret_cast<int*>(&sP);
+  for (int k = threadIdx.x; k < (int)(sizeof(DevParams) / 4); k += blockDim.x) dst[k] = src[k];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const long long step = sP.st->step;
+    sP.step = step;
+    sP.dens_cur = L[line].dens[step & 1];
+    sP.dens_next = L[line].dens[(step + 1) & 1];
+  }
+  __syncthreads();
+}
+
+// clear every line's current (start of a step)
+__global__ void k_ens_clear(EnsArgs A) {
+  const int2 it = A.cell_items[blockIdx.x];
+  const EnsLine& L = A.lines[it.x];
+  const int c = it.y + threadIdx.x;
+  if (c < L.P.N) L.P.J[c] = 0;
+}
+
+// the push of every line with the surrogate drag: items (line, tiles) from a
+// global queue; the tallies of an item go to its line
+__global__ void __launch_bounds__(sur::NT, 1) k_ens_push(EnsArgs A) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t bar_ld, bar_mma;
+  __shared__ uint32_t s_taddr;
+  __shared__ unsigned s_item;
+  __shared__ unsigned sCtr[C_COUNT];
+  __shared__ double sRed[2][sur::NT / 32];
+  __shared__ __align__(16) DevParams sP;
+  sur::MlpCta M;
+  sur::mlp_begin(M, smem_raw, &bar_ld, &bar_mma, &s_taddr, A.sur_img, A.sur_small);
+  const int t = threadIdx.x;
+  Tally T;
+#pragma unroll
+  for (int k = 0; k < C_COUNT; ++k) T.c[k] = 0;
+  T.n_lim = T.n_newt = 0;
+  T.ke = T.ke_c = T.kl = T.kl_c = 0.0f;
+  for (;;) {
+    if (t == 0) s_item = (unsigned)atomicAdd(A.work, 1ull);
+    __syncthreads();
+    const unsigned item = s_item;
+    if (item >= (unsigned)A.n_push_items) break;
+    const int4 it = A.push_items[item];
+    ens_load(A.lines, it.x, sP);
+    const long long c0 = clock64();
+    const uint32_t n = (uint32_t)sP.st->n_slots;
+    const unsigned passes0 = M.passes;
+    for (int k = 0; k < it.z; ++k) {
+      const uint32_t tile = (uint32_t)(it.y + k);
+      if (tile * sur::TM >= n) break;
+      if (sP.use_nmax) sur_tile<true>(sP, M, tile, n, T);
+      else sur_tile<false>(sP, M, tile, n, T);
+    }
+    sur_flush_tally(sP, T, sCtr, sRed, &A.lines[it.x].acc[3], true);
+    if (t == 0) {
+      atomicAdd(&A.lines[it.x].cycles, (unsigned long long)(clock64() - c0));
+      if (M.passes > passes0) atomicAdd(&sP.ctr->sur_rows, (unsigned long long)(M.passes - passes0) * sur::TM);
+    }
+    __syncthreads();
+  }
+  if (t == 0 && !M.ok) atomicOr(A.sur_err, 1u);
+  sur::mlp_end(M);
+}
+
+// Ampere update of every line (FP64) and the per-line sums of the step
+__global__ void __launch_bounds__(256) k_ens_field(EnsArgs A) {
+  const int2 it = A.cell_items[blockIdx.x];
+  EnsLine& L = A.lines[it.x];
+  const int c = it.y + threadIdx.x;
+  double so = 0.0, sn = 0.0, s2 = 0.0;
+  if (c < L.P.N) {
+    const double Eo = L.E64[c];
+    const double En = Eo + (L.a - L.cJ * (double)L.P.J[c]);
+    L.E64[c] = En;
+    L.E32[c] = (float)En;
+    if (L.P.use_nmax) L.dens[L.P.st->step & 1][c] = 0;
+    so = Eo;
+    sn = En;
+    s2 = En * En;
+  }
+  __shared__ double red[3][8];
+  for (int d = 16; d > 0; d >>= 1) {
+    so += __shfl_down_sync(0xffffffffu, so, d);
+    sn += __shfl_down_sync(0xffffffffu, sn, d);
+    s2 += __shfl_down_sync(0xffffffffu, s2, d);
+  }
+  const int wid = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) { red[0][wid] = so; red[1][wid] = sn; red[2][wid] = s2; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double x = 0, y = 0, z = 0;
+    for (int i = 0; i < 8; ++i) { x += red[0][i]; y += red[1][i]; z += red[2][i]; }
+    atomicAdd(&L.acc[0], x);
+    atomicAdd(&L.acc[1], y);
+    atomicAdd(&L.acc[2], z);
+  }
+}
+
+// per-line scalars of the step and slot bookkeeping (as k_finalize); the
+// next step's push queue starts empty
+__global__ void k_ens_finalize(EnsArgs A) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l == 0) *A.work = 0;
+  if (l >= A.n_lines) return;
+  EnsLine& L = A.lines[l];
+  StepState* st = L.P.st;
+  st->field_energy = L.acc[2] / (8.0 * 3.141592653589793);
+  st->vc = -L.acc[1];
+  st->ext_work += L.dt_jext * 0.5 * (L.acc[0] + L.acc[1]);
+  st->kinetic = L.acc[3];
+  const long long n = st->n_slots, app = st->append;
+  long long room = (L.P.cap - n) / 2 * 2;
+  if (room < 0) room = 0;
+  st->n_slots = n + (app < room ? app : room);
+  st->append = 0;
+  st->step += 1;
+  L.acc[0] = L.acc[1] = L.acc[2] = L.acc[3] = 0.0;
+}
+
+// after a line's sort: its current buffer is the other one
+__global__ void k_ens_flip(EnsLine* lines, int line) {
+  EnsLine& L = lines[line];
+  const int c = L.cur ^ 1;
+  L.cur = c;
+  L.P.pos = L.pos[c];
+  L.P.u = L.u[c];
+  L.P.w = L.w[c];
+  L.P.sp = L.sp[c];
+  L.P.id = L.id[c];
 }
 
 // --------------------------------------------------------------------------
@@ -1238,6 +1401,7 @@ __global__ void k_finalize(DevParams P, const double* fpart, int nfb, int npb, d
     if (room < 0) room = 0;
     st->n_slots = n + (app < room ? app : room);
     st->append = 0;
+    st->step += 1;
   }
 }
 
@@ -1546,6 +1710,37 @@ cudaError_t launch_push_sur(const DevParams& P, int grid, cudaStream_t s) {
   }
   if (P.use_nmax) k_push_sur<true><<<grid, sur::NT, sur::MF_SMEM, s>>>(P);
   else k_push_sur<false><<<grid, sur::NT, sur::MF_SMEM, s>>>(P);
+  return cudaGetLastError();
+}
+
+cudaError_t ens_launch_clear(const EnsArgs& A, cudaStream_t s) {
+  if (A.n_cell_items > 0) k_ens_clear<<<A.n_cell_items, 256, 0, s>>>(A);
+  return cudaGetLastError();
+}
+
+cudaError_t ens_launch_push(const EnsArgs& A, int grid, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_ens_push, cudaFuncAttributeMaxDynamicSharedMemorySize, sur::MF_SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_ens_push<<<grid, sur::NT, sur::MF_SMEM, s>>>(A);
+  return cudaGetLastError();
+}
+
+cudaError_t ens_launch_field(const EnsArgs& A, cudaStream_t s) {
+  if (A.n_cell_items > 0) k_ens_field<<<A.n_cell_items, 256, 0, s>>>(A);
+  return cudaGetLastError();
+}
+
+cudaError_t ens_launch_finalize(const EnsArgs& A, cudaStream_t s) {
+  k_ens_finalize<<<(A.n_lines + 127) / 128, 128, 0, s>>>(A);
+  return cudaGetLastError();
+}
+
+cudaError_t ens_launch_flip(EnsLine* lines, int line, cudaStream_t s) {
+  k_ens_flip<<<1, 1, 0, s>>>(lines, line);
   return cudaGetLastError();
 }
 

@@ -592,6 +592,7 @@ int pic1d_set_state(pic1d_ctx* c, int64_t n, const uint32_t* pos, const float* u
   c->step = step;
   StepState st{};
   st.n_slots = n;
+  st.step = step;
   CK(cudaMemcpyAsync(c->st, &st, sizeof(st), cudaMemcpyHostToDevice, c->s), "set_state st");
   CK(cudaMemsetAsync(c->dens[0], 0, c->N * sizeof(long long), c->s), "set_state dens");
   CK(cudaMemsetAsync(c->dens[1], 0, c->N * sizeof(long long), c->s), "set_state dens");
@@ -1038,6 +1039,402 @@ int pic1d_train_surrogate(pic1d_ctx* c, const pic1d_train_cfg* cfg, pic1d_train_
   rep->lnN_err_p99 = pct(le, 0.99);
   rep->lnN_err_max = le.empty() ? 0.0 : *std::max_element(le.begin(), le.end());
   return sur_check(c);
+}
+
+// ------------------------------------------------------------- ensemble
+}  // extern "C"
+
+namespace {
+constexpr int kEnsSuper = 80;               // steps per captured graph
+const int kEnsCadences[3] = {10, 20, 40};   // sort cadences (each divides kEnsSuper / 2)
+const int kEnsChunks[3] = {1, 4, 16};       // tiles of 128 slots per push item
+}  // namespace
+
+struct pic1d_ens {
+  int n = 0;
+  std::vector<pic1d_ctx*> lines;
+  cudaStream_t s = nullptr;
+  int sms = 0;
+  EnsLine* dlines = nullptr;
+  int4* push_items = nullptr;
+  int n_push_items = 0;
+  int2* cell_items = nullptr;
+  int n_cell_items = 0;
+  unsigned long long* work = nullptr;
+  std::vector<int> chunk, cadence;
+  cudaGraphExec_t graph = nullptr;
+  std::vector<long long> graph_phase;       // per line: step mod kEnsSuper at capture
+  std::vector<int> graph_cur;               // per line: buffer at capture
+  bool schedule_dirty = true;
+  std::string err;
+  // autotuner bookkeeping (eager steps)
+  bool time_sorts = false;
+  std::vector<double> sort_ms;
+  std::vector<int> sort_count;
+};
+
+namespace {
+
+int ens_fail(pic1d_ens* e, int code, const std::string& msg) {
+  if (e) e->err = msg;
+  return code;
+}
+
+#define ECK(call, where)                                                                        \
+  do {                                                                                          \
+    cudaError_t e_ = (call);                                                                    \
+    if (e_ != cudaSuccess)                                                                      \
+      return ens_fail(e, e_ == cudaErrorMemoryAllocation ? PIC1D_ENOMEM : PIC1D_ECUDA,          \
+                      std::string(where) + ": " + cudaGetErrorString(e_));                     \
+  } while (0)
+
+EnsLine ens_record(pic1d_ctx* c, pic1d_ctx* net) {
+  EnsLine L{};
+  L.P = dev_params(c);
+  L.P.sur_img = net->sur.img;
+  L.P.sur_small = net->sur.small;
+  L.P.sur_err = net->sur.err;
+  for (int b = 0; b < 2; ++b) {
+    L.pos[b] = c->pos[b]; L.u[b] = c->u[b]; L.w[b] = c->w[b]; L.sp[b] = c->sp[b]; L.id[b] = c->id[b];
+    L.dens[b] = c->dens[b];
+  }
+  L.E64 = c->E64;
+  L.E32 = c->E32;
+  L.a = 4.0 * kPi * c->dt * c->j_ext;
+  L.cJ = 4.0 * kPi * c->q_p * std::ldexp(1.0, -c->F - kWBits);
+  L.dt_jext = c->dt * c->j_ext;
+  L.cur = c->cur;
+  return L;
+}
+
+// upload the line records (the host contexts are the source of truth between calls)
+int ens_sync_records(pic1d_ens* e) {
+  std::vector<EnsLine> h(e->n);
+  for (int l = 0; l < e->n; ++l) h[l] = ens_record(e->lines[l], e->lines[0]);
+  ECK(cudaMemcpyAsync(e->dlines, h.data(), sizeof(EnsLine) * e->n, cudaMemcpyHostToDevice, e->s), "ensemble records");
+  ECK(cudaStreamSynchronize(e->s), "ensemble records");
+  return PIC1D_OK;
+}
+
+// push items: each line's capacity in items of chunk[l] tiles, largest lines first
+int ens_build_items(pic1d_ens* e) {
+  std::vector<int> order(e->n);
+  for (int l = 0; l < e->n; ++l) order[l] = l;
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return e->lines[a]->cap > e->lines[b]->cap; });
+  std::vector<int4> items;
+  for (int l : order) {
+    const long long tiles = (e->lines[l]->cap + 127) / 128;
+    for (long long t0 = 0; t0 < tiles; t0 += e->chunk[l])
+      items.push_back(make_int4(l, (int)t0, (int)std::min<long long>(e->chunk[l], tiles - t0), 0));
+  }
+  std::vector<int2> cells;
+  for (int l = 0; l < e->n; ++l)
+    for (int c0 = 0; c0 < e->lines[l]->N; c0 += 256) cells.push_back(make_int2(l, c0));
+  cudaFree(e->push_items);
+  cudaFree(e->cell_items);
+  e->push_items = nullptr;
+  e->cell_items = nullptr;
+  ECK(cudaMalloc(&e->push_items, sizeof(int4) * std::max<size_t>(1, items.size())), "ensemble items");
+  ECK(cudaMalloc(&e->cell_items, sizeof(int2) * std::max<size_t>(1, cells.size())), "ensemble items");
+  ECK(cudaMemcpyAsync(e->push_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, e->s),
+      "ensemble items");
+  ECK(cudaMemcpyAsync(e->cell_items, cells.data(), sizeof(int2) * cells.size(), cudaMemcpyHostToDevice, e->s),
+      "ensemble items");
+  ECK(cudaStreamSynchronize(e->s), "ensemble items");
+  e->n_push_items = (int)items.size();
+  e->n_cell_items = (int)cells.size();
+  return PIC1D_OK;
+}
+
+EnsArgs ens_args(pic1d_ens* e) {
+  EnsArgs A;
+  A.lines = e->dlines;
+  A.n_lines = e->n;
+  A.push_items = e->push_items;
+  A.n_push_items = e->n_push_items;
+  A.cell_items = e->cell_items;
+  A.n_cell_items = e->n_cell_items;
+  A.work = e->work;
+  A.sur_img = e->lines[0]->sur.img;
+  A.sur_small = e->lines[0]->sur.small;
+  A.sur_err = e->lines[0]->sur.err;
+  return A;
+}
+
+// enqueue k steps of every line on the stream; cur/step give each line's
+// buffer and step at the start and are advanced as the steps would
+int ens_enqueue(pic1d_ens* e, int k, std::vector<int>& cur, std::vector<long long>& step) {
+  const EnsArgs A = ens_args(e);
+  std::vector<cudaEvent_t> evs;
+  std::vector<int> ev_line;
+  for (int i = 0; i < k; ++i) {
+    ECK(ens_launch_clear(A, e->s), "ensemble clear");
+    ECK(ens_launch_push(A, e->sms * kSurPushPerSm, e->s), "ensemble push");
+    ECK(ens_launch_field(A, e->s), "ensemble field");
+    ECK(ens_launch_finalize(A, e->s), "ensemble finalize");
+    for (int l = 0; l < e->n; ++l) {
+      step[l] += 1;
+      if (step[l] % e->cadence[l] != 0) continue;
+      pic1d_ctx* c = e->lines[l];
+      const int keep = c->cur;
+      c->cur = cur[l];
+      DevParams P = dev_params(c);
+      c->cur = keep;
+      const int o = 1 - cur[l];
+      cudaEvent_t a = nullptr, b = nullptr;
+      if (e->time_sorts) {
+        ECK(cudaEventCreate(&a), "ensemble timing");
+        ECK(cudaEventCreate(&b), "ensemble timing");
+        ECK(cudaEventRecord(a, e->s), "ensemble timing");
+      }
+      ECK(launch_sort(P, c->counts, c->offsets, c->bsum, c->pos[o], c->u[o], c->w[o], c->sp[o], c->id[o],
+                      c->push_grid, e->s),
+          "ensemble sort");
+      ECK(ens_launch_flip(e->dlines, l, e->s), "ensemble sort");
+      if (e->time_sorts) {
+        ECK(cudaEventRecord(b, e->s), "ensemble timing");
+        evs.push_back(a);
+        evs.push_back(b);
+        ev_line.push_back(l);
+        e->sort_count[l] += 1;
+      }
+      cur[l] = o;
+    }
+  }
+  if (!evs.empty()) {
+    ECK(cudaStreamSynchronize(e->s), "ensemble timing");
+    for (size_t j = 0; j < ev_line.size(); ++j) {
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, evs[2 * j], evs[2 * j + 1]);
+      e->sort_ms[ev_line[j]] += ms;
+    }
+    for (cudaEvent_t x : evs) cudaEventDestroy(x);
+  }
+  return PIC1D_OK;
+}
+
+void ens_apply(pic1d_ens* e, const std::vector<int>& cur, const std::vector<long long>& step) {
+  for (int l = 0; l < e->n; ++l) {
+    e->lines[l]->cur = cur[l];
+    e->lines[l]->step = step[l];
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int pic1d_ens_init(const pic1d_params* params, int32_t n_lines, pic1d_ens** out) {
+  if (!out) return PIC1D_EINVAL;
+  *out = nullptr;
+  if (!params || n_lines < 1) return PIC1D_EINVAL;
+  for (int l = 0; l < n_lines; ++l) {
+    if (params[l].drag_law != PIC1D_DRAG_SURROGATE || params[l].inject_mode != PIC1D_INJECT_NONE ||
+        params[l].cuda_stream != params[0].cuda_stream) {
+      std::fprintf(stderr, "pic1d_ens_init: line %d: the ensemble runs drag law SURROGATE, no surface supply, "
+                           "and one stream for all lines\n", l);
+      return PIC1D_EINVAL;
+    }
+  }
+  pic1d_ens* e = new pic1d_ens();
+  e->n = n_lines;
+  e->lines.assign(n_lines, nullptr);
+  for (int l = 0; l < n_lines; ++l) {
+    const int rc = pic1d_init(&params[l], &e->lines[l]);
+    if (rc != PIC1D_OK) {
+      std::fprintf(stderr, "pic1d_ens_init: line %d failed (%d)\n", l, rc);
+      pic1d_ens_free(e);
+      return rc;
+    }
+  }
+  // one non-blocking stream of the ensemble's own for every line (a stream
+  // that can be captured into a graph)
+  if (cudaStreamCreateWithFlags(&e->s, cudaStreamNonBlocking) != cudaSuccess) {
+    e->s = nullptr;
+    pic1d_ens_free(e);
+    return PIC1D_ECUDA;
+  }
+  for (pic1d_ctx* c : e->lines) {
+    if (c->s) cudaStreamSynchronize(c->s);
+    c->s = e->s;
+  }
+  e->sms = e->lines[0]->sms;
+  e->chunk.assign(n_lines, 4);
+  e->cadence.assign(n_lines, 20);
+  for (int l = 0; l < n_lines; ++l) {
+    int best = kEnsCadences[0];
+    for (int cd : kEnsCadences)
+      if (std::abs(cd - params[l].sort_every) < std::abs(best - params[l].sort_every)) best = cd;
+    e->cadence[l] = best;
+  }
+  e->sort_ms.assign(n_lines, 0.0);
+  e->sort_count.assign(n_lines, 0);
+  int rc = sur_ensure(e->lines[0]);
+  cudaError_t ce = cudaSuccess;
+  if (rc == PIC1D_OK) ce = cudaMalloc(&e->dlines, sizeof(EnsLine) * n_lines);
+  if (rc == PIC1D_OK && ce == cudaSuccess) ce = cudaMalloc(&e->work, sizeof(unsigned long long));
+  if (rc == PIC1D_OK && ce == cudaSuccess) ce = cudaMemsetAsync(e->work, 0, sizeof(unsigned long long), e->s);
+  if (rc == PIC1D_OK && ce != cudaSuccess) rc = PIC1D_ECUDA;
+  if (rc == PIC1D_OK) rc = ens_build_items(e);
+  if (rc != PIC1D_OK) {
+    pic1d_ens_free(e);
+    return rc;
+  }
+  *out = e;
+  return PIC1D_OK;
+}
+
+pic1d_ctx* pic1d_ens_line(pic1d_ens* e, int32_t line) {
+  if (!e || line < 0 || line >= e->n) return nullptr;
+  return e->lines[line];
+}
+
+int pic1d_ens_set_schedule(pic1d_ens* e, const int32_t* chunk_tiles, const int32_t* sort_every) {
+  if (!e) return PIC1D_EINVAL;
+  for (int l = 0; l < e->n; ++l) {
+    if (chunk_tiles && chunk_tiles[l] < 1) return ens_fail(e, PIC1D_EINVAL, "set_schedule: chunk_tiles < 1");
+    if (sort_every && std::find(std::begin(kEnsCadences), std::end(kEnsCadences), sort_every[l]) ==
+                          std::end(kEnsCadences))
+      return ens_fail(e, PIC1D_EINVAL, "set_schedule: sort_every must be 10, 20 or 40");
+  }
+  for (int l = 0; l < e->n; ++l) {
+    if (chunk_tiles) e->chunk[l] = chunk_tiles[l];
+    if (sort_every) e->cadence[l] = sort_every[l];
+  }
+  e->schedule_dirty = true;
+  return ens_build_items(e);
+}
+
+int pic1d_ens_get_schedule(pic1d_ens* e, int32_t* chunk_tiles, int32_t* sort_every) {
+  if (!e) return PIC1D_EINVAL;
+  for (int l = 0; l < e->n; ++l) {
+    if (chunk_tiles) chunk_tiles[l] = e->chunk[l];
+    if (sort_every) sort_every[l] = e->cadence[l];
+  }
+  return PIC1D_OK;
+}
+
+int pic1d_ens_step(pic1d_ens* e, int n_steps) {
+  if (!e) return PIC1D_EINVAL;
+  if (n_steps < 0) return ens_fail(e, PIC1D_EINVAL, "ens_step: n_steps < 0");
+  if (!e->lines[0]->sur_on) return ens_fail(e, PIC1D_EINVAL, "ens_step: no network (set or train it on line 0)");
+  int rc = ens_sync_records(e);
+  if (rc != PIC1D_OK) return rc;
+  std::vector<int> cur(e->n);
+  std::vector<long long> step(e->n);
+  for (int l = 0; l < e->n; ++l) { cur[l] = e->lines[l]->cur; step[l] = e->lines[l]->step; }
+  while (n_steps >= kEnsSuper) {
+    // a captured super-step replays exactly when every line starts from the
+    // buffer and the step phase it had at capture
+    bool match = e->graph && !e->schedule_dirty;
+    for (int l = 0; l < e->n && match; ++l)
+      match = e->graph_cur[l] == cur[l] && e->graph_phase[l] == step[l] % kEnsSuper;
+    if (!match) {
+      if (e->graph) { cudaGraphExecDestroy(e->graph); e->graph = nullptr; }
+      std::vector<int> c2 = cur;
+      std::vector<long long> s2 = step;
+      cudaGraph_t g = nullptr;
+      ECK(cudaStreamBeginCapture(e->s, cudaStreamCaptureModeThreadLocal), "ensemble capture");
+      rc = ens_enqueue(e, kEnsSuper, c2, s2);
+      cudaError_t ce = cudaStreamEndCapture(e->s, &g);
+      if (rc != PIC1D_OK) { if (g) cudaGraphDestroy(g); return rc; }
+      ECK(ce, "ensemble capture");
+      ce = cudaGraphInstantiate(&e->graph, g, 0);
+      cudaGraphDestroy(g);
+      ECK(ce, "ensemble graph");
+      e->graph_cur = cur;
+      e->graph_phase.resize(e->n);
+      for (int l = 0; l < e->n; ++l) e->graph_phase[l] = step[l] % kEnsSuper;
+      e->schedule_dirty = false;
+    }
+    ECK(cudaGraphLaunch(e->graph, e->s), "ensemble graph launch");
+    for (int l = 0; l < e->n; ++l) {
+      long long sorts = 0;
+      for (long long k = step[l] + 1; k <= step[l] + kEnsSuper; ++k) sorts += (k % e->cadence[l] == 0);
+      if (sorts & 1) cur[l] ^= 1;
+      step[l] += kEnsSuper;
+    }
+    n_steps -= kEnsSuper;
+  }
+  if (n_steps > 0) {
+    rc = ens_enqueue(e, n_steps, cur, step);
+    if (rc != PIC1D_OK) return rc;
+  }
+  ens_apply(e, cur, step);
+  return PIC1D_OK;
+}
+
+int pic1d_ens_tune(pic1d_ens* e, int32_t trial_steps, int32_t* chunk_out, int32_t* cadence_out, double* cost_ms) {
+  if (!e) return PIC1D_EINVAL;
+  if (trial_steps < 1) return ens_fail(e, PIC1D_EINVAL, "ens_tune: trial_steps < 1");
+  if (!e->lines[0]->sur_on) return ens_fail(e, PIC1D_EINVAL, "ens_tune: no network (set or train it on line 0)");
+  int clock_khz = 0;
+  ECK(cudaDeviceGetAttribute(&clock_khz, cudaDevAttrClockRate, 0), "ens_tune");
+  const int nc = 3, nk = 3;
+  std::vector<double> cost((size_t)e->n * nc * nk, 0.0);
+  const std::vector<int> chunk0 = e->chunk, cad0 = e->cadence;
+  for (int ci = 0; ci < nc; ++ci) {
+    for (int ki = 0; ki < nk; ++ki) {
+      for (int l = 0; l < e->n; ++l) { e->chunk[l] = kEnsChunks[ci]; e->cadence[l] = kEnsCadences[ki]; }
+      int rc = ens_build_items(e);
+      if (rc != PIC1D_OK) return rc;
+      rc = ens_sync_records(e);
+      if (rc != PIC1D_OK) return rc;
+      std::vector<int> cur(e->n);
+      std::vector<long long> step(e->n);
+      for (int l = 0; l < e->n; ++l) { cur[l] = e->lines[l]->cur; step[l] = e->lines[l]->step; }
+      // a trial long enough to hold at least one sort of every line
+      const int steps = std::max<int>(trial_steps, kEnsCadences[ki]);
+      std::fill(e->sort_ms.begin(), e->sort_ms.end(), 0.0);
+      std::fill(e->sort_count.begin(), e->sort_count.end(), 0);
+      e->time_sorts = true;
+      rc = ens_enqueue(e, steps, cur, step);
+      e->time_sorts = false;
+      if (rc != PIC1D_OK) return rc;
+      ECK(cudaStreamSynchronize(e->s), "ens_tune");
+      std::vector<EnsLine> h(e->n);
+      ECK(cudaMemcpy(h.data(), e->dlines, sizeof(EnsLine) * e->n, cudaMemcpyDeviceToHost), "ens_tune");
+      ens_apply(e, cur, step);
+      for (int l = 0; l < e->n; ++l) {
+        const double push_ms = (double)h[l].cycles / (double)clock_khz / steps;   // SM-clock ms per step
+        const double sort_ms = e->sort_count[l] ? e->sort_ms[l] / e->sort_count[l] : 0.0;
+        cost[((size_t)l * nc + ci) * nk + ki] = push_ms + sort_ms / kEnsCadences[ki];
+      }
+    }
+  }
+  for (int l = 0; l < e->n; ++l) {
+    int bc = 0, bk = 0;
+    for (int ci = 0; ci < nc; ++ci)
+      for (int ki = 0; ki < nk; ++ki)
+        if (cost[((size_t)l * nc + ci) * nk + ki] < cost[((size_t)l * nc + bc) * nk + bk]) { bc = ci; bk = ki; }
+    e->chunk[l] = kEnsChunks[bc];
+    e->cadence[l] = kEnsCadences[bk];
+    if (chunk_out) chunk_out[l] = e->chunk[l];
+    if (cadence_out) cadence_out[l] = e->cadence[l];
+    if (cost_ms) cost_ms[l] = cost[((size_t)l * nc + bc) * nk + bk];
+  }
+  (void)chunk0;
+  (void)cad0;
+  e->schedule_dirty = true;
+  return ens_build_items(e);
+}
+
+const char* pic1d_ens_last_error(const pic1d_ens* e) {
+  if (!e) return "no ensemble";
+  return e->err.c_str();
+}
+
+void pic1d_ens_free(pic1d_ens* e) {
+  if (!e) return;
+  if (e->s) cudaStreamSynchronize(e->s);
+  if (e->graph) cudaGraphExecDestroy(e->graph);
+  cudaFree(e->dlines);
+  cudaFree(e->push_items);
+  cudaFree(e->cell_items);
+  cudaFree(e->work);
+  for (pic1d_ctx* c : e->lines) pic1d_free(c);
+  if (e->s) cudaStreamDestroy(e->s);
+  delete e;
 }
 
 const char* pic1d_last_error(const pic1d_ctx* c) {

@@ -36,6 +36,7 @@ struct StepState {
   double inj_acc[2];        // RATE injection accumulators (north, south)
   double field_energy, vc, ext_work, kinetic, ke_lost;
   unsigned long long work;  // next chunk of the push's dynamic schedule (cleared before each push)
+  long long step;           // steps taken (kept on the device for the ensemble's captured graphs)
 };
 
 // Everything a particle kernel needs, passed by value.
@@ -152,4 +153,44 @@ cudaError_t sur_launch_update(const SurBufs& B, int tiles, int mode, float lr, i
 cudaError_t sur_launch_infer(const SurBufs& B, const float* feat, int stride, long long n, float* out, int grid,
                              cudaStream_t s);
 cudaError_t sur_launch_val(const float* rec, const float* y, long long n, float* err2, cudaStream_t s);
+}  // namespace pic1d
+
+// ensemble of lines (kernels.cu, pic1d.cu)
+namespace pic1d {
+// device record of one line of an ensemble
+struct EnsLine {
+  DevParams P;                       // pointers of the current particle buffer
+  uint32_t* pos[2];
+  float* u[2];
+  float* w[2];
+  uint8_t* sp[2];
+  uint64_t* id[2];
+  long long* dens[2];
+  double* E64;
+  float* E32;
+  double a, cJ, dt_jext;             // field update constants of the line
+  double acc[4];                     // per-step sums: E_old, E_new, E_new^2, kinetic energy
+  unsigned long long cycles;         // SM clocks spent on the line's push items (autotuner)
+  int cur;
+  int pad;
+};
+
+struct EnsArgs {
+  EnsLine* lines;
+  int n_lines;
+  const int4* push_items;            // (line, first tile, tiles, 0)
+  int n_push_items;
+  const int2* cell_items;            // (line, first cell) of 256-cell blocks
+  int n_cell_items;
+  unsigned long long* work;          // next push item
+  const uint8_t* sur_img;            // the shared network
+  const float* sur_small;
+  unsigned* sur_err;
+};
+
+cudaError_t ens_launch_clear(const EnsArgs& A, cudaStream_t s);
+cudaError_t ens_launch_push(const EnsArgs& A, int grid, cudaStream_t s);
+cudaError_t ens_launch_field(const EnsArgs& A, cudaStream_t s);
+cudaError_t ens_launch_finalize(const EnsArgs& A, cudaStream_t s);
+cudaError_t ens_launch_flip(EnsLine* lines, int line, cudaStream_t s);
 }  // namespace pic1d

@@ -310,3 +310,39 @@ def sur_random_records(n: int, seed: int = 0) -> np.ndarray:
     r[:, 5] = rng.normal(0, 1, n)
     r[:, 6] = (rng.random(n) < 0.8).astype(np.float32)
     return r
+
+
+# ---------------------------------------------------------------- ensemble
+def _dipole_length(r_eq: float, n: int = 200001) -> float:
+    """Arc length (in R*) of the dipole line r = r_eq sin^2(theta) between its
+    footpoints, by the trapezoid rule on the line element (workload sizing)."""
+    th0 = math.asin(math.sqrt(1.0 / r_eq))
+    th = np.linspace(th0, math.pi - th0, n)
+    ds = r_eq * np.sin(th) * np.sqrt(1.0 + 3.0 * np.cos(th) ** 2)
+    return float(np.sum(0.5 * (ds[1:] + ds[:-1]) * np.diff(th)))
+
+
+def ensemble_configs(n_lines: int = 256, seed: int = 4, p_lo: float = 1e4, p_hi: float = 1e7,
+                     n_lo: int = 512, n_hi: int = 65536, r_lo: float = 2.0, r_hi: float = 30.0,
+                     multiplicity: float = 140.0):
+    """The batched workload: n_lines independent lines with r_eq log-uniform
+    in [r_lo, r_hi], cells affine in arc length over [n_lo, n_hi] (rounded to
+    a multiple of 128), twist amplitude j_psi uniform in [0.1, 1] x 28, and
+    macroparticles log-uniform in [p_lo, p_hi] per line (a pair-loaded state
+    of the given multiplicity over n0).  Drag law SURROGATE, no supply.
+    Returns (configs, particles per line)."""
+    rng = np.random.default_rng(seed)
+    r = r_lo * (r_hi / r_lo) ** rng.random(n_lines)
+    Lmin, Lmax = _dipole_length(r_lo), _dipole_length(r_hi)
+    counts = np.rint(p_lo * (p_hi / p_lo) ** rng.random(n_lines)).astype(np.int64)
+    amp = rng.uniform(0.1, 1.0, n_lines)
+    cfgs = []
+    for k in range(n_lines):
+        L = _dipole_length(float(r[k]))
+        N = int(round((n_lo + (L - Lmin) / (Lmax - Lmin) * (n_hi - n_lo)) / 128.0)) * 128
+        N = min(max(N, n_lo), n_hi)
+        ppc = counts[k] / N
+        cfgs.append(config("C1", r_eq=float(r[k]), n_cells=N, drag_law=DRAG_SURROGATE, j_psi=28.0 * amp[k],
+                           n0_ppc=max(ppc / multiplicity, 1e-3), capacity=int(counts[k] * 1.2) + 4096,
+                           seed=1 + k, sort_every=20))
+    return cfgs, counts
