@@ -370,6 +370,79 @@ def _bf16_peak():
         return 1400.0, "fallback sustained"
 
 
+def run_ensemble(args):
+    """The batched workload: 256 lines (r_eq log-uniform in [2, 30], cells
+    affine in arc length over [512, 65536], twist 0.1-1 of j_psi = 28,
+    1e4-1e7 macroparticles each), surrogate drag with one network trained in
+    the run, schedule from the autotuner, timed over whole captured
+    super-steps (80 steps each)."""
+    import torch
+    from paper_2609_17661_b300 import Ensemble
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    cfgs, counts = W.ensemble_configs()
+    t0 = time.perf_counter()
+    states = [W.load_pair_loaded(c, int(n), seed=100 + k) for k, (c, n) in enumerate(zip(cfgs, counts))]
+    t_gen = time.perf_counter() - t0
+    ens = Ensemble(cfgs)
+    ens.lines[0].sur_set_params(W.sur_init_params(0))
+    rep = ens.lines[0].train_surrogate(**W.SUR_TRAIN_ENSEMBLE_COSINE)
+    for ln, st in zip(ens.lines, states):
+        ln.set_state(st)
+        ln.sort()
+    del states
+    t0 = time.perf_counter()
+    chunk, cad, cost = ens.tune(trial_steps=10)
+    t_tune = time.perf_counter() - t0
+    ens.step(80)                      # capture and one warm-up replay
+    torch.cuda.synchronize()
+    slots0 = sum(ln.diag()["n_slots"] for ln in ens.lines)
+    rows0 = sum(ln.diag()["sur_rows"] for ln in ens.lines)
+    steps = max(80, (args.steps // 80) * 80)
+    clk = Clocks(0)
+    clk.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    es = ens.stream()            # the ensemble launches on a stream of its own
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(es)
+    ens.step(steps)
+    e1.record(es)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    diags = [ln.diag() for ln in ens.lines]
+    slots1 = sum(d["n_slots"] for d in diags)
+    rows = sum(d["sur_rows"] for d in diags) - rows0
+    units = 0.5 * (slots0 + slots1) * steps      # slots per step, averaged over the run
+    value = units / (ms * 1e-3)
+    peak = _bf16_peak()
+    tflops = rows * SUR_TENSOR_FLOP_PER_ROW / (ms * 1e-3) / 1e12
+    out = {"metric": "particle-steps/s", "value": value, "unit": "particle-steps/s", "n_gpus": 1,
+           "steps": steps, "warmup": 80, "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic",
+           "config": {"workload": "ensemble of 256 dipole lines, r_eq log-uniform in [2, 30], 512-65536 cells "
+                                  "affine in arc length, 1e4-1e7 macroparticles each, surrogate drag",
+                      "lines": len(cfgs), "particles": int(counts.sum()),
+                      "cells": int(sum(c["n_cells"] for c in cfgs)), "parallelism": "one GPU, all lines per launch",
+                      "l2": "inputs far larger than the 126 MB L2"},
+           "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak[0], "unit": "TFLOP/s",
+                        "frac": tflops / peak[0], "peak_kind": peak[1], "kernel": "k_ens_push (network layers)",
+                        "traffic": None},
+           "clocks": clocks,
+           "autotuner": {"chunk_tiles": {str(k): int((chunk == k).sum()) for k in (1, 4, 16)},
+                         "sort_every": {str(k): int((cad == k).sum()) for k in (10, 20, 40)},
+                         "tune_s": t_tune},
+           "training": {k: rep[k] for k in ("steps", "samples_ms", "train_ms", "drag_err_median", "drag_err_p99",
+                                            "lnN_err_median", "lnN_err_p99")},
+           "gpu_launches": 4 * steps + sum(7 * (steps // int(c)) for c in cad),
+           "setup_s": {"host_state": t_gen}}
+    print(json.dumps(out), flush=True)
+    ens.close()
+
+
 def gpu_launches(steps, cfg, step0):
     """Kernels of this library launched in the timed region: per step push,
     field, finalize (+ inject with surface supply); per sort hist, scan
@@ -385,7 +458,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
-    ap.add_argument("--workload", default="C5", choices=["C5", "C2", "C1"])
+    ap.add_argument("--workload", default="C5", choices=["C5", "C2", "C1", "C4"])
     ap.add_argument("--particles", type=float, default=1e9)
     ap.add_argument("--cells", type=int, default=0,
                     help="override the line's cell count (smaller lines at the same density for ncu captures)")
@@ -400,6 +473,8 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "C4":
+        run_ensemble(args)
     else:
         run_gpu(args)
 

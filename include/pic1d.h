@@ -398,6 +398,9 @@ int pic1d_ens_step(pic1d_ens* e, int n_steps);
 int pic1d_ens_tune(pic1d_ens* e, int32_t trial_steps, int32_t* chunk_out, int32_t* cadence_out,
                    double* cost_ms);
 
+/* The ensemble's CUDA stream (a cudaStream_t), for events and synchronisation. */
+void* pic1d_ens_stream(pic1d_ens* e);
+
 const char* pic1d_ens_last_error(const pic1d_ens* e);
 void pic1d_ens_free(pic1d_ens* e);
 

@@ -265,6 +265,11 @@ class Ensemble:
     def step(self, n=1):
         self._check(self.L.pic1d_ens_step(self.h, int(n)))
 
+    def stream(self):
+        """The ensemble's stream as a torch.cuda.ExternalStream."""
+        import torch
+        return torch.cuda.ExternalStream(self.L.pic1d_ens_stream(self.h))
+
     def schedule(self):
         n = len(self.cfgs)
         a, b = np.zeros(n, np.int32), np.zeros(n, np.int32)

@@ -1419,6 +1419,8 @@ int pic1d_ens_tune(pic1d_ens* e, int32_t trial_steps, int32_t* chunk_out, int32_
   return ens_build_items(e);
 }
 
+void* pic1d_ens_stream(pic1d_ens* e) { return e ? reinterpret_cast<void*>(e->s) : nullptr; }
+
 const char* pic1d_ens_last_error(const pic1d_ens* e) {
   if (!e) return "no ensemble";
   return e->err.c_str();

@@ -62,7 +62,8 @@ def _compare(ens, singles):
         for f in ("step", "n_alive", "pairs_created", "scatters", "limiter_branch", "newton_branch",
                   "lost_north", "lost_south", "rng_draws"):
             assert d0[f] == d1[f], (k, f, d0[f], d1[f])
-        assert d0["kinetic_energy"] == pytest.approx(d1["kinetic_energy"], rel=1e-9)
+        # per-thread FP32 (compensated) energy sums group the particles by schedule
+        assert d0["kinetic_energy"] == pytest.approx(d1["kinetic_energy"], rel=1e-6)
 
 
 def test_ensemble_equals_lines_alone():
