@@ -244,12 +244,63 @@ __device__ __forceinline__ void warp_flush(long long (&a)[3], int c_ref, long lo
 // --------------------------------------------------------------------------
 enum { C_SCAT, C_CLAMP, C_LIM, C_NEWT, C_NONFIN, C_LOSTN, C_LOSTS, C_PAIRS, C_DROP, C_REJ, C_WALL, C_DRAW, C_COUNT };
 
-// Per-thread tallies of one push launch (registers).
+// Tallies of one push launch.  The frequent ones stay in each thread's
+// registers (drag branches, a Kahan-compensated FP32 sum of w m (gamma - 1));
+// rare events are counted straight into the block's shared counters, and the
+// energy carried out at the walls into a shared sum, so that they hold no
+// registers in the particle loop.
 struct Tally {
-  unsigned c[C_COUNT];
+  unsigned* sc;               // the block's counters (C_COUNT, shared memory)
+  float* skl;                 // the block's lost kinetic energy (shared memory)
   unsigned n_lim, n_newt;
-  float ke, ke_c, kl, kl_c;   // Kahan-compensated FP32 sums of w m (gamma - 1)
+  float ke, ke_c;
 };
+
+__device__ __forceinline__ void tally(Tally& T, int k) { atomicAdd(T.sc + k, 1u); }
+
+__device__ __forceinline__ void tally_init(Tally& T, unsigned* sc, float* skl) {
+  T.sc = sc;
+  T.skl = skl;
+  T.n_lim = T.n_newt = 0;
+  T.ke = T.ke_c = 0.0f;
+}
+
+// The block's tallies into its line (block-wide; sRed holds one double per
+// warp): branch counts and shared counters to the line's counters, kinetic
+// energy to *ke_dst (added atomically or stored), lost energy to the line's
+// state.  The tallies and shared counters start again from zero.
+__device__ void flush_tally(const DevParams& P, Tally& T, double* sRed, double* ke_dst, bool ke_atomic) {
+  const int t = threadIdx.x, lane = t & 31;
+  const unsigned a = __reduce_add_sync(0xffffffffu, T.n_lim), b = __reduce_add_sync(0xffffffffu, T.n_newt);
+  if (lane == 0) {
+    if (a) atomicAdd(T.sc + C_LIM, a);
+    if (b) atomicAdd(T.sc + C_NEWT, b);
+  }
+  double ked = (double)T.ke - (double)T.ke_c;
+  for (int d = 16; d > 0; d >>= 1) ked += __shfl_down_sync(0xffffffffu, ked, d);
+  if (lane == 0) sRed[t >> 5] = ked;
+  __syncthreads();
+  if (t == 0) {
+    double ke = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) ke += sRed[i];
+    if (ke_atomic) atomicAdd(ke_dst, ke);
+    else *ke_dst = ke;
+    if (*T.skl != 0.0f) atomicAdd(&P.st->ke_lost, (double)*T.skl);
+    *T.skl = 0.0f;
+    Counters* C = P.ctr;
+    unsigned long long* dst[C_COUNT] = {&C->scatters, &C->psc_clamped, &C->limiter_branch, &C->newton_branch,
+                                        &C->nonfinite, &C->lost_north, &C->lost_south, &C->pairs_created,
+                                        &C->pairs_dropped_cap, &C->pairs_rejected_nmax, &C->pairs_lost_wall,
+                                        &C->rng_draws};
+    for (int k = 0; k < C_COUNT; ++k) {
+      if (T.sc[k]) atomicAdd(dst[k], (unsigned long long)T.sc[k]);
+      T.sc[k] = 0;
+    }
+  }
+  __syncthreads();
+  T.n_lim = T.n_newt = 0;
+  T.ke = T.ke_c = 0.0f;
+}
 
 __device__ __forceinline__ void kahan(float& s, float& c, float x) {
   const float y = x - c, t = s + y;
@@ -342,14 +393,14 @@ __device__ __forceinline__ PushOut push_one(const DevParams& P, uint32_t idx, ui
   if (mc) {
     const DragVal dv = drag_eval(P, u, S, false);
     float psc = P.drag_k * expf(dv.lnN) * P.dt;
-    if (psc > 1.0f) { psc = 1.0f; ++T.c[C_CLAMP]; }
+    if (psc > 1.0f) { psc = 1.0f; tally(T, C_CLAMP); }
     if (psc > 0.0f) {
-      ++T.c[C_DRAW];
+      tally(T, C_DRAW);
       o.pid = P.id[idx];
       const uint4 r = philox4x32_10(
           make_uint4((uint32_t)o.pid, (uint32_t)(o.pid >> 32), (uint32_t)P.step, kTagRics), P.key0, P.key1);
       if (unit24(r.x) < psc) {
-        ++T.c[C_SCAT];
+        tally(T, C_SCAT);
         const float beta = u * rsqrtf(fmaf(u, u, 1.0f));
         const float d = (S.mu > beta) ? 1.0f : -1.0f;
         const float ct = dipole_cos(unit24(r.y));
@@ -365,7 +416,7 @@ __device__ __forceinline__ PushOut push_one(const DevParams& P, uint32_t idx, ui
   const int sw0 = qs * wint;
   if (!isfinite(u)) {
     // removed in place: no current, counted (the step reports PIC1D_ENUMERIC)
-    ++T.c[C_NONFIN];
+    tally(T, C_NONFIN);
     o.u = 0.0f;
     o.pos = pos0;
     o.lost = true;
@@ -379,7 +430,7 @@ __device__ __forceinline__ PushOut push_one(const DevParams& P, uint32_t idx, ui
   const bool lostS = dfix > 0 && (uint32_t)dfix > P.top1 - pos0;
   o.lost = lostN || lostS;
   kahan(T.ke, T.ke_c, o.lost ? 0.0f : e);
-  kahan(T.kl, T.kl_c, o.lost ? e : 0.0f);
+  if (o.lost) atomicAdd(T.skl, e);
   // 7. charge-conserving deposit: signed length of the path inside each cell
   uint32_t p1;
   if (!o.lost) {
@@ -394,18 +445,18 @@ __device__ __forceinline__ PushOut push_one(const DevParams& P, uint32_t idx, ui
   } else {
     // leaves through a wall: the path is clamped at the conductor (64-bit: the
     // southern wall sits at top, which may be 2^32)
-    ++T.c[lostN ? C_LOSTN : C_LOSTS];
+    tally(T, lostN ? C_LOSTN : C_LOSTS);
     // the path ends at the wall: to node 0 from cell 0, or to node N from cell N-1
     const int d = lostN ? -(int)pos0 : (int)(P.top - (long long)pos0);
     path_split(d, pos0 & fmask, P.F, sw0, o.xm, o.x0, o.xp);
     o.pos = lostN ? 0u : (uint32_t)(P.top - 1);
-    if (make_pair) ++T.c[C_WALL];     // the parent left the line: no pair
+    if (make_pair) tally(T, C_WALL);     // the parent left the line: no pair
     make_pair = false;
   }
   o.u = u;
   if (make_pair) {
     if (NMAX && P.dens_cur[(int)(o.pos >> P.F)] >= P.nmax_int) {
-      ++T.c[C_REJ];
+      tally(T, C_REJ);
     } else {
       o.want_pair = true;
       o.child_u = 0.5f * Pg;
@@ -463,7 +514,7 @@ __device__ __forceinline__ void push_fast(const DevParams& P, uint32_t pos0, flo
     u = fmaf(qm * Ep, P.dt, u);
   }
   if (!isfinite(u)) {
-    ++T.c[C_NONFIN];
+    tally(T, C_NONFIN);
     o.u = 0.0f;
     o.pos = pos0;
     o.lost = true;
@@ -473,7 +524,6 @@ __device__ __forceinline__ void push_fast(const DevParams& P, uint32_t pos0, flo
   const float r = rsqrtf(q);
   const int dfix = __float2int_rn(P.dt * (u * r) * (float)(1u << P.F));
   kahan(T.ke, T.ke_c, w * mass * __fdividef(u * u * r, 1.0f + r));
-  kahan(T.kl, T.kl_c, 0.0f);
   const uint32_t p1 = pos0 + (uint32_t)dfix;
   path_split(dfix, pos0 & fmask, P.F, qs * __float2int_rn(w * 4096.0f), o.xm, o.x0, o.xp);
   o.pos = p1;
@@ -586,9 +636,11 @@ __global__ void __launch_bounds__(kBlock, MINB) k_push(DevParams P) {
   const uint32_t n = (uint32_t)P.st->n_slots;
   const int lane = threadIdx.x & 31;
 
+  __shared__ float sKl;
   if (NMAX)
     for (int i = threadIdx.x; i < kWindow; i += kBlock) sD[i] = 0;
   if (threadIdx.x < C_COUNT) sCtr[threadIdx.x] = 0;
+  if (threadIdx.x == 0) sKl = 0.0f;
   if (threadIdx.x == 0) {
     s_rngD[0] = kWindow;
     s_rngD[1] = -1;
@@ -597,10 +649,7 @@ __global__ void __launch_bounds__(kBlock, MINB) k_push(DevParams P) {
   __syncthreads();
 
   Tally T;
-#pragma unroll
-  for (int k = 0; k < C_COUNT; ++k) T.c[k] = 0;
-  T.n_lim = T.n_newt = 0;
-  T.ke = T.ke_c = T.kl = T.kl_c = 0.0f;
+  tally_init(T, sCtr, &sKl);
   long long aJ[3] = {0, 0, 0};
   int c_ref = -4;
   int dlo = kWindow, dhi = -1;   // density window range this thread touched
@@ -701,9 +750,9 @@ __global__ void __launch_bounds__(kBlock, MINB) k_push(DevParams P) {
             if (o.want_pair) {
               const long long dst = (long long)n + slot0 + 2ll * __popc(m & lanemask_lt());
               if (dst + 2 > P.cap) {
-                ++T.c[C_DROP];
+                tally(T, C_DROP);
               } else {
-                ++T.c[C_PAIRS];
+                tally(T, C_PAIRS);
 #pragma unroll
                 for (int mm = 0; mm < 2; ++mm) {
                   P.pos[dst + mm] = o.pos;
@@ -778,33 +827,7 @@ __global__ void __launch_bounds__(kBlock, MINB) k_push(DevParams P) {
   }
 
   // counters and energy totals of the block
-  T.c[C_LIM] = T.n_lim;
-  T.c[C_NEWT] = T.n_newt;
-#pragma unroll
-  for (int k = 0; k < C_COUNT; ++k) {
-    const unsigned v = __reduce_add_sync(0xffffffffu, T.c[k]);
-    if (lane == 0 && v) atomicAdd(&sCtr[k], v);
-  }
-  double ked = (double)T.ke - (double)T.ke_c, kld = (double)T.kl - (double)T.kl_c;
-  for (int d = 16; d > 0; d >>= 1) {
-    ked += __shfl_down_sync(0xffffffffu, ked, d);
-    kld += __shfl_down_sync(0xffffffffu, kld, d);
-  }
-  if (lane == 0) { sRed[0][threadIdx.x >> 5] = ked; sRed[1][threadIdx.x >> 5] = kld; }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = 0.0, b = 0.0;
-    for (int i = 0; i < kBlock / 32; ++i) { a += sRed[0][i]; b += sRed[1][i]; }
-    P.ke_partial[blockIdx.x] = a;
-    if (b != 0.0) atomicAdd(&P.st->ke_lost, b);
-    Counters* C = P.ctr;
-    unsigned long long* dst[C_COUNT] = {&C->scatters, &C->psc_clamped, &C->limiter_branch, &C->newton_branch,
-                                        &C->nonfinite, &C->lost_north, &C->lost_south, &C->pairs_created,
-                                        &C->pairs_dropped_cap, &C->pairs_rejected_nmax, &C->pairs_lost_wall,
-                                        &C->rng_draws};
-    for (int k = 0; k < C_COUNT; ++k)
-      if (sCtr[k]) atomicAdd(dst[k], (unsigned long long)sCtr[k]);
-  }
+  flush_tally(P, T, sRed[0], P.ke_partial + blockIdx.x, false);
 }
 
 // --------------------------------------------------------------------------
@@ -977,14 +1000,14 @@ __device__ void sur_tile(const DevParams& P, sur::MlpCta& M, uint32_t tile, uint
     const DragVal dv = sur_eval(P, M, u, S, sL, mc);
     if (mc) {
       float psc = P.drag_k * expf(dv.lnN) * P.dt;
-      if (psc > 1.0f) { psc = 1.0f; ++T.c[C_CLAMP]; }
+      if (psc > 1.0f) { psc = 1.0f; tally(T, C_CLAMP); }
       if (psc > 0.0f) {
-        ++T.c[C_DRAW];
+        tally(T, C_DRAW);
         pid = P.id[idx];
         const uint4 r = philox4x32_10(
             make_uint4((uint32_t)pid, (uint32_t)(pid >> 32), (uint32_t)P.step, kTagRics), P.key0, P.key1);
         if (unit24(r.x) < psc) {
-          ++T.c[C_SCAT];
+          tally(T, C_SCAT);
           const float beta = u * rsqrtf(fmaf(u, u, 1.0f));
           const float d = (S.mu > beta) ? 1.0f : -1.0f;
           const float ct = dipole_cos(unit24(r.y));
@@ -1003,7 +1026,7 @@ __device__ void sur_tile(const DevParams& P, sur::MlpCta& M, uint32_t tile, uint
   const int wint = __float2int_rn(w * 4096.0f);
   if (valid) {
     if (!isfinite(u)) {
-      ++T.c[C_NONFIN];
+      tally(T, C_NONFIN);
       u = 0.0f;
       lost = true;
       make_pair = false;
@@ -1016,23 +1039,23 @@ __device__ void sur_tile(const DevParams& P, sur::MlpCta& M, uint32_t tile, uint
       const bool lostS = dfix > 0 && (uint32_t)dfix > P.top1 - pos0;
       lost = lostN || lostS;
       kahan(T.ke, T.ke_c, lost ? 0.0f : e);
-      kahan(T.kl, T.kl_c, lost ? e : 0.0f);
+      if (lost) atomicAdd(T.skl, e);
       if (!lost) {
         p1 = pos0 + (uint32_t)dfix;
         path_split(dfix, pos0 & fmask, P.F, qs * wint, xm, x0, xp);
       } else {
-        ++T.c[lostN ? C_LOSTN : C_LOSTS];
+        tally(T, lostN ? C_LOSTN : C_LOSTS);
         const int dd = lostN ? -(int)pos0 : (int)(P.top - (long long)pos0);
         path_split(dd, pos0 & fmask, P.F, qs * wint, xm, x0, xp);
         p1 = lostN ? 0u : (uint32_t)(P.top - 1);
-        if (make_pair) ++T.c[C_WALL];
+        if (make_pair) tally(T, C_WALL);
         make_pair = false;
       }
     }
   }
   if (make_pair) {
     if (NMAX && P.dens_cur[(int)(p1 >> P.F)] >= P.nmax_int) {
-      ++T.c[C_REJ];
+      tally(T, C_REJ);
       make_pair = false;
     }
   }
@@ -1055,9 +1078,9 @@ __device__ void sur_tile(const DevParams& P, sur::MlpCta& M, uint32_t tile, uint
     if (make_pair) {
       const long long dst = (long long)n + slot0 + 2ll * __popc(mp & lanemask_lt());
       if (dst + 2 > P.cap) {
-        ++T.c[C_DROP];
+        tally(T, C_DROP);
       } else {
-        ++T.c[C_PAIRS];
+        tally(T, C_PAIRS);
         for (int mm = 0; mm < 2; ++mm) {
           P.pos[dst + mm] = p1;
           P.u[dst + mm] = 0.5f * Pg;
@@ -1078,47 +1101,6 @@ __device__ void sur_tile(const DevParams& P, sur::MlpCta& M, uint32_t tile, uint
   }
 }
 
-// Counters and energy totals of a CTA's tallies into its line (block-wide)
-__device__ void sur_flush_tally(const DevParams& P, Tally& T, unsigned* sCtr, double (*sRed)[sur::NT / 32],
-                                double* ke_dst, bool ke_atomic) {
-  const int t = threadIdx.x, lane = t & 31;
-  if (t < C_COUNT) sCtr[t] = 0;
-  __syncthreads();
-  T.c[C_LIM] = T.n_lim;
-  T.c[C_NEWT] = T.n_newt;
-#pragma unroll
-  for (int k = 0; k < C_COUNT; ++k) {
-    const unsigned v = __reduce_add_sync(0xffffffffu, T.c[k]);
-    if (lane == 0 && v) atomicAdd(&sCtr[k], v);
-  }
-  double ked = (double)T.ke - (double)T.ke_c, kld = (double)T.kl - (double)T.kl_c;
-  for (int d = 16; d > 0; d >>= 1) {
-    ked += __shfl_down_sync(0xffffffffu, ked, d);
-    kld += __shfl_down_sync(0xffffffffu, kld, d);
-  }
-  if (lane == 0) { sRed[0][t >> 5] = ked; sRed[1][t >> 5] = kld; }
-  __syncthreads();
-  if (t == 0) {
-    double a = 0.0, b = 0.0;
-    for (int i = 0; i < sur::NT / 32; ++i) { a += sRed[0][i]; b += sRed[1][i]; }
-    if (ke_atomic) atomicAdd(ke_dst, a);
-    else *ke_dst = a;
-    if (b != 0.0) atomicAdd(&P.st->ke_lost, b);
-    Counters* C = P.ctr;
-    unsigned long long* dst[C_COUNT] = {&C->scatters, &C->psc_clamped, &C->limiter_branch, &C->newton_branch,
-                                        &C->nonfinite, &C->lost_north, &C->lost_south, &C->pairs_created,
-                                        &C->pairs_dropped_cap, &C->pairs_rejected_nmax, &C->pairs_lost_wall,
-                                        &C->rng_draws};
-    for (int k = 0; k < C_COUNT; ++k)
-      if (sCtr[k]) atomicAdd(dst[k], (unsigned long long)sCtr[k]);
-  }
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < C_COUNT; ++k) T.c[k] = 0;
-  T.n_lim = T.n_newt = 0;
-  T.ke = T.ke_c = T.kl = T.kl_c = 0.0f;
-}
-
 template <bool NMAX>
 __global__ void __launch_bounds__(sur::NT, 1) k_push_sur(DevParams P) {
   extern __shared__ uint8_t smem_raw[];
@@ -1126,19 +1108,21 @@ __global__ void __launch_bounds__(sur::NT, 1) k_push_sur(DevParams P) {
   __shared__ uint32_t s_taddr;
   __shared__ unsigned s_tile;
   __shared__ unsigned sCtr[C_COUNT];
-  __shared__ double sRed[2][sur::NT / 32];
+  __shared__ float sKl;
+  __shared__ double sRed[sur::NT / 32];
   sur::MlpCta M;
   sur::mlp_begin(M, smem_raw, &bar_ld, &bar_mma, &s_taddr, P.sur_img, P.sur_small);
   const int t = threadIdx.x;
-  if (t == 0) s_tile = (unsigned)atomicAdd(&P.st->work, 1ull);
+  if (t < C_COUNT) sCtr[t] = 0;
+  if (t == 0) {
+    sKl = 0.0f;
+    s_tile = (unsigned)atomicAdd(&P.st->work, 1ull);
+  }
   __syncthreads();
   const uint32_t n = (uint32_t)P.st->n_slots;
   const uint32_t ntiles = (n + sur::TM - 1) / sur::TM;
   Tally T;
-#pragma unroll
-  for (int k = 0; k < C_COUNT; ++k) T.c[k] = 0;
-  T.n_lim = T.n_newt = 0;
-  T.ke = T.ke_c = T.kl = T.kl_c = 0.0f;
+  tally_init(T, sCtr, &sKl);
   unsigned tile = s_tile;
   while (tile < ntiles) {
     sur_tile<NMAX>(P, M, tile, n, T);
@@ -1147,7 +1131,7 @@ __global__ void __launch_bounds__(sur::NT, 1) k_push_sur(DevParams P) {
     __syncthreads();
     tile = s_tile;
   }
-  sur_flush_tally(P, T, sCtr, sRed, P.ke_partial + blockIdx.x, false);
+  flush_tally(P, T, sRed, P.ke_partial + blockIdx.x, false);
   if (t == 0) {
     if (M.passes) atomicAdd(&P.ctr->sur_rows, (unsigned long long)M.passes * sur::TM);
     if (!M.ok) atomicOr(P.sur_err, 1u);
@@ -1191,16 +1175,16 @@ __global__ void __launch_bounds__(sur::NT, 1) k_ens_push(EnsArgs A) {
   __shared__ uint32_t s_taddr;
   __shared__ unsigned s_item;
   __shared__ unsigned sCtr[C_COUNT];
-  __shared__ double sRed[2][sur::NT / 32];
+  __shared__ float sKl;
+  __shared__ double sRed[sur::NT / 32];
   __shared__ __align__(16) DevParams sP;
   sur::MlpCta M;
   sur::mlp_begin(M, smem_raw, &bar_ld, &bar_mma, &s_taddr, A.sur_img, A.sur_small);
   const int t = threadIdx.x;
+  if (t < C_COUNT) sCtr[t] = 0;
+  if (t == 0) sKl = 0.0f;
   Tally T;
-#pragma unroll
-  for (int k = 0; k < C_COUNT; ++k) T.c[k] = 0;
-  T.n_lim = T.n_newt = 0;
-  T.ke = T.ke_c = T.kl = T.kl_c = 0.0f;
+  tally_init(T, sCtr, &sKl);
   for (;;) {
     if (t == 0) s_item = (unsigned)atomicAdd(A.work, 1ull);
     __syncthreads();
@@ -1217,7 +1201,7 @@ __global__ void __launch_bounds__(sur::NT, 1) k_ens_push(EnsArgs A) {
       if (sP.use_nmax) sur_tile<true>(sP, M, tile, n, T);
       else sur_tile<false>(sP, M, tile, n, T);
     }
-    sur_flush_tally(sP, T, sCtr, sRed, &A.lines[it.x].acc[3], true);
+    flush_tally(sP, T, sRed, &A.lines[it.x].acc[3], true);
     if (t == 0) {
       atomicAdd(&A.lines[it.x].cycles, (unsigned long long)(clock64() - c0));
       if (M.passes > passes0) atomicAdd(&sP.ctr->sur_rows, (unsigned long long)(M.passes - passes0) * sur::TM);
