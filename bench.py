@@ -38,10 +38,10 @@ BYTES_PER_CREATED = 21   # pos, u, w, sp, id written per created particle
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_push
 # launch per slot it read, from one ncu capture of the same kernel sources on
-# a smaller line at the same density (1e8 macroparticles, 26,214 cells: 2.1195
+# a smaller line at the same density (1e8 macroparticles, 26,214 cells: 2.1054
 # GB for 1.0e8 slots); traffic grows in proportion to the slots.  Reported
 # only while the kernel sources hash to the captured ones, else null.
-PUSH_TRAFFIC = {"sources_sha256": "541dfcb4ea8587d475c90db5a5ab3cdd5ba72ac8fb72f7c33893dd5e7d248b7d", "bytes_per_slot": 21.195}
+PUSH_TRAFFIC = {"sources_sha256": "00087705c655f5649efc8cd9fef2ad8cb88078db3c0d7c8a0e6abd8596112445", "bytes_per_slot": 21.054}
 PUSH_SOURCES = ("paper_2609_17661_b300/csrc/kernels.cu", "paper_2609_17661_b300/csrc/pic1d_internal.h")
 
 
@@ -317,7 +317,7 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-SUR_TENSOR_FLOP_PER_ROW = 2 * 2 * 2 * 64 * 64   # layers 2 and 3, value and tangent, 2 flop per multiply-add
+SUR_TENSOR_FLOP_PER_ROW = 2 * 2 * 64 * 64   # layers 2 and 3, 2 flop per multiply-add (the tangent doubles it)
 
 
 def surrogate_leg(cfg, view, stream, steps, value_plain, barrier):
@@ -346,14 +346,15 @@ def surrogate_leg(cfg, view, stream, steps, value_plain, barrier):
     d1 = line.diag()
     line.close()
     units = d1["push_slots"]
-    rows = d1["sur_rows"] - d0["sur_rows"]
+    rows = d1["sur_rows"] - d0["sur_rows"] + d1["sur_rows_tangent"] - d0["sur_rows_tangent"]
     push_s = d1["push_ms"] * 1e-3
     peak = _bf16_peak()
     tflops = rows * SUR_TENSOR_FLOP_PER_ROW / push_s / 1e12
     v = units / (ms * 1e-3)
     return {"value": v, "unit": "particle-steps/s", "steps": steps, "ms_per_step": ms / steps,
             "vs_plain": v / value_plain, "drag": "surrogate (one network for r_eq in [2, 30], trained in the run)",
-            "network_rows_per_particle_step": rows / max(units, 1),
+            "network_rows_per_particle_step": (d1["sur_rows"] - d0["sur_rows"]) / max(units, 1),
+            "tangent_rows_per_particle_step": (d1["sur_rows_tangent"] - d0["sur_rows_tangent"]) / max(units, 1),
             "tensor": {"bound": "tensor", "achieved": tflops, "peak": peak[0], "unit": "TFLOP/s",
                        "frac": tflops / peak[0], "peak_kind": peak[1],
                        "flop_per_row": SUR_TENSOR_FLOP_PER_ROW},
@@ -398,7 +399,7 @@ def run_ensemble(args):
     ens.step(80)                      # capture and one warm-up replay
     torch.cuda.synchronize()
     slots0 = sum(ln.diag()["n_slots"] for ln in ens.lines)
-    rows0 = sum(ln.diag()["sur_rows"] for ln in ens.lines)
+    rows0 = sum(ln.diag()["sur_rows"] + ln.diag()["sur_rows_tangent"] for ln in ens.lines)
     steps = max(80, (args.steps // 80) * 80)
     clk = Clocks(0)
     clk.start()
@@ -415,7 +416,7 @@ def run_ensemble(args):
     ms = e0.elapsed_time(e1)
     diags = [ln.diag() for ln in ens.lines]
     slots1 = sum(d["n_slots"] for d in diags)
-    rows = sum(d["sur_rows"] for d in diags) - rows0
+    rows = sum(d["sur_rows"] + d["sur_rows_tangent"] for d in diags) - rows0
     units = 0.5 * (slots0 + slots1) * steps      # slots per step, averaged over the run
     value = units / (ms * 1e-3)
     peak = _bf16_peak()

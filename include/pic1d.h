@@ -132,7 +132,8 @@ typedef struct pic1d_diag_t {
   int64_t scatters, psc_clamped, limiter_branch, newton_branch, nonfinite;
   int64_t rng_draws;        /* Philox draws (one 8-byte id read each) */
   int64_t sur_rows;         /* network rows evaluated inside the push (drag law SURROGATE;
-                               each row: 2 x 2 x 64 x 64 multiply-adds on the tensor cores) */
+                               each row: 2 x 64 x 64 multiply-adds on the tensor cores) */
+  int64_t sur_rows_tangent; /* of which with the forward-mode tangent (as many again) */
   int64_t push_launches;    /* push kernels timed since pic1d_timing(c, 1) */
   double push_ms;           /* their summed CUDA-event durations, ms     */
   int64_t push_slots;       /* sum over those launches of the slots read */

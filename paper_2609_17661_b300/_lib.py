@@ -42,7 +42,7 @@ class Diag(C.Structure):
         ("injected_dropped", C.c_int64),
         ("scatters", C.c_int64), ("psc_clamped", C.c_int64), ("limiter_branch", C.c_int64),
         ("newton_branch", C.c_int64), ("nonfinite", C.c_int64),
-        ("rng_draws", C.c_int64), ("sur_rows", C.c_int64), ("push_launches", C.c_int64), ("push_ms", C.c_double), ("push_slots", C.c_int64),
+        ("rng_draws", C.c_int64), ("sur_rows", C.c_int64), ("sur_rows_tangent", C.c_int64), ("push_launches", C.c_int64), ("push_ms", C.c_double), ("push_slots", C.c_int64),
         ("field_energy", C.c_double), ("kinetic_energy", C.c_double), ("ext_work", C.c_double),
         ("vc", C.c_double), ("ke_lost", C.c_double),
         ("q_p", C.c_double), ("j_ext", C.c_double), ("dt", C.c_double), ("tau_min", C.c_double),

@@ -860,7 +860,8 @@ __device__ __forceinline__ float sur_lnrad(const DevParams& P, float u, float ga
 // particle.  Collective: every thread of the CTA calls it; `want` only says
 // whether the caller uses the result.  Outside the training box (gamma above
 // 10^G, b outside the range of f2) the closed form stands in.
-__device__ DragVal sur_eval(const DevParams& P, sur::MlpCta& M, float u, const Site& S, float sL, bool want) {
+__device__ DragVal sur_eval(const DevParams& P, sur::MlpCta& M, float u, const Site& S, float sL, bool want,
+                           bool with_dF) {
   const float q = fmaf(u, u, 1.0f);
   const float gam = sqrtf(q);
   float x[4];
@@ -871,12 +872,12 @@ __device__ DragVal sur_eval(const DevParams& P, sur::MlpCta& M, float u, const S
   const bool inbox = x[0] <= 1.0f && x[2] >= -1.0f && x[2] <= 1.0f;
   if (!want || !inbox) { x[0] = 0.0f; x[1] = 0.0f; x[2] = 0.0f; }
   float y0, y1, g0, g1;
-  sur::mlp_tile(M, x, y0, y1, g0, g1);
+  sur::mlp_tile(M, x, y0, y1, g0, g1, with_dF);
   DragVal d;
   d.F = d.dF = 0.0f;
   d.lnN = -700.0f;
   if (!want) return d;
-  if (!inbox) return closed_eval(P, u, S, true);
+  if (!inbox) return closed_eval(P, u, S, with_dF);
   float d1, d2;
   const float l1 = sur_lnrad(P, u, gam, S.x, S.b, S.mu, d1);
   const float ths = acosf(fmaxf(-1.0f, fminf(1.0f, S.mu))), am = asinf(fminf(1.0f, 1.0f / S.x));
@@ -891,9 +892,11 @@ __device__ DragVal sur_eval(const DevParams& P, sur::MlpCta& M, float u, const S
   d.lnN = Bc + y1;
   const float N = __expf(d.lnN);
   d.F = gam * S.b * N * y0;
-  const float df0 = 2.0f / P.sur_G * u / (q * 2.302585093f);
-  const float dln = dBc + g1 * df0;
-  d.dF = S.b * N * ((u / gam) * y0 + gam * y0 * dln + gam * g0 * df0);
+  if (with_dF) {
+    const float df0 = 2.0f / P.sur_G * u / (q * 2.302585093f);
+    const float dln = dBc + g1 * df0;
+    d.dF = S.b * N * ((u / gam) * y0 + gam * y0 * dln + gam * g0 * df0);
+  }
   return d;
 }
 
@@ -901,7 +904,7 @@ __device__ DragVal sur_eval(const DevParams& P, sur::MlpCta& M, float u, const S
 __device__ float sur_drag_half(const DevParams& P, sur::MlpCta& M, const Site& S, float sL, float u0, bool act,
                                unsigned& n_lim, unsigned& n_newt) {
   const float h = P.half_dt;
-  const float F0 = P.drag_k * sur_eval(P, M, u0, S, sL, act).F;
+  const float F0 = P.drag_k * sur_eval(P, M, u0, S, sL, act, false).F;
   const bool newton = act && (!P.limiter_on || (fabsf(F0) * P.tau_min < fabsf(u0)));
   float u1 = u0;
   if (act) {
@@ -917,7 +920,7 @@ __device__ float sur_drag_half(const DevParams& P, sur::MlpCta& M, const Site& S
   bool going = newton;
   int it = 0;
   while (__syncthreads_or(going)) {
-    const DragVal d1 = sur_eval(P, M, u1, S, sL, going);
+    const DragVal d1 = sur_eval(P, M, u1, S, sL, going, true);
     if (going) {
       const float F1 = P.drag_k * d1.F;
       const float G = u1 - u0 - 0.5f * h * (F0 + F1);
@@ -997,7 +1000,7 @@ __device__ void sur_tile(const DevParams& P, sur::MlpCta& M, uint32_t tile, uint
   float Pg = 0.0f;
   unsigned long long pid = 0;
   if (__syncthreads_or(mc)) {
-    const DragVal dv = sur_eval(P, M, u, S, sL, mc);
+    const DragVal dv = sur_eval(P, M, u, S, sL, mc, false);
     if (mc) {
       float psc = P.drag_k * expf(dv.lnN) * P.dt;
       if (psc > 1.0f) { psc = 1.0f; tally(T, C_CLAMP); }
@@ -1102,7 +1105,7 @@ __device__ void sur_tile(const DevParams& P, sur::MlpCta& M, uint32_t tile, uint
 }
 
 template <bool NMAX>
-__global__ void __launch_bounds__(sur::NT, 1) k_push_sur(DevParams P) {
+__global__ void __launch_bounds__(sur::NT, 4) k_push_sur(DevParams P) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t bar_ld, bar_mma;
   __shared__ uint32_t s_taddr;
@@ -1134,6 +1137,7 @@ __global__ void __launch_bounds__(sur::NT, 1) k_push_sur(DevParams P) {
   flush_tally(P, T, sRed, P.ke_partial + blockIdx.x, false);
   if (t == 0) {
     if (M.passes) atomicAdd(&P.ctr->sur_rows, (unsigned long long)M.passes * sur::TM);
+    if (M.passes_t) atomicAdd(&P.ctr->sur_rows_tangent, (unsigned long long)M.passes_t * sur::TM);
     if (!M.ok) atomicOr(P.sur_err, 1u);
   }
   sur::mlp_end(M);
@@ -1169,7 +1173,7 @@ __global__ void k_ens_clear(EnsArgs A) {
 
 // the push of every line with the surrogate drag: items (line, tiles) from a
 // global queue; the tallies of an item go to its line
-__global__ void __launch_bounds__(sur::NT, 1) k_ens_push(EnsArgs A) {
+__global__ void __launch_bounds__(sur::NT, 4) k_ens_push(EnsArgs A) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t bar_ld, bar_mma;
   __shared__ uint32_t s_taddr;
@@ -1194,7 +1198,7 @@ __global__ void __launch_bounds__(sur::NT, 1) k_ens_push(EnsArgs A) {
     ens_load(A.lines, it.x, sP);
     const long long c0 = clock64();
     const uint32_t n = (uint32_t)sP.st->n_slots;
-    const unsigned passes0 = M.passes;
+    const unsigned passes0 = M.passes, passes_t0 = M.passes_t;
     for (int k = 0; k < it.z; ++k) {
       const uint32_t tile = (uint32_t)(it.y + k);
       if (tile * sur::TM >= n) break;
@@ -1205,6 +1209,8 @@ __global__ void __launch_bounds__(sur::NT, 1) k_ens_push(EnsArgs A) {
     if (t == 0) {
       atomicAdd(&A.lines[it.x].cycles, (unsigned long long)(clock64() - c0));
       if (M.passes > passes0) atomicAdd(&sP.ctr->sur_rows, (unsigned long long)(M.passes - passes0) * sur::TM);
+      if (M.passes_t > passes_t0)
+        atomicAdd(&sP.ctr->sur_rows_tangent, (unsigned long long)(M.passes_t - passes_t0) * sur::TM);
     }
     __syncthreads();
   }
@@ -1689,6 +1695,11 @@ cudaError_t launch_push_sur(const DevParams& P, int grid, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(k_push_sur<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sur::MF_SMEM);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_push_sur<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sur::MF_SMEM);
+    // the whole unified L1/shared capacity as shared memory: 4 CTAs per SM
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_push_sur<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_push_sur<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
     attr = true;
   }
@@ -1706,6 +1717,7 @@ cudaError_t ens_launch_push(const EnsArgs& A, int grid, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_ens_push, cudaFuncAttributeMaxDynamicSharedMemorySize, sur::MF_SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ens_push, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
     attr = true;
   }

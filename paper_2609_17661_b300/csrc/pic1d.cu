@@ -704,6 +704,7 @@ int pic1d_diag(pic1d_ctx* c, pic1d_diag_t* out) {
   out->nonfinite = C.nonfinite;
   out->rng_draws = C.rng_draws;
   out->sur_rows = C.sur_rows;
+  out->sur_rows_tangent = C.sur_rows_tangent;
   {
     int rc = timing_collect(c);
     if (rc != PIC1D_OK) return rc;

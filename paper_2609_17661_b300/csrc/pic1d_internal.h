@@ -25,7 +25,7 @@ struct Counters {
   unsigned long long scatters, psc_clamped, limiter_branch, newton_branch, nonfinite;
   unsigned long long rng_draws;
   unsigned long long sur_rows;   // rows evaluated by the surrogate network inside the push
-  unsigned long long pad[1];
+  unsigned long long sur_rows_tangent;   // of which with the forward-mode tangent
 };
 
 // Per-step device scalars.

@@ -80,6 +80,7 @@ __device__ __forceinline__ void mma_k64(uint32_t d, const uint8_t* A, const uint
 struct MlpCta {
   uint8_t* sm;
   unsigned passes;   // forward passes made by this CTA
+  unsigned passes_t; // of which with the tangent
   uint64_t* bar_ld;
   uint64_t* bar_mma;
   uint32_t tmem;
@@ -113,6 +114,7 @@ __device__ __forceinline__ void mlp_begin(MlpCta& M, uint8_t* smem_raw, uint64_t
   M.tmem = *s_taddr;
   M.ph = 0;
   M.passes = 0;
+  M.passes_t = 0;
   M.ok = tc::mbar_wait(bar_ld, 0);
 }
 
@@ -124,10 +126,11 @@ __device__ __forceinline__ void mlp_end(MlpCta& M) {
 }
 
 // One forward pass of the CTA's 128 rows (thread t holds row t's inputs x):
-// outputs y0, y1 and their derivatives g0, g1 in x[0].  All NT threads call
-// it; a wait that gives up clears M.ok (the outputs are then meaningless).
+// outputs y0, y1 and, if `tangent` (the same for every thread of the CTA),
+// their derivatives g0, g1 in x[0] (else zero).  All NT threads call it; a
+// wait that gives up clears M.ok (the outputs are then meaningless).
 __device__ __forceinline__ void mlp_tile(MlpCta& M, const float (&x)[4], float& y0, float& y1, float& g0,
-                                         float& g1) {
+                                         float& g1, bool tangent = true) {
   const int t = threadIdx.x, warp = t >> 5;
   uint8_t* sA = M.sm + MF_A;
   uint8_t* sAd = M.sm + MF_AD;
@@ -142,10 +145,10 @@ __device__ __forceinline__ void mlp_tile(MlpCta& M, const float (&x)[4], float& 
 #pragma unroll
       for (int i = 0; i < 4; ++i) z = fmaf(sSmall[S_W1 + 4 * j + i], x[i], z);
       hv[e] = silu(z);
-      hd[e] = dsilu(z) * sSmall[S_W1 + 4 * j];
+      hd[e] = tangent ? dsilu(z) * sSmall[S_W1 + 4 * j] : 0.0f;
     }
     store_chunk(sA, t, c, hv);
-    store_chunk(sAd, t, c, hd);
+    if (tangent) store_chunk(sAd, t, c, hd);
   }
   float a0 = sSmall[S_B4], a1 = sSmall[S_B4 + 1], d0 = 0.f, d1 = 0.f;
   for (int layer = 0; layer < 2; ++layer) {
@@ -155,7 +158,7 @@ __device__ __forceinline__ void mlp_tile(MlpCta& M, const float (&x)[4], float& 
     if (t == 0) {
       tc::fence_after();
       mma_k64(M.tmem, sA, M.sm + MF_W + 8192 * layer);
-      mma_k64(M.tmem + 64, sAd, M.sm + MF_W + 8192 * layer);
+      if (tangent) mma_k64(M.tmem + 64, sAd, M.sm + MF_W + 8192 * layer);
       tc::mma_commit(M.bar_mma);
     }
     M.ok = M.ok && tc::mbar_wait(M.bar_mma, M.ph);
@@ -165,19 +168,21 @@ __device__ __forceinline__ void mlp_tile(MlpCta& M, const float (&x)[4], float& 
     for (int c = 0; c < 4; ++c) {
       float v[16], vd[16];
       tc::tmem_ld16(tl + 16 * c, v);
-      tc::tmem_ld16(tl + 64 + 16 * c, vd);
+      if (tangent) tc::tmem_ld16(tl + 64 + 16 * c, vd);
       float hv[16], hd[16];
 #pragma unroll
       for (int e = 0; e < 16; ++e) {
         const float z = v[e] + bias[16 * c + e];
         hv[e] = silu(z);
-        hd[e] = dsilu(z) * vd[e];
+        hd[e] = tangent ? dsilu(z) * vd[e] : 0.0f;
       }
       if (layer == 0) {
         store_chunk(sA, t, 2 * c, hv);
         store_chunk(sA, t, 2 * c + 1, hv + 8);
-        store_chunk(sAd, t, 2 * c, hd);
-        store_chunk(sAd, t, 2 * c + 1, hd + 8);
+        if (tangent) {
+          store_chunk(sAd, t, 2 * c, hd);
+          store_chunk(sAd, t, 2 * c + 1, hd + 8);
+        }
       } else {
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
@@ -195,6 +200,7 @@ __device__ __forceinline__ void mlp_tile(MlpCta& M, const float (&x)[4], float& 
   g0 = d0;
   g1 = d1;
   ++M.passes;
+  if (tangent) ++M.passes_t;
   // the next pass's writes to the tiles and to TMEM come after this barrier
   tc::fence_before();
   __syncthreads();
