@@ -37,21 +37,23 @@ BYTES_PER_DRAW = 8       # id read of a lepton that draws a Philox number
 BYTES_PER_CREATED = 21   # pos, u, w, sp, id written per created particle
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_push
-# launch per slot it read, from one ncu capture of the same kernel sources on
-# a smaller line at the same density (1e8 macroparticles, 26,214 cells: 2.1054
+# launch per slot it read, from one ncu capture of the same push source on a
+# smaller line at the same density (1e8 macroparticles, 26,214 cells: 2.1054
 # GB for 1.0e8 slots); traffic grows in proportion to the slots.  Reported
-# only while the kernel sources hash to the captured ones, else null.
-PUSH_TRAFFIC = {"sources_sha256": "00087705c655f5649efc8cd9fef2ad8cb88078db3c0d7c8a0e6abd8596112445", "bytes_per_slot": 21.054}
-PUSH_SOURCES = ("paper_2609_17661_b300/csrc/kernels.cu", "paper_2609_17661_b300/csrc/pic1d_internal.h")
+# only while the push's source -- kernels.cu up to the surrogate-push section,
+# which holds k_push and every device function it calls -- hashes to the
+# captured one, else null.
+PUSH_TRAFFIC = {"sources_sha256": "2c81c278feed83c52387648114abfa22a4057a8fa34abb4734a7831e62d05572", "bytes_per_slot": 21.054}
+PUSH_SOURCE = "paper_2609_17661_b300/csrc/kernels.cu"
+PUSH_SOURCE_END = "// the push with drag law SURROGATE"
 
 
 def _push_sources_sha256():
     import hashlib
-    h = hashlib.sha256()
-    for rel in PUSH_SOURCES:
-        with open(os.path.join(ROOT, rel), "rb") as f:
-            h.update(f.read())
-    return h.hexdigest()
+    with open(os.path.join(ROOT, PUSH_SOURCE)) as f:
+        text = f.read()
+    end = text.find(PUSH_SOURCE_END)
+    return hashlib.sha256(text[:end if end >= 0 else len(text)].encode()).hexdigest()
 
 
 def _peaks():
