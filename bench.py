@@ -35,6 +35,8 @@ from paper_2609_17661_b300 import workloads as W  # noqa: E402
 BYTES_PER_SLOT = 21      # push: read pos 4 + u 4 + w 4 + sp 1, write pos 4 + u 4
 BYTES_PER_DRAW = 8       # id read of a lepton that draws a Philox number
 BYTES_PER_CREATED = 21   # pos, u, w, sp, id written per created particle
+SORT_BYTES_PER_SLOT = 62 # a sort reads and writes 29 B per slot, plus a 4 B key pass
+NOMINAL_HBM_GBS = 7700.0 # B300 HBM3e, nominal
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_push
 # launch per slot it read, from one ncu capture of the same push source on a
@@ -261,7 +263,15 @@ def run_gpu(args):
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "kernel": "k_push", "launches": launches,
             "bytes_per_launch": push_bytes / max(launches, 1), "mean_launch_ms": d1["push_ms"] / max(launches, 1),
-            "peak_kind": peak_kind, "push_share_of_step": d1["push_ms"] / ms}
+            "peak_kind": peak_kind, "push_share_of_step": d1["push_ms"] / ms,
+            "frac_of_nominal": achieved / NOMINAL_HBM_GBS}
+    # the whole step against the roofline: push bytes plus the sort's share
+    # (read and write every slot with its id, and a key pass, once per
+    # sort_every steps), over the step time
+    sorts = sum(1 for k in range(d0["step"] + 1, d0["step"] + args.steps + 1) if k % cfg["sort_every"] == 0)
+    step_bytes = push_bytes + sorts * SORT_BYTES_PER_SLOT * (units / max(launches, 1))
+    roof["step"] = {"achieved": step_bytes / (ms * 1e-3) / 1e9, "frac": step_bytes / (ms * 1e-3) / 1e9 / peak,
+                    "bytes_per_particle_step": step_bytes / max(units, 1)}
 
     # end to end through the C ABI from pinned host buffers: upload the state,
     # K steps, read back the diagnostics and the field every step
