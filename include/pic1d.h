@@ -257,6 +257,21 @@ int pic1d_sort_static(int32_t n_cells, int64_t n, const uint32_t* pos, const flo
                       const uint8_t* sp, const uint64_t* id, uint32_t* pos_out, float* u_out, float* w_out,
                       uint8_t* sp_out, uint64_t* id_out, int64_t* n_out, void* cuda_stream);
 
+/* Checkpoint and resume.  pic1d_save writes the context's whole state to a
+ * file: the parameters (to be checked on load), the step, the particle slots
+ * (including removed ones not yet dropped by a sort), E (FP64), the last
+ * step's J, the pair-cap densities of this step and the next, the counters
+ * and per-step scalars (with the surface-supply accumulators), and the
+ * surrogate network with its Adam state if the context has one.
+ * pic1d_load restores such a file into a context created with the same
+ * parameters (the stream and the capacity may differ; the capacity must hold
+ * the saved slots): stepping on from there gives what the saved context
+ * would have given.  Push timing records are not saved.  Both synchronise.
+ * Errors: EINVAL (cannot open, not a checkpoint, other parameters, truncated),
+ * ENOMEM, ECUDA. */
+int pic1d_save(pic1d_ctx* c, const char* path);
+int pic1d_load(pic1d_ctx* c, const char* path);
+
 /* ------------------------------------------------------------------------
  * Learned surrogate of the photon-field quadrature (Sec. 2.2, Eq.
  * scatteringNdot and the momentum given per scattering).

@@ -184,6 +184,15 @@ class Line:
         return J
 
 
+    # ---------------------------------------------------------- checkpoints
+    def save(self, path):
+        """pic1d_save: the whole state of the line to a file."""
+        self._check(self.L.pic1d_save(self.h, str(path).encode()))
+
+    def load(self, path):
+        """pic1d_load: restore a file written by save (same parameters)."""
+        self._check(self.L.pic1d_load(self.h, str(path).encode()))
+
     # ------------------------------------------------------------ surrogate
     def sur_set_params(self, theta):
         """pic1d_sur_set_params from a host array of 8770 FP32 values."""

@@ -1042,6 +1042,153 @@ int pic1d_train_surrogate(pic1d_ctx* c, const pic1d_train_cfg* cfg, pic1d_train_
   return sur_check(c);
 }
 
+// ------------------------------------------------------------- checkpoints
+}  // extern "C"
+
+namespace {
+
+const char kCkptMagic[8] = {'P', 'I', 'C', '1', 'D', 'C', 'K', '1'};
+constexpr uint32_t kCkptVersion = 1;
+
+// The parameters as they must agree between a checkpoint and the context
+// that loads it, field by field (the struct's padding is not part of it; the
+// stream and the capacity may differ): doubles by their bit patterns,
+// integers by value.
+std::vector<uint64_t> ckpt_params(const pic1d_params& p) {
+  auto d = [](double x) { uint64_t u; std::memcpy(&u, &x, 8); return u; };
+  return {d(p.r_eq), (uint64_t)p.n_cells, d(p.cfl), d(p.b_star), (uint64_t)p.b_convention, d(p.kT_keV),
+          (uint64_t)p.photon_model, (uint64_t)p.drag_law, d(p.drag_scale), (uint64_t)p.table_n_gamma,
+          (uint64_t)p.table_n_s, d(p.table_log10g_max), (uint64_t)p.quad_n_mu, (uint64_t)p.quad_n_phi,
+          d(p.eta_min), (uint64_t)p.rics_mode, (uint64_t)p.mc_on, d(p.cells_per_skin_depth), d(p.j_psi),
+          d(p.n0_ppc), d(p.mass_ratio), (uint64_t)p.inject_mode, d(p.inject_T), (uint64_t)p.pairs_on,
+          d(p.b_pair_threshold), d(p.pair_energy_threshold), d(p.n_max_ppc), p.seed, d(p.r_star_cm),
+          (uint64_t)p.sort_every};
+}
+
+struct File {
+  FILE* f = nullptr;
+  explicit File(FILE* x) : f(x) {}
+  ~File() { if (f) std::fclose(f); }
+  bool put(const void* p, size_t n) { return n == 0 || std::fwrite(p, 1, n, f) == n; }
+  bool get(void* p, size_t n) { return n == 0 || std::fread(p, 1, n, f) == n; }
+};
+
+// device array -> file (through a host buffer)
+template <typename T>
+bool put_dev(pic1d_ctx* c, File& F, const T* d, long long n) {
+  std::vector<T> h((size_t)n);
+  if (n > 0 && cudaMemcpyAsync(h.data(), d, sizeof(T) * (size_t)n, cudaMemcpyDeviceToHost, c->s) != cudaSuccess)
+    return false;
+  if (cudaStreamSynchronize(c->s) != cudaSuccess) return false;
+  return F.put(h.data(), sizeof(T) * (size_t)n);
+}
+
+template <typename T>
+bool get_dev(pic1d_ctx* c, File& F, T* d, long long n) {
+  std::vector<T> h((size_t)n);
+  if (!F.get(h.data(), sizeof(T) * (size_t)n)) return false;
+  if (n > 0 && cudaMemcpyAsync(d, h.data(), sizeof(T) * (size_t)n, cudaMemcpyHostToDevice, c->s) != cudaSuccess)
+    return false;
+  return cudaStreamSynchronize(c->s) == cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pic1d_save(pic1d_ctx* c, const char* path) {
+  if (!c || !path) return fail(c, PIC1D_EINVAL, "save: NULL argument");
+  CK(cudaStreamSynchronize(c->s), "save");
+  StepState st{};
+  Counters ctr{};
+  CK(cudaMemcpy(&st, c->st, sizeof(st), cudaMemcpyDeviceToHost), "save");
+  CK(cudaMemcpy(&ctr, c->ctr, sizeof(ctr), cudaMemcpyDeviceToHost), "save");
+  File F(std::fopen(path, "wb"));
+  if (!F.f) return fail(c, PIC1D_EINVAL, std::string("save: cannot open ") + path);
+  const std::vector<uint64_t> q = ckpt_params(c->p);
+  const uint32_t ver = kCkptVersion, nq = (uint32_t)q.size();
+  const long long step = c->step, n = st.n_slots;
+  const int N = c->N, b = c->cur;
+  bool ok = F.put(kCkptMagic, 8) && F.put(&ver, 4) && F.put(&nq, 4) && F.put(q.data(), 8 * q.size()) &&
+            F.put(&step, 8) && F.put(&n, 8) && F.put(&N, 4);
+  ok = ok && put_dev(c, F, c->pos[b], n) && put_dev(c, F, c->u[b], n) && put_dev(c, F, c->w[b], n) &&
+       put_dev(c, F, c->sp[b], n) && put_dev(c, F, c->id[b], n);
+  ok = ok && put_dev(c, F, c->E64, N) && put_dev(c, F, c->J, N);
+  // the pair-cap density of this step, then of the next
+  ok = ok && put_dev(c, F, c->dens[step & 1], N) && put_dev(c, F, c->dens[(step + 1) & 1], N);
+  ok = ok && F.put(&ctr, sizeof(ctr)) && F.put(&st, sizeof(st));
+  const int32_t sur = c->sur_on ? 1 : 0;
+  ok = ok && F.put(&sur, 4);
+  if (ok && sur) {
+    const int32_t t = c->sur_t;
+    ok = F.put(&t, 4) && put_dev(c, F, c->sur.master, W_N_PARAMS) && put_dev(c, F, c->sur.m, W_N_PARAMS) &&
+         put_dev(c, F, c->sur.v, W_N_PARAMS);
+  }
+  if (!ok) return fail(c, PIC1D_ECUDA, std::string("save: write to ") + path + " failed");
+  return PIC1D_OK;
+}
+
+int pic1d_load(pic1d_ctx* c, const char* path) {
+  if (!c || !path) return fail(c, PIC1D_EINVAL, "load: NULL argument");
+  File F(std::fopen(path, "rb"));
+  if (!F.f) return fail(c, PIC1D_EINVAL, std::string("load: cannot open ") + path);
+  char magic[8];
+  uint32_t ver = 0, nq = 0;
+  const std::vector<uint64_t> mine = ckpt_params(c->p);
+  std::vector<uint64_t> q(mine.size());
+  if (!F.get(magic, 8) || std::memcmp(magic, kCkptMagic, 8) != 0 || !F.get(&ver, 4) || ver != kCkptVersion ||
+      !F.get(&nq, 4) || nq != mine.size() || !F.get(q.data(), 8 * q.size()))
+    return fail(c, PIC1D_EINVAL, std::string("load: ") + path + " is not a checkpoint of this library version");
+  if (q != mine) return fail(c, PIC1D_EINVAL, "load: the checkpoint was written with other parameters");
+  long long step = 0, n = 0;
+  int N = 0;
+  if (!F.get(&step, 8) || !F.get(&n, 8) || !F.get(&N, 4) || N != c->N || n < 0 || step < 0)
+    return fail(c, PIC1D_EINVAL, "load: bad checkpoint header");
+  if (c->p.capacity > 0 && n > c->p.capacity) return fail(c, PIC1D_EINVAL, "load: more slots than the capacity");
+  if (n > c->cap) {
+    const int rc = alloc_particles(c, c->p.capacity > 0 ? c->p.capacity : 2 * n + 4 * kTile);
+    if (rc != PIC1D_OK) return rc;
+  }
+  CK(cudaStreamSynchronize(c->s), "load");
+  c->cur = 0;
+  bool ok = get_dev(c, F, c->pos[0], n) && get_dev(c, F, c->u[0], n) && get_dev(c, F, c->w[0], n) &&
+            get_dev(c, F, c->sp[0], n) && get_dev(c, F, c->id[0], n);
+  ok = ok && cudaMemsetAsync(c->sp[0] + n, PIC1D_SP_DEAD, (size_t)(c->alloc - n), c->s) == cudaSuccess;
+  std::vector<double> E((size_t)N);
+  ok = ok && F.get(E.data(), sizeof(double) * (size_t)N);
+  std::vector<float> E32((size_t)N);
+  for (int i = 0; i < N; ++i) E32[i] = (float)E[i];
+  ok = ok && cudaMemcpy(c->E64, E.data(), sizeof(double) * N, cudaMemcpyHostToDevice) == cudaSuccess &&
+       cudaMemcpy(c->E32, E32.data(), sizeof(float) * N, cudaMemcpyHostToDevice) == cudaSuccess;
+  ok = ok && get_dev(c, F, c->J, N) && get_dev(c, F, c->dens[step & 1], N) &&
+       get_dev(c, F, c->dens[(step + 1) & 1], N);
+  Counters ctr{};
+  StepState st{};
+  ok = ok && F.get(&ctr, sizeof(ctr)) && F.get(&st, sizeof(st));
+  int32_t sur = 0;
+  ok = ok && F.get(&sur, 4);
+  if (!ok) return fail(c, PIC1D_EINVAL, std::string("load: ") + path + " is truncated or unreadable");
+  st.n_slots = n;
+  st.append = 0;
+  st.work = 0;
+  st.step = step;
+  CK(cudaMemcpy(c->ctr, &ctr, sizeof(ctr), cudaMemcpyHostToDevice), "load");
+  CK(cudaMemcpy(c->st, &st, sizeof(st), cudaMemcpyHostToDevice), "load");
+  c->step = step;
+  if (sur) {
+    int rc = sur_ensure(c);
+    if (rc != PIC1D_OK) return rc;
+    int32_t t = 0;
+    ok = F.get(&t, 4) && get_dev(c, F, c->sur.master, W_N_PARAMS) && get_dev(c, F, c->sur.m, W_N_PARAMS) &&
+         get_dev(c, F, c->sur.v, W_N_PARAMS);
+    if (!ok) return fail(c, PIC1D_EINVAL, std::string("load: ") + path + " is truncated (network)");
+    CK(sur_launch_update(c->sur, 0, 2, 0.0f, 1, nullptr, nullptr, c->s), "load");
+    CK(cudaStreamSynchronize(c->s), "load");
+    c->sur_t = t;
+  }
+  return PIC1D_OK;
+}
+
 // ------------------------------------------------------------- ensemble
 }  // extern "C"
 
