@@ -40,6 +40,7 @@
 #ifndef PIC1D_H
 #define PIC1D_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -257,6 +258,14 @@ int pic1d_sort_static(int32_t n_cells, int64_t n, const uint32_t* pos, const flo
                       const uint8_t* sp, const uint64_t* id, uint32_t* pos_out, float* u_out, float* w_out,
                       uint8_t* sp_out, uint64_t* id_out, int64_t* n_out, void* cuda_stream);
 
+/* Charge density at the N+1 nodes (the CIC shape of Sec. 3's grid): for a
+ * live particle at pos = i 2^F + f, node i gets q w_int (2^F - f) and node
+ * i+1 gets q w_int f, in the units of the current J (charge x 2^F, w_int =
+ * rint(w 2^12)).  The discrete Gauss law then reads rho^{n+1} - rho^n =
+ * -(J_i - J_{i-1}) at every interior node, exactly.  rho: N+1 int64, host
+ * (mem 0) or device (mem 1).  Synchronises.  Errors: EINVAL, ECUDA. */
+int pic1d_get_rho(pic1d_ctx* c, int64_t* rho, int mem);
+
 /* Checkpoint and resume.  pic1d_save writes the context's whole state to a
  * file: the parameters (to be checked on load), the step, the particle slots
  * (including removed ones not yet dropped by a sort), E (FP64), the last
@@ -419,6 +428,20 @@ void* pic1d_ens_stream(pic1d_ens* e);
 
 const char* pic1d_ens_last_error(const pic1d_ens* e);
 void pic1d_ens_free(pic1d_ens* e);
+
+/* Device memory.  Contexts and ensembles take all their device memory from
+ * one process-wide allocator: cudaMalloc / cudaFree by default, or the
+ * caller's pair of hooks (for instance a framework's caching allocator, so
+ * that the library's buffers and the framework's share one pool).  alloc
+ * returns a device pointer to `bytes` bytes aligned to at least 256 bytes,
+ * or NULL on failure (the call then fails with ENOMEM); free_fn releases
+ * it.  Both NULL restores cudaMalloc / cudaFree.  The hooks may be changed
+ * only while no context is alive, so that every buffer is freed by the
+ * allocator that made it.  Errors: EINVAL (one hook without the other,
+ * contexts alive). */
+typedef void* (*pic1d_alloc_fn)(size_t bytes, void* user);
+typedef void (*pic1d_free_fn)(void* ptr, void* user);
+int pic1d_set_allocator(pic1d_alloc_fn alloc, pic1d_free_fn free_fn, void* user);
 
 /* Message of the last error on this context (never NULL). */
 const char* pic1d_last_error(const pic1d_ctx* c);

@@ -59,6 +59,40 @@ def _arr(a, dtype):
     return C.c_void_p(a.ctypes.data), 0, a
 
 
+_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+_hooks = None
+
+
+def use_torch_allocator(on: bool = True):
+    """pic1d_set_allocator: take the library's device memory from PyTorch's
+    caching allocator (on the current stream), or back from cudaMalloc.
+    Only while no Line or Ensemble is alive."""
+    global _hooks
+    import torch
+    L = _lib.load()
+    if on:
+        def alloc(n, user):
+            try:
+                return torch.cuda.caching_allocator_alloc(int(n))
+            except Exception:
+                return None
+
+        def free(p, user):
+            torch.cuda.caching_allocator_delete(p)
+
+        hooks = (_ALLOC_FN(alloc), _FREE_FN(free))
+        rc = L.pic1d_set_allocator(C.cast(hooks[0], C.c_void_p), C.cast(hooks[1], C.c_void_p), None)
+        if rc == 0:
+            _hooks = hooks            # the callbacks must outlive every buffer they made
+    else:
+        rc = L.pic1d_set_allocator(None, None, None)
+        if rc == 0:
+            _hooks = None
+    if rc != 0:
+        raise PicError(rc, "pic1d_set_allocator refused (contexts alive?)")
+
+
 class Line:
     """One field line on the GPU (a ``pic1d_ctx``)."""
 
@@ -157,6 +191,12 @@ class Line:
         J = np.zeros(self.N, np.int64)
         self._check(self.L.pic1d_get_fields(self.h, E.ctypes.data, J.ctypes.data, 0))
         return E, J
+
+    def rho(self):
+        """pic1d_get_rho: integer node charge (N+1 values, units of J)."""
+        r = np.zeros(self.N + 1, np.int64)
+        self._check(self.L.pic1d_get_rho(self.h, C.c_void_p(r.ctypes.data), 0))
+        return r
 
     def particles(self, alive_only=True) -> dict:
         n = self.slots()

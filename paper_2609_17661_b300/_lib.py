@@ -87,6 +87,8 @@ SIGNATURES = {
     "pic1d_set_variant": (C.c_int, [C.c_void_p, C.c_int]),
     "pic1d_variant_info": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "pic1d_sort_static": (C.c_int, [C.c_int32, C.c_int64] + [C.c_void_p] * 11 + [C.c_void_p]),
+    "pic1d_set_allocator": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "pic1d_get_rho": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "pic1d_save": (C.c_int, [C.c_void_p, C.c_char_p]),
     "pic1d_load": (C.c_int, [C.c_void_p, C.c_char_p]),
     "pic1d_sur_set_params": (C.c_int, [C.c_void_p, C.c_void_p]),

@@ -1645,6 +1645,24 @@ __global__ void k_deposit(DevParams P, long long n, const long long* p0, const l
   }
 }
 
+// integer charge at the N+1 nodes with the CIC shape: a live particle at
+// pos = i 2^F + f gives q w_int (2^F - f) to node i and q w_int f to node
+// i + 1 (the units of J: charge x 2^F)
+__global__ void k_rho(DevParams P, long long* rho) {
+  const long long n = P.st->n_slots;
+  const long long one = 1ll << P.F;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    const uint8_t s = P.sp[k];
+    if (s == PIC1D_SP_DEAD) continue;
+    const uint32_t x = P.pos[k];
+    const int i = min((int)(x >> P.F), P.N - 1);
+    const long long f = (long long)x - ((long long)i << P.F);
+    const long long q = (long long)P.qs[s & 3] * __float2ll_rn(P.w[k] * 4096.0f);
+    atomicAdd(reinterpret_cast<unsigned long long*>(rho + i), (unsigned long long)(q * (one - f)));
+    atomicAdd(reinterpret_cast<unsigned long long*>(rho + i + 1), (unsigned long long)(q * f));
+  }
+}
+
 __global__ void k_count_species(DevParams P, unsigned long long* out4) {
   const long long n = P.st->n_slots;
   unsigned c[4] = {0, 0, 0, 0};
@@ -1790,6 +1808,11 @@ cudaError_t launch_deposit(const DevParams& P, long long n, const long long* p0,
                            const uint8_t* sp, long long* J, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   k_deposit<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P, n, p0, p1, w, sp, J);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rho(const DevParams& P, long long* rho, int grid, cudaStream_t s) {
+  k_rho<<<grid, 256, 0, s>>>(P, rho);
   return cudaGetLastError();
 }
 

@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <atomic>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -174,6 +175,7 @@ struct pic1d_ctx {
   double* sur_gw = nullptr;
   float* sur_grad = nullptr;
   float* sur_loss = nullptr;     // loss sum of a gradient call
+  long long* rho = nullptr;      // node charge of pic1d_get_rho (allocated on first use)
 };
 
 namespace {
@@ -194,14 +196,35 @@ int cuda_fail(pic1d_ctx* c, cudaError_t e, const char* where) {
     if (e_ != cudaSuccess) return cuda_fail(c, e_, where); \
   } while (0)
 
+// Device memory of contexts and ensembles comes from one process-wide
+// allocator: cudaMalloc/cudaFree, or the caller's hooks (pic1d_set_allocator).
+// The hooks may change only while no context or ensemble is alive, so every
+// buffer is freed by the allocator that made it.
+pic1d_alloc_fn g_alloc = nullptr;
+pic1d_free_fn g_free = nullptr;
+void* g_alloc_user = nullptr;
+std::atomic<long long> g_live{0};
+
+cudaError_t raw_alloc(void** p, size_t bytes) {
+  if (!g_alloc) return cudaMalloc(p, bytes);
+  *p = g_alloc(bytes, g_alloc_user);
+  return *p ? cudaSuccess : cudaErrorMemoryAllocation;
+}
+
+void dfree(void* p) {
+  if (!p) return;
+  if (g_free) g_free(p, g_alloc_user);
+  else cudaFree(p);
+}
+
 template <typename T>
 cudaError_t dalloc(T** p, size_t n) {
-  return cudaMalloc(reinterpret_cast<void**>(p), std::max<size_t>(n, 1) * sizeof(T));
+  return raw_alloc(reinterpret_cast<void**>(p), std::max<size_t>(n, 1) * sizeof(T));
 }
 
 void free_particles(pic1d_ctx* c) {
   for (int b = 0; b < 2; ++b) {
-    cudaFree(c->pos[b]); cudaFree(c->u[b]); cudaFree(c->w[b]); cudaFree(c->sp[b]); cudaFree(c->id[b]);
+    dfree(c->pos[b]); dfree(c->u[b]); dfree(c->w[b]); dfree(c->sp[b]); dfree(c->id[b]);
     c->pos[b] = nullptr; c->u[b] = nullptr; c->w[b] = nullptr; c->sp[b] = nullptr; c->id[b] = nullptr;
   }
 }
@@ -393,7 +416,7 @@ int build_tables(pic1d_ctx* c) {
     CK(dalloc(&c->tpair, (size_t)2 * (Ns - 1) * Ng), "alloc table");
     CK(launch_pair_table(c->table, Ng, Ns, c->tpair, c->s), "pair table");
     CK(cudaStreamSynchronize(c->s), "table sync");
-    cudaFree(dxs); cudaFree(dbs); cudaFree(dms); cudaFree(dgx); cudaFree(dgw);
+    dfree(dxs); dfree(dbs); dfree(dms); dfree(dgx); dfree(dgw);
   }
   return PIC1D_OK;
 }
@@ -451,7 +474,7 @@ int timing_begin(pic1d_ctx* c) {
     if (c->slot_log) {
       CK(cudaMemcpyAsync(nl, c->slot_log, c->slot_log_cap * sizeof(long long), cudaMemcpyDeviceToDevice, c->s), "timing");
       CK(cudaStreamSynchronize(c->s), "timing");
-      cudaFree(c->slot_log);
+      dfree(c->slot_log);
     }
     c->slot_log = nl;
     c->slot_log_cap = ncap;
@@ -493,6 +516,7 @@ int pic1d_init(const pic1d_params* p, pic1d_ctx** out) {
     return PIC1D_EINVAL;
   }
   pic1d_ctx* c = new pic1d_ctx();
+  g_live.fetch_add(1);
   c->p = *p;
   c->s = reinterpret_cast<cudaStream_t>(p->cuda_stream);
   c->N = p->n_cells;
@@ -969,7 +993,7 @@ int pic1d_train_surrogate(pic1d_ctx* c, const pic1d_train_cfg* cfg, pic1d_train_
   CK(cudaEventCreate(&e2), "train");
   CK(cudaEventCreate(&e3), "train");
   auto cleanup = [&]() {
-    cudaFree(rec); cudaFree(vrec); cudaFree(vy); cudaFree(verr); cudaFree(losses);
+    dfree(rec); dfree(vrec); dfree(vy); dfree(verr); dfree(losses);
     cudaEventDestroy(e0); cudaEventDestroy(e1); cudaEventDestroy(e2); cudaEventDestroy(e3);
   };
   cudaError_t e = dalloc(&rec, (size_t)n * kSurRecord);
@@ -1278,12 +1302,12 @@ int ens_build_items(pic1d_ens* e) {
   std::vector<int2> cells;
   for (int l = 0; l < e->n; ++l)
     for (int c0 = 0; c0 < e->lines[l]->N; c0 += 256) cells.push_back(make_int2(l, c0));
-  cudaFree(e->push_items);
-  cudaFree(e->cell_items);
+  dfree(e->push_items);
+  dfree(e->cell_items);
   e->push_items = nullptr;
   e->cell_items = nullptr;
-  ECK(cudaMalloc(&e->push_items, sizeof(int4) * std::max<size_t>(1, items.size())), "ensemble items");
-  ECK(cudaMalloc(&e->cell_items, sizeof(int2) * std::max<size_t>(1, cells.size())), "ensemble items");
+  ECK(raw_alloc(reinterpret_cast<void**>(&e->push_items), sizeof(int4) * std::max<size_t>(1, items.size())), "ensemble items");
+  ECK(raw_alloc(reinterpret_cast<void**>(&e->cell_items), sizeof(int2) * std::max<size_t>(1, cells.size())), "ensemble items");
   ECK(cudaMemcpyAsync(e->push_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, e->s),
       "ensemble items");
   ECK(cudaMemcpyAsync(e->cell_items, cells.data(), sizeof(int2) * cells.size(), cudaMemcpyHostToDevice, e->s),
@@ -1419,8 +1443,8 @@ int pic1d_ens_init(const pic1d_params* params, int32_t n_lines, pic1d_ens** out)
   e->sort_count.assign(n_lines, 0);
   int rc = sur_ensure(e->lines[0]);
   cudaError_t ce = cudaSuccess;
-  if (rc == PIC1D_OK) ce = cudaMalloc(&e->dlines, sizeof(EnsLine) * n_lines);
-  if (rc == PIC1D_OK && ce == cudaSuccess) ce = cudaMalloc(&e->work, sizeof(unsigned long long));
+  if (rc == PIC1D_OK) ce = raw_alloc(reinterpret_cast<void**>(&e->dlines), sizeof(EnsLine) * n_lines);
+  if (rc == PIC1D_OK && ce == cudaSuccess) ce = raw_alloc(reinterpret_cast<void**>(&e->work), sizeof(unsigned long long));
   if (rc == PIC1D_OK && ce == cudaSuccess) ce = cudaMemsetAsync(e->work, 0, sizeof(unsigned long long), e->s);
   if (rc == PIC1D_OK && ce != cudaSuccess) rc = PIC1D_ECUDA;
   if (rc == PIC1D_OK) rc = ens_build_items(e);
@@ -1578,13 +1602,40 @@ void pic1d_ens_free(pic1d_ens* e) {
   if (!e) return;
   if (e->s) cudaStreamSynchronize(e->s);
   if (e->graph) cudaGraphExecDestroy(e->graph);
-  cudaFree(e->dlines);
-  cudaFree(e->push_items);
-  cudaFree(e->cell_items);
-  cudaFree(e->work);
+  dfree(e->dlines);
+  dfree(e->push_items);
+  dfree(e->cell_items);
+  dfree(e->work);
   for (pic1d_ctx* c : e->lines) pic1d_free(c);
   if (e->s) cudaStreamDestroy(e->s);
   delete e;
+}
+
+int pic1d_get_rho(pic1d_ctx* c, int64_t* rho, int mem) {
+  if (!c) return PIC1D_EINVAL;
+  if (!rho || (mem != 0 && mem != 1)) return fail(c, PIC1D_EINVAL, "get_rho: bad arguments");
+  if (!c->rho) CK(dalloc(&c->rho, c->N + 1), "get_rho");
+  CK(cudaMemsetAsync(c->rho, 0, sizeof(long long) * (c->N + 1), c->s), "get_rho");
+  CK(launch_rho(dev_params(c), c->rho, c->sms * 8, c->s), "get_rho");
+  CK(cudaMemcpyAsync(rho, c->rho, sizeof(long long) * (c->N + 1),
+                     mem ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->s), "get_rho");
+  CK(cudaStreamSynchronize(c->s), "get_rho");
+  return PIC1D_OK;
+}
+
+int pic1d_set_allocator(pic1d_alloc_fn alloc, pic1d_free_fn free_fn, void* user) {
+  if ((alloc == nullptr) != (free_fn == nullptr)) {
+    std::fprintf(stderr, "pic1d_set_allocator: give both hooks or neither\n");
+    return PIC1D_EINVAL;
+  }
+  if (g_live.load() != 0) {
+    std::fprintf(stderr, "pic1d_set_allocator: %lld contexts are alive; free them first\n", g_live.load());
+    return PIC1D_EINVAL;
+  }
+  g_alloc = alloc;
+  g_free = free_fn;
+  g_alloc_user = user;
+  return PIC1D_OK;
 }
 
 const char* pic1d_last_error(const pic1d_ctx* c) {
@@ -1601,9 +1652,10 @@ void pic1d_free(pic1d_ctx* c) {
   void* ptrs[] = {c->E64, c->E32, c->J, c->dens[0], c->dens[1], c->nb, c->nmu, c->nx, c->zone, c->dens_flag, c->fast_cell, c->table,
                   c->ctr, c->st, c->ke_partial, c->field_partial, c->counts, c->offsets, c->spc, c->slot_log,
                   c->tpair, c->bsum, c->sur.master, c->sur.m, c->sur.v, c->sur.img, c->sur.small,
-                  c->sur.part, c->sur.loss_part, c->sur.err, c->sur_gx, c->sur_gw, c->sur_grad, c->sur_loss};
-  for (void* q : ptrs) cudaFree(q);
+                  c->sur.part, c->sur.loss_part, c->sur.err, c->sur_gx, c->sur_gw, c->sur_grad, c->sur_loss, c->rho};
+  for (void* q : ptrs) dfree(q);
   delete c;
+  g_live.fetch_sub(1);
 }
 
 }  // extern "C"

@@ -112,6 +112,7 @@ cudaError_t launch_table(int Ng, int Ns, int n_mu, int n_phi, double log10g_max,
 cudaError_t launch_deposit(const DevParams& P, long long n, const long long* p0, const long long* p1,
                            const float* w, const uint8_t* sp, long long* J, cudaStream_t s);
 cudaError_t launch_count_species(const DevParams& P, unsigned long long* out4, cudaStream_t s);
+cudaError_t launch_rho(const DevParams& P, long long* rho, int grid, cudaStream_t s);
 int push_blocks_per_sm(int variant, bool nmax);
 }  // namespace pic1d
 

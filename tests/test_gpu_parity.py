@@ -323,6 +323,27 @@ def test_gauss_law_integer_exact_every_step():
     assert d["pairs_created"] > 0 and d["lost_north"] + d["lost_south"] > 0
 
 
+def test_device_rho_and_gauss_law_on_the_device():
+    """pic1d_get_rho equals the node charge summed on the host from the
+    particles, and the device rho and J obey the discrete Gauss law exactly
+    step by step."""
+    N = 512
+    F = W.fbits(N)
+    cfg = W.config("C1", n_cells=N, drag_scale=3e-4, sort_every=3)
+    st = W.load_drifting_plasma(cfg)
+    line = _line(cfg)
+    line.set_state(st, E=_field0(N))
+    r0 = line.rho()
+    p = line.particles()
+    np.testing.assert_array_equal(r0, _rho_int(p["pos"], p["w"], p["sp"], N, F))
+    for k in range(6):
+        line.step(1)
+        r1 = line.rho()
+        _, J = line.fields()
+        np.testing.assert_array_equal((r1 - r0)[1:N], -(J[1:N] - J[0:N - 1]))
+        r0 = r1
+
+
 def test_current_invariant_under_permutation_and_sort_cadence():
     """J_int is an exact integer sum: identical under any storage order of
     the particles and any sort cadence."""

@@ -246,12 +246,12 @@ def test_gain_over_quadrature_and_tables():
     Y = line.sur_infer(X).cpu().numpy().astype(np.float64)
     gam = np.sqrt(1 + D["u"] ** 2)
     Fn, lnNn = S.reconstruct(Y, D["lnN_base"], gam, D["b"])
-    err_net = S.drag_error(Fn, D["F"], D["F_abs"])[keep]
+    err_net = S.drag_error(Fn[keep], D["F"][keep], D["F_abs"][keep])
     T = O.Sim(dict(cfg, r_eq=20.0, n_cells=4096, drag_law=O.DRAG_TABLE))
     k = cfg["drag_scale"] / T.scalars()["R_cells"]
     s_cells = (D["f1"] + 1) / 2 * 4096
     Ft = np.array([T.drag(u, s)[0] / k for u, s in zip(D["u"], s_cells)])
-    err_tab = S.drag_error(Ft, D["F"], D["F_abs"])[keep]
+    err_tab = S.drag_error(Ft[keep], D["F"][keep], D["F_abs"][keep])
     print("gain: quadrature %.1f ms, network %.2f ms per 1e6 points (x%.0f); network 35 KB for all lines vs "
           "1 MiB table per line; drag error median/p99 network %.2e/%.2e, table %.2e/%.2e; training %s"
           % (t_quad, t_net, t_quad / t_net, np.median(err_net), np.percentile(err_net, 99),
