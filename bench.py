@@ -456,6 +456,34 @@ def run_ensemble(args):
     ens.close()
 
 
+def run_tp_map(args):
+    """The test-particle drag map: 4096 dipole lines, r_eq log-spaced in
+    [2, 100], gamma0 = 1000, B*/B_QED = 10, 1 keV radially streaming photons,
+    dt = 1e-3 R*/c to the equator or t = 200 R*/c; one FP64 thread per line.
+    Reports line-steps/s and the critical radius found."""
+    import torch
+    from paper_2609_17661_b300 import tp_map
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    cfg = W.config("C1", kT_keV=1.0, photon_model=0, drag_scale=1.0)
+    r = np.geomspace(2.0, 100.0, 4096)
+    tp_map(cfg, r[:64], dt=1e-3, t_max=20.0)            # warm-up
+    res, ms = tp_map(cfg, r, dt=1e-3, t_max=200.0)
+    steps = float(res["steps"].sum())
+    third = r[res["region"] == 3]
+    out = {"metric": "line-steps/s", "value": steps / (ms * 1e-3), "unit": "line-steps/s", "n_gpus": 1,
+           "steps": 1, "warmup": 1, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "test-particle drag map, 4096 dipole lines r_eq in [2, 100], gamma0 1000, "
+                                  "b*=10, 1 keV radial photons, dt 1e-3", "lines": int(r.size)},
+           "lines_per_s": r.size / (ms * 1e-3),
+           "r_crit": float(third.min()) if third.size else None,
+           "regions": {str(k): int((res["region"] == k).sum()) for k in (1, 2, 3)},
+           "gpu_launches": 1}
+    print(json.dumps(out), flush=True)
+
+
 def gpu_launches(steps, cfg, step0):
     """Kernels of this library launched in the timed region: per step push,
     field, finalize (+ inject with surface supply); per sort hist, scan
@@ -471,7 +499,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
-    ap.add_argument("--workload", default="C5", choices=["C5", "C2", "C1", "C4"])
+    ap.add_argument("--workload", default="C5", choices=["C5", "C2", "C1", "C4", "TP"])
     ap.add_argument("--particles", type=float, default=1e9)
     ap.add_argument("--cells", type=int, default=0,
                     help="override the line's cell count (smaller lines at the same density for ncu captures)")
@@ -488,6 +516,8 @@ def main():
         run_reference(args)
     elif args.workload == "C4":
         run_ensemble(args)
+    elif args.workload == "TP":
+        run_tp_map(args)
     else:
         run_gpu(args)
 

@@ -258,6 +258,35 @@ int pic1d_sort_static(int32_t n_cells, int64_t n, const uint32_t* pos, const flo
                       const uint8_t* sp, const uint64_t* id, uint32_t* pos_out, float* u_out, float* w_out,
                       uint8_t* sp_out, uint64_t* id_out, int64_t* n_out, void* cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Test-particle drag maps (the paper's appendix on the extent of the
+ * pair-producing region, Figs. 6 and 7).  For each of n field lines of
+ * equatorial radius r_eq[i], a lepton enters at the northern footpoint with
+ * gamma0 and moves under the drag alone, from radially streaming photons
+ * (Eq. contdrag) with the physics of `p` (b_star, b_convention, kT_keV,
+ * r_star_cm, drag_scale; the other fields are not used).  One GPU thread
+ * follows one line in FP64 with steps of dt (R_star/c): the drag update
+ * u1 - u0 - dt/2 (F(u0) + F(u1)) = 0 by Newton at fixed theta, the expected
+ * scatterings tau += dt/2 (N(u0) + N(u1)), and theta += dt/2 (beta0 + beta1) /
+ * (ds/dtheta).  It stops at the equator or at t_max.  Per line: gamma_min;
+ * the first scattering (tau = 1) as theta_first and s_first (-1: none); the
+ * point where b falls below b_thr (theta_b, s_b; the equator if it does not);
+ * the line length L; l_pp = s_b - s_first, or L - 2 s_first when b stays
+ * above b_thr to the equator (the zone spans both hemispheres); b at the
+ * equator; region 1 (b > b_thr everywhere, gamma_min > 1 + gamma_eps), 2 (b
+ * falls below b_thr, gamma_min > 1 + gamma_eps) or 3 (gamma_min <= 1 +
+ * gamma_eps).  out: host, n results; ms_out (may be NULL): the kernel's
+ * device time.  Errors: EINVAL, ENOMEM, ECUDA.
+ * ------------------------------------------------------------------------ */
+typedef struct pic1d_tp_result {
+  double gamma_min, theta_first, theta_b, s_first, s_b, L, l_pp, b_eq, t_end, u_end;
+  int64_t steps;
+  int32_t region, pad;
+} pic1d_tp_result;
+
+int pic1d_tp_map(const pic1d_params* p, const double* r_eq, int32_t n, double gamma0, double dt, double t_max,
+                 double b_thr, double gamma_eps, pic1d_tp_result* out, double* ms_out);
+
 /* Charge density at the N+1 nodes (the CIC shape of Sec. 3's grid): for a
  * live particle at pos = i 2^F + f, node i gets q w_int (2^F - f) and node
  * i+1 gets q w_int f, in the units of the current J (charge x 2^F, w_int =

@@ -126,6 +126,8 @@ def lib():
             "orc_node_interp_public": (C.c_double, [C.c_void_p, C.c_int, C.c_double]),
             "orc_sur_edge_mu": (C.c_double, [C.c_double, C.c_double, C.c_double]),
             "orc_set_surrogate": (None, [C.c_void_p, _D]),
+            "orc_tp_line": (None, [C.POINTER(OrcParams), C.c_double, C.c_double, C.c_double, C.c_double,
+                                   C.c_double, C.c_double, _D]),
             "orc_sur_forward": (None, [_D, _D, _D, _D]),
             "orc_sur_baseline": (C.c_double, [C.POINTER(OrcParams), C.c_double, C.c_double, C.c_double, C.c_double]),
             "orc_sur_point": (None, [C.POINTER(OrcParams), C.c_double, C.c_double, C.c_double, C.c_int, _D]),
@@ -389,3 +391,15 @@ def sur_forward(theta, x):
     y, dy = np.zeros(2), np.zeros(2)
     lib().orc_sur_forward(_ptr(th, _D), _ptr(xx, _D), _ptr(y, _D), _ptr(dy, _D))
     return y, dy
+
+
+TP_FIELDS = ("gamma_min", "theta_first", "theta_b", "s_first", "s_b", "L", "l_pp", "region", "b_eq", "steps",
+             "t_end", "u_end")
+
+
+def tp_line(cfg, r_eq, gamma0=1000.0, dt=1e-3, t_max=1e3, b_thr=0.1, gamma_eps=0.01):
+    """One line of the test-particle drag map (dict of TP_FIELDS)."""
+    p = make_params(cfg)
+    out = np.zeros(12)
+    lib().orc_tp_line(C.byref(p), r_eq, gamma0, dt, t_max, b_thr, gamma_eps, _ptr(out, _D))
+    return dict(zip(TP_FIELDS, out))

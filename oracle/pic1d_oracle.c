@@ -470,6 +470,109 @@ void orc_sur_samples(const orc_params* p, uint64_t seed, uint64_t start, int64_t
 }
 
 /* ------------------------------------------------------------------------ */
+/* Test-particle drag maps (App. on the extent of the pair-producing region): */
+/* a lepton enters a field line at the northern footpoint with gamma0 and    */
+/* moves under the drag alone (radially streaming photons, Eq. contdrag).    */
+/* The line is followed in theta (ds = r_eq sin(theta) sqrt(1+3cos^2) dtheta, */
+/* time in R_star/c).  One step of dt:                                       */
+/*   u1 from u1 - u0 - dt/2 (F(u0) + F(u1)) = 0 at fixed theta (Newton on the */
+/*      exact derivative of the closed form),                                 */
+/*   tau += dt/2 (N(u0) + N(u1))    (expected scatterings, N^ = Ndot R_star / c), */
+/*   theta += dt/2 (beta0 + beta1) / (ds/dtheta at theta0).                  */
+/* It stops at the equator (theta = pi/2; the line is symmetric) or at      */
+/* t_max.  Reported: gamma_min over the path; the first scattering where tau */
+/* reaches 1 (linear in the step); the point where b falls below b_thr.      */
+/* out[12]: gamma_min, theta_first (-1: none), theta_b, s_first, s_b, L,     */
+/*          l_pp, region (1, 2, 3), b_eq, steps, t_end, u_end                */
+/* ------------------------------------------------------------------------ */
+static void orc_tp_drag(const orc_params* p, double u, double x, double b, double mu, double* F, double* dF,
+                        double* N)
+{
+  double Fh, Nh;
+  orc_radial(p, u, x, b, mu, &Fh, &Nh);
+  double th = orc_theta_T(p);
+  double gam = sqrt(1.0 + u * u), beta = u / gam;
+  double D = gam * orc_one_minus_beta_m(u, gam, mu);
+  double y = b / (th * D);
+  double g = orc_g(y);
+  double K = ORC_R_E * p->r_star_cm / (ORC_LAMBDABAR * ORC_LAMBDABAR) * th * th * th / (4.0 * x * x);
+  double gp = g * (3.0 / y - 1.0 / (-expm1(-y)));
+  double dydu = -y * (beta - mu) / D;
+  *F = p->drag_scale * Fh;
+  *dF = p->drag_scale * K * ((beta * mu - 1.0) * g + gam * (mu - beta) * gp * dydu);
+  *N = p->drag_scale * Nh;
+}
+
+void orc_tp_line(const orc_params* p0, double r_eq, double gamma0, double dt, double t_max, double b_thr,
+                 double gamma_eps, double* out)
+{
+  orc_params q = *p0;
+  q.r_eq = r_eq;
+  const orc_params* p = &q;
+  double th = orc_theta0(r_eq);
+  double u = sqrt(gamma0 * gamma0 - 1.0);
+  double gmin = gamma0, tau = 0.0, t = 0.0, th_first = -1.0;
+  long steps = 0;
+  while (th < 0.5 * ORC_PI && t < t_max) {
+    double x, b, mu;
+    orc_field_at_theta(p, th, &x, &b, &mu);
+    double F0, dF0, N0;
+    orc_tp_drag(p, u, x, b, mu, &F0, &dF0, &N0);
+    double u1 = u + dt * F0;
+    for (int it = 0; it < 50; ++it) {
+      double F1, dF1, N1;
+      orc_tp_drag(p, u1, x, b, mu, &F1, &dF1, &N1);
+      double G = u1 - u - 0.5 * dt * (F0 + F1);
+      double dG = 1.0 - 0.5 * dt * dF1;
+      if (dG < 0.5) dG = 0.5;
+      double un = u1 - G / dG;
+      int done = fabs(un - u1) <= 1e-14 * (1.0 + fabs(un));
+      u1 = un;
+      if (done) break;
+    }
+    double F1, dF1, N1;
+    orc_tp_drag(p, u1, x, b, mu, &F1, &dF1, &N1);
+    double tau1 = tau + 0.5 * dt * (N0 + N1);
+    double beta0 = u / sqrt(1.0 + u * u), beta1 = u1 / sqrt(1.0 + u1 * u1);
+    double c = cos(th);
+    double h = r_eq * sin(th) * sqrt(1.0 + 3.0 * c * c);
+    double th1 = th + 0.5 * dt * (beta0 + beta1) / h;
+    if (th_first < 0.0 && tau < 1.0 && tau1 >= 1.0) th_first = th + (1.0 - tau) / (tau1 - tau) * (th1 - th);
+    u = u1;
+    tau = tau1;
+    th = th1;
+    t += dt;
+    ++steps;
+    double g1 = sqrt(1.0 + u * u);
+    if (g1 < gmin) gmin = g1;
+  }
+  /* where b falls below b_thr (b decreases from the footpoint to the equator) */
+  double xe, be, me;
+  orc_field_at_theta(p, 0.5 * ORC_PI, &xe, &be, &me);
+  double th_b = 0.5 * ORC_PI;
+  if (be < b_thr) {
+    double lo = orc_theta0(r_eq), hi = 0.5 * ORC_PI;
+    for (int it = 0; it < 200; ++it) {
+      double mid = 0.5 * (lo + hi), xm, bm, mm;
+      orc_field_at_theta(p, mid, &xm, &bm, &mm);
+      if (bm >= b_thr) lo = mid; else hi = mid;
+    }
+    th_b = 0.5 * (lo + hi);
+  }
+  double L = orc_line_length(r_eq);
+  double s_first = (th_first >= 0.0) ? orc_arc_length(r_eq, th_first) : -1.0;
+  double s_b = orc_arc_length(r_eq, th_b);
+  double lpp = 0.0;
+  if (s_first >= 0.0) {
+    if (be >= b_thr) lpp = L - 2.0 * s_first;           /* across the equator, symmetric */
+    else lpp = (s_b > s_first) ? s_b - s_first : 0.0;
+  }
+  int region = (gmin <= 1.0 + gamma_eps) ? 3 : ((be >= b_thr) ? 1 : 2);
+  out[0] = gmin; out[1] = th_first; out[2] = th_b; out[3] = s_first; out[4] = s_b; out[5] = L;
+  out[6] = lpp; out[7] = region; out[8] = be; out[9] = (double)steps; out[10] = t; out[11] = u;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Simulation state                                                          */
 /* ------------------------------------------------------------------------ */
 typedef struct {

@@ -93,6 +93,23 @@ def use_torch_allocator(on: bool = True):
         raise PicError(rc, "pic1d_set_allocator refused (contexts alive?)")
 
 
+def tp_map(cfg: dict, r_eq, gamma0=1000.0, dt=1e-3, t_max=1e3, b_thr=0.1, gamma_eps=0.01):
+    """pic1d_tp_map: test-particle drag map over the lines r_eq (array).
+    Returns (dict of arrays per TpResult field, kernel ms)."""
+    import torch
+    L = _lib.load()
+    r = np.ascontiguousarray(r_eq, dtype=np.float64)
+    out = (_lib.TpResult * r.size)()
+    ms = C.c_double()
+    p = make_params(cfg, torch.cuda.current_stream().cuda_stream)
+    rc = L.pic1d_tp_map(C.byref(p), C.c_void_p(r.ctypes.data), r.size, gamma0, dt, t_max, b_thr, gamma_eps,
+                        C.cast(out, C.c_void_p), C.byref(ms))
+    if rc != 0:
+        raise PicError(rc, "pic1d_tp_map failed (see stderr)")
+    res = {name: np.array([getattr(o, name) for o in out]) for name, _ in _lib.TpResult._fields_ if name != "pad"}
+    return res, ms.value
+
+
 class Line:
     """One field line on the GPU (a ``pic1d_ctx``)."""
 

@@ -66,6 +66,12 @@ class TrainReport(C.Structure):
                 ("lnN_err_max", C.c_double), ("lnN_err_p99", C.c_double), ("lnN_err_median", C.c_double)]
 
 
+class TpResult(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("gamma_min", "theta_first", "theta_b", "s_first", "s_b", "L", "l_pp",
+                                          "b_eq", "t_end", "u_end")] + \
+               [("steps", C.c_int64), ("region", C.c_int32), ("pad", C.c_int32)]
+
+
 SUR_N_PARAMS = 8770
 SUR_RECORD = 16
 
@@ -89,6 +95,8 @@ SIGNATURES = {
     "pic1d_sort_static": (C.c_int, [C.c_int32, C.c_int64] + [C.c_void_p] * 11 + [C.c_void_p]),
     "pic1d_set_allocator": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "pic1d_get_rho": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "pic1d_tp_map": (C.c_int, [C.POINTER(Params), C.c_void_p, C.c_int32, C.c_double, C.c_double, C.c_double,
+                               C.c_double, C.c_double, C.c_void_p, C.POINTER(C.c_double)]),
     "pic1d_save": (C.c_int, [C.c_void_p, C.c_char_p]),
     "pic1d_load": (C.c_int, [C.c_void_p, C.c_char_p]),
     "pic1d_sur_set_params": (C.c_int, [C.c_void_p, C.c_void_p]),

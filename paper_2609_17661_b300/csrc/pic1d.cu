@@ -1611,6 +1611,46 @@ void pic1d_ens_free(pic1d_ens* e) {
   delete e;
 }
 
+int pic1d_tp_map(const pic1d_params* p, const double* r_eq, int32_t n, double gamma0, double dt, double t_max,
+                 double b_thr, double gamma_eps, pic1d_tp_result* out, double* ms_out) {
+  if (!p || !r_eq || !out || n < 1 || !(gamma0 >= 1.0) || !(dt > 0.0) || !(t_max > 0.0) || !(b_thr > 0.0)) {
+    std::fprintf(stderr, "pic1d_tp_map: bad arguments\n");
+    return PIC1D_EINVAL;
+  }
+  for (int i = 0; i < n; ++i)
+    if (!(r_eq[i] > 1.0)) {
+      std::fprintf(stderr, "pic1d_tp_map: r_eq[%d] = %g must exceed 1\n", i, r_eq[i]);
+      return PIC1D_EINVAL;
+    }
+  double* dr = nullptr;
+  pic1d_tp_result* dout = nullptr;
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t e = raw_alloc(reinterpret_cast<void**>(&dr), sizeof(double) * n);
+  if (e == cudaSuccess) e = raw_alloc(reinterpret_cast<void**>(&dout), sizeof(pic1d_tp_result) * n);
+  if (e == cudaSuccess) e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(p->cuda_stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dr, r_eq, sizeof(double) * n, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaEventRecord(a, s);
+  if (e == cudaSuccess) e = tp_launch_map(*p, dr, n, gamma0, dt, t_max, b_thr, gamma_eps, dout, s);
+  if (e == cudaSuccess) e = cudaEventRecord(b, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out, dout, sizeof(pic1d_tp_result) * n, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  float ms = 0.0f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+  if (ms_out) *ms_out = ms;
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  dfree(dr);
+  dfree(dout);
+  if (e != cudaSuccess) {
+    std::fprintf(stderr, "pic1d_tp_map: %s\n", cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? PIC1D_ENOMEM : PIC1D_ECUDA;
+  }
+  return PIC1D_OK;
+}
+
 int pic1d_get_rho(pic1d_ctx* c, int64_t* rho, int mem) {
   if (!c) return PIC1D_EINVAL;
   if (!rho || (mem != 0 && mem != 1)) return fail(c, PIC1D_EINVAL, "get_rho: bad arguments");

@@ -195,3 +195,10 @@ cudaError_t ens_launch_field(const EnsArgs& A, cudaStream_t s);
 cudaError_t ens_launch_finalize(const EnsArgs& A, cudaStream_t s);
 cudaError_t ens_launch_flip(EnsLine* lines, int line, cudaStream_t s);
 }  // namespace pic1d
+
+// test-particle drag maps (tp_map.cu)
+namespace pic1d {
+cudaError_t tp_launch_map(const pic1d_params& p, const double* r_eq_dev, int n, double gamma0, double dt,
+                          double t_max, double b_thr, double gamma_eps, pic1d_tp_result* out_dev,
+                          cudaStream_t s);
+}  // namespace pic1d
