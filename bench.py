@@ -456,28 +456,43 @@ def run_ensemble(args):
     ens.close()
 
 
+# FP64 operations per line-step of the map kernel (adds, multiplies, and two
+# per fused multiply-add), counted by ncu on a map of 4096 lines (1084 =
+# 7.57e10 operations over 6.23e7 line-steps); used for the kernel's
+# arithmetic roofline against the nominal FP64 rate
+TP_FP64_PER_STEP = 1084.0
+FP64_NOMINAL_TFLOPS = 1.25
+
+
 def run_tp_map(args):
-    """The test-particle drag map: 4096 dipole lines, r_eq log-spaced in
-    [2, 100], gamma0 = 1000, B*/B_QED = 10, 1 keV radially streaming photons,
-    dt = 1e-3 R*/c to the equator or t = 200 R*/c; one FP64 thread per line.
-    Reports line-steps/s and the critical radius found."""
+    """The test-particle drag map: `--tp-lines` dipole lines (65,536 by
+    default), r_eq log-spaced in [2, 100], gamma0 = 1000, B*/B_QED = 10,
+    1 keV radially streaming photons, dt = 1e-3 R*/c to the equator or
+    `--tp-tmax` R*/c; one FP64 thread per line.  Reports line-steps/s and the
+    critical radius found."""
     import torch
     from paper_2609_17661_b300 import tp_map
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     if int(os.environ.get("RANK", "0")) != 0:
         return
     cfg = W.config("C1", kT_keV=1.0, photon_model=0, drag_scale=1.0)
-    r = np.geomspace(2.0, 100.0, 4096)
+    r = np.geomspace(2.0, 100.0, args.tp_lines)
     tp_map(cfg, r[:64], dt=1e-3, t_max=20.0)            # warm-up
-    res, ms = tp_map(cfg, r, dt=1e-3, t_max=200.0)
+    res, ms = tp_map(cfg, r, dt=1e-3, t_max=args.tp_tmax)
     steps = float(res["steps"].sum())
     third = r[res["region"] == 3]
+    roof = None
+    if TP_FP64_PER_STEP:
+        ach = steps * TP_FP64_PER_STEP / (ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s (FP64)",
+                "frac": ach / FP64_NOMINAL_TFLOPS, "peak_kind": "nominal", "kernel": "k_tp_map", "traffic": None}
     out = {"metric": "line-steps/s", "value": steps / (ms * 1e-3), "unit": "line-steps/s", "n_gpus": 1,
            "steps": 1, "warmup": 1, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": "test-particle drag map, 4096 dipole lines r_eq in [2, 100], gamma0 1000, "
-                                  "b*=10, 1 keV radial photons, dt 1e-3", "lines": int(r.size)},
-           "lines_per_s": r.size / (ms * 1e-3),
+           "config": {"workload": f"test-particle drag map, {r.size} dipole lines r_eq in [2, 100], gamma0 1000, "
+                                  f"b*=10, 1 keV radial photons, dt 1e-3, t_max {args.tp_tmax:g}",
+                      "lines": int(r.size)},
+           "roofline": roof, "lines_per_s": r.size / (ms * 1e-3),
            "r_crit": float(third.min()) if third.size else None,
            "regions": {str(k): int((res["region"] == k).sum()) for k in (1, 2, 3)},
            "gpu_launches": 1}
@@ -509,6 +524,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--sur-steps", type=int, default=3)
+    ap.add_argument("--tp-lines", type=int, default=65536)
+    ap.add_argument("--tp-tmax", type=float, default=200.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "b300":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
