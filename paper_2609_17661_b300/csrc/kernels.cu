@@ -1408,10 +1408,16 @@ constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
 constexpr int kScanChunk = kScanThreads * kScanItems;
 
+// Sort key: four runs (leptons with u >= 0, u < 0, ions with u >= 0, u < 0),
+// each in cell order, and inside a cell four bands of |u| (below 3, 3-30,
+// 30-300, above), so that the lanes of a warp mostly take the same branch of
+// the drag update (the limiter test |F| tau_min < |u| depends on |u|).
 __device__ __forceinline__ int sort_key(const DevParams& P, uint32_t pos, uint8_t sp, float u) {
   const int cell = min((int)(pos >> P.F), P.N - 1);
   const int group = (sp == PIC1D_SP_ION ? 2 : 0) + (u < 0.0f ? 1 : 0);
-  return group * P.N + cell;
+  const float au = fabsf(u);
+  const int band = (au < 3.0f) ? 0 : ((au < 30.0f) ? 1 : ((au < 300.0f) ? 2 : 3));
+  return (group * P.N + cell) * 4 + band;
 }
 
 __global__ void __launch_bounds__(256) k_hist(DevParams P, uint32_t* counts) {
@@ -1772,7 +1778,7 @@ cudaError_t launch_field(const DevParams& P, double* E64, float* E32, double a, 
   return cudaGetLastError();
 }
 
-int sort_bins(int N) { return 4 * N; }
+int sort_bins(int N) { return 16 * N; }
 int scan_blocks(int N) { return (sort_bins(N) + kScanChunk - 1) / kScanChunk; }
 
 cudaError_t launch_sort(const DevParams& P, uint32_t* counts, long long* offsets, long long* bsum, uint32_t* pos2,

@@ -17,7 +17,9 @@ torch = pytest.importorskip("torch")
 
 
 def _key(pos, sp, u, F, N):
-    return (2 * (sp == W.SP_ION) + (u < 0)) * N + (pos.astype(np.int64) >> F)
+    au = np.abs(u)
+    band = np.where(au < 3, 0, np.where(au < 30, 1, np.where(au < 300, 2, 3)))
+    return ((2 * (sp == W.SP_ION) + (u < 0)) * N + (pos.astype(np.int64) >> F)) * 4 + band
 
 
 @pytest.mark.gpu
