@@ -192,10 +192,10 @@ int pic1d_get_particles(pic1d_ctx* c, int64_t n, uint32_t* pos, float* u, float*
                         uint64_t* id, int mem);
 
 /* Sort the particles by cell now (histogram, scan, scatter) and drop the
- * removed slots.  Key ((2*(ion) + (u < 0)) * n_cells + cell) * 4 + band:
+ * removed slots.  Key ((2*(ion) + (u < 0)) * n_cells + cell) * 8 + band:
  * four runs (leptons moving +s, leptons moving -s, ions moving +s, ions
- * moving -s), each in cell order, and inside a cell four bands of |u|
- * (below 3, 3 to 30, 30 to 300, above).  Asynchronous.
+ * moving -s), each in cell order, and inside a cell eight bands of |u|
+ * with edges 1.5, 3, 10, 30, 100, 300, 1000.  Asynchronous.
  * Errors: ECUDA. */
 int pic1d_sort(pic1d_ctx* c);
 
@@ -236,12 +236,12 @@ int pic1d_variant_info(int variant, int* particles_per_thread, int* min_blocks_p
  * memory an application has reserved in full -- and so cannot create a
  * context, whose sort scratch comes from cudaMalloc.  It sorts n particles of
  * a line of n_cells cells (SoA device arrays in the layout above) by the key
- * ((2*(ion) + (u < 0)) * n_cells + cell) * 4 + band (the key of pic1d_sort), drops removed slots (species PIC1D_SP_DEAD), writes
+ * ((2*(ion) + (u < 0)) * n_cells + cell) * 8 + band (the key of pic1d_sort), drops removed slots (species PIC1D_SP_DEAD), writes
  * the sorted particles to the *_out device arrays (capacity n each) and the
  * number kept to *n_out (a device int64).  The order inside one key is not
  * specified.  Input and output arrays must not overlap.
  *
- * Its scratch (histogram, offsets, block sums, counters; about 12.6 MB) is one
+ * Its scratch (histogram, offsets, block sums, counters; about 25.2 MB) is one
  * fixed-size device array inside this library: every GPU that loads the
  * library holds it until the process exits, so n_cells is limited to
  * PIC1D_SORT_STATIC_MAX_CELLS and larger lines are rejected with

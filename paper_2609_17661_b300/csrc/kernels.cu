@@ -1409,15 +1409,16 @@ constexpr int kScanItems = 4;
 constexpr int kScanChunk = kScanThreads * kScanItems;
 
 // Sort key: four runs (leptons with u >= 0, u < 0, ions with u >= 0, u < 0),
-// each in cell order, and inside a cell four bands of |u| (below 3, 3-30,
-// 30-300, above), so that the lanes of a warp mostly take the same branch of
+// each in cell order, and inside a cell eight bands of |u| (edges 1.5, 3,
+// 10, 30, 100, 300, 1000), so that the lanes of a warp mostly take the same branch of
 // the drag update (the limiter test |F| tau_min < |u| depends on |u|).
 __device__ __forceinline__ int sort_key(const DevParams& P, uint32_t pos, uint8_t sp, float u) {
   const int cell = min((int)(pos >> P.F), P.N - 1);
   const int group = (sp == PIC1D_SP_ION ? 2 : 0) + (u < 0.0f ? 1 : 0);
   const float au = fabsf(u);
-  const int band = (au < 3.0f) ? 0 : ((au < 30.0f) ? 1 : ((au < 300.0f) ? 2 : 3));
-  return (group * P.N + cell) * 4 + band;
+  const int band = (au < 1.5f) ? 0 : (au < 3.0f) ? 1 : (au < 10.0f) ? 2 : (au < 30.0f) ? 3 :
+                   (au < 100.0f) ? 4 : (au < 300.0f) ? 5 : (au < 1000.0f) ? 6 : 7;
+  return (group * P.N + cell) * 8 + band;
 }
 
 __global__ void __launch_bounds__(256) k_hist(DevParams P, uint32_t* counts) {
@@ -1778,7 +1779,7 @@ cudaError_t launch_field(const DevParams& P, double* E64, float* E32, double a, 
   return cudaGetLastError();
 }
 
-int sort_bins(int N) { return 16 * N; }
+int sort_bins(int N) { return 32 * N; }
 int scan_blocks(int N) { return (sort_bins(N) + kScanChunk - 1) / kScanChunk; }
 
 cudaError_t launch_sort(const DevParams& P, uint32_t* counts, long long* offsets, long long* bsum, uint32_t* pos2,

@@ -18,8 +18,8 @@ torch = pytest.importorskip("torch")
 
 def _key(pos, sp, u, F, N):
     au = np.abs(u)
-    band = np.where(au < 3, 0, np.where(au < 30, 1, np.where(au < 300, 2, 3)))
-    return ((2 * (sp == W.SP_ION) + (u < 0)) * N + (pos.astype(np.int64) >> F)) * 4 + band
+    band = np.searchsorted(np.array([1.5, 3, 10, 30, 100, 300, 1000], dtype=np.float32), au, side="right")
+    return ((2 * (sp == W.SP_ION) + (u < 0)) * N + (pos.astype(np.int64) >> F)) * 8 + band
 
 
 @pytest.mark.gpu
