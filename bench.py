@@ -40,12 +40,12 @@ NOMINAL_HBM_GBS = 7700.0 # B300 HBM3e, nominal
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_push
 # launch per slot it read, from one ncu capture of the same push source on a
-# smaller line at the same density (1e8 macroparticles, 26,214 cells: 2.1054
+# smaller line at the same density (1e8 macroparticles, 26,214 cells: 2.0954
 # GB for 1.0e8 slots); traffic grows in proportion to the slots.  Reported
 # only while the push's source -- kernels.cu up to the surrogate-push section,
 # which holds k_push and every device function it calls -- hashes to the
 # captured one, else null.
-PUSH_TRAFFIC = {"sources_sha256": "2c81c278feed83c52387648114abfa22a4057a8fa34abb4734a7831e62d05572", "bytes_per_slot": 21.054}
+PUSH_TRAFFIC = {"sources_sha256": "6b82c0499c2e99d3c1d11367bf098b942fd1da17908cb7af073f41a432aa7a9b", "bytes_per_slot": 20.954}
 PUSH_SOURCE = "paper_2609_17661_b300/csrc/kernels.cu"
 PUSH_SOURCE_END = "// the push with drag law SURROGATE"
 
@@ -262,7 +262,8 @@ def run_gpu(args):
         traffic = PUSH_TRAFFIC["bytes_per_slot"] * units / max(launches, 1)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "kernel": "k_push", "launches": launches,
-            "bytes_per_launch": push_bytes / max(launches, 1), "mean_launch_ms": d1["push_ms"] / max(launches, 1),
+            "bytes_per_launch": push_bytes / max(launches, 1), "slots_per_launch": units / max(launches, 1),
+            "mean_launch_ms": d1["push_ms"] / max(launches, 1),
             "peak_kind": peak_kind, "push_share_of_step": d1["push_ms"] / ms,
             "frac_of_nominal": achieved / NOMINAL_HBM_GBS}
     # the whole step against the roofline: push bytes plus the sort's share

@@ -74,6 +74,19 @@ extern "C" {
 /* surface supply (Sec. 3, App. B.1) */
 #define PIC1D_INJECT_NONE 0
 #define PIC1D_INJECT_RATE 1 /* neutral e- + ion pairs per footpoint per step at the rate carrying j_ext */
+/* The atmosphere of Sec. 3 and App. B.1 (Eq. densprofile): a cell whose centre
+ * sits at radius x (in R_star) has the target density
+ * n/n0 = atmo_a0 exp(-(x - 1) R_star / atmo_h), atmo_h in cells; the
+ * atmosphere is the set of cells where that is >= atmo_ncut.  After each
+ * push, a cell of the atmosphere whose plasma weight (every species, after
+ * the move, not counting the step's new pairs) is below
+ * floor(n/n0 n0_ppc 2^12) / 2^12 receives neutral e- (PIC1D_SP_ATMO) + ion
+ * pairs of weight 1 until the deficit is under one pair: positions uniform
+ * in the cell, momenta Maxwellian at inject_T in both directions.  Gravity,
+ * the force -inject_T/atmo_h along r (-inject_T/atmo_h mu_s along s), acts
+ * on every particle inside the atmosphere (linear between cell centres, like
+ * E) and is zero outside it.  Not with drag law SURROGATE. */
+#define PIC1D_INJECT_TOPUP 2
 
 /* species codes */
 #define PIC1D_SP_ELECTRON 0
@@ -112,6 +125,9 @@ typedef struct pic1d_params {
   /* supply and pairs */
   int32_t inject_mode;      /* PIC1D_INJECT_*                           */
   double inject_T;          /* temperature of injected particles, m_e c^2 */
+  double atmo_a0;           /* TOPUP: n/n0 of the atmosphere at the surface */
+  double atmo_h;            /* TOPUP: scale height, cells               */
+  double atmo_ncut;         /* TOPUP: the atmosphere ends where n/n0 < atmo_ncut */
   int32_t pairs_on;
   double b_pair_threshold;  /* b above which scattering is discrete and may make pairs (0.09) */
   double pair_energy_threshold; /* photon energy for a pair, m_e c^2 (2.0) */

@@ -32,7 +32,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 PHOTON_RADIAL, PHOTON_DISK = 0, 1
 DRAG_OFF, DRAG_CLOSED, DRAG_TABLE, DRAG_SURROGATE = 0, 1, 2, 3
 RICS_SPLIT, RICS_DRAG_PLUS_PAIRS = 0, 1
-INJECT_NONE, INJECT_RATE = 0, 1
+INJECT_NONE, INJECT_RATE, INJECT_TOPUP = 0, 1, 2
 S_BITS = 12
 
 
@@ -56,6 +56,7 @@ class OrcParams(C.Structure):
         ("cells_per_skin_depth", C.c_double), ("j_psi", C.c_double), ("n0_ppc", C.c_double),
         ("mass_ratio", C.c_double),
         ("inject_mode", C.c_int32), ("inject_T", C.c_double),
+        ("atmo_a0", C.c_double), ("atmo_h", C.c_double), ("atmo_ncut", C.c_double),
         ("pairs_on", C.c_int32), ("b_pair_threshold", C.c_double), ("pair_energy_threshold", C.c_double),
         ("n_max_ppc", C.c_double),
         ("seed", C.c_uint64), ("r_star_cm", C.c_double),
@@ -92,6 +93,7 @@ def lib():
             "orc_splitmix64": (C.c_uint64, [C.c_uint64]),
             "orc_child_id": (C.c_uint64, [C.c_uint64, C.c_int64, C.c_int]),
             "orc_inject_id": (C.c_uint64, [C.c_int64, C.c_int, C.c_int64, C.c_int]),
+            "orc_atmo_id": (C.c_uint64, [C.c_int64, C.c_int, C.c_int64, C.c_int]),
             "orc_gauss_legendre": (None, [C.c_int, _D, _D]),
             "orc_theta0": (C.c_double, [C.c_double]),
             "orc_arc_length": (C.c_double, [C.c_double, C.c_double]),
@@ -173,6 +175,10 @@ def child_id(parent, step, member):
 
 def inject_id(step, foot, slot, member):
     return int(lib().orc_inject_id(int(step), int(foot), int(slot), int(member)))
+
+
+def atmo_id(step, cell, slot, member):
+    return int(lib().orc_atmo_id(int(step), int(cell), int(slot), int(member)))
 
 
 def gauss_legendre(n):

@@ -39,6 +39,17 @@
  *     step (integer fixed-point sums) against n_max.
  *   - surface supply (RATE): neutral e- + ion pairs injected per footpoint
  *     per step at the rate that carries j_ext, inward half-Maxwellian.
+ *   - atmosphere (TOPUP, Sec. 3 and App. B.1 [densprofile]): a cell whose
+ *     centre sits at radius x has the target density
+ *     n/n0 = a0 exp(-(x - 1) R_star / h) (h in cells); the atmosphere is the
+ *     set of cells where that is >= n_cut (gravity is off elsewhere, where
+ *     n/n0 << 1).  After the move, a cell's plasma weight W (all species,
+ *     integer fixed point, this step's pairs not included) is compared with
+ *     the target weight floor(n/n0 n0_ppc 2^12); the deficit is filled with
+ *     neutral e- + ion pairs of weight 1, uniform in the cell, Maxwellian at
+ *     T in both directions.  Gravity: the force -T/h along r, i.e.
+ *     -T/h mu_s along s, on every particle, kept at cell centres of the
+ *     atmosphere (zero elsewhere) and gathered like E; du = (q/m E + g/m) dt.
  */
 #include <math.h>
 #include <stdint.h>
@@ -57,11 +68,12 @@
 enum { ORC_PHOTON_RADIAL = 0, ORC_PHOTON_DISK = 1 };
 enum { ORC_DRAG_OFF = 0, ORC_DRAG_CLOSED = 1, ORC_DRAG_TABLE = 2, ORC_DRAG_SURROGATE = 3 };
 enum { ORC_RICS_SPLIT = 0, ORC_RICS_DRAG_PLUS_PAIRS = 1 };
-enum { ORC_INJECT_NONE = 0, ORC_INJECT_RATE = 1 };
+enum { ORC_INJECT_NONE = 0, ORC_INJECT_RATE = 1, ORC_INJECT_TOPUP = 2 };
 enum { ORC_SP_ELEC = 0, ORC_SP_POSI = 1, ORC_SP_ION = 2, ORC_SP_ATMO = 3 };
 
 #define ORC_TAG_RICS 0x52494353u   /* counter word 3 of the scattering draw */
 #define ORC_TAG_INJ  0x494E4A31u   /* counter word 3 of the injection draw  */
+#define ORC_TAG_ATM  0x41544D4Fu   /* counter word 3 of the atmosphere draw */
 #define ORC_S_BITS   12            /* weight fixed point: w_int = rint(w*2^12) */
 
 typedef struct {
@@ -71,7 +83,7 @@ typedef struct {
   int32_t quad_n_mu; int32_t quad_n_phi;
   double eta_min; int32_t rics_mode; int32_t mc_on;
   double cells_per_skin_depth; double j_psi; double n0_ppc; double mass_ratio;
-  int32_t inject_mode; double inject_T;
+  int32_t inject_mode; double inject_T; double atmo_a0; double atmo_h; double atmo_ncut;
   int32_t pairs_on; double b_pair_threshold; double pair_energy_threshold; double n_max_ppc;
   uint64_t seed; double r_star_cm;
 } orc_params;
@@ -123,6 +135,14 @@ uint64_t orc_inject_id(int64_t step, int foot, int64_t slot, int member)
 {
   uint64_t key = ((uint64_t)step << 24) ^ ((uint64_t)foot << 23) ^ ((uint64_t)slot << 1) ^ (uint64_t)member;
   return orc_splitmix64(key ^ 0x5A17A5EEDull) | 0x8000000000000000ull;
+}
+
+/* atmosphere particle `slot` (member 0: e-, 1: ion) of cell `cell` at `step` */
+uint64_t orc_atmo_id(int64_t step, int cell, int64_t slot, int member)
+{
+  uint64_t a = orc_splitmix64(((uint64_t)step << 1) | (uint64_t)member);
+  uint64_t b = ((uint64_t)(uint32_t)cell << 32) | (uint64_t)(uint32_t)slot;
+  return orc_splitmix64(a ^ b ^ 0xA7305EEDull) | 0x8000000000000000ull;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -593,6 +613,9 @@ typedef struct {
   double tau_min;   /* drag-time floor [code time]                        */
   double *node_x, *node_b, *node_mu;   /* N+1 nodes                       */
   unsigned char* zone;                 /* N cells: b(centre) > b_thr      */
+  int64_t* atmo_target;                /* N cells: TOPUP target weight (w_int), -1 outside */
+  double* grav;                        /* N cell centres: gravity along s (per unit mass) */
+  int grav_on;
   double* table;
   double* sur;                         /* surrogate parameters (8770) or NULL */
   double *E, *J;
@@ -665,12 +688,26 @@ orc_sim* orc_create(const orc_params* p, const double* table_or_null)
     orc_field_at_theta(p, th, &S->node_x[k], &S->node_b[k], &S->node_mu[k]);
   }
   S->zone = malloc(N);
+  S->atmo_target = malloc(N * sizeof(int64_t));
+  S->grav = malloc(N * sizeof(double));
   for (int c = 0; c < N; ++c) {
     double th = orc_theta_of_s(p->r_eq, S->L_R * (c + 0.5) / N);
     double x, b, mu;
     orc_field_at_theta(p, th, &x, &b, &mu);
     S->zone[c] = (b > p->b_pair_threshold) ? 1 : 0;
+    S->atmo_target[c] = -1;
+    S->grav[c] = 0.0;
+    if (p->inject_mode == ORC_INJECT_TOPUP) {
+      /* [densprofile]: n/n0 = a0 exp(-(r - R_star)/h), r - R_star in cells */
+      double n = p->atmo_a0 * exp(-(x - 1.0) * S->R_cells / p->atmo_h);
+      if (n >= p->atmo_ncut) {
+        S->atmo_target[c] = (int64_t)floor(n * p->n0_ppc * (double)(1 << ORC_S_BITS));
+        /* hydrostatic: T dn/dr = n g, g = -T/h along r; along s: g mu_s */
+        S->grav[c] = -(p->inject_T / p->atmo_h) * mu;
+      }
+    }
   }
+  S->grav_on = (p->inject_mode == ORC_INJECT_TOPUP);
   if (p->drag_law == ORC_DRAG_TABLE) {
     size_t nt = (size_t)2 * p->table_n_s * p->table_n_gamma * 2;
     S->table = malloc(nt * sizeof(double));
@@ -687,6 +724,7 @@ void orc_free(orc_sim* S)
 {
   if (!S) return;
   free(S->node_x); free(S->node_b); free(S->node_mu); free(S->zone); free(S->table);
+  free(S->atmo_target); free(S->grav);
   free(S->E); free(S->J); free(S->dens); free(S->sur);
   free(S->s); free(S->u); free(S->w); free(S->sp); free(S->id);
   free(S);
@@ -1037,15 +1075,17 @@ void orc_deposit_int(int N, int Fbits, int64_t n, const int64_t* p0, const int64
 }
 
 /* E at s: linear between cell centres c + 1/2, constant beyond the ends */
-static double orc_gather(const orc_sim* S, double s)
+static double orc_gather_at(const orc_sim* S, const double* a, double s)
 {
   double x = s - 0.5;
   int i = (int)floor(x);
-  if (i < 0) return S->E[0];
-  if (i >= S->N - 1) return S->E[S->N - 1];
+  if (i < 0) return a[0];
+  if (i >= S->N - 1) return a[S->N - 1];
   double f = x - i;
-  return (1.0 - f) * S->E[i] + f * S->E[i + 1];
+  return (1.0 - f) * a[i] + f * a[i + 1];
 }
+
+static double orc_gather(const orc_sim* S, double s) { return orc_gather_at(S, S->E, s); }
 
 /* ------------------------------------------------------------------------ */
 /* One PIC cycle (Sec. 3), n -> n+1.  E at integer times, u at half times.    */
@@ -1081,7 +1121,8 @@ void orc_step(orc_sim* S)
     double Ep = orc_gather(S, s);
     /* 2-4. Strang: drag dt/2, Lorentz kick dt, drag dt/2 */
     if (cont) u = orc_drag_half(S, u, s);
-    u += orc_qm(S, sp) * Ep * dt;
+    if (S->grav_on) u += (orc_qm(S, sp) * Ep + orc_gather_at(S, S->grav, s) / orc_mass(S, sp)) * dt;
+    else u += orc_qm(S, sp) * Ep * dt;
     if (cont) u = orc_drag_half(S, u, s);
     /* 5. Monte-Carlo RICS in the pair zone */
     int make_pair = 0;
@@ -1158,10 +1199,12 @@ void orc_step(orc_sim* S)
   (void)E_old_sum_sq;
 
   /* 9. remove losses, append pairs then surface injection */
+  int64_t* wcell = S->grav_on ? calloc(N, sizeof(int64_t)) : NULL;   /* plasma weight after the move */
   int64_t m = 0;
   for (int64_t k = 0; k < n0; ++k) {
     if (!alive[k]) continue;
     S->s[m] = S->s[k]; S->u[m] = S->u[k]; S->w[m] = S->w[k]; S->sp[m] = S->sp[k]; S->id[m] = S->id[k];
+    if (wcell) wcell[(int)floor(S->s[m])] += orc_wint(S->w[m]);
     m++;
   }
   S->n = m;
@@ -1200,6 +1243,35 @@ void orc_step(orc_sim* S)
       }
     }
   }
+  if (p->inject_mode == ORC_INJECT_TOPUP) {
+    /* atmosphere: fill each cell's deficit with neutral pairs of weight 1 */
+    const int64_t pair_w = 2 * (int64_t)(1 << ORC_S_BITS);
+    for (int c = 0; c < N; ++c) {
+      if (S->atmo_target[c] < 0) continue;
+      int64_t deficit = S->atmo_target[c] - wcell[c];
+      int64_t cnt = deficit > 0 ? deficit / pair_w : 0;
+      orc_grow(S, S->n + 2 * cnt);
+      for (int64_t slot = 0; slot < cnt; ++slot) {
+        uint32_t ctr[4] = { (uint32_t)slot, (uint32_t)c, (uint32_t)S->step, ORC_TAG_ATM };
+        uint32_t r[4];
+        orc_philox4x32_10(ctr, key, r);
+        double pos = (double)c + (double)(r[0] >> 16) * (1.0 / 65536.0);
+        double rad = sqrt(-2.0 * log(1.0 - orc_u24(r[1])));
+        double ang = 2.0 * ORC_PI * orc_u24(r[2]);
+        double ue = sqrt(p->inject_T) * rad * cos(ang);
+        double ui = sqrt(p->inject_T / p->mass_ratio) * rad * sin(ang);
+        for (int mem = 0; mem < 2; ++mem) {
+          S->s[S->n] = pos; S->w[S->n] = 1.0;
+          S->u[S->n] = mem == 0 ? ue : ui;
+          S->sp[S->n] = mem == 0 ? ORC_SP_ATMO : ORC_SP_ION;
+          S->id[S->n] = orc_atmo_id(S->step, c, slot, mem);
+          S->n++;
+        }
+        S->d.injected += 2;
+      }
+    }
+  }
+  free(wcell);
   S->step++;
   orc_recount_density(S);
   free(cs); free(cu); free(cw); free(csp); free(cid); free(alive);

@@ -26,6 +26,7 @@ class Params(C.Structure):
         ("cells_per_skin_depth", C.c_double), ("j_psi", C.c_double), ("n0_ppc", C.c_double),
         ("mass_ratio", C.c_double),
         ("inject_mode", C.c_int32), ("inject_T", C.c_double),
+        ("atmo_a0", C.c_double), ("atmo_h", C.c_double), ("atmo_ncut", C.c_double),
         ("pairs_on", C.c_int32), ("b_pair_threshold", C.c_double), ("pair_energy_threshold", C.c_double),
         ("n_max_ppc", C.c_double),
         ("seed", C.c_uint64), ("r_star_cm", C.c_double),

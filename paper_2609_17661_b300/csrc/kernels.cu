@@ -54,6 +54,12 @@ __device__ __forceinline__ unsigned long long supply_id(long long step, int foot
                                ((unsigned long long)slot << 1) ^ (unsigned long long)m;
   return mix64(k ^ 0x5A17A5EEDull) | 0x8000000000000000ull;
 }
+// id of atmosphere particle `slot` (m = 0: e-, 1: ion) topped up in `cell` at `step`
+__device__ __forceinline__ unsigned long long atmo_id(long long step, int cell, long long slot, int m) {
+  const unsigned long long a = mix64(((unsigned long long)step << 1) | (unsigned long long)m);
+  const unsigned long long b = ((unsigned long long)(uint32_t)cell << 32) | (unsigned long long)(uint32_t)slot;
+  return mix64(a ^ b ^ 0xA7305EEDull) | 0x8000000000000000ull;
+}
 
 __device__ __forceinline__ unsigned lanemask_lt() {
   unsigned m;
@@ -339,8 +345,9 @@ struct PushOut {
 // One PIC cycle of one particle (Sec. 3): gather, Strang-split drag, kick,
 // Monte-Carlo RICS, move, and the charge-conserving deposit contributions.
 // Positions are u32 fixed point; every particle alive at the start of a step
-// has pos < top, and a step is shorter than one cell.
-template <bool NMAX>
+// has pos < top, and a step is shorter than one cell.  ATMO adds gravity
+// (inject mode TOPUP), gathered like E.
+template <bool NMAX, bool ATMO = false>
 __device__ __forceinline__ PushOut push_one(const DevParams& P, uint32_t idx, uint32_t pos0, float u, float w,
                                             int sp, Tally& T) {
   const uint32_t fmask = (1u << P.F) - 1u;
@@ -356,7 +363,7 @@ __device__ __forceinline__ PushOut push_one(const DevParams& P, uint32_t idx, ui
   const int cell = (int)(pos0 >> P.F);
   o.cell = cell;
   // 1. gather E linearly between cell centres (constant beyond the end centres)
-  float Ep;
+  float Ep, Gp = 0.0f;
   {
     const uint32_t x = pos0 < half ? 0u : pos0 - half;
     int ig = (int)(x >> P.F);
@@ -364,6 +371,10 @@ __device__ __forceinline__ PushOut push_one(const DevParams& P, uint32_t idx, ui
     if (ig > P.N - 2) { ig = P.N - 2; f = 1.0f; }
     const float e0 = __ldg(P.E32 + ig), e1 = __ldg(P.E32 + ig + 1);
     Ep = fmaf(f, e1 - e0, e0);
+    if (ATMO) {
+      const float g0 = __ldg(P.G32 + ig), g1 = __ldg(P.G32 + ig + 1);
+      Gp = fmaf(f, g1 - g0, g0);
+    }
   }
   const bool zone = __ldg(P.zone + cell) != 0;
   const bool cont = lep && P.drag_law != PIC1D_DRAG_OFF && (P.rics_mode == PIC1D_RICS_DRAG_PLUS_PAIRS || !zone);
@@ -385,7 +396,8 @@ __device__ __forceinline__ PushOut push_one(const DevParams& P, uint32_t idx, ui
   }
   // 2-4. Strang split: drag dt/2, Lorentz kick dt, drag dt/2
   if (cont) u = drag_half(P, S, u, T.n_lim, T.n_newt);
-  u = fmaf(qm * Ep, P.dt, u);
+  if (ATMO) u = fmaf(fmaf(qm, Ep, Gp / mass), P.dt, u);
+  else u = fmaf(qm * Ep, P.dt, u);
   if (cont) u = drag_half(P, S, u, T.n_lim, T.n_newt);
   // 5. Monte-Carlo RICS in the pair zone
   bool make_pair = false;
@@ -619,8 +631,11 @@ __device__ __forceinline__ void window_drain(long long* sWin, int win_lo, const 
 // touched range is drained to global memory at the end of the chunk.  The
 // lepton density of the pair cap is summed per warp in a warp-uniform pending
 // register while the warp's contributions stay in one cell.  Slot indices are
-// 32-bit (capacity < 2^31).
-template <int PPT, int MINB, bool NMAX>
+// 32-bit (capacity < 2^31).  ATMO (inject mode TOPUP): gravity, and the plasma
+// weight of each atmosphere cell after the move, summed into P.atmo_w (the
+// atmosphere and the two cells around it are never fast cells, so every
+// particle that ends a step there goes through push_one).
+template <int PPT, int MINB, bool NMAX, bool ATMO = false>
 __global__ void __launch_bounds__(kBlock, MINB) k_push(DevParams P) {
   using VU = typename Vec<PPT>::U;
   using VF = typename Vec<PPT>::F;
@@ -716,7 +731,19 @@ __global__ void __launch_bounds__(kBlock, MINB) k_push(DevParams P) {
         } else {
           o.want_pair = false;
           o.want_dens = false;
-          if (valid) o = push_one<NMAX>(P, idx, pp[k], uu[k], ww[k], ss[k] & 3, T);
+          if (valid) o = push_one<NMAX, ATMO>(P, idx, pp[k], uu[k], ww[k], ss[k] & 3, T);
+          // plasma weight of the atmosphere cells after the move
+          if (ATMO) {
+            const bool ma = valid && !o.lost && __ldg(P.atmo_flag + (o.pos >> P.F)) != 0;
+            const unsigned am = __ballot_sync(0xffffffffu, ma);
+            if (ma) {
+              const int ac = (int)(o.pos >> P.F);
+              const unsigned grp = __match_any_sync(am, ac);
+              const long long sum = group_sum64(grp, (long long)__float2int_rn(ww[k] * 4096.0f));
+              if (lane == __ffs(grp) - 1)
+                atomicAdd(reinterpret_cast<unsigned long long*>(P.atmo_w + ac), (unsigned long long)sum);
+            }
+          }
           // lepton density for the pair cap: only cells where a pair can be tested
           if (NMAX) {
             const unsigned md = __ballot_sync(0xffffffffu, o.want_dens);
@@ -1336,6 +1363,50 @@ __global__ void k_inject(DevParams P, double carriers, float sig_e, float sig_i)
 }
 
 // --------------------------------------------------------------------------
+// atmosphere top-up (TOPUP): one block per atmosphere cell fills the cell's
+// deficit (target minus the plasma weight the push summed) with neutral
+// e- + ion pairs of weight 1, uniform in the cell, Maxwellian in both
+// directions.  The slots of a cell are one contiguous range taken from the
+// step's append counter; pair k of a cell draws Philox (k, cell, step, tag).
+// --------------------------------------------------------------------------
+__global__ void k_topup(DevParams P, const int* cells, const long long* target, float sig_e, float sig_i) {
+  __shared__ long long s_slot0;
+  const int c = cells[blockIdx.x];
+  const long long deficit = target[blockIdx.x] - P.atmo_w[c];
+  const long long npair = deficit > 0 ? deficit / (2ll * 4096ll) : 0;
+  if (npair == 0) return;                       // the same for every thread of the block
+  if (threadIdx.x == 0)
+    s_slot0 = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&P.st->append),
+                                   (unsigned long long)(2 * npair));
+  __syncthreads();
+  const long long n = P.st->n_slots;
+  unsigned ok = 0, drop = 0;
+  for (long long k = threadIdx.x; k < npair; k += blockDim.x) {
+    const long long dst = n + s_slot0 + 2 * k;
+    if (dst + 2 > P.cap) { ++drop; continue; }
+    const uint4 r = philox4x32_10(make_uint4((uint32_t)k, (uint32_t)c, (uint32_t)P.step, kTagAtmo), P.key0, P.key1);
+    const uint32_t q = r.x >> 16;               // 16 fractional bits of the cell
+    const uint32_t frac = P.F >= 16 ? (q << (P.F - 16)) : (q >> (16 - P.F));
+    const uint32_t pfix = ((uint32_t)c << P.F) + frac;
+    const float rad = sqrtf(-2.0f * logf(1.0f - unit24(r.y)));
+    const float ang = 6.283185307179586f * unit24(r.z);
+    const float ue = sig_e * rad * cosf(ang);
+    const float ui = sig_i * rad * sinf(ang);
+    for (int m = 0; m < 2; ++m) {
+      P.pos[dst + m] = pfix;
+      P.u[dst + m] = m == 0 ? ue : ui;
+      P.w[dst + m] = 1.0f;
+      P.sp[dst + m] = m == 0 ? PIC1D_SP_ATMO : PIC1D_SP_ION;
+      P.id[dst + m] = atmo_id(P.step, c, k, m);
+    }
+    if (P.use_nmax) atomicAdd(reinterpret_cast<unsigned long long*>(P.dens_next + c), 4096ull);
+    ++ok;
+  }
+  if (ok) atomicAdd(&P.ctr->injected, 2ull * ok);
+  if (drop) atomicAdd(&P.ctr->injected_dropped, 2ull * drop);
+}
+
+// --------------------------------------------------------------------------
 // field update, FP64: E += 4 pi dt j_ext - 4 pi q_p 2^(-F-12) J_int (J_int is kept
 // until the next step clears it, so that it can be read back)
 // --------------------------------------------------------------------------
@@ -1695,6 +1766,8 @@ struct PushVariant {
 #define PV(PPT_, MINB_) {PPT_, MINB_, (const void*)k_push<PPT_, MINB_, false>, (const void*)k_push<PPT_, MINB_, true>}
 static const PushVariant kPushVariants[] = {PV(1, 4), PV(1, 3), PV(2, 3), PV(2, 4)};
 #undef PV
+// the atmosphere's push (inject mode TOPUP): one particle per thread, whatever the variant
+static const void* const kPushAtmo[2] = {(const void*)k_push<1, 4, false, true>, (const void*)k_push<1, 4, true, true>};
 constexpr int kNumPushVariants = sizeof(kPushVariants) / sizeof(kPushVariants[0]);
 
 int push_variant_count() { return kNumPushVariants; }
@@ -1711,6 +1784,7 @@ int push_blocks_per_sm(int v, bool nmax) {
 cudaError_t launch_push(const DevParams& P, int variant, int grid, cudaStream_t s) {
   const PushVariant& V = kPushVariants[variant];
   void* args[] = {const_cast<DevParams*>(&P)};
+  if (P.G32) return cudaLaunchKernel(kPushAtmo[P.use_nmax ? 1 : 0], dim3(grid), dim3(kBlock), args, 0, s);
   return cudaLaunchKernel(P.use_nmax ? V.k_nmax : V.k_plain, dim3(grid), dim3(kBlock), args, 0, s);
 }
 
@@ -1762,6 +1836,13 @@ cudaError_t ens_launch_finalize(const EnsArgs& A, cudaStream_t s) {
 
 cudaError_t ens_launch_flip(EnsLine* lines, int line, cudaStream_t s) {
   k_ens_flip<<<1, 1, 0, s>>>(lines, line);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_topup(const DevParams& P, const int* cells, const long long* target, int n_cells, float sig_e,
+                         float sig_i, cudaStream_t s) {
+  if (n_cells <= 0) return cudaSuccess;
+  k_topup<<<n_cells, 128, 0, s>>>(P, cells, target, sig_e, sig_i);
   return cudaGetLastError();
 }
 

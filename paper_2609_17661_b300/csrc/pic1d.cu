@@ -143,6 +143,13 @@ struct pic1d_ctx {
   uint8_t* zone = nullptr;
   uint8_t* dens_flag = nullptr;
   uint8_t* fast_cell = nullptr;
+  // atmosphere (inject mode TOPUP)
+  float* G32 = nullptr;             // gravity along s per unit mass at cell centres
+  uint8_t* atmo_flag = nullptr;     // cells of the atmosphere
+  long long* atmo_w = nullptr;      // plasma weight per cell after the push (w_int)
+  int* atmo_cells = nullptr;        // the atmosphere's cells
+  long long* atmo_target = nullptr; // their target weights (w_int)
+  int n_atmo = 0;
   float2* table = nullptr;
   float4* tpair = nullptr;
   Counters* ctr = nullptr;
@@ -294,6 +301,9 @@ DevParams dev_params(pic1d_ctx* c) {
   P.zone = c->zone;
   P.dens_flag = c->dens_flag;
   P.fast_cell = c->fast_cell;
+  P.G32 = c->G32;
+  P.atmo_flag = c->atmo_flag;
+  P.atmo_w = c->atmo_w;
   P.dens_cur = c->dens[c->step & 1];
   P.dens_next = c->dens[(c->step + 1) & 1];
   P.cap = c->cap;
@@ -327,7 +337,14 @@ int validate(const pic1d_params* p, std::string& why) {
   if (p->rics_mode != PIC1D_RICS_SPLIT && p->rics_mode != PIC1D_RICS_DRAG_PLUS_PAIRS) return bad("bad rics_mode");
   if (!(p->cells_per_skin_depth > 0.0) || !(p->n0_ppc > 0.0) || !(p->j_psi >= 0.0)) return bad("bad plasma scales");
   if (!(p->mass_ratio > 0.0)) return bad("mass_ratio must be positive");
-  if (p->inject_mode != PIC1D_INJECT_NONE && p->inject_mode != PIC1D_INJECT_RATE) return bad("bad inject_mode");
+  if (p->inject_mode != PIC1D_INJECT_NONE && p->inject_mode != PIC1D_INJECT_RATE &&
+      p->inject_mode != PIC1D_INJECT_TOPUP)
+    return bad("bad inject_mode");
+  if (p->inject_mode == PIC1D_INJECT_TOPUP) {
+    if (!(p->atmo_a0 > 0.0) || !(p->atmo_h > 0.0) || !(p->atmo_ncut > 0.0) || !(p->inject_T >= 0.0))
+      return bad("TOPUP needs atmo_a0, atmo_h, atmo_ncut > 0 and inject_T >= 0");
+    if (p->drag_law == PIC1D_DRAG_SURROGATE) return bad("TOPUP is not available with drag law SURROGATE");
+  }
   if (p->sort_every < 1) return bad("sort_every must be >= 1");
   if (p->capacity < 0) return bad("capacity must be >= 0");
   if (!(p->r_star_cm > 0.0)) return bad("r_star_cm must be positive");
@@ -341,7 +358,11 @@ int build_tables(pic1d_ctx* c) {
   c->L_R = line.L;
   c->R_cells = N / line.L;
   std::vector<float> hb(N + 1), hmu(N + 1), hx(N + 1);
-  std::vector<uint8_t> hz(N);
+  std::vector<uint8_t> hz(N), ha(N, 0);
+  std::vector<float> hg(N, 0.0f);
+  std::vector<int> acells;
+  std::vector<long long> atarget;
+  const bool topup = p.inject_mode == PIC1D_INJECT_TOPUP;
   double guess = line.th0;
   for (int k = 0; k <= N; ++k) {
     const double th = line.theta_of(line.L * (double)k / N, guess);
@@ -357,6 +378,16 @@ int build_tables(pic1d_ctx* c) {
     double x, b, mu;
     field_at(p, th, x, b, mu);
     hz[cc] = (b > p.b_pair_threshold) ? 1 : 0;
+    if (topup) {
+      // Eq. densprofile with r - R_star in cells; hydrostatic gravity -T/h along r
+      const double n_rel = p.atmo_a0 * std::exp(-(x - 1.0) * c->R_cells / p.atmo_h);
+      if (n_rel >= p.atmo_ncut) {
+        ha[cc] = 1;
+        hg[cc] = (float)(-(p.inject_T / p.atmo_h) * mu);
+        acells.push_back(cc);
+        atarget.push_back((long long)std::floor(n_rel * p.n0_ppc * 4096.0));
+      }
+    }
   }
   CK(dalloc(&c->nb, N + 1), "alloc nodes");
   CK(dalloc(&c->nmu, N + 1), "alloc nodes");
@@ -367,15 +398,33 @@ int build_tables(pic1d_ctx* c) {
     hf[cc] = hz[cc] | (cc > 0 ? hz[cc - 1] : 0) | (cc + 1 < N ? hz[cc + 1] : 0);
   CK(dalloc(&c->dens_flag, N), "alloc zone");
   CK(cudaMemcpyAsync(c->dens_flag, hf.data(), N, cudaMemcpyHostToDevice, c->s), "copy zone");
-  // fast cells: no zone cell within two cells, not an end cell
+  // fast cells: no zone or atmosphere cell within two cells, not an end cell
   std::vector<uint8_t> hq(N);
   for (int cc = 0; cc < N; ++cc) {
     bool ok = cc >= 1 && cc <= N - 2;
     for (int d = -2; d <= 2 && ok; ++d) {
       const int k = cc + d;
-      if (k >= 0 && k < N && hz[k]) ok = false;
+      if (k >= 0 && k < N && (hz[k] || ha[k])) ok = false;
     }
     hq[cc] = ok ? 1 : 0;
+  }
+  if (topup) {
+    c->n_atmo = (int)acells.size();
+    CK(dalloc(&c->G32, N), "alloc atmosphere");
+    CK(dalloc(&c->atmo_flag, N), "alloc atmosphere");
+    CK(dalloc(&c->atmo_w, N), "alloc atmosphere");
+    CK(dalloc(&c->atmo_cells, std::max<size_t>(acells.size(), 1)), "alloc atmosphere");
+    CK(dalloc(&c->atmo_target, std::max<size_t>(atarget.size(), 1)), "alloc atmosphere");
+    CK(cudaMemcpyAsync(c->G32, hg.data(), N * sizeof(float), cudaMemcpyHostToDevice, c->s), "copy atmosphere");
+    CK(cudaMemcpyAsync(c->atmo_flag, ha.data(), N, cudaMemcpyHostToDevice, c->s), "copy atmosphere");
+    if (!acells.empty()) {
+      CK(cudaMemcpyAsync(c->atmo_cells, acells.data(), acells.size() * sizeof(int), cudaMemcpyHostToDevice, c->s),
+         "copy atmosphere");
+      CK(cudaMemcpyAsync(c->atmo_target, atarget.data(), atarget.size() * sizeof(long long),
+                         cudaMemcpyHostToDevice, c->s),
+         "copy atmosphere");
+    }
+    CK(cudaStreamSynchronize(c->s), "copy atmosphere");
   }
   CK(dalloc(&c->fast_cell, N), "alloc zone");
   CK(cudaMemcpyAsync(c->fast_cell, hq.data(), N, cudaMemcpyHostToDevice, c->s), "copy zone");
@@ -662,6 +711,7 @@ int pic1d_step(pic1d_ctx* c, int n_steps) {
     DevParams P = dev_params(c);
     CK(cudaMemsetAsync(c->J, 0, c->N * sizeof(long long), c->s), "clear J");
     CK(cudaMemsetAsync(&c->st->work, 0, sizeof(unsigned long long), c->s), "clear schedule");
+    if (c->atmo_w) CK(cudaMemsetAsync(c->atmo_w, 0, c->N * sizeof(long long), c->s), "clear atmosphere");
     if (c->timing) {
       int rc = timing_begin(c);
       if (rc != PIC1D_OK) return rc;
@@ -675,6 +725,8 @@ int pic1d_step(pic1d_ctx* c, int n_steps) {
     }
     if (c->timing) CK(cudaEventRecord(c->ev.back(), c->s), "timing");
     if (p.inject_mode == PIC1D_INJECT_RATE) CK(launch_inject(P, carriers, sig_e, sig_i, c->s), "inject");
+    if (p.inject_mode == PIC1D_INJECT_TOPUP)
+      CK(launch_topup(P, c->atmo_cells, c->atmo_target, c->n_atmo, sig_e, sig_i, c->s), "top-up");
     CK(launch_field(P, c->E64, c->E32, a, cJ, dt_jext, c->field_partial, grid, c->s), "field");
     c->step += 1;
     if (c->step % p.sort_every == 0) {
@@ -1072,7 +1124,7 @@ int pic1d_train_surrogate(pic1d_ctx* c, const pic1d_train_cfg* cfg, pic1d_train_
 namespace {
 
 const char kCkptMagic[8] = {'P', 'I', 'C', '1', 'D', 'C', 'K', '1'};
-constexpr uint32_t kCkptVersion = 1;
+constexpr uint32_t kCkptVersion = 2;
 
 // The parameters as they must agree between a checkpoint and the context
 // that loads it, field by field (the struct's padding is not part of it; the
@@ -1084,7 +1136,8 @@ std::vector<uint64_t> ckpt_params(const pic1d_params& p) {
           (uint64_t)p.photon_model, (uint64_t)p.drag_law, d(p.drag_scale), (uint64_t)p.table_n_gamma,
           (uint64_t)p.table_n_s, d(p.table_log10g_max), (uint64_t)p.quad_n_mu, (uint64_t)p.quad_n_phi,
           d(p.eta_min), (uint64_t)p.rics_mode, (uint64_t)p.mc_on, d(p.cells_per_skin_depth), d(p.j_psi),
-          d(p.n0_ppc), d(p.mass_ratio), (uint64_t)p.inject_mode, d(p.inject_T), (uint64_t)p.pairs_on,
+          d(p.n0_ppc), d(p.mass_ratio), (uint64_t)p.inject_mode, d(p.inject_T), d(p.atmo_a0), d(p.atmo_h),
+          d(p.atmo_ncut), (uint64_t)p.pairs_on,
           d(p.b_pair_threshold), d(p.pair_energy_threshold), d(p.n_max_ppc), p.seed, d(p.r_star_cm),
           (uint64_t)p.sort_every};
 }
@@ -1692,7 +1745,8 @@ void pic1d_free(pic1d_ctx* c) {
   void* ptrs[] = {c->E64, c->E32, c->J, c->dens[0], c->dens[1], c->nb, c->nmu, c->nx, c->zone, c->dens_flag, c->fast_cell, c->table,
                   c->ctr, c->st, c->ke_partial, c->field_partial, c->counts, c->offsets, c->spc, c->slot_log,
                   c->tpair, c->bsum, c->sur.master, c->sur.m, c->sur.v, c->sur.img, c->sur.small,
-                  c->sur.part, c->sur.loss_part, c->sur.err, c->sur_gx, c->sur_gw, c->sur_grad, c->sur_loss, c->rho};
+                  c->sur.part, c->sur.loss_part, c->sur.err, c->sur_gx, c->sur_gw, c->sur_grad, c->sur_loss, c->rho,
+                  c->G32, c->atmo_flag, c->atmo_w, c->atmo_cells, c->atmo_target};
   for (void* q : ptrs) dfree(q);
   delete c;
   g_live.fetch_sub(1);

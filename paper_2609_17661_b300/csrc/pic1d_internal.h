@@ -16,6 +16,7 @@ constexpr int kChunkTiles = 32;      // tiles per dynamically scheduled chunk of
 constexpr int kWBits = 12;           // weight fixed point: w_int = rint(w * 2^12)
 constexpr uint32_t kTagRics = 0x52494353u;
 constexpr uint32_t kTagInj = 0x494E4A31u;
+constexpr uint32_t kTagAtmo = 0x41544D4Fu;   // atmosphere top-up draws
 constexpr int kMaxFieldBlocks = 1024;
 
 // Device-side counters, accumulated over the life of the context.
@@ -75,6 +76,10 @@ struct DevParams {
   const uint8_t* dens_flag; // cells where the pair cap can be tested: zone cells and their neighbours
   const uint8_t* fast_cell; // no zone cell within two cells and not at a wall: the push's fast path
   long long* dens_cur; long long* dens_next;
+  // atmosphere (inject mode TOPUP; null otherwise)
+  const float* G32;         // gravity along s per unit mass at cell centres (zero outside the atmosphere)
+  const uint8_t* atmo_flag; // cells of the atmosphere
+  long long* atmo_w;        // plasma weight (w_int) per cell after the move, summed by the push
   long long cap;
   Counters* ctr;
   StepState* st;
@@ -98,6 +103,9 @@ int push_variant_ppt(int v);
 int push_variant_minb(int v);
 cudaError_t launch_inject(const DevParams& P, double carriers_per_step, float sig_e, float sig_i,
                           cudaStream_t s);
+// atmosphere top-up (TOPUP): n_cells cells of the atmosphere with their target weights (w_int)
+cudaError_t launch_topup(const DevParams& P, const int* cells, const long long* target, int n_cells, float sig_e,
+                         float sig_i, cudaStream_t s);
 cudaError_t launch_field(const DevParams& P, double* E64, float* E32, double four_pi_dt_jext, double cJ,
                          double dt_jext, double* field_partial, int grid_push, cudaStream_t s);
 cudaError_t launch_sort(const DevParams& P, uint32_t* counts, long long* offsets, long long* bsum,

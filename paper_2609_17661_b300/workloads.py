@@ -30,7 +30,7 @@ import numpy as np
 PHOTON_RADIAL, PHOTON_DISK = 0, 1
 DRAG_OFF, DRAG_CLOSED, DRAG_TABLE, DRAG_SURROGATE = 0, 1, 2, 3
 RICS_SPLIT, RICS_DRAG_PLUS_PAIRS = 0, 1
-INJECT_NONE, INJECT_RATE = 0, 1
+INJECT_NONE, INJECT_RATE, INJECT_TOPUP = 0, 1, 2
 SP_ELEC, SP_POSI, SP_ION, SP_ATMO = 0, 1, 2, 3
 
 BASE = dict(
@@ -44,6 +44,9 @@ BASE = dict(
     cells_per_skin_depth=48.0, j_psi=28.0, n0_ppc=6.0 / 28.0, mass_ratio=50.0,
     # supply and pairs
     inject_mode=INJECT_NONE, inject_T=0.01,
+    # atmosphere (TOPUP): n/n0 = a0 exp(-(r - R*)/h) with h in cells, down to n_cut;
+    # a0 = 18 j_psi puts n/n_psi = 18 at the surface
+    atmo_a0=18.0 * 28.0, atmo_h=8.0, atmo_ncut=0.01,
     pairs_on=1, b_pair_threshold=0.09, pair_energy_threshold=2.0, n_max_ppc=0.0,
     seed=1, r_star_cm=1.0e6,
     # library only
