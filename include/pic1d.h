@@ -88,6 +88,22 @@ extern "C" {
  * E) and is zero outside it.  Not with drag law SURROGATE. */
 #define PIC1D_INJECT_TOPUP 2
 
+/* PIC1D_ANNIHILATION -- annihilation at n_max (Sec. 3: pairs are annihilated
+ * where the density reaches the skin-depth limit n_max; Sec. 5 on the
+ * annihilation zone).  With annihilate_every = K > 0 (and n_max_ppc > 0),
+ * at the end of every K-th step, right after a cell sort (a sort is added
+ * when K is not a multiple of sort_every): a cell whose lepton weight W
+ * (every lepton species, integer units of 2^-12) exceeds n_max loses the
+ * same weight A = min((W - n_max)/2, W+, W-) of positrons (W+) and of pair
+ * electrons (W-).  Inside each species weight is taken in increasing order
+ * of the key splitmix64(id ^ splitmix64(step ^ 0xA1111A7E)) (step counted
+ * after the step), the last particle touched keeping the rest of its
+ * weight; particles left with no weight are removed.  The removed charge is
+ * carried to the cell's left node first, which adds the current through the
+ * cell to E there, so the discrete Gauss law still holds exactly.  Atmospheric
+ * electrons count in W but are not annihilated.  diag.annihilated sums
+ * 2A over cells and passes. */
+
 /* species codes */
 #define PIC1D_SP_ELECTRON 0
 #define PIC1D_SP_POSITRON 1
@@ -132,6 +148,7 @@ typedef struct pic1d_params {
   double b_pair_threshold;  /* b above which scattering is discrete and may make pairs (0.09) */
   double pair_energy_threshold; /* photon energy for a pair, m_e c^2 (2.0) */
   double n_max_ppc;         /* no pair in a cell holding this lepton weight (<= 0: off) */
+  int32_t annihilate_every; /* > 0: annihilation at n_max every this many steps (PIC1D_ANNIHILATION) */
   uint64_t seed;            /* Philox key                               */
   double r_star_cm;         /* stellar radius, cm                       */
   /* library */
@@ -148,6 +165,7 @@ typedef struct pic1d_diag_t {
   int64_t lost_north, lost_south, injected, injected_dropped;
   int64_t scatters, psc_clamped, limiter_branch, newton_branch, nonfinite;
   int64_t rng_draws;        /* Philox draws (one 8-byte id read each) */
+  int64_t annihilated;      /* weight removed by annihilation, both species, units of 2^-12 */
   int64_t sur_rows;         /* network rows evaluated inside the push (drag law SURROGATE;
                                each row: 2 x 64 x 64 multiply-adds on the tensor cores) */
   int64_t sur_rows_tangent; /* of which with the forward-mode tangent (as many again) */

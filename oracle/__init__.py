@@ -58,7 +58,7 @@ class OrcParams(C.Structure):
         ("inject_mode", C.c_int32), ("inject_T", C.c_double),
         ("atmo_a0", C.c_double), ("atmo_h", C.c_double), ("atmo_ncut", C.c_double),
         ("pairs_on", C.c_int32), ("b_pair_threshold", C.c_double), ("pair_energy_threshold", C.c_double),
-        ("n_max_ppc", C.c_double),
+        ("n_max_ppc", C.c_double), ("annihilate_every", C.c_int32),
         ("seed", C.c_uint64), ("r_star_cm", C.c_double),
     ]
 
@@ -70,6 +70,7 @@ class OrcDiag(C.Structure):
         ("pairs_lost_wall", C.c_int64),
         ("lost_north", C.c_int64), ("lost_south", C.c_int64), ("injected", C.c_int64), ("scatters", C.c_int64),
         ("psc_clamped", C.c_int64), ("limiter_branch", C.c_int64), ("newton_branch", C.c_int64),
+        ("annihilated", C.c_int64),
         ("field_energy", C.c_double), ("kinetic_energy", C.c_double), ("ext_work", C.c_double),
         ("vc", C.c_double), ("charge", C.c_double), ("ke_lost", C.c_double),
     ]
@@ -94,6 +95,7 @@ def lib():
             "orc_child_id": (C.c_uint64, [C.c_uint64, C.c_int64, C.c_int]),
             "orc_inject_id": (C.c_uint64, [C.c_int64, C.c_int, C.c_int64, C.c_int]),
             "orc_atmo_id": (C.c_uint64, [C.c_int64, C.c_int, C.c_int64, C.c_int]),
+            "orc_annih_key": (C.c_uint64, [C.c_uint64, C.c_int64]),
             "orc_gauss_legendre": (None, [C.c_int, _D, _D]),
             "orc_theta0": (C.c_double, [C.c_double]),
             "orc_arc_length": (C.c_double, [C.c_double, C.c_double]),
@@ -179,6 +181,10 @@ def inject_id(step, foot, slot, member):
 
 def atmo_id(step, cell, slot, member):
     return int(lib().orc_atmo_id(int(step), int(cell), int(slot), int(member)))
+
+
+def annih_key(pid, step):
+    return int(lib().orc_annih_key(int(pid), int(step)))
 
 
 def gauss_legendre(n):

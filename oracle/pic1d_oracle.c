@@ -50,6 +50,17 @@
  *     T in both directions.  Gravity: the force -T/h along r, i.e.
  *     -T/h mu_s along s, on every particle, kept at cell centres of the
  *     atmosphere (zero elsewhere) and gathered like E; du = (q/m E + g/m) dt.
+ *   - annihilation at n_max (Sec. 3; Sec. 5 on the annihilation zone): every
+ *     annihilate_every steps, at the end of the step, a cell whose lepton
+ *     weight W (all leptons) exceeds n_max loses the same weight
+ *     A = min((W - n_max)/2, W+, W-) of positrons and of pair electrons
+ *     (integer fixed point).  Within each species, weight goes in increasing
+ *     order of the key splitmix64(id ^ splitmix64(step ^ salt)) (a bijection
+ *     of the id, so there are no ties); the last particle touched may keep
+ *     part of its weight.  The removed charge is first carried to the cell's
+ *     left node, which deposits the current (q delta (s - c)) through the
+ *     cell; then the removed positive and negative weight, equal and at one
+ *     point, vanish: the discrete Gauss law holds exactly.
  */
 #include <math.h>
 #include <stdint.h>
@@ -85,6 +96,7 @@ typedef struct {
   double cells_per_skin_depth; double j_psi; double n0_ppc; double mass_ratio;
   int32_t inject_mode; double inject_T; double atmo_a0; double atmo_h; double atmo_ncut;
   int32_t pairs_on; double b_pair_threshold; double pair_energy_threshold; double n_max_ppc;
+  int32_t annihilate_every;
   uint64_t seed; double r_star_cm;
 } orc_params;
 
@@ -599,6 +611,7 @@ typedef struct {
   int64_t n_alive[4];
   int64_t pairs_created, pairs_dropped_cap, pairs_rejected_nmax, pairs_lost_wall;
   int64_t lost_north, lost_south, injected, scatters, psc_clamped, limiter_branch, newton_branch;
+  int64_t annihilated;            /* weight removed by annihilation, units of 2^-12 */
   double field_energy, kinetic_energy, ext_work, vc, charge, ke_lost;
 } orc_diag;
 
@@ -1088,6 +1101,98 @@ static double orc_gather_at(const orc_sim* S, const double* a, double s)
 static double orc_gather(const orc_sim* S, double s) { return orc_gather_at(S, S->E, s); }
 
 /* ------------------------------------------------------------------------ */
+/* Annihilation at n_max (see the readings at the top).  Called at the end of */
+/* a step, after the step counter has advanced.                              */
+/* ------------------------------------------------------------------------ */
+/* order key of a particle in the annihilation at `step` */
+uint64_t orc_annih_key(uint64_t id, int64_t step)
+{
+  return orc_splitmix64(id ^ orc_splitmix64((uint64_t)step ^ 0xA1111A7Eull));
+}
+
+typedef struct { uint64_t key; int64_t k; } orc_keyed;
+
+static int orc_keyed_cmp(const void* a, const void* b)
+{
+  uint64_t x = ((const orc_keyed*)a)->key, y = ((const orc_keyed*)b)->key;
+  return (x > y) - (x < y);
+}
+
+static void orc_annihilate(orc_sim* S)
+{
+  const int N = S->N;
+  const int64_t nmax = (int64_t)floor(S->p.n_max_ppc * (double)(1 << ORC_S_BITS));
+  int64_t *W = calloc(N, sizeof(int64_t)), *Wp = calloc(N, sizeof(int64_t)), *We = calloc(N, sizeof(int64_t));
+  int64_t* cnt = calloc(N, sizeof(int64_t));
+  for (int64_t k = 0; k < S->n; ++k) {
+    int sp = S->sp[k];
+    if (!orc_is_lepton(sp)) continue;
+    int c = (int)floor(S->s[k]);
+    int64_t w = orc_wint(S->w[k]);
+    W[c] += w;
+    if (sp == ORC_SP_POSI) { Wp[c] += w; cnt[c]++; }
+    if (sp == ORC_SP_ELEC) { We[c] += w; cnt[c]++; }
+  }
+  /* the pair particles of every cell that annihilates, with their keys */
+  int64_t* first = malloc((N + 1) * sizeof(int64_t));
+  int64_t* A = calloc(N, sizeof(int64_t));
+  first[0] = 0;
+  for (int c = 0; c < N; ++c) {
+    if (W[c] > nmax) {
+      int64_t a = (W[c] - nmax) / 2;
+      if (a > Wp[c]) a = Wp[c];
+      if (a > We[c]) a = We[c];
+      A[c] = a;
+    }
+    first[c + 1] = first[c] + (A[c] > 0 ? cnt[c] : 0);
+  }
+  orc_keyed* list = malloc((first[N] > 0 ? first[N] : 1) * sizeof(orc_keyed));
+  int64_t* fill = calloc(N, sizeof(int64_t));
+  for (int64_t k = 0; k < S->n; ++k) {
+    int sp = S->sp[k];
+    if (sp != ORC_SP_POSI && sp != ORC_SP_ELEC) continue;
+    int c = (int)floor(S->s[k]);
+    if (A[c] <= 0) continue;
+    list[first[c] + fill[c]].key = orc_annih_key(S->id[k], S->step);
+    list[first[c] + fill[c]].k = k;
+    fill[c]++;
+  }
+  unsigned char* gone = calloc(S->n > 0 ? S->n : 1, 1);
+  for (int c = 0; c < N; ++c) {
+    if (A[c] <= 0) continue;
+    orc_keyed* L = list + first[c];
+    int64_t m = cnt[c];
+    qsort(L, (size_t)m, sizeof(orc_keyed), orc_keyed_cmp);
+    int64_t left[2] = { A[c], A[c] };   /* [0]: electrons, [1]: positrons */
+    double X = 0.0;                      /* sum of q delta (s - c), weight units */
+    for (int64_t i = 0; i < m; ++i) {
+      int64_t k = L[i].k;
+      int sp = S->sp[k];
+      int64_t* r = &left[sp == ORC_SP_POSI ? 1 : 0];
+      if (*r == 0) continue;
+      int64_t w = orc_wint(S->w[k]);
+      int64_t d = w < *r ? w : *r;
+      *r -= d;
+      X += ORC_QS[sp] * ((double)d / (double)(1 << ORC_S_BITS)) * (S->s[k] - (double)c);
+      S->w[k] = (double)(w - d) / (double)(1 << ORC_S_BITS);
+      if (w - d == 0) gone[k] = 1;
+    }
+    /* the current of the removed charge carried to node c, through cell c:
+     * E_c -= 4 pi dt J with J dt = -X q_p */
+    S->E[c] += 4.0 * ORC_PI * S->q_p * X;
+    S->d.annihilated += 2 * A[c];
+  }
+  int64_t n = 0;
+  for (int64_t k = 0; k < S->n; ++k) {
+    if (gone[k]) continue;
+    S->s[n] = S->s[k]; S->u[n] = S->u[k]; S->w[n] = S->w[k]; S->sp[n] = S->sp[k]; S->id[n] = S->id[k];
+    n++;
+  }
+  S->n = n;
+  free(W); free(Wp); free(We); free(cnt); free(first); free(A); free(list); free(fill); free(gone);
+}
+
+/* ------------------------------------------------------------------------ */
 /* One PIC cycle (Sec. 3), n -> n+1.  E at integer times, u at half times.    */
 /* ------------------------------------------------------------------------ */
 void orc_step(orc_sim* S)
@@ -1273,6 +1378,7 @@ void orc_step(orc_sim* S)
   }
   free(wcell);
   S->step++;
+  if (p->annihilate_every > 0 && p->n_max_ppc > 0.0 && S->step % p->annihilate_every == 0) orc_annihilate(S);
   orc_recount_density(S);
   free(cs); free(cu); free(cw); free(csp); free(cid); free(alive);
 }

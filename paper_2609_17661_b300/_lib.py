@@ -28,7 +28,7 @@ class Params(C.Structure):
         ("inject_mode", C.c_int32), ("inject_T", C.c_double),
         ("atmo_a0", C.c_double), ("atmo_h", C.c_double), ("atmo_ncut", C.c_double),
         ("pairs_on", C.c_int32), ("b_pair_threshold", C.c_double), ("pair_energy_threshold", C.c_double),
-        ("n_max_ppc", C.c_double),
+        ("n_max_ppc", C.c_double), ("annihilate_every", C.c_int32),
         ("seed", C.c_uint64), ("r_star_cm", C.c_double),
         ("capacity", C.c_int64), ("sort_every", C.c_int32), ("cuda_stream", C.c_void_p),
     ]
@@ -43,7 +43,7 @@ class Diag(C.Structure):
         ("injected_dropped", C.c_int64),
         ("scatters", C.c_int64), ("psc_clamped", C.c_int64), ("limiter_branch", C.c_int64),
         ("newton_branch", C.c_int64), ("nonfinite", C.c_int64),
-        ("rng_draws", C.c_int64), ("sur_rows", C.c_int64), ("sur_rows_tangent", C.c_int64), ("push_launches", C.c_int64), ("push_ms", C.c_double), ("push_slots", C.c_int64),
+        ("rng_draws", C.c_int64), ("annihilated", C.c_int64), ("sur_rows", C.c_int64), ("sur_rows_tangent", C.c_int64), ("push_launches", C.c_int64), ("push_ms", C.c_double), ("push_slots", C.c_int64),
         ("field_energy", C.c_double), ("kinetic_energy", C.c_double), ("ext_work", C.c_double),
         ("vc", C.c_double), ("ke_lost", C.c_double),
         ("q_p", C.c_double), ("j_ext", C.c_double), ("dt", C.c_double), ("tau_min", C.c_double),

@@ -1628,6 +1628,155 @@ __global__ void k_sort_done(DevParams P) {
   P.st->append = 0;
 }
 
+// --------------------------------------------------------------------------
+// annihilation at n_max, right after a sort.  The sort leaves each cell's
+// leptons in two contiguous slot ranges (u >= 0 and u < 0, each over the
+// cell's eight |u| bands); `offsets` holds the end of every bin, `counts` its
+// size.  k_annih_scan: one warp per cell sums the lepton, positron and
+// pair-electron weight and lists the cells above n_max with the weight A each
+// species loses.  k_annih_cell: one block per listed cell finds, per species,
+// the smallest key theta whose prefix weight (keys <= theta) reaches A by a
+// 64-step bisection over the key space, takes all weight below theta and the
+// rest of A from the particle at theta, and moves E at the cell by the current
+// of the removed charge carried to the cell's left node.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long annih_key(unsigned long long id, long long step) {
+  return mix64(id ^ mix64((unsigned long long)step ^ 0xA1111A7Eull));
+}
+
+__device__ __forceinline__ void lepton_ranges(const DevParams& P, const uint32_t* counts, const long long* offsets,
+                                              int c, long long (&a)[2], long long (&b)[2]) {
+  for (int g = 0; g < 2; ++g) {
+    const int k0 = (g * P.N + c) * 8;
+    a[g] = offsets[k0] - (long long)counts[k0];
+    b[g] = offsets[k0 + 7];
+  }
+}
+
+__global__ void k_annih_scan(DevParams P, const uint32_t* counts, const long long* offsets, int* list,
+                             long long* amount, unsigned* count) {
+  const int c = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (c >= P.N) return;                          // whole warps
+  long long a[2], b[2];
+  lepton_ranges(P, counts, offsets, c, a, b);
+  long long W = 0, Wp = 0, We = 0;
+  for (int g = 0; g < 2; ++g) {
+    for (long long i = a[g] + lane; i < b[g]; i += 32) {
+      const uint8_t sp = P.sp[i];
+      const long long w = __float2ll_rn(P.w[i] * 4096.0f);
+      W += w;
+      if (sp == PIC1D_SP_POSITRON) Wp += w;
+      if (sp == PIC1D_SP_ELECTRON) We += w;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    W += __shfl_down_sync(0xffffffffu, W, o);
+    Wp += __shfl_down_sync(0xffffffffu, Wp, o);
+    We += __shfl_down_sync(0xffffffffu, We, o);
+  }
+  if (lane == 0 && W > P.nmax_int) {
+    long long A = (W - P.nmax_int) / 2;
+    A = min(A, min(Wp, We));
+    if (A > 0) {
+      const unsigned k = atomicAdd(count, 1u);
+      list[k] = c;
+      amount[k] = A;
+    }
+  }
+}
+
+// block-wide sums of two int64 values (blockDim.x = kAnnThreads); every thread gets them
+constexpr int kAnnThreads = 256;
+__device__ __forceinline__ void block_sum2(long long& x, long long& y, long long (*sh)[kAnnThreads / 32]) {
+  for (int o = 16; o > 0; o >>= 1) {
+    x += __shfl_down_sync(0xffffffffu, x, o);
+    y += __shfl_down_sync(0xffffffffu, y, o);
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) { sh[0][w] = x; sh[1][w] = y; }
+  __syncthreads();
+  x = 0;
+  y = 0;
+  for (int k = 0; k < kAnnThreads / 32; ++k) { x += sh[0][k]; y += sh[1][k]; }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kAnnThreads) k_annih_cell(DevParams P, const uint32_t* counts,
+                                                            const long long* offsets, const int* list,
+                                                            const long long* amount, const unsigned* count,
+                                                            double* E64, float* E32, double cJ) {
+  __shared__ long long sh[2][kAnnThreads / 32];
+  const unsigned ncell = *count;
+  const uint32_t fmask = (1u << P.F) - 1u;
+  for (unsigned item = blockIdx.x; item < ncell; item += gridDim.x) {
+    const int c = list[item];
+    const long long A = amount[item];
+    long long a[2], b[2];
+    lepton_ranges(P, counts, offsets, c, a, b);
+    // bisection: theta[s] = the smallest key with sum_{key <= theta, species s} w >= A
+    unsigned long long lo[2] = {0ull, 0ull}, hi[2] = {~0ull, ~0ull};
+    for (int it = 0; it < 64; ++it) {
+      const unsigned long long mid0 = lo[0] + (hi[0] - lo[0]) / 2, mid1 = lo[1] + (hi[1] - lo[1]) / 2;
+      long long s0 = 0, s1 = 0;
+      for (int g = 0; g < 2; ++g)
+        for (long long i = a[g] + threadIdx.x; i < b[g]; i += kAnnThreads) {
+          const uint8_t sp = P.sp[i];
+          if (sp != PIC1D_SP_ELECTRON && sp != PIC1D_SP_POSITRON) continue;
+          const unsigned long long key = annih_key(P.id[i], P.step);
+          const long long w = __float2ll_rn(P.w[i] * 4096.0f);
+          if (sp == PIC1D_SP_ELECTRON) { if (key <= mid0) s0 += w; }
+          else if (key <= mid1) s1 += w;
+        }
+      block_sum2(s0, s1, sh);
+      if (s0 >= A) hi[0] = mid0; else lo[0] = mid0 + 1;
+      if (s1 >= A) hi[1] = mid1; else lo[1] = mid1 + 1;
+    }
+    const unsigned long long th0 = lo[0], th1 = lo[1];
+    // weight strictly below theta
+    long long B0 = 0, B1 = 0;
+    for (int g = 0; g < 2; ++g)
+      for (long long i = a[g] + threadIdx.x; i < b[g]; i += kAnnThreads) {
+        const uint8_t sp = P.sp[i];
+        if (sp != PIC1D_SP_ELECTRON && sp != PIC1D_SP_POSITRON) continue;
+        const unsigned long long key = annih_key(P.id[i], P.step);
+        const long long w = __float2ll_rn(P.w[i] * 4096.0f);
+        if (sp == PIC1D_SP_ELECTRON) { if (key < th0) B0 += w; }
+        else if (key < th1) B1 += w;
+      }
+    block_sum2(B0, B1, sh);
+    // remove the weight; X = sum q delta frac (fixed point) of the removed charge
+    long long X = 0, unused = 0;
+    for (int g = 0; g < 2; ++g)
+      for (long long i = a[g] + threadIdx.x; i < b[g]; i += kAnnThreads) {
+        const uint8_t sp = P.sp[i];
+        if (sp != PIC1D_SP_ELECTRON && sp != PIC1D_SP_POSITRON) continue;
+        const bool pos = sp == PIC1D_SP_POSITRON;
+        const unsigned long long key = annih_key(P.id[i], P.step);
+        const unsigned long long th = pos ? th1 : th0;
+        const long long w = __float2ll_rn(P.w[i] * 4096.0f);
+        long long d = 0;
+        if (key < th) d = w;
+        else if (key == th) d = A - (pos ? B1 : B0);
+        if (d > 0) {
+          const long long wn = w - d;
+          if (wn == 0) P.sp[i] = PIC1D_SP_DEAD;
+          else P.w[i] = (float)wn * (1.0f / 4096.0f);
+          X += (pos ? d : -d) * (long long)(P.pos[i] & fmask);
+        }
+      }
+    block_sum2(X, unused, sh);
+    if (threadIdx.x == 0) {
+      const double En = E64[c] + cJ * (double)X;
+      E64[c] = En;
+      E32[c] = (float)En;
+      if (P.use_nmax) P.dens_cur[c] -= 2 * A;
+      atomicAdd(&P.ctr->annihilated, (unsigned long long)(2 * A));
+    }
+    __syncthreads();
+  }
+}
+
 // device copy of the table with neighbouring s-rows paired (see table_eval)
 __global__ void k_pair_table(const float2* t, int Ng, int Ns, float4* out) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1874,6 +2023,17 @@ cudaError_t launch_sort(const DevParams& P, uint32_t* counts, long long* offsets
   k_scan_apply<<<nb, kScanThreads, 0, s>>>(counts, B, bsum, offsets);
   k_scatter<<<grid, 256, 0, s>>>(P, offsets, pos2, u2, w2, sp2, id2);
   k_sort_done<<<1, 1, 0, s>>>(P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_annihilate(const DevParams& P, const uint32_t* counts, const long long* offsets, int* list,
+                              long long* amount, unsigned* count, double* E64, float* E32, double cJ, int sms,
+                              cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  const long long threads = 32ll * P.N;
+  k_annih_scan<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(P, counts, offsets, list, amount, count);
+  k_annih_cell<<<2 * sms, kAnnThreads, 0, s>>>(P, counts, offsets, list, amount, count, E64, E32, cJ);
   return cudaGetLastError();
 }
 

@@ -150,6 +150,10 @@ struct pic1d_ctx {
   int* atmo_cells = nullptr;        // the atmosphere's cells
   long long* atmo_target = nullptr; // their target weights (w_int)
   int n_atmo = 0;
+  // annihilation at n_max (annihilate_every > 0)
+  int* ann_list = nullptr;          // cells that annihilate in a pass
+  long long* ann_amount = nullptr;  // weight each species loses there (w_int)
+  unsigned* ann_count = nullptr;
   float2* table = nullptr;
   float4* tpair = nullptr;
   Counters* ctr = nullptr;
@@ -345,6 +349,8 @@ int validate(const pic1d_params* p, std::string& why) {
       return bad("TOPUP needs atmo_a0, atmo_h, atmo_ncut > 0 and inject_T >= 0");
     if (p->drag_law == PIC1D_DRAG_SURROGATE) return bad("TOPUP is not available with drag law SURROGATE");
   }
+  if (p->annihilate_every < 0) return bad("annihilate_every must be >= 0");
+  if (p->annihilate_every > 0 && !(p->n_max_ppc > 0.0)) return bad("annihilation needs n_max_ppc > 0");
   if (p->sort_every < 1) return bad("sort_every must be >= 1");
   if (p->capacity < 0) return bad("capacity must be >= 0");
   if (!(p->r_star_cm > 0.0)) return bad("r_star_cm must be positive");
@@ -592,6 +598,11 @@ int pic1d_init(const pic1d_params* p, pic1d_ctx** out) {
     chain(dalloc(&c->offsets, sort_bins(N) + 1));
     chain(dalloc(&c->bsum, scan_blocks(N)));
     chain(dalloc(&c->spc, 4));
+    if (p->annihilate_every > 0) {
+      chain(dalloc(&c->ann_list, N));
+      chain(dalloc(&c->ann_amount, N));
+      chain(dalloc(&c->ann_count, 1));
+    }
     int dev = 0, sms = 0;
     chain(cudaGetDevice(&dev));
     chain(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -729,9 +740,16 @@ int pic1d_step(pic1d_ctx* c, int n_steps) {
       CK(launch_topup(P, c->atmo_cells, c->atmo_target, c->n_atmo, sig_e, sig_i, c->s), "top-up");
     CK(launch_field(P, c->E64, c->E32, a, cJ, dt_jext, c->field_partial, grid, c->s), "field");
     c->step += 1;
-    if (c->step % p.sort_every == 0) {
+    const bool ann = p.annihilate_every > 0 && c->step % p.annihilate_every == 0;
+    if (c->step % p.sort_every == 0 || ann) {
       int rc = do_sort(c);
       if (rc != PIC1D_OK) return rc;
+    }
+    if (ann) {
+      const DevParams Q = dev_params(c);     // the sorted buffer, the step just finished
+      CK(launch_annihilate(Q, c->counts, c->offsets, c->ann_list, c->ann_amount, c->ann_count, c->E64, c->E32, cJ,
+                           c->sms, c->s),
+         "annihilate");
     }
   }
   return PIC1D_OK;
@@ -779,6 +797,7 @@ int pic1d_diag(pic1d_ctx* c, pic1d_diag_t* out) {
   out->newton_branch = C.newton_branch;
   out->nonfinite = C.nonfinite;
   out->rng_draws = C.rng_draws;
+  out->annihilated = (int64_t)C.annihilated;
   out->sur_rows = C.sur_rows;
   out->sur_rows_tangent = C.sur_rows_tangent;
   {
@@ -1124,7 +1143,7 @@ int pic1d_train_surrogate(pic1d_ctx* c, const pic1d_train_cfg* cfg, pic1d_train_
 namespace {
 
 const char kCkptMagic[8] = {'P', 'I', 'C', '1', 'D', 'C', 'K', '1'};
-constexpr uint32_t kCkptVersion = 2;
+constexpr uint32_t kCkptVersion = 3;
 
 // The parameters as they must agree between a checkpoint and the context
 // that loads it, field by field (the struct's padding is not part of it; the
@@ -1138,7 +1157,8 @@ std::vector<uint64_t> ckpt_params(const pic1d_params& p) {
           d(p.eta_min), (uint64_t)p.rics_mode, (uint64_t)p.mc_on, d(p.cells_per_skin_depth), d(p.j_psi),
           d(p.n0_ppc), d(p.mass_ratio), (uint64_t)p.inject_mode, d(p.inject_T), d(p.atmo_a0), d(p.atmo_h),
           d(p.atmo_ncut), (uint64_t)p.pairs_on,
-          d(p.b_pair_threshold), d(p.pair_energy_threshold), d(p.n_max_ppc), p.seed, d(p.r_star_cm),
+          d(p.b_pair_threshold), d(p.pair_energy_threshold), d(p.n_max_ppc), (uint64_t)p.annihilate_every, p.seed,
+          d(p.r_star_cm),
           (uint64_t)p.sort_every};
 }
 
@@ -1455,9 +1475,9 @@ int pic1d_ens_init(const pic1d_params* params, int32_t n_lines, pic1d_ens** out)
   if (!params || n_lines < 1) return PIC1D_EINVAL;
   for (int l = 0; l < n_lines; ++l) {
     if (params[l].drag_law != PIC1D_DRAG_SURROGATE || params[l].inject_mode != PIC1D_INJECT_NONE ||
-        params[l].cuda_stream != params[0].cuda_stream) {
+        params[l].annihilate_every != 0 || params[l].cuda_stream != params[0].cuda_stream) {
       std::fprintf(stderr, "pic1d_ens_init: line %d: the ensemble runs drag law SURROGATE, no surface supply, "
-                           "and one stream for all lines\n", l);
+                           "no annihilation, and one stream for all lines\n", l);
       return PIC1D_EINVAL;
     }
   }
@@ -1746,7 +1766,8 @@ void pic1d_free(pic1d_ctx* c) {
                   c->ctr, c->st, c->ke_partial, c->field_partial, c->counts, c->offsets, c->spc, c->slot_log,
                   c->tpair, c->bsum, c->sur.master, c->sur.m, c->sur.v, c->sur.img, c->sur.small,
                   c->sur.part, c->sur.loss_part, c->sur.err, c->sur_gx, c->sur_gw, c->sur_grad, c->sur_loss, c->rho,
-                  c->G32, c->atmo_flag, c->atmo_w, c->atmo_cells, c->atmo_target};
+                  c->G32, c->atmo_flag, c->atmo_w, c->atmo_cells, c->atmo_target, c->ann_list, c->ann_amount,
+                  c->ann_count};
   for (void* q : ptrs) dfree(q);
   delete c;
   g_live.fetch_sub(1);

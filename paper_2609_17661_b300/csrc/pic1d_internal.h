@@ -27,6 +27,7 @@ struct Counters {
   unsigned long long rng_draws;
   unsigned long long sur_rows;   // rows evaluated by the surrogate network inside the push
   unsigned long long sur_rows_tangent;   // of which with the forward-mode tangent
+  unsigned long long annihilated;        // weight removed by annihilation (w_int units)
 };
 
 // Per-step device scalars.
@@ -103,6 +104,11 @@ int push_variant_ppt(int v);
 int push_variant_minb(int v);
 cudaError_t launch_inject(const DevParams& P, double carriers_per_step, float sig_e, float sig_i,
                           cudaStream_t s);
+// annihilation at n_max, right after a sort (offsets: the sort's bin ends, counts: its histogram);
+// list/amount/count: scratch of N cells, N cells, 1 counter; cJ: E change per unit of J_int
+cudaError_t launch_annihilate(const DevParams& P, const uint32_t* counts, const long long* offsets, int* list,
+                              long long* amount, unsigned* count, double* E64, float* E32, double cJ, int sms,
+                              cudaStream_t s);
 // atmosphere top-up (TOPUP): n_cells cells of the atmosphere with their target weights (w_int)
 cudaError_t launch_topup(const DevParams& P, const int* cells, const long long* target, int n_cells, float sig_e,
                          float sig_i, cudaStream_t s);

@@ -47,7 +47,7 @@ BASE = dict(
     # atmosphere (TOPUP): n/n0 = a0 exp(-(r - R*)/h) with h in cells, down to n_cut;
     # a0 = 18 j_psi puts n/n_psi = 18 at the surface
     atmo_a0=18.0 * 28.0, atmo_h=8.0, atmo_ncut=0.01,
-    pairs_on=1, b_pair_threshold=0.09, pair_energy_threshold=2.0, n_max_ppc=0.0,
+    pairs_on=1, b_pair_threshold=0.09, pair_energy_threshold=2.0, n_max_ppc=0.0, annihilate_every=0,
     seed=1, r_star_cm=1.0e6,
     # library only
     capacity=0, sort_every=20,
