@@ -490,6 +490,25 @@ int pic1d_ens_tune(pic1d_ens* e, int32_t trial_steps, int32_t* chunk_out, int32_
 /* The ensemble's CUDA stream (a cudaStream_t), for events and synchronisation. */
 void* pic1d_ens_stream(pic1d_ens* e);
 
+/* Per-step history of every line, kept on the device by the step's last
+ * kernel (recorded inside captured super-steps too, no host
+ * synchronisation): after each of the next `capacity` steps, the line's
+ * circuit potential V_c = -sum_c E_c dx (Sec. 3) and its cumulative count of
+ * created pairs.  A call re-arms the record (the previous one is dropped);
+ * capacity 0 stops recording.  Synchronises.  Errors: EINVAL, ENOMEM, ECUDA. */
+int pic1d_ens_record(pic1d_ens* e, int32_t capacity);
+
+/* Line `line`'s record: *n_out steps (<= capacity); vc[k] = V_c after the
+ * k-th recorded step, pairs[k] = pairs created since the record was armed,
+ * pair_rate[k] = pairs created per unit time (cell-crossing times) over the
+ * last `window` steps, over the k + 1 steps recorded while k + 1 < window --
+ * with window = n_cells / cfl steps, the rate averaged over a light-crossing
+ * time of the line that the paper reports.  Output arrays are caller-owned
+ * host memory of `capacity` entries, each may be NULL.  Synchronises.
+ * Errors: EINVAL (no such line, window < 1 with pair_rate), ECUDA. */
+int pic1d_ens_history(pic1d_ens* e, int32_t line, int32_t window, double* vc, int64_t* pairs, double* pair_rate,
+                      int32_t* n_out);
+
 const char* pic1d_ens_last_error(const pic1d_ens* e);
 void pic1d_ens_free(pic1d_ens* e);
 

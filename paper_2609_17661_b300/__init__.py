@@ -356,6 +356,29 @@ class Ensemble:
                                           C.c_void_p(b.ctypes.data), C.c_void_p(c.ctypes.data)))
         return a, b, c
 
+    def record(self, capacity):
+        """pic1d_ens_record: keep V_c and the pair count of every line after
+        each of the next `capacity` steps (on the device)."""
+        self._check(self.L.pic1d_ens_record(self.h, int(capacity)))
+        self._rec_cap = int(capacity)
+
+    def history(self, line, window=None):
+        """pic1d_ens_history: dict(vc, pairs, pair_rate) of one line's record;
+        window defaults to one light-crossing time of the line (n_cells / cfl
+        steps)."""
+        cap = getattr(self, "_rec_cap", 0)
+        if window is None:
+            cfg = self.cfgs[line] if 0 <= line < len(self.cfgs) else None
+            window = max(1, int(round(cfg["n_cells"] / cfg["cfl"]))) if cfg else 1
+        vc, rate = np.zeros(max(cap, 1)), np.zeros(max(cap, 1))
+        pairs = np.zeros(max(cap, 1), np.int64)
+        n = C.c_int32()
+        self._check(self.L.pic1d_ens_history(self.h, int(line), int(window), C.c_void_p(vc.ctypes.data),
+                                             C.c_void_p(pairs.ctypes.data), C.c_void_p(rate.ctypes.data),
+                                             C.byref(n)))
+        k = n.value
+        return dict(vc=vc[:k], pairs=pairs[:k], pair_rate=rate[:k], window=int(window))
+
     def close(self):
         if getattr(self, "h", None):
             for ln in self.lines:

@@ -1298,6 +1298,16 @@ __global__ void k_ens_finalize(EnsArgs A) {
   st->append = 0;
   st->step += 1;
   L.acc[0] = L.acc[1] = L.acc[2] = L.acc[3] = 0.0;
+  // the line's history (pic1d_ens_record)
+  const EnsRec* R = A.rec;
+  if (R && R->cap > 0) {
+    const int k = R->n[l];
+    if (k < R->cap) {
+      R->vc[(size_t)l * R->cap + k] = st->vc;
+      R->pairs[(size_t)l * R->cap + k] = (long long)L.P.ctr->pairs_created;
+      R->n[l] = k + 1;
+    }
+  }
 }
 
 // after a line's sort: its current buffer is the other one

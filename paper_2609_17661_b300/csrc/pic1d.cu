@@ -1316,6 +1316,10 @@ struct pic1d_ens {
   bool time_sorts = false;
   std::vector<double> sort_ms;
   std::vector<int> sort_count;
+  // per-step history (pic1d_ens_record)
+  EnsRec* drec = nullptr;           // descriptor read by the finalize kernel
+  EnsRec rec{};                     // host copy of it
+  std::vector<long long> rec_base;  // pairs_created of each line when the record was armed
 };
 
 namespace {
@@ -1403,6 +1407,7 @@ EnsArgs ens_args(pic1d_ens* e) {
   A.sur_img = e->lines[0]->sur.img;
   A.sur_small = e->lines[0]->sur.small;
   A.sur_err = e->lines[0]->sur.err;
+  A.rec = e->drec;
   return A;
 }
 
@@ -1519,6 +1524,8 @@ int pic1d_ens_init(const pic1d_params* params, int32_t n_lines, pic1d_ens** out)
   if (rc == PIC1D_OK) ce = raw_alloc(reinterpret_cast<void**>(&e->dlines), sizeof(EnsLine) * n_lines);
   if (rc == PIC1D_OK && ce == cudaSuccess) ce = raw_alloc(reinterpret_cast<void**>(&e->work), sizeof(unsigned long long));
   if (rc == PIC1D_OK && ce == cudaSuccess) ce = cudaMemsetAsync(e->work, 0, sizeof(unsigned long long), e->s);
+  if (rc == PIC1D_OK && ce == cudaSuccess) ce = raw_alloc(reinterpret_cast<void**>(&e->drec), sizeof(EnsRec));
+  if (rc == PIC1D_OK && ce == cudaSuccess) ce = cudaMemsetAsync(e->drec, 0, sizeof(EnsRec), e->s);
   if (rc == PIC1D_OK && ce != cudaSuccess) rc = PIC1D_ECUDA;
   if (rc == PIC1D_OK) rc = ens_build_items(e);
   if (rc != PIC1D_OK) {
@@ -1671,6 +1678,68 @@ const char* pic1d_ens_last_error(const pic1d_ens* e) {
   return e->err.c_str();
 }
 
+int pic1d_ens_record(pic1d_ens* e, int32_t capacity) {
+  if (!e) return PIC1D_EINVAL;
+  if (capacity < 0) return ens_fail(e, PIC1D_EINVAL, "record: capacity < 0");
+  ECK(cudaStreamSynchronize(e->s), "record");
+  dfree(e->rec.vc);
+  dfree(e->rec.pairs);
+  dfree(e->rec.n);
+  e->rec = EnsRec{};
+  if (capacity > 0) {
+    const size_t m = (size_t)e->n * (size_t)capacity;
+    ECK(raw_alloc(reinterpret_cast<void**>(&e->rec.vc), m * sizeof(double)), "record");
+    ECK(raw_alloc(reinterpret_cast<void**>(&e->rec.pairs), m * sizeof(long long)), "record");
+    ECK(raw_alloc(reinterpret_cast<void**>(&e->rec.n), (size_t)e->n * sizeof(int)), "record");
+    ECK(cudaMemsetAsync(e->rec.n, 0, (size_t)e->n * sizeof(int), e->s), "record");
+    e->rec.cap = capacity;
+  }
+  e->rec_base.assign(e->n, 0);
+  for (int l = 0; l < e->n; ++l) {
+    Counters C{};
+    ECK(cudaMemcpyAsync(&C, e->lines[l]->ctr, sizeof(C), cudaMemcpyDeviceToHost, e->s), "record");
+    ECK(cudaStreamSynchronize(e->s), "record");
+    e->rec_base[l] = (long long)C.pairs_created;
+  }
+  ECK(cudaMemcpyAsync(e->drec, &e->rec, sizeof(EnsRec), cudaMemcpyHostToDevice, e->s), "record");
+  ECK(cudaStreamSynchronize(e->s), "record");
+  return PIC1D_OK;
+}
+
+int pic1d_ens_history(pic1d_ens* e, int32_t line, int32_t window, double* vc, int64_t* pairs, double* pair_rate,
+                      int32_t* n_out) {
+  if (!e || !n_out) return PIC1D_EINVAL;
+  if (line < 0 || line >= e->n) return ens_fail(e, PIC1D_EINVAL, "history: no such line");
+  if (window < 1 && pair_rate) return ens_fail(e, PIC1D_EINVAL, "history: window < 1");
+  *n_out = 0;
+  if (e->rec.cap == 0) return PIC1D_OK;
+  int n = 0;
+  ECK(cudaStreamSynchronize(e->s), "history");
+  ECK(cudaMemcpy(&n, e->rec.n + line, sizeof(int), cudaMemcpyDeviceToHost), "history");
+  n = std::min(n, e->rec.cap);
+  std::vector<double> hv(n);
+  std::vector<long long> hp(n);
+  const size_t off = (size_t)line * (size_t)e->rec.cap;
+  if (n > 0) {
+    ECK(cudaMemcpy(hv.data(), e->rec.vc + off, n * sizeof(double), cudaMemcpyDeviceToHost), "history");
+    ECK(cudaMemcpy(hp.data(), e->rec.pairs + off, n * sizeof(long long), cudaMemcpyDeviceToHost), "history");
+  }
+  for (int k = 0; k < n; ++k) hp[k] -= e->rec_base[line];
+  if (vc) std::copy(hv.begin(), hv.end(), vc);
+  if (pairs) for (int k = 0; k < n; ++k) pairs[k] = hp[k];
+  if (pair_rate) {
+    // pairs created per unit time over the last `window` steps (fewer at the start)
+    const double dt = e->lines[line]->dt;
+    for (int k = 0; k < n; ++k) {
+      const int w = std::min(k + 1, (int)window);
+      const long long before = (k >= window) ? hp[k - window] : 0;
+      pair_rate[k] = (double)(hp[k] - before) / (w * dt);
+    }
+  }
+  *n_out = n;
+  return PIC1D_OK;
+}
+
 void pic1d_ens_free(pic1d_ens* e) {
   if (!e) return;
   if (e->s) cudaStreamSynchronize(e->s);
@@ -1679,6 +1748,10 @@ void pic1d_ens_free(pic1d_ens* e) {
   dfree(e->push_items);
   dfree(e->cell_items);
   dfree(e->work);
+  dfree(e->drec);
+  dfree(e->rec.vc);
+  dfree(e->rec.pairs);
+  dfree(e->rec.n);
   for (pic1d_ctx* c : e->lines) pic1d_free(c);
   if (e->s) cudaStreamDestroy(e->s);
   delete e;

@@ -190,6 +190,16 @@ struct EnsLine {
   int pad;
 };
 
+// per-step record of every line (pic1d_ens_record): V_c and the cumulative
+// pair count after each step, line l's step k at [l * cap + k]
+struct EnsRec {
+  double* vc;
+  long long* pairs;
+  int* n;                            // steps recorded per line
+  int cap;                           // steps per line the buffers hold (0: not recording)
+  int pad;
+};
+
 struct EnsArgs {
   EnsLine* lines;
   int n_lines;
@@ -201,6 +211,7 @@ struct EnsArgs {
   const uint8_t* sur_img;            // the shared network
   const float* sur_small;
   unsigned* sur_err;
+  EnsRec* rec;                       // the record's descriptor (device; cap 0 when off)
 };
 
 cudaError_t ens_launch_clear(const EnsArgs& A, cudaStream_t s);
