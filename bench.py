@@ -194,6 +194,21 @@ def workload_name(args):
             "C1": "dipole line r_eq=4, 1024 cells, 32/cell"}[args.workload]
 
 
+def reduce_over_ranks(elapsed, units, world, device):
+    """(max of `elapsed`, sum of `units`) over the ranks of the default
+    process group: the whole job's time is its slowest rank's, its work is
+    every rank's."""
+    if world <= 1:
+        return float(elapsed), float(units)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(elapsed)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(u[0])
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -243,13 +258,7 @@ def run_gpu(args):
     units = d1["push_slots"]
     draws = d1["rng_draws"] - d0["rng_draws"]
     created = (d1["pairs_created"] - d0["pairs_created"]) * 2 + (d1["injected"] - d0["injected"])
-    t = torch.tensor([ms, units], dtype=torch.float64, device="cuda")
-    if world > 1:
-        tm = t.clone()
-        dist.all_reduce(tm[0:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(tm[1:2], op=dist.ReduceOp.SUM)
-        t = tm
-    ms_max, units_all = float(t[0]), float(t[1])
+    ms_max, units_all = reduce_over_ranks(ms, units, world, "cuda")
     value = units_all / (ms_max * 1e-3)
 
     # roofline of the push kernel: algorithmic bytes per launch / mean launch time
@@ -285,17 +294,13 @@ def run_gpu(args):
         line.sort()
         for _ in range(args.steps):
             line.step(1)
-            dd = line.diag()
+            line.diag()
             line.fields()
         barrier()
         te = time.perf_counter() - t0
-        units_e = float(dd["step"]) * 0 + args.steps * n
-        tt = torch.tensor([te, units_e], dtype=torch.float64, device="cuda")
-        if world > 1:
-            dist.all_reduce(tt[0:1], op=dist.ReduceOp.MAX)
-            dist.all_reduce(tt[1:2], op=dist.ReduceOp.SUM)
+        te_max, units_e = reduce_over_ranks(te, args.steps * n, world, "cuda")
         h2d = 21 * n
-        e2e = {"value": float(tt[1]) / float(tt[0]), "unit": "particle-steps/s",
+        e2e = {"value": units_e / te_max, "unit": "particle-steps/s",
                "h2d_bytes_per_step": h2d / args.steps,
                "d2h_bytes_per_step": 8 * cfg["n_cells"] + 8 * cfg["n_cells"] + 256}
         del Eh
@@ -391,13 +396,27 @@ def run_ensemble(args):
     the run, schedule from the autotuner, timed over whole captured
     super-steps (80 steps each)."""
     import torch
+    import torch.distributed as dist
     from paper_2609_17661_b300 import Ensemble
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    if int(os.environ.get("RANK", "0")) != 0:
-        return
-    cfgs, counts = W.ensemble_configs()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # every rank runs an ensemble of its own (lines drawn with a rank-dependent
+    # seed): the lines are independent, so there is no data-path collective
+    cfgs, counts = W.ensemble_configs(seed=4 + 1000 * rank)
     t0 = time.perf_counter()
-    states = [W.load_pair_loaded(c, int(n), seed=100 + k) for k, (c, n) in enumerate(zip(cfgs, counts))]
+    states = [W.load_pair_loaded(c, int(n), seed=100 + k + 1000 * rank) for k, (c, n) in
+              enumerate(zip(cfgs, counts))]
     t_gen = time.perf_counter() - t0
     ens = Ensemble(cfgs)
     ens.lines[0].sur_set_params(W.sur_init_params(0))
@@ -414,33 +433,43 @@ def run_ensemble(args):
     slots0 = sum(ln.diag()["n_slots"] for ln in ens.lines)
     rows0 = sum(ln.diag()["sur_rows"] + ln.diag()["sur_rows_tangent"] for ln in ens.lines)
     steps = max(80, (args.steps // 80) * 80)
-    clk = Clocks(0)
+    clk = Clocks(local)
     clk.start()
     time.sleep(0.3)
-    torch.cuda.synchronize()
+    barrier()
     es = ens.stream()            # the ensemble launches on a stream of its own
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(es)
     ens.step(steps)
     e1.record(es)
-    torch.cuda.synchronize()
+    barrier()
     clocks = clk.stop()
     ms = e0.elapsed_time(e1)
     diags = [ln.diag() for ln in ens.lines]
     slots1 = sum(d["n_slots"] for d in diags)
     rows = sum(d["sur_rows"] + d["sur_rows_tangent"] for d in diags) - rows0
     units = 0.5 * (slots0 + slots1) * steps      # slots per step, averaged over the run
-    value = units / (ms * 1e-3)
+    ms_max, units_all = reduce_over_ranks(ms, units, world, "cuda")
+    _, rows_all = reduce_over_ranks(ms, rows, world, "cuda")
+    _, particles_all = reduce_over_ranks(ms, int(counts.sum()), world, "cuda")
+    if world > 1:
+        dist.destroy_process_group()
+    if rank != 0:
+        ens.close()
+        return
+    value = units_all / (ms_max * 1e-3)
     peak = _bf16_peak()
-    tflops = rows * SUR_TENSOR_FLOP_PER_ROW / (ms * 1e-3) / 1e12
-    out = {"metric": "particle-steps/s", "value": value, "unit": "particle-steps/s", "n_gpus": 1,
-           "steps": steps, "warmup": 80, "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
+    tflops = rows_all * SUR_TENSOR_FLOP_PER_ROW / (ms_max * 1e-3) / 1e12 / world
+    out = {"metric": "particle-steps/s", "value": value, "unit": "particle-steps/s", "n_gpus": world,
+           "steps": steps, "warmup": 80, "ms_per_step": ms_max / steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic",
            "config": {"workload": "ensemble of 256 dipole lines, r_eq log-uniform in [2, 30], 512-65536 cells "
                                   "affine in arc length, 1e4-1e7 macroparticles each, surrogate drag",
-                      "lines": len(cfgs), "particles": int(counts.sum()),
-                      "cells": int(sum(c["n_cells"] for c in cfgs)), "parallelism": "one GPU, all lines per launch",
+                      "lines": len(cfgs) * world, "particles": int(particles_all),
+                      "cells": int(sum(c["n_cells"] for c in cfgs)),
+                      "parallelism": "one ensemble of 256 lines per GPU, all lines per launch" if world > 1
+                      else "one GPU, all lines per launch",
                       "l2": "inputs far larger than the 126 MB L2"},
            "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak[0], "unit": "TFLOP/s",
                         "frac": tflops / peak[0], "peak_kind": peak[1], "kernel": "k_ens_push (network layers)",

@@ -14,20 +14,36 @@ from __future__ import annotations
 import itertools
 
 
-def eta_mass_sweep(base_cfg: dict, eta_mins, mass_ratios, steps: int, theta, states=None, window=None):
+def sweep_configs(base_cfg: dict, eta_mins, mass_ratios):
+    """[(eta_min, mass_ratio, config)] of the grid, one line each (seed
+    advanced per line)."""
+    out = []
+    for k, (eta, mr) in enumerate(itertools.product(eta_mins, mass_ratios)):
+        c = dict(base_cfg)
+        c.update(eta_min=float(eta), mass_ratio=float(mr), seed=int(base_cfg.get("seed", 1)) + k)
+        out.append((float(eta), float(mr), c))
+    return out
+
+
+def eta_mass_sweep(base_cfg: dict, eta_mins, mass_ratios, steps: int, theta, states=None, window=None,
+                   rank: int = 0, world: int = 1, weights=None):
     """Run one line per (eta_min, mass_ratio) of the grid from `base_cfg`
     (drag law SURROGATE, the network `theta` shared by all lines) for
     `steps` steps; `states` maps a line's config to its initial particle
-    state (default: an empty line).  Returns one dict per line with the
-    parameters and its record (vc, pairs, pair_rate, window)."""
+    state (default: an empty line).  In a job of `world` ranks, this rank
+    runs its share of the grid (``shard.shard_lines`` by `weights`, one per
+    grid point, equal by default).  Returns one dict per line run here with
+    the grid index, the parameters and its record (vc, pairs, pair_rate,
+    window)."""
     from . import Ensemble
+    from .shard import my_lines
 
-    grid = list(itertools.product(eta_mins, mass_ratios))
-    cfgs = []
-    for k, (eta, mr) in enumerate(grid):
-        c = dict(base_cfg)
-        c.update(eta_min=float(eta), mass_ratio=float(mr), seed=int(base_cfg.get("seed", 1)) + k)
-        cfgs.append(c)
+    grid = sweep_configs(base_cfg, eta_mins, mass_ratios)
+    mine = my_lines(weights if weights is not None else [1.0] * len(grid), rank, world)
+    if not mine:
+        return []
+    grid = [grid[k] for k in mine]
+    cfgs = [c for _, _, c in grid]
     ens = Ensemble(cfgs)
     try:
         ens.lines[0].sur_set_params(theta)
@@ -37,9 +53,9 @@ def eta_mass_sweep(base_cfg: dict, eta_mins, mass_ratios, steps: int, theta, sta
         ens.record(steps)
         ens.step(steps)
         out = []
-        for k, ((eta, mr), c) in enumerate(zip(grid, cfgs)):
+        for k, (g, (eta, mr, c)) in enumerate(zip(mine, grid)):
             h = ens.history(k, window)
-            out.append(dict(eta_min=float(eta), mass_ratio=float(mr), cfg=c, **h))
+            out.append(dict(index=g, eta_min=eta, mass_ratio=mr, cfg=c, **h))
         return out
     finally:
         ens.close()
