@@ -360,7 +360,7 @@ int pic1d_load(pic1d_ctx* c, const char* path);
  * N^_rad(mu_s) + 0.1 N^_rad(mu_e)) is the closed form for photons along one
  * direction [contdrag] taken along the radial and along the disk edge most
  * favourable to the resonance; -30 clamps the targets, and the network is
- * judged where ln N^ > -20 (below it a rate is negligible).  G is the
+ * scored where ln N^ > -20 (below it a rate is negligible).  G is the
  * context's table_log10g_max; the quadrature uses the context's photon
  * model, kT, quad_n_mu x quad_n_phi nodes, b_star and b_convention.
  *

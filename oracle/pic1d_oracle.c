@@ -407,9 +407,9 @@ void orc_build_table(const orc_params* p, double* table)
 /* largest 1 - beta mu_k), whose Wien factor dominates the rate near the     */
 /* star.  Two floors: rates below LE = -20 are negligible (less than one     */
 /* scattering per 1e12 particle-steps; the drag then moves u by less than    */
-/* FP32 rounding), and the surrogate is judged only above LE; the targets   */
+/* FP32 rounding), and the surrogate is scored only above LE; the targets   */
 /* are clamped at LT = -30, ten e-folds lower, so that the kink of the clamp */
-/* lies outside the judged region.  t1 is masked (weight 0) where ln N^ <=   */
+/* lies outside the scored region.  t1 is masked (weight 0) where ln N^ <=   */
 /* LT.                                                                       */
 /* Inputs, each in [-1, 1] over the training box:                            */
 /*   f0 = 2 log10(gamma)/G - 1, f1 = 2 s/L - 1,                              */

@@ -15,7 +15,7 @@ training samples in ``pic1d_oracle.c`` (``orc_sur_point``):
 
 from which the drag and rate follow as ``ln N^ = max(B, LT) + y1`` and
 ``F^ = gamma b N^ y0``.  LT = -30 clamps the targets; the surrogate is
-judged where ln N^ > LE = -20 (below it a rate is negligible).
+scored where ln N^ > LE = -20 (below it a rate is negligible).
 
 The tensor-core layers (W2, W3 and the activations h1, h2 that feed them)
 are BF16 on the GPU; layers 1 and 4 and the biases are FP32.
@@ -40,7 +40,7 @@ import numpy as np
 
 SIZES = ((64, 4), (64, 64), (64, 64), (2, 64))   # (out, in) per layer
 LT = -30.0          # clamp of the rate targets (ln N^)
-LE = -20.0          # floor of the judged region (ln N^)
+LE = -20.0          # floor of the scored region (ln N^)
 B_MID, B_HALF = -1.25, 2.75
 BASE_MIX = (0.9, 0.1)  # weights of N^_rad(mu_s) and N^_rad(mu_edge) in the baseline
 

@@ -20,7 +20,7 @@ namespace sur {
 constexpr int TM = 128;        // rows per tile = TMEM lanes = threads of a CTA
 constexpr int NT = 128;
 constexpr float LT = -30.0f;   // clamp of the rate targets (ln N^)
-constexpr float LE = -20.0f;   // floor of the judged region
+constexpr float LE = -20.0f;   // floor of the scored region
 constexpr double B_MID = -1.25, B_HALF = 2.75;
 constexpr uint32_t kTagSur = 0x53555247u;
 

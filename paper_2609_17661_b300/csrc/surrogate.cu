@@ -12,7 +12,7 @@
 // where B = ln(0.9 N^_rad(mu_s) + 0.1 N^_rad(mu_e)) is a closed-form
 // baseline (the single-direction form [contdrag] along the local radial and
 // along the disk edge most favourable to the resonance) and LT = -30 the
-// clamp of the targets; the network is judged where ln N^ > LE = -20, below
+// clamp of the targets; the network is scored where ln N^ > LE = -20, below
 // which a rate is negligible.  Inputs: f0 = 2 log10(gamma)/G - 1,
 // f1 = 2 s/L - 1, f2 = (log10 b + 1.25)/2.75, f3 = sign(u).
 // The tensor-core operands (W2, W3 and the activations h1, h2) are BF16;
@@ -556,7 +556,7 @@ __global__ void __launch_bounds__(NT, 1) k_sur_infer(InferArgs A) {
 // ------------------------------------------------------------- validation
 // errors of the network against quadrature, per record: drag error
 // |F_nn - F_q| / (|F_q| + F_abs) and |ln N_nn - ln N_q|; -1 where the rate is
-// below the judged floor LE
+// below the scoring floor LE
 __global__ void k_sur_val(const float* rec, const float* y, long long n, float* err2) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
