@@ -125,6 +125,10 @@ def cfg_for(args):
         cfg["n_cells"] = args.cells
     if args.workload == "C5":
         cfg["capacity"] = int(args.particles * 1.06) + (1 << 20)
+    if args.atmosphere:
+        cfg["inject_mode"] = W.INJECT_TOPUP
+    if args.annihilate_every:
+        cfg["annihilate_every"] = args.annihilate_every
     return cfg
 
 
@@ -188,10 +192,15 @@ def run_reference(args):
 
 def workload_name(args):
     cells = args.cells or 262144
-    return {"C5": f"pair-loaded dipole line r_eq=30, {cells} cells, {args.particles:.3g} macroparticles, "
+    name = {"C5": f"pair-loaded dipole line r_eq=30, {cells} cells, {args.particles:.3g} macroparticles, "
                   "table drag, pairs on (n_max cap), sort every 20",
             "C2": "dipole line r_eq=20, 65536 cells, 256/cell, surface injection",
             "C1": "dipole line r_eq=4, 1024 cells, 32/cell"}[args.workload]
+    if args.atmosphere:
+        name += ", atmosphere topped up with gravity"
+    if args.annihilate_every:
+        name += f", annihilation at n_max every {args.annihilate_every} steps"
+    return name
 
 
 def reduce_over_ranks(elapsed, units, world, device):
@@ -267,7 +276,8 @@ def run_gpu(args):
     peak, peak_kind = _peaks()
     achieved = push_bytes / (d1["push_ms"] * 1e-3) / 1e9
     traffic = None
-    if _push_sources_sha256() == PUSH_TRAFFIC["sources_sha256"]:
+    # the capture is of the push without the atmosphere (another instantiation)
+    if _push_sources_sha256() == PUSH_TRAFFIC["sources_sha256"] and not args.atmosphere:
         traffic = PUSH_TRAFFIC["bytes_per_slot"] * units / max(launches, 1)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "kernel": "k_push", "launches": launches,
@@ -531,11 +541,15 @@ def run_tp_map(args):
 
 def gpu_launches(steps, cfg, step0):
     """Kernels of this library launched in the timed region: per step push,
-    field, finalize (+ inject with surface supply); per sort hist, scan
-    reduce, scan top, scan apply, scatter, done."""
+    field, finalize (+ inject or top-up with surface supply); per sort hist,
+    scan reduce, scan top, scan apply, scatter, done; per annihilation pass
+    its scan and cell kernels (after a sort, added when off the cadence)."""
     per = 3 + (1 if cfg["inject_mode"] else 0)
-    sorts = sum(1 for s in range(step0 + 1, step0 + steps + 1) if s % cfg["sort_every"] == 0)
-    return per * steps + 6 * sorts
+    K = cfg.get("annihilate_every", 0)
+    steps_run = range(step0 + 1, step0 + steps + 1)
+    sorts = sum(1 for s in steps_run if s % cfg["sort_every"] == 0 or (K and s % K == 0))
+    passes = sum(1 for s in steps_run if K and s % K == 0)
+    return per * steps + 6 * sorts + 2 * passes
 
 
 def main():
@@ -556,6 +570,10 @@ def main():
     ap.add_argument("--sur-steps", type=int, default=3)
     ap.add_argument("--tp-lines", type=int, default=65536)
     ap.add_argument("--tp-tmax", type=float, default=200.0)
+    ap.add_argument("--atmosphere", action="store_true",
+                    help="the line's supply is the paper's atmosphere (inject mode TOPUP, gravity)")
+    ap.add_argument("--annihilate-every", type=int, default=0,
+                    help="annihilation at n_max every this many steps (0: off)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "b300":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -68,3 +68,35 @@ def test_no_cpu_fallback_without_device():
     from paper_2609_17661_b300 import Line, workloads as W
     with pytest.raises(RuntimeError):
         Line(W.config("C1"))
+
+
+def test_init_rejects_bad_parameters_before_any_device_work():
+    """pic1d_init and pic1d_ens_init check their parameters before touching a
+    device: each rule below returns PIC1D_EINVAL on a machine without one."""
+    import ctypes as C
+    from paper_2609_17661_b300 import _lib, make_params, workloads as W
+    L = _lib.load()
+    bad = [
+        dict(inject_mode=W.INJECT_TOPUP, drag_law=W.DRAG_SURROGATE),    # atmosphere without the surrogate
+        dict(inject_mode=W.INJECT_TOPUP, atmo_h=0.0),
+        dict(inject_mode=W.INJECT_TOPUP, atmo_a0=-1.0),
+        dict(inject_mode=W.INJECT_TOPUP, atmo_ncut=0.0),
+        dict(inject_mode=3),
+        dict(annihilate_every=1, n_max_ppc=0.0),                        # annihilation needs n_max
+        dict(annihilate_every=-1),
+        dict(sort_every=0),
+        dict(n_cells=0),
+    ]
+    for over in bad:
+        p = make_params(W.config("C1", **over))
+        h = C.c_void_p()
+        assert L.pic1d_init(C.byref(p), C.byref(h)) == _lib.EINVAL, over
+        assert not h.value
+    # the ensemble refuses lines with supply or annihilation
+    for over in (dict(annihilate_every=20, n_max_ppc=10.0), dict(inject_mode=W.INJECT_TOPUP),
+                 dict(drag_law=W.DRAG_TABLE)):
+        cfg = W.config("C1", drag_law=W.DRAG_SURROGATE)
+        cfg.update(over)
+        arr = (_lib.Params * 1)(make_params(cfg))
+        h = C.c_void_p()
+        assert L.pic1d_ens_init(arr, 1, C.byref(h)) == _lib.EINVAL, over
