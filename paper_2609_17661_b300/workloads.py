@@ -256,6 +256,54 @@ def fill_pair_loaded(cfg: dict, out: dict, start_cell: int, end_cell: int, count
     return offset + 2 * m
 
 
+def pair_loaded_torch(cfg: dict, total: int, seed: int = 0, device="cuda", ion_frac: float = 0.1) -> dict:
+    """The pair-loaded line of ``load_pair_loaded`` drawn with torch's
+    generator on `device` (the same per-cell counts and distributions, other
+    random numbers), for full-size tests without a host copy of the state.
+    Tensors: pos int32 (the u32 fixed-point bits), u, w float32, sp uint8,
+    id int64 (the u64 bits), cell-sorted."""
+    import torch
+
+    N = cfg["n_cells"]
+    F = fbits(N)
+    half = torch.from_numpy(pair_loaded_counts(N, total) // 2).to(device)
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    cells = torch.repeat_interleave(torch.arange(N, device=device, dtype=torch.int64), half)
+    m = cells.numel()
+
+    def rnd():
+        return torch.rand(m, generator=g, device=device, dtype=torch.float32)
+
+    def log_gamma(inner):
+        z = torch.randn(m, generator=g, device=device, dtype=torch.float32)
+        return torch.where(inner, 0.3 + 0.15 * z, 1.5 + 0.5 * z)
+
+    def sign():
+        return torch.where(rnd() < 0.5, -1.0, 1.0)
+
+    q = torch.clamp((rnd().to(torch.float64) * (1 << F)).to(torch.int64), max=(1 << F) - 1)
+    pos = cells * (1 << F) + q
+    pos = torch.where(pos >= (1 << 31), pos - (1 << 32), pos).to(torch.int32)   # u32 bits as int32
+    x = (cells.to(torch.float32) + 0.5) / N
+    inner = (x < 0.1) | (x > 0.9)
+    del cells, x
+    gam = torch.clamp(10.0 ** log_gamma(inner), min=1.0 + 1e-6)
+    u_e = torch.sqrt(gam * gam - 1.0) * sign()
+    partner_ion = rnd() < 2.0 * ion_frac
+    gam = torch.clamp(10.0 ** log_gamma(inner), min=1.0 + 1e-6)
+    u_p = torch.where(partner_ion, 0.01 * torch.randn(m, generator=g, device=device, dtype=torch.float32),
+                      torch.sqrt(gam * gam - 1.0) * sign())
+    del gam, inner
+    sp_p = torch.where(partner_ion, SP_ION, SP_POSI).to(torch.uint8)
+    out = dict(pos=torch.stack([pos, pos], 1).reshape(-1),
+               u=torch.stack([u_e, u_p], 1).reshape(-1),
+               sp=torch.stack([torch.full_like(sp_p, SP_ELEC), sp_p], 1).reshape(-1),
+               w=torch.ones(2 * m, device=device, dtype=torch.float32),
+               id=torch.arange(2 * m, device=device, dtype=torch.int64))
+    return out
+
+
 def load_pair_loaded(cfg: dict, total: int, seed=None, chunk_cells=8192, out=None) -> dict:
     """Whole pair-loaded line (cell-sorted), optionally into given arrays."""
     N = cfg["n_cells"]

@@ -1,0 +1,179 @@
+"""Parity at the benchmark's full size: the pair-loaded r_eq = 30 line with
+262,144 cells and 1e9 macroparticles (table drag, pairs with the n_max cap,
+sort every 20 steps), in the launch configuration the benchmark times.
+
+After three steps, one more step is checked
+* at every node: the device's integer node charge changes by exactly minus
+  the difference of the step's integer currents (discrete continuity, hence
+  the Gauss law with the FP64 field update);
+* in the particle count: alive after = alive before - lost + 2 x pairs;
+* on 4,000 sampled particles (half of them in the pair zones near the
+  footpoints), against the FP64 oracle stepping the same particles in the
+  same field: each momentum to 1e-5 of the larger of its magnitudes before
+  and after the step (at least 1e-3), each position to the fixed-point
+  quantum plus the displacement of that momentum error.
+  A sampled particle is left out only where a decision the FP32 path takes
+  may legitimately differ from the oracle's: its scattering draw within
+  1e-4 (relative) of p_sc, or the photon direction sign(mu - beta) within
+  1e-4, or a wall within one cell.  (At these parameters the drag limiter's
+  floor tau_min makes either drag branch change u by less than 1e-6, so its
+  branch needs no margin.)
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2609_17661_b300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-5
+TAG_RICS = 0x52494353          # counter word 3 of the scattering draw
+N_SAMPLE = 4000
+
+
+def full_size_cfg():
+    cfg = W.config("C5")
+    cfg["capacity"] = int(1e9 * 1.06) + (1 << 20)       # as the benchmark
+    return cfg
+
+
+def device_sample(line, n, idx):
+    """Slots `idx` of the first n slots, read through pic1d_get_particles
+    into device memory: dict of numpy arrays (pos as uint32, id as uint64)."""
+    dev = torch.device("cuda")
+    pos = torch.empty(n, dtype=torch.int32, device=dev)
+    u = torch.empty(n, dtype=torch.float32, device=dev)
+    sp = torch.empty(n, dtype=torch.uint8, device=dev)
+    pid = torch.empty(n, dtype=torch.int64, device=dev)
+    rc = line.L.pic1d_get_particles(line.h, n, C.c_void_p(pos.data_ptr()), C.c_void_p(u.data_ptr()), None,
+                                    C.c_void_p(sp.data_ptr()), C.c_void_p(pid.data_ptr()), 1)
+    assert rc == 0
+    t = torch.from_numpy(np.asarray(idx, np.int64)).to(dev)
+    out = dict(pos=pos[t].cpu().numpy().view(np.uint32), u=u[t].cpu().numpy(), sp=sp[t].cpu().numpy(),
+               id=pid[t].cpu().numpy().view(np.uint64))
+    del pos, u, sp, pid
+    torch.cuda.empty_cache()
+    return out
+
+
+def sample_slots(cfg, n, line=None, pos=None):
+    """N_SAMPLE slot indices: half uniform over the line, half among the
+    slots whose cell lies in a pair zone (the first and last 6 % of the
+    line hold them on this r_eq = 30 line: b > 0.09 out to r of about 6)."""
+    rng = np.random.default_rng(9)
+    N = cfg["n_cells"]
+    F = W.fbits(N)
+    if pos is None:                        # positions of every slot, on the device
+        dev = torch.device("cuda")
+        p = torch.empty(n, dtype=torch.int32, device=dev)
+        assert line.L.pic1d_get_particles(line.h, n, C.c_void_p(p.data_ptr()), None, None, None, None, 1) == 0
+        cell = (p.to(torch.int64) & 0xFFFFFFFF) >> F
+        near = torch.nonzero((cell < int(0.06 * N)) | (cell >= N - int(0.06 * N))).flatten().cpu().numpy()
+        del p, cell
+        torch.cuda.empty_cache()
+    else:
+        cell = pos.astype(np.int64) >> F
+        near = np.nonzero((cell < int(0.06 * N)) | (cell >= N - int(0.06 * N)))[0]
+    a = rng.choice(n, N_SAMPLE // 2, replace=False)
+    b = rng.choice(near, N_SAMPLE - N_SAMPLE // 2, replace=False)
+    return np.unique(np.concatenate([a, b]))
+
+
+def compare_sample_with_oracle(cfg, snap0, snap1, E0, step, S=None):
+    """One oracle step of the sampled particles (all of weight 1) in the
+    field E0 at `step`; returns (kept, checked) after asserting parity on the
+    particles whose decisions sit clear of FP32 reach."""
+    N = cfg["n_cells"]
+    F = W.fbits(N)
+    dt = cfg["cfl"]
+    if S is None:
+        S = O.Sim(cfg)
+    s0 = snap0["pos"].astype(np.float64) / float(1 << F)
+    n = s0.size
+    S.set_particles(s0, snap0["u"].astype(np.float64), np.ones(n), snap0["sp"].astype(np.int32),
+                    snap0["id"].astype(np.uint64))
+    S.set_field(E0)
+    S.set_step(step)
+    zone = S.nodes()["zone"]
+    key = [cfg["seed"] & 0xFFFFFFFF, cfg["seed"] >> 32]
+    keep = np.ones(n, bool)
+    keep &= (s0 >= 1.0) & (s0 <= N - 1.0)
+    for k in range(n):
+        sp = int(snap0["sp"][k])
+        if sp == W.SP_ION or not zone[min(int(s0[k]), N - 1)]:
+            continue
+        # pair zone: no continuous drag, the kick, then the scattering draw
+        qm = 1.0 if sp == W.SP_POSI else -1.0
+        uk = float(snap0["u"][k]) + qm * S.gather(s0[k]) * dt
+        _, _, rate = S.drag(uk, s0[k])
+        psc = min(1.0, rate * dt)
+        if psc <= 0.0:
+            continue
+        pid = int(snap0["id"][k])
+        r = O.philox4x32_10([pid & 0xFFFFFFFF, pid >> 32, step & 0xFFFFFFFF, TAG_RICS], key)
+        U = float(int(r[0]) >> 8) * 2.0 ** -24
+        if abs(U - psc) <= 1e-4 * psc:
+            keep[k] = False
+        mu = S.node_interp(2, s0[k])
+        if abs(mu - uk / np.sqrt(1.0 + uk * uk)) <= 1e-4:
+            keep[k] = False
+    S.step(1)
+    o = S.particles()
+    oid = {int(i): j for j, i in enumerate(o["id"])}
+    assert snap1["id"].tolist() == snap0["id"].tolist()
+    du, dpos = [], []
+    for k in np.nonzero(keep)[0]:
+        pid = int(snap0["id"][k])
+        dead = snap1["sp"][k] == 255
+        assert dead == (pid not in oid), pid                # left the line on both sides or on neither
+        if dead:
+            continue
+        j = oid[pid]
+        assert int(snap1["sp"][k]) == int(o["sp"][j])
+        scale = max(abs(float(snap0["u"][k])), abs(o["u"][j]), 1e-3)
+        du.append(abs(float(snap1["u"][k]) - o["u"][j]) / scale)
+        dpos.append(abs(float(snap1["pos"][k]) / float(1 << F) - o["s"][j]))
+    assert max(du) <= RTOL, max(du)
+    assert max(dpos) <= 2.0 ** -F + dt * RTOL
+    return int(keep.sum()), len(du)
+
+
+def test_full_size_line_one_step():
+    from paper_2609_17661_b300 import Line
+    cfg = full_size_cfg()
+    N = cfg["n_cells"]
+    st = W.pair_loaded_torch(cfg, 1_000_000_000, seed=5)
+    line = Line(cfg)
+    line.set_state(st)
+    del st
+    torch.cuda.empty_cache()
+    line.sort()                                  # as the benchmark
+    line.step(3)
+    d0 = line.diag()
+    E0, _ = line.fields()
+    r0 = line.rho()
+    n0 = line.slots()
+    assert n0 > 9.9e8
+    idx = sample_slots(cfg, n0, line)
+    snap0 = device_sample(line, n0, idx)
+    line.step(1)                                 # step 4: not a sort step, slots keep their places
+    d1 = line.diag()
+    _, J = line.fields()
+    r1 = line.rho()
+    snap1 = device_sample(line, line.slots(), idx)
+    line.close()
+    # every node: integer continuity
+    np.testing.assert_array_equal((r1 - r0)[1:N], -(J[1:N] - J[0:N - 1]))
+    # the particle count
+    lost = (d1["lost_north"] - d0["lost_north"]) + (d1["lost_south"] - d0["lost_south"])
+    created = d1["pairs_created"] - d0["pairs_created"]
+    assert d1["nonfinite"] == 0
+    assert sum(d1["n_alive"]) == sum(d0["n_alive"]) - lost + 2 * created
+    assert d1["scatters"] > d0["scatters"] and d1["limiter_branch"] > d0["limiter_branch"]
+    # sampled particles against the oracle
+    kept, checked = compare_sample_with_oracle(cfg, snap0, snap1, E0, int(d0["step"]))
+    assert kept >= 0.95 * len(idx) and checked >= 0.9 * len(idx)
