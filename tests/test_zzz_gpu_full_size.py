@@ -14,10 +14,10 @@ After three steps, one more step is checked
   quantum plus the displacement of that momentum error.
   A sampled particle is left out only where a decision the FP32 path takes
   may legitimately differ from the oracle's: its scattering draw within
-  1e-4 (relative) of p_sc, or the photon direction sign(mu - beta) within
-  1e-4, or a wall within one cell.  (At these parameters the drag limiter's
-  floor tau_min makes either drag branch change u by less than 1e-6, so its
-  branch needs no margin.)
+  1e-4 (relative) of p_sc, the photon direction sign(mu - beta) within 1e-4,
+  the drag limiter's test |F| tau_min < |u| within 1e-4 (relative) in either
+  half step (the two branches differ by up to (dt/2)/tau_min (2|u| + |u~|),
+  about 1e-5 of u near the footpoints), or a wall within one cell.
 """
 import ctypes as C
 
@@ -99,15 +99,28 @@ def compare_sample_with_oracle(cfg, snap0, snap1, E0, step, S=None):
     S.set_field(E0)
     S.set_step(step)
     zone = S.nodes()["zone"]
+    tau = S.scalars()["tau_min"]
     key = [cfg["seed"] & 0xFFFFFFFF, cfg["seed"] >> 32]
     keep = np.ones(n, bool)
     keep &= (s0 >= 1.0) & (s0 <= N - 1.0)
+
+    def near_limiter(u):
+        F, _, _ = S.drag(u, s0[k])
+        return abs(abs(F) * tau - abs(u)) <= 1e-4 * max(abs(u), 1e-30)
+
     for k in range(n):
         sp = int(snap0["sp"][k])
-        if sp == W.SP_ION or not zone[min(int(s0[k]), N - 1)]:
+        if sp == W.SP_ION:
+            continue
+        qm = 1.0 if sp == W.SP_POSI else -1.0
+        if not zone[min(int(s0[k]), N - 1)]:
+            # continuous drag: the limiter test at the start of each half step
+            ua = float(snap0["u"][k])
+            ub = S.drag_half(ua, s0[k]) + qm * S.gather(s0[k]) * dt
+            if tau > 0.0 and (near_limiter(ua) or near_limiter(ub)):
+                keep[k] = False
             continue
         # pair zone: no continuous drag, the kick, then the scattering draw
-        qm = 1.0 if sp == W.SP_POSI else -1.0
         uk = float(snap0["u"][k]) + qm * S.gather(s0[k]) * dt
         _, _, rate = S.drag(uk, s0[k])
         psc = min(1.0, rate * dt)
