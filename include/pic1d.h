@@ -201,10 +201,13 @@ int pic1d_init(const pic1d_params* p, pic1d_ctx** out);
 int pic1d_set_state(pic1d_ctx* c, int64_t n, const uint32_t* pos, const float* u, const float* w,
                     const uint8_t* sp, const uint64_t* id, const double* E, int64_t step, int mem);
 
-/* Advance n_steps PIC cycles (Sec. 3) on the context's stream, sorting the
- * particles by cell every sort_every steps.  Asynchronous: returns after
- * issuing the work (errors of the step show up in pic1d_diag).
- * Errors: EINVAL (n_steps < 0), ECUDA. */
+/* Advance n_steps PIC cycles (Sec. 3) on the context's stream.  One cycle:
+ * the push (gather, drag, kick, scattering and pairs, move, deposit), the
+ * surface supply (RATE injection or the TOPUP atmosphere), the field update;
+ * then a cell sort every sort_every steps and, with annihilate_every > 0,
+ * the annihilation pass every annihilate_every steps (after a sort).
+ * Asynchronous: returns after issuing the work (errors of the step show up
+ * in pic1d_diag).  Errors: EINVAL (n_steps < 0), ECUDA. */
 int pic1d_step(pic1d_ctx* c, int n_steps);
 
 /* Synchronise and fill `out` (host).  Returns PIC1D_ENUMERIC if a step met
