@@ -190,3 +190,57 @@ def test_full_size_line_one_step():
     # sampled particles against the oracle
     kept, checked = compare_sample_with_oracle(cfg, snap0, snap1, E0, int(d0["step"]))
     assert kept >= 0.95 * len(idx) and checked >= 0.9 * len(idx)
+
+
+def compare_all_with_oracle(cfg, st, E, step, g, dg, Eg, S=None):
+    """One oracle step of the whole state `st` in the field E at `step`,
+    against the device's particles `g` (every slot, sorted by id), its diag
+    `dg` and its field `Eg`: counts exact, momenta and E to 1e-5 of their
+    largest value, positions to the fixed-point quantum plus the
+    displacement of that momentum error."""
+    N = cfg["n_cells"]
+    F = W.fbits(N)
+    if S is None:
+        S = O.Sim(cfg)
+    o = W.to_oracle(st, N)
+    S.set_particles(o["s"], o["u"], o["w"], o["sp"], o["id"])
+    S.set_field(E)
+    S.set_step(step)
+    S.step(1)
+    do = S.diag()
+    for k in ("n_alive", "injected", "lost_north", "lost_south", "pairs_created"):
+        assert dg[k] == do[k], (k, dg[k], do[k])
+    p = S.particles()
+    order = np.argsort(p["id"])
+    p = {k: v[order] for k, v in p.items()}
+    assert np.array_equal(g["id"], p["id"])
+    assert np.array_equal(g["sp"].astype(np.int32), p["sp"])
+    assert np.max(np.abs(g["u"].astype(np.float64) - p["u"])) <= RTOL * np.max(np.abs(p["u"]))
+    s = g["pos"].astype(np.float64) / float(1 << F)
+    assert np.max(np.abs(s - p["s"])) <= 2.0 ** -F + cfg["cfl"] * RTOL
+    Eo, _ = S.fields()
+    assert np.max(np.abs(Eg - Eo)) <= RTOL * np.max(np.abs(Eo))
+
+
+def test_c2_line_one_step_every_particle():
+    """The r_eq = 20 line with 65,536 cells and 256 particles per cell
+    (1.68e7, the C1 recipe at eight times the density), surface supply at
+    the rate that carries j0, table drag: one step from the same state on the
+    device and in the oracle, every particle compared."""
+    from paper_2609_17661_b300 import Line
+    cfg = W.config("C2", capacity=40_000_000)
+    N = cfg["n_cells"]
+    st = W.load_drifting_plasma(cfg, ppc_e=128, ppc_p=64, ppc_i=64)
+    x = (np.arange(N) + 0.5) / N
+    E = 0.02 * np.sin(2 * np.pi * 5 * x) + 0.005 * np.cos(2 * np.pi * 17 * x + 0.3)
+    line = Line(cfg)
+    line.set_state(st, E=E, step=7)
+    line.step(1)
+    g = line.particles()
+    order = np.argsort(g["id"])
+    g = {k: v[order] for k, v in g.items()}
+    dg = line.diag()
+    Eg, _ = line.fields()
+    line.close()
+    assert g["id"].size > 1.6e7 and dg["injected"] > 0
+    compare_all_with_oracle(cfg, st, E, 7, g, dg, Eg)
