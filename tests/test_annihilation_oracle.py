@@ -192,3 +192,23 @@ def test_gauss_law_every_step_with_annihilation():
         g = (E[1:] - E[:-1]) - 4 * np.pi * r[1:N]
         assert np.max(np.abs(g - g0)) <= 1e-12 * max(1.0, np.max(np.abs(E)))
     assert S.diag()["annihilated"] > 0
+
+
+def test_gauss_law_with_the_atmosphere_and_annihilation_together():
+    """Top-up pairs appear neutral at one point and annihilation carries its
+    removed charge to a node first: with both on (and gravity, drag,
+    scattering, pairs), the discrete Gauss residual stays constant."""
+    cfg = _cfg(drag_law=O.DRAG_CLOSED, mc_on=1, pairs_on=1, drag_scale=1e-3, annihilate_every=3, n_max_ppc=60.0,
+               inject_mode=O.INJECT_TOPUP, atmo_a0=2000.0, atmo_h=4.0)
+    st = _dense_pairs(cfg, seed=8)
+    S = _sim(cfg, st, 0)
+    N = cfg["n_cells"]
+    E, _ = S.fields()
+    g0 = (E[1:] - E[:-1]) - 4 * np.pi * S.rho()[1:N]
+    for _ in range(9):
+        S.step(1)
+        E, _ = S.fields()
+        g = (E[1:] - E[:-1]) - 4 * np.pi * S.rho()[1:N]
+        assert np.max(np.abs(g - g0)) <= 1e-12 * max(1.0, np.max(np.abs(E)))
+    d = S.diag()
+    assert d["annihilated"] > 0 and d["injected"] > 0
