@@ -1682,6 +1682,11 @@ int pic1d_ens_record(pic1d_ens* e, int32_t capacity) {
   if (!e) return PIC1D_EINVAL;
   if (capacity < 0) return ens_fail(e, PIC1D_EINVAL, "record: capacity < 0");
   ECK(cudaStreamSynchronize(e->s), "record");
+  // the finalize kernel stops recording before the old buffers go (a failed
+  // allocation below then leaves the record off, not pointing at freed memory)
+  const EnsRec off{};
+  ECK(cudaMemcpyAsync(e->drec, &off, sizeof(EnsRec), cudaMemcpyHostToDevice, e->s), "record");
+  ECK(cudaStreamSynchronize(e->s), "record");
   dfree(e->rec.vc);
   dfree(e->rec.pairs);
   dfree(e->rec.n);
