@@ -212,3 +212,17 @@ def test_gauss_law_with_the_atmosphere_and_annihilation_together():
         assert np.max(np.abs(g - g0)) <= 1e-12 * max(1.0, np.max(np.abs(E)))
     d = S.diag()
     assert d["annihilated"] > 0 and d["injected"] > 0
+
+
+def test_a_cell_with_one_species_does_not_annihilate():
+    """Degenerate cell: far above n_max but holding positrons only (no pair
+    electrons), so A = min(..., W+, W-) = 0 and nothing is removed."""
+    cfg = _cfg(n_max_ppc=5.0)
+    rng = np.random.default_rng(2)
+    n = 200
+    st = dict(s=60 + rng.random(n), u=np.zeros(n), w=np.ones(n), sp=np.full(n, W.SP_POSI, np.int32),
+              id=np.arange(n, dtype=np.uint64))
+    S = _sim(cfg, st, 0)
+    S.step(1)
+    assert S.diag()["annihilated"] == 0
+    assert S.particles()["s"].size == n

@@ -170,3 +170,16 @@ def test_injected_momenta_are_maxwellian_at_T(c1):
         assert stats.kstest(u / math.sqrt(var), "norm").pvalue > 1e-4
     frac = p["s"] - np.floor(p["s"])
     assert stats.kstest(frac, "uniform").pvalue > 1e-4
+
+
+def test_no_atmosphere_when_the_cut_is_above_the_surface_density():
+    """Degenerate profile: atmo_ncut above atmo_a0 leaves no atmosphere
+    cell, so nothing is topped up and there is no gravity anywhere."""
+    cfg = _cfg(atmo_ncut=2.0 * 18.0 * 28.0, j_psi=0.0, cells_per_skin_depth=1e9)
+    S = O.Sim(cfg)
+    N = cfg["n_cells"]
+    s0 = np.array([0.5, 3.5, N - 3.5])
+    S.set_particles(s0, np.zeros(3), np.ones(3), np.full(3, W.SP_ION, np.int32), np.arange(3, dtype=np.uint64))
+    S.step(2)
+    assert S.diag()["injected"] == 0
+    assert np.all(S.particles()["u"] == 0.0)
