@@ -74,7 +74,7 @@ def test_single_rank_is_the_identity():
         shard_lines([1.0], 0)
 
 
-def test_reference_arm_under_torchrun_prints_one_line():
+def test_reference_arm_under_torchrun_prints_one_line(tmp_path):
     """`bench.py --impl reference` launched as two ranks: rank 0 alone times
     the oracle and prints one JSON line, the other rank exits 0 without work."""
     import json
@@ -83,7 +83,8 @@ def test_reference_arm_under_torchrun_prints_one_line():
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
            "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.join(ROOT, "bench.py"),
            "--impl", "reference", "--gpus", "2", "--steps", "2", "--warmup", "3", "--ref-sample", "20000"]
-    r = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=ROOT)
+    env = dict(os.environ, TMPDIR=str(tmp_path))          # torchrun's scratch stays in the test's directory
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=ROOT, env=env)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
     assert len(lines) == 1, r.stdout[-2000:]
