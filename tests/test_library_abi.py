@@ -100,3 +100,32 @@ def test_init_rejects_bad_parameters_before_any_device_work():
         arr = (_lib.Params * 1)(make_params(cfg))
         h = C.c_void_p()
         assert L.pic1d_ens_init(arr, 1, C.byref(h)) == _lib.EINVAL, over
+
+
+def test_header_is_plain_c99_and_links(tmp_path):
+    """include/pic1d.h compiles as strict C99 (no C++ or torch types at the
+    boundary) and a C program links against the library and calls it."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    from paper_2609_17661_b300 import _lib
+    _lib.load()
+    libdir = os.path.join(ROOT, "paper_2609_17661_b300")
+    src = tmp_path / "use_abi.c"
+    src.write_text(
+        '#include "pic1d.h"\n'
+        "int main(void) {\n"
+        "  pic1d_params p = {0};\n"
+        "  pic1d_ctx* c = 0;\n"
+        "  pic1d_diag_t d;\n"
+        "  (void)d;\n"
+        "  return pic1d_init(&p, &c) == PIC1D_EINVAL && c == 0 ? 0 : 1;\n"
+        "}\n")
+    exe = tmp_path / "use_abi"
+    cc = subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I",
+                         os.path.join(ROOT, "include"), str(src), "-L", libdir, "-lpic1d",
+                         f"-Wl,-rpath,{libdir}", "-o", str(exe)], capture_output=True, text=True)
+    assert cc.returncode == 0, cc.stderr
+    run = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert run.returncode == 0, run.stderr
