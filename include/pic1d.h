@@ -515,6 +515,18 @@ int pic1d_ens_history(pic1d_ens* e, int32_t line, int32_t window, double* vc, in
 const char* pic1d_ens_last_error(const pic1d_ens* e);
 void pic1d_ens_free(pic1d_ens* e);
 
+/* The library's random numbers on caller-given counters: Philox4x32-10
+ * (Salmon, Moraes, Dror, Shaw, SC'11; ten rounds) with key (key & 0xffffffff,
+ * key >> 32), so that a caller can reproduce any draw of a step.  The push
+ * draws the scattering of a lepton with counter (id_lo, id_hi, step,
+ * 0x52494353) and key = seed; the RATE supply with (slot, footpoint, step,
+ * 0x494E4A31) and the atmosphere with (slot, cell, step, 0x41544D4F).
+ * ctr: n counters of four u32 words; out: n outputs of four u32 words.
+ * mem 0: host arrays; 1: device arrays, 16-byte aligned.  Needs no context;
+ * runs on the default stream and synchronises.
+ * Errors: EINVAL (n < 0, NULL arrays, misaligned device arrays), ENOMEM, ECUDA. */
+int pic1d_philox(const uint32_t* ctr, int64_t n, uint64_t key, uint32_t* out, int mem);
+
 /* Device memory.  Contexts and ensembles take all their device memory from
  * one process-wide allocator: cudaMalloc / cudaFree by default, or the
  * caller's pair of hooks (for instance a framework's caching allocator, so

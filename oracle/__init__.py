@@ -91,6 +91,7 @@ def lib():
         L = C.CDLL(build())
         sig = {
             "orc_philox4x32_10": (None, [_U32, _U32, _U32]),
+            "orc_philox4x32_10_n": (None, [_U32, C.c_int64, _U32, _U32]),
             "orc_splitmix64": (C.c_uint64, [C.c_uint64]),
             "orc_child_id": (C.c_uint64, [C.c_uint64, C.c_int64, C.c_int]),
             "orc_inject_id": (C.c_uint64, [C.c_int64, C.c_int, C.c_int64, C.c_int]),
@@ -164,6 +165,15 @@ def philox4x32_10(ctr, key):
     k = np.ascontiguousarray(key, dtype=np.uint32)
     out = np.zeros(4, np.uint32)
     lib().orc_philox4x32_10(_ptr(c, _U32), _ptr(k, _U32), _ptr(out, _U32))
+    return out
+
+
+def philox4x32_10_n(ctr, key):
+    """The generator on an (n, 4) array of counters."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros_like(c)
+    lib().orc_philox4x32_10_n(_ptr(c, _U32), c.shape[0], _ptr(k, _U32), _ptr(out, _U32))
     return out
 
 

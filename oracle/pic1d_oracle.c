@@ -129,6 +129,12 @@ static double orc_u24(uint32_t x) { return (double)(x >> 8) * (1.0 / 16777216.0)
 
 /* SplitMix64 finaliser (Steele, Lea, Flood 2014) -- used only to derive
  * stable identifiers for created particles. */
+/* the generator on n counters (4 words each): out[4i..] = Philox4x32-10(ctr[4i..], key) */
+void orc_philox4x32_10_n(const uint32_t* ctr, int64_t n, const uint32_t key_in[2], uint32_t* out)
+{
+  for (int64_t i = 0; i < n; ++i) orc_philox4x32_10(ctr + 4 * i, key_in, out + 4 * i);
+}
+
 uint64_t orc_splitmix64(uint64_t z)
 {
   z += 0x9E3779B97F4A7C15ull;

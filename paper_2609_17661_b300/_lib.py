@@ -116,6 +116,7 @@ SIGNATURES = {
     "pic1d_ens_tune": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "pic1d_ens_stream": (C.c_void_p, [C.c_void_p]),
     "pic1d_ens_record": (C.c_int, [C.c_void_p, C.c_int32]),
+    "pic1d_philox": (C.c_int, [C.c_void_p, C.c_int64, C.c_uint64, C.c_void_p, C.c_int]),
     "pic1d_ens_history": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
                                     C.c_void_p]),
     "pic1d_ens_last_error": (C.c_char_p, [C.c_void_p]),

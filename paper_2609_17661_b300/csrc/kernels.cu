@@ -2047,6 +2047,22 @@ cudaError_t launch_annihilate(const DevParams& P, const uint32_t* counts, const 
   return cudaGetLastError();
 }
 
+// the library's generator on caller-given counters (pic1d_philox)
+__global__ void k_philox(const uint4* ctr, long long n, uint32_t k0, uint32_t k1, uint4* out) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    out[i] = philox4x32_10(ctr[i], k0, k1);
+}
+
+cudaError_t launch_philox(const void* ctr, long long n, unsigned long long key, void* out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const long long blocks = (n + 255) / 256;
+  const int grid = (int)(blocks < 148 * 16 ? blocks : 148 * 16);
+  k_philox<<<grid, 256, 0, s>>>(reinterpret_cast<const uint4*>(ctr), n, (uint32_t)key, (uint32_t)(key >> 32),
+                                reinterpret_cast<uint4*>(out));
+  return cudaGetLastError();
+}
+
 cudaError_t launch_pair_table(const float2* t, int Ng, int Ns, float4* out, cudaStream_t s) {
   const int total = 2 * (Ns - 1) * Ng;
   k_pair_table<<<(total + 255) / 256, 256, 0, s>>>(t, Ng, Ns, out);

@@ -1814,6 +1814,41 @@ int pic1d_get_rho(pic1d_ctx* c, int64_t* rho, int mem) {
   return PIC1D_OK;
 }
 
+int pic1d_philox(const uint32_t* ctr, int64_t n, uint64_t key, uint32_t* out, int mem) {
+  if (n < 0 || (n > 0 && (!ctr || !out)) || (mem != 0 && mem != 1)) {
+    std::fprintf(stderr, "pic1d_philox: bad arguments\n");
+    return PIC1D_EINVAL;
+  }
+  if (n == 0) return PIC1D_OK;
+  if (mem == 1 && ((reinterpret_cast<uintptr_t>(ctr) | reinterpret_cast<uintptr_t>(out)) & 15u)) {
+    std::fprintf(stderr, "pic1d_philox: device arrays must be 16-byte aligned\n");
+    return PIC1D_EINVAL;
+  }
+  const size_t bytes = (size_t)n * 4 * sizeof(uint32_t);
+  void* dc = const_cast<uint32_t*>(ctr);
+  void* dout = out;
+  cudaError_t e = cudaSuccess;
+  if (mem == 0) {
+    dc = nullptr;
+    dout = nullptr;
+    e = raw_alloc(&dc, bytes);
+    if (e == cudaSuccess) e = raw_alloc(&dout, bytes);
+    if (e == cudaSuccess) e = cudaMemcpy(dc, ctr, bytes, cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess) e = launch_philox(dc, n, key, dout, nullptr);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
+  if (e == cudaSuccess && mem == 0) e = cudaMemcpy(out, dout, bytes, cudaMemcpyDeviceToHost);
+  if (mem == 0) {
+    dfree(dc);
+    dfree(dout);
+  }
+  if (e != cudaSuccess) {
+    std::fprintf(stderr, "pic1d_philox: %s\n", cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? PIC1D_ENOMEM : PIC1D_ECUDA;
+  }
+  return PIC1D_OK;
+}
+
 int pic1d_set_allocator(pic1d_alloc_fn alloc, pic1d_free_fn free_fn, void* user) {
   if ((alloc == nullptr) != (free_fn == nullptr)) {
     std::fprintf(stderr, "pic1d_set_allocator: give both hooks or neither\n");

@@ -109,6 +109,8 @@ cudaError_t launch_inject(const DevParams& P, double carriers_per_step, float si
 cudaError_t launch_annihilate(const DevParams& P, const uint32_t* counts, const long long* offsets, int* list,
                               long long* amount, unsigned* count, double* E64, float* E32, double cJ, int sms,
                               cudaStream_t s);
+// Philox4x32-10 of n counters (16-byte aligned device arrays of n x 4 u32), key (lo, hi)
+cudaError_t launch_philox(const void* ctr, long long n, unsigned long long key, void* out, cudaStream_t s);
 // atmosphere top-up (TOPUP): n_cells cells of the atmosphere with their target weights (w_int)
 cudaError_t launch_topup(const DevParams& P, const int* cells, const long long* target, int n_cells, float sig_e,
                          float sig_i, cudaStream_t s);

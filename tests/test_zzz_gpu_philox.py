@@ -1,0 +1,120 @@
+"""The device's random numbers (Philox4x32-10, Salmon et al. 2011) through
+pic1d_philox:
+* the published known-answer vectors;
+* bitwise equal to the FP64 oracle's generator on a million counters, both
+  random ones and counters laid out as the push, the supply and the
+  atmosphere lay them out;
+* cuRAND's Philox4_32_10, run (not read) through its device API, gives the
+  same four words under one of two counter mappings (seed = key; the other
+  two words as the subsequence and four times the first two as the offset,
+  or the other way round), matched empirically here.
+"""
+import ctypes as C
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+GOLD = os.path.join(ROOT, "tests", "golden")
+
+
+def device_philox(ctr, key):
+    from paper_2609_17661_b300 import _lib
+    L = _lib.load()
+    c = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    out = np.zeros_like(c)
+    assert L.pic1d_philox(C.c_void_p(c.ctypes.data), c.shape[0], int(key), C.c_void_p(out.ctypes.data), 0) == 0
+    return out
+
+
+def test_known_answers_on_the_device():
+    with open(os.path.join(GOLD, "philox4x32_10_kat.txt")) as f:
+        rows = [[int(x, 16) for x in l.split()] for l in f if l.strip() and not l.startswith("#")]
+    for v in rows:
+        key = v[4] | (v[5] << 32)
+        assert device_philox(v[0:4], key)[0].tolist() == v[6:10]
+
+
+def test_device_equals_the_oracle_on_a_million_counters():
+    rng = np.random.default_rng(17)
+    n = 1_000_000
+    ctr = rng.integers(0, 2**32, size=(n, 4), dtype=np.uint64).astype(np.uint32)
+    # a quarter laid out as the library draws: (id_lo, id_hi, step, scattering tag), (slot, footpoint,
+    # step, supply tag), (slot, cell, step, atmosphere tag)
+    q = n // 4
+    ctr[:q, 3] = 0x52494353
+    ctr[q:2 * q, 1] = rng.integers(0, 2, q)
+    ctr[q:2 * q, 3] = 0x494E4A31
+    ctr[2 * q:3 * q, 3] = 0x41544D4F
+    for key in (1, 0x0123456789ABCDEF):
+        dev = device_philox(ctr, key)
+        ref = O.philox4x32_10_n(ctr, [key & 0xFFFFFFFF, key >> 32])
+        assert np.array_equal(dev, ref), int(np.sum(np.any(dev != ref, axis=1)))
+
+
+CURAND_SRC = r"""
+#include <curand_kernel.h>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+__global__ void k_curand(const uint32_t* ctr, int n, unsigned long long key, int mapping, uint32_t* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t* c = ctr + 4 * i;
+  const unsigned long long lo = (unsigned long long)c[0] | ((unsigned long long)c[1] << 32);
+  const unsigned long long hi = (unsigned long long)c[2] | ((unsigned long long)c[3] << 32);
+  curandStatePhilox4_32_10_t st;
+  if (mapping == 0) curand_init(key, hi, 4ull * lo, &st);
+  else curand_init(key, lo, 4ull * hi, &st);
+  const uint4 r = curand4(&st);
+  out[4 * i] = r.x; out[4 * i + 1] = r.y; out[4 * i + 2] = r.z; out[4 * i + 3] = r.w;
+}
+
+extern "C" int run(const uint32_t* ctr, int n, unsigned long long key, int mapping, uint32_t* out) {
+  uint32_t *dc = nullptr, *dout = nullptr;
+  const size_t bytes = (size_t)n * 16;
+  if (cudaMalloc(&dc, bytes) != cudaSuccess || cudaMalloc(&dout, bytes) != cudaSuccess) return 1;
+  cudaMemcpy(dc, ctr, bytes, cudaMemcpyHostToDevice);
+  k_curand<<<(n + 255) / 256, 256>>>(dc, n, key, mapping, dout);
+  const cudaError_t e = cudaDeviceSynchronize();
+  cudaMemcpy(out, dout, bytes, cudaMemcpyDeviceToHost);
+  cudaFree(dc);
+  cudaFree(dout);
+  return e == cudaSuccess ? 0 : 2;
+}
+"""
+
+
+def test_curand_philox_agrees_under_a_counter_mapping(tmp_path):
+    if shutil.which("nvcc") is None:
+        pytest.skip("no nvcc")
+    src = tmp_path / "curand_philox.cu"
+    src.write_text(CURAND_SRC)
+    so = tmp_path / "libcurand_philox.so"
+    cc = subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O2", "-shared", "-Xcompiler",
+                         "-fPIC", str(src), "-o", str(so)], capture_output=True, text=True, timeout=600)
+    assert cc.returncode == 0, cc.stderr[-2000:]
+    lib = C.CDLL(str(so))
+    lib.run.argtypes = [C.c_void_p, C.c_int, C.c_ulonglong, C.c_int, C.c_void_p]
+    rng = np.random.default_rng(23)
+    n = 100_000
+    ctr = rng.integers(0, 2**32, size=(n, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[:, 1] &= 0x3FFFFFFF          # four times a 64-bit word must not overflow the offset
+    ctr[:, 3] &= 0x3FFFFFFF
+    key = 0x0123456789ABCDEF
+    ours = device_philox(ctr, key)
+    matched = []
+    for mapping in (0, 1):
+        out = np.zeros_like(ctr)
+        assert lib.run(C.c_void_p(ctr.ctypes.data), n, key, mapping, C.c_void_p(out.ctypes.data)) == 0
+        if np.array_equal(out, ours):
+            matched.append(mapping)
+    assert matched, "cuRAND's Philox4_32_10 agrees under neither counter mapping"
