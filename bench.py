@@ -172,11 +172,65 @@ def cpu_baseline(cfg, sample_total, budget_s, max_steps):
                       f"(the oracle is single-threaded C, FP64)"}, steps, st["pos"].size
 
 
+def tp_cfg():
+    """The test-particle map's physics: B*/B_QED = 10, 1 keV radially
+    streaming photons, physical drag."""
+    return W.config("C1", kT_keV=1.0, photon_model=0, drag_scale=1.0)
+
+
+def cpu_baseline_tp(r_all, t_max, budget_s):
+    """The oracle's test-particle line (single thread, as it stands) on a
+    bounded sample of the map's lines, evenly spread in r_eq."""
+    import oracle as O
+    cfg = tp_cfg()
+    idx = np.unique(np.linspace(0, r_all.size - 1, 64).astype(np.int64))
+    steps, done = 0.0, 0
+    t0 = time.perf_counter()
+    for k in idx:
+        steps += O.tp_line(cfg, float(r_all[k]), 1000.0, 1e-3, t_max)["steps"]
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    t = time.perf_counter() - t0
+    return {"value": steps / t, "unit": "line-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{done} of the {r_all.size} lines, evenly spread in r_eq, the same dt and t_max "
+                      f"(single-threaded C, FP64)"}, steps, t
+
+
+def cpu_baseline_ensemble(cfgs, counts, theta, budget_s, per_line=20000):
+    """The oracle (single thread, as it stands) on a bounded sample of the
+    ensemble: lines spread over the set, `per_line` macroparticles each in
+    the same pair-loaded profile, drag law SURROGATE with the network
+    `theta`, stepped until the budget is spent."""
+    import oracle as O
+    idx = np.unique(np.linspace(0, len(cfgs) - 1, 8).astype(np.int64))
+    units, done = 0.0, 0
+    t_sum = 0.0
+    for k in idx:
+        st = W.load_pair_loaded(cfgs[k], per_line, seed=7)
+        o = W.to_oracle(st, cfgs[k]["n_cells"])
+        S = O.Sim(cfgs[k])
+        S.set_surrogate(theta)
+        S.set_particles(o["s"], o["u"], o["w"], o["sp"], o["id"])
+        t0 = time.perf_counter()
+        S.step(2)
+        t_sum += time.perf_counter() - t0
+        units += 2 * o["s"].size
+        done += 1
+        if t_sum > budget_s:
+            break
+    return {"value": units / t_sum, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{done} of the {len(cfgs)} lines, {per_line} macroparticles each in the same profile, "
+                      f"2 steps, drag law SURROGATE (single-threaded C, FP64)"}, units, t_sum
+
+
 def run_reference(args):
-    cfg = cfg_for(args)
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    if args.workload in ("TP", "C4"):
+        return run_reference_other(args)
+    cfg = cfg_for(args)
     sample = args.ref_sample
     cb, steps, n = cpu_baseline(cfg, sample, budget_s=max(5.0, 0.6 * args.steps), max_steps=args.steps)
     v = cb["value"]
@@ -187,6 +241,27 @@ def run_reference(args):
                        "particles": n, "sort_every": cfg["sort_every"], "drag": "table"},
             "impl": "reference", "cpu_baseline": cb,
             "e2e": {"value": v, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_other(args):
+    """The reference arm of the map and ensemble workloads: the oracle on a
+    bounded sample of the same workload."""
+    if args.workload == "TP":
+        r = np.geomspace(2.0, 100.0, args.tp_lines)
+        cb, units, t = cpu_baseline_tp(r, args.tp_tmax, budget_s=max(5.0, 0.6 * args.steps))
+        metric, name = "line-steps/s", (f"test-particle drag map, {r.size} dipole lines r_eq in [2, 100], "
+                                         f"gamma0 1000, b*=10, 1 keV radial photons, dt 1e-3, t_max {args.tp_tmax:g}")
+    else:
+        cfgs, counts = W.ensemble_configs()
+        cb, units, t = cpu_baseline_ensemble(cfgs, counts, W.sur_init_params(0), budget_s=max(5.0, 0.6 * args.steps))
+        metric, name = "particle-steps/s", ("ensemble of 256 dipole lines, r_eq log-uniform in [2, 30], 512-65536 "
+                                             "cells affine in arc length, 1e4-1e7 macroparticles each, surrogate drag")
+    v = cb["value"]
+    line = {"metric": metric, "value": v, "unit": metric, "n_gpus": args.gpus, "steps": args.steps, "warmup": 0,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": name}, "impl": "reference", "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": metric, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -491,6 +566,8 @@ def run_ensemble(args):
            "training": {k: rep[k] for k in ("steps", "samples_ms", "train_ms", "drag_err_median", "drag_err_p99",
                                             "lnN_err_median", "lnN_err_p99")},
            "gpu_launches": 4 * steps + sum(7 * (steps // int(c)) for c in cad),
+           "cpu_baseline": None if args.no_cpu else
+           cpu_baseline_ensemble(cfgs, counts, ens.lines[0].sur_get_params(), budget_s=15.0)[0],
            "setup_s": {"host_state": t_gen}}
     print(json.dumps(out), flush=True)
     ens.close()
@@ -533,6 +610,7 @@ def run_tp_map(args):
                                   f"b*=10, 1 keV radial photons, dt 1e-3, t_max {args.tp_tmax:g}",
                       "lines": int(r.size)},
            "roofline": roof, "lines_per_s": r.size / (ms * 1e-3),
+           "cpu_baseline": None if args.no_cpu else cpu_baseline_tp(r, args.tp_tmax, budget_s=15.0)[0],
            "r_crit": float(third.min()) if third.size else None,
            "regions": {str(k): int((res["region"] == k).sum()) for k in (1, 2, 3)},
            "gpu_launches": 1}
