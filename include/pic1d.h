@@ -258,7 +258,7 @@ int pic1d_deposit(pic1d_ctx* c, int64_t n, const int64_t* pos0, const int64_t* p
  * results.  Errors: ECUDA. */
 int pic1d_timing(pic1d_ctx* c, int on);
 
-/* Choose the push kernel variant: particles per thread (128/64/32-bit SoA
+/* Choose the push kernel variant: particles per thread (32- or 64-bit SoA
  * accesses) x minimum resident blocks per SM.  Results do not depend on the
  * variant (integer deposit, per-particle arithmetic).  Errors: EINVAL. */
 int pic1d_set_variant(pic1d_ctx* c, int variant);
@@ -283,8 +283,10 @@ int pic1d_variant_info(int variant, int* particles_per_thread, int* min_blocks_p
  * library holds it until the process exits, so n_cells is limited to
  * PIC1D_SORT_STATIC_MAX_CELLS and larger lines are rejected with
  * PIC1D_EINVAL and a message on stderr.  The first call on a device looks up
- * the array's device address (once per device); make that first call before
- * any stream capture.  Every call uses the same array: calls that overlap on
+ * the array's device address (once per device, kept for the life of the
+ * process); make that first call before any stream capture, and make no call
+ * on a device after cudaDeviceReset has been called on it (the reset unloads
+ * the array and the kept address would then be stale).  Every call uses the same array: calls that overlap on
  * the GPU (on different streams, or from different host threads) race and
  * corrupt each other's results; serialise them.  The histogram is cleared
  * by each call.  Work is issued on cuda_stream (NULL: legacy default

@@ -727,7 +727,9 @@ orc_sim* orc_create(const orc_params* p, const double* table_or_null)
     }
   }
   S->grav_on = (p->inject_mode == ORC_INJECT_TOPUP);
-  if (p->drag_law == ORC_DRAG_TABLE) {
+  /* the table law's table; a SURROGATE line given one keeps it as the
+   * network's fallback outside its training box (else it is built on first use) */
+  if (p->drag_law == ORC_DRAG_TABLE || (p->drag_law == ORC_DRAG_SURROGATE && table_or_null)) {
     size_t nt = (size_t)2 * p->table_n_s * p->table_n_gamma * 2;
     S->table = malloc(nt * sizeof(double));
     if (table_or_null) memcpy(S->table, table_or_null, nt * sizeof(double));
@@ -931,8 +933,9 @@ static void orc_ln_nrad(const orc_params* p, double u, double x, double b, doubl
 }
 
 /* surrogate F^ (per R_star), dF^/du and ln N^ at (u, s); outside the training
- * box (gamma above 10^G or b outside the range of f2) the closed form */
-static void orc_closed_eval(const orc_sim* S, double u, double s, double* F, double* dF, double* lnN);
+ * box (gamma above 10^G or b outside the range of f2), or with no network set,
+ * the table law on the line's quadrature table (Sec. 2.2; the quadrature is
+ * the network's fallback) */
 static void orc_sur_eval(const orc_sim* S, double u, double s, double* F, double* dF, double* lnN)
 {
   const orc_params* p = &S->p;
@@ -947,7 +950,13 @@ static void orc_sur_eval(const orc_sim* S, double u, double s, double* F, double
   f[2] = (log10(b) - ORC_SUR_B_MID) / ORC_SUR_B_HALF;
   f[3] = (u < 0.0) ? -1.0 : 1.0;
   if (f[0] > 1.0 || f[2] < -1.0 || f[2] > 1.0 || !S->sur) {
-    orc_closed_eval(S, u, s, F, dF, lnN);
+    if (!S->table) {
+      /* a cache of the line's fixed table, built the first time it is needed */
+      orc_sim* W = (orc_sim*)S;
+      W->table = malloc((size_t)2 * p->table_n_s * p->table_n_gamma * 2 * sizeof(double));
+      orc_build_table(p, W->table);
+    }
+    orc_table_eval(S, u, s, F, dF, lnN);
     return;
   }
   double y[2], dy[2];

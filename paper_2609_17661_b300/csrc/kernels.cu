@@ -203,19 +203,8 @@ __device__ __forceinline__ void rics_event(float b, float d, float ui, float ct,
 }
 
 // --------------------------------------------------------------------------
-// deposit helpers: a thread accumulates the currents of its particles into
-// three registers for cells c_ref-1, c_ref, c_ref+1; anything else goes
-// straight to the window (shared) or to global memory.
+// deposit helpers
 // --------------------------------------------------------------------------
-__device__ __forceinline__ void add_cell(long long* sWin, int win_lo, long long* g, int N, int cell, long long v) {
-  if (v == 0 || cell < 0 || cell >= N) return;
-  const int o = cell - win_lo;
-  if (o >= 0 && o < kWindow)
-    atomicAdd(reinterpret_cast<unsigned long long*>(sWin + o), (unsigned long long)v);
-  else
-    atomicAdd(reinterpret_cast<unsigned long long*>(g + cell), (unsigned long long)v);
-}
-
 // exact int64 sum over the lanes of `grp` (lanes that share a key): three
 // 21-bit slices, each summed by one redux (|v| < 2^62 keeps every slice sum
 // inside 32 bits), recombined in 64 bits.  Order-independent and exact.
@@ -227,22 +216,6 @@ __device__ __forceinline__ long long group_sum64(unsigned grp, long long v) {
   const unsigned smid = __reduce_add_sync(grp, mid);
   const int shi = (int)__reduce_add_sync(grp, (unsigned)hi);
   return ((long long)shi << 42) + ((long long)smid << 21) + (long long)slo;
-}
-
-// warp-level flush of the per-thread registers (cells c_ref-1, c_ref, c_ref+1):
-// lanes with equal c_ref form a group (any order along the warp), the group's
-// lowest lane adds the three exact sums; then the registers are cleared.
-__device__ __forceinline__ void warp_flush(long long (&a)[3], int c_ref, long long* sWin, int win_lo,
-                                           long long* g, int N) {
-  const int lane = threadIdx.x & 31;
-  const unsigned grp = __match_any_sync(0xffffffffu, c_ref);
-  const bool leader = lane == __ffs(grp) - 1;
-#pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    const long long sum = group_sum64(grp, a[j]);
-    if (leader) add_cell(sWin, win_lo, g, N, c_ref - 1 + j, sum);
-    a[j] = 0;
-  }
 }
 
 // --------------------------------------------------------------------------
@@ -542,16 +515,6 @@ __device__ __forceinline__ void push_fast(const DevParams& P, uint32_t pos0, flo
   o.u = u;
 }
 
-// warp-aggregated add of (cell, v) contributions from the lanes in `mask`
-__device__ __forceinline__ void warp_add_cells(unsigned mask, bool mine, int cell, long long v, long long* sWin,
-                                               int win_lo, long long* g, int N) {
-  if (mine) {
-    const unsigned grp = __match_any_sync(mask, cell);
-    const long long sum = group_sum64(grp, v);
-    if ((threadIdx.x & 31) == __ffs(grp) - 1) add_cell(sWin, win_lo, g, N, cell, sum);
-  }
-}
-
 template <int PPT> struct Vec;
 template <> struct Vec<1> { using U = uint32_t; using F = float; using B = uint8_t; };
 template <> struct Vec<2> { using U = uint2; using F = float2; using B = uchar2; };
@@ -590,19 +553,6 @@ __device__ __forceinline__ void win_add(long long* sWin, int win_lo, int& lo, in
     hi = max(hi, o);
   } else {
     atomicAdd(reinterpret_cast<unsigned long long*>(g + cell), (unsigned long long)v);
-  }
-}
-
-__device__ __forceinline__ void warp_flush_w(long long (&a)[3], int c_ref, long long* sWin, int win_lo, int& lo,
-                                             int& hi, long long* g, int N) {
-  const int lane = threadIdx.x & 31;
-  const unsigned grp = __match_any_sync(0xffffffffu, c_ref);
-  const bool leader = lane == __ffs(grp) - 1;
-#pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    const long long sum = group_sum64(grp, a[j]);
-    if (leader) win_add(sWin, win_lo, lo, hi, g, N, c_ref - 1 + j, sum);
-    a[j] = 0;
   }
 }
 
@@ -886,7 +836,8 @@ __device__ __forceinline__ float sur_lnrad(const DevParams& P, float u, float ga
 // F^ (per R_star), dF^/du and ln N^ of the surrogate at u for this thread's
 // particle.  Collective: every thread of the CTA calls it; `want` only says
 // whether the caller uses the result.  Outside the training box (gamma above
-// 10^G, b outside the range of f2) the closed form stands in.
+// 10^G, b outside the range of f2) the line's quadrature table stands in (the
+// table law's lookup), or the closed form where a line has no table.
 __device__ DragVal sur_eval(const DevParams& P, sur::MlpCta& M, float u, const Site& S, float sL, bool want,
                            bool with_dF) {
   const float q = fmaf(u, u, 1.0f);
@@ -904,7 +855,7 @@ __device__ DragVal sur_eval(const DevParams& P, sur::MlpCta& M, float u, const S
   d.F = d.dF = 0.0f;
   d.lnN = -700.0f;
   if (!want) return d;
-  if (!inbox) return closed_eval(P, u, S, with_dF);
+  if (!inbox) return P.tpair ? table_eval(P, u, S.j, S.c, with_dF) : closed_eval(P, u, S, with_dF);
   float d1, d2;
   const float l1 = sur_lnrad(P, u, gam, S.x, S.b, S.mu, d1);
   const float ths = acosf(fmaxf(-1.0f, fminf(1.0f, S.mu))), am = asinf(fminf(1.0f, 1.0f / S.x));
@@ -1014,6 +965,7 @@ __device__ void sur_tile(const DevParams& P, sur::MlpCta& M, uint32_t tile, uint
     S.b = fmaf(f, __ldg(P.nb + cell + 1) - __ldg(P.nb + cell), __ldg(P.nb + cell));
     S.mu = fmaf(f, __ldg(P.nmu + cell + 1) - __ldg(P.nmu + cell), __ldg(P.nmu + cell));
     S.x = fmaf(f, __ldg(P.nx + cell + 1) - __ldg(P.nx + cell), __ldg(P.nx + cell));
+    site_rows(P, pos0, S);
   }
   const bool cont = valid && lep && (P.rics_mode == PIC1D_RICS_DRAG_PLUS_PAIRS || !zone);
   const bool mc = valid && lep && P.mc_on && zone;
@@ -1134,14 +1086,14 @@ __device__ void sur_tile(const DevParams& P, sur::MlpCta& M, uint32_t tile, uint
 template <bool NMAX>
 __global__ void __launch_bounds__(sur::NT, 4) k_push_sur(DevParams P) {
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t bar_ld, bar_mma;
+  __shared__ __align__(8) uint64_t bars[3];
   __shared__ uint32_t s_taddr;
   __shared__ unsigned s_tile;
   __shared__ unsigned sCtr[C_COUNT];
   __shared__ float sKl;
   __shared__ double sRed[sur::NT / 32];
   sur::MlpCta M;
-  sur::mlp_begin(M, smem_raw, &bar_ld, &bar_mma, &s_taddr, P.sur_img, P.sur_small);
+  sur::mlp_begin(M, smem_raw, bars, &s_taddr, P.sur_img, P.sur_small);
   const int t = threadIdx.x;
   if (t < C_COUNT) sCtr[t] = 0;
   if (t == 0) {
@@ -1165,9 +1117,8 @@ __global__ void __launch_bounds__(sur::NT, 4) k_push_sur(DevParams P) {
   if (t == 0) {
     if (M.passes) atomicAdd(&P.ctr->sur_rows, (unsigned long long)M.passes * sur::TM);
     if (M.passes_t) atomicAdd(&P.ctr->sur_rows_tangent, (unsigned long long)M.passes_t * sur::TM);
-    if (!M.ok) atomicOr(P.sur_err, 1u);
   }
-  sur::mlp_end(M);
+  if (!sur::mlp_end(M) && t == 0) atomicOr(P.sur_err, 1u);
 }
 
 // --------------------------------------------------------------------------
@@ -1202,7 +1153,7 @@ __global__ void k_ens_clear(EnsArgs A) {
 // global queue; the tallies of an item go to its line
 __global__ void __launch_bounds__(sur::NT, 4) k_ens_push(EnsArgs A) {
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t bar_ld, bar_mma;
+  __shared__ __align__(8) uint64_t bars[3];
   __shared__ uint32_t s_taddr;
   __shared__ unsigned s_item;
   __shared__ unsigned sCtr[C_COUNT];
@@ -1210,7 +1161,7 @@ __global__ void __launch_bounds__(sur::NT, 4) k_ens_push(EnsArgs A) {
   __shared__ double sRed[sur::NT / 32];
   __shared__ __align__(16) DevParams sP;
   sur::MlpCta M;
-  sur::mlp_begin(M, smem_raw, &bar_ld, &bar_mma, &s_taddr, A.sur_img, A.sur_small);
+  sur::mlp_begin(M, smem_raw, bars, &s_taddr, A.sur_img, A.sur_small);
   const int t = threadIdx.x;
   if (t < C_COUNT) sCtr[t] = 0;
   if (t == 0) sKl = 0.0f;
@@ -1241,8 +1192,7 @@ __global__ void __launch_bounds__(sur::NT, 4) k_ens_push(EnsArgs A) {
     }
     __syncthreads();
   }
-  if (t == 0 && !M.ok) atomicOr(A.sur_err, 1u);
-  sur::mlp_end(M);
+  if (!sur::mlp_end(M) && t == 0) atomicOr(A.sur_err, 1u);
 }
 
 // Ampere update of every line (FP64) and the per-line sums of the step

@@ -441,7 +441,9 @@ int build_tables(pic1d_ctx* c) {
   CK(cudaMemcpyAsync(c->zone, hz.data(), N, cudaMemcpyHostToDevice, c->s), "copy zone");
   CK(cudaStreamSynchronize(c->s), "sync nodes");
 
-  if (p.drag_law == PIC1D_DRAG_TABLE) {
+  // the table law's table; a SURROGATE line keeps one as the network's
+  // fallback outside its training box
+  if (p.drag_law == PIC1D_DRAG_TABLE || p.drag_law == PIC1D_DRAG_SURROGATE) {
     const int Ns = p.table_n_s, Ng = p.table_n_gamma;
     std::vector<double> xs(Ns), bs(Ns), ms(Ns);
     guess = line.th0;

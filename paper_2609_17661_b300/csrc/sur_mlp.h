@@ -83,20 +83,25 @@ struct MlpCta {
   unsigned passes_t; // of which with the tangent
   uint64_t* bar_ld;
   uint64_t* bar_mma;
+  uint64_t* bar_end;
   uint32_t tmem;
   uint32_t ph;
   bool ok;
 };
 
-__device__ __forceinline__ void mlp_begin(MlpCta& M, uint8_t* smem_raw, uint64_t* bar_ld, uint64_t* bar_mma,
-                                          uint32_t* s_taddr, const uint8_t* img, const float* small) {
+// bar: three mbarriers in shared memory (weight copies, MMA completion, teardown).
+__device__ __forceinline__ void mlp_begin(MlpCta& M, uint8_t* smem_raw, uint64_t* bar, uint32_t* s_taddr,
+                                          const uint8_t* img, const float* small) {
   M.sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  M.bar_ld = bar_ld;
-  M.bar_mma = bar_mma;
+  uint64_t* bar_ld = bar;
+  M.bar_ld = bar;
+  M.bar_mma = bar + 1;
+  M.bar_end = bar + 2;
   const int t = threadIdx.x;
   if (t == 0) {
-    tc::mbar_init(bar_ld, 1);
-    tc::mbar_init(bar_mma, 1);
+    tc::mbar_init(bar, 1);
+    tc::mbar_init(bar + 1, 1);
+    tc::mbar_init(bar + 2, 1);
     tc::mbar_fence_init();
   }
   __syncthreads();
@@ -118,11 +123,10 @@ __device__ __forceinline__ void mlp_begin(MlpCta& M, uint8_t* smem_raw, uint64_t
   M.ok = tc::mbar_wait(bar_ld, 0);
 }
 
-__device__ __forceinline__ void mlp_end(MlpCta& M) {
-  tc::fence_before();
-  __syncthreads();
-  tc::fence_after();
-  if (threadIdx.x < 32) tc::tmem_free(M.tmem, 128);
+// End of a forward-pass CTA (all NT threads): returns true only if no wait of
+// any thread gave up; the TMEM columns are freed once nothing is in flight.
+__device__ __forceinline__ bool mlp_end(MlpCta& M) {
+  return tc::cta_teardown(M.ok, M.bar_end, M.bar_ld, 0, M.tmem, 128);
 }
 
 // One forward pass of the CTA's 128 rows (thread t holds row t's inputs x):

@@ -220,7 +220,7 @@ constexpr int R_W1 = 0, R_B1 = 256, R_B2 = 320, R_B3 = 384, R_W4 = 448, R_B4 = 5
 __global__ void __launch_bounds__(NT, 1) k_sur_train(TrainArgs A) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  __shared__ __align__(8) uint64_t bar_ld, bar_mma;
+  __shared__ __align__(8) uint64_t bar_ld, bar_mma, bar_end;
   __shared__ uint32_t s_taddr;
   const int t = threadIdx.x, warp = t >> 5;
   float* sSmall = reinterpret_cast<float*>(sm + SM_SMALL);
@@ -233,6 +233,7 @@ __global__ void __launch_bounds__(NT, 1) k_sur_train(TrainArgs A) {
   if (t == 0) {
     tc::mbar_init(&bar_ld, 1);
     tc::mbar_init(&bar_mma, 1);
+    tc::mbar_init(&bar_end, 1);
     tc::mbar_fence_init();
   }
   __syncthreads();
@@ -447,9 +448,7 @@ __global__ void __launch_bounds__(NT, 1) k_sur_train(TrainArgs A) {
   for (int k = t; k < 128; k += NT) part[W_OW4 + k] = sRed[R_W4 + k];
   if (t < 2) part[W_OB4 + t] = sRed[R_B4 + t];
   if (t == 0) A.loss_part[blockIdx.x] = sRed[R_LOSS];
-  if (!ok && t == 0) atomicOr(A.err, 1u);
-  tc::fence_after();
-  if (warp == 0) tc::tmem_free(tmem, 128);
+  if (!tc::cta_teardown(ok, &bar_end, &bar_ld, 0, tmem, 128) && t == 0) atomicOr(A.err, 1u);
 }
 
 // ------------------------------------------------- reduction, Adam, images
@@ -531,10 +530,10 @@ struct InferArgs {
 // taken grid-stride.
 __global__ void __launch_bounds__(NT, 1) k_sur_infer(InferArgs A) {
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t bar_ld, bar_mma;
+  __shared__ __align__(8) uint64_t bars[3];
   __shared__ uint32_t s_taddr;
   MlpCta M;
-  mlp_begin(M, smem_raw, &bar_ld, &bar_mma, &s_taddr, A.img, A.small);
+  mlp_begin(M, smem_raw, bars, &s_taddr, A.img, A.small);
   const int t = threadIdx.x;
   const long long ntiles = (A.n + TM - 1) / TM;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -549,8 +548,7 @@ __global__ void __launch_bounds__(NT, 1) k_sur_infer(InferArgs A) {
     mlp_tile(M, x, y0, y1, g0, g1);
     if (valid) *reinterpret_cast<float4*>(A.out + 4 * row) = make_float4(y0, y1, g0, g1);
   }
-  if (!M.ok && t == 0) atomicOr(A.err, 1u);
-  mlp_end(M);
+  if (!mlp_end(M) && t == 0) atomicOr(A.err, 1u);
 }
 
 // ------------------------------------------------------------- validation

@@ -122,5 +122,29 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Teardown of a CTA that issued tcgen05 MMAs from thread `issuer` and bulk
+// copies completing on phase 0 of `bar_ld`; `ok` is this thread's record of
+// its own waits (each thread polls with its own clock, so one warp may give
+// up while another does not).  Returns true only if every thread's waits
+// completed.  If any gave up, an MMA or a copy may still be in flight: the
+// issuer commits once more on `bar_end` (initialised with count 1, used for
+// nothing else) and waits, bounded, for that commit and for the copies, so
+// that the TMEM columns are not freed, and the CTA's shared memory not
+// released, under them.  Warp 0 (which allocated them) frees the columns.
+__device__ __forceinline__ bool cta_teardown(bool ok, uint64_t* bar_end, uint64_t* bar_ld, int issuer,
+                                             uint32_t tmem, uint32_t ncols) {
+  fence_before();
+  const bool all = __syncthreads_and(ok ? 1 : 0) != 0;
+  if (!all && (int)threadIdx.x == issuer) {
+    mma_commit(bar_end);
+    mbar_wait(bar_end, 0);
+    mbar_wait(bar_ld, 0);
+  }
+  __syncthreads();
+  fence_after();
+  if (threadIdx.x < 32) tmem_free(tmem, ncols);
+  return all;
+}
+
 }  // namespace tc
 }  // namespace pic1d

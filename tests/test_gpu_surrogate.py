@@ -257,3 +257,43 @@ def test_gain_over_quadrature_and_tables():
           % (t_quad, t_net, t_quad / t_net, np.median(err_net), np.percentile(err_net, 99),
              np.median(err_tab), np.percentile(err_tab, 99), {k2: rep[k2] for k2 in ("train_ms", "steps")}))
     assert np.median(err_net) < 2e-2
+
+
+def test_push_outside_the_training_box_uses_the_table_law():
+    """Above gamma = 10^G (the network's box) the surrogate law hands over to
+    the line's own quadrature table: one step of such leptons with drag law
+    SURROGATE gives bit for bit the momenta and positions of the same step
+    with drag law TABLE."""
+    from paper_2609_17661_b300 import Line
+    cfg = _sur_cfg(eta_min=1.0)
+    st = W.load_beam(cfg, 20_000, gamma_lo=2e8, gamma_hi=3e9, seed=31)
+    out = {}
+    for law in (O.DRAG_SURROGATE, O.DRAG_TABLE):
+        line = Line(dict(cfg, drag_law=law))
+        if law == O.DRAG_SURROGATE:
+            line.sur_set_params(_bf16_params(32, scale=1.0).astype(np.float32))
+        line.set_state(st)
+        line.step(1)
+        out[law] = _by_id(line.particles())
+        line.close()
+    a, b = out[O.DRAG_SURROGATE], out[O.DRAG_TABLE]
+    np.testing.assert_array_equal(a["id"], b["id"])
+    np.testing.assert_array_equal(a["u"], b["u"])
+    np.testing.assert_array_equal(a["pos"], b["pos"])
+
+
+@pytest.mark.slow
+def test_full_training_run_holds_its_measured_accuracy():
+    """The workload's training run on the r_eq = 20 line (1e7 quadrature
+    samples, 20 epochs of 8192, Adam with the cosine decay 3e-3 -> 1e-5):
+    the held-out drag error against quadrature stays at the measured
+    median <= 1e-3 (the target) and p99 <= 3.5e-2 (the tail, where the target
+    is not met), and the rate's median within 2e-3 in ln N."""
+    line = _line()
+    line.sur_set_params(W.sur_init_params(0))
+    rep = line.train_surrogate(**W.SUR_TRAIN_COSINE)
+    print({k: rep[k] for k in rep if "err" in k})
+    assert rep["drag_err_median"] <= 1e-3, rep["drag_err_median"]
+    assert rep["drag_err_p99"] <= 3.5e-2, rep["drag_err_p99"]
+    assert rep["lnN_err_median"] <= 2e-3, rep["lnN_err_median"]
+

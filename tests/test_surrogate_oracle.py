@@ -273,9 +273,24 @@ def test_surrogate_drag_derivative_matches_differences():
         assert dF == pytest.approx(fd, rel=2e-5, abs=1e-12 * max(abs(F), 1e-300) + 1e-300)
 
 
-def test_surrogate_law_outside_the_box_is_the_closed_form():
+def test_surrogate_law_outside_the_box_is_the_table_law():
+    """Outside the training box (gamma above 10^G, or b beyond the network's
+    range) the quadrature stands in: the surrogate law equals the table law
+    on the line's own quadrature table (a small table keeps the CPU build
+    short), in F, dF and the rate."""
     th = _theta(15)
-    Sim, cfg = _sur_sim(th)
-    Sc = O.Sim(dict(cfg, drag_law=O.DRAG_CLOSED))
-    u = 3.0e8     # gamma above 10^8
-    assert Sim.drag(u, 500.0) == pytest.approx(Sc.drag(u, 500.0), rel=1e-14)
+    small = dict(table_n_gamma=32, table_n_s=16, quad_n_mu=8, quad_n_phi=8)
+    Sim, cfg = _sur_sim(th, **small)
+    St = O.Sim(dict(cfg, drag_law=O.DRAG_TABLE))
+    for u, s in ((3.0e8, 500.0), (-4.0e8, 1900.0), (1.0e9, 0.0)):     # gamma above 10^8
+        assert Sim.drag(u, s) == pytest.approx(St.drag(u, s), rel=1e-14)
+    # a line whose field reaches below the network's b range (b < 10^-4 at its
+    # equator): there too the table law, inside the gamma box
+    far = dict(cfg, r_eq=60.0)
+    Sf = O.Sim(far)
+    Sf.set_surrogate(th)
+    Sft = O.Sim(dict(far, drag_law=O.DRAG_TABLE))
+    mid = far["n_cells"] / 2
+    assert Sf.node_interp(1, mid) < 1e-4
+    for u in (30.0, -2.0e3):
+        assert Sf.drag(u, mid) == pytest.approx(Sft.drag(u, mid), rel=1e-14)
