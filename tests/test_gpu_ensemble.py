@@ -104,3 +104,66 @@ def test_autotuned_schedule_keeps_results():
     assert steps == 80 + 10 * 3 + 20 * 3 + 40 * 3
     _compare(ens, _singles(cfgs, states, steps))
     ens.close()
+
+
+def test_ensemble_lines_match_the_oracle():
+    """Three small lines with drag law SURROGATE advanced 80 steps by the
+    ensemble (one replay of its captured super-step) against the FP64
+    oracle with the same network, line by line: drag (the implicit midpoint
+    through the network, no limiter) and the Lorentz force in a static
+    non-uniform field with a negligible self-field and no scattering, the
+    regime where FP32 and FP64 can agree over many steps.  Momenta agree to
+    1e-5 of the line's scale plus 3 % of the drag's own change of u over the
+    run (the network's BF16 activations, as for one step of a single line),
+    positions and E to 1e-5 of the line."""
+    import oracle as O
+    from oracle import surrogate as S
+    from paper_2609_17661_b300 import Ensemble
+    theta = S.bf16_tensor_layers(W.sur_init_params(21).astype(np.float64))
+    cfgs, states, fields = [], [], []
+    for k, (r, N, n) in enumerate([(3.0, 512, 1500), (8.0, 1024, 1500), (20.0, 2048, 1000)]):
+        c = W.config("C1", r_eq=r, n_cells=N, drag_law=W.DRAG_SURROGATE, b_pair_threshold=1e30, mc_on=0,
+                     pairs_on=0, eta_min=0.0, drag_scale=3e-3, cells_per_skin_depth=1e6, seed=1 + k,
+                     sort_every=20, capacity=4 * n + 65536, table_n_gamma=64, table_n_s=32)
+        st = W.load_random(c, 4 * n, u_scale=3000.0, seed=40 + k)
+        F = W.fbits(N)
+        keep = (st["pos"] >= (48 << F)) & (st["pos"] < ((N - 48) << F))      # 80 steps move < 37 cells
+        st = {kk: v[keep][:n] for kk, v in st.items()}
+        x = (np.arange(N) + 0.5) / N
+        cfgs.append(c)
+        states.append(st)
+        fields.append(0.02 * np.sin(2 * np.pi * 3 * x) + 0.01)
+    ens = Ensemble(cfgs)
+    ens.lines[0].sur_set_params(theta.astype(np.float32))
+    for ln, st, E in zip(ens.lines, states, fields):
+        ln.set_state(st, E=E)
+    ens.step(80)
+    for k, (ln, c, st, E) in enumerate(zip(ens.lines, cfgs, states, fields)):
+        N = c["n_cells"]
+        F = W.fbits(N)
+        g = _by_id(ln.particles())
+        Eg, _ = ln.fields()
+        o_ = W.to_oracle(st, N)
+        runs = {}
+        for law in (O.DRAG_SURROGATE, O.DRAG_OFF):
+            So = O.Sim(dict(c, drag_law=law))
+            if law == O.DRAG_SURROGATE:
+                So.set_surrogate(theta)
+            So.set_particles(o_["s"], o_["u"], o_["w"], o_["sp"], o_["id"])
+            So.set_field(E)
+            So.step(80)
+            runs[law] = (_by_id(So.particles()), So.fields()[0], So.diag())
+        o, Eo, do = runs[O.DRAG_SURROGATE]
+        o0 = runs[O.DRAG_OFF][0]
+        assert g["id"].tolist() == o["id"].tolist() == o0["id"].tolist(), k
+        du_drag = np.abs(o["u"] - o0["u"])
+        assert np.mean(du_drag > 1e-3) > 0.1, k                 # the drag acts
+        tol = 1e-5 * np.max(np.abs(o["u"])) + 0.03 * du_drag
+        err = np.abs(g["u"].astype(np.float64) - o["u"])
+        assert np.all(err <= tol), (k, float(np.max(err / tol)), int(np.sum(err > tol)))
+        s = g["pos"].astype(np.float64) / float(1 << F)
+        assert np.max(np.abs(s - o["s"])) <= 1e-5 * N, k
+        assert np.max(np.abs(Eg - Eo)) <= 1e-5 * np.max(np.abs(Eo)), k
+        assert ln.diag()["newton_branch"] == do["newton_branch"], k
+    ens.close()
+

@@ -297,6 +297,36 @@ def _rho_int(pos, w, sp, N, F):
     return r
 
 
+def test_push_current_equals_the_integer_deposit_of_its_paths():
+    """G3: the int64 current the push deposits equals, in every cell (the
+    wall cells included), the oracle's integer deposit of the same step's
+    paths (old to new fixed-point position; a particle that leaves the line
+    ends at its wall): the C1 plasma with beams in the end cells that leave
+    through both walls, one step from the loaded state and one more after a
+    cell sort (the push's flushes on the sorted layout)."""
+    from deposit_ref import step_current
+    cfg = W.config("C1")
+    N = cfg["n_cells"]
+    st = W.load_drifting_plasma(cfg)
+    beam = W.load_beam(cfg, 4000, gamma_lo=3.0, gamma_hi=3e3, seed=12, cells=[0, 1, N - 2, N - 1])
+    beam["id"] += 10**7
+    st = {k: np.concatenate([st[k], beam[k]]) for k in st}
+    line = _line(cfg)
+    line.set_state(st, E=_field0(N))
+    line.step(1)
+    after = line.particles(alive_only=False)
+    _, J = line.fields()
+    np.testing.assert_array_equal(J, step_current(st, after, N))
+    d = line.diag()
+    assert d["lost_north"] > 0 and d["lost_south"] > 0 and d["pairs_created"] > 0
+    line.sort()
+    before = line.particles(alive_only=False)
+    line.step(1)
+    after = line.particles(alive_only=False)
+    _, J = line.fields()
+    np.testing.assert_array_equal(J, step_current(before, after, N))
+
+
 def test_gauss_law_integer_exact_every_step():
     """Discrete charge continuity in integers: rho(n+1) - rho(n) = -(J_i -
     J_{i-1}) at every interior node for every step, with J_int the step's own

@@ -75,3 +75,51 @@ def test_record_rearm_and_bounds():
     with pytest.raises(RuntimeError):
         ens.history(2)
     ens.close()
+
+
+def test_sweep_record_matches_the_oracle():
+    """The sweep's device record against the FP64 oracle stepped one step at
+    a time with the same network: two lines of the grid (eta_min 1e2 and
+    1e3), a weak self-field (a skin depth of 1000 cells: no plasma
+    oscillation within the run, so FP32 and FP64 stay together), scattering
+    and pairs on in the pair zones, 16 steps (the record of steps launched
+    directly; the captured super-steps keep the same record, checked above
+    against the lines alone).  The pair cascade multiplies any scattering
+    draw that sits within the network's BF16 reach of p_sc (1e-3 relative in
+    the rate): over longer runs such a draw grows into thousands of pairs,
+    so the window ends while the oracle against itself with the rate moved
+    by 1e-3 stays within 18 pairs of 2.4e4 and 4e-7 in V_c.  V_c after every
+    step within 1e-5 of its largest value; the cumulative pair count within
+    0.5 % + 10 of the oracle's at every step."""
+    import oracle as O
+    from oracle import surrogate as S
+    from paper_2609_17661_b300.sweeps import eta_mass_sweep
+    steps = 16
+    theta = S.bf16_tensor_layers(W.sur_init_params(31).astype(np.float64))
+    base = dict(_base(), cells_per_skin_depth=1e3, table_n_gamma=64, table_n_s=32)
+
+    def state(cfg):
+        return W.load_beam(cfg, 2000, gamma_lo=30.0, gamma_hi=3e4, seed=int(cfg["seed"]) + 41)
+
+    res = eta_mass_sweep(base, [1e2, 1e3], [50.0], steps, theta.astype(np.float32), states=state)
+    assert len(res) == 2
+    for r in res:
+        c = r["cfg"]
+        So = O.Sim(c)
+        So.set_surrogate(theta)
+        o_ = W.to_oracle(state(c), c["n_cells"])
+        So.set_particles(o_["s"], o_["u"], o_["w"], o_["sp"], o_["id"])
+        vc, pairs = [], []
+        for _ in range(steps):
+            So.step(1)
+            d = So.diag()
+            vc.append(d["vc"])
+            pairs.append(d["pairs_created"])
+        vc, pairs = np.array(vc), np.array(pairs)
+        dv = np.max(np.abs(r["vc"] - vc)) / np.max(np.abs(vc))
+        dp = np.max(np.abs(r["pairs"] - pairs))
+        print("eta_min %.0e: V_c max rel diff %.2e, pairs %d (oracle) max diff %d" % (r["eta_min"], dv,
+                                                                                 pairs[-1], dp))
+        assert pairs[-1] > 1000
+        assert dv <= 1e-5
+        assert dp <= 0.005 * pairs[-1] + 10

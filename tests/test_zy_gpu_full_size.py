@@ -6,6 +6,9 @@ After three steps, one more step is checked
 * at every node: the device's integer node charge changes by exactly minus
   the difference of the step's integer currents (discrete continuity, hence
   the Gauss law with the FP64 field update);
+* in every cell: with that, the sum of the current over the cells equals the
+  charge-weighted sum of the particles' paths (walls included), so the
+  current is exact everywhere;
 * in the particle count: alive after = alive before - lost + 2 x pairs;
 * on 4,000 sampled particles (half of them in the pair zones near the
   footpoints), against the FP64 oracle stepping the same particles in the
@@ -58,6 +61,41 @@ def device_sample(line, n, idx):
     del pos, u, sp, pid
     torch.cuda.empty_cache()
     return out
+
+
+def device_slots(line, n, with_w):
+    """Positions (int64, the u32 bits), species and optionally weights of
+    the first n slots, on the device."""
+    dev = torch.device("cuda")
+    pos = torch.empty(n, dtype=torch.int32, device=dev)
+    sp = torch.empty(n, dtype=torch.uint8, device=dev)
+    w = torch.empty(n, dtype=torch.float32, device=dev) if with_w else None
+    rc = line.L.pic1d_get_particles(line.h, n, C.c_void_p(pos.data_ptr()), None,
+                                    C.c_void_p(w.data_ptr()) if with_w else None, C.c_void_p(sp.data_ptr()),
+                                    None, 1)
+    assert rc == 0
+    return dict(pos=pos.to(torch.int64) & 0xFFFFFFFF, sp=sp, w=w)
+
+
+def charge_weighted_displacement(before, after, N):
+    """Sum over the particles alive at the start of a step of q_sign w_int
+    (p1 - p0) in fixed point, with p1 clamped at the wall a particle left
+    through (it is removed there, at position 0 or top - 1) and no path for
+    one removed in place; by the charge-conserving deposit (Sec. 3) this is
+    the sum of the step's integer current over all cells."""
+    F = W.fbits(N)
+    top = N << F
+    p0, p1 = before["pos"], after["pos"]
+    alive = before["sp"] != 255
+    dead = after["sp"] == 255
+    c0 = p0 >> F
+    north = dead & (p1 == 0) & (c0 == 0)
+    south = dead & (p1 == top - 1) & (c0 == N - 1)
+    p1 = torch.where(north, torch.zeros_like(p1), torch.where(south, torch.full_like(p1, top), p1))
+    p1 = torch.where(dead & ~north & ~south, p0, p1)
+    qs = torch.tensor([-1, 1, 1, -1], dtype=torch.int64, device=p0.device)[(before["sp"] & 3).to(torch.int64)]
+    wint = torch.round(before["w"].to(torch.float64) * 4096.0).to(torch.int64)
+    return int(torch.where(alive, qs * wint * (p1 - p0), torch.zeros_like(p0)).sum().item())
 
 
 def sample_slots(cfg, n, line=None, pos=None):
@@ -173,14 +211,22 @@ def test_full_size_line_one_step():
     assert n0 > 9.9e8
     idx = sample_slots(cfg, n0, line)
     snap0 = device_sample(line, n0, idx)
+    before = device_slots(line, n0, with_w=True)
     line.step(1)                                 # step 4: not a sort step, slots keep their places
     d1 = line.diag()
     _, J = line.fields()
     r1 = line.rho()
     snap1 = device_sample(line, line.slots(), idx)
+    after = device_slots(line, n0, with_w=False)
+    total = charge_weighted_displacement(before, after, N)
+    del before, after
+    torch.cuda.empty_cache()
     line.close()
-    # every node: integer continuity
+    # every node: integer continuity, which fixes J up to one constant ...
     np.testing.assert_array_equal((r1 - r0)[1:N], -(J[1:N] - J[0:N - 1]))
+    # ... and the sum over cells (sum of q w times each path, clamped at the
+    # walls, over every particle) fixes that constant: J exact in every cell
+    assert int(J.sum()) == total, (int(J.sum()), total)
     # the particle count
     lost = (d1["lost_north"] - d0["lost_north"]) + (d1["lost_south"] - d0["lost_south"])
     created = d1["pairs_created"] - d0["pairs_created"]
@@ -236,11 +282,16 @@ def test_c2_line_one_step_every_particle():
     line = Line(cfg)
     line.set_state(st, E=E, step=7)
     line.step(1)
-    g = line.particles()
-    order = np.argsort(g["id"])
-    g = {k: v[order] for k, v in g.items()}
+    every = line.particles(alive_only=False)
+    keep = every["sp"] != 255
+    order = np.argsort(every["id"][keep])
+    g = {k: v[keep][order] for k, v in every.items()}
     dg = line.diag()
-    Eg, _ = line.fields()
+    Eg, J = line.fields()
     line.close()
     assert g["id"].size > 1.6e7 and dg["injected"] > 0
     compare_all_with_oracle(cfg, st, E, 7, g, dg, Eg)
+    # G3 at this size: the push's current in every cell (walls included) is
+    # the oracle's integer deposit of the step's paths
+    from deposit_ref import step_current
+    np.testing.assert_array_equal(J, step_current(st, every, N))
