@@ -37,10 +37,11 @@ S_BITS = 12
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle into ``oracle/liboracle.so`` (gcc, -O2, strict FP)."""
+    """Compile the oracle into ``oracle/liboracle.so`` (gcc, -O2, strict FP,
+    OpenMP for the step's particle blocks; one thread unless set_threads)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         subprocess.check_call(
-            ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math", "-ffp-contract=off",
+            ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math", "-ffp-contract=off", "-fopenmp",
              "-o", _LIB, _SRC, "-lm"])
     return _LIB
 
@@ -123,6 +124,8 @@ def lib():
             "orc_cos_dipole": (C.c_double, [C.c_double]),
             "orc_deposit_int": (None, [C.c_int, C.c_int, C.c_int64, _I64, _I64, _D, _I32, _I64]),
             "orc_step": (None, [C.c_void_p]),
+            "orc_set_threads": (None, [C.c_int]),
+            "orc_get_threads": (C.c_int, []),
             "orc_run": (None, [C.c_void_p, C.c_int64]),
             "orc_rho": (None, [C.c_void_p, _D]),
             "orc_get_diag": (None, [C.c_void_p, C.POINTER(OrcDiag)]),
@@ -160,6 +163,14 @@ def make_params(cfg: dict) -> OrcParams:
 
 
 # ---------------------------------------------------------------- functions
+def set_threads(n: int) -> int:
+    """Threads of the oracle's step (process-wide; results do not depend on
+    it: the step sums its particles in fixed blocks merged in order).
+    Returns the count in effect."""
+    lib().orc_set_threads(int(n))
+    return int(lib().orc_get_threads())
+
+
 def philox4x32_10(ctr, key):
     c = np.ascontiguousarray(ctr, dtype=np.uint32)
     k = np.ascontiguousarray(key, dtype=np.uint32)

@@ -997,7 +997,7 @@ void orc_drag_code(const orc_sim* S, double u, double s, double* F, double* dF, 
 /* One drag update over dt/2 at fixed s (Sec. 3): limiter test, then either
  * the implicit midpoint [implicit] by Newton or exponential damping to
  * p~ = mu/sqrt(1-mu^2). */
-static double orc_drag_half(orc_sim* S, double u0, double s)
+static double orc_drag_half_n(const orc_sim* S, double u0, double s, int64_t* n_newton, int64_t* n_limiter)
 {
   double h = 0.5 * S->dt;
   double F0, dF0;
@@ -1007,7 +1007,7 @@ static double orc_drag_half(orc_sim* S, double u0, double s)
    * p0 = 0 always takes the damping branch */
   if (S->tau_min > 0.0) newton = fabs(F0) * S->tau_min < fabs(u0);
   if (newton) {
-    S->d.newton_branch++;
+    (*n_newton)++;
     double u1 = u0 + h * F0;
     for (int it = 0; it < 4; ++it) {
       double F1, dF1;
@@ -1019,10 +1019,15 @@ static double orc_drag_half(orc_sim* S, double u0, double s)
     }
     return u1;
   }
-  S->d.limiter_branch++;
+  (*n_limiter)++;
   double mu = orc_node_interp(S, S->node_mu, s);
   double ut = mu / sqrt(1.0 - mu * mu);
   return ut + (u0 - ut) * exp(-h / S->tau_min);
+}
+
+static double orc_drag_half(orc_sim* S, double u0, double s)
+{
+  return orc_drag_half_n(S, u0, s, &S->d.newton_branch, &S->d.limiter_branch);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1068,7 +1073,7 @@ double orc_cos_dipole(double U)
 /* Charge-conserving deposit: the signed length of [a, b] inside every cell  */
 /* (the flux through that cell's E point), weighted by q w / dt.             */
 /* ------------------------------------------------------------------------ */
-static void orc_deposit_path(orc_sim* S, double a, double b, double qw)
+static void orc_deposit_path(const orc_sim* S, double* J, int* jlo, int* jhi, double a, double b, double qw)
 {
   double lo = fmin(a, b), hi = fmax(a, b);
   double sgn = (b >= a) ? 1.0 : -1.0;
@@ -1077,7 +1082,11 @@ static void orc_deposit_path(orc_sim* S, double a, double b, double qw)
   if (c0 < 0) c0 = 0;
   for (int c = c0; c <= c1; ++c) {
     double l = fmin(hi, (double)(c + 1)) - fmax(lo, (double)c);
-    if (l > 0.0) S->J[c] += sgn * qw * l * S->q_p / S->dt;
+    if (l > 0.0) {
+      J[c] += sgn * qw * l * S->q_p / S->dt;
+      if (c < *jlo) *jlo = c;
+      if (c > *jhi) *jhi = c;
+    }
   }
 }
 
@@ -1210,25 +1219,76 @@ static void orc_annihilate(orc_sim* S)
 /* ------------------------------------------------------------------------ */
 /* One PIC cycle (Sec. 3), n -> n+1.  E at integer times, u at half times.    */
 /* ------------------------------------------------------------------------ */
-void orc_step(orc_sim* S)
+/* The particles of a step are taken in fixed blocks of ORC_BLOCK; each block
+ * sums its current, tallies, lost energy and created particles on its own,
+ * and the blocks are merged in block order.  The result is then the same,
+ * bit for bit, whether the blocks run one after another or on several
+ * threads (orc_set_threads, an OpenMP build): the sums group the particles
+ * by block in both cases.  (Grouping a sum changes it only at rounding.) */
+#define ORC_BLOCK 4096
+
+static int orc_threads = 1;
+
+void orc_set_threads(int n) { orc_threads = n > 0 ? n : 1; }
+
+int orc_get_threads(void)
+{
+#ifdef _OPENMP
+  return orc_threads;
+#else
+  return 1;
+#endif
+}
+
+typedef struct {
+  double* J;                           /* N, zero outside [jlo, jhi] */
+  int jlo, jhi;
+  int64_t psc_clamped, scatters, lost_north, lost_south, pairs_lost_wall, pairs_rejected_nmax, pairs_created;
+  int64_t newton_branch, limiter_branch;
+  double ke_lost;
+  int64_t nc, ccap;                    /* created particles, in particle order */
+  double *cs, *cu, *cw;
+  int32_t* csp;
+  uint64_t* cid;
+} orc_acc;
+
+static void orc_acc_init(orc_acc* A, int N)
+{
+  memset(A, 0, sizeof(*A));
+  A->J = calloc(N, sizeof(double));
+  A->jlo = N; A->jhi = -1;
+  A->ccap = 256;
+  A->cs = malloc(A->ccap * sizeof(double)); A->cu = malloc(A->ccap * sizeof(double));
+  A->cw = malloc(A->ccap * sizeof(double)); A->csp = malloc(A->ccap * sizeof(int32_t));
+  A->cid = malloc(A->ccap * sizeof(uint64_t));
+}
+
+static void orc_acc_free(orc_acc* A)
+{
+  free(A->J); free(A->cs); free(A->cu); free(A->cw); free(A->csp); free(A->cid);
+}
+
+static void orc_acc_push(orc_acc* A, double s, double u, double w, int32_t sp, uint64_t id)
+{
+  if (A->nc + 1 > A->ccap) {
+    A->ccap *= 2;
+    A->cs = realloc(A->cs, A->ccap * sizeof(double)); A->cu = realloc(A->cu, A->ccap * sizeof(double));
+    A->cw = realloc(A->cw, A->ccap * sizeof(double)); A->csp = realloc(A->csp, A->ccap * sizeof(int32_t));
+    A->cid = realloc(A->cid, A->ccap * sizeof(uint64_t));
+  }
+  A->cs[A->nc] = s; A->cu[A->nc] = u; A->cw[A->nc] = w; A->csp[A->nc] = sp; A->cid[A->nc] = id;
+  A->nc++;
+}
+
+/* Steps 1-7 of the PIC cycle for particles [k0, k1) into A; writes their new
+ * s, u and alive flag. */
+static void orc_push_range(orc_sim* S, int64_t k0, int64_t k1, const uint32_t key[2], int64_t nmax_int,
+                           unsigned char* alive, orc_acc* A)
 {
   const orc_params* p = &S->p;
   int N = S->N;
   double dt = S->dt;
-  int64_t n0 = S->n;
-  /* created particles are collected here and appended at the end */
-  int64_t nc = 0, ccap = 1024;
-  double *cs = malloc(ccap * sizeof(double)), *cu = malloc(ccap * sizeof(double)), *cw = malloc(ccap * sizeof(double));
-  int32_t* csp = malloc(ccap * sizeof(int32_t));
-  uint64_t* cid = malloc(ccap * sizeof(uint64_t));
-  unsigned char* alive = malloc(n0 > 0 ? n0 : 1);
-  uint32_t key[2] = { (uint32_t)p->seed, (uint32_t)(p->seed >> 32) };
-  int64_t nmax_int = (p->n_max_ppc > 0.0) ? (int64_t)floor(p->n_max_ppc * (double)(1 << ORC_S_BITS)) : -1;
-  memset(S->J, 0, N * sizeof(double));
-  double E_old_sum_sq = 0.0;
-  for (int c = 0; c < N; ++c) E_old_sum_sq += S->E[c] * S->E[c];
-
-  for (int64_t k = 0; k < n0; ++k) {
+  for (int64_t k = k0; k < k1; ++k) {
     int sp = S->sp[k];
     double s = S->s[k], u = S->u[k], w = S->w[k];
     int lep = orc_is_lepton(sp);
@@ -1240,10 +1300,10 @@ void orc_step(orc_sim* S)
     /* 1. gather */
     double Ep = orc_gather(S, s);
     /* 2-4. Strang: drag dt/2, Lorentz kick dt, drag dt/2 */
-    if (cont) u = orc_drag_half(S, u, s);
+    if (cont) u = orc_drag_half_n(S, u, s, &A->newton_branch, &A->limiter_branch);
     if (S->grav_on) u += (orc_qm(S, sp) * Ep + orc_gather_at(S, S->grav, s) / orc_mass(S, sp)) * dt;
     else u += orc_qm(S, sp) * Ep * dt;
-    if (cont) u = orc_drag_half(S, u, s);
+    if (cont) u = orc_drag_half_n(S, u, s, &A->newton_branch, &A->limiter_branch);
     /* 5. Monte-Carlo RICS in the pair zone */
     int make_pair = 0;
     double Pg = 0.0;
@@ -1251,13 +1311,13 @@ void orc_step(orc_sim* S)
       double F, rate;
       orc_drag_code(S, u, s, &F, NULL, &rate);
       double psc = rate * dt;
-      if (psc > 1.0) { psc = 1.0; S->d.psc_clamped++; }
+      if (psc > 1.0) { psc = 1.0; A->psc_clamped++; }
       if (psc > 0.0) {
         uint32_t ctr[4] = { (uint32_t)S->id[k], (uint32_t)(S->id[k] >> 32), (uint32_t)S->step, ORC_TAG_RICS };
         uint32_t r[4];
         orc_philox4x32_10(ctr, key, r);
         if (orc_u24(r[0]) < psc) {
-          S->d.scatters++;
+          A->scatters++;
           double b = orc_node_interp(S, S->node_b, s);
           double mu = orc_node_interp(S, S->node_mu, s);
           double gam = sqrt(1.0 + u * u);
@@ -1276,37 +1336,89 @@ void orc_step(orc_sim* S)
     int lost = (s1 < 0.0) || (s1 >= (double)N);
     /* 7. deposit along the path, clamped at the conducting walls */
     double s1c = s1 < 0.0 ? 0.0 : (s1 > (double)N ? (double)N : s1);
-    orc_deposit_path(S, s, s1c, ORC_QS[sp] * w);
+    orc_deposit_path(S, A->J, &A->jlo, &A->jhi, s, s1c, ORC_QS[sp] * w);
     S->s[k] = s1;
     S->u[k] = u;
     alive[k] = !lost;
     if (lost) {
-      if (s1 < 0.0) S->d.lost_north++; else S->d.lost_south++;
-      S->d.ke_lost += S->q_p * w * orc_mass(S, sp) * (gam - 1.0);   /* energy carried out */
+      if (s1 < 0.0) A->lost_north++; else A->lost_south++;
+      A->ke_lost += S->q_p * w * orc_mass(S, sp) * (gam - 1.0);   /* energy carried out */
     }
     if (make_pair) {
-      if (lost) { S->d.pairs_lost_wall++; }
+      if (lost) { A->pairs_lost_wall++; }
       else {
         int pc = (int)floor(s1);
-        if (nmax_int >= 0 && S->dens[pc] >= nmax_int) { S->d.pairs_rejected_nmax++; }
+        if (nmax_int >= 0 && S->dens[pc] >= nmax_int) { A->pairs_rejected_nmax++; }
         else {
-          if (nc + 2 > ccap) {
-            ccap *= 2;
-            cs = realloc(cs, ccap * sizeof(double)); cu = realloc(cu, ccap * sizeof(double));
-            cw = realloc(cw, ccap * sizeof(double)); csp = realloc(csp, ccap * sizeof(int32_t));
-            cid = realloc(cid, ccap * sizeof(uint64_t));
-          }
-          for (int m = 0; m < 2; ++m) {
-            cs[nc] = s1; cu[nc] = 0.5 * Pg; cw[nc] = w;
-            csp[nc] = (m == 0) ? ORC_SP_ELEC : ORC_SP_POSI;
-            cid[nc] = orc_child_id(S->id[k], S->step, m);
-            nc++;
-          }
-          S->d.pairs_created++;
+          for (int m = 0; m < 2; ++m)
+            orc_acc_push(A, s1, 0.5 * Pg, w, (m == 0) ? ORC_SP_ELEC : ORC_SP_POSI, orc_child_id(S->id[k], S->step, m));
+          A->pairs_created++;
         }
       }
     }
   }
+}
+
+/* a block's sums into the step's (in block order), then A is cleared */
+static void orc_acc_merge(orc_sim* S, orc_acc* A, orc_acc* G)
+{
+  for (int c = A->jlo; c <= A->jhi; ++c) { S->J[c] += A->J[c]; A->J[c] = 0.0; }
+  A->jlo = S->N; A->jhi = -1;
+  S->d.psc_clamped += A->psc_clamped; S->d.scatters += A->scatters;
+  S->d.lost_north += A->lost_north; S->d.lost_south += A->lost_south;
+  S->d.pairs_lost_wall += A->pairs_lost_wall; S->d.pairs_rejected_nmax += A->pairs_rejected_nmax;
+  S->d.pairs_created += A->pairs_created;
+  S->d.newton_branch += A->newton_branch; S->d.limiter_branch += A->limiter_branch;
+  S->d.ke_lost += A->ke_lost;
+  for (int64_t i = 0; i < A->nc; ++i) orc_acc_push(G, A->cs[i], A->cu[i], A->cw[i], A->csp[i], A->cid[i]);
+  A->psc_clamped = A->scatters = A->lost_north = A->lost_south = 0;
+  A->pairs_lost_wall = A->pairs_rejected_nmax = A->pairs_created = 0;
+  A->newton_branch = A->limiter_branch = 0;
+  A->ke_lost = 0.0;
+  A->nc = 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One PIC cycle (Sec. 3), n -> n+1.  E at integer times, u at half times.    */
+/* ------------------------------------------------------------------------ */
+void orc_step(orc_sim* S)
+{
+  const orc_params* p = &S->p;
+  int N = S->N;
+  double dt = S->dt;
+  int64_t n0 = S->n;
+  unsigned char* alive = malloc(n0 > 0 ? n0 : 1);
+  uint32_t key[2] = { (uint32_t)p->seed, (uint32_t)(p->seed >> 32) };
+  int64_t nmax_int = (p->n_max_ppc > 0.0) ? (int64_t)floor(p->n_max_ppc * (double)(1 << ORC_S_BITS)) : -1;
+  memset(S->J, 0, N * sizeof(double));
+  /* created particles, collected in particle order and appended at the end */
+  orc_acc G;
+  orc_acc_init(&G, 1);
+  int64_t nblk = (n0 + ORC_BLOCK - 1) / ORC_BLOCK;
+  int nthr = orc_get_threads();
+  if (nthr > 1 && p->drag_law == ORC_DRAG_SURROGATE && !S->table) {
+    /* the surrogate's table fallback is built on first use: build it before
+     * the threads start */
+    S->table = malloc((size_t)2 * p->table_n_s * p->table_n_gamma * 2 * sizeof(double));
+    orc_build_table(p, S->table);
+  }
+#pragma omp parallel num_threads(nthr) if (nthr > 1 && nblk > 1)
+  {
+    orc_acc A;
+    orc_acc_init(&A, N);
+#pragma omp for ordered schedule(static, 1)
+    for (int64_t b = 0; b < nblk; ++b) {
+      int64_t k1 = (b + 1) * ORC_BLOCK < n0 ? (b + 1) * ORC_BLOCK : n0;
+      orc_push_range(S, b * ORC_BLOCK, k1, key, nmax_int, alive, &A);
+#pragma omp ordered
+      orc_acc_merge(S, &A, &G);
+    }
+    orc_acc_free(&A);
+  }
+  int64_t nc = G.nc;
+  double *cs = G.cs, *cu = G.cu, *cw = G.cw;
+  int32_t* csp = G.csp;
+  uint64_t* cid = G.cid;
 
   /* 8. Ampere with the external current: dE/dt = 4 pi (j_ext - J) */
   double E_new_sum = 0.0, E_old_sum = 0.0;
@@ -1316,7 +1428,6 @@ void orc_step(orc_sim* S)
     E_old_sum += Eo; E_new_sum += S->E[c];
   }
   S->d.ext_work += dt * S->j_ext * 0.5 * (E_old_sum + E_new_sum);
-  (void)E_old_sum_sq;
 
   /* 9. remove losses, append pairs then surface injection */
   int64_t* wcell = S->grav_on ? calloc(N, sizeof(int64_t)) : NULL;   /* plasma weight after the move */
@@ -1395,7 +1506,8 @@ void orc_step(orc_sim* S)
   S->step++;
   if (p->annihilate_every > 0 && p->n_max_ppc > 0.0 && S->step % p->annihilate_every == 0) orc_annihilate(S);
   orc_recount_density(S);
-  free(cs); free(cu); free(cw); free(csp); free(cid); free(alive);
+  orc_acc_free(&G);
+  free(alive);
 }
 
 void orc_run(orc_sim* S, int64_t steps) { for (int64_t i = 0; i < steps; ++i) orc_step(S); }

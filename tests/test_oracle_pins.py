@@ -643,3 +643,38 @@ def test_pair_yield_brute_force_tiny():
         p = bf[int(got["id"][k])]
         assert got["s"][k] == pytest.approx(p["s"], rel=1e-12, abs=1e-12)
         assert got["u"][k] == pytest.approx(p["u"], rel=1e-12, abs=1e-12)
+
+
+# ------------------------------------------------------------- threads
+def test_threaded_oracle_is_bit_identical_to_one_thread():
+    """The oracle's step sums its particles in fixed blocks merged in block
+    order, so running the blocks on several threads (the multi-core CPU
+    baseline) gives the one-thread result bit for bit: every particle, E, J
+    and every tally, over 12 steps of the C1 plasma with beams (scattering,
+    pairs, the pair cap, losses at both walls, the limiter in both branches,
+    RATE supply)."""
+    cfg = W.config("C1", rics_mode=O.RICS_DRAG_PLUS_PAIRS, n_max_ppc=40.0, inject_mode=O.INJECT_RATE)
+    N = cfg["n_cells"]
+    st = W.load_drifting_plasma(cfg)
+    beam = W.load_beam(cfg, 6000, gamma_lo=2.0, gamma_hi=3e4, seed=13)
+    beam["id"] += 10**7
+    st = {k: np.concatenate([st[k], beam[k]]) for k in st}
+    o = W.to_oracle(st, N)
+    runs = []
+    try:
+        for threads in (1, 4):
+            assert O.set_threads(threads) == threads
+            S = O.Sim(cfg)
+            S.set_particles(o["s"], o["u"], o["w"], o["sp"], o["id"])
+            S.step(12)
+            E, J = S.fields()
+            runs.append((S.particles(), E, J, S.diag()))
+    finally:
+        O.set_threads(1)
+    (p1, E1, J1, d1), (p4, E4, J4, d4) = runs
+    for k in ("s", "u", "w", "sp", "id"):
+        assert np.array_equal(p1[k], p4[k]), k
+    assert np.array_equal(E1, E4) and np.array_equal(J1, J4)
+    assert d1 == d4
+    assert d1["pairs_created"] > 0 and d1["limiter_branch"] > 0 and d1["newton_branch"] > 0
+    assert d1["lost_north"] > 0 and d1["lost_south"] > 0 and d1["pairs_rejected_nmax"] > 0
