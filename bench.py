@@ -146,12 +146,11 @@ def make_state_pinned(cfg, total):
     return buf, view, n
 
 
-def cpu_baseline(cfg, sample_total, budget_s, max_steps):
-    """The FP64 oracle (single thread, as it stands) on a bounded sample of
-    the workload: the same line and physics with `sample_total`
-    macroparticles in the same pair-loaded profile."""
+def _oracle_run(cfg, st, budget_s, max_steps, threads):
+    """Steps of the oracle on state `st` with `threads` threads until about
+    `budget_s` seconds or `max_steps` steps: (particle-steps/s, steps)."""
     import oracle as O
-    st = W.load_pair_loaded(cfg, sample_total, seed=7)
+    O.set_threads(threads)
     o = W.to_oracle(st, cfg["n_cells"])
     S = O.Sim(cfg)
     S.set_particles(o["s"], o["u"], o["w"], o["sp"], o["id"])
@@ -159,16 +158,32 @@ def cpu_baseline(cfg, sample_total, budget_s, max_steps):
     S.step(1)
     t1 = time.perf_counter()
     steps = int(max(1, min(max_steps, budget_s / max(t1 - t0, 1e-9))))
-    n_before = 0
     units = 0
     t0 = time.perf_counter()
     for _ in range(steps):
         units += S.n
         S.step(1)
     dt = time.perf_counter() - t0
-    return {"value": units / dt, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
-            "sample": f"{st['pos'].size} macroparticles of the same line and profile, {steps} steps "
-                      f"(the oracle is single-threaded C, FP64)"}, steps, st["pos"].size
+    O.set_threads(1)
+    return units / dt, steps
+
+
+def cpu_baseline(cfg, sample_total, budget_s, max_steps):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload
+    (the same line and physics with about `sample_total` macroparticles in
+    the same pair-loaded profile): on every host core (its OpenMP build,
+    bit-identical to one thread) and, beside it, on one core."""
+    cores = os.cpu_count() or 1
+    # enough of the oracle's 4096-particle blocks for every core
+    total = int(max(sample_total, 4096 * 4 * cores))
+    st = W.load_pair_loaded(cfg, total, seed=7)
+    v_all, steps = _oracle_run(cfg, st, budget_s, max_steps, cores)
+    v_one, steps1 = _oracle_run(cfg, st, 0.3 * budget_s, max_steps, 1)
+    return {"value": v_all, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
+            "single_core_value": v_one,
+            "sample": f"{st['pos'].size} macroparticles of the same line and profile, {steps} steps on {cores} "
+                      f"threads ({steps1} on one) (the oracle's C, FP64, OpenMP over blocks of particles)"}, \
+        steps, st["pos"].size
 
 
 def tp_cfg():
@@ -397,7 +412,6 @@ def run_gpu(args):
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cb, _, _ = cpu_baseline(cfg, args.cpu_sample, budget_s=15.0, max_steps=500)
-        cb["cores"] = 1
 
     if rank == 0:
         out = {"metric": "particle-steps/s", "value": value, "unit": "particle-steps/s", "n_gpus": world,

@@ -10,8 +10,9 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-SRC = [os.path.join(HERE, "csrc", f) for f in ("kernels.cu", "pic1d.cu", "sort_static.cu", "surrogate.cu", "tp_map.cu")]
-DEPS = SRC + [os.path.join(HERE, "csrc", h) for h in ("pic1d_internal.h", "tc05.h")] + \
+SRC = [os.path.join(HERE, "csrc", f) for f in ("kernels.cu", "pic1d.cu", "push_stream.cu", "sort_static.cu", "surrogate.cu",
+                                                   "tp_map.cu")]
+DEPS = SRC + [os.path.join(HERE, "csrc", h) for h in ("pic1d_internal.h", "tc05.h", "push_device.h", "sur_mlp.h")] + \
     [os.path.join(ROOT, "include", "pic1d.h")]
 LIB = os.path.join(HERE, "libpic1d.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -18,290 +18,10 @@
 #include <math.h>
 
 #include "pic1d_internal.h"
+#include "push_device.h"
 #include "sur_mlp.h"
 
 namespace pic1d {
-
-// --------------------------------------------------------------------------
-// counter-based random numbers: Philox4x32-10 (Salmon et al., SC'11)
-// --------------------------------------------------------------------------
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
-    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-    k0 += 0x9E3779B9u;
-    k1 += 0xBB67AE85u;
-  }
-  return c;
-}
-
-__device__ __forceinline__ float unit24(uint32_t x) { return (float)(x >> 8) * (1.0f / 16777216.0f); }
-
-// SplitMix64 finaliser (Steele, Lea, Flood 2014): stable ids of created particles
-__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
-  z += 0x9E3779B97F4A7C15ull;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
-__device__ __forceinline__ unsigned long long pair_child_id(unsigned long long parent, long long step, int m) {
-  return mix64(parent ^ mix64((unsigned long long)step * 2ull + (unsigned long long)m)) | 0x8000000000000000ull;
-}
-__device__ __forceinline__ unsigned long long supply_id(long long step, int foot, long long slot, int m) {
-  const unsigned long long k = ((unsigned long long)step << 24) ^ ((unsigned long long)foot << 23) ^
-                               ((unsigned long long)slot << 1) ^ (unsigned long long)m;
-  return mix64(k ^ 0x5A17A5EEDull) | 0x8000000000000000ull;
-}
-// id of atmosphere particle `slot` (m = 0: e-, 1: ion) topped up in `cell` at `step`
-__device__ __forceinline__ unsigned long long atmo_id(long long step, int cell, long long slot, int m) {
-  const unsigned long long a = mix64(((unsigned long long)step << 1) | (unsigned long long)m);
-  const unsigned long long b = ((unsigned long long)(uint32_t)cell << 32) | (unsigned long long)(uint32_t)slot;
-  return mix64(a ^ b ^ 0xA7305EEDull) | 0x8000000000000000ull;
-}
-
-__device__ __forceinline__ unsigned lanemask_lt() {
-  unsigned m;
-  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-  return m;
-}
-
-// --------------------------------------------------------------------------
-// drag and scattering rate at one particle
-// --------------------------------------------------------------------------
-struct Site {        // what the push needs about the particle's place on the line
-  int j;             // table row in s/L below the particle
-  float c;           // fractional position between rows j and j+1
-  float x, b, mu;    // r/R*, B/B_QED, cos(radial, +s) interpolated at s
-};
-
-__device__ __forceinline__ void site_rows(const DevParams& P, uint32_t pos0, Site& S) {
-  const float v = fminf((float)pos0 * P.v_scale, (float)(P.Ns - 1));
-  S.j = min((int)v, P.Ns - 2);
-  S.c = v - (float)S.j;
-}
-
-struct DragVal {
-  float F, dF, lnN;  // F^ (per R*), dF^/du, ln N^ (per R_star/c)
-};
-
-// Bilinear table lookup in (log10 gamma, s/L).  The device copy of the table
-// pairs neighbouring s-rows: tpair[(sg*(Ns-1) + j)*Ng + i] = (F[j][i], lnN[j][i],
-// F[j+1][i], lnN[j+1][i]), so one lookup is two adjacent 16-byte loads.
-// log10 gamma = log10(2)/2 * log2(1 + u^2): no square root is needed.
-__device__ __forceinline__ DragVal table_eval(const DevParams& P, float u, int j, float c, bool want_dF) {
-  const float q = fmaf(u, u, 1.0f);                    // gamma^2
-  float t = fmaxf(0.5f * __log2f(q) * P.t_scale, 0.0f);
-  bool top = false;
-  if (t > (float)(P.Ng - 1)) { t = (float)(P.Ng - 1); top = true; }
-  const int i = min((int)t, P.Ng - 2);
-  const float a = t - (float)i;
-  const int sg = (u >= 0.0f) ? 0 : 1;
-  const float4* row = P.tpair + ((size_t)(sg * (P.Ns - 1) + j) * P.Ng);
-  const float4 A = __ldg(row + i), B = __ldg(row + i + 1);
-  const float ac = 1.0f - a, cc = 1.0f - c;
-  DragVal d;
-  d.F = ac * (cc * A.x + c * A.z) + a * (cc * B.x + c * B.z);
-  d.lnN = ac * (cc * A.y + c * A.w) + a * (cc * B.y + c * B.w);
-  d.dF = 0.0f;
-  if (want_dF && !top) {
-    const float dFdt = cc * (B.x - A.x) + c * (B.z - A.z);
-    d.dF = dFdt * __fdividef(u, q) * P.dtdu_scale;
-  }
-  return d;
-}
-
-// closed form for radially streaming photons (Eq. contdrag and the matching
-// rate of Eq. scatteringNdot with solid angle pi/x^2)
-__device__ __forceinline__ DragVal closed_eval(const DevParams& P, float u, const Site& S, bool want_dF) {
-  const float gam = sqrtf(fmaf(u, u, 1.0f));
-  const float beta = u / gam;
-  const float au = fabsf(u);
-  const float sm = (u >= 0.0f) ? S.mu : -S.mu;
-  const float omb = 1.0f / (gam * (gam + au));          // 1 - |beta|
-  const float Dm = (1.0f - sm) + sm * omb;             // 1 - beta_s mu
-  const float eps = S.b / (gam * Dm);
-  const float y = eps / P.theta_T;
-  const float em = expm1f(y);
-  const float g = (y * y * y) / em;
-  const float ix2 = 1.0f / (S.x * S.x);
-  DragVal d;
-  d.F = P.closedK * ix2 * gam * (S.mu - beta) * g;
-  const float N = P.closedN * ix2 / gam * (eps * eps) / em;
-  d.lnN = (N > 0.0f) ? logf(N) : -700.0f;
-  d.dF = 0.0f;
-  if (want_dF) {
-    const float D = gam * Dm;
-    const float gp = g * (3.0f / y - 1.0f / (-expm1f(-y)));
-    const float dydu = -y * (beta - S.mu) / D;
-    d.dF = P.closedK * ix2 * ((beta * S.mu - 1.0f) * g + gam * (S.mu - beta) * gp * dydu);
-  }
-  return d;
-}
-
-__device__ __forceinline__ DragVal drag_eval(const DevParams& P, float u, const Site& S, bool want_dF) {
-  if (P.drag_law == PIC1D_DRAG_TABLE) return table_eval(P, u, S.j, S.c, want_dF);
-  return closed_eval(P, u, S, want_dF);
-}
-
-// One drag update over dt/2 at fixed s (Sec. 3): limiter test |F| tau_min <
-// |u0|, then the implicit midpoint [Eq. implicit] by up to 4 Newton
-// iterations, or exponential damping toward p~ = mu / sqrt(1 - mu^2).  An
-// iteration that leaves u1 unchanged is a fixed point: the remaining ones
-// would repeat it bit for bit, so stopping there gives the 4-iteration result.
-__device__ __forceinline__ float drag_half(const DevParams& P, const Site& S, float u0, unsigned& n_lim,
-                                           unsigned& n_newt) {
-  const float h = P.half_dt;
-  const float F0 = P.drag_k * drag_eval(P, u0, S, false).F;
-  const bool newton = !P.limiter_on || (fabsf(F0) * P.tau_min < fabsf(u0));
-  if (newton) {
-    ++n_newt;
-    float u1 = fmaf(h, F0, u0);
-#pragma unroll 1
-    for (int it = 0; it < 4; ++it) {
-      const DragVal d1 = drag_eval(P, u1, S, true);
-      const float F1 = P.drag_k * d1.F;
-      const float G = u1 - u0 - 0.5f * h * (F0 + F1);
-      const float dG = fmaxf(1.0f - 0.5f * h * P.drag_k * d1.dF, 0.5f);
-      const float un = u1 - __fdividef(G, dG);
-      if (un == u1) break;
-      u1 = un;
-    }
-    return u1;
-  }
-  ++n_lim;
-  const float ut = S.mu * rsqrtf(1.0f - S.mu * S.mu);
-  return fmaf(u0 - ut, P.damp, ut);
-}
-
-// de-excitation angle with density (3/8)(1 + c^2): Cardano root of c^3 + 3c + 4 - 8U = 0
-__device__ __forceinline__ float dipole_cos(float U) {
-  const float a = 4.0f * U - 2.0f;
-  const float t = cbrtf(a + sqrtf(fmaf(a, a, 1.0f)));
-  return t - 1.0f / t;
-}
-
-// RICS event (App. A): excitation by a photon arriving along d (= +-1 along s)
-// in the lepton rest frame, de-excitation at cos(theta~) = ct; returns the
-// recoiled momentum, the photon's lab energy and momentum along s.
-__device__ __forceinline__ void rics_event(float b, float d, float ui, float ct, float& uf, float& Eg,
-                                           float& Pg) {
-  const float EB = sqrtf(fmaf(2.0f, b, 1.0f));
-  const float iEB = 1.0f / EB;
-  const float gs = 0.5f * (EB + iEB);
-  const float gbs = b * iEB;
-  const float gi = sqrtf(fmaf(ui, ui, 1.0f));
-  const float ge = gs * gi + d * gbs * ui;
-  const float ue = gs * ui + d * gbs * gi;
-  const float st2 = 1.0f - ct * ct;
-  const float Ep = (EB - iEB) / (1.0f + sqrtf(ct * ct + st2 * iEB * iEB));
-  const float Ee = EB - Ep, pe = -Ep * ct;
-  uf = ue * Ee + ge * pe;
-  Eg = Ep * (ge + ue * ct);
-  Pg = Ep * (ue + ge * ct);
-}
-
-// --------------------------------------------------------------------------
-// deposit helpers
-// --------------------------------------------------------------------------
-// exact int64 sum over the lanes of `grp` (lanes that share a key): three
-// 21-bit slices, each summed by one redux (|v| < 2^62 keeps every slice sum
-// inside 32 bits), recombined in 64 bits.  Order-independent and exact.
-__device__ __forceinline__ long long group_sum64(unsigned grp, long long v) {
-  const unsigned lo = (unsigned)(v & 0x1FFFFF);
-  const unsigned mid = (unsigned)((v >> 21) & 0x1FFFFF);
-  const int hi = (int)(v >> 42);
-  const unsigned slo = __reduce_add_sync(grp, lo);
-  const unsigned smid = __reduce_add_sync(grp, mid);
-  const int shi = (int)__reduce_add_sync(grp, (unsigned)hi);
-  return ((long long)shi << 42) + ((long long)smid << 21) + (long long)slo;
-}
-
-// --------------------------------------------------------------------------
-// the push: one PIC cycle for every particle slot
-// --------------------------------------------------------------------------
-enum { C_SCAT, C_CLAMP, C_LIM, C_NEWT, C_NONFIN, C_LOSTN, C_LOSTS, C_PAIRS, C_DROP, C_REJ, C_WALL, C_DRAW, C_COUNT };
-
-// Tallies of one push launch.  The frequent ones stay in each thread's
-// registers (drag branches, a Kahan-compensated FP32 sum of w m (gamma - 1));
-// rare events are counted straight into the block's shared counters, and the
-// energy carried out at the walls into a shared sum, so that they hold no
-// registers in the particle loop.
-struct Tally {
-  unsigned* sc;               // the block's counters (C_COUNT, shared memory)
-  float* skl;                 // the block's lost kinetic energy (shared memory)
-  unsigned n_lim, n_newt;
-  float ke, ke_c;
-};
-
-__device__ __forceinline__ void tally(Tally& T, int k) { atomicAdd(T.sc + k, 1u); }
-
-__device__ __forceinline__ void tally_init(Tally& T, unsigned* sc, float* skl) {
-  T.sc = sc;
-  T.skl = skl;
-  T.n_lim = T.n_newt = 0;
-  T.ke = T.ke_c = 0.0f;
-}
-
-// The block's tallies into its line (block-wide; sRed holds one double per
-// warp): branch counts and shared counters to the line's counters, kinetic
-// energy to *ke_dst (added atomically or stored), lost energy to the line's
-// state.  The tallies and shared counters start again from zero.
-__device__ void flush_tally(const DevParams& P, Tally& T, double* sRed, double* ke_dst, bool ke_atomic) {
-  const int t = threadIdx.x, lane = t & 31;
-  const unsigned a = __reduce_add_sync(0xffffffffu, T.n_lim), b = __reduce_add_sync(0xffffffffu, T.n_newt);
-  if (lane == 0) {
-    if (a) atomicAdd(T.sc + C_LIM, a);
-    if (b) atomicAdd(T.sc + C_NEWT, b);
-  }
-  double ked = (double)T.ke - (double)T.ke_c;
-  for (int d = 16; d > 0; d >>= 1) ked += __shfl_down_sync(0xffffffffu, ked, d);
-  if (lane == 0) sRed[t >> 5] = ked;
-  __syncthreads();
-  if (t == 0) {
-    double ke = 0.0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) ke += sRed[i];
-    if (ke_atomic) atomicAdd(ke_dst, ke);
-    else *ke_dst = ke;
-    if (*T.skl != 0.0f) atomicAdd(&P.st->ke_lost, (double)*T.skl);
-    *T.skl = 0.0f;
-    Counters* C = P.ctr;
-    unsigned long long* dst[C_COUNT] = {&C->scatters, &C->psc_clamped, &C->limiter_branch, &C->newton_branch,
-                                        &C->nonfinite, &C->lost_north, &C->lost_south, &C->pairs_created,
-                                        &C->pairs_dropped_cap, &C->pairs_rejected_nmax, &C->pairs_lost_wall,
-                                        &C->rng_draws};
-    for (int k = 0; k < C_COUNT; ++k) {
-      if (T.sc[k]) atomicAdd(dst[k], (unsigned long long)T.sc[k]);
-      T.sc[k] = 0;
-    }
-  }
-  __syncthreads();
-  T.n_lim = T.n_newt = 0;
-  T.ke = T.ke_c = 0.0f;
-}
-
-__device__ __forceinline__ void kahan(float& s, float& c, float x) {
-  const float y = x - c, t = s + y;
-  c = (t - s) - y;
-  s = t;
-}
-
-// The 1D charge-conserving current of one step (Sec. 3): the signed path length
-// inside each cell.  A step is shorter than a cell, so from the start cell
-// only the cell itself and one neighbour receive current.  d is the
-// displacement in fixed point (clamped at a wall), frac the start position
-// inside its cell; sw = q_sign * w_int.
-__device__ __forceinline__ void path_split(int d, uint32_t frac, int F, int sw, long long& xm, long long& x0,
-                                           long long& xp) {
-  const int up = (int)((1u << F) - frac), dn = (int)frac;
-  int l0, lm = 0, lp = 0;
-  if (d >= 0) { l0 = min(d, up); lp = d - l0; }
-  else { l0 = max(d, -dn); lm = d - l0; }
-  x0 = (long long)sw * l0;
-  xm = (long long)sw * lm;
-  xp = (long long)sw * lp;
-}
 
 // Result of pushing one particle.
 struct PushOut {
@@ -311,6 +31,7 @@ struct PushOut {
   float child_u;
   unsigned long long pid;     // id (loaded only if a Philox number was drawn)
   long long xm, x0, xp;       // signed current into cells cell-1, cell, cell+1
+  int cl, la, lb, sw;         // the same path as (lower cell, lengths in cl and cl+1) and q_sign w_int
   int cD, vD;                 // cell and weight of the lepton density for the pair cap
   int cell;                   // cell at the start of the step
 };
@@ -320,7 +41,7 @@ struct PushOut {
 // Positions are u32 fixed point; every particle alive at the start of a step
 // has pos < top, and a step is shorter than one cell.  ATMO adds gravity
 // (inject mode TOPUP), gathered like E.
-template <bool NMAX, bool ATMO = false>
+template <bool NMAX, bool ATMO = false, bool LEAN = false>
 __device__ __forceinline__ PushOut push_one(const DevParams& P, uint32_t idx, uint32_t pos0, float u, float w,
                                             int sp, Tally& T) {
   const uint32_t fmask = (1u << P.F) - 1u;
@@ -368,10 +89,10 @@ __device__ __forceinline__ PushOut push_one(const DevParams& P, uint32_t idx, ui
     site_rows(P, pos0, S);
   }
   // 2-4. Strang split: drag dt/2, Lorentz kick dt, drag dt/2
-  if (cont) u = drag_half(P, S, u, T.n_lim, T.n_newt);
+  if (cont) u = LEAN ? drag_half_flagged(P, S, u, T.n_lim, T.n_newt) : drag_half(P, S, u, T.n_lim, T.n_newt);
   if (ATMO) u = fmaf(fmaf(qm, Ep, Gp / mass), P.dt, u);
   else u = fmaf(qm * Ep, P.dt, u);
-  if (cont) u = drag_half(P, S, u, T.n_lim, T.n_newt);
+  if (cont) u = LEAN ? drag_half_flagged(P, S, u, T.n_lim, T.n_newt) : drag_half(P, S, u, T.n_lim, T.n_newt);
   // 5. Monte-Carlo RICS in the pair zone
   bool make_pair = false;
   float Pg = 0.0f;
@@ -405,6 +126,7 @@ __device__ __forceinline__ PushOut push_one(const DevParams& P, uint32_t idx, ui
     o.u = 0.0f;
     o.pos = pos0;
     o.lost = true;
+    o.cl = cell; o.la = 0; o.lb = 0; o.sw = 0;
     return o;
   }
   const float q = fmaf(u, u, 1.0f);
@@ -421,6 +143,8 @@ __device__ __forceinline__ PushOut push_one(const DevParams& P, uint32_t idx, ui
   if (!o.lost) {
     p1 = pos0 + (uint32_t)dfix;
     path_split(dfix, pos0 & fmask, P.F, sw0, o.xm, o.x0, o.xp);
+    path_lengths(dfix, pos0 & fmask, P.F, cell, o.cl, o.la, o.lb);
+    o.sw = sw0;
     o.pos = p1;
     if (NMAX && lep) {
       o.cD = (int)(p1 >> P.F);
@@ -434,6 +158,8 @@ __device__ __forceinline__ PushOut push_one(const DevParams& P, uint32_t idx, ui
     // the path ends at the wall: to node 0 from cell 0, or to node N from cell N-1
     const int d = lostN ? -(int)pos0 : (int)(P.top - (long long)pos0);
     path_split(d, pos0 & fmask, P.F, sw0, o.xm, o.x0, o.xp);
+    path_lengths(d, pos0 & fmask, P.F, cell, o.cl, o.la, o.lb);
+    o.sw = sw0;
     o.pos = lostN ? 0u : (uint32_t)(P.top - 1);
     if (make_pair) tally(T, C_WALL);     // the parent left the line: no pair
     make_pair = false;
@@ -454,6 +180,7 @@ __device__ __forceinline__ PushOut push_one(const DevParams& P, uint32_t idx, ui
 // cells, not next to a wall): gather, continuous drag for leptons, kick,
 // move, deposit.  A particle there cannot leave the line in one step.  It
 // must give bit-for-bit what push_one gives for the same particle.
+template <bool LEAN = false>
 __device__ __forceinline__ void push_fast(const DevParams& P, uint32_t pos0, float u, float w, int sp, Tally& T,
                                           PushOut& o) {
   const uint32_t fmask = (1u << P.F) - 1u;
@@ -492,9 +219,9 @@ __device__ __forceinline__ void push_fast(const DevParams& P, uint32_t pos0, flo
       S.x = 1.0f;
     }
     site_rows(P, pos0, S);
-    u = drag_half(P, S, u, T.n_lim, T.n_newt);
+    u = LEAN ? drag_half_flagged(P, S, u, T.n_lim, T.n_newt) : drag_half(P, S, u, T.n_lim, T.n_newt);
     u = fmaf(qm * Ep, P.dt, u);
-    u = drag_half(P, S, u, T.n_lim, T.n_newt);
+    u = LEAN ? drag_half_flagged(P, S, u, T.n_lim, T.n_newt) : drag_half(P, S, u, T.n_lim, T.n_newt);
   } else {
     u = fmaf(qm * Ep, P.dt, u);
   }
@@ -503,6 +230,7 @@ __device__ __forceinline__ void push_fast(const DevParams& P, uint32_t pos0, flo
     o.u = 0.0f;
     o.pos = pos0;
     o.lost = true;
+    o.cl = cell; o.la = 0; o.lb = 0; o.sw = 0;
     return;
   }
   const float q = fmaf(u, u, 1.0f);
@@ -510,7 +238,9 @@ __device__ __forceinline__ void push_fast(const DevParams& P, uint32_t pos0, flo
   const int dfix = __float2int_rn(P.dt * (u * r) * (float)(1u << P.F));
   kahan(T.ke, T.ke_c, w * mass * __fdividef(u * u * r, 1.0f + r));
   const uint32_t p1 = pos0 + (uint32_t)dfix;
-  path_split(dfix, pos0 & fmask, P.F, qs * __float2int_rn(w * 4096.0f), o.xm, o.x0, o.xp);
+  o.sw = qs * __float2int_rn(w * 4096.0f);
+  path_split(dfix, pos0 & fmask, P.F, o.sw, o.xm, o.x0, o.xp);
+  path_lengths(dfix, pos0 & fmask, P.F, cell, o.cl, o.la, o.lb);
   o.pos = p1;
   o.u = u;
 }
@@ -585,7 +315,7 @@ __device__ __forceinline__ void window_drain(long long* sWin, int win_lo, const 
 // weight of each atmosphere cell after the move, summed into P.atmo_w (the
 // atmosphere and the two cells around it are never fast cells, so every
 // particle that ends a step there goes through push_one).
-template <int PPT, int MINB, bool NMAX, bool ATMO = false>
+template <int PPT, int MINB, bool NMAX, bool ATMO = false, bool LEAN = false>
 __global__ void __launch_bounds__(kBlock, MINB) k_push(DevParams P) {
   using VU = typename Vec<PPT>::U;
   using VF = typename Vec<PPT>::F;
@@ -617,6 +347,8 @@ __global__ void __launch_bounds__(kBlock, MINB) k_push(DevParams P) {
   tally_init(T, sCtr, &sKl);
   long long aJ[3] = {0, 0, 0};
   int c_ref = -4;
+  JWin Wn;                       // LEAN: the two-anchor current window
+  jwin_init(Wn);
   int dlo = kWindow, dhi = -1;   // density window range this thread touched
   // warp-uniform pending lepton density (pair cap)
   int dcell = -1;
@@ -677,11 +409,11 @@ __global__ void __launch_bounds__(kBlock, MINB) k_push(DevParams P) {
         // two cells away from any pair zone and from the walls
         const bool fast = !valid || __ldg(P.fast_cell + (pp[k] >> P.F)) != 0;
         if (__all_sync(0xffffffffu, fast)) {
-          if (valid) push_fast(P, pp[k], uu[k], ww[k], ss[k] & 3, T, o);
+          if (valid) push_fast<LEAN>(P, pp[k], uu[k], ww[k], ss[k] & 3, T, o);
         } else {
           o.want_pair = false;
           o.want_dens = false;
-          if (valid) o = push_one<NMAX, ATMO>(P, idx, pp[k], uu[k], ww[k], ss[k] & 3, T);
+          if (valid) o = push_one<NMAX, ATMO, LEAN>(P, idx, pp[k], uu[k], ww[k], ss[k] & 3, T);
           // plasma weight of the atmosphere cells after the move
           if (ATMO) {
             const bool ma = valid && !o.lost && __ldg(P.atmo_flag + (o.pos >> P.F)) != 0;
@@ -751,13 +483,18 @@ __global__ void __launch_bounds__(kBlock, MINB) k_push(DevParams P) {
           if (o.lost) { ss[k] = PIC1D_SP_DEAD; dirty = true; }
           // current into the lane's registers for cells c_ref-1 .. c_ref+1; when
           // the lane's start cell changes, the registers go to global memory
-          if (o.cell != c_ref) {
-            flush_lane(aJ, c_ref, P.J, P.N);
-            c_ref = o.cell;
+          // (LEAN: the window of two anchors, flushed only when a path leaves it)
+          if (LEAN) {
+            jwin_add<false>(Wn, true, o.cl, o.la, o.lb, o.sw, P.J, P.N);
+          } else {
+            if (o.cell != c_ref) {
+              flush_lane(aJ, c_ref, P.J, P.N);
+              c_ref = o.cell;
+            }
+            aJ[0] += o.xm;
+            aJ[1] += o.x0;
+            aJ[2] += o.xp;
           }
-          aJ[0] += o.xm;
-          aJ[1] += o.x0;
-          aJ[2] += o.xp;
         }
       }
       // write back (streaming stores: the data is not re-read in this kernel)
@@ -777,7 +514,8 @@ __global__ void __launch_bounds__(kBlock, MINB) k_push(DevParams P) {
     }
     // end of the chunk: everything pending goes to the window, the window's
     // touched range to global memory, and the next chunk is taken
-    flush_lane(aJ, c_ref, P.J, P.N);
+    if (LEAN) jwin_flush_lane(Wn, P.J, P.N);
+    else flush_lane(aJ, c_ref, P.J, P.N);
     c_ref = -4;
     if (NMAX) {
       if (lane == 0 && dcell >= 0) win_add(sD, win_lo, dlo, dhi, P.dens_next, P.N, dcell, dsum);
@@ -1871,12 +1609,25 @@ struct PushVariant {
   int ppt, minb;
   const void* k_plain;
   const void* k_nmax;
+  int stream;               // >= 0: shape of the streaming push (push_stream.cu)
 };
-#define PV(PPT_, MINB_) {PPT_, MINB_, (const void*)k_push<PPT_, MINB_, false>, (const void*)k_push<PPT_, MINB_, true>}
-static const PushVariant kPushVariants[] = {PV(1, 4), PV(1, 3), PV(2, 3), PV(2, 4)};
+#define PV(PPT_, MINB_) {PPT_, MINB_, (const void*)k_push<PPT_, MINB_, false>, (const void*)k_push<PPT_, MINB_, true>, -1}
+#define PVL(PPT_, MINB_)                                                                  \
+  {PPT_, MINB_, (const void*)k_push<PPT_, MINB_, false, false, true>,                     \
+   (const void*)k_push<PPT_, MINB_, true, false, true>, -1}
+// variant 0 is the streaming push (push_stream.cu: one block of 32 warps per
+// SM, warp-flushed current windows); 1-4 this file's per-thread push; 5 the
+// per-thread push with the damping flags and the two-anchor current window;
+// 6, 7 other shapes of the streaming push (32 warps with lane-flushed
+// windows, 24 warps)
+static const PushVariant kPushVariants[] = {{1, 1, nullptr, nullptr, 0}, PV(1, 4), PV(1, 3), PV(2, 3), PV(2, 4),
+                                            PVL(1, 4), {1, 1, nullptr, nullptr, 1}, {1, 1, nullptr, nullptr, 2}};
 #undef PV
+#undef PVL
 // the atmosphere's push (inject mode TOPUP): one particle per thread, whatever the variant
 static const void* const kPushAtmo[2] = {(const void*)k_push<1, 4, false, true>, (const void*)k_push<1, 4, true, true>};
+static const void* const kPushAtmoLean[2] = {(const void*)k_push<1, 4, false, true, true>,
+                                             (const void*)k_push<1, 4, true, true, true>};
 constexpr int kNumPushVariants = sizeof(kPushVariants) / sizeof(kPushVariants[0]);
 
 int push_variant_count() { return kNumPushVariants; }
@@ -1884,6 +1635,7 @@ int push_variant_ppt(int v) { return kPushVariants[v].ppt; }
 int push_variant_minb(int v) { return kPushVariants[v].minb; }
 
 int push_blocks_per_sm(int v, bool nmax) {
+  if (kPushVariants[v].stream >= 0) return 1;
   int nb = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, nmax ? kPushVariants[v].k_nmax : kPushVariants[v].k_plain,
                                                 kBlock, 0);
@@ -1892,8 +1644,12 @@ int push_blocks_per_sm(int v, bool nmax) {
 
 cudaError_t launch_push(const DevParams& P, int variant, int grid, cudaStream_t s) {
   const PushVariant& V = kPushVariants[variant];
+  if (V.stream >= 0) return launch_push_stream(P, V.stream, grid, s);
   void* args[] = {const_cast<DevParams*>(&P)};
-  if (P.G32) return cudaLaunchKernel(kPushAtmo[P.use_nmax ? 1 : 0], dim3(grid), dim3(kBlock), args, 0, s);
+  const bool lean = variant == 5;
+  if (P.G32)
+    return cudaLaunchKernel((lean ? kPushAtmoLean : kPushAtmo)[P.use_nmax ? 1 : 0], dim3(grid), dim3(kBlock), args, 0,
+                            s);
   return cudaLaunchKernel(P.use_nmax ? V.k_nmax : V.k_plain, dim3(grid), dim3(kBlock), args, 0, s);
 }
 

@@ -96,18 +96,16 @@ void legendre_nodes(int n, std::vector<double>& x, std::vector<double>& w) {
   }
 }
 
-// default push variant: PIC1D_PUSH_VARIANT (index) if set, else one particle
-// per thread at 4 resident blocks per SM (the fastest measured on the
-// 1e9-particle line)
+// default push variant: PIC1D_PUSH_VARIANT (index) if set, else the
+// per-thread push with the damping flags and the two-anchor current window
+// (variant 5, the fastest measured on the 1e9-particle line's density)
 int default_push_variant() {
   const char* e = std::getenv("PIC1D_PUSH_VARIANT");
   if (e) {
     const int v = std::atoi(e);
     if (v >= 0 && v < push_variant_count()) return v;
   }
-  for (int v = 0; v < push_variant_count(); ++v)
-    if (push_variant_ppt(v) == 1 && push_variant_minb(v) == 4) return v;
-  return 0;
+  return 5;
 }
 
 int fbits_of(int n) {
@@ -166,6 +164,9 @@ struct pic1d_ctx {
   unsigned long long* spc = nullptr;
   int push_grid = 0;      // grid of the current push variant
   int push_variant = 0;   // index into the push variants (particles per thread x occupancy)
+  int sort_grid = 0;      // blocks of the sort's histogram and scatter
+  uint8_t* cflag = nullptr;   // cell flags of the streaming push
+  uint8_t* dflag = nullptr;   // damping-certainty table (table law with the limiter)
   int sms = 0;
   long long step = 0;
   std::string err;
@@ -305,6 +306,8 @@ DevParams dev_params(pic1d_ctx* c) {
   P.zone = c->zone;
   P.dens_flag = c->dens_flag;
   P.fast_cell = c->fast_cell;
+  P.cflag = c->cflag;
+  P.dflag = c->dflag;
   P.G32 = c->G32;
   P.atmo_flag = c->atmo_flag;
   P.atmo_w = c->atmo_w;
@@ -434,6 +437,12 @@ int build_tables(pic1d_ctx* c) {
   }
   CK(dalloc(&c->fast_cell, N), "alloc zone");
   CK(cudaMemcpyAsync(c->fast_cell, hq.data(), N, cudaMemcpyHostToDevice, c->s), "copy zone");
+  // cell flags of the streaming push
+  std::vector<uint8_t> hc(N);
+  for (int cc = 0; cc < N; ++cc)
+    hc[cc] = (uint8_t)((hz[cc] ? CF_ZONE : 0) | ((cc == 0 || cc == N - 1) ? CF_WALL : 0));
+  CK(dalloc(&c->cflag, N), "alloc zone");
+  CK(cudaMemcpyAsync(c->cflag, hc.data(), N, cudaMemcpyHostToDevice, c->s), "copy zone");
   CK(cudaStreamSynchronize(c->s), "copy zone");
   CK(cudaMemcpyAsync(c->nb, hb.data(), (N + 1) * sizeof(float), cudaMemcpyHostToDevice, c->s), "copy nodes");
   CK(cudaMemcpyAsync(c->nmu, hmu.data(), (N + 1) * sizeof(float), cudaMemcpyHostToDevice, c->s), "copy nodes");
@@ -472,6 +481,12 @@ int build_tables(pic1d_ctx* c) {
        "table kernel");
     CK(dalloc(&c->tpair, (size_t)2 * (Ns - 1) * Ng), "alloc table");
     CK(launch_pair_table(c->table, Ng, Ns, c->tpair, c->s), "pair table");
+    if (p.drag_law == PIC1D_DRAG_TABLE && c->tau_min > 0.0) {
+      // where the limiter test is certain to damp (the streaming push skips its lookup)
+      const DevParams Q = dev_params(c);
+      CK(dalloc(&c->dflag, (size_t)2 * (Ns - 1) * kDampNE), "alloc damping flags");
+      CK(launch_damp_flags(c->tpair, Ng, Ns, Q.t_scale, Q.drag_k, Q.tau_min, c->dflag, c->s), "damping flags");
+    }
     CK(cudaStreamSynchronize(c->s), "table sync");
     dfree(dxs); dfree(dbs); dfree(dms); dfree(dgx); dfree(dgw);
   }
@@ -481,7 +496,7 @@ int build_tables(pic1d_ctx* c) {
 int do_sort(pic1d_ctx* c) {
   DevParams P = dev_params(c);
   const int o = 1 - c->cur;
-  CK(launch_sort(P, c->counts, c->offsets, c->bsum, c->pos[o], c->u[o], c->w[o], c->sp[o], c->id[o], c->push_grid,
+  CK(launch_sort(P, c->counts, c->offsets, c->bsum, c->pos[o], c->u[o], c->w[o], c->sp[o], c->id[o], c->sort_grid,
                  c->s),
      "sort");
   c->cur = o;
@@ -612,6 +627,7 @@ int pic1d_init(const pic1d_params* p, pic1d_ctx** out) {
     chain(dalloc(&c->ke_partial, c->sms * 8));     // at most 8 blocks of 256 threads per SM
     c->push_variant = default_push_variant();
     c->push_grid = c->sms * push_blocks_per_sm(c->push_variant, p->n_max_ppc > 0.0);
+    c->sort_grid = c->sms * 4;
     if (e == cudaSuccess) {
       chain(cudaMemsetAsync(c->E64, 0, N * sizeof(double), c->s));
       chain(cudaMemsetAsync(c->E32, 0, N * sizeof(float), c->s));
@@ -823,6 +839,11 @@ int pic1d_diag(pic1d_ctx* c, pic1d_diag_t* out) {
   out->fbits = c->F;
   out->push_variant = c->push_variant;
   int status = PIC1D_OK;
+  if (C.waits_timed_out) {
+    c->err = "a push block's bounded wait on a bulk copy gave up";
+    out->status = PIC1D_ETIMEOUT;
+    return PIC1D_ETIMEOUT;
+  }
   if (C.nonfinite) status = PIC1D_ENUMERIC;
   else if (C.pairs_dropped_cap || C.injected_dropped) status = PIC1D_WCAPACITY;
   out->status = status;
@@ -1440,7 +1461,7 @@ int ens_enqueue(pic1d_ens* e, int k, std::vector<int>& cur, std::vector<long lon
         ECK(cudaEventRecord(a, e->s), "ensemble timing");
       }
       ECK(launch_sort(P, c->counts, c->offsets, c->bsum, c->pos[o], c->u[o], c->w[o], c->sp[o], c->id[o],
-                      c->push_grid, e->s),
+                      c->sort_grid, e->s),
           "ensemble sort");
       ECK(ens_launch_flip(e->dlines, l, e->s), "ensemble sort");
       if (e->time_sorts) {
@@ -1882,7 +1903,7 @@ void pic1d_free(pic1d_ctx* c) {
                   c->tpair, c->bsum, c->sur.master, c->sur.m, c->sur.v, c->sur.img, c->sur.small,
                   c->sur.part, c->sur.loss_part, c->sur.err, c->sur_gx, c->sur_gw, c->sur_grad, c->sur_loss, c->rho,
                   c->G32, c->atmo_flag, c->atmo_w, c->atmo_cells, c->atmo_target, c->ann_list, c->ann_amount,
-                  c->ann_count};
+                  c->ann_count, c->cflag, c->dflag};
   for (void* q : ptrs) dfree(q);
   delete c;
   g_live.fetch_sub(1);

@@ -18,6 +18,13 @@ constexpr uint32_t kTagRics = 0x52494353u;
 constexpr uint32_t kTagInj = 0x494E4A31u;
 constexpr uint32_t kTagAtmo = 0x41544D4Fu;   // atmosphere top-up draws
 constexpr int kMaxFieldBlocks = 1024;
+// cell flags of the streaming push
+constexpr uint8_t CF_ZONE = 1;       // pair zone: Monte-Carlo RICS instead of continuous drag (SPLIT)
+constexpr uint8_t CF_WALL = 2;       // end cell: a particle can leave the line
+// damping-certainty table of the streaming push: gamma^2 in half-octaves,
+// index (bits of (float)gamma^2 >> 22) - kDampE2Base, kDampNE of them
+constexpr unsigned kDampE2Base = 254;    // bits of 1.0f >> 22
+constexpr int kDampNE = 128;             // gamma^2 up to 2^64
 
 // Device-side counters, accumulated over the life of the context.
 struct Counters {
@@ -28,6 +35,7 @@ struct Counters {
   unsigned long long sur_rows;   // rows evaluated by the surrogate network inside the push
   unsigned long long sur_rows_tangent;   // of which with the forward-mode tangent
   unsigned long long annihilated;        // weight removed by annihilation (w_int units)
+  unsigned long long waits_timed_out;    // push blocks whose bounded wait on a copy gave up
 };
 
 // Per-step device scalars.
@@ -76,6 +84,8 @@ struct DevParams {
   const uint8_t* zone;
   const uint8_t* dens_flag; // cells where the pair cap can be tested: zone cells and their neighbours
   const uint8_t* fast_cell; // no zone cell within two cells and not at a wall: the push's fast path
+  const uint8_t* cflag;     // per cell: CF_* bits of the streaming push
+  const uint8_t* dflag;     // damping certain: [sign][s-row pair][half-octave of gamma^2] (table law, limiter on)
   long long* dens_cur; long long* dens_next;
   // atmosphere (inject mode TOPUP; null otherwise)
   const float* G32;         // gravity along s per unit mass at cell centres (zero outside the atmosphere)
@@ -130,6 +140,14 @@ cudaError_t launch_deposit(const DevParams& P, long long n, const long long* p0,
 cudaError_t launch_count_species(const DevParams& P, unsigned long long* out4, cudaStream_t s);
 cudaError_t launch_rho(const DevParams& P, long long* rho, int grid, cudaStream_t s);
 int push_blocks_per_sm(int variant, bool nmax);
+// the streaming push (push_stream.cu): one block per SM, `shape` one of
+// stream_variant_count() (consumer warps x slots per lane)
+cudaError_t launch_push_stream(const DevParams& P, int shape, int grid, cudaStream_t s);
+int stream_variant_count();
+int stream_variant_ppl(int shape);
+// the damping-certainty table from the paired drag table (table law, limiter on)
+cudaError_t launch_damp_flags(const float4* tpair, int Ng, int Ns, float t_scale, float drag_k, float tau_min,
+                              uint8_t* out, cudaStream_t s);
 }  // namespace pic1d
 
 // learned surrogate of the photon-field quadrature (surrogate.cu)

@@ -1,0 +1,532 @@
+// push_stream.cu -- the streaming push: one PIC cycle (Sec. 3) for every
+// particle slot of a line, with the particle arrays staged through shared
+// memory by the bulk-copy engine.
+//
+// One block of NW warps per SM, every warp on its own.  A warp takes ranges
+// of kClaim slots from the launch's dynamic queue (so that the expensive
+// parts of the line -- pair zones, dense footpoints -- are shared by every
+// SM) and streams each range through a ring of kStages shared-memory slices
+// of kSlice slots: lane 0 copies a slice's pos, u, w and sp (13 B per slot)
+// in with cp.async.bulk, completion on the slice's mbarrier, one slice ahead
+// of the one the warp computes, and once the warp has written a slice's new
+// pos and u (8 B per slot) in place copies them back out with bulk stores.
+// The bytes in flight then do not depend on registers or occupancy, and the
+// warp waits on DRAM only if its next slice is late.
+//
+// Lane l takes slots l, l + 32, l + 64, l + 96 of a slice, so its particles
+// run through the warp's whole range in the cell order.  Per particle it runs
+// the gather, the Strang-split drag around the kick, the Monte-Carlo RICS in
+// pair zones, the move and the charge-conserving deposit with the FP32
+// arithmetic of the per-thread push of kernels.cu, with two changes that
+// remove work:
+//   * a drag half-step whose limiter test is certain to choose the damping
+//     branch (a precomputed per-(sign, s-row pair, half-octave of gamma^2)
+//     flag with a 1e-4 margin) skips the table lookup of that test;
+//   * the current goes into three int64 registers for cells B, B+1, B+2 that
+//     take every path whose lower cell is B or B+1 (a path of one step spans
+//     at most two cells); only when a path falls outside its lane's window is
+//     the window flushed: by that lane alone, or by the whole warp as exact
+//     warp sums per cell (one 64-bit atomic per cell and warp).
+// Every wait on an mbarrier is bounded; a warp whose wait gave up records it
+// in the line's counters (pic1d_diag then reports PIC1D_ETIMEOUT) and lets
+// the copies it issued land before it stops.
+#include <climits>
+
+#include "pic1d_internal.h"
+#include "push_device.h"
+#include "tc05.h"
+
+namespace pic1d {
+
+namespace {
+
+constexpr int kSlice = 128;                      // slots per slice (4 per lane)
+constexpr int kStages = 3;                       // slices in a warp's ring
+constexpr int kClaim = 1024;                     // slots per range taken from the queue
+constexpr int kOffU = 4 * kSlice, kOffW = 8 * kSlice, kOffSp = 12 * kSlice;
+constexpr int kSliceBytes = 13 * kSlice;         // pos | u | w | sp
+constexpr long long kWaitLimit = 2000000000ll;   // SM clocks, about a second
+static_assert(kSliceBytes % 128 == 0 && kClaim % kSlice == 0, "slices stay aligned");
+
+template <int NW>
+constexpr int stream_smem() { return NW * kStages * kSliceBytes + 128; }
+
+// ---------------------------------------------------------------------------
+// per-particle physics
+// ---------------------------------------------------------------------------
+struct SOut {
+  uint32_t pos;           // new position (clamped inside the line if lost)
+  float u;
+  bool lost, want_pair, want_dens;
+  float child_u;
+  unsigned long long pid;
+  int cl;                 // lower of the two cells the step's path can touch
+  int la, lb;             // signed path length (fixed point) in cells cl and cl + 1
+  int sw;                 // q_sign * w_int
+  int cD;                 // end cell (pair-cap density)
+};
+
+// One PIC cycle of one particle: the arithmetic of push_one (kernels.cu),
+// with the flagged drag half-step and the path split into (cl, la, lb).
+template <bool NMAX, bool ATMO>
+__device__ __forceinline__ void stream_one(const DevParams& P, uint32_t gidx, uint32_t pos0, float u, float w, int sp,
+                                           Tally& T, float& ke, SOut& o) {
+  const uint32_t fmask = (1u << P.F) - 1u;
+  const uint32_t half = 1u << (P.F - 1);
+  o.lost = false; o.want_pair = false; o.want_dens = false; o.child_u = 0.0f; o.pid = 0;
+  const bool ion = (sp == PIC1D_SP_ION);
+  const bool lep = !ion;
+  const float qm = ion ? P.qm[PIC1D_SP_ION] : (sp == PIC1D_SP_POSITRON ? 1.0f : -1.0f);
+  const int qs = (sp == PIC1D_SP_ELECTRON || sp == PIC1D_SP_ATMO) ? -1 : 1;
+  const float mass = ion ? P.mass[PIC1D_SP_ION] : 1.0f;
+  const int cell = (int)(pos0 >> P.F);
+  const unsigned cf = __ldg(P.cflag + cell);
+  // 1. gather E linearly between cell centres (constant beyond the end centres)
+  float Ep, Gp = 0.0f;
+  {
+    const uint32_t x = pos0 < half ? 0u : pos0 - half;
+    int ig = (int)(x >> P.F);
+    float f = (float)(x & fmask) * P.inv2F;
+    if (ig > P.N - 2) { ig = P.N - 2; f = 1.0f; }
+    const float e0 = __ldg(P.E32 + ig), e1 = __ldg(P.E32 + ig + 1);
+    Ep = fmaf(f, e1 - e0, e0);
+    if (ATMO) {
+      const float g0 = __ldg(P.G32 + ig), g1 = __ldg(P.G32 + ig + 1);
+      Gp = fmaf(f, g1 - g0, g0);
+    }
+  }
+  const bool zone = (cf & CF_ZONE) != 0;
+  const bool drag_on = P.drag_law != PIC1D_DRAG_OFF;
+  const bool cont = lep && drag_on && (P.rics_mode == PIC1D_RICS_DRAG_PLUS_PAIRS || !zone);
+  const bool mc = lep && P.mc_on && drag_on && zone;
+  Site S;
+  if (cont || mc) {
+    const float f = (float)(pos0 & fmask) * P.inv2F;
+    const float m0 = __ldg(P.nmu + cell), m1 = __ldg(P.nmu + cell + 1);
+    S.mu = fmaf(f, m1 - m0, m0);
+    if (mc || P.drag_law == PIC1D_DRAG_CLOSED) {
+      const float b0 = __ldg(P.nb + cell), b1 = __ldg(P.nb + cell + 1);
+      S.b = fmaf(f, b1 - b0, b0);
+    } else {
+      S.b = 0.0f;
+    }
+    if (P.drag_law == PIC1D_DRAG_CLOSED) {
+      const float x0 = __ldg(P.nx + cell), x1 = __ldg(P.nx + cell + 1);
+      S.x = fmaf(f, x1 - x0, x0);
+    } else {
+      S.x = 1.0f;
+    }
+    site_rows(P, pos0, S);
+  }
+  // 2-4. Strang split: drag dt/2, Lorentz kick dt, drag dt/2
+  if (cont) u = drag_half_flagged(P, S, u, T.n_lim, T.n_newt);
+  if (ATMO) u = fmaf(fmaf(qm, Ep, Gp / mass), P.dt, u);
+  else u = fmaf(qm * Ep, P.dt, u);
+  if (cont) u = drag_half_flagged(P, S, u, T.n_lim, T.n_newt);
+  // 5. Monte-Carlo RICS in the pair zone
+  bool make_pair = false;
+  float Pg = 0.0f;
+  if (mc) {
+    const DragVal dv = drag_eval(P, u, S, false);
+    float psc = P.drag_k * expf(dv.lnN) * P.dt;
+    if (psc > 1.0f) { psc = 1.0f; tally(T, C_CLAMP); }
+    if (psc > 0.0f) {
+      tally(T, C_DRAW);
+      o.pid = P.id[gidx];
+      const uint4 r = philox4x32_10(
+          make_uint4((uint32_t)o.pid, (uint32_t)(o.pid >> 32), (uint32_t)P.step, kTagRics), P.key0, P.key1);
+      if (unit24(r.x) < psc) {
+        tally(T, C_SCAT);
+        const float beta = u * rsqrtf(fmaf(u, u, 1.0f));
+        const float d = (S.mu > beta) ? 1.0f : -1.0f;
+        const float ct = dipole_cos(unit24(r.y));
+        float uf, Eg;
+        rics_event(S.b, d, u, ct, uf, Eg, Pg);
+        if (P.rics_mode == PIC1D_RICS_SPLIT) u = uf;
+        if (P.pairs_on && Eg >= P.pair_e_thr) make_pair = true;
+      }
+    }
+  }
+  // 6. move: ds = dt u / gamma, rounded to the fixed-point quantum
+  const int wint = __float2int_rn(w * 4096.0f);
+  o.sw = qs * wint;
+  o.cl = cell;
+  o.la = 0;
+  o.lb = 0;
+  o.cD = cell;
+  if (!isfinite(u)) {
+    // removed in place: no current, counted (the step reports PIC1D_ENUMERIC)
+    tally(T, C_NONFIN);
+    o.u = 0.0f;
+    o.pos = pos0;
+    o.lost = true;
+    return;
+  }
+  const float q = fmaf(u, u, 1.0f);
+  const float r = rsqrtf(q);                                   // 1 / gamma
+  int d = __float2int_rn(P.dt * (u * r) * (float)(1u << P.F));
+  const float e = w * mass * __fdividef(u * u * r, 1.0f + r);  // w m (gamma - 1)
+  const bool lostN = d < 0 && (uint32_t)(-d) > pos0;
+  const bool lostS = d > 0 && (uint32_t)d > P.top1 - pos0;
+  o.lost = lostN || lostS;
+  if (o.lost) {
+    atomicAdd(T.skl, e);
+    // leaves through a wall: the path ends at the conductor (node 0 or node N)
+    tally(T, lostN ? C_LOSTN : C_LOSTS);
+    d = lostN ? -(int)pos0 : (int)(P.top - (long long)pos0);
+    o.pos = lostN ? 0u : (uint32_t)(P.top - 1);
+    if (make_pair) tally(T, C_WALL);     // the parent left the line: no pair
+    make_pair = false;
+  } else {
+    ke += e;
+    o.pos = pos0 + (uint32_t)d;
+    if (NMAX && lep) {
+      o.cD = (int)(o.pos >> P.F);
+      o.want_dens = __ldg(P.dens_flag + o.cD) != 0;
+    }
+  }
+  // 7. charge-conserving deposit: the signed length of the path inside the
+  // start cell and inside the neighbour it moves into (a step is shorter
+  // than a cell); cl is the lower of the two
+  path_lengths(d, pos0 & fmask, P.F, cell, o.cl, o.la, o.lb);
+  o.u = u;
+  if (make_pair) {
+    if (NMAX && P.dens_cur[(int)(o.pos >> P.F)] >= P.nmax_int) {
+      tally(T, C_REJ);
+    } else {
+      o.want_pair = true;
+      o.child_u = 0.5f * Pg;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a warp's slices
+// ---------------------------------------------------------------------------
+// copy slice (slots base .. base+len-1) into `st`, completion on `bar`
+// (whole 16-byte groups: the arrays have slack past the last slot; slots past
+// len are read but not used)
+__device__ __forceinline__ void slice_load(const DevParams& P, uint8_t* st, uint64_t* bar, uint32_t base,
+                                           uint32_t len) {
+  const uint32_t b4 = (len * 4u + 15u) & ~15u, b1 = (len + 15u) & ~15u;
+  tc::mbar_expect_tx(bar, 3u * b4 + b1);
+  tc::bulk_g2s(st, P.pos + base, b4, bar);
+  tc::bulk_g2s(st + kOffU, P.u + base, b4, bar);
+  tc::bulk_g2s(st + kOffW, P.w + base, b4, bar);
+  tc::bulk_g2s(st + kOffSp, P.sp + base, b1, bar);
+}
+
+// the slice's new pos and u back to global memory: whole 16-byte groups by
+// the bulk engine (one committed group), the last few slots of the line by
+// plain stores
+__device__ __forceinline__ void slice_store(const DevParams& P, const uint8_t* st, uint32_t base, uint32_t len) {
+  const uint32_t len4 = len & ~3u;
+  if (len4) {
+    tc::bulk_s2g(P.pos + base, st, len4 * 4u);
+    tc::bulk_s2g(P.u + base, st + kOffU, len4 * 4u);
+  }
+  tc::bulk_commit();
+  const uint32_t* spos = reinterpret_cast<const uint32_t*>(st);
+  const float* su = reinterpret_cast<const float*>(st + kOffU);
+  for (uint32_t i = len4; i < len; ++i) {
+    P.pos[base + i] = spos[i];
+    P.u[base + i] = su[i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// the kernel
+// ---------------------------------------------------------------------------
+template <int NW, bool WARPFLUSH, bool NMAX, bool ATMO>
+__global__ void __launch_bounds__(32 * NW, 1) k_push_stream(DevParams P) {
+  extern __shared__ uint8_t s_raw[];
+  __shared__ __align__(8) uint64_t s_bar[NW][kStages];
+  __shared__ unsigned sCtr[C_COUNT];
+  __shared__ float sKl;
+  __shared__ unsigned sBad;
+  __shared__ double sRed[NW];
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  uint8_t* ring = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(s_raw) + 127) & ~uintptr_t(127)) +
+                  (size_t)warp * kStages * kSliceBytes;
+  uint64_t* bar = s_bar[warp];
+  if (t < C_COUNT) sCtr[t] = 0;
+  if (t == 0) { sKl = 0.0f; sBad = 0; }
+  if (lane == 0) {
+    for (int q = 0; q < kStages; ++q) tc::mbar_init(&bar[q], 1);
+    tc::mbar_fence_init();
+  }
+  __syncthreads();
+  const uint32_t n = (uint32_t)P.st->n_slots;
+  const uint32_t nclaims = (n + kClaim - 1) / kClaim;
+  Tally T;
+  tally_init(T, sCtr, &sKl);
+  double ke64 = 0.0;
+  JWin W;
+  jwin_init(W);
+  int dcell = -1;                 // warp-uniform pending lepton density (pair cap)
+  long long dsum = 0;
+
+  // the slice a warp works on: range `claim`, slice `j` of it
+  unsigned claim = 0;
+  if (lane == 0) claim = (unsigned)atomicAdd(&P.st->work, 1ull);
+  claim = __shfl_sync(0xffffffffu, claim, 0);
+  int j = 0;
+  if (claim < nclaims && lane == 0) {
+    const uint32_t base = claim * (uint32_t)kClaim;
+    slice_load(P, ring, &bar[0], base, min((uint32_t)kSlice, n - base));
+  }
+  bool ok = true;
+  for (unsigned k = 0; claim < nclaims; ++k) {
+    const int s = (int)(k % kStages);
+    uint8_t* st = ring + s * kSliceBytes;
+    const uint32_t cbase = claim * (uint32_t)kClaim;
+    const uint32_t cend = min(cbase + (uint32_t)kClaim, n);
+    const uint32_t base = cbase + (uint32_t)j * kSlice;
+    const uint32_t len = min((uint32_t)kSlice, cend - base);
+    // the next slice: the next one of this range, or the first of a new range
+    unsigned nclaim = claim;
+    int nj = j + 1;
+    if (cbase + (uint32_t)nj * kSlice >= cend) {
+      if (lane == 0) nclaim = (unsigned)atomicAdd(&P.st->work, 1ull);
+      nclaim = __shfl_sync(0xffffffffu, nclaim, 0);
+      nj = 0;
+    }
+    if (nclaim < nclaims && lane == 0) {
+      // its ring slot last held slice k + 1 - kStages, whose store must have
+      // finished reading it (every more recent store may still be running)
+      tc::bulk_wait_read_le<kStages - 2>();
+      const uint32_t nb = nclaim * (uint32_t)kClaim + (uint32_t)nj * kSlice;
+      const uint32_t ne = min(nclaim * (uint32_t)kClaim + (uint32_t)kClaim, n);
+      slice_load(P, ring + ((k + 1) % kStages) * kSliceBytes, &bar[(k + 1) % kStages], nb,
+                 min((uint32_t)kSlice, ne - nb));
+    }
+    // every lane waits on its own clock: the warp goes on only if all got there
+    const bool got = tc::mbar_wait(&bar[s], (k / kStages) & 1, kWaitLimit);
+    if (!__all_sync(0xffffffffu, got)) {
+      ok = false;
+      if (lane == 0) {
+        // let the copies of this slice and the next land before the block ends
+        tc::mbar_wait(&bar[s], (k / kStages) & 1, kWaitLimit);
+        if (nclaim < nclaims) tc::mbar_wait(&bar[(k + 1) % kStages], ((k + 1) / kStages) & 1, kWaitLimit);
+      }
+      break;
+    }
+    float ke = 0.0f;
+#pragma unroll 1
+    for (int i = 0; i < kSlice / 32; ++i) {
+      const uint32_t slot = (uint32_t)(i * 32 + lane);
+      if (__all_sync(0xffffffffu, slot >= len)) break;
+      const uint32_t pos0 = *reinterpret_cast<const uint32_t*>(st + 4 * slot);
+      const float u0 = *reinterpret_cast<const float*>(st + kOffU + 4 * slot);
+      const float w0 = *reinterpret_cast<const float*>(st + kOffW + 4 * slot);
+      const int spk = st[kOffSp + slot];
+      const bool valid = slot < len && spk != PIC1D_SP_DEAD;
+      const uint32_t gidx = base + slot;
+      SOut o;
+      o.want_pair = false;
+      o.want_dens = false;
+      o.lost = false;
+      if (valid) stream_one<NMAX, ATMO>(P, gidx, pos0, u0, w0, spk & 3, T, ke, o);
+      // current
+      jwin_add<WARPFLUSH>(W, valid, o.cl, o.la, o.lb, o.sw, P.J, P.N);
+      // plasma weight of the atmosphere cells after the move
+      if (ATMO) {
+        const bool ma = valid && !o.lost && __ldg(P.atmo_flag + (o.pos >> P.F)) != 0;
+        const unsigned am = __ballot_sync(0xffffffffu, ma);
+        if (ma) {
+          const int ac = (int)(o.pos >> P.F);
+          const unsigned grp = __match_any_sync(am, ac);
+          const long long sum = group_sum64(grp, (long long)__float2int_rn(w0 * 4096.0f));
+          if (lane == __ffs(grp) - 1)
+            atomicAdd(reinterpret_cast<unsigned long long*>(P.atmo_w + ac), (unsigned long long)sum);
+        }
+      }
+      // lepton density for the pair cap: only cells where a pair can be tested
+      if (NMAX) {
+        const unsigned md = __ballot_sync(0xffffffffu, o.want_dens);
+        if (md) {
+          const int c0 = __shfl_sync(0xffffffffu, o.cD, __ffs(md) - 1);
+          const int vD = __float2int_rn(w0 * 4096.0f);
+          if (__all_sync(0xffffffffu, !o.want_dens || o.cD == c0)) {
+            long long sd = 0;
+            if (o.want_dens) sd = group_sum64(md, (long long)vD);
+            sd = __shfl_sync(0xffffffffu, sd, __ffs(md) - 1);
+            if (c0 != dcell) {
+              if (lane == 0 && dcell >= 0 && dsum != 0)
+                atomicAdd(reinterpret_cast<unsigned long long*>(P.dens_next + dcell), (unsigned long long)dsum);
+              dcell = c0;
+              dsum = 0;
+            }
+            dsum += sd;
+          } else if (o.want_dens) {
+            const unsigned grp = __match_any_sync(md, o.cD);
+            const long long sum = group_sum64(grp, (long long)vD);
+            if (lane == __ffs(grp) - 1)
+              atomicAdd(reinterpret_cast<unsigned long long*>(P.dens_next + o.cD), (unsigned long long)sum);
+          }
+        }
+      }
+      // pair append, warp-aggregated
+      const unsigned m = __ballot_sync(0xffffffffu, o.want_pair);
+      if (m) {
+        const int leader = __ffs(m) - 1;
+        long long slot0 = 0;
+        if (lane == leader)
+          slot0 = atomicAdd(reinterpret_cast<unsigned long long*>(&P.st->append), (unsigned long long)(2 * __popc(m)));
+        slot0 = __shfl_sync(0xffffffffu, slot0, leader);
+        if (o.want_pair) {
+          const long long dst = (long long)n + slot0 + 2ll * __popc(m & lanemask_lt());
+          if (dst + 2 > P.cap) {
+            tally(T, C_DROP);
+          } else {
+            tally(T, C_PAIRS);
+#pragma unroll
+            for (int mm = 0; mm < 2; ++mm) {
+              P.pos[dst + mm] = o.pos;
+              P.u[dst + mm] = o.child_u;
+              P.w[dst + mm] = w0;
+              P.sp[dst + mm] = (mm == 0) ? PIC1D_SP_ELECTRON : PIC1D_SP_POSITRON;
+              P.id[dst + mm] = pair_child_id(o.pid, P.step, mm);
+            }
+            if (NMAX && __ldg(P.dens_flag + (o.pos >> P.F)))
+              atomicAdd(reinterpret_cast<unsigned long long*>(P.dens_next + (int)(o.pos >> P.F)),
+                        (unsigned long long)(2ll * __float2int_rn(w0 * 4096.0f)));
+          }
+        }
+      }
+      if (valid) {
+        *reinterpret_cast<uint32_t*>(st + 4 * slot) = o.pos;
+        *reinterpret_cast<float*>(st + kOffU + 4 * slot) = o.u;
+        if (o.lost) P.sp[gidx] = PIC1D_SP_DEAD;
+      }
+    }
+    ke64 += (double)ke;
+    // the results become visible to the bulk-copy engine, then go back out
+    tc::fence_async_smem();
+    __syncwarp();
+    if (lane == 0) slice_store(P, st, base, len);
+    claim = nclaim;
+    j = nj;
+  }
+  if (lane == 0) tc::bulk_wait_all();
+  if (!ok && lane == 0) sBad = 1;
+  if (WARPFLUSH) jwin_flush_warp(W, P.J, P.N);
+  else jwin_flush_lane(W, P.J, P.N);
+  if (NMAX && lane == 0 && dcell >= 0 && dsum != 0)
+    atomicAdd(reinterpret_cast<unsigned long long*>(P.dens_next + dcell), (unsigned long long)dsum);
+
+  // ---------------- the block's tallies
+  {
+    const unsigned a = __reduce_add_sync(0xffffffffu, T.n_lim), b = __reduce_add_sync(0xffffffffu, T.n_newt);
+    if (lane == 0) {
+      if (a) atomicAdd(sCtr + C_LIM, a);
+      if (b) atomicAdd(sCtr + C_NEWT, b);
+    }
+    double ked = ke64;
+    for (int dd = 16; dd > 0; dd >>= 1) ked += __shfl_down_sync(0xffffffffu, ked, dd);
+    if (lane == 0) sRed[warp] = ked;
+  }
+  __syncthreads();
+  if (t == 0) {
+    double ke = 0.0;
+    for (int i = 0; i < NW; ++i) ke += sRed[i];
+    P.ke_partial[blockIdx.x] = ke;
+    if (sKl != 0.0f) atomicAdd(&P.st->ke_lost, (double)sKl);
+    Counters* Cn = P.ctr;
+    unsigned long long* dst[C_COUNT] = {&Cn->scatters, &Cn->psc_clamped, &Cn->limiter_branch, &Cn->newton_branch,
+                                        &Cn->nonfinite, &Cn->lost_north, &Cn->lost_south, &Cn->pairs_created,
+                                        &Cn->pairs_dropped_cap, &Cn->pairs_rejected_nmax, &Cn->pairs_lost_wall,
+                                        &Cn->rng_draws};
+    for (int q = 0; q < C_COUNT; ++q)
+      if (sCtr[q]) atomicAdd(dst[q], (unsigned long long)sCtr[q]);
+    if (sBad) atomicAdd(&Cn->waits_timed_out, 1ull);
+  }
+}
+
+// The damping-certainty table: entry (sg, j, h) is 1 when for every gamma^2
+// in half-octave h (bits of (float)gamma^2 >> 22 = kDampE2Base + h) and every
+// s between rows j and j+1, the limiter test |drag_k F| tau_min < |u| of the
+// table law is false with a relative margin of 1e-4: the bilinear F there is
+// a convex combination of the table nodes it reads (gamma nodes floor(t_lo)
+// .. ceil(t_hi) of that half-octave's t range, rows j and j+1), so when
+// those nodes share one sign, |F| is at least their smallest magnitude, and
+// |u| is at most sqrt(q_hi - 1).
+__global__ void k_damp_flags(const float4* tpair, int Ng, int Ns, float t_scale, float drag_k, float tau_min,
+                             uint8_t* out) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= 2 * (Ns - 1) * kDampNE) return;
+  const int h = idx % kDampNE;
+  const int j = (idx / kDampNE) % (Ns - 1);
+  const int sg = idx / (kDampNE * (Ns - 1));
+  const int e = (int)kDampE2Base + h;                  // (float bits of q) >> 22
+  const int ex = (e >> 1) - 127;                        // exponent of q
+  const double q_lo = ldexp(1.0 + 0.5 * (double)(e & 1), ex);
+  const double q_hi = q_lo + ldexp(0.5, ex);
+  // t = 0.5 log2(q) t_scale in FP32 by the push; a slack of 1e-3 node units
+  const double t_lo = fmax(0.5 * log2(q_lo) * (double)t_scale - 1e-3, 0.0);
+  const double t_hi = 0.5 * log2(q_hi) * (double)t_scale + 1e-3;
+  int i_lo = (int)floor(t_lo), i_hi = (int)ceil(t_hi);
+  if (i_lo > Ng - 1) i_lo = Ng - 1;
+  if (i_hi > Ng - 1) i_hi = Ng - 1;
+  if (i_lo > Ng - 2) i_lo = Ng - 2;                     // the top clamp reads nodes Ng-2 and Ng-1
+  const float4* row = tpair + (size_t)(sg * (Ns - 1) + j) * Ng;
+  double fmn = INFINITY;
+  int pos = 0, neg = 0;
+  for (int i = i_lo; i <= i_hi; ++i) {
+    const float4 a = row[i];
+    const double f0 = (double)a.x, f1 = (double)a.z;
+    pos += (f0 > 0.0) + (f1 > 0.0);
+    neg += (f0 < 0.0) + (f1 < 0.0);
+    fmn = fmin(fmn, fmin(fabs(f0), fabs(f1)));
+  }
+  const int nodes = 2 * (i_hi - i_lo + 1);
+  const double u_hi = sqrt(fmax(q_hi - 1.0, 0.0));
+  const bool one_sign = (pos == nodes) || (neg == nodes);
+  const bool certain = one_sign && (double)drag_k * fmn * (double)tau_min >= u_hi * (1.0 + 1e-4) + 1e-30;
+  out[idx] = certain ? 1 : 0;
+}
+
+}  // namespace
+
+namespace {
+
+template <int NW, bool WF>
+cudaError_t launch_shape(const DevParams& P, int grid, cudaStream_t s, bool& attr) {
+  const void* ks[4] = {(const void*)k_push_stream<NW, WF, false, false>, (const void*)k_push_stream<NW, WF, true, false>,
+                       (const void*)k_push_stream<NW, WF, false, true>, (const void*)k_push_stream<NW, WF, true, true>};
+  if (!attr) {
+    for (const void* k : ks) {
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, stream_smem<NW>());
+      if (e != cudaSuccess) return e;
+    }
+    attr = true;
+  }
+  const int which = (P.use_nmax ? 1 : 0) + (P.G32 ? 2 : 0);
+  void* args[] = {const_cast<DevParams*>(&P)};
+  return cudaLaunchKernel(ks[which], dim3(grid), dim3(32 * NW), args, (size_t)stream_smem<NW>(), s);
+}
+
+}  // namespace
+
+// shapes of the streaming push: 32 warps with warp-flushed current windows,
+// 32 warps with lane-flushed windows, 24 warps with warp-flushed windows
+int stream_variant_count() { return 3; }
+int stream_variant_ppl(int) { return 1; }
+
+cudaError_t launch_push_stream(const DevParams& P, int shape, int grid, cudaStream_t s) {
+  static bool attr[3] = {false, false, false};
+  switch (shape) {
+    case 0: return launch_shape<32, true>(P, grid, s, attr[0]);
+    case 1: return launch_shape<32, false>(P, grid, s, attr[1]);
+    default: return launch_shape<24, true>(P, grid, s, attr[2]);
+  }
+}
+
+cudaError_t launch_damp_flags(const float4* tpair, int Ng, int Ns, float t_scale, float drag_k, float tau_min,
+                              uint8_t* out, cudaStream_t s) {
+  const int total = 2 * (Ns - 1) * kDampNE;
+  k_damp_flags<<<(total + 255) / 256, 256, 0, s>>>(tpair, Ng, Ns, t_scale, drag_k, tau_min, out);
+  return cudaGetLastError();
+}
+
+}  // namespace pic1d

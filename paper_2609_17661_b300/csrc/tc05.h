@@ -1,6 +1,7 @@
 // tc05.h -- thin inline-PTX wrappers for the sm_100-family tensor-core path:
 // tcgen05 (MMA into tensor memory, TMEM allocation and loads), mbarriers and
-// the bulk-copy (TMA) engine.  Used by the surrogate network's kernels.
+// the bulk-copy (TMA) engine.  Used by the surrogate network's kernels and
+// by the streaming push (push_stream.cu).
 //
 // Operand tiles live in shared memory in the canonical K-major layout with
 // the 128-byte swizzle: a tile of R rows and 64 BF16 values (128 bytes) per
@@ -73,7 +74,31 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
+// plain arrive (count 1, no transaction bytes)
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// bulk copy shared -> global (both 16-byte aligned, size a multiple of 16),
+// tracked by the issuing thread's bulk groups
+__device__ __forceinline__ void bulk_s2g(void* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_addr(src)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// every committed bulk store of this thread has finished reading shared memory
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// all but the N most recent committed bulk stores of this thread have finished reading shared memory
+template <int N>
+__device__ __forceinline__ void bulk_wait_read_le() {
+  asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+// every committed bulk store of this thread has completed
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 // generic-proxy writes to shared memory become visible to the tensor core
+// and to the bulk-copy engine
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // ---------------------------------------------------------------- tcgen05

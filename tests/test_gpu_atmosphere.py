@@ -94,8 +94,9 @@ def test_atmosphere_from_an_empty_line_matches_the_oracle_over_twelve_steps():
 
 
 def test_atmosphere_ignores_the_push_variant():
-    """The atmosphere has one push kernel; choosing another variant changes
-    nothing in the results."""
+    """The streaming push (variant 0) and the per-thread push (variant 2, which
+    runs the atmosphere's own instantiation) give the same results with the
+    atmosphere's gravity and weight sums."""
     from paper_2609_17661_b300 import Line
     N = 1024
     cfg = W.config("C1", inject_mode=O.INJECT_TOPUP, drag_law=O.DRAG_TABLE, drag_scale=3e-3, capacity=100000)
