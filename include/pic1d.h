@@ -258,6 +258,17 @@ int pic1d_deposit(pic1d_ctx* c, int64_t n, const int64_t* pos0, const int64_t* p
  * results.  Errors: ECUDA. */
 int pic1d_timing(pic1d_ctx* c, int on);
 
+/* Check of the library's failure path for device waits: runs, on the
+ * context's stream, the bounded wait that the push kernels use on their
+ * copies' mbarriers, on a barrier that nothing completes (no copy is issued,
+ * nothing arrives), with a limit of limit_clocks SM clocks (1 .. 4e9; at
+ * 2 GHz 2e6 clocks are a millisecond).  The wait gives up, is counted like a
+ * push block whose copy never landed, and the call returns PIC1D_OK once
+ * the kernel has ended; the next pic1d_diag then returns PIC1D_ETIMEOUT
+ * (the count restarts, so the one after it does not) and the context stays
+ * usable.  The paper has no counterpart.  Errors: EINVAL, ECUDA. */
+int pic1d_check_wait(pic1d_ctx* c, int64_t limit_clocks);
+
 /* Choose the push kernel variant: particles per thread (32- or 64-bit SoA
  * accesses) x minimum resident blocks per SM.  Results do not depend on the
  * variant (integer deposit, per-particle arithmetic).  Errors: EINVAL. */

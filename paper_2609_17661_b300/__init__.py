@@ -176,6 +176,10 @@ class Line:
         """pic1d_timing: bracket every push launch with CUDA events."""
         self._check(self.L.pic1d_timing(self.h, 1 if on else 0))
 
+    def check_wait(self, limit_clocks=2_000_000):
+        """pic1d_check_wait: a bounded device wait that nothing completes"""
+        self._check(self.L.pic1d_check_wait(self.h, int(limit_clocks)))
+
     def set_variant(self, v):
         """pic1d_set_variant: choose the push kernel variant."""
         self._check(self.L.pic1d_set_variant(self.h, int(v)))

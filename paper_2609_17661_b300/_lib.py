@@ -92,6 +92,7 @@ SIGNATURES = {
                                 C.c_void_p]),
     "pic1d_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "pic1d_set_variant": (C.c_int, [C.c_void_p, C.c_int]),
+    "pic1d_check_wait": (C.c_int, [C.c_void_p, C.c_int64]),
     "pic1d_variant_info": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "pic1d_sort_static": (C.c_int, [C.c_int32, C.c_int64] + [C.c_void_p] * 11 + [C.c_void_p]),
     "pic1d_set_allocator": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),

@@ -101,7 +101,7 @@ __device__ __forceinline__ PushOut push_one(const DevParams& P, uint32_t idx, ui
     float psc = P.drag_k * expf(dv.lnN) * P.dt;
     if (psc > 1.0f) { psc = 1.0f; tally(T, C_CLAMP); }
     if (psc > 0.0f) {
-      tally(T, C_DRAW);
+      ++T.n_draw;
       o.pid = P.id[idx];
       const uint4 r = philox4x32_10(
           make_uint4((uint32_t)o.pid, (uint32_t)(o.pid >> 32), (uint32_t)P.step, kTagRics), P.key0, P.key1);
@@ -722,7 +722,7 @@ __device__ void sur_tile(const DevParams& P, sur::MlpCta& M, uint32_t tile, uint
       float psc = P.drag_k * expf(dv.lnN) * P.dt;
       if (psc > 1.0f) { psc = 1.0f; tally(T, C_CLAMP); }
       if (psc > 0.0f) {
-        tally(T, C_DRAW);
+        ++T.n_draw;
         pid = P.id[idx];
         const uint4 r = philox4x32_10(
             make_uint4((uint32_t)pid, (uint32_t)(pid >> 32), (uint32_t)P.step, kTagRics), P.key0, P.key1);

@@ -463,32 +463,39 @@ int build_tables(pic1d_ctx* c) {
     }
     std::vector<double> gx, gw;
     legendre_nodes(std::max(1, p.quad_n_mu), gx, gw);
-    double *dxs, *dbs, *dms, *dgx, *dgw;
-    CK(dalloc(&dxs, Ns), "alloc quad");
-    CK(dalloc(&dbs, Ns), "alloc quad");
-    CK(dalloc(&dms, Ns), "alloc quad");
-    CK(dalloc(&dgx, gx.size()), "alloc quad");
-    CK(dalloc(&dgw, gw.size()), "alloc quad");
-    CK(cudaMemcpyAsync(dxs, xs.data(), Ns * sizeof(double), cudaMemcpyHostToDevice, c->s), "copy quad");
-    CK(cudaMemcpyAsync(dbs, bs.data(), Ns * sizeof(double), cudaMemcpyHostToDevice, c->s), "copy quad");
-    CK(cudaMemcpyAsync(dms, ms.data(), Ns * sizeof(double), cudaMemcpyHostToDevice, c->s), "copy quad");
-    CK(cudaMemcpyAsync(dgx, gx.data(), gx.size() * sizeof(double), cudaMemcpyHostToDevice, c->s), "copy quad");
-    CK(cudaMemcpyAsync(dgw, gw.data(), gw.size() * sizeof(double), cudaMemcpyHostToDevice, c->s), "copy quad");
-    CK(dalloc(&c->table, (size_t)2 * Ns * Ng), "alloc table");
-    const double pref = kRe * p.r_star_cm / (4.0 * kPi * kLbar * kLbar);
-    CK(launch_table(Ng, Ns, p.quad_n_mu, p.quad_n_phi, p.table_log10g_max, p.kT_keV / kMeKeV, pref, dxs, dbs, dms,
-                    dgx, dgw, p.photon_model, c->table, c->s),
-       "table kernel");
-    CK(dalloc(&c->tpair, (size_t)2 * (Ns - 1) * Ng), "alloc table");
-    CK(launch_pair_table(c->table, Ng, Ns, c->tpair, c->s), "pair table");
-    if (p.drag_law == PIC1D_DRAG_TABLE && c->tau_min > 0.0) {
-      // where the limiter test is certain to damp (the streaming push skips its lookup)
-      const DevParams Q = dev_params(c);
-      CK(dalloc(&c->dflag, (size_t)2 * (Ns - 1) * kDampNE), "alloc damping flags");
-      CK(launch_damp_flags(c->tpair, Ng, Ns, Q.t_scale, Q.drag_k, Q.tau_min, c->dflag, c->s), "damping flags");
-    }
-    CK(cudaStreamSynchronize(c->s), "table sync");
+    // the quadrature's inputs, freed on every way out
+    double *dxs = nullptr, *dbs = nullptr, *dms = nullptr, *dgx = nullptr, *dgw = nullptr;
+    auto table_build = [&]() -> int {
+      CK(dalloc(&dxs, Ns), "alloc quad");
+      CK(dalloc(&dbs, Ns), "alloc quad");
+      CK(dalloc(&dms, Ns), "alloc quad");
+      CK(dalloc(&dgx, gx.size()), "alloc quad");
+      CK(dalloc(&dgw, gw.size()), "alloc quad");
+      CK(cudaMemcpyAsync(dxs, xs.data(), Ns * sizeof(double), cudaMemcpyHostToDevice, c->s), "copy quad");
+      CK(cudaMemcpyAsync(dbs, bs.data(), Ns * sizeof(double), cudaMemcpyHostToDevice, c->s), "copy quad");
+      CK(cudaMemcpyAsync(dms, ms.data(), Ns * sizeof(double), cudaMemcpyHostToDevice, c->s), "copy quad");
+      CK(cudaMemcpyAsync(dgx, gx.data(), gx.size() * sizeof(double), cudaMemcpyHostToDevice, c->s), "copy quad");
+      CK(cudaMemcpyAsync(dgw, gw.data(), gw.size() * sizeof(double), cudaMemcpyHostToDevice, c->s), "copy quad");
+      CK(dalloc(&c->table, (size_t)2 * Ns * Ng), "alloc table");
+      const double pref = kRe * p.r_star_cm / (4.0 * kPi * kLbar * kLbar);
+      CK(launch_table(Ng, Ns, p.quad_n_mu, p.quad_n_phi, p.table_log10g_max, p.kT_keV / kMeKeV, pref, dxs, dbs,
+                      dms, dgx, dgw, p.photon_model, c->table, c->s),
+         "table kernel");
+      CK(dalloc(&c->tpair, (size_t)2 * (Ns - 1) * Ng), "alloc table");
+      CK(launch_pair_table(c->table, Ng, Ns, c->tpair, c->s), "pair table");
+      if (p.drag_law == PIC1D_DRAG_TABLE && c->tau_min > 0.0) {
+        // where the limiter test is certain to damp (the push skips its lookup)
+        const DevParams Q = dev_params(c);
+        CK(dalloc(&c->dflag, (size_t)2 * (Ns - 1) * kDampNE), "alloc damping flags");
+        CK(launch_damp_flags(c->tpair, Ng, Ns, Q.t_scale, Q.drag_k, Q.tau_min, c->dflag, c->s), "damping flags");
+      }
+      CK(cudaStreamSynchronize(c->s), "table sync");
+      return PIC1D_OK;
+    };
+    const int rc = table_build();
+    if (rc != PIC1D_OK) cudaStreamSynchronize(c->s);
     dfree(dxs); dfree(dbs); dfree(dms); dfree(dgx); dfree(dgw);
+    if (rc != PIC1D_OK) return rc;
   }
   return PIC1D_OK;
 }
@@ -840,7 +847,11 @@ int pic1d_diag(pic1d_ctx* c, pic1d_diag_t* out) {
   out->push_variant = c->push_variant;
   int status = PIC1D_OK;
   if (C.waits_timed_out) {
-    c->err = "a push block's bounded wait on a bulk copy gave up";
+    // reported once: the count restarts, the context stays usable
+    CK(cudaMemsetAsync(&c->ctr->waits_timed_out, 0, sizeof(unsigned long long), c->s), "diag");
+    CK(cudaStreamSynchronize(c->s), "diag sync");
+    c->err = "a push block's bounded wait on a bulk copy gave up (" + std::to_string(C.waits_timed_out) +
+             " blocks)";
     out->status = PIC1D_ETIMEOUT;
     return PIC1D_ETIMEOUT;
   }
@@ -896,6 +907,13 @@ int pic1d_deposit(pic1d_ctx* c, int64_t n, const int64_t* pos0, const int64_t* p
                     reinterpret_cast<long long*>(J), c->s),
      "deposit");
   CK(cudaStreamSynchronize(c->s), "deposit sync");
+  return PIC1D_OK;
+}
+
+int pic1d_check_wait(pic1d_ctx* c, int64_t limit_clocks) {
+  if (!c || limit_clocks < 1 || limit_clocks > (int64_t)4000000000ll) return PIC1D_EINVAL;
+  CK(launch_wait_check(c->ctr, (long long)limit_clocks, c->s), "check wait");
+  CK(cudaStreamSynchronize(c->s), "check wait");
   return PIC1D_OK;
 }
 

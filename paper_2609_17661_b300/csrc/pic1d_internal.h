@@ -144,6 +144,8 @@ int push_blocks_per_sm(int variant, bool nmax);
 // stream_variant_count() (consumer warps x slots per lane)
 cudaError_t launch_push_stream(const DevParams& P, int shape, int grid, cudaStream_t s);
 int stream_variant_count();
+// a bounded wait that nothing completes, for pic1d_check_wait
+cudaError_t launch_wait_check(Counters* ctr, long long limit_clocks, cudaStream_t s);
 int stream_variant_ppl(int shape);
 // the damping-certainty table from the paired drag table (table law, limiter on)
 cudaError_t launch_damp_flags(const float4* tpair, int Ng, int Ns, float t_scale, float drag_k, float tau_min,

@@ -229,7 +229,7 @@ enum { C_SCAT, C_CLAMP, C_LIM, C_NEWT, C_NONFIN, C_LOSTN, C_LOSTS, C_PAIRS, C_DR
 struct Tally {
   unsigned* sc;               // the block's counters (C_COUNT, shared memory)
   float* skl;                 // the block's lost kinetic energy (shared memory)
-  unsigned n_lim, n_newt;
+  unsigned n_lim, n_newt, n_draw;   // drag branches and Monte-Carlo draws, in registers
   float ke, ke_c;
 };
 
@@ -238,7 +238,7 @@ __device__ __forceinline__ void tally(Tally& T, int k) { atomicAdd(T.sc + k, 1u)
 __device__ __forceinline__ void tally_init(Tally& T, unsigned* sc, float* skl) {
   T.sc = sc;
   T.skl = skl;
-  T.n_lim = T.n_newt = 0;
+  T.n_lim = T.n_newt = T.n_draw = 0;
   T.ke = T.ke_c = 0.0f;
 }
 
@@ -249,9 +249,11 @@ __device__ __forceinline__ void tally_init(Tally& T, unsigned* sc, float* skl) {
 __device__ inline void flush_tally(const DevParams& P, Tally& T, double* sRed, double* ke_dst, bool ke_atomic) {
   const int t = threadIdx.x, lane = t & 31;
   const unsigned a = __reduce_add_sync(0xffffffffu, T.n_lim), b = __reduce_add_sync(0xffffffffu, T.n_newt);
+  const unsigned c = __reduce_add_sync(0xffffffffu, T.n_draw);
   if (lane == 0) {
     if (a) atomicAdd(T.sc + C_LIM, a);
     if (b) atomicAdd(T.sc + C_NEWT, b);
+    if (c) atomicAdd(T.sc + C_DRAW, c);
   }
   double ked = (double)T.ke - (double)T.ke_c;
   for (int d = 16; d > 0; d >>= 1) ked += __shfl_down_sync(0xffffffffu, ked, d);
@@ -275,7 +277,7 @@ __device__ inline void flush_tally(const DevParams& P, Tally& T, double* sRed, d
     }
   }
   __syncthreads();
-  T.n_lim = T.n_newt = 0;
+  T.n_lim = T.n_newt = T.n_draw = 0;
   T.ke = T.ke_c = 0.0f;
 }
 

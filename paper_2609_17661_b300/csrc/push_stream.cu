@@ -131,7 +131,7 @@ __device__ __forceinline__ void stream_one(const DevParams& P, uint32_t gidx, ui
     float psc = P.drag_k * expf(dv.lnN) * P.dt;
     if (psc > 1.0f) { psc = 1.0f; tally(T, C_CLAMP); }
     if (psc > 0.0f) {
-      tally(T, C_DRAW);
+      ++T.n_draw;
       o.pid = P.id[gidx];
       const uint4 r = philox4x32_10(
           make_uint4((uint32_t)o.pid, (uint32_t)(o.pid >> 32), (uint32_t)P.step, kTagRics), P.key0, P.key1);
@@ -418,9 +418,11 @@ __global__ void __launch_bounds__(32 * NW, 1) k_push_stream(DevParams P) {
   // ---------------- the block's tallies
   {
     const unsigned a = __reduce_add_sync(0xffffffffu, T.n_lim), b = __reduce_add_sync(0xffffffffu, T.n_newt);
+    const unsigned c = __reduce_add_sync(0xffffffffu, T.n_draw);
     if (lane == 0) {
       if (a) atomicAdd(sCtr + C_LIM, a);
       if (b) atomicAdd(sCtr + C_NEWT, b);
+      if (c) atomicAdd(sCtr + C_DRAW, c);
     }
     double ked = ke64;
     for (int dd = 16; dd > 0; dd >>= 1) ked += __shfl_down_sync(0xffffffffu, ked, dd);
@@ -520,6 +522,24 @@ cudaError_t launch_push_stream(const DevParams& P, int shape, int grid, cudaStre
     case 1: return launch_shape<32, false>(P, grid, s, attr[1]);
     default: return launch_shape<24, true>(P, grid, s, attr[2]);
   }
+}
+
+// The bounded wait of the push kernels on an mbarrier that nothing
+// completes (no copy, no arrive): it gives up after `limit` SM clocks and the
+// block records that in the line's counters, like a push block whose copy
+// never landed.
+__global__ void k_wait_check(Counters* ctr, long long limit) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::mbar_fence_init();
+    if (!tc::mbar_wait(&bar, 0, limit)) atomicAdd(&ctr->waits_timed_out, 1ull);
+  }
+}
+
+cudaError_t launch_wait_check(Counters* ctr, long long limit_clocks, cudaStream_t s) {
+  k_wait_check<<<1, 32, 0, s>>>(ctr, limit_clocks);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_damp_flags(const float4* tpair, int Ng, int Ns, float t_scale, float drag_k, float tau_min,

@@ -48,3 +48,44 @@ def test_torch_allocator_hooks():
         assert torch.cuda.memory_allocated() == base
     finally:
         use_torch_allocator(False)
+
+
+def test_allocator_that_refuses_gives_enomem():
+    """A caller's allocator that runs out (returns NULL) makes pic1d_init fail
+    with PIC1D_ENOMEM, after it has handed back every buffer it did get; the
+    process is left able to make lines again once the hooks are restored."""
+    import ctypes as C
+    import gc
+
+    from paper_2609_17661_b300 import Line, PicError, _lib
+    from paper_2609_17661_b300 import _ALLOC_FN, _FREE_FN
+    L = _lib.load()
+    gc.collect()
+    torch.cuda.synchronize()
+    given, freed = [], []
+    budget = [12]                      # the first 12 requests succeed, then the pool is "full"
+
+    def alloc(n, user):
+        if budget[0] <= 0:
+            return None
+        budget[0] -= 1
+        p = torch.cuda.caching_allocator_alloc(int(n))
+        given.append(p)
+        return p
+
+    def free(p, user):
+        freed.append(p)
+        torch.cuda.caching_allocator_delete(p)
+
+    hooks = (_ALLOC_FN(alloc), _FREE_FN(free))
+    assert L.pic1d_set_allocator(C.cast(hooks[0], C.c_void_p), C.cast(hooks[1], C.c_void_p), None) == 0
+    try:
+        with pytest.raises(PicError) as e:
+            Line(W.config("C1"))
+        assert e.value.code == -2                       # PIC1D_ENOMEM
+        assert budget[0] == 0 and len(given) == 12
+        assert sorted(freed) == sorted(given)           # nothing leaked
+    finally:
+        assert L.pic1d_set_allocator(None, None, None) == 0
+    line = Line(W.config("C1"))                         # cudaMalloc again
+    line.close()

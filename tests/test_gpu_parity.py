@@ -574,3 +574,25 @@ def test_invalid_state_rejected():
     good = {k: torch.from_numpy(v).cuda() for k, v in W.load_random(cfg, 10, seed=2).items()}
     line.set_state(good)
     assert line.slots() == 10
+
+
+def test_a_device_wait_that_gives_up_is_reported_and_the_line_goes_on():
+    """A bounded device wait on a barrier that nothing completes (no copy in
+    flight) gives up after its limit; the next pic1d_diag returns
+    PIC1D_ETIMEOUT once, and the line then steps on with correct results."""
+    cfg = W.config("C1", pairs_on=0)
+    st = W.load_drifting_plasma(cfg)
+    line = _line(cfg)
+    line.set_state(st)
+    assert line.diag()["rc"] == 0
+    line.check_wait(2_000_000)            # about a millisecond of SM clocks
+    d = line.diag()
+    assert d["rc"] == -5                  # PIC1D_ETIMEOUT
+    assert line.diag()["rc"] == 0         # reported once
+    line.step(5)
+    S = _orc(cfg, st)
+    S.step(5)
+    Eg, _ = line.fields()
+    Eo, _ = S.fields()
+    assert _relmax(Eg, Eo) <= RTOL
+    assert line.diag()["rc"] == 0
