@@ -1616,10 +1616,10 @@ struct PushVariant {
   {PPT_, MINB_, (const void*)k_push<PPT_, MINB_, false, false, true>,                     \
    (const void*)k_push<PPT_, MINB_, true, false, true>, -1}
 // variant 0 is the streaming push (push_stream.cu: one block of 32 warps per
-// SM, warp-flushed current windows); 1-4 this file's per-thread push; 5 the
-// per-thread push with the damping flags and the two-anchor current window;
-// 6, 7 other shapes of the streaming push (32 warps with lane-flushed
-// windows, 24 warps)
+// SM, lane-flushed current windows; the default); 1-4 this file's per-thread
+// push; 5 the per-thread push with the branch-certainty table and the
+// two-anchor current window; 6, 7 other shapes of the streaming push (32
+// warps with warp-flushed windows, 24 warps)
 static const PushVariant kPushVariants[] = {{1, 1, nullptr, nullptr, 0}, PV(1, 4), PV(1, 3), PV(2, 3), PV(2, 4),
                                             PVL(1, 4), {1, 1, nullptr, nullptr, 1}, {1, 1, nullptr, nullptr, 2}};
 #undef PV

@@ -97,15 +97,14 @@ void legendre_nodes(int n, std::vector<double>& x, std::vector<double>& w) {
 }
 
 // default push variant: PIC1D_PUSH_VARIANT (index) if set, else the
-// per-thread push with the damping flags and the two-anchor current window
-// (variant 5, the fastest measured on the 1e9-particle line's density)
+// streaming push (variant 0, the fastest measured on the 1e9-particle line)
 int default_push_variant() {
   const char* e = std::getenv("PIC1D_PUSH_VARIANT");
   if (e) {
     const int v = std::atoi(e);
     if (v >= 0 && v < push_variant_count()) return v;
   }
-  return 5;
+  return 0;
 }
 
 int fbits_of(int n) {
@@ -166,6 +165,7 @@ struct pic1d_ctx {
   int push_variant = 0;   // index into the push variants (particles per thread x occupancy)
   int sort_grid = 0;      // blocks of the sort's histogram and scatter
   uint8_t* cflag = nullptr;   // cell flags of the streaming push
+  float2* nmu2 = nullptr;     // mu at both nodes of each cell
   uint8_t* dflag = nullptr;   // damping-certainty table (table law with the limiter)
   int sms = 0;
   long long step = 0;
@@ -303,6 +303,7 @@ DevParams dev_params(pic1d_ctx* c) {
   P.J = c->J;
   P.tpair = c->tpair;
   P.nb = c->nb; P.nmu = c->nmu; P.nx = c->nx;
+  P.nmu2 = c->nmu2;
   P.zone = c->zone;
   P.dens_flag = c->dens_flag;
   P.fast_cell = c->fast_cell;
@@ -440,9 +441,15 @@ int build_tables(pic1d_ctx* c) {
   // cell flags of the streaming push
   std::vector<uint8_t> hc(N);
   for (int cc = 0; cc < N; ++cc)
-    hc[cc] = (uint8_t)((hz[cc] ? CF_ZONE : 0) | ((cc == 0 || cc == N - 1) ? CF_WALL : 0));
+    hc[cc] = (uint8_t)((hz[cc] ? CF_ZONE : 0) | ((cc == 0 || cc == N - 1) ? CF_WALL : 0) |
+                       ((hf[cc] || (cc > 0 && hf[cc - 1]) || (cc + 1 < N && hf[cc + 1])) ? CF_DENSN : 0));
   CK(dalloc(&c->cflag, N), "alloc zone");
   CK(cudaMemcpyAsync(c->cflag, hc.data(), N, cudaMemcpyHostToDevice, c->s), "copy zone");
+  std::vector<float2> hm2(N);
+  for (int cc = 0; cc < N; ++cc) hm2[cc] = make_float2(hmu[cc], hmu[cc + 1]);
+  CK(dalloc(&c->nmu2, N), "alloc nodes");
+  CK(cudaMemcpyAsync(c->nmu2, hm2.data(), N * sizeof(float2), cudaMemcpyHostToDevice, c->s), "copy nodes");
+  CK(cudaStreamSynchronize(c->s), "copy nodes");
   CK(cudaStreamSynchronize(c->s), "copy zone");
   CK(cudaMemcpyAsync(c->nb, hb.data(), (N + 1) * sizeof(float), cudaMemcpyHostToDevice, c->s), "copy nodes");
   CK(cudaMemcpyAsync(c->nmu, hmu.data(), (N + 1) * sizeof(float), cudaMemcpyHostToDevice, c->s), "copy nodes");
@@ -487,7 +494,8 @@ int build_tables(pic1d_ctx* c) {
         // where the limiter test is certain to damp (the push skips its lookup)
         const DevParams Q = dev_params(c);
         CK(dalloc(&c->dflag, (size_t)2 * (Ns - 1) * kDampNE), "alloc damping flags");
-        CK(launch_damp_flags(c->tpair, Ng, Ns, Q.t_scale, Q.drag_k, Q.tau_min, c->dflag, c->s), "damping flags");
+        CK(launch_damp_flags(c->tpair, Ng, Ns, Q.t_scale, Q.drag_k, Q.tau_min, Q.dt, c->dflag, c->s),
+           "damping flags");
       }
       CK(cudaStreamSynchronize(c->s), "table sync");
       return PIC1D_OK;
@@ -1921,7 +1929,7 @@ void pic1d_free(pic1d_ctx* c) {
                   c->tpair, c->bsum, c->sur.master, c->sur.m, c->sur.v, c->sur.img, c->sur.small,
                   c->sur.part, c->sur.loss_part, c->sur.err, c->sur_gx, c->sur_gw, c->sur_grad, c->sur_loss, c->rho,
                   c->G32, c->atmo_flag, c->atmo_w, c->atmo_cells, c->atmo_target, c->ann_list, c->ann_amount,
-                  c->ann_count, c->cflag, c->dflag};
+                  c->ann_count, c->cflag, c->dflag, c->nmu2};
   for (void* q : ptrs) dfree(q);
   delete c;
   g_live.fetch_sub(1);

@@ -21,6 +21,10 @@ constexpr int kMaxFieldBlocks = 1024;
 // cell flags of the streaming push
 constexpr uint8_t CF_ZONE = 1;       // pair zone: Monte-Carlo RICS instead of continuous drag (SPLIT)
 constexpr uint8_t CF_WALL = 2;       // end cell: a particle can leave the line
+constexpr uint8_t CF_DENSN = 4;      // a cell of the pair cap's density within one cell
+// entries of the branch-certainty table
+constexpr uint8_t kDampCertain = 1;  // the limiter test chooses damping
+constexpr uint8_t kNewtonStill = 2;  // it chooses Newton, whose update leaves u unchanged in FP32
 // damping-certainty table of the streaming push: gamma^2 in half-octaves,
 // index (bits of (float)gamma^2 >> 22) - kDampE2Base, kDampNE of them
 constexpr unsigned kDampE2Base = 254;    // bits of 1.0f >> 22
@@ -81,11 +85,12 @@ struct DevParams {
   long long* J;
   const float4* tpair;      // table with neighbouring s-rows paired
   const float* nb; const float* nmu; const float* nx;
+  const float2* nmu2;       // (mu[c], mu[c+1]) per cell
   const uint8_t* zone;
   const uint8_t* dens_flag; // cells where the pair cap can be tested: zone cells and their neighbours
   const uint8_t* fast_cell; // no zone cell within two cells and not at a wall: the push's fast path
   const uint8_t* cflag;     // per cell: CF_* bits of the streaming push
-  const uint8_t* dflag;     // damping certain: [sign][s-row pair][half-octave of gamma^2] (table law, limiter on)
+  const uint8_t* dflag;     // branch certain: [sign][s-row pair][half-octave of gamma^2] (table law, limiter on)
   long long* dens_cur; long long* dens_next;
   // atmosphere (inject mode TOPUP; null otherwise)
   const float* G32;         // gravity along s per unit mass at cell centres (zero outside the atmosphere)
@@ -149,7 +154,7 @@ cudaError_t launch_wait_check(Counters* ctr, long long limit_clocks, cudaStream_
 int stream_variant_ppl(int shape);
 // the damping-certainty table from the paired drag table (table law, limiter on)
 cudaError_t launch_damp_flags(const float4* tpair, int Ng, int Ns, float t_scale, float drag_k, float tau_min,
-                              uint8_t* out, cudaStream_t s);
+                              float dt, uint8_t* out, cudaStream_t s);
 }  // namespace pic1d
 
 // learned surrogate of the photon-field quadrature (surrogate.cu)

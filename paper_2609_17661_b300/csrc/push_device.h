@@ -314,11 +314,12 @@ __device__ __forceinline__ void path_lengths(int d, uint32_t frac, int F, int ce
   lb = neg ? l0 : ln;
 }
 
-// A drag half-step (drag_half) that first consults the damping-certainty
+// A drag half-step (drag_half) that first consults the branch-certainty
 // table (table law with the limiter): where the entry of this sign, s-row
 // pair and half-octave of gamma^2 is set, the limiter test would choose the
-// damping branch for every momentum there, so its table lookup is skipped;
-// the damping update is drag_half's.
+// damping branch for every momentum there (the damping update is
+// drag_half's), or the Newton branch with an update too small to change u in
+// FP32 (u is returned as it is), so the table lookup is skipped.
 __device__ __forceinline__ float drag_half_flagged(const DevParams& P, const Site& S, float u0, unsigned& n_lim,
                                                    unsigned& n_newt) {
   if (P.dflag) {
@@ -326,10 +327,15 @@ __device__ __forceinline__ float drag_half_flagged(const DevParams& P, const Sit
     const unsigned e2 = (__float_as_uint(q) >> 22) - kDampE2Base;
     if (e2 < (unsigned)kDampNE) {
       const int sg = (u0 >= 0.0f) ? 0 : 1;
-      if (__ldg(P.dflag + ((size_t)(sg * (P.Ns - 1) + S.j) * kDampNE + e2))) {
+      const unsigned f = __ldg(P.dflag + ((size_t)(sg * (P.Ns - 1) + S.j) * kDampNE + e2));
+      if (f == kDampCertain) {
         ++n_lim;
         const float ut = S.mu * rsqrtf(1.0f - S.mu * S.mu);
         return fmaf(u0 - ut, P.damp, ut);
+      }
+      if (f == kNewtonStill) {      // drag_half's Newton step would leave u0 as it is
+        ++n_newt;
+        return u0;
       }
     }
   }

@@ -13,7 +13,7 @@
 // The bytes in flight then do not depend on registers or occupancy, and the
 // warp waits on DRAM only if its next slice is late.
 //
-// Lane l takes slots l, l + 32, l + 64, l + 96 of a slice, so its particles
+// Lane l takes slots l, l + 32, ..., l + 224 of a slice, so its particles
 // run through the warp's whole range in the cell order.  Per particle it runs
 // the gather, the Strang-split drag around the kick, the Monte-Carlo RICS in
 // pair zones, the move and the charge-conserving deposit with the FP32
@@ -40,8 +40,8 @@ namespace pic1d {
 
 namespace {
 
-constexpr int kSlice = 128;                      // slots per slice (4 per lane)
-constexpr int kStages = 3;                       // slices in a warp's ring
+constexpr int kSlice = 256;                      // slots per slice (8 per lane)
+constexpr int kStages = 2;                       // slices in a warp's ring
 constexpr int kClaim = 1024;                     // slots per range taken from the queue
 constexpr int kOffU = 4 * kSlice, kOffW = 8 * kSlice, kOffSp = 12 * kSlice;
 constexpr int kSliceBytes = 13 * kSlice;         // pos | u | w | sp
@@ -65,6 +65,19 @@ struct SOut {
   int sw;                 // q_sign * w_int
   int cD;                 // end cell (pair-cap density)
 };
+
+// A RICS scattering of this lane's lepton (App. A): recoil in SPLIT mode,
+// true when its photon makes a pair.  Out of line: a few lanes in a million
+// scatter, and the others should not carry its arithmetic.
+__device__ __noinline__ bool rics_scatter(const DevParams& P, const Site& S, uint32_t ry, float& u, float& Pg) {
+  const float beta = u * rsqrtf(fmaf(u, u, 1.0f));
+  const float d = (S.mu > beta) ? 1.0f : -1.0f;
+  const float ct = dipole_cos(unit24(ry));
+  float uf, Eg;
+  rics_event(S.b, d, u, ct, uf, Eg, Pg);
+  if (P.rics_mode == PIC1D_RICS_SPLIT) u = uf;
+  return P.pairs_on && Eg >= P.pair_e_thr;
+}
 
 // One PIC cycle of one particle: the arithmetic of push_one (kernels.cu),
 // with the flagged drag half-step and the path split into (cl, la, lb).
@@ -102,8 +115,8 @@ __device__ __forceinline__ void stream_one(const DevParams& P, uint32_t gidx, ui
   Site S;
   if (cont || mc) {
     const float f = (float)(pos0 & fmask) * P.inv2F;
-    const float m0 = __ldg(P.nmu + cell), m1 = __ldg(P.nmu + cell + 1);
-    S.mu = fmaf(f, m1 - m0, m0);
+    const float2 mm = __ldg(P.nmu2 + cell);
+    S.mu = fmaf(f, mm.y - mm.x, mm.x);
     if (mc || P.drag_law == PIC1D_DRAG_CLOSED) {
       const float b0 = __ldg(P.nb + cell), b1 = __ldg(P.nb + cell + 1);
       S.b = fmaf(f, b1 - b0, b0);
@@ -137,13 +150,7 @@ __device__ __forceinline__ void stream_one(const DevParams& P, uint32_t gidx, ui
           make_uint4((uint32_t)o.pid, (uint32_t)(o.pid >> 32), (uint32_t)P.step, kTagRics), P.key0, P.key1);
       if (unit24(r.x) < psc) {
         tally(T, C_SCAT);
-        const float beta = u * rsqrtf(fmaf(u, u, 1.0f));
-        const float d = (S.mu > beta) ? 1.0f : -1.0f;
-        const float ct = dipole_cos(unit24(r.y));
-        float uf, Eg;
-        rics_event(S.b, d, u, ct, uf, Eg, Pg);
-        if (P.rics_mode == PIC1D_RICS_SPLIT) u = uf;
-        if (P.pairs_on && Eg >= P.pair_e_thr) make_pair = true;
+        make_pair = rics_scatter(P, S, r.y, u, Pg);
       }
     }
   }
@@ -180,7 +187,7 @@ __device__ __forceinline__ void stream_one(const DevParams& P, uint32_t gidx, ui
   } else {
     ke += e;
     o.pos = pos0 + (uint32_t)d;
-    if (NMAX && lep) {
+    if (NMAX && lep && (cf & CF_DENSN)) {
       o.cD = (int)(o.pos >> P.F);
       o.want_dens = __ldg(P.dens_flag + o.cD) != 0;
     }
@@ -263,8 +270,9 @@ __global__ void __launch_bounds__(32 * NW, 1) k_push_stream(DevParams P) {
   double ke64 = 0.0;
   JWin W;
   jwin_init(W);
-  int dcell = -1;                 // warp-uniform pending lepton density (pair cap)
-  long long dsum = 0;
+  // the pair cap's lepton density of this lane: cells Dc and Dc + 1
+  int Dc = -(1 << 29);
+  long long D0 = 0, D1 = 0;
 
   // the slice a warp works on: range `claim`, slice `j` of it
   unsigned claim = 0;
@@ -341,30 +349,20 @@ __global__ void __launch_bounds__(32 * NW, 1) k_push_stream(DevParams P) {
             atomicAdd(reinterpret_cast<unsigned long long*>(P.atmo_w + ac), (unsigned long long)sum);
         }
       }
-      // lepton density for the pair cap: only cells where a pair can be tested
-      if (NMAX) {
-        const unsigned md = __ballot_sync(0xffffffffu, o.want_dens);
-        if (md) {
-          const int c0 = __shfl_sync(0xffffffffu, o.cD, __ffs(md) - 1);
-          const int vD = __float2int_rn(w0 * 4096.0f);
-          if (__all_sync(0xffffffffu, !o.want_dens || o.cD == c0)) {
-            long long sd = 0;
-            if (o.want_dens) sd = group_sum64(md, (long long)vD);
-            sd = __shfl_sync(0xffffffffu, sd, __ffs(md) - 1);
-            if (c0 != dcell) {
-              if (lane == 0 && dcell >= 0 && dsum != 0)
-                atomicAdd(reinterpret_cast<unsigned long long*>(P.dens_next + dcell), (unsigned long long)dsum);
-              dcell = c0;
-              dsum = 0;
-            }
-            dsum += sd;
-          } else if (o.want_dens) {
-            const unsigned grp = __match_any_sync(md, o.cD);
-            const long long sum = group_sum64(grp, (long long)vD);
-            if (lane == __ffs(grp) - 1)
-              atomicAdd(reinterpret_cast<unsigned long long*>(P.dens_next + o.cD), (unsigned long long)sum);
-          }
+      // lepton density for the pair cap (only cells where a pair can be
+      // tested): two registers per lane, to global memory when a lepton ends
+      // outside them
+      if (NMAX && o.want_dens) {
+        const int kd = o.cD - Dc;
+        if ((unsigned)kd > 1u) {
+          if (D0) atomicAdd(reinterpret_cast<unsigned long long*>(P.dens_next + Dc), (unsigned long long)D0);
+          if (D1) atomicAdd(reinterpret_cast<unsigned long long*>(P.dens_next + Dc + 1), (unsigned long long)D1);
+          D0 = D1 = 0;
+          Dc = (o.cD > Dc) ? o.cD - 1 : o.cD;
         }
+        const long long vD = (long long)__float2int_rn(w0 * 4096.0f);
+        if (o.cD == Dc) D0 += vD;
+        else D1 += vD;
       }
       // pair append, warp-aggregated
       const unsigned m = __ballot_sync(0xffffffffu, o.want_pair);
@@ -412,8 +410,10 @@ __global__ void __launch_bounds__(32 * NW, 1) k_push_stream(DevParams P) {
   if (!ok && lane == 0) sBad = 1;
   if (WARPFLUSH) jwin_flush_warp(W, P.J, P.N);
   else jwin_flush_lane(W, P.J, P.N);
-  if (NMAX && lane == 0 && dcell >= 0 && dsum != 0)
-    atomicAdd(reinterpret_cast<unsigned long long*>(P.dens_next + dcell), (unsigned long long)dsum);
+  if (NMAX) {
+    if (D0) atomicAdd(reinterpret_cast<unsigned long long*>(P.dens_next + Dc), (unsigned long long)D0);
+    if (D1) atomicAdd(reinterpret_cast<unsigned long long*>(P.dens_next + Dc + 1), (unsigned long long)D1);
+  }
 
   // ---------------- the block's tallies
   {
@@ -445,15 +445,18 @@ __global__ void __launch_bounds__(32 * NW, 1) k_push_stream(DevParams P) {
   }
 }
 
-// The damping-certainty table: entry (sg, j, h) is 1 when for every gamma^2
+// The branch-certainty table: entry (sg, j, h) is kDampCertain when for every gamma^2
 // in half-octave h (bits of (float)gamma^2 >> 22 = kDampE2Base + h) and every
 // s between rows j and j+1, the limiter test |drag_k F| tau_min < |u| of the
 // table law is false with a relative margin of 1e-4: the bilinear F there is
 // a convex combination of the table nodes it reads (gamma nodes floor(t_lo)
 // .. ceil(t_hi) of that half-octave's t range, rows j and j+1), so when
 // those nodes share one sign, |F| is at least their smallest magnitude, and
-// |u| is at most sqrt(q_hi - 1).
-__global__ void k_damp_flags(const float4* tpair, int Ng, int Ns, float t_scale, float drag_k, float tau_min,
+// |u| is at most sqrt(q_hi - 1).  It is kNewtonStill when the test is
+// certain to choose the Newton branch there and that branch's update moves u
+// by less than a quarter of the FP32 spacing of the smallest |u| of the
+// half-octave, so that the half-step returns u unchanged.
+__global__ void k_damp_flags(const float4* tpair, int Ng, int Ns, float t_scale, float drag_k, float tau_min, float dt,
                              uint8_t* out) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= 2 * (Ns - 1) * kDampNE) return;
@@ -481,11 +484,26 @@ __global__ void k_damp_flags(const float4* tpair, int Ng, int Ns, float t_scale,
     neg += (f0 < 0.0) + (f1 < 0.0);
     fmn = fmin(fmn, fmin(fabs(f0), fabs(f1)));
   }
+  double fmx = 0.0;
+  for (int i = i_lo; i <= i_hi; ++i) {
+    const float4 a = row[i];
+    fmx = fmax(fmx, fmax(fabs((double)a.x), fabs((double)a.z)));
+  }
   const int nodes = 2 * (i_hi - i_lo + 1);
-  const double u_hi = sqrt(fmax(q_hi - 1.0, 0.0));
+  const double u_lo = sqrt(fmax(q_lo - 1.0, 0.0)), u_hi = sqrt(fmax(q_hi - 1.0, 0.0));
   const bool one_sign = (pos == nodes) || (neg == nodes);
-  const bool certain = one_sign && (double)drag_k * fmn * (double)tau_min >= u_hi * (1.0 + 1e-4) + 1e-30;
-  out[idx] = certain ? 1 : 0;
+  const bool damp = one_sign && (double)drag_k * fmn * (double)tau_min >= u_hi * (1.0 + 1e-4) + 1e-30;
+  // Newton branch with a change below a quarter of the FP32 spacing at u_lo:
+  // |u1 - u0| <= h |F| / (1 - h F'/2) <= 2 h |F| (the denominator is at least
+  // 1/2), so u0 + (u1 - u0) rounds to u0
+  bool still = false;
+  if (!damp && u_lo > 0.0) {
+    const double fk = (double)drag_k * fmx * (1.0 + 1e-3);
+    const double h = 0.5 * (double)dt;
+    const double ulp = ldexp(1.0, ilogb(u_lo) - 23);
+    still = fk * (double)tau_min < u_lo * (1.0 - 1e-4) && 2.0 * h * fk <= 0.25 * ulp;
+  }
+  out[idx] = damp ? kDampCertain : (still ? kNewtonStill : 0);
 }
 
 }  // namespace
@@ -510,16 +528,17 @@ cudaError_t launch_shape(const DevParams& P, int grid, cudaStream_t s, bool& att
 
 }  // namespace
 
-// shapes of the streaming push: 32 warps with warp-flushed current windows,
-// 32 warps with lane-flushed windows, 24 warps with warp-flushed windows
+// shapes of the streaming push: 32 warps with lane-flushed current windows
+// (the fastest measured), 32 warps with warp-flushed windows, 24 warps with
+// warp-flushed windows
 int stream_variant_count() { return 3; }
 int stream_variant_ppl(int) { return 1; }
 
 cudaError_t launch_push_stream(const DevParams& P, int shape, int grid, cudaStream_t s) {
   static bool attr[3] = {false, false, false};
   switch (shape) {
-    case 0: return launch_shape<32, true>(P, grid, s, attr[0]);
-    case 1: return launch_shape<32, false>(P, grid, s, attr[1]);
+    case 0: return launch_shape<32, false>(P, grid, s, attr[0]);
+    case 1: return launch_shape<32, true>(P, grid, s, attr[1]);
     default: return launch_shape<24, true>(P, grid, s, attr[2]);
   }
 }
@@ -543,9 +562,9 @@ cudaError_t launch_wait_check(Counters* ctr, long long limit_clocks, cudaStream_
 }
 
 cudaError_t launch_damp_flags(const float4* tpair, int Ng, int Ns, float t_scale, float drag_k, float tau_min,
-                              uint8_t* out, cudaStream_t s) {
+                              float dt, uint8_t* out, cudaStream_t s) {
   const int total = 2 * (Ns - 1) * kDampNE;
-  k_damp_flags<<<(total + 255) / 256, 256, 0, s>>>(tpair, Ng, Ns, t_scale, drag_k, tau_min, out);
+  k_damp_flags<<<(total + 255) / 256, 256, 0, s>>>(tpair, Ng, Ns, t_scale, drag_k, tau_min, dt, out);
   return cudaGetLastError();
 }
 
