@@ -138,6 +138,22 @@ typedef struct pic1d_params {
   double j_psi;             /* j_ext / (n0 e c)                         */
   double n0_ppc;            /* weight per cell that represents n0       */
   double mass_ratio;        /* m_i / m_e (ion charge +1)                */
+  /* initial plasma (Sec. 3: a pair plasma of multiplicity M drifting at
+   * beta = -+1/M, the twist current's carriers), loaded by pic1d_init when
+   * ppc_e > 0: per cell ppc_e electrons at stratified positions (electron k
+   * of cell c in [c + k/ppc_e, c + (k+1)/ppc_e), from one Philox4x32-10 draw
+   * with counter (c, k, 0, 'INIT') and key = seed), positrons on the
+   * positions of its first ppc_p electrons and ions on the next ppc_i
+   * (ppc_p + ppc_i = ppc_e: every node neutral), weight 1, momenta Gaussian
+   * with spread u_sigma in each species' own m c around -u_d (electrons),
+   * +u_d (positrons) and 0 (ions), u_d = beta_d / sqrt(1 - beta_d^2),
+   * beta_d = 1 / init_multiplicity; the Gaussian of particle k of species m
+   * (0 e-, 1 e+, 2 ion) in cell c is Box-Muller on words 1 and 2 of the draw
+   * (c, k, m, 'INIT').  Slots and ids: electrons cell by cell, then the
+   * positrons, then the ions. */
+  int32_t ppc_e, ppc_p, ppc_i;
+  double init_multiplicity; /* M (> 1)                                  */
+  double u_sigma;           /* spread of the initial momenta (>= 0)     */
   /* supply and pairs */
   int32_t inject_mode;      /* PIC1D_INJECT_*                           */
   double inject_T;          /* temperature of injected particles, m_e c^2 */

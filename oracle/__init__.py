@@ -56,6 +56,8 @@ class OrcParams(C.Structure):
         ("eta_min", C.c_double), ("rics_mode", C.c_int32), ("mc_on", C.c_int32),
         ("cells_per_skin_depth", C.c_double), ("j_psi", C.c_double), ("n0_ppc", C.c_double),
         ("mass_ratio", C.c_double),
+        ("ppc_e", C.c_int32), ("ppc_p", C.c_int32), ("ppc_i", C.c_int32), ("init_multiplicity", C.c_double),
+        ("u_sigma", C.c_double),
         ("inject_mode", C.c_int32), ("inject_T", C.c_double),
         ("atmo_a0", C.c_double), ("atmo_h", C.c_double), ("atmo_ncut", C.c_double),
         ("pairs_on", C.c_int32), ("b_pair_threshold", C.c_double), ("pair_energy_threshold", C.c_double),

@@ -85,6 +85,7 @@ enum { ORC_SP_ELEC = 0, ORC_SP_POSI = 1, ORC_SP_ION = 2, ORC_SP_ATMO = 3 };
 #define ORC_TAG_RICS 0x52494353u   /* counter word 3 of the scattering draw */
 #define ORC_TAG_INJ  0x494E4A31u   /* counter word 3 of the injection draw  */
 #define ORC_TAG_ATM  0x41544D4Fu   /* counter word 3 of the atmosphere draw */
+#define ORC_TAG_INIT 0x494E4954u   /* counter word 3 of the initial load    */
 #define ORC_S_BITS   12            /* weight fixed point: w_int = rint(w*2^12) */
 
 typedef struct {
@@ -94,6 +95,7 @@ typedef struct {
   int32_t quad_n_mu; int32_t quad_n_phi;
   double eta_min; int32_t rics_mode; int32_t mc_on;
   double cells_per_skin_depth; double j_psi; double n0_ppc; double mass_ratio;
+  int32_t ppc_e; int32_t ppc_p; int32_t ppc_i; double init_multiplicity; double u_sigma;
   int32_t inject_mode; double inject_T; double atmo_a0; double atmo_h; double atmo_ncut;
   int32_t pairs_on; double b_pair_threshold; double pair_energy_threshold; double n_max_ppc;
   int32_t annihilate_every;
@@ -683,6 +685,67 @@ static double orc_node_interp(const orc_sim* S, const double* tab, double s)
   return (1.0 - f) * tab[i] + f * tab[i + 1];
 }
 
+static void orc_recount_density(orc_sim* S);
+
+/* The initial plasma of Sec. 3: a pair plasma of multiplicity M whose
+ * leptons drift at beta = -+1/M (the carriers of the twist current), with
+ * ions, by the recipe the parameters document.  Electron k of cell c sits at
+ * the fixed-point position c 2^F + floor((k 2^24 + (X >> 8)) 2^F / (ppc_e
+ * 2^24)), X word 0 of Philox(c, k, 0, INIT): uniform inside the k-th of
+ * ppc_e equal parts of the cell.  Positrons take the positions of the cell's
+ * first ppc_p electrons and ions those of the next ppc_i, so that every node
+ * is neutral.  Momenta are u = drift + sigma g with g = sqrt(-2 ln U1)
+ * cos(2 pi U2) (Box-Muller), U1 = ((Y >> 8) + 1) 2^-24, U2 = (Z >> 8) 2^-24
+ * from words 1 and 2 of Philox(c, k, m, INIT), m = 0, 1, 2 for e-, e+, ion;
+ * drift -u_d, +u_d, 0 with u_d = beta_d / sqrt(1 - beta_d^2), beta_d = 1/M. */
+static void orc_initial_load(orc_sim* S)
+{
+  const orc_params* p = &S->p;
+  int N = S->N;
+  int lg = 0;
+  while ((1 << lg) < N) ++lg;
+  int F = 32 - lg;
+  int64_t ne = (int64_t)N * p->ppc_e, np = (int64_t)N * p->ppc_p, ni = (int64_t)N * p->ppc_i;
+  int64_t n = ne + np + ni;
+  orc_grow(S, n);
+  double beta_d = 1.0 / p->init_multiplicity;
+  double u_d = beta_d / sqrt(1.0 - beta_d * beta_d);
+  uint32_t key[2] = { (uint32_t)p->seed, (uint32_t)(p->seed >> 32) };
+  for (int c = 0; c < N; ++c) {
+    for (int k = 0; k < p->ppc_e; ++k) {
+      uint32_t r[4], ctr[4] = { (uint32_t)c, (uint32_t)k, 0u, ORC_TAG_INIT };
+      orc_philox4x32_10(ctr, key, r);
+      uint64_t A = ((uint64_t)k << 24) + (uint64_t)(r[0] >> 8);
+      uint64_t frac = F >= 24 ? (A << (F - 24)) / (uint64_t)p->ppc_e : A / ((uint64_t)p->ppc_e << (24 - F));
+      double s = (double)(((uint64_t)c << F) + frac) / (double)((uint64_t)1 << F);
+      for (int m = 0; m < 3; ++m) {
+        int64_t slot;
+        if (m == 0) slot = (int64_t)c * p->ppc_e + k;
+        else if (m == 1 && k < p->ppc_p) slot = ne + (int64_t)c * p->ppc_p + k;
+        else if (m == 2 && k >= p->ppc_p) slot = ne + np + (int64_t)c * p->ppc_i + (k - p->ppc_p);
+        else continue;
+        uint32_t q[4];
+        if (m == 0) { q[1] = r[1]; q[2] = r[2]; }
+        else {
+          uint32_t cm[4] = { (uint32_t)c, (uint32_t)k, (uint32_t)m, ORC_TAG_INIT };
+          orc_philox4x32_10(cm, key, q);
+        }
+        double U1 = (double)((q[1] >> 8) + 1u) * (1.0 / 16777216.0);
+        double U2 = (double)(q[2] >> 8) * (1.0 / 16777216.0);
+        double g = sqrt(-2.0 * log(U1)) * cos(2.0 * ORC_PI * U2);
+        double drift = m == 0 ? -u_d : (m == 1 ? u_d : 0.0);
+        S->s[slot] = s;
+        S->u[slot] = drift + p->u_sigma * g;
+        S->w[slot] = 1.0;
+        S->sp[slot] = m == 0 ? ORC_SP_ELEC : (m == 1 ? ORC_SP_POSI : ORC_SP_ION);
+        S->id[slot] = (uint64_t)slot;
+      }
+    }
+  }
+  S->n = n;
+  orc_recount_density(S);
+}
+
 orc_sim* orc_create(const orc_params* p, const double* table_or_null)
 {
   orc_sim* S = (orc_sim*)calloc(1, sizeof(orc_sim));
@@ -738,6 +801,7 @@ orc_sim* orc_create(const orc_params* p, const double* table_or_null)
   S->E = calloc(N, sizeof(double));
   S->J = calloc(N, sizeof(double));
   S->dens = calloc(N, sizeof(int64_t));
+  if (p->ppc_e > 0) orc_initial_load(S);
   return S;
 }
 

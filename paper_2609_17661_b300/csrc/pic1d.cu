@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "pic1d_internal.h"
+#include "push_device.h"
 
 using namespace pic1d;
 
@@ -332,6 +333,14 @@ int validate(const pic1d_params* p, std::string& why) {
   if (!(p->r_eq > 1.0)) return bad("r_eq must exceed 1 (the line must leave the star)");
   if (p->n_cells < 8 || p->n_cells > (1 << 24)) return bad("n_cells must be in [8, 2^24]");
   if (!(p->cfl > 0.0 && p->cfl < 1.0)) return bad("cfl must be in (0, 1)");
+  if (p->ppc_e < 0 || p->ppc_p < 0 || p->ppc_i < 0 || p->ppc_e > 4096)
+    return bad("ppc_e, ppc_p, ppc_i must be in [0, 4096]");
+  if (p->ppc_e > 0) {
+    if (p->ppc_p + p->ppc_i != p->ppc_e) return bad("the initial load needs ppc_p + ppc_i = ppc_e (neutral nodes)");
+    if (!(p->init_multiplicity > 1.0)) return bad("init_multiplicity must exceed 1 (drift beta = 1/M)");
+    if (!(p->u_sigma >= 0.0)) return bad("u_sigma must be >= 0");
+    if ((long long)p->n_cells * 2 * p->ppc_e >= (1ll << 31)) return bad("the initial load exceeds 2^31 particles");
+  }
   if (!(p->b_star > 0.0)) return bad("b_star must be positive");
   if (p->b_convention != 0 && p->b_convention != 1) return bad("b_convention must be 0 or 1");
   if (!(p->kT_keV > 0.0)) return bad("kT_keV must be positive");
@@ -518,6 +527,41 @@ int do_sort(pic1d_ctx* c) {
   return PIC1D_OK;
 }
 
+// The initial plasma of Sec. 3 (pic1d_params' recipe): thread (c, k) writes
+// electron k of cell c and the positron or ion on its position.  Positions in
+// integer arithmetic from word 0 of Philox(c, k, 0, INIT); Gaussians by
+// Box-Muller on words 1 and 2 of Philox(c, k, m, INIT).
+__global__ void k_init_load(DevParams P, int ppc_e, int ppc_p, int ppc_i, float u_d, float sigma) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)P.N * ppc_e) return;
+  const int c = (int)(t / ppc_e), k = (int)(t % ppc_e);
+  const long long ne = (long long)P.N * ppc_e, np = (long long)P.N * ppc_p;
+  const uint4 r = philox4x32_10(make_uint4((uint32_t)c, (uint32_t)k, 0u, kTagInit), P.key0, P.key1);
+  const unsigned long long A = ((unsigned long long)k << 24) + (unsigned long long)(r.x >> 8);
+  const unsigned long long frac = P.F >= 24 ? (A << (P.F - 24)) / (unsigned long long)ppc_e
+                                            : A / ((unsigned long long)ppc_e << (24 - P.F));
+  const uint32_t pos = (uint32_t)(((unsigned long long)c << P.F) + frac);
+#pragma unroll 1
+  for (int m = 0; m < 3; ++m) {
+    long long slot;
+    if (m == 0) slot = (long long)c * ppc_e + k;
+    else if (m == 1 && k < ppc_p) slot = ne + (long long)c * ppc_p + k;
+    else if (m == 2 && k >= ppc_p) slot = ne + np + (long long)c * ppc_i + (k - ppc_p);
+    else continue;
+    const uint4 q = m == 0 ? r : philox4x32_10(make_uint4((uint32_t)c, (uint32_t)k, (uint32_t)m, kTagInit), P.key0,
+                                              P.key1);
+    const float U1 = (float)((q.y >> 8) + 1u) * (1.0f / 16777216.0f);
+    const float U2 = (float)(q.z >> 8) * (1.0f / 16777216.0f);
+    const float g = sqrtf(-2.0f * logf(U1)) * cospif(2.0f * U2);
+    const float drift = m == 0 ? -u_d : (m == 1 ? u_d : 0.0f);
+    P.pos[slot] = pos;
+    P.u[slot] = fmaf(sigma, g, drift);
+    P.w[slot] = 1.0f;
+    P.sp[slot] = m == 0 ? PIC1D_SP_ELECTRON : (m == 1 ? PIC1D_SP_POSITRON : PIC1D_SP_ION);
+    P.id[slot] = (unsigned long long)slot;
+  }
+}
+
 // Check a freshly loaded state (species in range, positions on the line) and
 // accumulate the integer lepton weight of every cell that the pair cap reads.
 // Leptons of one warp that share a cell (the usual case for states stored in
@@ -544,6 +588,32 @@ __global__ void k_load(DevParams P, long long n, long long top, int want_density
   } else if (lep) {
     atomicAdd(reinterpret_cast<unsigned long long*>(P.dens_cur + cell), (unsigned long long)v);
   }
+}
+
+// pic1d_init's initial plasma: the particles, then the state a set_state of
+// them leaves (step 0, E = 0, the pair cap's density)
+int initial_load(pic1d_ctx* c) {
+  const pic1d_params& p = c->p;
+  const long long n = (long long)c->N * (p.ppc_e + p.ppc_p + p.ppc_i);
+  const double beta_d = 1.0 / p.init_multiplicity;
+  const double u_d = beta_d / std::sqrt(1.0 - beta_d * beta_d);
+  c->cur = 0;
+  DevParams P = dev_params(c);
+  const long long threads = (long long)c->N * p.ppc_e;
+  k_init_load<<<(unsigned)((threads + 255) / 256), 256, 0, c->s>>>(P, p.ppc_e, p.ppc_p, p.ppc_i, (float)u_d,
+                                                                   (float)p.u_sigma);
+  CK(cudaGetLastError(), "initial load");
+  StepState st{};
+  st.n_slots = n;
+  CK(cudaMemcpyAsync(c->st, &st, sizeof(st), cudaMemcpyHostToDevice, c->s), "initial load");
+  CK(cudaMemsetAsync(c->dens[0], 0, c->N * sizeof(long long), c->s), "initial load");
+  CK(cudaMemsetAsync(c->dens[1], 0, c->N * sizeof(long long), c->s), "initial load");
+  CK(cudaMemsetAsync(c->spc, 0, sizeof(unsigned long long), c->s), "initial load");
+  const long long top = (long long)c->N << c->F;
+  k_load<<<(unsigned)((n + 255) / 256), 256, 0, c->s>>>(P, n, top, p.n_max_ppc > 0.0 ? 1 : 0, c->spc);
+  CK(cudaGetLastError(), "initial load");
+  CK(cudaStreamSynchronize(c->s), "initial load");
+  return PIC1D_OK;
 }
 
 // record the start event of one timed push launch and log the slot count it reads
@@ -655,7 +725,13 @@ int pic1d_init(const pic1d_params* p, pic1d_ctx** out) {
     }
     if (e != cudaSuccess) rc = cuda_fail(c, e, "init");
   }
-  if (rc == PIC1D_OK) rc = alloc_particles(c, p->capacity > 0 ? p->capacity : 4 * kTile);
+  if (rc == PIC1D_OK) {
+    const long long n_load = (long long)p->n_cells * (p->ppc_e + p->ppc_p + p->ppc_i);
+    const long long want = p->capacity > 0 ? std::max<long long>(p->capacity, n_load)
+                                           : (n_load > 0 ? 2 * n_load + 4 * kTile : 4 * kTile);
+    rc = alloc_particles(c, want);
+  }
+  if (rc == PIC1D_OK && p->ppc_e > 0) rc = initial_load(c);
   if (rc == PIC1D_OK) {
     cudaError_t e = cudaStreamSynchronize(c->s);
     if (e != cudaSuccess) rc = cuda_fail(c, e, "init sync");

@@ -17,6 +17,7 @@ constexpr int kWBits = 12;           // weight fixed point: w_int = rint(w * 2^1
 constexpr uint32_t kTagRics = 0x52494353u;
 constexpr uint32_t kTagInj = 0x494E4A31u;
 constexpr uint32_t kTagAtmo = 0x41544D4Fu;   // atmosphere top-up draws
+constexpr uint32_t kTagInit = 0x494E4954u;   // initial load draws
 constexpr int kMaxFieldBlocks = 1024;
 // cell flags of the streaming push
 constexpr uint8_t CF_ZONE = 1;       // pair zone: Monte-Carlo RICS instead of continuous drag (SPLIT)

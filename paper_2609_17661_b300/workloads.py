@@ -1,10 +1,13 @@
 """Configurations and seeded synthetic inputs for the field-line workloads.
 
-This module holds no arithmetic of the method itself: it only names
-parameter sets and draws initial particle states from numpy's seeded
-generators.  Both the CUDA library (through ``pic1d_set_state``) and the
-FP64 oracle in the tests consume the same arrays, so the two sides start
-from identical states.
+This module names parameter sets and draws initial particle states from
+numpy's seeded generators.  Both the CUDA library (through
+``pic1d_set_state``) and the FP64 oracle in the tests consume the same
+arrays, so the two sides start from identical states.  The only piece of
+the method's setup it holds is the drift of ``load_drifting_plasma``
+(leptons at beta = -+1/M, the carriers of the twist current, Sec. 3); the
+library's own initial load (``pic1d_init`` with ``ppc_e > 0``) draws the
+same recipe on the device, and the oracle draws it independently.
 
 Positions are returned as unsigned 32-bit fixed point over the line,
 ``pos = s * 2**F`` with ``s`` in cells and ``F = fbits(n_cells)`` fractional
@@ -42,6 +45,8 @@ BASE = dict(
     eta_min=1.0e3, rics_mode=RICS_SPLIT, mc_on=1,
     # plasma and twist (Sec. 3)
     cells_per_skin_depth=48.0, j_psi=28.0, n0_ppc=6.0 / 28.0, mass_ratio=50.0,
+    # initial plasma loaded by pic1d_init (ppc_e = 0: an empty line)
+    ppc_e=0, ppc_p=0, ppc_i=0, init_multiplicity=4.0, u_sigma=0.1,
     # supply and pairs
     inject_mode=INJECT_NONE, inject_T=0.01,
     # atmosphere (TOPUP): n/n0 = a0 exp(-(r - R*)/h) with h in cells, down to n_cut;

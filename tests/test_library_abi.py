@@ -86,6 +86,10 @@ def test_init_rejects_bad_parameters_before_any_device_work():
         dict(annihilate_every=-1),
         dict(sort_every=0),
         dict(n_cells=0),
+        dict(ppc_e=16, ppc_p=8, ppc_i=4),                                # initial load not neutral
+        dict(ppc_e=16, ppc_p=8, ppc_i=8, init_multiplicity=1.0),         # drift beta = 1/M = 1
+        dict(ppc_e=16, ppc_p=8, ppc_i=8, u_sigma=-0.1),
+        dict(ppc_e=-1),
     ]
     for over in bad:
         p = make_params(W.config("C1", **over))
