@@ -687,7 +687,7 @@ __device__ void sur_tile(const DevParams& P, sur::MlpCta& M, uint32_t tile, uint
   const int qs = (sp == PIC1D_SP_ELECTRON || sp == PIC1D_SP_ATMO) ? -1 : 1;
   const float mass = ion ? P.mass[PIC1D_SP_ION] : 1.0f;
   const int cell = valid ? (int)(pos0 >> P.F) : 0;
-  float Ep = 0.0f;
+  float Ep = 0.0f, Gp = 0.0f;
   Site S;
   S.x = 1.0f; S.b = 1.0f; S.mu = 0.0f; S.j = 0; S.c = 0.0f;
   bool zone = false;
@@ -698,6 +698,10 @@ __device__ void sur_tile(const DevParams& P, sur::MlpCta& M, uint32_t tile, uint
     if (ig > P.N - 2) { ig = P.N - 2; fg = 1.0f; }
     const float e0 = __ldg(P.E32 + ig), e1 = __ldg(P.E32 + ig + 1);
     Ep = fmaf(fg, e1 - e0, e0);
+    if (P.G32) {            // the atmosphere's gravity (inject mode TOPUP), gathered like E
+      const float g0 = __ldg(P.G32 + ig), g1 = __ldg(P.G32 + ig + 1);
+      Gp = fmaf(fg, g1 - g0, g0);
+    }
     zone = __ldg(P.zone + cell) != 0;
     const float f = (float)(pos0 & fmask) * P.inv2F;
     S.b = fmaf(f, __ldg(P.nb + cell + 1) - __ldg(P.nb + cell), __ldg(P.nb + cell));
@@ -710,7 +714,7 @@ __device__ void sur_tile(const DevParams& P, sur::MlpCta& M, uint32_t tile, uint
   const float sL = (float)((double)pos0 / (double)P.top);
   // 2-4. Strang split with the surrogate drag
   u = sur_drag_half(P, M, S, sL, u, cont, T.n_lim, T.n_newt);
-  if (valid) u = fmaf(qm * Ep, P.dt, u);
+  if (valid) u = P.G32 ? fmaf(fmaf(qm, Ep, Gp / mass), P.dt, u) : fmaf(qm * Ep, P.dt, u);
   u = sur_drag_half(P, M, S, sL, u, cont, T.n_lim, T.n_newt);
   // 5. Monte-Carlo RICS in the pair zone
   bool make_pair = false;
@@ -786,6 +790,12 @@ __device__ void sur_tile(const DevParams& P, sur::MlpCta& M, uint32_t tile, uint
     const int cD = (int)(p1 >> P.F);
     const bool wd = valid && lep && !lost && __ldg(P.dens_flag + cD) != 0;
     warp_atomic_cell(wd, cD, (long long)wint, P.dens_next, P.N);
+  }
+  if (P.G32) {
+    // plasma weight of the atmosphere cells after the move (every species)
+    const int ca = (int)(p1 >> P.F);
+    const bool wa = valid && !lost && __ldg(P.atmo_flag + ca) != 0;
+    warp_atomic_cell(wa, ca, (long long)wint, P.atmo_w, P.N);
   }
   // pair append, warp-aggregated
   const unsigned mp = __ballot_sync(0xffffffffu, make_pair);

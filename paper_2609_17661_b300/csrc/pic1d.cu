@@ -360,7 +360,6 @@ int validate(const pic1d_params* p, std::string& why) {
   if (p->inject_mode == PIC1D_INJECT_TOPUP) {
     if (!(p->atmo_a0 > 0.0) || !(p->atmo_h > 0.0) || !(p->atmo_ncut > 0.0) || !(p->inject_T >= 0.0))
       return bad("TOPUP needs atmo_a0, atmo_h, atmo_ncut > 0 and inject_T >= 0");
-    if (p->drag_law == PIC1D_DRAG_SURROGATE) return bad("TOPUP is not available with drag law SURROGATE");
   }
   if (p->annihilate_every < 0) return bad("annihilate_every must be >= 0");
   if (p->annihilate_every > 0 && !(p->n_max_ppc > 0.0)) return bad("annihilation needs n_max_ppc > 0");

@@ -116,9 +116,58 @@ def test_atmosphere_ignores_the_push_variant():
     assert np.array_equal(J0, J1)
 
 
-def test_top_up_is_refused_with_the_surrogate_drag_law():
+def test_atmosphere_with_the_surrogate_drag_law_matches_the_oracle():
+    """The atmosphere (top-up and gravity) with drag law SURROGATE: five
+    steps of the C1 line from a sparse random state, against the oracle with
+    the same BF16-exact network.  Counts (top-up, losses, pairs) exact; the
+    momenta to 1e-5 of the line's scale plus 3 % of the drag's own change of
+    u (the network's BF16 activations); E to 1e-5."""
+    from oracle import surrogate as SU
     from paper_2609_17661_b300 import Line
-    with pytest.raises(RuntimeError):
-        Line(W.config("C1", inject_mode=O.INJECT_TOPUP, drag_law=W.DRAG_SURROGATE))
+    N = 1024
+    # continuous drag everywhere (no scattering draws that the network's BF16
+    # rate could tip), Newton without the limiter
+    cfg = W.config("C1", inject_mode=O.INJECT_TOPUP, drag_law=O.DRAG_SURROGATE, drag_scale=3e-3, capacity=200000,
+                   b_pair_threshold=1e30, mc_on=0, pairs_on=0, eta_min=0.0)
+    theta = SU.bf16_tensor_layers(W.sur_init_params(21).astype(np.float64))
+    st = W.load_random(cfg, 6000, u_scale=3000.0, seed=11)
+    E = _field0(N)
+    line = Line(cfg)
+    line.sur_set_params(theta.astype(np.float32))
+    line.set_state(st, E=E, step=3)
+    line.step(5)
+    o_ = W.to_oracle(st, N)
+    runs = {}
+    for law in (O.DRAG_SURROGATE, O.DRAG_OFF):
+        S = O.Sim(dict(cfg, drag_law=law))
+        if law == O.DRAG_SURROGATE:
+            S.set_surrogate(theta)
+        S.set_particles(o_["s"], o_["u"], o_["w"], o_["sp"], o_["id"])
+        S.set_field(E)
+        S.set_step(3)
+        S.step(5)
+        runs[law] = S
+    S = runs[O.DRAG_SURROGATE]
+    dg, do = line.diag(), S.diag()
+    for k in ("injected", "n_alive", "lost_north", "lost_south", "newton_branch"):
+        assert dg[k] == do[k], (k, dg[k], do[k])
+    assert do["injected"] > 1400
+    g = _by_id(line.particles())
+    o = _by_id(S.particles())
+    o0 = _by_id(runs[O.DRAG_OFF].particles())
+    assert g["id"].tolist() == o["id"].tolist()
+    drag_du = np.zeros(o["u"].size)
+    common = np.isin(o["id"], o0["id"])
+    drag_du[common] = np.abs(o["u"][common] - o0["u"][np.searchsorted(o0["id"], o["id"][common])])
+    tol = 1e-5 * np.max(np.abs(o["u"])) + 0.03 * drag_du
+    err = np.abs(g["u"].astype(np.float64) - o["u"])
+    assert np.all(err <= tol), (float(np.max(err / tol)), int(np.sum(err > tol)))
+    Eg, _ = line.fields()
+    Eo, _ = S.fields()
+    assert _relmax(Eg, Eo) <= RTOL
+
+
+def test_top_up_parameters_are_checked():
+    from paper_2609_17661_b300 import Line
     with pytest.raises(RuntimeError):
         Line(W.config("C1", inject_mode=O.INJECT_TOPUP, atmo_h=0.0))

@@ -77,7 +77,6 @@ def test_init_rejects_bad_parameters_before_any_device_work():
     from paper_2609_17661_b300 import _lib, make_params, workloads as W
     L = _lib.load()
     bad = [
-        dict(inject_mode=W.INJECT_TOPUP, drag_law=W.DRAG_SURROGATE),    # atmosphere without the surrogate
         dict(inject_mode=W.INJECT_TOPUP, atmo_h=0.0),
         dict(inject_mode=W.INJECT_TOPUP, atmo_a0=-1.0),
         dict(inject_mode=W.INJECT_TOPUP, atmo_ncut=0.0),
