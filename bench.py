@@ -37,24 +37,24 @@ BYTES_PER_CREATED = 21   # pos, u, w, sp, id written per created particle
 SORT_BYTES_PER_SLOT = 62 # a sort reads and writes 29 B per slot, plus a 4 B key pass
 NOMINAL_HBM_GBS = 7700.0 # B300 HBM3e, nominal
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_push
-# launch per slot it read, from one ncu capture of the same push source on a
-# smaller line at the same density (1e8 macroparticles, 26,214 cells: 2.0954
-# GB for 1.0e8 slots); traffic grows in proportion to the slots.  Reported
-# only while the push's source -- kernels.cu up to the surrogate-push section,
-# which holds k_push and every device function it calls -- hashes to the
-# captured one, else null.
-PUSH_TRAFFIC = {"sources_sha256": "6b82c0499c2e99d3c1d11367bf098b942fd1da17908cb7af073f41a432aa7a9b", "bytes_per_slot": 20.954}
-PUSH_SOURCE = "paper_2609_17661_b300/csrc/kernels.cu"
-PUSH_SOURCE_END = "// the push with drag law SURROGATE"
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the default push (the streaming push, k_push_stream) per slot it read, from
+# one ncu capture of the same push source on a smaller line at the same
+# density (1e8 macroparticles, 26,214 cells: 2.0980 GB for 1.0e8 slots);
+# traffic grows in proportion to the slots.  Reported only while the push's
+# source -- push_device.h (the per-particle physics) and push_stream.cu (the
+# kernel) -- hashes to the captured one, else null.
+PUSH_TRAFFIC = {"sources_sha256": "7938175872af73b8dcd0ad67a2e2978908d254dce50b3465c1e9dce917f6abd5", "bytes_per_slot": 20.980}
+PUSH_SOURCES = ("paper_2609_17661_b300/csrc/push_device.h", "paper_2609_17661_b300/csrc/push_stream.cu")
 
 
 def _push_sources_sha256():
     import hashlib
-    with open(os.path.join(ROOT, PUSH_SOURCE)) as f:
-        text = f.read()
-    end = text.find(PUSH_SOURCE_END)
-    return hashlib.sha256(text[:end if end >= 0 else len(text)].encode()).hexdigest()
+    text = ""
+    for p in PUSH_SOURCES:
+        with open(os.path.join(ROOT, p)) as f:
+            text += f.read()
+    return hashlib.sha256(text.encode()).hexdigest()
 
 
 def _peaks():
@@ -365,11 +365,14 @@ def run_gpu(args):
     peak, peak_kind = _peaks()
     achieved = push_bytes / (d1["push_ms"] * 1e-3) / 1e9
     traffic = None
-    # the capture is of the push without the atmosphere (another instantiation)
-    if _push_sources_sha256() == PUSH_TRAFFIC["sources_sha256"] and not args.atmosphere:
+    variant = d1["push_variant"]
+    # the capture is of the default push (variant 0) without the atmosphere
+    # (another instantiation)
+    if _push_sources_sha256() == PUSH_TRAFFIC["sources_sha256"] and not args.atmosphere and variant == 0:
         traffic = PUSH_TRAFFIC["bytes_per_slot"] * units / max(launches, 1)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic, "kernel": "k_push", "launches": launches,
+            "traffic": traffic, "kernel": "k_push_stream" if variant in (0, 6, 7) else "k_push",
+            "push_variant": variant, "launches": launches,
             "bytes_per_launch": push_bytes / max(launches, 1), "slots_per_launch": units / max(launches, 1),
             "mean_launch_ms": d1["push_ms"] / max(launches, 1),
             "peak_kind": peak_kind, "push_share_of_step": d1["push_ms"] / ms,
