@@ -484,14 +484,20 @@ int pic1d_train_surrogate(pic1d_ctx* c, const pic1d_train_cfg* cfg, pic1d_train_
  *
  * The ensemble runs drag law PIC1D_DRAG_SURROGATE with one network for all
  * lines: the network of line 0's context (pic1d_sur_set_params or
- * pic1d_train_surrogate on pic1d_ens_line(e, 0)).  No surface supply.  The
+ * pic1d_train_surrogate on pic1d_ens_line(e, 0)).  A line may have a surface
+ * supply (RATE or the atmosphere, TOPUP) and annihilation at n_max: its
+ * supply runs after the push of every step, its annihilation after the sort
+ * at the end of every annihilate_every-th step, as for the line alone (the
+ * kernels read the step from the line's device state, so that the captured
+ * super-steps draw the random numbers of the steps they replay).  The
  * ensemble works on a stream of its own (cuda_stream of the parameters is
  * not used); pic1d_ens_step is asynchronous, the per-line calls synchronise.
  * ------------------------------------------------------------------------ */
 typedef struct pic1d_ens pic1d_ens;
 
-/* Create n_lines lines from params[0..n_lines-1] (drag_law SURROGATE,
- * inject_mode NONE, capacity per line).  Errors: EINVAL, ENOMEM, ECUDA. */
+/* Create n_lines lines from params[0..n_lines-1] (drag_law SURROGATE, one
+ * stream for all, capacity per line; annihilate_every, where set, divides the
+ * super-step of 80).  Errors: EINVAL, ENOMEM, ECUDA. */
 int pic1d_ens_init(const pic1d_params* params, int32_t n_lines, pic1d_ens** out);
 
 /* The context of one line (owned by the ensemble; NULL if out of range). */

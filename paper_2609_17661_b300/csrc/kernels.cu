@@ -894,7 +894,10 @@ __global__ void k_ens_clear(EnsArgs A) {
   const int2 it = A.cell_items[blockIdx.x];
   const EnsLine& L = A.lines[it.x];
   const int c = it.y + threadIdx.x;
-  if (c < L.P.N) L.P.J[c] = 0;
+  if (c < L.P.N) {
+    L.P.J[c] = 0;
+    if (L.P.atmo_w) L.P.atmo_w[c] = 0;      // the atmosphere's weight sums of the step
+  }
 }
 
 // the push of every line with the surrogate drag: items (line, tiles) from a
@@ -1026,6 +1029,9 @@ __global__ void k_ens_flip(EnsLine* lines, int line) {
 __global__ void k_inject(DevParams P, double carriers, float sig_e, float sig_i) {
   __shared__ long long cnt[2];
   __shared__ long long slot0;
+  // the step being taken, from the device (also right inside an ensemble's
+  // captured super-steps, where the launch's parameters are fixed)
+  const long long step = P.st->step;
   if (threadIdx.x == 0) {
     for (int f = 0; f < 2; ++f) {
       const double acc = P.st->inj_acc[f] + carriers;
@@ -1045,7 +1051,7 @@ __global__ void k_inject(DevParams P, double carriers, float sig_e, float sig_i)
     const long long slot = foot ? k - cnt[0] : k;
     const long long dst = n + slot0 + 2 * k;
     if (dst + 2 > P.cap) { ++drop; continue; }
-    const uint4 r = philox4x32_10(make_uint4((uint32_t)slot, (uint32_t)foot, (uint32_t)P.step, kTagInj), P.key0, P.key1);
+    const uint4 r = philox4x32_10(make_uint4((uint32_t)slot, (uint32_t)foot, (uint32_t)step, kTagInj), P.key0, P.key1);
     const long long q = (long long)(r.x >> 16);
     long long pfix;
     if (P.F >= 16) pfix = foot == 0 ? (q << (P.F - 16)) : P.top - ((q + 1) << (P.F - 16));
@@ -1060,7 +1066,7 @@ __global__ void k_inject(DevParams P, double carriers, float sig_e, float sig_i)
       P.u[dst + m] = m == 0 ? ue : ui;
       P.w[dst + m] = 1.0f;
       P.sp[dst + m] = m == 0 ? PIC1D_SP_ATMO : PIC1D_SP_ION;
-      P.id[dst + m] = supply_id(P.step, foot, slot, m);
+      P.id[dst + m] = supply_id(step, foot, slot, m);
     }
     if (P.use_nmax)
       atomicAdd(reinterpret_cast<unsigned long long*>(P.dens_next + (int)(pfix >> P.F)), 4096ull);
@@ -1079,6 +1085,7 @@ __global__ void k_inject(DevParams P, double carriers, float sig_e, float sig_i)
 // --------------------------------------------------------------------------
 __global__ void k_topup(DevParams P, const int* cells, const long long* target, float sig_e, float sig_i) {
   __shared__ long long s_slot0;
+  const long long step = P.st->step;     // the step being taken (see k_inject)
   const int c = cells[blockIdx.x];
   const long long deficit = target[blockIdx.x] - P.atmo_w[c];
   const long long npair = deficit > 0 ? deficit / (2ll * 4096ll) : 0;
@@ -1092,7 +1099,7 @@ __global__ void k_topup(DevParams P, const int* cells, const long long* target, 
   for (long long k = threadIdx.x; k < npair; k += blockDim.x) {
     const long long dst = n + s_slot0 + 2 * k;
     if (dst + 2 > P.cap) { ++drop; continue; }
-    const uint4 r = philox4x32_10(make_uint4((uint32_t)k, (uint32_t)c, (uint32_t)P.step, kTagAtmo), P.key0, P.key1);
+    const uint4 r = philox4x32_10(make_uint4((uint32_t)k, (uint32_t)c, (uint32_t)step, kTagAtmo), P.key0, P.key1);
     const uint32_t q = r.x >> 16;               // 16 fractional bits of the cell
     const uint32_t frac = P.F >= 16 ? (q << (P.F - 16)) : (q >> (16 - P.F));
     const uint32_t pfix = ((uint32_t)c << P.F) + frac;
@@ -1105,7 +1112,7 @@ __global__ void k_topup(DevParams P, const int* cells, const long long* target, 
       P.u[dst + m] = m == 0 ? ue : ui;
       P.w[dst + m] = 1.0f;
       P.sp[dst + m] = m == 0 ? PIC1D_SP_ATMO : PIC1D_SP_ION;
-      P.id[dst + m] = atmo_id(P.step, c, k, m);
+      P.id[dst + m] = atmo_id(step, c, k, m);
     }
     if (P.use_nmax) atomicAdd(reinterpret_cast<unsigned long long*>(P.dens_next + c), 4096ull);
     ++ok;
@@ -1417,6 +1424,9 @@ __global__ void __launch_bounds__(kAnnThreads) k_annih_cell(DevParams P, const u
   __shared__ long long sh[2][kAnnThreads / 32];
   const unsigned ncell = *count;
   const uint32_t fmask = (1u << P.F) - 1u;
+  // the step just completed, from the device (also right inside an
+  // ensemble's captured super-steps, where the launch's parameters are fixed)
+  const long long step = P.st->step;
   for (unsigned item = blockIdx.x; item < ncell; item += gridDim.x) {
     const int c = list[item];
     const long long A = amount[item];
@@ -1431,7 +1441,7 @@ __global__ void __launch_bounds__(kAnnThreads) k_annih_cell(DevParams P, const u
         for (long long i = a[g] + threadIdx.x; i < b[g]; i += kAnnThreads) {
           const uint8_t sp = P.sp[i];
           if (sp != PIC1D_SP_ELECTRON && sp != PIC1D_SP_POSITRON) continue;
-          const unsigned long long key = annih_key(P.id[i], P.step);
+          const unsigned long long key = annih_key(P.id[i], step);
           const long long w = __float2ll_rn(P.w[i] * 4096.0f);
           if (sp == PIC1D_SP_ELECTRON) { if (key <= mid0) s0 += w; }
           else if (key <= mid1) s1 += w;
@@ -1447,7 +1457,7 @@ __global__ void __launch_bounds__(kAnnThreads) k_annih_cell(DevParams P, const u
       for (long long i = a[g] + threadIdx.x; i < b[g]; i += kAnnThreads) {
         const uint8_t sp = P.sp[i];
         if (sp != PIC1D_SP_ELECTRON && sp != PIC1D_SP_POSITRON) continue;
-        const unsigned long long key = annih_key(P.id[i], P.step);
+        const unsigned long long key = annih_key(P.id[i], step);
         const long long w = __float2ll_rn(P.w[i] * 4096.0f);
         if (sp == PIC1D_SP_ELECTRON) { if (key < th0) B0 += w; }
         else if (key < th1) B1 += w;
@@ -1460,7 +1470,7 @@ __global__ void __launch_bounds__(kAnnThreads) k_annih_cell(DevParams P, const u
         const uint8_t sp = P.sp[i];
         if (sp != PIC1D_SP_ELECTRON && sp != PIC1D_SP_POSITRON) continue;
         const bool pos = sp == PIC1D_SP_POSITRON;
-        const unsigned long long key = annih_key(P.id[i], P.step);
+        const unsigned long long key = annih_key(P.id[i], step);
         const unsigned long long th = pos ? th1 : th0;
         const long long w = __float2ll_rn(P.w[i] * 4096.0f);
         long long d = 0;

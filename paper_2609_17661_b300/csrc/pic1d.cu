@@ -1535,6 +1535,25 @@ EnsArgs ens_args(pic1d_ens* e) {
   return A;
 }
 
+// a line's kernel parameters for buffer `cur` at step `step` (the ensemble
+// enqueues steps ahead of the line's own bookkeeping)
+DevParams line_params(pic1d_ctx* c, int cur, long long step) {
+  const int keep_cur = c->cur;
+  const long long keep_step = c->step;
+  c->cur = cur;
+  c->step = step;
+  const DevParams P = dev_params(c);
+  c->cur = keep_cur;
+  c->step = keep_step;
+  return P;
+}
+
+// sorts a line takes at the end of step k: its cadence, and annihilation's
+bool ens_sorts_at(const pic1d_ens* e, int l, long long k) {
+  const int ae = e->lines[l]->p.annihilate_every;
+  return k % e->cadence[l] == 0 || (ae > 0 && k % ae == 0);
+}
+
 // enqueue k steps of every line on the stream; cur/step give each line's
 // buffer and step at the start and are advanced as the steps would
 int ens_enqueue(pic1d_ens* e, int k, std::vector<int>& cur, std::vector<long long>& step) {
@@ -1544,16 +1563,25 @@ int ens_enqueue(pic1d_ens* e, int k, std::vector<int>& cur, std::vector<long lon
   for (int i = 0; i < k; ++i) {
     ECK(ens_launch_clear(A, e->s), "ensemble clear");
     ECK(ens_launch_push(A, e->sms * kSurPushPerSm, e->s), "ensemble push");
+    // the surface supply of the lines that have one (Sec. 3, App. B.1)
+    for (int l = 0; l < e->n; ++l) {
+      pic1d_ctx* c = e->lines[l];
+      const pic1d_params& p = c->p;
+      if (p.inject_mode == PIC1D_INJECT_NONE) continue;
+      const DevParams P = line_params(c, cur[l], step[l]);
+      const float sig_e = (float)std::sqrt(p.inject_T), sig_i = (float)std::sqrt(p.inject_T / p.mass_ratio);
+      if (p.inject_mode == PIC1D_INJECT_RATE)
+        ECK(launch_inject(P, p.j_psi * p.n0_ppc * c->dt, sig_e, sig_i, e->s), "ensemble supply");
+      else
+        ECK(launch_topup(P, c->atmo_cells, c->atmo_target, c->n_atmo, sig_e, sig_i, e->s), "ensemble top-up");
+    }
     ECK(ens_launch_field(A, e->s), "ensemble field");
     ECK(ens_launch_finalize(A, e->s), "ensemble finalize");
     for (int l = 0; l < e->n; ++l) {
       step[l] += 1;
-      if (step[l] % e->cadence[l] != 0) continue;
+      if (!ens_sorts_at(e, l, step[l])) continue;
       pic1d_ctx* c = e->lines[l];
-      const int keep = c->cur;
-      c->cur = cur[l];
-      DevParams P = dev_params(c);
-      c->cur = keep;
+      DevParams P = line_params(c, cur[l], step[l]);
       const int o = 1 - cur[l];
       cudaEvent_t a = nullptr, b = nullptr;
       if (e->time_sorts) {
@@ -1573,6 +1601,15 @@ int ens_enqueue(pic1d_ens* e, int k, std::vector<int>& cur, std::vector<long lon
         e->sort_count[l] += 1;
       }
       cur[l] = o;
+      const int ae = c->p.annihilate_every;
+      if (ae > 0 && step[l] % ae == 0) {
+        // annihilation at n_max on the sorted buffer (Sec. 3)
+        const DevParams Q = line_params(c, cur[l], step[l]);
+        const double cJ = 4.0 * kPi * c->q_p * std::ldexp(1.0, -c->F - kWBits);
+        ECK(launch_annihilate(Q, c->counts, c->offsets, c->ann_list, c->ann_amount, c->ann_count, c->E64, c->E32,
+                              cJ, c->sms, e->s),
+            "ensemble annihilation");
+      }
     }
   }
   if (!evs.empty()) {
@@ -1603,10 +1640,10 @@ int pic1d_ens_init(const pic1d_params* params, int32_t n_lines, pic1d_ens** out)
   *out = nullptr;
   if (!params || n_lines < 1) return PIC1D_EINVAL;
   for (int l = 0; l < n_lines; ++l) {
-    if (params[l].drag_law != PIC1D_DRAG_SURROGATE || params[l].inject_mode != PIC1D_INJECT_NONE ||
-        params[l].annihilate_every != 0 || params[l].cuda_stream != params[0].cuda_stream) {
-      std::fprintf(stderr, "pic1d_ens_init: line %d: the ensemble runs drag law SURROGATE, no surface supply, "
-                           "no annihilation, and one stream for all lines\n", l);
+    if (params[l].drag_law != PIC1D_DRAG_SURROGATE || params[l].cuda_stream != params[0].cuda_stream ||
+        (params[l].annihilate_every > 0 && kEnsSuper % params[l].annihilate_every != 0)) {
+      std::fprintf(stderr, "pic1d_ens_init: line %d: the ensemble runs drag law SURROGATE, one stream for all "
+                           "lines, and an annihilation cadence that divides %d\n", l, kEnsSuper);
       return PIC1D_EINVAL;
     }
   }
@@ -1726,7 +1763,7 @@ int pic1d_ens_step(pic1d_ens* e, int n_steps) {
     ECK(cudaGraphLaunch(e->graph, e->s), "ensemble graph launch");
     for (int l = 0; l < e->n; ++l) {
       long long sorts = 0;
-      for (long long k = step[l] + 1; k <= step[l] + kEnsSuper; ++k) sorts += (k % e->cadence[l] == 0);
+      for (long long k = step[l] + 1; k <= step[l] + kEnsSuper; ++k) sorts += ens_sorts_at(e, l, k);
       if (sorts & 1) cur[l] ^= 1;
       step[l] += kEnsSuper;
     }

@@ -95,9 +95,9 @@ def test_init_rejects_bad_parameters_before_any_device_work():
         h = C.c_void_p()
         assert L.pic1d_init(C.byref(p), C.byref(h)) == _lib.EINVAL, over
         assert not h.value
-    # the ensemble refuses lines with supply or annihilation
-    for over in (dict(annihilate_every=20, n_max_ppc=10.0), dict(inject_mode=W.INJECT_TOPUP),
-                 dict(drag_law=W.DRAG_TABLE)):
+    # the ensemble refuses lines without the surrogate drag law, and an
+    # annihilation cadence that does not divide its captured super-step of 80
+    for over in (dict(annihilate_every=30, n_max_ppc=10.0), dict(drag_law=W.DRAG_TABLE)):
         cfg = W.config("C1", drag_law=W.DRAG_SURROGATE)
         cfg.update(over)
         arr = (_lib.Params * 1)(make_params(cfg))
