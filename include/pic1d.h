@@ -196,6 +196,11 @@ typedef struct pic1d_diag_t {
   double q_p, j_ext, dt, tau_min, R_cells, L_Rstar; /* derived constants         */
   int32_t fbits, status;
   int32_t push_variant;     /* push kernel variant in use (pic1d_set_variant) */
+  int32_t gauss_marked;     /* 1 after pic1d_gauss_mark (until the next set_state/load) */
+  int64_t gauss_residual_max;  /* discrete continuity since the mark (pic1d_gauss_mark):
+                                  max over interior nodes of |residual|, integer, 0 when
+                                  charge is conserved exactly; -1 without a mark */
+  int64_t gauss_residual_node; /* first node reaching it (-1 without a mark) */
 } pic1d_diag_t;
 
 typedef struct pic1d_ctx pic1d_ctx;
@@ -361,6 +366,21 @@ int pic1d_tp_map(const pic1d_params* p, const double* r_eq, int32_t n, double ga
  * -(J_i - J_{i-1}) at every interior node, exactly.  rho: N+1 int64, host
  * (mem 0) or device (mem 1).  Synchronises.  Errors: EINVAL, ECUDA. */
 int pic1d_get_rho(pic1d_ctx* c, int64_t* rho, int mem);
+
+/* Mark the state for the discrete continuity check (Sec. 3: the deposit
+ * conserves charge, so Gauss's law dE/ds = 4 pi rho stays satisfied if it
+ * held).  Records the node charge rho_ref (as pic1d_get_rho) and restarts
+ * the cumulative current Jcum of every cell, which each step's field update
+ * and each annihilation pass (a current -X in the cell whose left node takes
+ * the removed charge) add to.  From then on pic1d_diag reports, in the
+ * integer units of pic1d_get_rho,
+ *   max over nodes 1..N-1 of |rho_i - rho_ref_i - (Jcum_{i-1} - Jcum_i)|,
+ * which is 0 as long as every particle's charge moves only by the deposit
+ * (pairs and supply are created neutral at one position; losses change only
+ * the wall nodes; a particle removed for a non-finite momentum breaks it).
+ * set_state and load clear the mark.  Costs one charge deposit per mark and
+ * per diag call.  Synchronises.  Errors: EINVAL, ENOMEM, ECUDA. */
+int pic1d_gauss_mark(pic1d_ctx* c);
 
 /* Checkpoint and resume.  pic1d_save writes the context's whole state to a
  * file: the parameters (to be checked on load), the step, the particle slots

@@ -219,6 +219,11 @@ class Line:
         self._check(self.L.pic1d_get_rho(self.h, C.c_void_p(r.ctypes.data), 0))
         return r
 
+    def gauss_mark(self):
+        """pic1d_gauss_mark: start the discrete continuity check; diag() then
+        reports gauss_residual_max (0 while charge is conserved exactly)."""
+        self._check(self.L.pic1d_gauss_mark(self.h))
+
     def particles(self, alive_only=True) -> dict:
         n = self.slots()
         out = dict(pos=np.zeros(n, np.uint32), u=np.zeros(n, np.float32), w=np.zeros(n, np.float32),

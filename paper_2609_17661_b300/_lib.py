@@ -50,7 +50,8 @@ class Diag(C.Structure):
         ("vc", C.c_double), ("ke_lost", C.c_double),
         ("q_p", C.c_double), ("j_ext", C.c_double), ("dt", C.c_double), ("tau_min", C.c_double),
         ("R_cells", C.c_double), ("L_Rstar", C.c_double),
-        ("fbits", C.c_int32), ("status", C.c_int32), ("push_variant", C.c_int32),
+        ("fbits", C.c_int32), ("status", C.c_int32), ("push_variant", C.c_int32), ("gauss_marked", C.c_int32),
+        ("gauss_residual_max", C.c_int64), ("gauss_residual_node", C.c_int64),
     ]
 
 
@@ -99,6 +100,7 @@ SIGNATURES = {
     "pic1d_sort_static": (C.c_int, [C.c_int32, C.c_int64] + [C.c_void_p] * 11 + [C.c_void_p]),
     "pic1d_set_allocator": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "pic1d_get_rho": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "pic1d_gauss_mark": (C.c_int, [C.c_void_p]),
     "pic1d_tp_map": (C.c_int, [C.POINTER(Params), C.c_void_p, C.c_int32, C.c_double, C.c_double, C.c_double,
                                C.c_double, C.c_double, C.c_void_p, C.POINTER(C.c_double)]),
     "pic1d_save": (C.c_int, [C.c_void_p, C.c_char_p]),

@@ -958,6 +958,7 @@ __global__ void __launch_bounds__(256) k_ens_field(EnsArgs A) {
     L.E64[c] = En;
     L.E32[c] = (float)En;
     if (L.P.use_nmax) L.dens[L.P.st->step & 1][c] = 0;
+    if (L.P.jcum) L.P.jcum[c] += L.P.J[c];
     so = Eo;
     sn = En;
     s2 = En * En;
@@ -1134,6 +1135,7 @@ __global__ void __launch_bounds__(256) k_field(DevParams P, double* E64, float* 
     E64[c] = En;
     E32[c] = (float)En;
     if (P.use_nmax) P.dens_cur[c] = 0;     // becomes the next step's accumulator
+    if (P.jcum) P.jcum[c] += P.J[c];
     so += Eo;
     sn += En;
     s2 += En * En;
@@ -1488,6 +1490,7 @@ __global__ void __launch_bounds__(kAnnThreads) k_annih_cell(DevParams P, const u
       const double En = E64[c] + cJ * (double)X;
       E64[c] = En;
       E32[c] = (float)En;
+      if (P.jcum) P.jcum[c] -= X;           // the carry to the left node is a current -X in cell c
       if (P.use_nmax) P.dens_cur[c] -= 2 * A;
       atomicAdd(&P.ctr->annihilated, (unsigned long long)(2 * A));
     }
@@ -1813,6 +1816,32 @@ cudaError_t launch_deposit(const DevParams& P, long long n, const long long* p0,
 
 cudaError_t launch_rho(const DevParams& P, long long* rho, int grid, cudaStream_t s) {
   k_rho<<<grid, 256, 0, s>>>(P, rho);
+  return cudaGetLastError();
+}
+
+// Discrete continuity, exact in the integer units of the deposit: the node
+// charge rho_i (CIC, Sec. 3) changes by the currents of the two cells beside
+// node i, rho_i - rho_ref_i = Jcum_{i-1} - Jcum_i at every interior node
+// (pairs and supply are created neutral, annihilation carries its charge to
+// a node as a current).  out2[0] = max |residual|, out2[1] = the first node
+// where it is reached (two passes).
+__global__ void k_gauss_residual(DevParams P, const long long* rho, const long long* rho_ref,
+                                 unsigned long long* out2, int pass) {
+  for (int i = 1 + blockIdx.x * blockDim.x + threadIdx.x; i < P.N; i += gridDim.x * blockDim.x) {
+    const long long r = rho[i] - rho_ref[i] - (P.jcum[i - 1] - P.jcum[i]);
+    const unsigned long long a = (unsigned long long)(r < 0 ? -r : r);
+    if (pass == 0) atomicMax(&out2[0], a);
+    else if (a == out2[0]) atomicMin(&out2[1], (unsigned long long)i);
+  }
+}
+
+cudaError_t launch_gauss_residual(const DevParams& P, const long long* rho, const long long* rho_ref,
+                                  unsigned long long* out2, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out2, 0, sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(out2 + 1, 0xff, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  const int grid = P.N / 256 + 1 < 1184 ? P.N / 256 + 1 : 1184;
+  for (int pass = 0; pass < 2; ++pass) k_gauss_residual<<<grid, 256, 0, s>>>(P, rho, rho_ref, out2, pass);
   return cudaGetLastError();
 }
 

@@ -5,6 +5,7 @@
 // quadrature on the device, owns all device memory of a context and issues
 // the per-step kernels of kernels.cu on the caller's stream.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -19,6 +20,16 @@
 
 #include "pic1d_internal.h"
 #include "push_device.h"
+
+namespace {
+// an NVTX range over a host scope (free when no tool is attached)
+struct Nvtx {
+  explicit Nvtx(const char* name) { nvtxRangePushA(name); }
+  ~Nvtx() { nvtxRangePop(); }
+  Nvtx(const Nvtx&) = delete;
+  Nvtx& operator=(const Nvtx&) = delete;
+};
+}  // namespace
 
 using namespace pic1d;
 
@@ -189,6 +200,13 @@ struct pic1d_ctx {
   float* sur_grad = nullptr;
   float* sur_loss = nullptr;     // loss sum of a gradient call
   long long* rho = nullptr;      // node charge of pic1d_get_rho (allocated on first use)
+  // discrete continuity check (pic1d_gauss_mark): the cumulative current of
+  // every cell (always kept, added by the field update) and the node charge
+  // when the mark was taken
+  long long* jcum = nullptr;
+  long long* rho_ref = nullptr;
+  unsigned long long* gauss_out = nullptr;
+  bool gauss_on = false;
 };
 
 namespace {
@@ -313,6 +331,7 @@ DevParams dev_params(pic1d_ctx* c) {
   P.G32 = c->G32;
   P.atmo_flag = c->atmo_flag;
   P.atmo_w = c->atmo_w;
+  P.jcum = c->jcum;
   P.dens_cur = c->dens[c->step & 1];
   P.dens_next = c->dens[(c->step + 1) & 1];
   P.cap = c->cap;
@@ -517,6 +536,7 @@ int build_tables(pic1d_ctx* c) {
 }
 
 int do_sort(pic1d_ctx* c) {
+  Nvtx range("sort");
   DevParams P = dev_params(c);
   const int o = 1 - c->cur;
   CK(launch_sort(P, c->counts, c->offsets, c->bsum, c->pos[o], c->u[o], c->w[o], c->sp[o], c->id[o], c->sort_grid,
@@ -690,6 +710,7 @@ int pic1d_init(const pic1d_params* p, pic1d_ctx** out) {
     chain(dalloc(&c->E64, N));
     chain(dalloc(&c->E32, N));
     chain(dalloc(&c->J, N));
+    chain(dalloc(&c->jcum, N));
     chain(dalloc(&c->dens[0], N));
     chain(dalloc(&c->dens[1], N));
     chain(dalloc(&c->ctr, 1));
@@ -716,6 +737,7 @@ int pic1d_init(const pic1d_params* p, pic1d_ctx** out) {
       chain(cudaMemsetAsync(c->E64, 0, N * sizeof(double), c->s));
       chain(cudaMemsetAsync(c->E32, 0, N * sizeof(float), c->s));
       chain(cudaMemsetAsync(c->J, 0, N * sizeof(long long), c->s));
+      chain(cudaMemsetAsync(c->jcum, 0, N * sizeof(long long), c->s));
       chain(cudaMemsetAsync(c->dens[0], 0, N * sizeof(long long), c->s));
       chain(cudaMemsetAsync(c->dens[1], 0, N * sizeof(long long), c->s));
       chain(cudaMemsetAsync(c->ctr, 0, sizeof(Counters), c->s));
@@ -781,6 +803,7 @@ int pic1d_set_state(pic1d_ctx* c, int64_t n, const uint32_t* pos, const float* u
     CK(cudaMemsetAsync(c->E32, 0, c->N * sizeof(float), c->s), "set_state E");
   }
   CK(cudaMemsetAsync(c->J, 0, c->N * sizeof(long long), c->s), "set_state J");
+  c->gauss_on = false;                   // a new state: the continuity mark no longer applies
   c->step = step;
   StepState st{};
   st.n_slots = n;
@@ -816,6 +839,7 @@ int pic1d_set_state(pic1d_ctx* c, int64_t n, const uint32_t* pos, const float* u
 
 int pic1d_step(pic1d_ctx* c, int n_steps) {
   if (!c) return PIC1D_EINVAL;
+  Nvtx range("pic1d_step");
   if (n_steps < 0) return fail(c, PIC1D_EINVAL, "step: n_steps < 0");
   const pic1d_params& p = c->p;
   const double four_pi = 4.0 * kPi;
@@ -836,17 +860,23 @@ int pic1d_step(pic1d_ctx* c, int n_steps) {
       if (rc != PIC1D_OK) return rc;
     }
     int grid = c->push_grid;
-    if (sur_law) {
-      grid = c->sms * kSurPushPerSm;
-      CK(launch_push_sur(P, grid, c->s), "push");
-    } else {
-      CK(launch_push(P, c->push_variant, c->push_grid, c->s), "push");
+    {
+      Nvtx push_range("push");
+      if (sur_law) {
+        grid = c->sms * kSurPushPerSm;
+        CK(launch_push_sur(P, grid, c->s), "push");
+      } else {
+        CK(launch_push(P, c->push_variant, c->push_grid, c->s), "push");
+      }
     }
     if (c->timing) CK(cudaEventRecord(c->ev.back(), c->s), "timing");
     if (p.inject_mode == PIC1D_INJECT_RATE) CK(launch_inject(P, carriers, sig_e, sig_i, c->s), "inject");
     if (p.inject_mode == PIC1D_INJECT_TOPUP)
       CK(launch_topup(P, c->atmo_cells, c->atmo_target, c->n_atmo, sig_e, sig_i, c->s), "top-up");
-    CK(launch_field(P, c->E64, c->E32, a, cJ, dt_jext, c->field_partial, grid, c->s), "field");
+    {
+      Nvtx field_range("field");
+      CK(launch_field(P, c->E64, c->E32, a, cJ, dt_jext, c->field_partial, grid, c->s), "field");
+    }
     c->step += 1;
     const bool ann = p.annihilate_every > 0 && c->step % p.annihilate_every == 0;
     if (c->step % p.sort_every == 0 || ann) {
@@ -854,6 +884,7 @@ int pic1d_step(pic1d_ctx* c, int n_steps) {
       if (rc != PIC1D_OK) return rc;
     }
     if (ann) {
+      Nvtx ann_range("annihilate");
       const DevParams Q = dev_params(c);     // the sorted buffer, the step just finished
       CK(launch_annihilate(Q, c->counts, c->offsets, c->ann_list, c->ann_amount, c->ann_count, c->E64, c->E32, cJ,
                            c->sms, c->s),
@@ -928,6 +959,19 @@ int pic1d_diag(pic1d_ctx* c, pic1d_diag_t* out) {
   out->L_Rstar = c->L_R;
   out->fbits = c->F;
   out->push_variant = c->push_variant;
+  out->gauss_marked = c->gauss_on ? 1 : 0;
+  out->gauss_residual_max = -1;
+  out->gauss_residual_node = -1;
+  if (c->gauss_on) {
+    CK(cudaMemsetAsync(c->rho, 0, sizeof(long long) * (c->N + 1), c->s), "diag continuity");
+    CK(launch_rho(P, c->rho, c->sms * 8, c->s), "diag continuity");
+    CK(launch_gauss_residual(P, c->rho, c->rho_ref, c->gauss_out, c->s), "diag continuity");
+    unsigned long long g[2];
+    CK(cudaMemcpyAsync(g, c->gauss_out, sizeof(g), cudaMemcpyDeviceToHost, c->s), "diag continuity");
+    CK(cudaStreamSynchronize(c->s), "diag continuity");
+    out->gauss_residual_max = (int64_t)g[0];
+    out->gauss_residual_node = g[1] == ~0ull ? -1 : (int64_t)g[1];
+  }
   int status = PIC1D_OK;
   if (C.waits_timed_out) {
     // reported once: the count restarts, the context stays usable
@@ -1170,6 +1214,7 @@ int pic1d_sur_infer(pic1d_ctx* c, const float* feat_dev, int32_t stride, int64_t
 
 int pic1d_train_surrogate(pic1d_ctx* c, const pic1d_train_cfg* cfg, pic1d_train_report* rep) {
   if (!c) return PIC1D_EINVAL;
+  Nvtx range("pic1d_train_surrogate");
   if (!cfg || !rep || cfg->n_samples < cfg->batch || cfg->batch < 128 || cfg->batch % 128 != 0 ||
       cfg->batch > kSurMaxTiles * 128 || cfg->epochs < 0 || !(cfg->lr > 0.0) || !(cfg->r_lo >= 1.0) ||
       !(cfg->r_hi >= cfg->r_lo) || cfg->n_val < 0)
@@ -1396,6 +1441,7 @@ int pic1d_load(pic1d_ctx* c, const char* path) {
   CK(cudaMemcpy(c->ctr, &ctr, sizeof(ctr), cudaMemcpyHostToDevice), "load");
   CK(cudaMemcpy(c->st, &st, sizeof(st), cudaMemcpyHostToDevice), "load");
   c->step = step;
+  c->gauss_on = false;
   if (sur) {
     int rc = sur_ensure(c);
     if (rc != PIC1D_OK) return rc;
@@ -1729,6 +1775,7 @@ int pic1d_ens_get_schedule(pic1d_ens* e, int32_t* chunk_tiles, int32_t* sort_eve
 
 int pic1d_ens_step(pic1d_ens* e, int n_steps) {
   if (!e) return PIC1D_EINVAL;
+  Nvtx range("pic1d_ens_step");
   if (n_steps < 0) return ens_fail(e, PIC1D_EINVAL, "ens_step: n_steps < 0");
   if (!e->lines[0]->sur_on) return ens_fail(e, PIC1D_EINVAL, "ens_step: no network (set or train it on line 0)");
   int rc = ens_sync_records(e);
@@ -1925,6 +1972,7 @@ void pic1d_ens_free(pic1d_ens* e) {
 
 int pic1d_tp_map(const pic1d_params* p, const double* r_eq, int32_t n, double gamma0, double dt, double t_max,
                  double b_thr, double gamma_eps, pic1d_tp_result* out, double* ms_out) {
+  Nvtx range("pic1d_tp_map");
   if (!p || !r_eq || !out || n < 1 || !(gamma0 >= 1.0) || !(dt > 0.0) || !(t_max > 0.0) || !(b_thr > 0.0)) {
     std::fprintf(stderr, "pic1d_tp_map: bad arguments\n");
     return PIC1D_EINVAL;
@@ -1960,6 +2008,19 @@ int pic1d_tp_map(const pic1d_params* p, const double* r_eq, int32_t n, double ga
     std::fprintf(stderr, "pic1d_tp_map: %s\n", cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? PIC1D_ENOMEM : PIC1D_ECUDA;
   }
+  return PIC1D_OK;
+}
+
+int pic1d_gauss_mark(pic1d_ctx* c) {
+  if (!c) return PIC1D_EINVAL;
+  if (!c->rho) CK(dalloc(&c->rho, c->N + 1), "gauss_mark");
+  if (!c->rho_ref) CK(dalloc(&c->rho_ref, c->N + 1), "gauss_mark");
+  if (!c->gauss_out) CK(dalloc(&c->gauss_out, 2), "gauss_mark");
+  CK(cudaMemsetAsync(c->rho_ref, 0, sizeof(long long) * (c->N + 1), c->s), "gauss_mark");
+  CK(launch_rho(dev_params(c), c->rho_ref, c->sms * 8, c->s), "gauss_mark");
+  CK(cudaMemsetAsync(c->jcum, 0, sizeof(long long) * c->N, c->s), "gauss_mark");
+  CK(cudaStreamSynchronize(c->s), "gauss_mark");
+  c->gauss_on = true;
   return PIC1D_OK;
 }
 
@@ -2041,7 +2102,7 @@ void pic1d_free(pic1d_ctx* c) {
                   c->tpair, c->bsum, c->sur.master, c->sur.m, c->sur.v, c->sur.img, c->sur.small,
                   c->sur.part, c->sur.loss_part, c->sur.err, c->sur_gx, c->sur_gw, c->sur_grad, c->sur_loss, c->rho,
                   c->G32, c->atmo_flag, c->atmo_w, c->atmo_cells, c->atmo_target, c->ann_list, c->ann_amount,
-                  c->ann_count, c->cflag, c->dflag, c->nmu2};
+                  c->ann_count, c->cflag, c->dflag, c->nmu2, c->jcum, c->rho_ref, c->gauss_out};
   for (void* q : ptrs) dfree(q);
   delete c;
   g_live.fetch_sub(1);

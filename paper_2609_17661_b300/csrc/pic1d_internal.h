@@ -96,6 +96,7 @@ struct DevParams {
   // atmosphere (inject mode TOPUP; null otherwise)
   const float* G32;         // gravity along s per unit mass at cell centres (zero outside the atmosphere)
   const uint8_t* atmo_flag; // cells of the atmosphere
+  long long* jcum;          // cumulative J per cell since pic1d_gauss_mark (null: not kept)
   long long* atmo_w;        // plasma weight (w_int) per cell after the move, summed by the push
   long long cap;
   Counters* ctr;
@@ -145,6 +146,8 @@ cudaError_t launch_deposit(const DevParams& P, long long n, const long long* p0,
                            const float* w, const uint8_t* sp, long long* J, cudaStream_t s);
 cudaError_t launch_count_species(const DevParams& P, unsigned long long* out4, cudaStream_t s);
 cudaError_t launch_rho(const DevParams& P, long long* rho, int grid, cudaStream_t s);
+cudaError_t launch_gauss_residual(const DevParams& P, const long long* rho, const long long* rho_ref,
+                                  unsigned long long* out2, cudaStream_t s);
 int push_blocks_per_sm(int variant, bool nmax);
 // the streaming push (push_stream.cu): one block per SM, `shape` one of
 // stream_variant_count() (consumer warps x slots per lane)
