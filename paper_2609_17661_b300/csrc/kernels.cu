@@ -1209,23 +1209,36 @@ __device__ __forceinline__ int sort_key(const DevParams& P, uint32_t pos, uint8_
   return (group * P.N + cell) * 8 + band;
 }
 
+// Histogram of the sort keys: K slots per thread per tile (256 K consecutive
+// slots, slot t0 + k 256 + thread), all loads issued before the first use so
+// that enough bytes are in flight to stream at the copy rate.  The slots were
+// sorted at the previous sort and the particles moved a few cells since, so
+// a warp's 32 consecutive slots hold a few distinct keys (interleaved: the
+// particles of one cell and band spread over two or three new cells): one
+// atomic per distinct key of the warp (match.any), not one per run.
+template <int K>
 __global__ void __launch_bounds__(256) k_hist(DevParams P, uint32_t* counts) {
   const long long n = P.st->n_slots;
-  const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  for (long long i0 = (long long)blockIdx.x * blockDim.x; i0 < n; i0 += (long long)gridDim.x * blockDim.x) {
-    const long long i = i0 + threadIdx.x;
-    bool valid = i < n;
-    int key = 0;
-    if (valid) {
-      const uint8_t sp = P.sp[i];
-      valid = sp != PIC1D_SP_DEAD;
-      key = sort_key(P, P.pos[i], sp, P.u[i]);
+  const long long tile = 256ll * K;
+  for (long long t0 = (long long)blockIdx.x * tile; t0 < n; t0 += (long long)gridDim.x * tile) {
+    uint32_t pos[K];
+    float u[K];
+    uint8_t sp[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const long long i = t0 + k * 256 + threadIdx.x;
+      const bool in = i < n;
+      sp[k] = in ? P.sp[i] : (uint8_t)PIC1D_SP_DEAD;
+      pos[k] = in ? P.pos[i] : 0u;
+      u[k] = in ? P.u[i] : 0.0f;
     }
-    const unsigned vm = __ballot_sync(full, valid);
-    if (valid) {
-      const unsigned grp = __match_any_sync(vm, key);
-      if (lane == __ffs(grp) - 1) atomicAdd(counts + key, (unsigned)__popc(grp));
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const bool valid = sp[k] != PIC1D_SP_DEAD;
+      const int key = valid ? sort_key(P, pos[k], sp[k], u[k]) : -1;
+      const unsigned grp = __match_any_sync(0xffffffffu, key);
+      if (valid && lane == __ffs(grp) - 1) atomicAdd(counts + key, (unsigned)__popc(grp));
     }
   }
 }
@@ -1303,39 +1316,60 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t* cou
   }
 }
 
+// Scatter into key order: per tile of 256 K slots, the keys first, then one
+// cursor atomic per distinct key of a warp (all K issued before any result
+// is used), then the remaining fields, then the stores; the slots of one key
+// in a warp land on consecutive destinations.
+template <int K>
 __global__ void __launch_bounds__(256) k_scatter(DevParams P, long long* cursor, uint32_t* pos2, float* u2,
                                                  float* w2, uint8_t* sp2, uint64_t* id2) {
   const long long n = P.st->n_slots;
-  const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  for (long long i0 = (long long)blockIdx.x * blockDim.x; i0 < n; i0 += (long long)gridDim.x * blockDim.x) {
-    const long long i = i0 + threadIdx.x;
-    bool valid = i < n;
-    uint32_t pos = 0;
-    uint8_t sp = 0;
-    float uu = 0.0f;
-    int key = 0;
-    if (valid) {
-      sp = P.sp[i];
-      pos = P.pos[i];
-      uu = P.u[i];
-      valid = sp != PIC1D_SP_DEAD;
-      key = sort_key(P, pos, sp, uu);
+  const long long tile = 256ll * K;
+  for (long long t0 = (long long)blockIdx.x * tile; t0 < n; t0 += (long long)gridDim.x * tile) {
+    uint32_t pos[K];
+    float u[K];
+    uint8_t sp[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const long long i = t0 + k * 256 + threadIdx.x;
+      const bool in = i < n;
+      sp[k] = in ? P.sp[i] : (uint8_t)PIC1D_SP_DEAD;
+      pos[k] = in ? P.pos[i] : 0u;
+      u[k] = in ? P.u[i] : 0.0f;
     }
-    const unsigned vm = __ballot_sync(full, valid);
-    if (valid) {
-      const unsigned grp = __match_any_sync(vm, key);
-      const int leader = __ffs(grp) - 1;
-      long long b = 0;
-      if (lane == leader)
-        b = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(cursor + key), (unsigned long long)__popc(grp));
-      b = __shfl_sync(grp, b, leader);
-      const long long dst = b + __popc(grp & lanemask_lt());
-      pos2[dst] = pos;
-      u2[dst] = uu;
-      w2[dst] = P.w[i];
-      sp2[dst] = sp;
-      id2[dst] = P.id[i];
+    long long base[K];
+    unsigned grp[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const bool valid = sp[k] != PIC1D_SP_DEAD;
+      const int key = valid ? sort_key(P, pos[k], sp[k], u[k]) : -1;
+      grp[k] = __match_any_sync(0xffffffffu, key);
+      base[k] = 0;
+      if (valid && lane == __ffs(grp[k]) - 1)
+        base[k] = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(cursor + key),
+                                       (unsigned long long)__popc(grp[k]));
+    }
+    float w[K];
+    uint64_t id[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const long long i = t0 + k * 256 + threadIdx.x;
+      const bool valid = sp[k] != PIC1D_SP_DEAD;
+      w[k] = valid ? P.w[i] : 0.0f;
+      id[k] = valid ? P.id[i] : 0ull;
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const long long b = __shfl_sync(0xffffffffu, base[k], __ffs(grp[k]) - 1);
+      if (sp[k] != PIC1D_SP_DEAD) {
+        const long long dst = b + __popc(grp[k] & lanemask_lt());
+        pos2[dst] = pos[k];
+        u2[dst] = u[k];
+        w2[dst] = w[k];
+        sp2[dst] = sp[k];
+        id2[dst] = id[k];
+      }
     }
   }
 }
@@ -1751,16 +1785,30 @@ cudaError_t launch_field(const DevParams& P, double* E64, float* E32, double a, 
 int sort_bins(int N) { return 32 * N; }
 int scan_blocks(int N) { return (sort_bins(N) + kScanChunk - 1) / kScanChunk; }
 
+constexpr int kHistK = 8;       // slots per thread per tile of the histogram
+constexpr int kScatterK = 8;    // and of the scatter
+
+// blocks of 256 threads resident on `sms` SMs (the sort's kernels stride over
+// the slots with a grid that fills the GPU once)
+template <typename Kern>
+int resident_grid(Kern kern, int sms) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0) != cudaSuccess || per_sm < 1) per_sm = 4;
+  return sms * per_sm;
+}
+
 cudaError_t launch_sort(const DevParams& P, uint32_t* counts, long long* offsets, long long* bsum, uint32_t* pos2,
-                        float* u2, float* w2, uint8_t* sp2, uint64_t* id2, int grid, cudaStream_t s) {
+                        float* u2, float* w2, uint8_t* sp2, uint64_t* id2, int sms, cudaStream_t s) {
+  static const int hist_per_sm = resident_grid(k_hist<kHistK>, 1);
+  static const int scatter_per_sm = resident_grid(k_scatter<kScatterK>, 1);
   const int B = sort_bins(P.N), nb = scan_blocks(P.N);
   cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(uint32_t) * (size_t)B, s);
   if (e != cudaSuccess) return e;
-  k_hist<<<grid, 256, 0, s>>>(P, counts);
+  k_hist<kHistK><<<sms * hist_per_sm, 256, 0, s>>>(P, counts);
   k_scan_reduce<<<nb, kScanThreads, 0, s>>>(counts, B, bsum);
   k_scan_top<<<1, kScanThreads, 0, s>>>(bsum, nb, P);
   k_scan_apply<<<nb, kScanThreads, 0, s>>>(counts, B, bsum, offsets);
-  k_scatter<<<grid, 256, 0, s>>>(P, offsets, pos2, u2, w2, sp2, id2);
+  k_scatter<kScatterK><<<sms * scatter_per_sm, 256, 0, s>>>(P, offsets, pos2, u2, w2, sp2, id2);
   k_sort_done<<<1, 1, 0, s>>>(P);
   return cudaGetLastError();
 }

@@ -175,7 +175,6 @@ struct pic1d_ctx {
   unsigned long long* spc = nullptr;
   int push_grid = 0;      // grid of the current push variant
   int push_variant = 0;   // index into the push variants (particles per thread x occupancy)
-  int sort_grid = 0;      // blocks of the sort's histogram and scatter
   uint8_t* cflag = nullptr;   // cell flags of the streaming push
   float2* nmu2 = nullptr;     // mu at both nodes of each cell
   uint8_t* dflag = nullptr;   // damping-certainty table (table law with the limiter)
@@ -539,7 +538,7 @@ int do_sort(pic1d_ctx* c) {
   Nvtx range("sort");
   DevParams P = dev_params(c);
   const int o = 1 - c->cur;
-  CK(launch_sort(P, c->counts, c->offsets, c->bsum, c->pos[o], c->u[o], c->w[o], c->sp[o], c->id[o], c->sort_grid,
+  CK(launch_sort(P, c->counts, c->offsets, c->bsum, c->pos[o], c->u[o], c->w[o], c->sp[o], c->id[o], c->sms,
                  c->s),
      "sort");
   c->cur = o;
@@ -732,7 +731,6 @@ int pic1d_init(const pic1d_params* p, pic1d_ctx** out) {
     chain(dalloc(&c->ke_partial, c->sms * 8));     // at most 8 blocks of 256 threads per SM
     c->push_variant = default_push_variant();
     c->push_grid = c->sms * push_blocks_per_sm(c->push_variant, p->n_max_ppc > 0.0);
-    c->sort_grid = c->sms * 4;
     if (e == cudaSuccess) {
       chain(cudaMemsetAsync(c->E64, 0, N * sizeof(double), c->s));
       chain(cudaMemsetAsync(c->E32, 0, N * sizeof(float), c->s));
@@ -1636,7 +1634,7 @@ int ens_enqueue(pic1d_ens* e, int k, std::vector<int>& cur, std::vector<long lon
         ECK(cudaEventRecord(a, e->s), "ensemble timing");
       }
       ECK(launch_sort(P, c->counts, c->offsets, c->bsum, c->pos[o], c->u[o], c->w[o], c->sp[o], c->id[o],
-                      c->sort_grid, e->s),
+                      c->sms, e->s),
           "ensemble sort");
       ECK(ens_launch_flip(e->dlines, l, e->s), "ensemble sort");
       if (e->time_sorts) {

@@ -134,7 +134,7 @@ cudaError_t launch_topup(const DevParams& P, const int* cells, const long long* 
 cudaError_t launch_field(const DevParams& P, double* E64, float* E32, double four_pi_dt_jext, double cJ,
                          double dt_jext, double* field_partial, int grid_push, cudaStream_t s);
 cudaError_t launch_sort(const DevParams& P, uint32_t* counts, long long* offsets, long long* bsum,
-                        uint32_t* pos2, float* u2, float* w2, uint8_t* sp2, uint64_t* id2, int grid,
+                        uint32_t* pos2, float* u2, float* w2, uint8_t* sp2, uint64_t* id2, int sms,
                         cudaStream_t s);
 cudaError_t launch_pair_table(const float2* t, int Ng, int Ns, float4* out, cudaStream_t s);
 int sort_bins(int N);

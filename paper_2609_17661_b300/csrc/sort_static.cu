@@ -122,7 +122,7 @@ extern "C" int pic1d_sort_static(int32_t n_cells, int64_t n, const uint32_t* pos
   k_static_begin<<<1, 1, 0, s>>>(st, (long long)n);
   e = cudaGetLastError();
   if (e == cudaSuccess)
-    e = launch_sort(P, counts, offsets, bsum, pos_out, u_out, w_out, sp_out, id_out, std::max(1, sms) * 4, s);
+    e = launch_sort(P, counts, offsets, bsum, pos_out, u_out, w_out, sp_out, id_out, std::max(1, sms), s);
   if (e == cudaSuccess) {
     k_static_end<<<1, 1, 0, s>>>(st, reinterpret_cast<long long*>(n_out));
     e = cudaGetLastError();
