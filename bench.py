@@ -452,15 +452,17 @@ SUR_TENSOR_FLOP_PER_ROW = 2 * 2 * 64 * 64   # layers 2 and 3, 2 flop per multipl
 
 
 def surrogate_leg(cfg, view, stream, steps, value_plain, barrier):
-    """The same line and state with drag law SURROGATE: the network is trained
-    first (1e7 quadrature samples over r_eq in [2, 30], 20 epochs), then
-    `steps` steps are timed like the plain path."""
+    """The same line and state with drag law SURROGATE: the line's network is
+    trained first (1e7 quadrature samples over its own (gamma, s) box, 20
+    epochs of 8192, cosine schedule), then `steps` steps are timed like the
+    plain path.  (The ensemble workload trains one network for r_eq in
+    [2, 30] and reports its accuracy on its own line.)"""
     import torch
     from paper_2609_17661_b300 import Line
     cs = dict(cfg, drag_law=3)
     line = Line(cs, stream=stream.cuda_stream)
     line.sur_set_params(W.sur_init_params(0))
-    rep = line.train_surrogate(**W.SUR_TRAIN_ENSEMBLE_COSINE)
+    rep = line.train_surrogate(**W.sur_train_line(cfg["r_eq"]))
     line.set_state(view)
     line.sort()
     line.step(1)
@@ -483,7 +485,7 @@ def surrogate_leg(cfg, view, stream, steps, value_plain, barrier):
     tflops = rows * SUR_TENSOR_FLOP_PER_ROW / push_s / 1e12
     v = units / (ms * 1e-3)
     return {"value": v, "unit": "particle-steps/s", "steps": steps, "ms_per_step": ms / steps,
-            "vs_plain": v / value_plain, "drag": "surrogate (one network for r_eq in [2, 30], trained in the run)",
+            "vs_plain": v / value_plain, "drag": "surrogate (the line's own network, trained in the run)",
             "network_rows_per_particle_step": (d1["sur_rows"] - d0["sur_rows"]) / max(units, 1),
             "tangent_rows_per_particle_step": (d1["sur_rows_tangent"] - d0["sur_rows_tangent"]) / max(units, 1),
             "tensor": {"bound": "tensor", "achieved": tflops, "peak": peak[0], "unit": "TFLOP/s",

@@ -341,6 +341,12 @@ SUR_TRAIN_ENSEMBLE = dict(SUR_TRAIN, r_lo=2.0, r_hi=30.0)
 SUR_TRAIN_ENSEMBLE_COSINE = dict(SUR_TRAIN_ENSEMBLE, lr=3e-3, lr_final=1e-5)
 
 
+def sur_train_line(r_eq: float) -> dict:
+    """The single-line protocol (1e7 samples over the line's own (gamma, s)
+    box, 20 epochs of 8192, the cosine schedule) for the line at r_eq."""
+    return dict(SUR_TRAIN_COSINE, r_lo=float(r_eq), r_hi=float(r_eq))
+
+
 def sur_init_params(seed: int = 0) -> np.ndarray:
     """Seeded initial parameters (FP32): every weight and bias uniform in
     +-1/sqrt(fan_in) of its layer."""
