@@ -535,7 +535,7 @@ def run_ensemble(args):
     t_gen = time.perf_counter() - t0
     ens = Ensemble(cfgs)
     ens.lines[0].sur_set_params(W.sur_init_params(0))
-    rep = ens.lines[0].train_surrogate(**W.SUR_TRAIN_ENSEMBLE_COSINE)
+    rep = ens.lines[0].train_surrogate(**W.SUR_TRAIN_SHARED)
     for ln, st in zip(ens.lines, states):
         ln.set_state(st)
         ln.sort()

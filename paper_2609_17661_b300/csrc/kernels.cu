@@ -1,20 +1,26 @@
-// kernels.cu -- sm_103a kernels of the per-step particle loop.
+// kernels.cu -- sm_103a kernels of the per-step particle loop (the default
+// push, k_push_stream, is in push_stream.cu).
 //
-//   k_push     gather E, Strang-split drag around the Lorentz kick (Sec. 3),
+//   k_push     the per-thread pushes (variants of pic1d_set_variant): gather
+//              E, Strang-split drag around the Lorentz kick (Sec. 3),
 //              Monte-Carlo RICS scattering with recoil and pair creation
-//              (Sec. 3, App. A), move, charge-conserving int64 deposit through
-//              a shared-memory cell window with warp-segmented reduction,
-//              loss flags at the conducting walls, pair append.
-//   k_inject   surface supply at both footpoints (RATE mode).
+//              (Sec. 3, App. A), move, charge-conserving int64 deposit from
+//              per-lane current registers, loss flags at the conducting
+//              walls, pair append.
+//   k_push_sur the push with drag law SURROGATE (the network on tcgen05).
+//   k_inject / k_topup   surface supply (RATE) and the atmosphere's top-up.
 //   k_field    Ampere with the external current in FP64 (Sec. 3) + totals.
 //   k_finalize per-step scalars in a fixed summation order.
 //   k_hist / k_scan / k_scatter   periodic cell sort (drops removed slots).
+//   k_annih_scan / k_annih_cell   annihilation at n_max after a sort.
+//   k_ens_*    the ensemble: many lines per launch.
 //   k_table    drag/rate table by FP64 quadrature over the stellar disk
 //              (Sec. 2.2, Eq. scatteringNdot and Eq. contdrag).
 //
-// The particle SoA is read with 128-bit loads: one thread owns 4 consecutive
-// particles, a block owns a contiguous range of tiles, so that cell-sorted
-// particles of one block fall into a narrow window of cells.
+// The per-thread pushes read the particle SoA with PPT-wide loads (a thread
+// owns PPT consecutive particles of a tile) and blocks take contiguous chunks
+// of tiles, so that cell-sorted particles of one block fall into a narrow
+// window of cells.
 #include <math.h>
 
 #include "pic1d_internal.h"
@@ -300,18 +306,19 @@ __device__ __forceinline__ void window_drain(long long* sWin, int win_lo, const 
   }
 }
 
-// The push kernel.  A thread owns PPT consecutive particles per tile (one
+// The per-thread push.  A thread owns PPT consecutive particles per tile (one
 // PPT-wide access per SoA array); blocks take chunks of kChunkTiles tiles
 // (kBlock * PPT particles each) from a global counter, so that expensive
 // regions of the line (pair zones, dense footpoints) are shared by all SMs.
-// The current registers of a thread (cells c_ref-1 .. c_ref+1) persist across
-// its particles and are flushed warp-wide (exact group sums) only when some
-// lane needs a cell outside its anchor range; block sums go through a
-// shared-memory cell window anchored at each chunk's first particle, whose
-// touched range is drained to global memory at the end of the chunk.  The
-// lepton density of the pair cap is summed per warp in a warp-uniform pending
-// register while the warp's contributions stay in one cell.  Slot indices are
-// 32-bit (capacity < 2^31).  ATMO (inject mode TOPUP): gravity, and the plasma
+// A lane's current goes into int64 registers for three cells (c_ref-1 ..
+// c_ref+1; with LEAN the two-anchor window JWin) that persist across its
+// particles and are added to J with 64-bit atomics, by that lane alone, when
+// a path falls outside them (exact and order-independent).  The lepton
+// density of the pair cap is summed per warp in a warp-uniform pending
+// register while the warp's contributions stay in one cell, else through a
+// shared-memory cell window anchored at each chunk's first particle and
+// drained to global memory at the end of the chunk.  Slot indices are 32-bit
+// (capacity < 2^31).  ATMO (inject mode TOPUP): gravity, and the plasma
 // weight of each atmosphere cell after the move, summed into P.atmo_w (the
 // atmosphere and the two cells around it are never fast cells, so every
 // particle that ends a step there goes through push_one).
