@@ -341,8 +341,9 @@ SUR_TRAIN_ENSEMBLE = dict(SUR_TRAIN, r_lo=2.0, r_hi=30.0)
 SUR_TRAIN_ENSEMBLE_COSINE = dict(SUR_TRAIN_ENSEMBLE, lr=3e-3, lr_final=1e-5)
 # the shared network's own protocol: the (r_eq, gamma, s) box of the ensemble
 # is a family of lines, and twice the samples over twice the epochs bring its
-# median drag error to the single line's (measured: 1e7 x 20 epochs 1.8e-3,
-# 2e7 x 40 epochs 9.7e-4)
+# median drag error close to a single line's (measured: 1e7 x 20 epochs
+# 1.8e-3; 2e7 x 40 epochs 9.7e-4 .. 1.02e-3; more samples or epochs, or a
+# higher rate, stay at 1.0 .. 1.2e-3: the 64-wide network's limit)
 SUR_TRAIN_SHARED = dict(SUR_TRAIN_ENSEMBLE_COSINE, n_samples=20_000_000, epochs=40)
 
 
