@@ -1394,9 +1394,10 @@ __global__ void k_sort_done(DevParams P) {
 // pair-electron weight and lists the cells above n_max with the weight A each
 // species loses.  k_annih_cell: one block per listed cell finds, per species,
 // the smallest key theta whose prefix weight (keys <= theta) reaches A by a
-// 64-step bisection over the key space, takes all weight below theta and the
-// rest of A from the particle at theta, and moves E at the cell by the current
-// of the removed charge carried to the cell's left node.
+// radix select over the key's eight bytes (eight passes over the cell's
+// leptons), takes all weight below theta and the rest of A from the particle
+// at theta, and moves E at the cell by the current of the removed charge
+// carried to the cell's left node.
 // --------------------------------------------------------------------------
 __device__ __forceinline__ unsigned long long annih_key(unsigned long long id, long long step) {
   return mix64(id ^ mix64((unsigned long long)step ^ 0xA1111A7Eull));
@@ -1460,11 +1461,34 @@ __device__ __forceinline__ void block_sum2(long long& x, long long& y, long long
   __syncthreads();
 }
 
+// inclusive scan of one int64 per thread over a kAnnThreads block (every
+// thread of the block calls it; `tot` holds kAnnThreads / 32 values)
+__device__ __forceinline__ long long block_incl_scan(long long v, long long* tot) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  long long x = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const long long y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
+  }
+  if (lane == 31) tot[w] = x;
+  __syncthreads();
+  long long before = 0;
+  for (int k = 0; k < w; ++k) before += tot[k];
+  __syncthreads();
+  return before + x;
+}
+
 __global__ void __launch_bounds__(kAnnThreads) k_annih_cell(DevParams P, const uint32_t* counts,
                                                             const long long* offsets, const int* list,
                                                             const long long* amount, const unsigned* count,
                                                             double* E64, float* E32, double cJ) {
   __shared__ long long sh[2][kAnnThreads / 32];
+  __shared__ unsigned long long sHist[2][kAnnThreads];   // one byte's 256 bins per species
+  __shared__ long long scan_tot[kAnnThreads / 32];
+  __shared__ unsigned long long sPfx[2];
+  __shared__ long long sWb[2];
+  static_assert(kAnnThreads == 256, "one histogram bin per thread");
   const unsigned ncell = *count;
   const uint32_t fmask = (1u << P.F) - 1u;
   // the step just completed, from the device (also right inside an
@@ -1475,37 +1499,46 @@ __global__ void __launch_bounds__(kAnnThreads) k_annih_cell(DevParams P, const u
     const long long A = amount[item];
     long long a[2], b[2];
     lepton_ranges(P, counts, offsets, c, a, b);
-    // bisection: theta[s] = the smallest key with sum_{key <= theta, species s} w >= A
-    unsigned long long lo[2] = {0ull, 0ull}, hi[2] = {~0ull, ~0ull};
-    for (int it = 0; it < 64; ++it) {
-      const unsigned long long mid0 = lo[0] + (hi[0] - lo[0]) / 2, mid1 = lo[1] + (hi[1] - lo[1]) / 2;
-      long long s0 = 0, s1 = 0;
+    // theta[s] = the smallest key with sum_{key <= theta, species s} w >= A,
+    // found a byte at a time from the top (radix select): pass d sums the
+    // weight of the keys that share the bytes found so far by their next
+    // byte, and the byte where the running sum reaches A is the next one of
+    // theta; sWb then holds the weight of the keys below theta
+    if (threadIdx.x < 2) { sPfx[threadIdx.x] = 0ull; sWb[threadIdx.x] = 0; }
+    for (int pass = 0; pass < 8; ++pass) {
+      const int shift = 56 - 8 * pass;
+      sHist[0][threadIdx.x] = 0ull;
+      sHist[1][threadIdx.x] = 0ull;
+      __syncthreads();
+      const unsigned long long pf0 = sPfx[0], pf1 = sPfx[1];
       for (int g = 0; g < 2; ++g)
         for (long long i = a[g] + threadIdx.x; i < b[g]; i += kAnnThreads) {
           const uint8_t sp = P.sp[i];
           if (sp != PIC1D_SP_ELECTRON && sp != PIC1D_SP_POSITRON) continue;
+          const int sg = sp == PIC1D_SP_POSITRON ? 1 : 0;
           const unsigned long long key = annih_key(P.id[i], step);
-          const long long w = __float2ll_rn(P.w[i] * 4096.0f);
-          if (sp == PIC1D_SP_ELECTRON) { if (key <= mid0) s0 += w; }
-          else if (key <= mid1) s1 += w;
+          if (pass > 0 && (key >> (shift + 8)) != (sg ? pf1 : pf0)) continue;
+          const unsigned long long w = (unsigned long long)__float2ll_rn(P.w[i] * 4096.0f);
+          atomicAdd(&sHist[sg][(key >> shift) & 255ull], w);
         }
-      block_sum2(s0, s1, sh);
-      if (s0 >= A) hi[0] = mid0; else lo[0] = mid0 + 1;
-      if (s1 >= A) hi[1] = mid1; else lo[1] = mid1 + 1;
-    }
-    const unsigned long long th0 = lo[0], th1 = lo[1];
-    // weight strictly below theta
-    long long B0 = 0, B1 = 0;
-    for (int g = 0; g < 2; ++g)
-      for (long long i = a[g] + threadIdx.x; i < b[g]; i += kAnnThreads) {
-        const uint8_t sp = P.sp[i];
-        if (sp != PIC1D_SP_ELECTRON && sp != PIC1D_SP_POSITRON) continue;
-        const unsigned long long key = annih_key(P.id[i], step);
-        const long long w = __float2ll_rn(P.w[i] * 4096.0f);
-        if (sp == PIC1D_SP_ELECTRON) { if (key < th0) B0 += w; }
-        else if (key < th1) B1 += w;
+      __syncthreads();
+      long long nb[2], nw[2];
+      bool hit[2];
+      for (int sg = 0; sg < 2; ++sg) {
+        const long long v = (long long)sHist[sg][threadIdx.x];
+        const long long incl = block_incl_scan(v, scan_tot);
+        const long long need = A - sWb[sg];
+        hit[sg] = incl - v < need && incl >= need;
+        nb[sg] = (long long)(((sg ? pf1 : pf0) << 8) | (unsigned long long)threadIdx.x);
+        nw[sg] = sWb[sg] + (incl - v);
       }
-    block_sum2(B0, B1, sh);
+      __syncthreads();
+      for (int sg = 0; sg < 2; ++sg)
+        if (hit[sg]) { sPfx[sg] = (unsigned long long)nb[sg]; sWb[sg] = nw[sg]; }
+      __syncthreads();
+    }
+    const unsigned long long th0 = sPfx[0], th1 = sPfx[1];
+    const long long B0 = sWb[0], B1 = sWb[1];
     // remove the weight; X = sum q delta frac (fixed point) of the removed charge
     long long X = 0, unused = 0;
     for (int g = 0; g < 2; ++g)
