@@ -596,3 +596,67 @@ def test_a_device_wait_that_gives_up_is_reported_and_the_line_goes_on():
     Eo, _ = S.fields()
     assert _relmax(Eg, Eo) <= RTOL
     assert line.diag()["rc"] == 0
+
+
+def test_degenerate_particles_match_the_oracle():
+    """Particles on the degenerate points of the method, two steps against
+    the oracle particle by particle, and the push's J of the first step
+    against the integer deposit of their paths: exactly on the wall nodes
+    moving out and in, on interior nodes and cell centres, one quantum inside
+    the line's ends, u = 0 and -0, |u| tiny and beyond the table's top
+    (gamma > 10^G, the clamped lookup), every species, weights 0.5 .. 2;
+    inside a random plasma so that the field is not trivial."""
+    from deposit_ref import step_current
+    cfg = W.config("C1", capacity=200000)
+    N = cfg["n_cells"]
+    F = W.fbits(N)
+    top = N << F
+    cell = 1 << F
+    positions = [0, 1, cell - 1, cell, cell + cell // 2, (N // 2) * cell, (N // 2) * cell - 1, top - cell,
+                 top - cell // 2, top - 2, top - 1]
+    momenta = [0.0, -0.0, 1e-30, -1e-30, 0.3, -0.3, 30.0, -30.0, 3e3, -3e3, 1e9, -1e9]
+    combos = [(p, u, s) for p in positions for u in momenta for s in (W.SP_ELEC, W.SP_POSI, W.SP_ION, W.SP_ATMO)]
+    edge = W.empty_state(len(combos))
+    edge["pos"][:] = np.array([c[0] for c in combos], np.uint32)
+    edge["u"][:] = np.array([c[1] for c in combos], np.float32)
+    edge["sp"][:] = np.array([c[2] for c in combos], np.uint8)
+    edge["w"][:] = np.resize(np.array([0.5, 1.0, 2.0], np.float32), len(combos))
+    edge["id"][:] = np.arange(len(combos), dtype=np.uint64) + 10**8
+    bg = W.load_random(cfg, 4000, u_scale=10.0, seed=31)
+    st = {k: np.concatenate([edge[k], bg[k]]) for k in edge}
+    line = _line(cfg)
+    E = _field0(N)
+    line.set_state(st, E=E)
+    line.step(1)
+    after = line.particles(alive_only=False)
+    _, J = line.fields()
+    np.testing.assert_array_equal(J, step_current(st, after, N))
+    line.step(1)
+    S = _orc(cfg, st, E)
+    S.step(2)
+    dg, do = line.diag(), S.diag()
+    for k in ("n_alive", "lost_north", "lost_south", "pairs_created", "scatters", "limiter_branch", "newton_branch"):
+        assert dg[k] == do[k], (k, dg[k], do[k])
+    g, o = _gpu_particles(line, N), _by_id(S.particles())
+    assert g["id"].tolist() == o["id"].tolist()
+    assert np.array_equal(g["sp"].astype(np.int32), o["sp"])
+    # FP32 momenta agree to 1e-5 of the largest momentum in their arithmetic:
+    # a particle's own |u| before and after, and for a pair child its
+    # parent's |u| at the start of the step that made it (a scattering from
+    # u = 3000 down to u ~ 90 cancels four digits)
+    S1 = _orc(cfg, st, E)
+    S1.step(1)
+    p1 = S1.particles()
+    scale_of = {}
+    for step, (ids, us) in enumerate(((st["id"], st["u"]), (p1["id"], p1["u"]))):
+        for i, u in zip(ids.tolist(), np.abs(us.astype(np.float64)).tolist()):
+            scale_of[i] = max(scale_of.get(i, 0.0), u)
+            for m in (0, 1):
+                c = O.child_id(i, step, m)
+                scale_of[c] = max(scale_of.get(c, 0.0), u)
+    scale = np.array([max(scale_of.get(int(i), 0.0), abs(u)) for i, u in zip(o["id"].tolist(), o["u"].tolist())])
+    err = np.abs(g["u"].astype(np.float64) - o["u"])
+    tol = 1e-5 * scale + 1e-6
+    assert np.all(err <= tol), float(np.max(err / tol))
+    assert np.max(np.abs(g["s"] - o["s"])) <= 2 * (2.0 ** -F + 1e-6)
+    assert dg["lost_north"] > 0 and dg["lost_south"] > 0
