@@ -24,6 +24,13 @@
  * cell c, in units of 2^-F); the physical current density is
  * J = q_p 2^(-F-12) J_int / dt.  E lives at cell centres (FP64).
  *
+ * Scattering draw: a lepton in a pair zone with probability p_sc = min(1,
+ * Ndot dt) draws one Philox4x32-10 block with counter (id_lo, id_hi, step,
+ * 'RICS') and key = seed when p_sc >= 2^-24, and scatters when U = ((x0 >>
+ * 8) + 1) 2^-24 (on (0, 1]) is <= p_sc; the de-excitation angle uses
+ * (x1 >> 8) 2^-24.  A p_sc below 2^-24, which the 24-bit uniform cannot
+ * resolve, never scatters and takes no draw.
+ *
  * Conventions for every entry point:
  *   - return 0 on success, a positive warning (state consistent) or a
  *     negative error; pic1d_last_error() gives a message.  After

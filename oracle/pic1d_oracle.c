@@ -128,6 +128,9 @@ void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint3
 
 /* 24-bit uniform in [0,1): identical in FP32 and FP64 */
 static double orc_u24(uint32_t x) { return (double)(x >> 8) * (1.0 / 16777216.0); }
+/* a uniform on (0, 1]: ((x >> 8) + 1) 2^-24 */
+static double orc_u24_open(uint32_t x) { return (double)((x >> 8) + 1u) * (1.0 / 16777216.0); }
+#define ORC_DRAW_MIN (1.0 / 16777216.0)
 
 /* SplitMix64 finaliser (Steele, Lea, Flood 2014) -- used only to derive
  * stable identifiers for created particles. */
@@ -1376,11 +1379,14 @@ static void orc_push_range(orc_sim* S, int64_t k0, int64_t k1, const uint32_t ke
       orc_drag_code(S, u, s, &F, NULL, &rate);
       double psc = rate * dt;
       if (psc > 1.0) { psc = 1.0; A->psc_clamped++; }
-      if (psc > 0.0) {
+      /* the draw's uniform lies on the lattice (0, 1] in steps of 2^-24 and
+       * the lepton scatters when it is <= p_sc: below 2^-24 there is nothing
+       * to draw */
+      if (psc >= ORC_DRAW_MIN) {
         uint32_t ctr[4] = { (uint32_t)S->id[k], (uint32_t)(S->id[k] >> 32), (uint32_t)S->step, ORC_TAG_RICS };
         uint32_t r[4];
         orc_philox4x32_10(ctr, key, r);
-        if (orc_u24(r[0]) < psc) {
+        if (orc_u24_open(r[0]) <= psc) {
           A->scatters++;
           double b = orc_node_interp(S, S->node_b, s);
           double mu = orc_node_interp(S, S->node_mu, s);

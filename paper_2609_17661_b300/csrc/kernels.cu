@@ -106,12 +106,12 @@ __device__ __forceinline__ PushOut push_one(const DevParams& P, uint32_t idx, ui
     const DragVal dv = drag_eval(P, u, S, false);
     float psc = P.drag_k * expf(dv.lnN) * P.dt;
     if (psc > 1.0f) { psc = 1.0f; tally(T, C_CLAMP); }
-    if (psc > 0.0f) {
+    if (psc >= kDrawMin) {
       ++T.n_draw;
       o.pid = P.id[idx];
       const uint4 r = philox4x32_10(
           make_uint4((uint32_t)o.pid, (uint32_t)(o.pid >> 32), (uint32_t)P.step, kTagRics), P.key0, P.key1);
-      if (unit24(r.x) < psc) {
+      if (unit24_open(r.x) <= psc) {
         tally(T, C_SCAT);
         const float beta = u * rsqrtf(fmaf(u, u, 1.0f));
         const float d = (S.mu > beta) ? 1.0f : -1.0f;
@@ -732,12 +732,12 @@ __device__ void sur_tile(const DevParams& P, sur::MlpCta& M, uint32_t tile, uint
     if (mc) {
       float psc = P.drag_k * expf(dv.lnN) * P.dt;
       if (psc > 1.0f) { psc = 1.0f; tally(T, C_CLAMP); }
-      if (psc > 0.0f) {
+      if (psc >= kDrawMin) {
         ++T.n_draw;
         pid = P.id[idx];
         const uint4 r = philox4x32_10(
             make_uint4((uint32_t)pid, (uint32_t)(pid >> 32), (uint32_t)P.step, kTagRics), P.key0, P.key1);
-        if (unit24(r.x) < psc) {
+        if (unit24_open(r.x) <= psc) {
           tally(T, C_SCAT);
           const float beta = u * rsqrtf(fmaf(u, u, 1.0f));
           const float d = (S.mu > beta) ? 1.0f : -1.0f;

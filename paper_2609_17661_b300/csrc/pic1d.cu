@@ -177,7 +177,7 @@ struct pic1d_ctx {
   int push_variant = 0;   // index into the push variants (particles per thread x occupancy)
   uint8_t* cflag = nullptr;   // cell flags of the streaming push
   float2* nmu2 = nullptr;     // mu at both nodes of each cell
-  uint8_t* dflag = nullptr;   // damping-certainty table (table law with the limiter)
+  uint8_t* dflag = nullptr;   // branch-certainty table of the table law (damping, Newton, rate)
   int sms = 0;
   long long step = 0;
   std::string err;
@@ -516,8 +516,9 @@ int build_tables(pic1d_ctx* c) {
          "table kernel");
       CK(dalloc(&c->tpair, (size_t)2 * (Ns - 1) * Ng), "alloc table");
       CK(launch_pair_table(c->table, Ng, Ns, c->tpair, c->s), "pair table");
-      if (p.drag_law == PIC1D_DRAG_TABLE && c->tau_min > 0.0) {
-        // where the limiter test is certain to damp (the push skips its lookup)
+      if (p.drag_law == PIC1D_DRAG_TABLE) {
+        // where the limiter test is certain (the push skips its lookup), and
+        // where no lepton can scatter (the Monte-Carlo step skips its rate)
         const DevParams Q = dev_params(c);
         CK(dalloc(&c->dflag, (size_t)2 * (Ns - 1) * kDampNE), "alloc damping flags");
         CK(launch_damp_flags(c->tpair, Ng, Ns, Q.t_scale, Q.drag_k, Q.tau_min, Q.dt, c->dflag, c->s),

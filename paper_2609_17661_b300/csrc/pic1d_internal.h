@@ -26,6 +26,7 @@ constexpr uint8_t CF_DENSN = 4;      // a cell of the pair cap's density within 
 // entries of the branch-certainty table
 constexpr uint8_t kDampCertain = 1;  // the limiter test chooses damping
 constexpr uint8_t kNewtonStill = 2;  // it chooses Newton, whose update leaves u unchanged in FP32
+constexpr uint8_t kRateNil = 4;      // the scattering probability is below the draw's resolution 2^-24
 // damping-certainty table of the streaming push: gamma^2 in half-octaves,
 // index (bits of (float)gamma^2 >> 22) - kDampE2Base, kDampNE of them
 constexpr unsigned kDampE2Base = 254;    // bits of 1.0f >> 22

@@ -26,6 +26,11 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 }
 
 __device__ __forceinline__ float unit24(uint32_t x) { return (float)(x >> 8) * (1.0f / 16777216.0f); }
+// the scattering draw's uniform on the lattice (0, 1] in steps of 2^-24 (exact
+// in FP32): a lepton scatters when it is <= p_sc, so a p_sc below 2^-24 can
+// never scatter and is not drawn for
+__device__ __forceinline__ float unit24_open(uint32_t x) { return (float)((x >> 8) + 1u) * (1.0f / 16777216.0f); }
+constexpr float kDrawMin = 0x1p-24f;
 
 // SplitMix64 finaliser (Steele, Lea, Flood 2014): stable ids of created particles
 __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
@@ -327,7 +332,7 @@ __device__ __forceinline__ float drag_half_flagged(const DevParams& P, const Sit
     const unsigned e2 = (__float_as_uint(q) >> 22) - kDampE2Base;
     if (e2 < (unsigned)kDampNE) {
       const int sg = (u0 >= 0.0f) ? 0 : 1;
-      const unsigned f = __ldg(P.dflag + ((size_t)(sg * (P.Ns - 1) + S.j) * kDampNE + e2));
+      const unsigned f = __ldg(P.dflag + ((size_t)(sg * (P.Ns - 1) + S.j) * kDampNE + e2)) & 3u;
       if (f == kDampCertain) {
         ++n_lim;
         const float ut = S.mu * rsqrtf(1.0f - S.mu * S.mu);

@@ -139,16 +139,27 @@ __device__ __forceinline__ void stream_one(const DevParams& P, uint32_t gidx, ui
   // 5. Monte-Carlo RICS in the pair zone
   bool make_pair = false;
   float Pg = 0.0f;
-  if (mc) {
+  bool nil = false;
+  if (mc && P.dflag) {
+    // table law: where every node the lookup can read gives p_sc < 2^-24,
+    // there is no draw to make and no rate to evaluate
+    const float q = fmaf(u, u, 1.0f);
+    const unsigned e2 = (__float_as_uint(q) >> 22) - kDampE2Base;
+    if (e2 < (unsigned)kDampNE) {
+      const int sg = (u >= 0.0f) ? 0 : 1;
+      nil = (__ldg(P.dflag + ((size_t)(sg * (P.Ns - 1) + S.j) * kDampNE + e2)) & kRateNil) != 0;
+    }
+  }
+  if (mc && !nil) {
     const DragVal dv = drag_eval(P, u, S, false);
     float psc = P.drag_k * expf(dv.lnN) * P.dt;
     if (psc > 1.0f) { psc = 1.0f; tally(T, C_CLAMP); }
-    if (psc > 0.0f) {
+    if (psc >= kDrawMin) {
       ++T.n_draw;
       o.pid = P.id[gidx];
       const uint4 r = philox4x32_10(
           make_uint4((uint32_t)o.pid, (uint32_t)(o.pid >> 32), (uint32_t)P.step, kTagRics), P.key0, P.key1);
-      if (unit24(r.x) < psc) {
+      if (unit24_open(r.x) <= psc) {
         tally(T, C_SCAT);
         make_pair = rics_scatter(P, S, r.y, u, Pg);
       }
@@ -455,7 +466,10 @@ __global__ void __launch_bounds__(32 * NW, 1) k_push_stream(DevParams P) {
 // |u| is at most sqrt(q_hi - 1).  It is kNewtonStill when the test is
 // certain to choose the Newton branch there and that branch's update moves u
 // by less than a quarter of the FP32 spacing of the smallest |u| of the
-// half-octave, so that the half-step returns u unchanged.
+// half-octave, so that the half-step returns u unchanged.  Bit kRateNil marks
+// the entries where the scattering probability drag_k N dt of every node the
+// lookup reads is below the draw's resolution 2^-24 (no lepton there can
+// scatter, so the Monte-Carlo step has nothing to evaluate or draw).
 __global__ void k_damp_flags(const float4* tpair, int Ng, int Ns, float t_scale, float drag_k, float tau_min, float dt,
                              uint8_t* out) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -484,10 +498,11 @@ __global__ void k_damp_flags(const float4* tpair, int Ng, int Ns, float t_scale,
     neg += (f0 < 0.0) + (f1 < 0.0);
     fmn = fmin(fmn, fmin(fabs(f0), fabs(f1)));
   }
-  double fmx = 0.0;
+  double fmx = 0.0, lmx = -INFINITY;
   for (int i = i_lo; i <= i_hi; ++i) {
     const float4 a = row[i];
     fmx = fmax(fmx, fmax(fabs((double)a.x), fabs((double)a.z)));
+    lmx = fmax(lmx, fmax((double)a.y, (double)a.w));
   }
   const int nodes = 2 * (i_hi - i_lo + 1);
   const double u_lo = sqrt(fmax(q_lo - 1.0, 0.0)), u_hi = sqrt(fmax(q_hi - 1.0, 0.0));
@@ -503,7 +518,11 @@ __global__ void k_damp_flags(const float4* tpair, int Ng, int Ns, float t_scale,
     const double ulp = ldexp(1.0, ilogb(u_lo) - 23);
     still = fk * (double)tau_min < u_lo * (1.0 - 1e-4) && 2.0 * h * fk <= 0.25 * ulp;
   }
-  out[idx] = damp ? kDampCertain : (still ? kNewtonStill : 0);
+  // the bilinear ln N is a convex combination of the nodes it reads, so p_sc
+  // = drag_k exp(ln N) dt is at most that of their largest ln N; a margin of
+  // 1e-3 covers the FP32 interpolation and expf
+  const bool nil = (double)drag_k * exp(lmx) * (double)dt < 0x1p-24 * (1.0 - 1e-3);
+  out[idx] = (uint8_t)((damp ? kDampCertain : (still ? kNewtonStill : 0)) | (nil ? kRateNil : 0));
 }
 
 }  // namespace

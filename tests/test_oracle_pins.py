@@ -610,9 +610,9 @@ def test_pair_yield_brute_force_tiny():
             if nodes["zone"][c]:
                 _, _, rate = S.drag(u, p["s"])
                 psc = min(1.0, rate * dt)
-                if psc > 0:
+                if psc >= 2.0 ** -24:
                     r = _py_philox([p["id"] & 0xFFFFFFFF, p["id"] >> 32, step, 0x52494353], key)
-                    if (r[0] >> 8) / 16777216.0 < psc:
+                    if ((r[0] >> 8) + 1) / 16777216.0 <= psc:
                         bb = S.node_interp(1, p["s"])
                         mu = S.node_interp(2, p["s"])
                         d = 1.0 if mu > u / math.sqrt(1 + u * u) else -1.0

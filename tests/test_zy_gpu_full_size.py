@@ -162,11 +162,15 @@ def compare_sample_with_oracle(cfg, snap0, snap1, E0, step, S=None):
         uk = float(snap0["u"][k]) + qm * S.gather(s0[k]) * dt
         _, _, rate = S.drag(uk, s0[k])
         psc = min(1.0, rate * dt)
-        if psc <= 0.0:
+        # the draw is made for p_sc >= 2^-24, the lepton scatters when the
+        # uniform ((x >> 8) + 1) 2^-24 is <= p_sc
+        if abs(psc - 2.0 ** -24) <= 1e-4 * 2.0 ** -24:
+            keep[k] = False
+        if psc < 2.0 ** -24:
             continue
         pid = int(snap0["id"][k])
         r = O.philox4x32_10([pid & 0xFFFFFFFF, pid >> 32, step & 0xFFFFFFFF, TAG_RICS], key)
-        U = float(int(r[0]) >> 8) * 2.0 ** -24
+        U = float((int(r[0]) >> 8) + 1) * 2.0 ** -24
         if abs(U - psc) <= 1e-4 * psc:
             keep[k] = False
         mu = S.node_interp(2, s0[k])
