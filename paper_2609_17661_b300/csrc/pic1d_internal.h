@@ -27,10 +27,13 @@ constexpr uint8_t CF_DENSN = 4;      // a cell of the pair cap's density within 
 constexpr uint8_t kDampCertain = 1;  // the limiter test chooses damping
 constexpr uint8_t kNewtonStill = 2;  // it chooses Newton, whose update leaves u unchanged in FP32
 constexpr uint8_t kRateNil = 4;      // the scattering probability is below the draw's resolution 2^-24
-// damping-certainty table of the streaming push: gamma^2 in half-octaves,
-// index (bits of (float)gamma^2 >> 22) - kDampE2Base, kDampNE of them
-constexpr unsigned kDampE2Base = 254;    // bits of 1.0f >> 22
-constexpr int kDampNE = 128;             // gamma^2 up to 2^64
+// index of the branch-certainty table in gamma^2: the exponent and the top
+// kDampMant mantissa bits of (float)gamma^2, (bits >> kDampShift) -
+// kDampE2Base, kDampNE of them (gamma^2 up to 2^64)
+constexpr int kDampMant = 1;
+constexpr int kDampShift = 23 - kDampMant;
+constexpr unsigned kDampE2Base = 0x3F800000u >> kDampShift;   // 1.0f
+constexpr int kDampNE = 64 << kDampMant;
 
 // Device-side counters, accumulated over the life of the context.
 struct Counters {

@@ -329,7 +329,7 @@ __device__ __forceinline__ float drag_half_flagged(const DevParams& P, const Sit
                                                    unsigned& n_newt) {
   if (P.dflag) {
     const float q = fmaf(u0, u0, 1.0f);
-    const unsigned e2 = (__float_as_uint(q) >> 22) - kDampE2Base;
+    const unsigned e2 = (__float_as_uint(q) >> kDampShift) - kDampE2Base;
     if (e2 < (unsigned)kDampNE) {
       const int sg = (u0 >= 0.0f) ? 0 : 1;
       const unsigned f = __ldg(P.dflag + ((size_t)(sg * (P.Ns - 1) + S.j) * kDampNE + e2)) & 3u;

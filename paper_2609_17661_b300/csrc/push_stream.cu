@@ -144,7 +144,7 @@ __device__ __forceinline__ void stream_one(const DevParams& P, uint32_t gidx, ui
     // table law: where every node the lookup can read gives p_sc < 2^-24,
     // there is no draw to make and no rate to evaluate
     const float q = fmaf(u, u, 1.0f);
-    const unsigned e2 = (__float_as_uint(q) >> 22) - kDampE2Base;
+    const unsigned e2 = (__float_as_uint(q) >> kDampShift) - kDampE2Base;
     if (e2 < (unsigned)kDampNE) {
       const int sg = (u >= 0.0f) ? 0 : 1;
       nil = (__ldg(P.dflag + ((size_t)(sg * (P.Ns - 1) + S.j) * kDampNE + e2)) & kRateNil) != 0;
@@ -477,10 +477,11 @@ __global__ void k_damp_flags(const float4* tpair, int Ng, int Ns, float t_scale,
   const int h = idx % kDampNE;
   const int j = (idx / kDampNE) % (Ns - 1);
   const int sg = idx / (kDampNE * (Ns - 1));
-  const int e = (int)kDampE2Base + h;                  // (float bits of q) >> 22
-  const int ex = (e >> 1) - 127;                        // exponent of q
-  const double q_lo = ldexp(1.0 + 0.5 * (double)(e & 1), ex);
-  const double q_hi = q_lo + ldexp(0.5, ex);
+  const int e = (int)kDampE2Base + h;                  // (float bits of q) >> kDampShift
+  const int ex = (e >> kDampMant) - 127;                // exponent of q
+  const double step = 1.0 / (double)(1 << kDampMant);   // the bin's width in units of 2^ex
+  const double q_lo = ldexp(1.0 + step * (double)(e & ((1 << kDampMant) - 1)), ex);
+  const double q_hi = q_lo + ldexp(step, ex);
   // t = 0.5 log2(q) t_scale in FP32 by the push; a slack of 1e-3 node units
   const double t_lo = fmax(0.5 * log2(q_lo) * (double)t_scale - 1e-3, 0.0);
   const double t_hi = 0.5 * log2(q_hi) * (double)t_scale + 1e-3;
