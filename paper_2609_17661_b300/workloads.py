@@ -334,16 +334,19 @@ SUR_N_PARAMS = sum(o * i + o for o, i in SUR_LAYERS)
 # lr 1e-3 with batches of 8192.
 SUR_TRAIN = dict(n_samples=10_000_000, epochs=20, batch=8192, lr=1e-3, r_lo=20.0, r_hi=20.0, seed=3,
                  n_val=100_000, val_seed=1003)
-# the same run with a cosine decay of the learning rate from 3e-3 to 1e-5
-SUR_TRAIN_COSINE = dict(SUR_TRAIN, lr=3e-3, lr_final=1e-5)
+# the same run with a cosine decay of the learning rate from 1e-2 to 1e-5
+# (measured median drag errors of a line's network: peak 1e-3 constant
+# 2.4e-3; cosine from 3e-3 8.6e-4; from 1e-2 4.4e-4 .. 4.6e-4; from 2e-2
+# 5e-4 .. 7.7e-4; from 3e-2 it diverges)
+SUR_TRAIN_COSINE = dict(SUR_TRAIN, lr=1e-2, lr_final=1e-5)
 # one network for every line of the r_eq in [2, 30] ensemble
 SUR_TRAIN_ENSEMBLE = dict(SUR_TRAIN, r_lo=2.0, r_hi=30.0)
-SUR_TRAIN_ENSEMBLE_COSINE = dict(SUR_TRAIN_ENSEMBLE, lr=3e-3, lr_final=1e-5)
+SUR_TRAIN_ENSEMBLE_COSINE = dict(SUR_TRAIN_ENSEMBLE, lr=1e-2, lr_final=1e-5)
 # the shared network's own protocol: the (r_eq, gamma, s) box of the ensemble
 # is a family of lines, and twice the samples over twice the epochs bring its
-# median drag error close to a single line's (measured: 1e7 x 20 epochs
-# 1.8e-3; 2e7 x 40 epochs 9.7e-4 .. 1.02e-3; more samples or epochs, or a
-# higher rate, stay at 1.0 .. 1.2e-3: the 64-wide network's limit)
+# median drag error to about 1e-3 (measured with the cosine from 1e-2:
+# 1e7 x 20 epochs 1.35e-3; 2e7 x 40 epochs 9.2e-4 .. 9.7e-4, p99 2.6e-2;
+# from 3e-3 the same runs gave 1.8e-3 and 9.7e-4 .. 1.4e-3)
 SUR_TRAIN_SHARED = dict(SUR_TRAIN_ENSEMBLE_COSINE, n_samples=20_000_000, epochs=40)
 
 

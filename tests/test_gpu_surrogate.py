@@ -285,32 +285,34 @@ def test_push_outside_the_training_box_uses_the_table_law():
 @pytest.mark.slow
 def test_full_training_run_holds_its_measured_accuracy():
     """The workload's training run on the r_eq = 20 line (1e7 quadrature
-    samples, 20 epochs of 8192, Adam with the cosine decay 3e-3 -> 1e-5):
-    the held-out drag error against quadrature stays at the measured
-    median <= 1e-3 (the target) and p99 <= 3.5e-2 (the tail, where the target
-    is not met), and the rate's median within 2e-3 in ln N."""
+    samples, 20 epochs of 8192, Adam with the cosine decay 1e-2 -> 1e-5):
+    the held-out drag error against quadrature stays below the target at
+    the median (measured 4.6e-4; bound 1e-3) and at its measured tail (p99
+    1.6e-2; bound 2.5e-2, where the 1e-3 target is not met), and the rate's
+    median within 1e-3 in ln N (measured 5e-4)."""
     line = _line()
     line.sur_set_params(W.sur_init_params(0))
     rep = line.train_surrogate(**W.SUR_TRAIN_COSINE)
     print({k: rep[k] for k in rep if "err" in k})
     assert rep["drag_err_median"] <= 1e-3, rep["drag_err_median"]
-    assert rep["drag_err_p99"] <= 3.5e-2, rep["drag_err_p99"]
-    assert rep["lnN_err_median"] <= 2e-3, rep["lnN_err_median"]
+    assert rep["drag_err_p99"] <= 2.5e-2, rep["drag_err_p99"]
+    assert rep["lnN_err_median"] <= 1e-3, rep["lnN_err_median"]
 
 
 @pytest.mark.slow
 def test_shared_network_holds_its_measured_accuracy():
     """One network for every line with r_eq in [2, 30] (the ensemble's),
     trained on 2e7 quadrature samples over 40 epochs of 8192 with the cosine
-    decay: held-out median drag error against quadrature <= 1.3e-3 (measured
-    9.7e-4 .. 1.02e-3 on two lines; the 1e-3 target sits at the edge of what
-    the 64-wide network reaches over the whole family of lines, while a
-    line's own network meets it), p99 <= 4.5e-2 (measured 3.8e-2)."""
+    decay from 1e-2: held-out median drag error against quadrature <= 1.3e-3
+    (measured 9.2e-4 .. 9.7e-4 on two lines; the 1e-3 target sits at the
+    edge of what the 64-wide network reaches over the whole family of lines,
+    while a line's own network meets it with room), p99 <= 3.5e-2 (measured
+    2.6e-2 .. 2.7e-2)."""
     line = _line()
     line.sur_set_params(W.sur_init_params(0))
     rep = line.train_surrogate(**W.SUR_TRAIN_SHARED)
     print({k: rep[k] for k in rep if "err" in k})
     assert rep["drag_err_median"] <= 1.3e-3, rep["drag_err_median"]
-    assert rep["drag_err_p99"] <= 4.5e-2, rep["drag_err_p99"]
+    assert rep["drag_err_p99"] <= 3.5e-2, rep["drag_err_p99"]
     assert rep["lnN_err_median"] <= 2e-3, rep["lnN_err_median"]
 
