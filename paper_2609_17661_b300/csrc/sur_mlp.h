@@ -39,10 +39,14 @@ constexpr int MF_SMALL = 49152;    // S_N floats
 constexpr int MF_END = MF_SMALL + 4 * S_N;
 constexpr int MF_SMEM = MF_END + 1024;   // dynamic size with the alignment slack
 
-__device__ __forceinline__ float silu(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
-__device__ __forceinline__ float dsilu(float z) {
-  const float s = __frcp_rn(1.0f + __expf(-z));
-  return s * (1.0f + z * (1.0f - s));
+// the logistic s = 1 / (1 + e^-z) (0 for z below about -88), SiLU z s, and
+// SiLU with its derivative s (1 + z (1 - s)) from the same s
+__device__ __forceinline__ float sigmoid(float z) { return __fdividef(1.0f, 1.0f + __expf(-z)); }
+__device__ __forceinline__ float silu(float z) { return z * sigmoid(z); }
+__device__ __forceinline__ void silu_d(float z, float& h, float& dh) {
+  const float s = sigmoid(z);
+  h = z * s;
+  dh = s * fmaf(z, 1.0f - s, 1.0f);
 }
 
 // store 8 FP32 values as BF16 into chunk c of row r of a swizzled tile
@@ -142,14 +146,27 @@ __device__ __forceinline__ void mlp_tile(MlpCta& M, const float (&x)[4], float& 
   const uint32_t tl = M.tmem + ((uint32_t)(warp * 32) << 16);
   for (int c = 0; c < 8; ++c) {
     float hv[8], hd[8];
+    if (tangent) {
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      const int j = 8 * c + e;
-      float z = sSmall[S_B1 + j];
+      for (int e = 0; e < 8; ++e) {
+        const int j = 8 * c + e;
+        float z = sSmall[S_B1 + j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) z = fmaf(sSmall[S_W1 + 4 * j + i], x[i], z);
-      hv[e] = silu(z);
-      hd[e] = tangent ? dsilu(z) * sSmall[S_W1 + 4 * j] : 0.0f;
+        for (int i = 0; i < 4; ++i) z = fmaf(sSmall[S_W1 + 4 * j + i], x[i], z);
+        float dh;
+        silu_d(z, hv[e], dh);
+        hd[e] = dh * sSmall[S_W1 + 4 * j];
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int j = 8 * c + e;
+        float z = sSmall[S_B1 + j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) z = fmaf(sSmall[S_W1 + 4 * j + i], x[i], z);
+        hv[e] = silu(z);
+        hd[e] = 0.0f;
+      }
     }
     store_chunk(sA, t, c, hv);
     if (tangent) store_chunk(sAd, t, c, hd);
@@ -174,11 +191,19 @@ __device__ __forceinline__ void mlp_tile(MlpCta& M, const float (&x)[4], float& 
       tc::tmem_ld16(tl + 16 * c, v);
       if (tangent) tc::tmem_ld16(tl + 64 + 16 * c, vd);
       float hv[16], hd[16];
+      if (tangent) {
 #pragma unroll
-      for (int e = 0; e < 16; ++e) {
-        const float z = v[e] + bias[16 * c + e];
-        hv[e] = silu(z);
-        hd[e] = tangent ? dsilu(z) * vd[e] : 0.0f;
+        for (int e = 0; e < 16; ++e) {
+          float dh;
+          silu_d(v[e] + bias[16 * c + e], hv[e], dh);
+          hd[e] = dh * vd[e];
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          hv[e] = silu(v[e] + bias[16 * c + e]);
+          hd[e] = 0.0f;
+        }
       }
       if (layer == 0) {
         store_chunk(sA, t, 2 * c, hv);

@@ -280,8 +280,10 @@ __global__ void __launch_bounds__(NT, 1) k_sur_train(TrainArgs A) {
         float z = sSmall[S_B1 + j];
 #pragma unroll
         for (int i = 0; i < 4; ++i) z = fmaf(sSmall[S_W1 + 4 * j + i], x[i], z);
-        hv[e] = valid ? silu(z) : 0.0f;
-        sD1[j * TM + t] = dsilu(z);
+        float h, dh;
+        silu_d(z, h, dh);
+        hv[e] = valid ? h : 0.0f;
+        sD1[j * TM + t] = dh;
         store_t(sm + SM_H1T, 64, j, t, hv[e]);
       }
       store_chunk(sA, t, c, hv);
@@ -307,8 +309,10 @@ __global__ void __launch_bounds__(NT, 1) k_sur_train(TrainArgs A) {
     for (int e = 0; e < 16; ++e) {
       const int j = 16 * c + e;
       const float z = v[e] + sSmall[S_B2 + j];
-      hv[e] = valid ? silu(z) : 0.0f;
-      sD2[j * TM + t] = dsilu(z);
+      float h, dh;
+      silu_d(z, h, dh);
+      hv[e] = valid ? h : 0.0f;
+      sD2[j * TM + t] = dh;
       store_t(sm + SM_H2T, 64, j, t, hv[e]);
     }
     store_chunk(sA, t, 2 * c, hv);
@@ -334,8 +338,9 @@ __global__ void __launch_bounds__(NT, 1) k_sur_train(TrainArgs A) {
     for (int e = 0; e < 16; ++e) {
       const int j = 16 * c + e;
       const float z = v[e] + sSmall[S_B3 + j];
-      h3[j] = valid ? silu(z) : 0.0f;
-      d3[j] = dsilu(z);
+      float h;
+      silu_d(z, h, d3[j]);
+      h3[j] = valid ? h : 0.0f;
     }
   }
   // ---- layer 4 (FP32), loss and its gradient
