@@ -321,11 +321,12 @@ int pic1d_variant_info(int variant, int* particles_per_thread, int* min_blocks_p
  * fixed-size device array inside this library: every GPU that loads the
  * library holds it until the process exits, so n_cells is limited to
  * PIC1D_SORT_STATIC_MAX_CELLS and larger lines are rejected with
- * PIC1D_EINVAL and a message on stderr.  The first call on a device looks up
- * the array's device address (once per device, kept for the life of the
- * process); make that first call before any stream capture, and make no call
- * on a device after cudaDeviceReset has been called on it (the reset unloads
- * the array and the kept address would then be stale).  Every call uses the same array: calls that overlap on
+ * PIC1D_EINVAL and a message on stderr.  Every call looks up the array's
+ * device address in the current context (cudaGetSymbolAddress, no stream
+ * work; after a cudaDeviceReset the module is loaded again and the new
+ * address is found); make the first call on a device outside any stream
+ * capture, since it may load the module.  Every call uses the same array:
+ * calls that overlap on
  * the GPU (on different streams, or from different host threads) race and
  * corrupt each other's results; serialise them.  The histogram is cleared
  * by each call.  Work is issued on cuda_stream (NULL: legacy default

@@ -12,7 +12,6 @@
 
 #include <algorithm>
 #include <cstdio>
-#include <mutex>
 
 #include "pic1d_internal.h"
 
@@ -39,24 +38,14 @@ constexpr size_t kScratchBytes = align_up(kOffState + sizeof(StepState));
 // from cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_sort_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
-unsigned char* g_scratch_ptr[kMaxDevices] = {nullptr};
-std::mutex g_setup_mutex;
-
-// device address of the scratch on the current device (looked up once per device)
+// device address of the scratch in the current context, looked up on every
+// call (cheap, no stream work): a cached address would go stale when the
+// context is reset and the module loaded again
 cudaError_t scratch_on_current_device(unsigned char** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_sort_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_sort_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_ptr[dev] = static_cast<unsigned char*>(p);
-  }
-  *out = g_scratch_ptr[dev];
+  *out = static_cast<unsigned char*>(p);
   return cudaSuccess;
 }
 
