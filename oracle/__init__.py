@@ -27,7 +27,10 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "pic1d_oracle.c")
-_LIB = os.path.join(_HERE, "liboracle.so")
+# a build of the same source made elsewhere (the sanitizer test's) can be
+# loaded instead through PIC1D_ORACLE_LIB
+_LIB_ENV = os.environ.get("PIC1D_ORACLE_LIB")
+_LIB = _LIB_ENV or os.path.join(_HERE, "liboracle.so")
 
 PHOTON_RADIAL, PHOTON_DISK = 0, 1
 DRAG_OFF, DRAG_CLOSED, DRAG_TABLE, DRAG_SURROGATE = 0, 1, 2, 3
@@ -39,6 +42,8 @@ S_BITS = 12
 def build(force: bool = False) -> str:
     """Compile the oracle into ``oracle/liboracle.so`` (gcc, -O2, strict FP,
     OpenMP for the step's particle blocks; one thread unless set_threads)."""
+    if _LIB_ENV:
+        return _LIB
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         subprocess.check_call(
             ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math", "-ffp-contract=off", "-fopenmp",
