@@ -62,6 +62,8 @@ extern "C" {
 #define PIC1D_ECUDA      -3   /* CUDA runtime error                       */
 #define PIC1D_ENUMERIC   -4   /* non-finite momentum met in a step        */
 #define PIC1D_ETIMEOUT   -5   /* a bounded wait inside a kernel gave up   */
+#define PIC1D_ECHECK     -6   /* checking build (PIC1D_CHECK): an index out of bounds or a
+                                 damaged guard region past a particle array */
 
 /* photon field model (Sec. 2.2, App. B.2) */
 #define PIC1D_PHOTON_RADIAL 0 /* radially streaming photons, solid angle pi/x^2 (Eq. contdrag) */

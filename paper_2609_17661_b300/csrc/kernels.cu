@@ -1245,7 +1245,8 @@ __global__ void __launch_bounds__(256) k_hist(DevParams P, uint32_t* counts) {
       const bool valid = sp[k] != PIC1D_SP_DEAD;
       const int key = valid ? sort_key(P, pos[k], sp[k], u[k]) : -1;
       const unsigned grp = __match_any_sync(0xffffffffu, key);
-      if (valid && lane == __ffs(grp) - 1) atomicAdd(counts + key, (unsigned)__popc(grp));
+      if (valid && lane == __ffs(grp) - 1 && PIC1D_BOUND(P, key < 32 * P.N, kChkSortKey))
+        atomicAdd(counts + key, (unsigned)__popc(grp));
     }
   }
 }
@@ -1369,8 +1370,8 @@ __global__ void __launch_bounds__(256) k_scatter(DevParams P, long long* cursor,
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const long long b = __shfl_sync(0xffffffffu, base[k], __ffs(grp[k]) - 1);
-      if (sp[k] != PIC1D_SP_DEAD) {
-        const long long dst = b + __popc(grp[k] & lanemask_lt());
+      const long long dst = b + __popc(grp[k] & lanemask_lt());
+      if (sp[k] != PIC1D_SP_DEAD && PIC1D_BOUND(P, dst >= 0 && dst < P.cap, kChkSortDst)) {
         pos2[dst] = pos[k];
         u2[dst] = u[k];
         w2[dst] = w[k];
@@ -1930,6 +1931,26 @@ cudaError_t launch_gauss_residual(const DevParams& P, const long long* rho, cons
   if (e != cudaSuccess) return e;
   const int grid = P.N / 256 + 1 < 1184 ? P.N / 256 + 1 : 1184;
   for (int pass = 0; pass < 2; ++pass) k_gauss_residual<<<grid, 256, 0, s>>>(P, rho, rho_ref, out2, pass);
+  return cudaGetLastError();
+}
+
+// checking build: the slack [cap, alloc) past each particle array still
+// holds its guard pattern (0xA5 bytes; removed-species code in sp)
+__global__ void k_guard_check(const uint8_t* const* arrays, const int* widths, int n_arrays, long long cap,
+                              long long alloc, unsigned* check) {
+  for (int a = 0; a < n_arrays; ++a) {
+    const int wbytes = widths[a];
+    const uint8_t want = wbytes == 1 ? (uint8_t)PIC1D_SP_DEAD : (uint8_t)0xA5;
+    const long long lo = cap * wbytes, hi = alloc * wbytes;
+    for (long long i = lo + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < hi;
+         i += (long long)gridDim.x * blockDim.x)
+      if (arrays[a][i] != want) atomicOr(check, (unsigned)kChkGuard);
+  }
+}
+
+cudaError_t launch_guard_check(const uint8_t* const* arrays, const int* widths, int n_arrays, long long cap,
+                               long long alloc, unsigned* check, cudaStream_t s) {
+  k_guard_check<<<64, 256, 0, s>>>(arrays, widths, n_arrays, cap, alloc, check);
   return cudaGetLastError();
 }
 

@@ -204,6 +204,10 @@ struct pic1d_ctx {
   // when the mark was taken
   long long* jcum = nullptr;
   long long* rho_ref = nullptr;
+  // checking build: the failed-bounds word, and the guard test's array table
+  unsigned* check = nullptr;
+  const uint8_t** guard_arrays = nullptr;
+  int* guard_widths = nullptr;
   unsigned long long* gauss_out = nullptr;
   bool gauss_on = false;
 };
@@ -274,6 +278,30 @@ int alloc_particles(pic1d_ctx* c, long long want) {
   }
   c->cap = want;
   c->alloc = cap;
+#ifdef PIC1D_CHECK
+  // the slack past the capacity: a guard pattern the step must leave alone
+  // (sp's slack already holds the removed-species code)
+  for (int b = 0; b < 2; ++b) {
+    CK(cudaMemsetAsync(c->pos[b] + want, 0xA5, (size_t)(cap - want) * sizeof(uint32_t), c->s), "guard");
+    CK(cudaMemsetAsync(c->u[b] + want, 0xA5, (size_t)(cap - want) * sizeof(float), c->s), "guard");
+    CK(cudaMemsetAsync(c->w[b] + want, 0xA5, (size_t)(cap - want) * sizeof(float), c->s), "guard");
+    CK(cudaMemsetAsync(c->id[b] + want, 0xA5, (size_t)(cap - want) * sizeof(uint64_t), c->s), "guard");
+  }
+  if (!c->guard_arrays) CK(dalloc(&c->guard_arrays, 10), "guard");
+  if (!c->guard_widths) CK(dalloc(&c->guard_widths, 10), "guard");
+  const uint8_t* arrays[10];
+  int widths[10];
+  for (int b = 0; b < 2; ++b) {
+    arrays[5 * b + 0] = reinterpret_cast<const uint8_t*>(c->pos[b]); widths[5 * b + 0] = 4;
+    arrays[5 * b + 1] = reinterpret_cast<const uint8_t*>(c->u[b]); widths[5 * b + 1] = 4;
+    arrays[5 * b + 2] = reinterpret_cast<const uint8_t*>(c->w[b]); widths[5 * b + 2] = 4;
+    arrays[5 * b + 3] = c->sp[b]; widths[5 * b + 3] = 1;
+    arrays[5 * b + 4] = reinterpret_cast<const uint8_t*>(c->id[b]); widths[5 * b + 4] = 8;
+  }
+  CK(cudaMemcpyAsync(c->guard_arrays, arrays, sizeof(arrays), cudaMemcpyHostToDevice, c->s), "guard");
+  CK(cudaMemcpyAsync(c->guard_widths, widths, sizeof(widths), cudaMemcpyHostToDevice, c->s), "guard");
+  CK(cudaStreamSynchronize(c->s), "guard");
+#endif
   return PIC1D_OK;
 }
 
@@ -331,6 +359,7 @@ DevParams dev_params(pic1d_ctx* c) {
   P.atmo_flag = c->atmo_flag;
   P.atmo_w = c->atmo_w;
   P.jcum = c->jcum;
+  P.check = c->check;
   P.dens_cur = c->dens[c->step & 1];
   P.dens_next = c->dens[(c->step + 1) & 1];
   P.cap = c->cap;
@@ -711,6 +740,10 @@ int pic1d_init(const pic1d_params* p, pic1d_ctx** out) {
     chain(dalloc(&c->E32, N));
     chain(dalloc(&c->J, N));
     chain(dalloc(&c->jcum, N));
+#ifdef PIC1D_CHECK
+    chain(dalloc(&c->check, 1));
+    if (e == cudaSuccess) chain(cudaMemsetAsync(c->check, 0, sizeof(unsigned), c->s));
+#endif
     chain(dalloc(&c->dens[0], N));
     chain(dalloc(&c->dens[1], N));
     chain(dalloc(&c->ctr, 1));
@@ -889,6 +922,11 @@ int pic1d_step(pic1d_ctx* c, int n_steps) {
                            c->sms, c->s),
          "annihilate");
     }
+#ifdef PIC1D_CHECK
+    // checking build: the slack past the particle arrays is intact
+    if (c->guard_arrays)
+      CK(launch_guard_check(c->guard_arrays, c->guard_widths, 10, c->cap, c->alloc, c->check, c->s), "guard check");
+#endif
   }
   return PIC1D_OK;
 }
@@ -972,6 +1010,20 @@ int pic1d_diag(pic1d_ctx* c, pic1d_diag_t* out) {
     out->gauss_residual_node = g[1] == ~0ull ? -1 : (int64_t)g[1];
   }
   int status = PIC1D_OK;
+#ifdef PIC1D_CHECK
+  if (c->check) {
+    unsigned chk = 0;
+    CK(cudaMemcpy(&chk, c->check, sizeof(chk), cudaMemcpyDeviceToHost), "diag check");
+    if (chk) {
+      char msg[160];
+      std::snprintf(msg, sizeof(msg), "checking build: failed bounds 0x%x (1 cell, 2 slot, 4 gather, 8 sort "
+                                      "destination, 16 sort key, 32 guard past the particle arrays)", chk);
+      c->err = msg;
+      out->status = PIC1D_ECHECK;
+      return PIC1D_ECHECK;
+    }
+  }
+#endif
   if (C.waits_timed_out) {
     // reported once: the count restarts, the context stays usable
     CK(cudaMemsetAsync(&c->ctr->waits_timed_out, 0, sizeof(unsigned long long), c->s), "diag");
@@ -2101,7 +2153,8 @@ void pic1d_free(pic1d_ctx* c) {
                   c->tpair, c->bsum, c->sur.master, c->sur.m, c->sur.v, c->sur.img, c->sur.small,
                   c->sur.part, c->sur.loss_part, c->sur.err, c->sur_gx, c->sur_gw, c->sur_grad, c->sur_loss, c->rho,
                   c->G32, c->atmo_flag, c->atmo_w, c->atmo_cells, c->atmo_target, c->ann_list, c->ann_amount,
-                  c->ann_count, c->cflag, c->dflag, c->nmu2, c->jcum, c->rho_ref, c->gauss_out};
+                  c->ann_count, c->cflag, c->dflag, c->nmu2, c->jcum, c->rho_ref, c->gauss_out, c->check,
+                  c->guard_arrays, c->guard_widths};
   for (void* q : ptrs) dfree(q);
   delete c;
   g_live.fetch_sub(1);

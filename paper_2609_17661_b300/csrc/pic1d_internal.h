@@ -59,6 +59,25 @@ struct StepState {
 };
 
 // Everything a particle kernel needs, passed by value.
+// Checking build (compiled with -DPIC1D_CHECK, libpic1d_check.so): the
+// kernels test the indexes below before they use them, record a failed test
+// as a bit of *P.check and skip the access; the host fills the slack past
+// every particle array with a guard pattern and tests it after each step.
+// In the product build the tests compile to nothing.
+enum CheckBit : unsigned {
+  kChkCell = 1u,       // a cell index from a position outside [0, N)
+  kChkSlot = 2u,       // a slot index at or past the capacity
+  kChkGather = 4u,     // a field gather outside [0, N)
+  kChkSortDst = 8u,    // a sort destination at or past the capacity
+  kChkSortKey = 16u,   // a sort key outside the histogram
+  kChkGuard = 32u,     // the guard region past a particle array was written
+};
+#ifdef PIC1D_CHECK
+#define PIC1D_BOUND(P, cond, bit) ((cond) ? true : (atomicOr((P).check, (unsigned)(bit)), false))
+#else
+#define PIC1D_BOUND(P, cond, bit) true
+#endif
+
 struct DevParams {
   int N, F;
   long long top;            // N << F
@@ -102,6 +121,7 @@ struct DevParams {
   const uint8_t* atmo_flag; // cells of the atmosphere
   long long* jcum;          // cumulative J per cell since pic1d_gauss_mark (null: not kept)
   long long* atmo_w;        // plasma weight (w_int) per cell after the move, summed by the push
+  unsigned* check;          // checking build: bits of the bounds that failed (null otherwise)
   long long cap;
   Counters* ctr;
   StepState* st;
@@ -150,6 +170,8 @@ cudaError_t launch_deposit(const DevParams& P, long long n, const long long* p0,
                            const float* w, const uint8_t* sp, long long* J, cudaStream_t s);
 cudaError_t launch_count_species(const DevParams& P, unsigned long long* out4, cudaStream_t s);
 cudaError_t launch_rho(const DevParams& P, long long* rho, int grid, cudaStream_t s);
+cudaError_t launch_guard_check(const uint8_t* const* arrays, const int* widths, int n_arrays, long long cap,
+                               long long alloc, unsigned* check, cudaStream_t s);
 cudaError_t launch_gauss_residual(const DevParams& P, const long long* rho, const long long* rho_ref,
                                   unsigned long long* out2, cudaStream_t s);
 int push_blocks_per_sm(int variant, bool nmax);

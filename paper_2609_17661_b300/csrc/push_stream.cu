@@ -101,6 +101,7 @@ __device__ __forceinline__ void stream_one(const DevParams& P, uint32_t gidx, ui
     int ig = (int)(x >> P.F);
     float f = (float)(x & fmask) * P.inv2F;
     if (ig > P.N - 2) { ig = P.N - 2; f = 1.0f; }
+    if (!PIC1D_BOUND(P, ig >= 0, kChkGather)) ig = 0;
     const float e0 = __ldg(P.E32 + ig), e1 = __ldg(P.E32 + ig + 1);
     Ep = fmaf(f, e1 - e0, e0);
     if (ATMO) {
@@ -200,7 +201,7 @@ __device__ __forceinline__ void stream_one(const DevParams& P, uint32_t gidx, ui
     o.pos = pos0 + (uint32_t)d;
     if (NMAX && lep && (cf & CF_DENSN)) {
       o.cD = (int)(o.pos >> P.F);
-      o.want_dens = __ldg(P.dens_flag + o.cD) != 0;
+      o.want_dens = PIC1D_BOUND(P, o.cD < P.N, kChkCell) && __ldg(P.dens_flag + o.cD) != 0;
     }
   }
   // 7. charge-conserving deposit: the signed length of the path inside the
@@ -339,8 +340,10 @@ __global__ void __launch_bounds__(32 * NW, 1) k_push_stream(DevParams P) {
       const float u0 = *reinterpret_cast<const float*>(st + kOffU + 4 * slot);
       const float w0 = *reinterpret_cast<const float*>(st + kOffW + 4 * slot);
       const int spk = st[kOffSp + slot];
-      const bool valid = slot < len && spk != PIC1D_SP_DEAD;
       const uint32_t gidx = base + slot;
+      const bool valid = slot < len && spk != PIC1D_SP_DEAD &&
+                         PIC1D_BOUND(P, (pos0 >> P.F) < (uint32_t)P.N, kChkCell) &&
+                         PIC1D_BOUND(P, (long long)gidx < P.cap, kChkSlot);
       SOut o;
       o.want_pair = false;
       o.want_dens = false;
