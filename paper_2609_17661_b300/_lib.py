@@ -12,7 +12,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.environ.get("PIC1D_LIB", os.path.join(HERE, "libpic1d.so"))
 
-OK, WCAPACITY, EINVAL, ENOMEM, ECUDA, ENUMERIC = 0, 1, -1, -2, -3, -4
+OK, WCAPACITY, EINVAL, ENOMEM, ECUDA, ENUMERIC, ETIMEOUT, ECHECK = 0, 1, -1, -2, -3, -4, -5, -6
 
 
 class Params(C.Structure):
