@@ -40,11 +40,11 @@ NOMINAL_HBM_GBS = 7700.0 # B300 HBM3e, nominal
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # the default push (the streaming push, k_push_stream) per slot it read, from
 # one ncu capture of the same push source on a smaller line at the same
-# density (1e8 macroparticles, 26,214 cells: 2.0638 GB for 1.0e8 slots);
+# density (1e8 macroparticles, 26,214 cells: 2.0635 GB for 1.0e8 slots);
 # traffic grows in proportion to the slots.  Reported only while the push's
 # source -- push_device.h (the per-particle physics) and push_stream.cu (the
 # kernel) -- hashes to the captured one, else null.
-PUSH_TRAFFIC = {"sources_sha256": "85ebf124c4626818298286924917d6a2818f840c0bded986ec54526d568329c9", "bytes_per_slot": 20.638}
+PUSH_TRAFFIC = {"sources_sha256": "041fbc1940114c150e0e90c928582491511929efe05fdd196824a89a8ea4b436", "bytes_per_slot": 20.635}
 PUSH_SOURCES = ("paper_2609_17661_b300/csrc/push_device.h", "paper_2609_17661_b300/csrc/push_stream.cu")
 
 
