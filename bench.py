@@ -40,11 +40,11 @@ NOMINAL_HBM_GBS = 7700.0 # B300 HBM3e, nominal
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # the default push (the streaming push, k_push_stream) per slot it read, from
 # one ncu capture of the same push source on a smaller line at the same
-# density (1e8 macroparticles, 26,214 cells: 2.0635 GB for 1.0e8 slots);
+# density (1e8 macroparticles, 26,214 cells: 2.0628 GB for 1.0e8 slots);
 # traffic grows in proportion to the slots.  Reported only while the push's
 # source -- push_device.h (the per-particle physics) and push_stream.cu (the
 # kernel) -- hashes to the captured one, else null.
-PUSH_TRAFFIC = {"sources_sha256": "041fbc1940114c150e0e90c928582491511929efe05fdd196824a89a8ea4b436", "bytes_per_slot": 20.635}
+PUSH_TRAFFIC = {"sources_sha256": "f8791427642ba7b456da2978625780b1899d01e524be9a325066877620ee081b", "bytes_per_slot": 20.628}
 PUSH_SOURCES = ("paper_2609_17661_b300/csrc/push_device.h", "paper_2609_17661_b300/csrc/push_stream.cu")
 
 

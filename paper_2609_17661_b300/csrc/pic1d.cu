@@ -497,7 +497,8 @@ int build_tables(pic1d_ctx* c) {
   std::vector<uint8_t> hc(N);
   for (int cc = 0; cc < N; ++cc)
     hc[cc] = (uint8_t)((hz[cc] ? CF_ZONE : 0) | ((cc == 0 || cc == N - 1) ? CF_WALL : 0) |
-                       ((hf[cc] || (cc > 0 && hf[cc - 1]) || (cc + 1 < N && hf[cc + 1])) ? CF_DENSN : 0));
+                       ((hf[cc] || (cc > 0 && hf[cc - 1]) || (cc + 1 < N && hf[cc + 1])) ? CF_DENSN : 0) |
+                       ((ha[cc] || (cc > 0 && ha[cc - 1]) || (cc + 1 < N && ha[cc + 1])) ? CF_ATMO : 0));
   CK(dalloc(&c->cflag, N), "alloc zone");
   CK(cudaMemcpyAsync(c->cflag, hc.data(), N, cudaMemcpyHostToDevice, c->s), "copy zone");
   std::vector<float2> hm2(N);

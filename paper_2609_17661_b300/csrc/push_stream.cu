@@ -64,6 +64,7 @@ struct SOut {
   int la, lb;             // signed path length (fixed point) in cells cl and cl + 1
   int sw;                 // q_sign * w_int
   int cD;                 // end cell (pair-cap density)
+  bool atmo;              // in or next to the atmosphere: gravity and the weight sums apply
 };
 
 // A RICS scattering of this lane's lepton (App. A): recoil in SPLIT mode,
@@ -86,7 +87,7 @@ __device__ __forceinline__ void stream_one(const DevParams& P, uint32_t gidx, ui
                                            Tally& T, float& ke, SOut& o) {
   const uint32_t fmask = (1u << P.F) - 1u;
   const uint32_t half = 1u << (P.F - 1);
-  o.lost = false; o.want_pair = false; o.want_dens = false; o.child_u = 0.0f; o.pid = 0;
+  o.lost = false; o.want_pair = false; o.want_dens = false; o.child_u = 0.0f; o.pid = 0; o.atmo = false;
   const bool ion = (sp == PIC1D_SP_ION);
   const bool lep = !ion;
   const float qm = ion ? P.qm[PIC1D_SP_ION] : (sp == PIC1D_SP_POSITRON ? 1.0f : -1.0f);
@@ -104,9 +105,11 @@ __device__ __forceinline__ void stream_one(const DevParams& P, uint32_t gidx, ui
     if (!PIC1D_BOUND(P, ig >= 0, kChkGather)) ig = 0;
     const float e0 = __ldg(P.E32 + ig), e1 = __ldg(P.E32 + ig + 1);
     Ep = fmaf(f, e1 - e0, e0);
-    if (ATMO) {
+    // gravity is zero beyond the atmosphere (and gathers as zero there)
+    if (ATMO && (cf & CF_ATMO)) {
       const float g0 = __ldg(P.G32 + ig), g1 = __ldg(P.G32 + ig + 1);
       Gp = fmaf(f, g1 - g0, g0);
+      o.atmo = true;
     }
   }
   const bool zone = (cf & CF_ZONE) != 0;
@@ -134,7 +137,9 @@ __device__ __forceinline__ void stream_one(const DevParams& P, uint32_t gidx, ui
   }
   // 2-4. Strang split: drag dt/2, Lorentz kick dt, drag dt/2
   if (cont) u = drag_half_flagged(P, S, u, T.n_lim, T.n_newt);
-  if (ATMO) u = fmaf(fmaf(qm, Ep, Gp / mass), P.dt, u);
+  // gravity's acceleration only in and next to the atmosphere (elsewhere Gp
+  // is zero and both forms give the same u)
+  if (ATMO && o.atmo) u = fmaf(fmaf(qm, Ep, Gp / mass), P.dt, u);
   else u = fmaf(qm * Ep, P.dt, u);
   if (cont) u = drag_half_flagged(P, S, u, T.n_lim, T.n_newt);
   // 5. Monte-Carlo RICS in the pair zone
@@ -348,12 +353,13 @@ __global__ void __launch_bounds__(32 * NW, 1) k_push_stream(DevParams P) {
       o.want_pair = false;
       o.want_dens = false;
       o.lost = false;
+      o.atmo = false;
       if (valid) stream_one<NMAX, ATMO>(P, gidx, pos0, u0, w0, spk & 3, T, ke, o);
       // current
       jwin_add<WARPFLUSH>(W, valid, o.cl, o.la, o.lb, o.sw, P.J, P.N);
       // plasma weight of the atmosphere cells after the move
       if (ATMO) {
-        const bool ma = valid && !o.lost && __ldg(P.atmo_flag + (o.pos >> P.F)) != 0;
+        const bool ma = valid && o.atmo && !o.lost && __ldg(P.atmo_flag + (o.pos >> P.F)) != 0;
         const unsigned am = __ballot_sync(0xffffffffu, ma);
         if (ma) {
           const int ac = (int)(o.pos >> P.F);
