@@ -44,7 +44,7 @@ NOMINAL_HBM_GBS = 7700.0 # B300 HBM3e, nominal
 # traffic grows in proportion to the slots.  Reported only while the push's
 # source -- push_device.h (the per-particle physics) and push_stream.cu (the
 # kernel) -- hashes to the captured one, else null.
-PUSH_TRAFFIC = {"sources_sha256": "f8791427642ba7b456da2978625780b1899d01e524be9a325066877620ee081b", "bytes_per_slot": 20.628}
+PUSH_TRAFFIC = {"sources_sha256": "7b818f550012d951164cdbc9ad504a30f498f9ed822ab6ae44ea0d55dad54706", "bytes_per_slot": 20.628}
 PUSH_SOURCES = ("paper_2609_17661_b300/csrc/push_device.h", "paper_2609_17661_b300/csrc/push_stream.cu")
 
 

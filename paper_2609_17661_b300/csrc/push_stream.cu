@@ -17,11 +17,14 @@
 // run through the warp's whole range in the cell order.  Per particle it runs
 // the gather, the Strang-split drag around the kick, the Monte-Carlo RICS in
 // pair zones, the move and the charge-conserving deposit with the FP32
-// arithmetic of the per-thread push of kernels.cu, with two changes that
+// arithmetic of the per-thread push of kernels.cu, with three changes that
 // remove work:
 //   * a drag half-step whose limiter test is certain to choose the damping
 //     branch (a precomputed per-(sign, s-row pair, half-octave of gamma^2)
 //     flag with a 1e-4 margin) skips the table lookup of that test;
+//   * a pair-zone lepton whose scattering probability is certainly below
+//     the draw's resolution 2^-24 (another bit of the same table) skips its
+//     rate: it cannot scatter and takes no draw;
 //   * the current goes into three int64 registers for cells B, B+1, B+2 that
 //     take every path whose lower cell is B or B+1 (a path of one step spans
 //     at most two cells); only when a path falls outside its lane's window is
