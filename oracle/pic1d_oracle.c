@@ -33,6 +33,10 @@
  *   - Newton: 4 fixed iterations from the explicit-Euler guess.
  *   - rest-frame photon direction before excitation: sign(mu_s - beta_s);
  *     de-excitation angle drawn from (3/8)(1 + cos^2).
+ *   - the scattering draw: one Philox4x32-10 block per lepton and step;
+ *     U = ((x0 >> 8) + 1) 2^-24 on (0, 1], the lepton scatters when
+ *     U <= p_sc, and no draw is made for p_sc < 2^-24 (which the 24-bit
+ *     uniform cannot resolve: such a lepton never scatters).
  *   - pair members each take half the photon momentum along s, placed at
  *     the parent's new position; none is made if that position left the line.
  *   - the pair cap compares the cell's lepton weight at the start of the
@@ -61,6 +65,11 @@
  *     left node, which deposits the current (q delta (s - c)) through the
  *     cell; then the removed positive and negative weight, equal and at one
  *     point, vanish: the discrete Gauss law holds exactly.
+ *
+ * Parity unpinned (the paper leaves them open; pinned only by internal
+ * identities): the de-excitation angular law, the pair-momentum split, the
+ * choice of omega_p in tau_min, the b convention, the initial species split
+ * and the photon model (stellar disk or radial).
  */
 #include <math.h>
 #include <stdint.h>
