@@ -1686,10 +1686,27 @@ __global__ void k_rho(DevParams P, long long* rho) {
   }
 }
 
+// live particles per species: 16 species bytes per thread and load, the
+// bytes equal to k found four at a time (__vcmpeq4 sets a matching byte to
+// 0xff, so a word's popcount is 8 per match); removed slots (255) match none
 __global__ void k_count_species(DevParams P, unsigned long long* out4) {
   const long long n = P.st->n_slots;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long nv = n / 16;
+  const uint4* sv = reinterpret_cast<const uint4*>(P.sp);
   unsigned c[4] = {0, 0, 0, 0};
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += stride) {
+    const uint4 q = __ldcs(sv + v);
+    const unsigned wd[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      unsigned bits = 0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bits += __popc(__vcmpeq4(wd[j], 0x01010101u * (unsigned)k));
+      c[k] += bits >> 3;
+    }
+  }
+  for (long long i = nv * 16 + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const uint8_t s = P.sp[i];
     if (s < 4) ++c[s];
   }
