@@ -55,6 +55,10 @@ extern "C" {
 #endif
 
 /* status codes */
+/* the most particle slots a line holds: slot indices in the kernels are
+ * 32-bit, with room for one tile of slack past the capacity */
+#define PIC1D_MAX_SLOTS  ((int64_t)2147483647 - 1048576)
+
 #define PIC1D_OK          0
 #define PIC1D_WCAPACITY   1   /* pairs/injections dropped: capacity full  */
 #define PIC1D_EINVAL     -1   /* invalid argument                         */
@@ -177,7 +181,8 @@ typedef struct pic1d_params {
   uint64_t seed;            /* Philox key                               */
   double r_star_cm;         /* stellar radius, cm                       */
   /* library */
-  int64_t capacity;         /* particle slots (0: grown on demand)      */
+  int64_t capacity;         /* particle slots (0: grown on demand); at most
+                               PIC1D_MAX_SLOTS (slot indices are 32-bit) */
   int32_t sort_every;       /* cell sort cadence in steps (>= 1)        */
   void* cuda_stream;        /* cudaStream_t for all work, may be NULL   */
 } pic1d_params;

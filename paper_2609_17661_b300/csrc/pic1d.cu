@@ -411,7 +411,9 @@ int validate(const pic1d_params* p, std::string& why) {
   if (p->annihilate_every < 0) return bad("annihilate_every must be >= 0");
   if (p->annihilate_every > 0 && !(p->n_max_ppc > 0.0)) return bad("annihilation needs n_max_ppc > 0");
   if (p->sort_every < 1) return bad("sort_every must be >= 1");
-  if (p->capacity < 0) return bad("capacity must be >= 0");
+  if (p->capacity < 0 || p->capacity > PIC1D_MAX_SLOTS) return bad("capacity must be in [0, PIC1D_MAX_SLOTS]");
+  if ((long long)p->n_cells * ((long long)p->ppc_e + p->ppc_p + p->ppc_i) > PIC1D_MAX_SLOTS)
+    return bad("the initial load exceeds PIC1D_MAX_SLOTS particles");
   if (!(p->r_star_cm > 0.0)) return bad("r_star_cm must be positive");
   return PIC1D_OK;
 }
@@ -782,7 +784,8 @@ int pic1d_init(const pic1d_params* p, pic1d_ctx** out) {
   if (rc == PIC1D_OK) {
     const long long n_load = (long long)p->n_cells * (p->ppc_e + p->ppc_p + p->ppc_i);
     const long long want = p->capacity > 0 ? std::max<long long>(p->capacity, n_load)
-                                           : (n_load > 0 ? 2 * n_load + 4 * kTile : 4 * kTile);
+                                           : std::min<long long>(n_load > 0 ? 2 * n_load + 4 * kTile : 4 * kTile,
+                                                                 PIC1D_MAX_SLOTS);
     rc = alloc_particles(c, want);
   }
   if (rc == PIC1D_OK && p->ppc_e > 0) rc = initial_load(c);
@@ -805,7 +808,9 @@ int pic1d_set_state(pic1d_ctx* c, int64_t n, const uint32_t* pos, const float* u
   if (n < 0 || (n > 0 && (!pos || !u || !w || !sp || !id)) || (mem != 0 && mem != 1) || step < 0)
     return fail(c, PIC1D_EINVAL, "set_state: bad arguments");
   const long long top = (long long)c->N << c->F;
-  const long long want = c->p.capacity > 0 ? std::max<long long>(c->p.capacity, n) : 2 * n + 4 * kTile;
+  if (n > PIC1D_MAX_SLOTS) return fail(c, PIC1D_EINVAL, "set_state: more than PIC1D_MAX_SLOTS particles");
+  const long long want = c->p.capacity > 0 ? std::max<long long>(c->p.capacity, n)
+                                           : std::min<long long>(2 * n + 4 * kTile, PIC1D_MAX_SLOTS);
   if (n > c->cap || (c->p.capacity == 0 && c->cap < want)) {
     int rc = alloc_particles(c, want);
     if (rc != PIC1D_OK) return rc;
@@ -1463,8 +1468,10 @@ int pic1d_load(pic1d_ctx* c, const char* path) {
   if (!F.get(&step, 8) || !F.get(&n, 8) || !F.get(&N, 4) || N != c->N || n < 0 || step < 0)
     return fail(c, PIC1D_EINVAL, "load: bad checkpoint header");
   if (c->p.capacity > 0 && n > c->p.capacity) return fail(c, PIC1D_EINVAL, "load: more slots than the capacity");
+  if (n > PIC1D_MAX_SLOTS) return fail(c, PIC1D_EINVAL, "load: more than PIC1D_MAX_SLOTS particles");
   if (n > c->cap) {
-    const int rc = alloc_particles(c, c->p.capacity > 0 ? c->p.capacity : 2 * n + 4 * kTile);
+    const int rc = alloc_particles(c, c->p.capacity > 0 ? c->p.capacity
+                                                      : std::min<long long>(2 * n + 4 * kTile, PIC1D_MAX_SLOTS));
     if (rc != PIC1D_OK) return rc;
   }
   CK(cudaStreamSynchronize(c->s), "load");

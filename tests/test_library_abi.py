@@ -89,6 +89,9 @@ def test_init_rejects_bad_parameters_before_any_device_work():
         dict(ppc_e=16, ppc_p=8, ppc_i=8, init_multiplicity=1.0),         # drift beta = 1/M = 1
         dict(ppc_e=16, ppc_p=8, ppc_i=8, u_sigma=-0.1),
         dict(ppc_e=-1),
+        dict(capacity=-1),
+        dict(capacity=2**31),                                            # slot indices are 32-bit
+        dict(n_cells=65536, ppc_e=32768, ppc_p=16384, ppc_i=16384),      # an initial load past the slots
     ]
     for over in bad:
         p = make_params(W.config("C1", **over))
