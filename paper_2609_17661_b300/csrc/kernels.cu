@@ -1204,16 +1204,16 @@ constexpr int kScanItems = 4;
 constexpr int kScanChunk = kScanThreads * kScanItems;
 
 // Sort key: four runs (leptons with u >= 0, u < 0, ions with u >= 0, u < 0),
-// each in cell order, and inside a cell eight bands of |u| (edges 1.5, 3,
-// 10, 30, 100, 300, 1000), so that the lanes of a warp mostly take the same branch of
+// each in cell order, and inside a cell kSortBands bands of gamma: its octave
+// (the exponent of the FP32 gamma^2 = 1 + u^2, halved), the last band open
+// (gamma >= 2^15), so that the lanes of a warp mostly take the same branch of
 // the drag update (the limiter test |F| tau_min < |u| depends on |u|).
 __device__ __forceinline__ int sort_key(const DevParams& P, uint32_t pos, uint8_t sp, float u) {
   const int cell = min((int)(pos >> P.F), P.N - 1);
   const int group = (sp == PIC1D_SP_ION ? 2 : 0) + (u < 0.0f ? 1 : 0);
-  const float au = fabsf(u);
-  const int band = (au < 1.5f) ? 0 : (au < 3.0f) ? 1 : (au < 10.0f) ? 2 : (au < 30.0f) ? 3 :
-                   (au < 100.0f) ? 4 : (au < 300.0f) ? 5 : (au < 1000.0f) ? 6 : 7;
-  return (group * P.N + cell) * 8 + band;
+  const int octave2 = (int)(__float_as_uint(fmaf(u, u, 1.0f)) >> 23) - 127;   // floor(log2 gamma^2) >= 0
+  const int band = min(octave2 >> 1, kSortBands - 1);
+  return (group * P.N + cell) * kSortBands + band;
 }
 
 // Histogram of the sort keys: K slots per thread per tile (256 K consecutive
@@ -1245,7 +1245,7 @@ __global__ void __launch_bounds__(256) k_hist(DevParams P, uint32_t* counts) {
       const bool valid = sp[k] != PIC1D_SP_DEAD;
       const int key = valid ? sort_key(P, pos[k], sp[k], u[k]) : -1;
       const unsigned grp = __match_any_sync(0xffffffffu, key);
-      if (valid && lane == __ffs(grp) - 1 && PIC1D_BOUND(P, key < 32 * P.N, kChkSortKey))
+      if (valid && lane == __ffs(grp) - 1 && PIC1D_BOUND(P, key < 4 * kSortBands * P.N, kChkSortKey))
         atomicAdd(counts + key, (unsigned)__popc(grp));
     }
   }
@@ -1390,7 +1390,7 @@ __global__ void k_sort_done(DevParams P) {
 // --------------------------------------------------------------------------
 // annihilation at n_max, right after a sort.  The sort leaves each cell's
 // leptons in two contiguous slot ranges (u >= 0 and u < 0, each over the
-// cell's eight |u| bands); `offsets` holds the end of every bin, `counts` its
+// cell's gamma bands); `offsets` holds the end of every bin, `counts` its
 // size.  k_annih_scan: one warp per cell sums the lepton, positron and
 // pair-electron weight and lists the cells above n_max with the weight A each
 // species loses.  k_annih_cell: one block per listed cell finds, per species,
@@ -1407,9 +1407,9 @@ __device__ __forceinline__ unsigned long long annih_key(unsigned long long id, l
 __device__ __forceinline__ void lepton_ranges(const DevParams& P, const uint32_t* counts, const long long* offsets,
                                               int c, long long (&a)[2], long long (&b)[2]) {
   for (int g = 0; g < 2; ++g) {
-    const int k0 = (g * P.N + c) * 8;
+    const int k0 = (g * P.N + c) * kSortBands;
     a[g] = offsets[k0] - (long long)counts[k0];
-    b[g] = offsets[k0 + 7];
+    b[g] = offsets[k0 + kSortBands - 1];
   }
 }
 
@@ -1840,7 +1840,7 @@ cudaError_t launch_field(const DevParams& P, double* E64, float* E32, double a, 
   return cudaGetLastError();
 }
 
-int sort_bins(int N) { return 32 * N; }
+int sort_bins(int N) { return 4 * kSortBands * N; }
 int scan_blocks(int N) { return (sort_bins(N) + kScanChunk - 1) / kScanChunk; }
 
 constexpr int kHistK = 8;       // slots per thread per tile of the histogram

@@ -20,7 +20,7 @@ using namespace pic1d;
 namespace {
 
 constexpr int kStaticMaxCells = PIC1D_SORT_STATIC_MAX_CELLS;
-constexpr int kStaticBins = 32 * kStaticMaxCells;          // key = ((2 * ion + (u < 0)) * n_cells + cell) * 8 + |u| band
+constexpr int kStaticBins = 4 * kSortBands * kStaticMaxCells;   // key = ((2 ion + (u < 0)) n_cells + cell) kSortBands + band
 constexpr int kStaticChunk = 4096;                         // bins per scan block
 constexpr size_t kCountsBytes = sizeof(uint32_t) * kStaticBins;
 constexpr size_t kOffsetsBytes = sizeof(long long) * (kStaticBins + 1);
