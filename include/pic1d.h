@@ -264,10 +264,10 @@ int pic1d_get_particles(pic1d_ctx* c, int64_t n, uint32_t* pos, float* u, float*
                         uint64_t* id, int mem);
 
 /* Sort the particles by cell now (histogram, scan, scatter) and drop the
- * removed slots.  Key ((2*(ion) + (u < 0)) * n_cells + cell) * 16 + band:
+ * removed slots.  Key ((2*(ion) + (u < 0)) * n_cells + cell) * 32 + band:
  * four runs (leptons moving +s, leptons moving -s, ions moving +s, ions
- * moving -s), each in cell order, and inside a cell sixteen bands of gamma,
- * band = min(floor(log2 gamma), 15) from the exponent of the FP32
+ * moving -s), each in cell order, and inside a cell 32 bands of gamma,
+ * band = min(floor(log2 gamma^2), 31) from the exponent of the FP32
  * gamma^2 = 1 + u^2 (rounded once).  The order inside a key is not fixed.
  * Asynchronous.  Errors: ECUDA. */
 int pic1d_sort(pic1d_ctx* c);
@@ -325,7 +325,7 @@ int pic1d_variant_info(int variant, int* particles_per_thread, int* min_blocks_p
  * number kept to *n_out (a device int64).  The order inside one key is not
  * specified.  Input and output arrays must not overlap.
  *
- * Its scratch (histogram, offsets, block sums, counters; about 50.3 MB) is one
+ * Its scratch (histogram, offsets, block sums, counters; about 100.7 MB) is one
  * fixed-size device array inside this library: every GPU that loads the
  * library holds it until the process exits, so n_cells is limited to
  * PIC1D_SORT_STATIC_MAX_CELLS and larger lines are rejected with

@@ -1204,15 +1204,16 @@ constexpr int kScanItems = 4;
 constexpr int kScanChunk = kScanThreads * kScanItems;
 
 // Sort key: four runs (leptons with u >= 0, u < 0, ions with u >= 0, u < 0),
-// each in cell order, and inside a cell kSortBands bands of gamma: its octave
-// (the exponent of the FP32 gamma^2 = 1 + u^2, halved), the last band open
-// (gamma >= 2^15), so that the lanes of a warp mostly take the same branch of
-// the drag update (the limiter test |F| tau_min < |u| depends on |u|).
+// each in cell order, and inside a cell kSortBands bands of gamma: the octave
+// of gamma^2 (the exponent of the FP32 gamma^2 = 1 + u^2), the last band open
+// (gamma^2 >= 2^31), so that the lanes of a warp mostly take the same branch
+// of the drag update (the limiter test |F| tau_min < |u| depends on |u|) and
+// read the same entries of the drag and branch-certainty tables.
 __device__ __forceinline__ int sort_key(const DevParams& P, uint32_t pos, uint8_t sp, float u) {
   const int cell = min((int)(pos >> P.F), P.N - 1);
   const int group = (sp == PIC1D_SP_ION ? 2 : 0) + (u < 0.0f ? 1 : 0);
   const int octave2 = (int)(__float_as_uint(fmaf(u, u, 1.0f)) >> 23) - 127;   // floor(log2 gamma^2) >= 0
-  const int band = min(octave2 >> 1, kSortBands - 1);
+  const int band = min(octave2, kSortBands - 1);
   return (group * P.N + cell) * kSortBands + band;
 }
 

@@ -24,8 +24,8 @@ constexpr uint8_t CF_ZONE = 1;       // pair zone: Monte-Carlo RICS instead of c
 constexpr uint8_t CF_WALL = 2;       // end cell: a particle can leave the line
 constexpr uint8_t CF_DENSN = 4;      // a cell of the pair cap's density within one cell
 constexpr uint8_t CF_ATMO = 8;       // an atmosphere cell within one cell (gravity, weight sums)
-// bins of the cell sort's key inside one cell (octaves of gamma, the last open)
-constexpr int kSortBands = 16;
+// bins of the cell sort's key inside one cell (octaves of gamma^2, the last open)
+constexpr int kSortBands = 32;
 // entries of the branch-certainty table
 constexpr uint8_t kDampCertain = 1;  // the limiter test chooses damping
 constexpr uint8_t kNewtonStill = 2;  // it chooses Newton, whose update leaves u unchanged in FP32

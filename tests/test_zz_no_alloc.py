@@ -17,11 +17,11 @@ torch = pytest.importorskip("torch")
 
 
 def _key(pos, sp, u, F, N):
-    # the octave of gamma: gamma^2 = 1 + u^2 rounded once to FP32 (exact in
-    # FP64 for |u| < 6e7), its exponent halved; 16 bands, the last one open
+    # the octave of gamma^2 = 1 + u^2, rounded once to FP32 (exact in FP64
+    # for |u| < 6e7): its exponent; 32 bands, the last one open
     q = (u.astype(np.float64) ** 2 + 1.0).astype(np.float32)
-    band = np.minimum(((q.view(np.uint32) >> 23).astype(np.int64) - 127) >> 1, 15)
-    return ((2 * (sp == W.SP_ION) + (u < 0)) * N + (pos.astype(np.int64) >> F)) * 16 + band
+    band = np.minimum((q.view(np.uint32) >> 23).astype(np.int64) - 127, 31)
+    return ((2 * (sp == W.SP_ION) + (u < 0)) * N + (pos.astype(np.int64) >> F)) * 32 + band
 
 
 @pytest.mark.gpu
