@@ -40,11 +40,11 @@ NOMINAL_HBM_GBS = 7700.0 # B300 HBM3e, nominal
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # the default push (the streaming push, k_push_stream) per slot it read, from
 # one ncu capture of the same push source on a smaller line at the same
-# density (1e8 macroparticles, 26,214 cells: 2.0628 GB for 1.0e8 slots);
+# density (1e8 macroparticles, 26,214 cells: 2.0616 GB for 1.0e8 slots);
 # traffic grows in proportion to the slots.  Reported only while the push's
 # source -- push_device.h (the per-particle physics) and push_stream.cu (the
 # kernel) -- hashes to the captured one, else null.
-PUSH_TRAFFIC = {"sources_sha256": "7b818f550012d951164cdbc9ad504a30f498f9ed822ab6ae44ea0d55dad54706", "bytes_per_slot": 20.628}
+PUSH_TRAFFIC = {"sources_sha256": "0db06d793185bb8f8d7ac1119b7dcd4cc9ed656666c12bdd8554a450e53fa8dc", "bytes_per_slot": 20.616}
 PUSH_SOURCES = ("paper_2609_17661_b300/csrc/push_device.h", "paper_2609_17661_b300/csrc/push_stream.cu")
 
 

@@ -133,8 +133,12 @@ __device__ __forceinline__ DragVal closed_eval(const DevParams& P, float u, cons
   return d;
 }
 
+// TBL: the caller knows the line's law is the table with the limiter on and
+// the branch-certainty table built (a push instantiated for such lines);
+// otherwise these switches are read from P.
+template <bool TBL = false>
 __device__ __forceinline__ DragVal drag_eval(const DevParams& P, float u, const Site& S, bool want_dF) {
-  if (P.drag_law == PIC1D_DRAG_TABLE) return table_eval(P, u, S.j, S.c, want_dF);
+  if (TBL || P.drag_law == PIC1D_DRAG_TABLE) return table_eval(P, u, S.j, S.c, want_dF);
   return closed_eval(P, u, S, want_dF);
 }
 
@@ -149,12 +153,13 @@ __device__ __forceinline__ DragVal drag_eval(const DevParams& P, float u, const 
 // unchanged is a fixed point and ends them).  With the limiter on, the
 // Newton branch is taken only where |h F0| < (h / tau_min) |u0|, far below
 // that bound, so one step is the whole update there.
+template <bool TBL = false>
 __device__ __forceinline__ float drag_half(const DevParams& P, const Site& S, float u0, unsigned& n_lim,
                                            unsigned& n_newt) {
   const float h = P.half_dt;
-  const DragVal d0 = drag_eval(P, u0, S, true);
+  const DragVal d0 = drag_eval<TBL>(P, u0, S, true);
   const float F0 = P.drag_k * d0.F;
-  const bool newton = !P.limiter_on || (fabsf(F0) * P.tau_min < fabsf(u0));
+  const bool newton = (!TBL && !P.limiter_on) || (fabsf(F0) * P.tau_min < fabsf(u0));
   if (newton) {
     ++n_newt;
     const float dG0 = fmaxf(1.0f - 0.5f * h * P.drag_k * d0.dF, 0.5f);
@@ -162,7 +167,7 @@ __device__ __forceinline__ float drag_half(const DevParams& P, const Site& S, fl
     if (fabsf(h * F0) > 0x1p-10f * fabsf(u0)) {
 #pragma unroll 1
       for (int it = 0; it < 4; ++it) {
-        const DragVal d1 = drag_eval(P, u1, S, true);
+        const DragVal d1 = drag_eval<TBL>(P, u1, S, true);
         const float F1 = P.drag_k * d1.F;
         const float G = u1 - u0 - 0.5f * h * (F0 + F1);
         const float dG = fmaxf(1.0f - 0.5f * h * P.drag_k * d1.dF, 0.5f);
@@ -325,9 +330,10 @@ __device__ __forceinline__ void path_lengths(int d, uint32_t frac, int F, int ce
 // damping branch for every momentum there (the damping update is
 // drag_half's), or the Newton branch with an update too small to change u in
 // FP32 (u is returned as it is), so the table lookup is skipped.
+template <bool TBL = false>
 __device__ __forceinline__ float drag_half_flagged(const DevParams& P, const Site& S, float u0, unsigned& n_lim,
                                                    unsigned& n_newt) {
-  if (P.dflag) {
+  if (TBL || P.dflag) {
     const float q = fmaf(u0, u0, 1.0f);
     const unsigned e2 = (__float_as_uint(q) >> kDampShift) - kDampE2Base;
     if (e2 < (unsigned)kDampNE) {
@@ -344,7 +350,7 @@ __device__ __forceinline__ float drag_half_flagged(const DevParams& P, const Sit
       }
     }
   }
-  return drag_half(P, S, u0, n_lim, n_newt);
+  return drag_half<TBL>(P, S, u0, n_lim, n_newt);
 }
 
 // ---------------------------------------------------------------------------

@@ -30,6 +30,10 @@
 //     at most two cells); only when a path falls outside its lane's window is
 //     the window flushed: by that lane alone, or by the whole warp as exact
 //     warp sums per cell (one 64-bit atomic per cell and warp).
+// Lines that run the table law with the limiter and the certainty table,
+// split RICS with the Monte-Carlo step and pairs on (the paper's setup) get an
+// instantiation in which those switches are constants, so that no particle
+// tests them.
 // Every wait on an mbarrier is bounded; a warp whose wait gave up records it
 // in the line's counters (pic1d_diag then reports PIC1D_ETIMEOUT) and lets
 // the copies it issued land before it stops.
@@ -73,19 +77,23 @@ struct SOut {
 // A RICS scattering of this lane's lepton (App. A): recoil in SPLIT mode,
 // true when its photon makes a pair.  Out of line: a few lanes in a million
 // scatter, and the others should not carry its arithmetic.
+template <bool TBL>
 __device__ __noinline__ bool rics_scatter(const DevParams& P, const Site& S, uint32_t ry, float& u, float& Pg) {
   const float beta = u * rsqrtf(fmaf(u, u, 1.0f));
   const float d = (S.mu > beta) ? 1.0f : -1.0f;
   const float ct = dipole_cos(unit24(ry));
   float uf, Eg;
   rics_event(S.b, d, u, ct, uf, Eg, Pg);
-  if (P.rics_mode == PIC1D_RICS_SPLIT) u = uf;
-  return P.pairs_on && Eg >= P.pair_e_thr;
+  if (TBL || P.rics_mode == PIC1D_RICS_SPLIT) u = uf;
+  return (TBL || P.pairs_on) && Eg >= P.pair_e_thr;
 }
 
 // One PIC cycle of one particle: the arithmetic of push_one (kernels.cu),
 // with the flagged drag half-step and the path split into (cl, la, lb).
-template <bool NMAX, bool ATMO>
+// TBL: the line is known to run the table law with the limiter and the
+// certainty table, split RICS with the Monte-Carlo step and pairs on (the
+// switches are then constants of the instantiation instead of tests of P).
+template <bool NMAX, bool ATMO, bool TBL>
 __device__ __forceinline__ void stream_one(const DevParams& P, uint32_t gidx, uint32_t pos0, float u, float w, int sp,
                                            Tally& T, float& ke, SOut& o) {
   const uint32_t fmask = (1u << P.F) - 1u;
@@ -116,21 +124,21 @@ __device__ __forceinline__ void stream_one(const DevParams& P, uint32_t gidx, ui
     }
   }
   const bool zone = (cf & CF_ZONE) != 0;
-  const bool drag_on = P.drag_law != PIC1D_DRAG_OFF;
-  const bool cont = lep && drag_on && (P.rics_mode == PIC1D_RICS_DRAG_PLUS_PAIRS || !zone);
-  const bool mc = lep && P.mc_on && drag_on && zone;
+  const bool drag_on = TBL || P.drag_law != PIC1D_DRAG_OFF;
+  const bool cont = lep && drag_on && ((!TBL && P.rics_mode == PIC1D_RICS_DRAG_PLUS_PAIRS) || !zone);
+  const bool mc = lep && (TBL || P.mc_on) && drag_on && zone;
   Site S;
   if (cont || mc) {
     const float f = (float)(pos0 & fmask) * P.inv2F;
     const float2 mm = __ldg(P.nmu2 + cell);
     S.mu = fmaf(f, mm.y - mm.x, mm.x);
-    if (mc || P.drag_law == PIC1D_DRAG_CLOSED) {
+    if (mc || (!TBL && P.drag_law == PIC1D_DRAG_CLOSED)) {
       const float b0 = __ldg(P.nb + cell), b1 = __ldg(P.nb + cell + 1);
       S.b = fmaf(f, b1 - b0, b0);
     } else {
       S.b = 0.0f;
     }
-    if (P.drag_law == PIC1D_DRAG_CLOSED) {
+    if (!TBL && P.drag_law == PIC1D_DRAG_CLOSED) {
       const float x0 = __ldg(P.nx + cell), x1 = __ldg(P.nx + cell + 1);
       S.x = fmaf(f, x1 - x0, x0);
     } else {
@@ -139,17 +147,17 @@ __device__ __forceinline__ void stream_one(const DevParams& P, uint32_t gidx, ui
     site_rows(P, pos0, S);
   }
   // 2-4. Strang split: drag dt/2, Lorentz kick dt, drag dt/2
-  if (cont) u = drag_half_flagged(P, S, u, T.n_lim, T.n_newt);
+  if (cont) u = drag_half_flagged<TBL>(P, S, u, T.n_lim, T.n_newt);
   // gravity's acceleration only in and next to the atmosphere (elsewhere Gp
   // is zero and both forms give the same u)
   if (ATMO && o.atmo) u = fmaf(fmaf(qm, Ep, Gp / mass), P.dt, u);
   else u = fmaf(qm * Ep, P.dt, u);
-  if (cont) u = drag_half_flagged(P, S, u, T.n_lim, T.n_newt);
+  if (cont) u = drag_half_flagged<TBL>(P, S, u, T.n_lim, T.n_newt);
   // 5. Monte-Carlo RICS in the pair zone
   bool make_pair = false;
   float Pg = 0.0f;
   bool nil = false;
-  if (mc && P.dflag) {
+  if (mc && (TBL || P.dflag)) {
     // table law: where every node the lookup can read gives p_sc < 2^-24,
     // there is no draw to make and no rate to evaluate
     const float q = fmaf(u, u, 1.0f);
@@ -160,7 +168,7 @@ __device__ __forceinline__ void stream_one(const DevParams& P, uint32_t gidx, ui
     }
   }
   if (mc && !nil) {
-    const DragVal dv = drag_eval(P, u, S, false);
+    const DragVal dv = drag_eval<TBL>(P, u, S, false);
     float psc = P.drag_k * expf(dv.lnN) * P.dt;
     if (psc > 1.0f) { psc = 1.0f; tally(T, C_CLAMP); }
     if (psc >= kDrawMin) {
@@ -170,7 +178,7 @@ __device__ __forceinline__ void stream_one(const DevParams& P, uint32_t gidx, ui
           make_uint4((uint32_t)o.pid, (uint32_t)(o.pid >> 32), (uint32_t)P.step, kTagRics), P.key0, P.key1);
       if (unit24_open(r.x) <= psc) {
         tally(T, C_SCAT);
-        make_pair = rics_scatter(P, S, r.y, u, Pg);
+        make_pair = rics_scatter<TBL>(P, S, r.y, u, Pg);
       }
     }
   }
@@ -264,7 +272,7 @@ __device__ __forceinline__ void slice_store(const DevParams& P, const uint8_t* s
 // ---------------------------------------------------------------------------
 // the kernel
 // ---------------------------------------------------------------------------
-template <int NW, bool WARPFLUSH, bool NMAX, bool ATMO>
+template <int NW, bool WARPFLUSH, bool NMAX, bool ATMO, bool TBL>
 __global__ void __launch_bounds__(32 * NW, 1) k_push_stream(DevParams P) {
   extern __shared__ uint8_t s_raw[];
   __shared__ __align__(8) uint64_t s_bar[NW][kStages];
@@ -357,7 +365,7 @@ __global__ void __launch_bounds__(32 * NW, 1) k_push_stream(DevParams P) {
       o.want_dens = false;
       o.lost = false;
       o.atmo = false;
-      if (valid) stream_one<NMAX, ATMO>(P, gidx, pos0, u0, w0, spk & 3, T, ke, o);
+      if (valid) stream_one<NMAX, ATMO, TBL>(P, gidx, pos0, u0, w0, spk & 3, T, ke, o);
       // current
       jwin_add<WARPFLUSH>(W, valid, o.cl, o.la, o.lb, o.sw, P.J, P.N);
       // plasma weight of the atmosphere cells after the move
@@ -542,10 +550,19 @@ __global__ void k_damp_flags(const float4* tpair, int Ng, int Ns, float t_scale,
 
 namespace {
 
-template <int NW, bool WF>
+// the lines the TBL instantiations serve: table law with the limiter and
+// the certainty table, split RICS, Monte-Carlo and pairs on
+bool table_line(const DevParams& P) {
+  return P.drag_law == PIC1D_DRAG_TABLE && P.dflag != nullptr && P.limiter_on && P.rics_mode == PIC1D_RICS_SPLIT &&
+         P.mc_on && P.pairs_on;
+}
+
+template <int NW, bool WF, bool TBL>
 cudaError_t launch_shape(const DevParams& P, int grid, cudaStream_t s, bool& attr) {
-  const void* ks[4] = {(const void*)k_push_stream<NW, WF, false, false>, (const void*)k_push_stream<NW, WF, true, false>,
-                       (const void*)k_push_stream<NW, WF, false, true>, (const void*)k_push_stream<NW, WF, true, true>};
+  const void* ks[4] = {(const void*)k_push_stream<NW, WF, false, false, TBL>,
+                       (const void*)k_push_stream<NW, WF, true, false, TBL>,
+                       (const void*)k_push_stream<NW, WF, false, true, TBL>,
+                       (const void*)k_push_stream<NW, WF, true, true, TBL>};
   if (!attr) {
     for (const void* k : ks) {
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, stream_smem<NW>());
@@ -561,17 +578,19 @@ cudaError_t launch_shape(const DevParams& P, int grid, cudaStream_t s, bool& att
 }  // namespace
 
 // shapes of the streaming push: 32 warps with lane-flushed current windows
-// (the fastest measured), 32 warps with warp-flushed windows, 24 warps with
-// warp-flushed windows
+// (the fastest measured; table-law lines run its TBL instantiation), 32 warps
+// with warp-flushed windows, 24 warps with warp-flushed windows
 int stream_variant_count() { return 3; }
 int stream_variant_ppl(int) { return 1; }
 
 cudaError_t launch_push_stream(const DevParams& P, int shape, int grid, cudaStream_t s) {
-  static bool attr[3] = {false, false, false};
+  static bool attr[4] = {false, false, false, false};
   switch (shape) {
-    case 0: return launch_shape<32, false>(P, grid, s, attr[0]);
-    case 1: return launch_shape<32, true>(P, grid, s, attr[1]);
-    default: return launch_shape<24, true>(P, grid, s, attr[2]);
+    case 0:
+      if (table_line(P)) return launch_shape<32, false, true>(P, grid, s, attr[3]);
+      return launch_shape<32, false, false>(P, grid, s, attr[0]);
+    case 1: return launch_shape<32, true, false>(P, grid, s, attr[1]);
+    default: return launch_shape<24, true, false>(P, grid, s, attr[2]);
   }
 }
 
