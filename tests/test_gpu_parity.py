@@ -366,6 +366,43 @@ def test_streaming_push_equals_the_per_thread_push(variant):
     assert d0["kinetic_energy"] == pytest.approx(d1["kinetic_energy"], rel=1e-6)
 
 
+def test_table_law_instantiation_equals_the_per_thread_push():
+    """On a line with the paper's setup (table law with the limiter, split
+    RICS: continuous drag outside the pair zones, Monte-Carlo scattering and
+    pairs inside them) the streaming push runs its instantiation with those
+    switches as constants; its particles, integer current, field and counts
+    equal the per-thread push's (variant 1, which tests them per particle)
+    after 25 steps with both drag branches, scattering, pairs, the pair cap,
+    losses at both walls and two sorts."""
+    cfg = W.config("C1", n_max_ppc=40.0, sort_every=10, rics_mode=O.RICS_SPLIT, b_pair_threshold=0.3,
+                   capacity=400_000)
+    N = cfg["n_cells"]
+    st = W.load_drifting_plasma(cfg)
+    beam = W.load_beam(cfg, 6000, gamma_lo=2.0, gamma_hi=3e4, seed=13)
+    beam["id"] += 10**7
+    st = {k: np.concatenate([st[k], beam[k]]) for k in st}
+    out = []
+    for v in (0, 1):
+        line = _line(cfg)
+        line.set_variant(v)
+        line.set_state(st, E=_field0(N))
+        line.step(25)
+        out.append((_by_id(line.particles()), line.fields(), line.diag()))
+        line.close()
+    (p0, (E0, J0), d0), (p1, (E1, J1), d1) = out
+    assert d0["pairs_dropped_cap"] == 0 and d1["pairs_dropped_cap"] == 0
+    for k in ("id", "pos", "u", "w", "sp"):
+        np.testing.assert_array_equal(p0[k], p1[k], err_msg=k)
+    np.testing.assert_array_equal(J0, J1)
+    np.testing.assert_array_equal(E0, E1)
+    for k in ("n_alive", "pairs_created", "pairs_rejected_nmax", "scatters", "limiter_branch", "newton_branch",
+              "lost_north", "lost_south", "rng_draws"):
+        assert d0[k] == d1[k], (k, d0[k], d1[k])
+    assert d0["limiter_branch"] > 0 and d0["newton_branch"] > 0 and d0["pairs_created"] > 0
+    assert d0["scatters"] > 0 and d0["pairs_rejected_nmax"] > 0
+    assert d0["lost_north"] > 0 and d0["lost_south"] > 0
+
+
 def test_gauss_law_integer_exact_every_step():
     """Discrete charge continuity in integers: rho(n+1) - rho(n) = -(J_i -
     J_{i-1}) at every interior node for every step, with J_int the step's own
