@@ -1732,7 +1732,8 @@ struct PushVariant {
   {PPT_, MINB_, (const void*)k_push<PPT_, MINB_, false, false, true>,                     \
    (const void*)k_push<PPT_, MINB_, true, false, true>, -1}
 // variant 0 is the streaming push (push_stream.cu: one block of 32 warps per
-// SM, lane-flushed current windows; the default); 1-4 this file's per-thread
+// SM, lane-flushed current windows, its table-law instantiation on lines with
+// the paper's setup; the default); 1-4 this file's per-thread
 // push; 5 the per-thread push with the branch-certainty table and the
 // two-anchor current window; 6, 7 other shapes of the streaming push (32
 // warps with warp-flushed windows, 24 warps)
