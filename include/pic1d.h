@@ -305,9 +305,16 @@ int pic1d_timing(pic1d_ctx* c, int on);
  * usable.  The paper has no counterpart.  Errors: EINVAL, ECUDA. */
 int pic1d_check_wait(pic1d_ctx* c, int64_t limit_clocks);
 
-/* Choose the push kernel variant: particles per thread (32- or 64-bit SoA
- * accesses) x minimum resident blocks per SM.  Results do not depend on the
- * variant (integer deposit, per-particle arithmetic).  Errors: EINVAL. */
+/* Choose the push kernel variant.  0 (the default): the streaming push, one
+ * block of 32 warps per SM staging slices of the particle arrays in shared
+ * memory by bulk copies (on a line with the table law and the limiter, split
+ * RICS, Monte-Carlo and pairs on, its instantiation with those switches as
+ * constants); 1-4: one thread per particle (or two), particles per thread x
+ * minimum resident blocks per SM as pic1d_variant_info reports them; 5: the
+ * per-thread push with the branch-certainty table and the current window;
+ * 6, 7: the streaming push with warp-collective current flushes (32 and 24
+ * warps).  Results do not depend on the variant (integer deposit, the same
+ * per-particle arithmetic).  Errors: EINVAL. */
 int pic1d_set_variant(pic1d_ctx* c, int variant);
 
 /* Describe push variant `variant`; returns the number of variants, or EINVAL.
@@ -320,7 +327,7 @@ int pic1d_variant_info(int variant, int* particles_per_thread, int* min_blocks_p
  * memory an application has reserved in full -- and so cannot create a
  * context, whose sort scratch comes from cudaMalloc.  It sorts n particles of
  * a line of n_cells cells (SoA device arrays in the layout above) by the key
- * ((2*(ion) + (u < 0)) * n_cells + cell) * 8 + band (the key of pic1d_sort), drops removed slots (species PIC1D_SP_DEAD), writes
+ * ((2*(ion) + (u < 0)) * n_cells + cell) * 32 + band (the key of pic1d_sort), drops removed slots (species PIC1D_SP_DEAD), writes
  * the sorted particles to the *_out device arrays (capacity n each) and the
  * number kept to *n_out (a device int64).  The order inside one key is not
  * specified.  Input and output arrays must not overlap.
